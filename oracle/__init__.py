@@ -1,0 +1,263 @@
+"""FP64 CPU oracle for the Gaussian-truncated short-range FMM (Wang, "A Hybrid
+Fast Multipole Method for Cosmological N-body Simulations").
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only users.  Nothing in the product
+package imports this module, and this module imports nothing from it.
+
+The C source ``orc.c`` holds the arithmetic (FP64, OpenMP); this file only
+compiles it with gcc and marshals numpy arrays through ctypes.
+
+Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
+  prefactors, derivative tensor, P2M/M2M/M2L/L2L/L2P, direct sum, tree,
+  traversal, FMM forces: pinned (closed forms, symbolic derivatives, exact
+  identities, brute force, special cases).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+_SRC = [os.path.join(_HERE, "orc.c")]
+_lock = threading.Lock()
+_lib = None
+
+# gcc flags: no FMA contraction and no fast-math, so the integer acceptance
+# decisions and the wrap come out identical on x86-64 and aarch64.
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``orc.c`` into ``oracle/_build/liborc.so`` (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(s) for s in _SRC)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *_SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_SO)
+            d, i64, i32 = C.c_double, C.c_int64, C.c_int
+            P = C.c_void_p
+            L.orc_ncoef.argtypes = [i32]
+            L.orc_ncoef.restype = i32
+            L.orc_multi_index.argtypes = [i32, P]
+            L.orc_prefactors.argtypes = [d, d, i32, P]
+            L.orc_deriv_tensor.argtypes = [P, d, i32, P]
+            L.orc_p2m.argtypes = [i64, P, P, P, i32, P]
+            L.orc_m2m.argtypes = [P, P, i32, P]
+            L.orc_m2l.argtypes = [P, P, d, i32, P]
+            L.orc_l2l.argtypes = [P, P, i32, P]
+            L.orc_l2p.argtypes = [P, P, i32, d, P, P]
+            L.orc_direct_sr.argtypes = [i64, P, P, d, d, d, d, i64, P, P]
+            L.orc_create.argtypes = [d, d, d, d, d, i32, i32, i32, i32]
+            L.orc_create.restype = P
+            L.orc_destroy.argtypes = [P]
+            L.orc_build_tree.argtypes = [P, i64, P, P]
+            L.orc_traverse.argtypes = [P]
+            L.orc_upward.argtypes = [P]
+            L.orc_m2l_pass.argtypes = [P]
+            L.orc_downward.argtypes = [P, P]
+            L.orc_p2p_pass.argtypes = [P, P]
+            L.orc_fmm_forces.argtypes = [P, P]
+            L.orc_size.argtypes = [P, i32]
+            L.orc_size.restype = i64
+            L.orc_export_particles.argtypes = [P, P, P, P]
+            L.orc_export_nodes.argtypes = [P, P]
+            L.orc_export_list.argtypes = [P, i32, P]
+            L.orc_export_expansions.argtypes = [P, i32, P]
+            L.orc_num_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+def ncoef(p: int) -> int:
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def multi_indices(p: int) -> np.ndarray:
+    """Graded multi-index order used by every expansion array: [ncoef(p)][3]."""
+    out = np.zeros((ncoef(p), 3), dtype=np.int32)
+    L = lib()
+    for c in range(ncoef(p)):
+        _check(L.orc_multi_index(c, _p(out[c])), "multi_index")
+    return out
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ---------------------------------------------------------------- kernels
+def prefactors(r: float, rs: float, p: int) -> np.ndarray:
+    """f_(0..p)(r); rs <= 0 selects the Newtonian prefactors."""
+    f = np.zeros(p + 1)
+    _check(lib().orc_prefactors(float(r), float(rs), int(p), _p(f)), "prefactors")
+    return f
+
+
+def deriv_tensor(R, rs: float, p: int) -> np.ndarray:
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    D = np.zeros(ncoef(p))
+    _check(lib().orc_deriv_tensor(_p(R), float(rs), int(p), _p(D)), "deriv_tensor")
+    return D
+
+
+def p2m(x, mu, z, p):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    M = np.zeros(ncoef(p))
+    _check(lib().orc_p2m(len(mu), _p(x), _p(mu), _p(z), p, _p(M)), "p2m")
+    return M
+
+
+def m2m(M, x, p):
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(ncoef(p))
+    _check(lib().orc_m2m(_p(M), _p(x), p, _p(out)), "m2m")
+    return out
+
+
+def m2l(M, R, rs, p, L=None):
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    L = np.zeros(ncoef(p)) if L is None else np.ascontiguousarray(L, dtype=np.float64).copy()
+    _check(lib().orc_m2l(_p(M), _p(R), float(rs), p, _p(L)), "m2l")
+    return L
+
+
+def l2l(L, x, p):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(ncoef(p))
+    _check(lib().orc_l2l(_p(L), _p(x), p, _p(out)), "l2l")
+    return out
+
+
+def l2p(L, u, p, G=1.0):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    phi = np.zeros(1)
+    a = np.zeros(3)
+    _check(lib().orc_l2p(_p(L), _p(u), p, float(G), _p(phi), _p(a)), "l2p")
+    return float(phi[0]), a
+
+
+# ---------------------------------------------------------------- direct sum
+def direct_sr(pos, mass, box, rs, rc, G=1.0, sinks=None) -> np.ndarray:
+    """Minimum-image direct truncated sum; pos [3][n] -> acc [3][nsink] (FP64)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    n = pos.shape[1]
+    if sinks is None:
+        ns, sp = n, None
+    else:
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        ns, sp = len(sinks), sinks
+    acc = np.zeros((3, ns))
+    _check(lib().orc_direct_sr(n, _p(pos), _p(mass), box, rs, rc, G, ns, _p(sp), _p(acc)), "direct_sr")
+    return acc
+
+
+# ---------------------------------------------------------------- FMM
+class FMM:
+    """FP64 truncated FMM with the same tree, MAC and lists as the GPU library."""
+
+    def __init__(self, box=1.0, rs=None, rc=None, G=1.0, theta=0.5, order=4, leaf_max=16,
+                 transition_rule=1, size_rule=1):
+        self._c = lib().orc_create(box, rs, rc, G, theta, order, leaf_max, transition_rule, size_rule)
+        if not self._c:
+            raise ValueError("invalid oracle parameters")
+        self.box, self.rs, self.rc, self.G, self.theta = box, rs, rc, G, theta
+        self.order, self.leaf_max, self.rule, self.size_rule = order, leaf_max, transition_rule, size_rule
+        self.n = 0
+
+    def __del__(self):
+        c = getattr(self, "_c", None)
+        if c:
+            lib().orc_destroy(c)
+            self._c = None
+
+    def build_tree(self, pos, mass):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        self.n = pos.shape[1]
+        _check(lib().orc_build_tree(self._c, self.n, _p(pos), _p(mass)), "build_tree")
+
+    def size(self, what):
+        return int(lib().orc_size(self._c, {"n": 0, "nodes": 1, "levels": 2, "p2p": 3, "m2l": 4}[what]))
+
+    def traverse(self):
+        _check(lib().orc_traverse(self._c), "traverse")
+
+    def forces(self) -> np.ndarray:
+        acc = np.zeros((3, self.n))
+        _check(lib().orc_fmm_forces(self._c, _p(acc)), "fmm_forces")
+        return acc
+
+    def particles(self):
+        n = self.n
+        key = np.zeros(n, dtype=np.uint64)
+        perm = np.zeros(n, dtype=np.int64)
+        xs = np.zeros((n, 3))
+        lib().orc_export_particles(self._c, _p(key), _p(perm), _p(xs))
+        return key, perm, xs
+
+    def nodes(self) -> np.ndarray:
+        out = np.zeros((self.size("nodes"), 8), dtype=np.int64)
+        lib().orc_export_nodes(self._c, _p(out))
+        return out
+
+    def lists(self):
+        p2p = np.zeros((self.size("p2p"), 3), dtype=np.int64)
+        m2l = np.zeros((self.size("m2l"), 3), dtype=np.int64)
+        lib().orc_export_list(self._c, 0, _p(p2p))
+        lib().orc_export_list(self._c, 1, _p(m2l))
+        return p2p, m2l
+
+    def expansions(self, which):
+        out = np.zeros((self.size("nodes"), ncoef(self.order)))
+        _check(lib().orc_export_expansions(self._c, {"M": 0, "L": 1}[which], _p(out)), "export_expansions")
+        return out
+
+    # phase-by-phase access for the tests
+    def upward(self):
+        _check(lib().orc_upward(self._c), "upward")
+
+    def m2l_pass(self):
+        _check(lib().orc_m2l_pass(self._c), "m2l_pass")
+
+    def downward(self):
+        a = np.zeros((self.n, 3))
+        _check(lib().orc_downward(self._c, _p(a)), "downward")
+        return a
+
+    def p2p_pass(self):
+        a = np.zeros((self.n, 3))
+        _check(lib().orc_p2p_pass(self._c, _p(a)), "p2p_pass")
+        return a

@@ -1,0 +1,823 @@
+/*
+ * FP64 CPU oracle for the Gaussian-truncated short-range FMM of
+ * "A Hybrid Fast Multipole Method for Cosmological N-body Simulations" (Wang).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * statement of what the GPU library computes.  Only the test-suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * Contents, each with the passage it follows:
+ *   - prefactors f_(k)(r) of the split kernel           Sec. 2.2, general-order equation
+ *     (Newtonian f~_(k) as the r_s -> infinity limit)   Sec. 2.1, Eq. pref
+ *   - derivative tensor D_n = grad^n psi_SR             Sec. 2.1 (after Eq. m2l), Sec. 2.2
+ *   - P2M, M2M, M2L, L2L, L2P                           Eqs. p2m, m2m, m2l, l2l, l2p
+ *   - direct truncated pair sum a = G sum m f_(1) r     Sec. 2.2, force equation g(r)
+ *   - Morton-key octree with a leaf limit               Sec. 2.1 (leaf limiter)
+ *   - dual-tree traversal with the three-rule MAC       Sec. 2.3, itemised criteria
+ *   - P2P with the hard cutoff                          Sec. 2.1 (P2P), Sec. 2.2
+ *
+ * Readings where the paper is silent or garbled (documented in the design doc):
+ *   D_n uses erfc(r/2r_s) (the factor 2 of the potential equation), is NOT
+ *   traceless, and is built from the radial derivatives f_(k) = ((1/r) d/dr)^k psi;
+ *   expansion centres are geometric; total order |n|+|m| <= p; the MAC compares
+ *   exact integer squared distances in units of L/2^22 against an FP64 threshold.
+ *
+ * Multi-index order (shared *format*, not code, with the GPU library): graded,
+ * for k = 0..p, nx = k..0, ny = k-nx..0, nz = k-nx-ny.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PMAX 10
+#define ORC_NCMAX 286 /* C(ORC_PMAX+3,3) */
+#define ORC_DEPTH 21
+#define ORC_PI 3.14159265358979323846
+
+static int g_mi[ORC_NCMAX][3];
+static int g_idx[ORC_PMAX + 1][ORC_PMAX + 1][ORC_PMAX + 1];
+static double g_fact[2 * ORC_PMAX + 2];
+
+__attribute__((constructor)) static void orc_tables(void) {
+  int c = 0;
+  for (int k = 0; k <= ORC_PMAX; ++k)
+    for (int nx = k; nx >= 0; --nx)
+      for (int ny = k - nx; ny >= 0; --ny) {
+        int nz = k - nx - ny;
+        g_mi[c][0] = nx;
+        g_mi[c][1] = ny;
+        g_mi[c][2] = nz;
+        g_idx[nx][ny][nz] = c;
+        ++c;
+      }
+  g_fact[0] = 1.0;
+  for (int i = 1; i < 2 * ORC_PMAX + 2; ++i) g_fact[i] = g_fact[i - 1] * i;
+}
+
+int orc_ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+int orc_multi_index(int c, int *n3) {
+  if (c < 0 || c >= ORC_NCMAX) return -1;
+  n3[0] = g_mi[c][0];
+  n3[1] = g_mi[c][1];
+  n3[2] = g_mi[c][2];
+  return 0;
+}
+
+static double dfact(int k) { /* k!! with (-1)!! = 0!! = 1 */
+  double r = 1.0;
+  for (int i = k; i > 1; i -= 2) r *= i;
+  return r;
+}
+
+static double ipow(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+static double mpow(const double *x, const int *n) { /* x^n for a multi-index */
+  return ipow(x[0], n[0]) * ipow(x[1], n[1]) * ipow(x[2], n[2]);
+}
+
+static double mfact(const int *n) { return g_fact[n[0]] * g_fact[n[1]] * g_fact[n[2]]; }
+
+/* ------------------------------------------------------------------------ */
+/* Prefactors.                                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * f_(k)(r) for k = 0..p.  rs > 0: the closed form of Sec. 2.2 (general order),
+ *   (-1)^k rs^(2k+1) f_(k) = (2k-1)!!/x^(2k+1) erfc(x/2)
+ *                          + sum_{q=1..k} 2^(q-k) (2k-1)!!/(2k-2q+1)!! e^(-x^2/4)/(sqrt(pi) x^(2q)),
+ *   x = r/rs.
+ * rs <= 0: the Newtonian prefactors of Eq. pref, f~_(k) = (-1)^k (2k-1)!!/r^(2k+1).
+ */
+int orc_prefactors(double r, double rs, int p, double *f) {
+  if (p < 0 || p > 2 * ORC_PMAX || !(r > 0.0)) return -1;
+  if (rs <= 0.0) {
+    for (int k = 0; k <= p; ++k) {
+      double v = dfact(2 * k - 1) / ipow(r, 2 * k + 1);
+      f[k] = (k & 1) ? -v : v;
+    }
+    return 0;
+  }
+  double x = r / rs;
+  double g = exp(-x * x / 4.0) / sqrt(ORC_PI);
+  double ec = erfc(x / 2.0);
+  for (int k = 0; k <= p; ++k) {
+    double df = dfact(2 * k - 1);
+    double s = df / ipow(x, 2 * k + 1) * ec;
+    for (int q = 1; q <= k; ++q) s += ldexp(1.0, q - k) * df / dfact(2 * k - 2 * q + 1) * g / ipow(x, 2 * q);
+    double v = s / ipow(rs, 2 * k + 1);
+    f[k] = (k & 1) ? -v : v;
+  }
+  return 0;
+}
+
+/*
+ * D_n(R) = d^n psi(R) for all |n| <= p (graded order), psi = erfc(r/2rs)/r
+ * (Newtonian 1/r if rs <= 0).  Derivative of a radial function:
+ *   d^n psi = sum_{k_d <= n_d/2} prod_d [ n_d! / (2^k_d k_d! (n_d-2k_d)!) R_d^(n_d-2k_d) ] f_(|n|-|k|)(r).
+ */
+int orc_deriv_tensor(const double *R, double rs, int p, double *D) {
+  if (p < 0 || p > ORC_PMAX) return -1;
+  double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+  double f[2 * ORC_PMAX + 1];
+  if (orc_prefactors(r, rs, p, f)) return -1;
+  int nc = orc_ncoef(p);
+  for (int c = 0; c < nc; ++c) {
+    const int *n = g_mi[c];
+    int nn = n[0] + n[1] + n[2];
+    double sum = 0.0;
+    for (int kx = 0; 2 * kx <= n[0]; ++kx)
+      for (int ky = 0; 2 * ky <= n[1]; ++ky)
+        for (int kz = 0; 2 * kz <= n[2]; ++kz) {
+          int k[3] = {kx, ky, kz};
+          double coef = 1.0;
+          for (int d = 0; d < 3; ++d)
+            coef *= g_fact[n[d]] / (ldexp(1.0, k[d]) * g_fact[k[d]] * g_fact[n[d] - 2 * k[d]]) *
+                    ipow(R[d], n[d] - 2 * k[d]);
+          sum += coef * f[nn - kx - ky - kz];
+        }
+    D[c] = sum;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Expansion operators on one cell (Sec. 2.1).                              */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. p2m: M_m(z) = sum_a mu_a (-1)^|m| / m! (x_a - z)^m, |m| <= p.  x is [n][3]. */
+int orc_p2m(int64_t n, const double *x, const double *mu, const double *z, int p, double *M) {
+  int nc = orc_ncoef(p);
+  for (int c = 0; c < nc; ++c) M[c] = 0.0;
+  for (int64_t a = 0; a < n; ++a) {
+    double d[3] = {x[3 * a] - z[0], x[3 * a + 1] - z[1], x[3 * a + 2] - z[2]};
+    for (int c = 0; c < nc; ++c) {
+      const int *m = g_mi[c];
+      double sg = ((m[0] + m[1] + m[2]) & 1) ? -1.0 : 1.0;
+      M[c] += mu[a] * sg / mfact(m) * mpow(d, m);
+    }
+  }
+  return 0;
+}
+
+/* Eq. m2m: M_m(z + x) = sum_{n <= m} x^n / n! M_{m-n}(z).  Mout is overwritten. */
+int orc_m2m(const double *Min, const double *x, int p, double *Mout) {
+  int nc = orc_ncoef(p);
+  for (int c = 0; c < nc; ++c) {
+    const int *m = g_mi[c];
+    double s = 0.0;
+    for (int nx = 0; nx <= m[0]; ++nx)
+      for (int ny = 0; ny <= m[1]; ++ny)
+        for (int nz = 0; nz <= m[2]; ++nz) {
+          int nn[3] = {nx, ny, nz};
+          s += mpow(x, nn) / mfact(nn) * Min[g_idx[m[0] - nx][m[1] - ny][m[2] - nz]];
+        }
+    Mout[c] = s;
+  }
+  return 0;
+}
+
+/* Eq. m2l: L_n += sum_{|m| <= p-|n|} M_m D_{n+m}(R), R = z_sink - z_source. */
+int orc_m2l(const double *M, const double *R, double rs, int p, double *L) {
+  double D[ORC_NCMAX];
+  if (orc_deriv_tensor(R, rs, p, D)) return -1;
+  int nc = orc_ncoef(p);
+  for (int c = 0; c < nc; ++c) {
+    const int *n = g_mi[c];
+    int rem = p - (n[0] + n[1] + n[2]);
+    double s = 0.0;
+    for (int e = 0; e < orc_ncoef(rem); ++e) {
+      const int *m = g_mi[e];
+      s += M[e] * D[g_idx[n[0] + m[0]][n[1] + m[1]][n[2] + m[2]]];
+    }
+    L[c] += s;
+  }
+  return 0;
+}
+
+/* Eq. l2l: L_n(z + x) = sum_{|m| <= p-|n|} x^m / m! L_{m+n}(z).  Lout is overwritten. */
+int orc_l2l(const double *Lin, const double *x, int p, double *Lout) {
+  int nc = orc_ncoef(p);
+  for (int c = 0; c < nc; ++c) {
+    const int *n = g_mi[c];
+    int rem = p - (n[0] + n[1] + n[2]);
+    double s = 0.0;
+    for (int e = 0; e < orc_ncoef(rem); ++e) {
+      const int *m = g_mi[e];
+      s += mpow(x, m) / mfact(m) * Lin[g_idx[n[0] + m[0]][n[1] + m[1]][n[2] + m[2]]];
+    }
+    Lout[c] = s;
+  }
+  return 0;
+}
+
+/*
+ * Eq. l2p: Psi(z + u) = sum_{|n| <= p} L_n u^n / n!, and its gradient
+ * a_i = G dPsi/du_i = G sum_{|n| <= p-1} L_{n+e_i} u^n / n!.
+ */
+int orc_l2p(const double *L, const double *u, int p, double G, double *phi, double *acc) {
+  double ph = 0.0, a[3] = {0, 0, 0};
+  for (int c = 0; c < orc_ncoef(p); ++c) {
+    const int *n = g_mi[c];
+    double t = mpow(u, n) / mfact(n);
+    ph += L[c] * t;
+    if (n[0] + n[1] + n[2] <= p - 1) {
+      a[0] += L[g_idx[n[0] + 1][n[1]][n[2]]] * t;
+      a[1] += L[g_idx[n[0]][n[1] + 1][n[2]]] * t;
+      a[2] += L[g_idx[n[0]][n[1]][n[2] + 1]] * t;
+    }
+  }
+  if (phi) *phi = G * ph;
+  for (int d = 0; d < 3; ++d) acc[d] = G * a[d];
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Periodic wrap and direct truncated sum.                                   */
+/* ------------------------------------------------------------------------ */
+
+/* x <- x - L floor(x / L): the particle's image inside the periodic box. */
+static double wrap1(double x, double box) {
+  double q = floor(x / box);
+  double t = box * q;
+  return x - t;
+}
+
+/* Pair force of Sec. 2.2: G m_j f_(1)(r) r, r = x_i - x_j, kept iff 0 < |r| < rc. */
+static void pair_acc(const double *d, double mj, double rs, double rc2, double *acc) {
+  double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  if (!(r2 > 0.0) || !(r2 < rc2)) return;
+  double f[2];
+  orc_prefactors(sqrt(r2), rs, 1, f);
+  for (int k = 0; k < 3; ++k) acc[k] += mj * f[1] * d[k];
+}
+
+/*
+ * Direct truncated short-range sum (the quantity the FMM approximates):
+ *   a_i = G sum_{j != i, 0 < |r_ij| < rc} m_j f_(1)(|r_ij|) r_ij,
+ * r_ij the minimum-image separation x_i - x_j in the periodic box of side L
+ * (rc < L/2, so that image is unique).  pos is SoA [3][n]; acc is SoA [3][nsink]
+ * for the sinks listed (all particles when sinks == NULL).  A cell list with
+ * cells of side >= rc restricts the candidates; it changes no result.
+ */
+int orc_direct_sr(int64_t n, const double *pos, const double *mass, double box, double rs, double rc,
+                  double G, int64_t nsink, const int64_t *sinks, double *acc) {
+  if (n < 0 || nsink < 0 || !(rc > 0.0) || !(rc < 0.5 * box)) return -1;
+  if (n == 0 || nsink == 0) return 0;
+  double *w = (double *)malloc(sizeof(double) * 3 * n);
+  int nc = (int)floor(box / rc);
+  if (nc < 1) nc = 1;
+  if (nc > 256) nc = 256;
+  int64_t ncell = (int64_t)nc * nc * nc;
+  int64_t *head = (int64_t *)malloc(sizeof(int64_t) * (ncell + 1));
+  int64_t *item = (int64_t *)malloc(sizeof(int64_t) * n);
+  int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * n);
+  if (!w || !head || !item || !cell) {
+    free(w); free(head); free(item); free(cell);
+    return -2;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t ci[3];
+    for (int d = 0; d < 3; ++d) {
+      w[3 * i + d] = wrap1(pos[d * n + i], box);
+      int64_t k = (int64_t)floor(w[3 * i + d] / box * nc);
+      if (k < 0) k = 0;
+      if (k > nc - 1) k = nc - 1;
+      ci[d] = k;
+    }
+    cell[i] = (ci[0] * nc + ci[1]) * nc + ci[2];
+  }
+  /* counting sort of particles by cell */
+  memset(head, 0, sizeof(int64_t) * (ncell + 1));
+  for (int64_t i = 0; i < n; ++i) head[cell[i] + 1]++;
+  for (int64_t c = 0; c < ncell; ++c) head[c + 1] += head[c];
+  {
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ncell);
+    memcpy(fill, head, sizeof(int64_t) * ncell);
+    for (int64_t i = 0; i < n; ++i) item[fill[cell[i]]++] = i;
+    free(fill);
+  }
+  double rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t s = 0; s < nsink; ++s) {
+    int64_t i = sinks ? sinks[s] : s;
+    double a[3] = {0, 0, 0};
+    int64_t c0 = cell[i];
+    int cz = (int)(c0 % nc), cy = (int)((c0 / nc) % nc), cx = (int)(c0 / ((int64_t)nc * nc));
+    /* distinct neighbour cells (fewer than 27 when nc < 3) */
+    int64_t nb[27];
+    int nnb = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          int64_t c = ((int64_t)((cx + dx + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cz + dz + nc) % nc;
+          int seen = 0;
+          for (int t = 0; t < nnb; ++t) seen |= (nb[t] == c);
+          if (!seen) nb[nnb++] = c;
+        }
+    for (int t = 0; t < nnb; ++t)
+      for (int64_t q = head[nb[t]]; q < head[nb[t] + 1]; ++q) {
+        int64_t j = item[q];
+        double d[3];
+        for (int k = 0; k < 3; ++k) {
+          double dd = w[3 * i + k] - w[3 * j + k];
+          d[k] = dd - box * nearbyint(dd / box);
+        }
+        pair_acc(d, mass[j], rs, rc2, a);
+      }
+    for (int k = 0; k < 3; ++k) acc[k * nsink + s] = G * a[k];
+  }
+  free(w); free(head); free(item); free(cell);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Octree (Sec. 2.1: tree with a leaf limiter; a Morton octree here).        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint64_t key;
+  int64_t idx;
+} keyidx;
+
+static int cmp_keyidx(const void *a, const void *b) {
+  const keyidx *x = (const keyidx *)a, *y = (const keyidx *)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+/* 63-bit Morton key: bit b of kx, ky, kz goes to bit 3b+2, 3b+1, 3b. */
+static uint64_t morton(uint32_t kx, uint32_t ky, uint32_t kz) {
+  uint64_t key = 0;
+  for (int b = 0; b < ORC_DEPTH; ++b) {
+    key |= (uint64_t)((kx >> b) & 1u) << (3 * b + 2);
+    key |= (uint64_t)((ky >> b) & 1u) << (3 * b + 1);
+    key |= (uint64_t)((kz >> b) & 1u) << (3 * b);
+  }
+  return key;
+}
+
+/* integer cell coordinate on the finest (2^21 per side) grid */
+static uint32_t grid_coord(double w, double box) {
+  double u = w / box;
+  double t = floor(u * 2097152.0);
+  if (t < 0.0) t = 0.0;
+  if (t > 2097151.0) t = 2097151.0;
+  return (uint32_t)t;
+}
+
+typedef struct {
+  /* parameters */
+  double box, rs, rc, G, theta;
+  int p, leaf_max, rule, size_rule;
+  /* particles, sorted by (key, input index) */
+  int64_t n;
+  double *x;      /* [n][3] wrapped positions */
+  double *m;      /* [n] */
+  uint64_t *key;  /* [n] */
+  int64_t *perm;  /* [n] input index of sorted particle */
+  /* nodes, breadth-first, key order within a level */
+  int64_t nnodes, ncap;
+  int nlevels;
+  int64_t level_start[ORC_DEPTH + 2];
+  int *lev;
+  uint32_t *ic; /* [nnodes][3] cell coordinate at its level */
+  int64_t *first, *count, *child_first;
+  int *nchild;
+  /* interaction lists: (sink, source, shift index 0..26) */
+  int64_t np2p, nm2l, cap_p2p, cap_m2l;
+  int64_t *p2p, *m2l;
+  /* expansions [nnodes][ncoef(p)] */
+  double *M, *L;
+  /* MAC thresholds */
+  double rc2h, theta2;
+} orc_ctx;
+
+void orc_destroy(orc_ctx *c) {
+  if (!c) return;
+  free(c->x); free(c->m); free(c->key); free(c->perm);
+  free(c->lev); free(c->ic); free(c->first); free(c->count); free(c->child_first); free(c->nchild);
+  free(c->p2p); free(c->m2l); free(c->M); free(c->L);
+  free(c);
+}
+
+/*
+ * rule: 0 = transition region S_c > R_c > S_m (as printed), 1 = S_max > R_c > S_m.
+ * size_rule: the length L in theta = L / S_c; 0 = side of the source cell (as
+ * printed), 1 = the larger side of the two cells.
+ */
+orc_ctx *orc_create(double box, double rs, double rc, double G, double theta, int p, int leaf_max, int rule,
+                    int size_rule) {
+  if (!(box > 0) || !(rs > 0) || !(rc > 0) || !(rc < 0.5 * box) || p < 1 || p > ORC_PMAX || leaf_max < 1 ||
+      (rule != 0 && rule != 1) || (size_rule != 0 && size_rule != 1) || !(theta >= 0))
+    return NULL;
+  orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  c->box = box; c->rs = rs; c->rc = rc; c->G = G; c->theta = theta;
+  c->p = p; c->leaf_max = leaf_max; c->rule = rule; c->size_rule = size_rule;
+  double t = rc * 4194304.0;
+  t = t / box;
+  c->rc2h = t * t;
+  c->theta2 = theta * theta;
+  return c;
+}
+
+static void push_node(orc_ctx *c, int lev, uint32_t ix, uint32_t iy, uint32_t iz, int64_t first, int64_t count) {
+  if (c->nnodes == c->ncap) {
+    c->ncap = c->ncap ? 2 * c->ncap : 1024;
+    c->lev = (int *)realloc(c->lev, sizeof(int) * c->ncap);
+    c->ic = (uint32_t *)realloc(c->ic, sizeof(uint32_t) * 3 * c->ncap);
+    c->first = (int64_t *)realloc(c->first, sizeof(int64_t) * c->ncap);
+    c->count = (int64_t *)realloc(c->count, sizeof(int64_t) * c->ncap);
+    c->child_first = (int64_t *)realloc(c->child_first, sizeof(int64_t) * c->ncap);
+    c->nchild = (int *)realloc(c->nchild, sizeof(int) * c->ncap);
+  }
+  int64_t k = c->nnodes++;
+  c->lev[k] = lev;
+  c->ic[3 * k] = ix; c->ic[3 * k + 1] = iy; c->ic[3 * k + 2] = iz;
+  c->first[k] = first; c->count[k] = count;
+  c->child_first[k] = -1; c->nchild[k] = 0;
+}
+
+/*
+ * Wrap, key, sort and build the octree.  A cell is split into its non-empty
+ * octants while it holds more than leaf_max particles and its level is below 21.
+ * pos is SoA [3][n].
+ */
+int orc_build_tree(orc_ctx *c, int64_t n, const double *pos, const double *mass) {
+  if (!c || n < 0) return -1;
+  free(c->x); free(c->m); free(c->key); free(c->perm);
+  c->x = NULL; c->m = NULL; c->key = NULL; c->perm = NULL;
+  c->nnodes = 0; c->nlevels = 0; c->np2p = 0; c->nm2l = 0;
+  c->n = n;
+  if (n == 0) return 0;
+  keyidx *ki = (keyidx *)malloc(sizeof(keyidx) * n);
+  double *w = (double *)malloc(sizeof(double) * 3 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t k3[3];
+    for (int d = 0; d < 3; ++d) {
+      w[3 * i + d] = wrap1(pos[d * n + i], c->box);
+      k3[d] = grid_coord(w[3 * i + d], c->box);
+    }
+    ki[i].key = morton(k3[0], k3[1], k3[2]);
+    ki[i].idx = i;
+  }
+  qsort(ki, (size_t)n, sizeof(keyidx), cmp_keyidx);
+  c->x = (double *)malloc(sizeof(double) * 3 * n);
+  c->m = (double *)malloc(sizeof(double) * n);
+  c->key = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  c->perm = (int64_t *)malloc(sizeof(int64_t) * n);
+  for (int64_t s = 0; s < n; ++s) {
+    int64_t i = ki[s].idx;
+    for (int d = 0; d < 3; ++d) c->x[3 * s + d] = w[3 * i + d];
+    c->m[s] = mass[i];
+    c->key[s] = ki[s].key;
+    c->perm[s] = i;
+  }
+  free(ki); free(w);
+
+  push_node(c, 0, 0, 0, 0, 0, n);
+  c->level_start[0] = 0;
+  int lev = 0;
+  for (;;) {
+    int64_t lo = c->level_start[lev], hi = c->nnodes;
+    c->level_start[lev + 1] = hi;
+    int any = 0;
+    for (int64_t k = lo; k < hi; ++k) {
+      if (c->count[k] <= c->leaf_max || lev >= ORC_DEPTH) continue;
+      int shift = 3 * (ORC_DEPTH - (lev + 1));
+      int64_t f = c->first[k], e = f + c->count[k];
+      c->child_first[k] = c->nnodes;
+      for (uint32_t o = 0; o < 8; ++o) {
+        int64_t a = f;
+        while (a < e && (uint32_t)((c->key[a] >> shift) & 7u) < o) ++a;
+        int64_t b = a;
+        while (b < e && (uint32_t)((c->key[b] >> shift) & 7u) == o) ++b;
+        if (b > a) {
+          push_node(c, lev + 1, 2 * c->ic[3 * k] + ((o >> 2) & 1u), 2 * c->ic[3 * k + 1] + ((o >> 1) & 1u),
+                    2 * c->ic[3 * k + 2] + (o & 1u), a, b - a);
+          c->nchild[k]++;
+          any = 1;
+        }
+      }
+    }
+    ++lev;
+    if (!any) break;
+  }
+  c->nlevels = lev;
+  c->level_start[lev] = c->nnodes;
+  return 0;
+}
+
+/* geometric centre of node k (Sec. 2.1: expansion about the geometric centre) */
+static void node_centre(const orc_ctx *c, int64_t k, double *z) {
+  double h = c->box / (double)(1u << c->lev[k]);
+  for (int d = 0; d < 3; ++d) z[d] = ((double)c->ic[3 * k + d] + 0.5) * h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dual-tree traversal with the hybrid MAC (Sec. 2.3).                       */
+/* ------------------------------------------------------------------------ */
+
+static void push3(int64_t **buf, int64_t *n, int64_t *cap, int64_t a, int64_t b, int64_t s) {
+  if (*n == *cap) {
+    *cap = *cap ? 2 * *cap : 4096;
+    *buf = (int64_t *)realloc(*buf, sizeof(int64_t) * 3 * *cap);
+  }
+  (*buf)[3 * *n] = a; (*buf)[3 * *n + 1] = b; (*buf)[3 * *n + 2] = s;
+  ++*n;
+}
+
+/*
+ * Classify an ordered (sink a, source b shifted by s*L) cell pair.
+ * Distances are exact integers in half units (L / 2^22):
+ *   S_c  = |z_b + s L - z_a|, S_m = minimum box-box distance, S_max = maximum.
+ * Returns 0 skip (S_m > R_c), 1 M2L, 2 open.
+ *   transition (must open): S_c > R_c (rule 0) or S_max > R_c (rule 1);
+ *   accept: L / S_c <= theta, i.e. (2 w)^2 <= theta^2 S_c^2, with w the half-unit
+ *   side of the source (size_rule 0) or of the larger cell (size_rule 1).
+ */
+static int mac_classify(const orc_ctx *c, int64_t a, int64_t b, int s) {
+  int64_t wa = (int64_t)1 << (ORC_DEPTH - c->lev[a]);
+  int64_t wb = (int64_t)1 << (ORC_DEPTH - c->lev[b]);
+  int sh[3] = {s / 9 - 1, (s / 3) % 3 - 1, s % 3 - 1};
+  int64_t sc2 = 0, sm2 = 0, sx2 = 0;
+  for (int d = 0; d < 3; ++d) {
+    int64_t ca = 2 * ((int64_t)c->ic[3 * a + d] * wa) + wa;
+    int64_t cb = 2 * ((int64_t)c->ic[3 * b + d] * wb) + wb + (int64_t)sh[d] * 4194304;
+    int64_t dd = cb - ca;
+    if (dd < 0) dd = -dd;
+    int64_t gap = dd - (wa + wb);
+    if (gap < 0) gap = 0;
+    int64_t far = dd + (wa + wb);
+    sc2 += dd * dd;
+    sm2 += gap * gap;
+    sx2 += far * far;
+  }
+  if ((double)sm2 > c->rc2h) return 0;
+  int trans = c->rule == 0 ? ((double)sc2 > c->rc2h) : ((double)sx2 > c->rc2h);
+  int64_t wl = (c->size_rule == 0) ? wb : (wa > wb ? wa : wb);
+  if (!trans && (double)(4 * wl * wl) <= c->theta2 * (double)sc2) return 1;
+  return 2;
+}
+
+int orc_traverse(orc_ctx *c) {
+  if (!c) return -1;
+  c->np2p = 0; c->nm2l = 0;
+  if (c->n == 0) return 0;
+  int64_t *stk = NULL, nst = 0, cst = 0;
+  for (int s = 0; s < 27; ++s) push3(&stk, &nst, &cst, 0, 0, s);
+  while (nst > 0) {
+    --nst;
+    int64_t a = stk[3 * nst], b = stk[3 * nst + 1];
+    int s = (int)stk[3 * nst + 2];
+    int cls = mac_classify(c, a, b, s);
+    if (cls == 0) continue;
+    if (cls == 1) {
+      push3(&c->m2l, &c->nm2l, &c->cap_m2l, a, b, s);
+      continue;
+    }
+    int leafa = c->nchild[a] == 0, leafb = c->nchild[b] == 0;
+    if (leafa && leafb) {
+      push3(&c->p2p, &c->np2p, &c->cap_p2p, a, b, s);
+      continue;
+    }
+    int opena, openb;
+    if (leafa) { opena = 0; openb = 1; }
+    else if (leafb) { opena = 1; openb = 0; }
+    else if (c->lev[a] < c->lev[b]) { opena = 1; openb = 0; }
+    else if (c->lev[b] < c->lev[a]) { opena = 0; openb = 1; }
+    else { opena = 1; openb = 1; }
+    int64_t a0 = opena ? c->child_first[a] : a, a1 = opena ? a0 + c->nchild[a] : a + 1;
+    int64_t b0 = openb ? c->child_first[b] : b, b1 = openb ? b0 + c->nchild[b] : b + 1;
+    for (int64_t x = a0; x < a1; ++x)
+      for (int64_t y = b0; y < b1; ++y) push3(&stk, &nst, &cst, x, y, s);
+  }
+  free(stk);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FMM passes (Sec. 2.1 order: upward, M2L, downward, P2P).                  */
+/* ------------------------------------------------------------------------ */
+
+static void shift_vec(int s, double box, double *v) {
+  v[0] = (s / 9 - 1) * box;
+  v[1] = ((s / 3) % 3 - 1) * box;
+  v[2] = (s % 3 - 1) * box;
+}
+
+int orc_upward(orc_ctx *c) {
+  if (!c) return -1;
+  int nc = orc_ncoef(c->p);
+  free(c->M);
+  c->M = (double *)calloc((size_t)(c->nnodes ? c->nnodes : 1) * nc, sizeof(double));
+  for (int l = c->nlevels - 1; l >= 0; --l) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = c->level_start[l]; k < c->level_start[l + 1]; ++k) {
+      double z[3];
+      node_centre(c, k, z);
+      if (c->nchild[k] == 0) {
+        orc_p2m(c->count[k], c->x + 3 * c->first[k], c->m + c->first[k], z, c->p, c->M + k * nc);
+      } else {
+        double tmp[ORC_NCMAX];
+        for (int64_t ch = c->child_first[k]; ch < c->child_first[k] + c->nchild[k]; ++ch) {
+          double zc[3], x[3];
+          node_centre(c, ch, zc);
+          for (int d = 0; d < 3; ++d) x[d] = z[d] - zc[d];
+          orc_m2m(c->M + ch * nc, x, c->p, tmp);
+          for (int e = 0; e < nc; ++e) c->M[k * nc + e] += tmp[e];
+        }
+      }
+    }
+  }
+  return 0;
+}
+
+static int cmp_triple(const void *a, const void *b) {
+  const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+  for (int i = 0; i < 3; ++i)
+    if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+  return 0;
+}
+
+/* sort a list by sink and return CSR offsets over nodes (caller frees) */
+static int64_t *sink_offsets(int64_t *list, int64_t n, int64_t nnodes) {
+  qsort(list, (size_t)n, 3 * sizeof(int64_t), cmp_triple);
+  int64_t *off = (int64_t *)calloc((size_t)nnodes + 1, sizeof(int64_t));
+  for (int64_t t = 0; t < n; ++t) off[list[3 * t] + 1]++;
+  for (int64_t k = 0; k < nnodes; ++k) off[k + 1] += off[k];
+  return off;
+}
+
+int orc_m2l_pass(orc_ctx *c) {
+  if (!c || !c->M) return -1;
+  int nc = orc_ncoef(c->p);
+  free(c->L);
+  c->L = (double *)calloc((size_t)(c->nnodes ? c->nnodes : 1) * nc, sizeof(double));
+  int64_t *off = sink_offsets(c->m2l, c->nm2l, c->nnodes);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t a = 0; a < c->nnodes; ++a) {
+    double za[3];
+    node_centre(c, a, za);
+    for (int64_t t = off[a]; t < off[a + 1]; ++t) {
+      int64_t b = c->m2l[3 * t + 1];
+      int s = (int)c->m2l[3 * t + 2];
+      double zb[3], sv[3], R[3];
+      node_centre(c, b, zb);
+      shift_vec(s, c->box, sv);
+      for (int d = 0; d < 3; ++d) R[d] = za[d] - (zb[d] + sv[d]);
+      orc_m2l(c->M + b * nc, R, c->rs, c->p, c->L + a * nc);
+    }
+  }
+  free(off);
+  return 0;
+}
+
+/* L2L top-down (Eq. l2l) then L2P at the leaves (Eq. l2p); acc_sorted [n][3] is overwritten. */
+int orc_downward(orc_ctx *c, double *acc_sorted) {
+  if (!c || !c->L) return -1;
+  int nc = orc_ncoef(c->p);
+  for (int l = 0; l < c->nlevels; ++l) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = c->level_start[l]; k < c->level_start[l + 1]; ++k) {
+      double z[3];
+      node_centre(c, k, z);
+      if (c->nchild[k] > 0) {
+        double tmp[ORC_NCMAX];
+        for (int64_t ch = c->child_first[k]; ch < c->child_first[k] + c->nchild[k]; ++ch) {
+          double zc[3], x[3];
+          node_centre(c, ch, zc);
+          for (int d = 0; d < 3; ++d) x[d] = zc[d] - z[d];
+          orc_l2l(c->L + k * nc, x, c->p, tmp);
+          for (int e = 0; e < nc; ++e) c->L[ch * nc + e] += tmp[e];
+        }
+      } else {
+        for (int64_t i = c->first[k]; i < c->first[k] + c->count[k]; ++i) {
+          double u[3];
+          for (int d = 0; d < 3; ++d) u[d] = c->x[3 * i + d] - z[d];
+          orc_l2p(c->L + k * nc, u, c->p, c->G, NULL, acc_sorted + 3 * i);
+        }
+      }
+    }
+  }
+  return 0;
+}
+
+/* P2P over the leaf-pair list with the hard cutoff 0 < |r| < R_c; adds into acc_sorted [n][3]. */
+int orc_p2p_pass(orc_ctx *c, double *acc_sorted) {
+  if (!c) return -1;
+  int64_t *off = sink_offsets(c->p2p, c->np2p, c->nnodes);
+  double rc2 = c->rc * c->rc;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t a = 0; a < c->nnodes; ++a) {
+    for (int64_t t = off[a]; t < off[a + 1]; ++t) {
+      int64_t b = c->p2p[3 * t + 1];
+      int s = (int)c->p2p[3 * t + 2];
+      double sv[3];
+      shift_vec(s, c->box, sv);
+      for (int64_t i = c->first[a]; i < c->first[a] + c->count[a]; ++i) {
+        double acc[3] = {0, 0, 0};
+        for (int64_t j = c->first[b]; j < c->first[b] + c->count[b]; ++j) {
+          double d[3];
+          for (int k = 0; k < 3; ++k) d[k] = c->x[3 * i + k] - (c->x[3 * j + k] + sv[k]);
+          pair_acc(d, c->m[j], c->rs, rc2, acc);
+        }
+        for (int k = 0; k < 3; ++k) acc_sorted[3 * i + k] += c->G * acc[k];
+      }
+    }
+  }
+  free(off);
+  return 0;
+}
+
+/* Whole short-range FMM; acc is SoA [3][n] in input order. */
+int orc_fmm_forces(orc_ctx *c, double *acc) {
+  if (!c) return -1;
+  int64_t n = c->n;
+  if (n == 0) return 0;
+  double *as = (double *)calloc((size_t)3 * n, sizeof(double));
+  int rc = orc_traverse(c);
+  if (!rc) rc = orc_upward(c);
+  if (!rc) rc = orc_m2l_pass(c);
+  if (!rc) rc = orc_downward(c, as);
+  if (!rc) rc = orc_p2p_pass(c, as);
+  if (!rc)
+    for (int64_t s = 0; s < n; ++s)
+      for (int d = 0; d < 3; ++d) acc[d * n + c->perm[s]] = as[3 * s + d];
+  free(as);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Export for the tests.                                                     */
+/* ------------------------------------------------------------------------ */
+
+enum { ORC_N = 0, ORC_NNODES, ORC_NLEVELS, ORC_NP2P, ORC_NM2L };
+
+int64_t orc_size(const orc_ctx *c, int what) {
+  switch (what) {
+    case ORC_N: return c->n;
+    case ORC_NNODES: return c->nnodes;
+    case ORC_NLEVELS: return c->nlevels;
+    case ORC_NP2P: return c->np2p;
+    case ORC_NM2L: return c->nm2l;
+  }
+  return -1;
+}
+
+/* keys [n] u64, perm [n] i64 */
+int orc_export_particles(const orc_ctx *c, uint64_t *key, int64_t *perm, double *xs) {
+  for (int64_t s = 0; s < c->n; ++s) {
+    if (key) key[s] = c->key[s];
+    if (perm) perm[s] = c->perm[s];
+    if (xs)
+      for (int d = 0; d < 3; ++d) xs[3 * s + d] = c->x[3 * s + d];
+  }
+  return 0;
+}
+
+/* nodes: [nnodes][8] i64 = level, ix, iy, iz, first, count, child_first(-1 for a leaf), nchild */
+int orc_export_nodes(const orc_ctx *c, int64_t *out) {
+  for (int64_t k = 0; k < c->nnodes; ++k) {
+    int64_t *o = out + 8 * k;
+    o[0] = c->lev[k];
+    o[1] = c->ic[3 * k]; o[2] = c->ic[3 * k + 1]; o[3] = c->ic[3 * k + 2];
+    o[4] = c->first[k]; o[5] = c->count[k];
+    o[6] = c->nchild[k] ? c->child_first[k] : -1;
+    o[7] = c->nchild[k];
+  }
+  return 0;
+}
+
+/* which = 0: P2P list, 1: M2L list; [len][3] i64 (sink, source, shift index) */
+int orc_export_list(const orc_ctx *c, int which, int64_t *out) {
+  int64_t n = which ? c->nm2l : c->np2p;
+  const int64_t *src = which ? c->m2l : c->p2p;
+  memcpy(out, src, sizeof(int64_t) * 3 * n);
+  return 0;
+}
+
+/* expansions: which = 0 multipoles M, 1 locals L; [nnodes][ncoef] */
+int orc_export_expansions(const orc_ctx *c, int which, double *out) {
+  const double *src = which ? c->L : c->M;
+  if (!src) return -1;
+  memcpy(out, src, sizeof(double) * c->nnodes * orc_ncoef(c->p));
+  return 0;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,213 @@
+"""Seeded synthetic particle sets shaped like the paper's workloads.
+
+The paper measures on a uniform (high-redshift) distribution and on a clustered
+z = 0 LambdaCDM snapshot (Sec. 3); neither data set is available, so these
+generators stand in for them.  This module holds no arithmetic of the method
+(no kernel, tree or expansion): it only draws positions and masses, and it is
+the one module that both the CUDA path and the FP64 oracle consume.
+
+Positions are returned as float64 SoA ``[3][N]`` in ``[0, box)``, masses as
+float32 ``[N]`` equal to ``1/N`` (total mass 1, mean density 1/box^3).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    """One workload: particle set + solver parameters."""
+
+    name: str
+    n: int
+    pm_grid: int
+    kind: str  # "uniform" | "nfw" | "zeldovich"
+    halo_count: int = 0
+    halo_frac: float = 0.0
+    order: int = 4
+    theta: float = 0.5
+    leaf_max: int = 16
+    rs_cells: float = 1.25
+    rcut_rs: float = 4.5
+    box: float = 1.0
+    seed: int = 1000
+
+    @property
+    def rs(self) -> float:
+        return self.rs_cells * (self.box / self.pm_grid)
+
+    @property
+    def rc(self) -> float:
+        return self.rcut_rs * self.rs
+
+
+CONFIGS = {
+    # uniform, N = 32^3, PM 32^3, theta 0.5, p 4
+    "uniform-32k": Config("uniform-32k", 32 ** 3, 32, "uniform", seed=1001),
+    # clustered, N = 128^3: 70% in 2000 NFW haloes, 30% uniform, PM 128^3, p 4
+    "nfw-2m": Config("nfw-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.7, seed=1002),
+    # Zel'dovich-like lattice, N = 256^3, 40% in 1000 NFW haloes, PM 256^3, p 6
+    "zeldovich-16m": Config("zeldovich-16m", 256 ** 3, 256, "zeldovich", halo_count=1000, halo_frac=0.4,
+                            order=6, seed=1003),
+    # learned-acceptance evaluation set, N = 128^3, 85% in 2000 NFW haloes
+    "nfw85-2m": Config("nfw85-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.85, seed=1004),
+    # large: 512^3 Zel'dovich + 4000 haloes (50%)
+    "zeldovich-134m": Config("zeldovich-134m", 512 ** 3, 512, "zeldovich", halo_count=4000, halo_frac=0.5,
+                             seed=1005),
+}
+
+
+def scaled(cfg: Config, n: int, pm_grid: int | None = None, **kw) -> Config:
+    """The same kind of set at another size (for fast tests)."""
+    return dataclasses.replace(cfg, n=n, pm_grid=pm_grid or cfg.pm_grid, name=f"{cfg.name}@{n}", **kw)
+
+
+def uniform(n: int, seed: int, box: float = 1.0):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((3, n)) * box
+    return pos, np.full(n, 1.0 / n, dtype=np.float32) if n else np.zeros(0, np.float32)
+
+
+def lattice(n_side: int, box: float = 1.0, offset: float = 0.5):
+    g = (np.arange(n_side, dtype=np.float64) + offset) * (box / n_side)
+    x, y, z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()])
+    n = pos.shape[1]
+    return pos, np.full(n, 1.0 / n, dtype=np.float32)
+
+
+def _nfw_mu(x):
+    return np.log1p(x) - x / (1.0 + x)
+
+
+def _nfw_radii(rng, c, count):
+    """Radii in units of r_200 drawn from the NFW enclosed-mass profile truncated at r_200."""
+    u = rng.random(count) * _nfw_mu(c)
+    lo = np.zeros(count)
+    hi = np.asarray(c, dtype=np.float64) * np.ones(count)
+    for _ in range(60):  # bisection on the monotone enclosed mass
+        mid = 0.5 * (lo + hi)
+        below = _nfw_mu(mid) < u
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return 0.5 * (lo + hi) / c
+
+
+def _halo_counts(rng, n_halo_particles, halo_count, slope=1.9, decades=3.0):
+    """Particle counts per halo with dN/dM ~ M^-slope over `decades` decades."""
+    a = slope - 1.0
+    u = rng.random(halo_count)
+    mrel = (1.0 - u * (1.0 - 10.0 ** (-a * decades))) ** (-1.0 / a)
+    w = mrel / mrel.sum() * n_halo_particles
+    cnt = np.floor(w).astype(np.int64)
+    cnt = np.maximum(cnt, 1)
+    short = n_halo_particles - cnt.sum()
+    order = np.argsort(-(w - np.floor(w)))
+    if short > 0:
+        cnt[order[:short]] += 1
+    elif short < 0:
+        big = np.argsort(-cnt)
+        i = 0
+        while short < 0:
+            if cnt[big[i % halo_count]] > 1:
+                cnt[big[i % halo_count]] -= 1
+                short += 1
+            i += 1
+    return cnt
+
+
+def place_in_haloes(pos, idx, halo_count, seed, box=1.0, n_total=None):
+    """Move particles `idx` into NFW haloes (in place).
+
+    Halo masses follow dN/dM ~ M^-1.9 over three decades, concentrations are
+    uniform in [5, 15], profiles are truncated at r_200 with
+    M = (4 pi / 3) 200 rho_mean r_200^3 (rho_mean = 1 / box^3 for unit total mass),
+    centres are uniform in the box and directions isotropic.
+    """
+    rng = np.random.default_rng(seed)
+    n_total = n_total or pos.shape[1]
+    cnt = _halo_counts(rng, len(idx), halo_count)
+    centres = rng.random((3, halo_count)) * box
+    conc = rng.uniform(5.0, 15.0, halo_count)
+    rho_mean = 1.0 / box ** 3
+    m_halo = cnt / n_total
+    r200 = (3.0 * m_halo / (4.0 * np.pi * 200.0 * rho_mean)) ** (1.0 / 3.0)
+    h_of = np.repeat(np.arange(halo_count), cnt)
+    r = _nfw_radii(rng, conc[h_of], len(idx)) * r200[h_of]
+    d = rng.standard_normal((3, len(idx)))
+    d /= np.linalg.norm(d, axis=0, keepdims=True)
+    p = centres[:, h_of] + r * d
+    pos[:, idx] = np.mod(p, box)
+    return pos
+
+
+def nfw_clustered(n: int, halo_count: int, halo_frac: float, seed: int, box: float = 1.0):
+    pos, mass = uniform(n, seed, box)
+    rng = np.random.default_rng(seed + 7)
+    nh = int(round(halo_frac * n))
+    idx = rng.permutation(n)[:nh]
+    place_in_haloes(pos, idx, halo_count, seed + 11, box)
+    return pos, mass
+
+
+def zeldovich(n_side: int, seed: int, box: float = 1.0, rms_spacing: float = 0.3, halo_count: int = 0,
+              halo_frac: float = 0.0):
+    """Cubic lattice displaced by a Gaussian field with P(k) ~ k^-2 exp(-(k/k_Nyq)^2).
+
+    The displacement is psi(k) = i k delta(k) / k^2, rescaled so that the RMS of
+    |psi| is `rms_spacing` lattice spacings; then a random `halo_frac` of the
+    particles is moved into NFW haloes.
+    """
+    rng = np.random.default_rng(seed)
+    n = n_side ** 3
+    pos, mass = lattice(n_side, box, offset=0.0)
+    white = rng.standard_normal((n_side, n_side, n_side)).astype(np.float32)
+    dk = np.fft.rfftn(white)
+    del white
+    kf = np.fft.fftfreq(n_side) * n_side
+    kr = np.fft.rfftfreq(n_side) * n_side
+    kx = kf[:, None, None].astype(np.float32)
+    ky = kf[None, :, None].astype(np.float32)
+    kz = kr[None, None, :].astype(np.float32)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    knyq = n_side / 2.0
+    amp = np.sqrt(k2 ** -1.0 * np.exp(-k2 / knyq ** 2)).astype(np.float32)
+    amp[0, 0, 0] = 0.0
+    dk *= amp
+    del amp
+    disp = []
+    for kk in (kx, ky, kz):
+        psi_k = 1j * kk * dk / k2
+        disp.append(np.fft.irfftn(psi_k, s=(n_side,) * 3).astype(np.float64).ravel())
+        del psi_k
+    disp = np.stack(disp)
+    rms = np.sqrt((disp ** 2).sum(axis=0).mean())
+    disp *= rms_spacing * (box / n_side) / max(rms, 1e-300)
+    pos = np.mod(pos + disp, box)
+    if halo_count and halo_frac > 0:
+        nh = int(round(halo_frac * n))
+        idx = np.random.default_rng(seed + 7).permutation(n)[:nh]
+        place_in_haloes(pos, idx, halo_count, seed + 11, box)
+    return pos, mass
+
+
+def make(cfg: Config):
+    """Positions [3][N] float64 and masses [N] float32 for a config."""
+    if cfg.kind == "uniform":
+        return uniform(cfg.n, cfg.seed, cfg.box)
+    if cfg.kind == "nfw":
+        return nfw_clustered(cfg.n, cfg.halo_count, cfg.halo_frac, cfg.seed, cfg.box)
+    if cfg.kind == "zeldovich":
+        side = round(cfg.n ** (1.0 / 3.0))
+        assert side ** 3 == cfg.n
+        return zeldovich(side, cfg.seed, cfg.box, halo_count=cfg.halo_count, halo_frac=cfg.halo_frac)
+    raise ValueError(cfg.kind)
+
+
+def subsample(n: int, k: int, seed: int) -> np.ndarray:
+    """Seeded sink subsample (sorted indices) for oracle checks at large N."""
+    k = min(k, n)
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False)).astype(np.int64)
