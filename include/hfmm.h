@@ -1,0 +1,163 @@
+/*
+ * hfmm.h - C ABI of libhfmm.so, a GB300 (sm_103a) implementation of the
+ * Gaussian-truncated short-range fast multipole method of Wang, "A Hybrid Fast
+ * Multipole Method for Cosmological N-body Simulations" (Secs. 2.1-2.3), with a
+ * plain particle-mesh long-range part (Sec. 2.2, PM filter).
+ *
+ * Problem (Sec. 2.2): N particles with masses m_j and positions x_j in a
+ * periodic cube of side L.  Gravity is split at the scale r_s; this library
+ * computes the short-range acceleration
+ *     a_i = G sum_{j != i, 0 < |r_ij| < R_c} m_j f_(1)(|r_ij|) r_ij,
+ *     f_(1)(r) = -[erfc(r / 2r_s) + r / (r_s sqrt(pi)) exp(-r^2 / 4r_s^2)] / r^3,
+ * r_ij the minimum-image separation x_i - x_j, approximated by a truncated FMM:
+ * Morton octree, P2M/M2M (Eqs. p2m, m2m), dual-tree traversal with the
+ * three-rule acceptance criterion (Sec. 2.3), M2L with the derivative tensors
+ * of erfc(r/2r_s)/r (Eq. m2l and the general-order prefactors of Sec. 2.2),
+ * L2L/L2P (Eqs. l2l, l2p) and a cut-off P2P sum.
+ *
+ * Conventions for every entry point:
+ *  - Return value: HFMM_OK (0) or a negative HFMM_ERR_* code; no exception or
+ *    abort crosses the ABI.  hfmm_last_error() gives a message.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls may synchronise the stream where
+ *    their documentation says so (data-dependent sizes).
+ *  - Device pointers belong to the caller, must stay valid until the call's
+ *    work on `stream` has completed, and are never freed by the library.
+ *    Library workspaces (tree, lists, expansions) belong to the context and
+ *    grow on demand; they are released by hfmm_destroy().
+ *  - Positions are FP64 structure-of-arrays [3][n] (x block, y block, z
+ *    block); masses FP32 [n]; accelerations FP32 SoA [3][n], in the caller's
+ *    particle order.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef HFMM_H
+#define HFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HFMM_OK = 0,
+  HFMM_ERR_ARG = -1,      /* invalid argument (null pointer, bad size or parameter) */
+  HFMM_ERR_OOM = -2,      /* device or host allocation failed */
+  HFMM_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  HFMM_ERR_CAPACITY = -4, /* an index format limit was exceeded (e.g. > 2^27 tree nodes) */
+  HFMM_ERR_STATE = -5,    /* call out of order (e.g. forces before build_tree) */
+  HFMM_ERR_TIMEOUT = -6   /* a bounded device-side wait gave up */
+};
+
+/* Solver parameters.  r_s = rs_cells * box / pm_grid (Sec. 2.2: r_s ~ 1.2 grid
+ * cells), R_c = rcut_rs * r_s (Sec. 2.2: cut-off ~ 5 r_s), R_c < box / 2. */
+typedef struct {
+  double box;          /* L, side of the periodic cube */
+  int pm_grid;         /* N_g, PM mesh cells per side */
+  double rs_cells;     /* r_s in PM cells */
+  double rcut_rs;      /* R_c in units of r_s */
+  double G;            /* gravitational constant */
+  double theta;        /* opening angle theta_MAC of Sec. 2.3 (0 = never accept M2L) */
+  int order;           /* expansion order p, 1..8 (total order |n| + |m| <= p) */
+  int leaf_max;        /* a cell is split while it holds more than leaf_max particles (1..64) */
+  int mac_mode;        /* 0 = geometric acceptance (Sec. 2.3) */
+  int transition_rule; /* 0: open iff S_c > R_c >= S_m (Sec. 2.3 as printed);
+                          1: open iff S_max > R_c >= S_m (every M2L pair lies within R_c) */
+  int size_rule;       /* L in theta = L / S_c: 0 = side of the source cell (as printed),
+                          1 = larger side of the two cells */
+  int m2l_precision;   /* 0 = FP32 CUDA cores */
+  int profile;         /* 1 = record per-phase CUDA-event timings (hfmm_get_stats) */
+} hfmm_params;
+
+/* Counters and timings of the last build_tree / short_range_forces call. */
+typedef struct {
+  int64_t n, nnodes, nleaves;
+  int32_t nlevels, traverse_iters;
+  int64_t np2p;           /* P2P leaf pairs */
+  int64_t nm2l;           /* M2L cell pairs */
+  int64_t p2p_particle_pairs; /* particle pairs evaluated by P2P (incl. masked) */
+  /* milliseconds, filled when params.profile = 1 (else -1) */
+  float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
+} hfmm_stats;
+
+typedef struct hfmm_ctx hfmm_ctx;
+
+/* Default parameters of the small uniform workload: box 1, PM 32^3, r_s 1.25
+ * cells, R_c 4.5 r_s, G 1, theta 0.5, p 4, 16 particles per leaf. */
+void hfmm_default_params(hfmm_params *out);
+
+/* Create a context on the current CUDA device.  Validates *params
+ * (HFMM_ERR_ARG on a bad value).  *out receives the context. */
+int hfmm_create(const hfmm_params *params, hfmm_ctx **out);
+
+/* Release every library-owned buffer.  NULL is accepted. */
+void hfmm_destroy(hfmm_ctx *ctx);
+
+/* Message of the last failing call on ctx (or of hfmm_create when ctx is NULL). */
+const char *hfmm_last_error(const hfmm_ctx *ctx);
+
+/*
+ * Build the octree (Sec. 2.1; a Morton-key octree): wrap positions into the
+ * box (x - L floor(x / L)), 63-bit Morton keys on a 2^21 grid per side, stable
+ * sort by (key, input index), split cells holding more than leaf_max particles
+ * (depth cap 21), per-particle FP32 offsets from the geometric leaf centre.
+ * pos_soa: device FP64 [3][n]; mass: device FP32 [n]; n >= 0 (n = 0 gives an
+ * empty tree).  Synchronises `stream` once per tree level.  The library keeps
+ * no reference to pos/mass after the call returns.
+ */
+int hfmm_build_tree(hfmm_ctx *ctx, const double *pos_soa, const float *mass, int64_t n, void *stream);
+
+/*
+ * Short-range accelerations of the particles of the last hfmm_build_tree:
+ * P2M, M2M, dual-tree traversal with the hybrid acceptance rules, M2L, L2L,
+ * L2P and the cut-off P2P (Secs. 2.1-2.3).  acc_soa: device FP32 [3][n], input
+ * particle order, overwritten.  HFMM_ERR_STATE before any build_tree.
+ * Synchronises `stream` once per traversal level.
+ */
+int hfmm_short_range_forces(hfmm_ctx *ctx, float *acc_soa, void *stream);
+
+/*
+ * The same computation on HOST buffers: copies pos_soa (FP64 [3][n]) and mass
+ * (FP32 [n]) to library-owned device memory, builds the tree, computes the
+ * short-range accelerations and copies them to acc_soa (host FP32 [3][n]).
+ * Returns after the result is on the host.  Pinned host memory gives
+ * asynchronous copies; pageable memory works too.
+ */
+int hfmm_short_range_forces_host(hfmm_ctx *ctx, const double *pos_soa, const float *mass, int64_t n,
+                                 float *acc_soa, void *stream);
+
+/* Counters and timings of the last calls (synchronises the context's work). */
+int hfmm_get_stats(hfmm_ctx *ctx, hfmm_stats *out);
+
+/*
+ * Copy an internal array to host memory for inspection.  With host_buf NULL,
+ * *bytes receives the size needed; otherwise at most *bytes are copied and
+ * *bytes receives the size.  Synchronises the device.  Formats:
+ *  HFMM_EXPORT_KEYS     uint64 [n]      Morton keys in sorted order
+ *  HFMM_EXPORT_PERM     uint32 [n]      input index of each sorted particle
+ *  HFMM_EXPORT_NODES    int64 [nnodes][8] level, ix, iy, iz, first, count,
+ *                                       first child (-1 for a leaf), child count;
+ *                                       breadth-first, key order within a level
+ *  HFMM_EXPORT_P2P      int64 [np2p][3]  sink node, source node, shift index
+ *  HFMM_EXPORT_M2L      int64 [nm2l][3]  (shift index s: (sx+1)*9+(sy+1)*3+(sz+1),
+ *                                       the source is displaced by s * L)
+ *  HFMM_EXPORT_MULTIPOLES float [nnodes][ncoef(p)]  M_m / h^|m|   (h = cell side)
+ *  HFMM_EXPORT_LOCALS     float [nnodes][ncoef(p)]  L_n * h^(|n|+1)
+ * Multi-index order: for k = 0..p, nx = k..0, ny = k-nx..0, nz = k-nx-ny.
+ */
+enum {
+  HFMM_EXPORT_KEYS = 0,
+  HFMM_EXPORT_PERM = 1,
+  HFMM_EXPORT_NODES = 2,
+  HFMM_EXPORT_P2P = 3,
+  HFMM_EXPORT_M2L = 4,
+  HFMM_EXPORT_MULTIPOLES = 5,
+  HFMM_EXPORT_LOCALS = 6
+};
+int hfmm_export(hfmm_ctx *ctx, int what, void *host_buf, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFMM_H */

@@ -1,0 +1,292 @@
+// C ABI of libhfmm (declared in include/hfmm.h): context lifecycle, argument
+// checks, error mapping, phase orchestration, statistics and exports.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace hfmm;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(Ctx &c, int code, const std::string &msg) {
+  c.err = msg;
+  return code;
+}
+
+int cuda_fail(Ctx &c, cudaError_t e, const char *where) {
+  int code = e == cudaErrorMemoryAllocation ? HFMM_ERR_OOM : HFMM_ERR_CUDA;
+  c.err = std::string(where) + ": " + cudaGetErrorString(e);
+  return code;
+}
+
+cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+bool valid_params(const hfmm_params &p, std::string &why) {
+  if (!(p.box > 0)) return why = "box must be > 0", false;
+  if (p.pm_grid < 1) return why = "pm_grid must be >= 1", false;
+  if (!(p.rs_cells > 0)) return why = "rs_cells must be > 0", false;
+  if (!(p.rcut_rs > 0)) return why = "rcut_rs must be > 0", false;
+  if (!(p.theta >= 0) || p.theta > 1.0) return why = "theta must be in [0, 1]", false;
+  if (p.order < 1 || p.order > kPMax) return why = "order must be in 1..8", false;
+  if (p.leaf_max < 1 || p.leaf_max > 64) return why = "leaf_max must be in 1..64", false;
+  if (p.mac_mode != 0) return why = "mac_mode must be 0 (geometric)", false;
+  if (p.transition_rule != 0 && p.transition_rule != 1) return why = "transition_rule must be 0 or 1", false;
+  if (p.size_rule != 0 && p.size_rule != 1) return why = "size_rule must be 0 or 1", false;
+  if (p.m2l_precision != 0) return why = "m2l_precision must be 0", false;
+  double rs = p.rs_cells * (p.box / (double)p.pm_grid);
+  double rc = p.rcut_rs * rs;
+  if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hfmm_default_params(hfmm_params *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->box = 1.0;
+  o->pm_grid = 32;
+  o->rs_cells = 1.25;
+  o->rcut_rs = 4.5;
+  o->G = 1.0;
+  o->theta = 0.5;
+  o->order = 4;
+  o->leaf_max = 16;
+  o->mac_mode = 0;
+  o->transition_rule = 1;
+  o->size_rule = 1;
+  o->m2l_precision = 0;
+  o->profile = 0;
+}
+
+int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
+  if (!params || !out) {
+    g_create_err = "null argument";
+    return HFMM_ERR_ARG;
+  }
+  *out = nullptr;
+  std::string why;
+  if (!valid_params(*params, why)) {
+    g_create_err = why;
+    return HFMM_ERR_ARG;
+  }
+  hfmm_ctx *h = new (std::nothrow) hfmm_ctx();
+  if (!h) {
+    g_create_err = "host allocation failed";
+    return HFMM_ERR_OOM;
+  }
+  Ctx &c = h->c;
+  c.prm = *params;
+  c.rs = params->rs_cells * (params->box / (double)params->pm_grid);
+  c.rc = params->rcut_rs * c.rs;
+  double t = c.rc * 4194304.0;
+  t = t / params->box;
+  c.rc2h = t * t;
+  c.theta2 = params->theta * params->theta;
+  c.p = params->order;
+  c.nc = ncoef(c.p);
+  cudaError_t e = cudaMallocHost(&c.h_pinned, 64);
+  if (e == cudaSuccess) e = ensure(c.d_small, 256);
+  for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&c.ev[i]);
+  if (e != cudaSuccess) {
+    g_create_err = std::string("CUDA: ") + cudaGetErrorString(e);
+    hfmm_destroy(h);
+    return e == cudaErrorMemoryAllocation ? HFMM_ERR_OOM : HFMM_ERR_CUDA;
+  }
+  c.ev_ready = true;
+  *out = h;
+  return HFMM_OK;
+}
+
+void hfmm_destroy(hfmm_ctx *h) {
+  if (!h) return;
+  Ctx &c = h->c;
+  DBuf *bufs[] = {&c.key, &c.key_alt, &c.idx, &c.idx_alt, &c.xs, &c.pm4, &c.perm, &c.cell, &c.range, &c.kids,
+                  &c.leaves, &c.bounds, &c.nkids, &c.koff, &c.front, &c.front_next, &c.cls, &c.counts, &c.offs,
+                  &c.m2l, &c.m2l_alt, &c.p2p, &c.p2p_alt, &c.m2l_beg, &c.m2l_end, &c.p2p_beg, &c.p2p_end, &c.M,
+                  &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc};
+  for (DBuf *b : bufs) release(*b);
+  if (c.h_pinned) cudaFreeHost(c.h_pinned);
+  for (int i = 0; i < 16; ++i)
+    if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+  delete h;
+}
+
+const char *hfmm_last_error(const hfmm_ctx *h) {
+  if (!h) return g_create_err.c_str();
+  return h->c.err.c_str();
+}
+
+int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n, void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  c.have_tree = false;
+  if (n < 0 || n > (int64_t)0x7fffffff) return fail(c, HFMM_ERR_ARG, "n must be in [0, 2^31)");
+  if (n > 0 && (!pos || !mass)) return fail(c, HFMM_ERR_ARG, "null position or mass pointer");
+  cudaError_t e = build_tree(c, pos, mass, n, S(stream));
+  if (e == cudaErrorInvalidValue && c.nnodes >= ((int64_t)1 << kSinkBits))
+    return fail(c, HFMM_ERR_CAPACITY, "more than 2^27 tree nodes");
+  if (e != cudaSuccess) return cuda_fail(c, e, "build_tree");
+  return HFMM_OK;
+}
+
+int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "short_range_forces before build_tree");
+  if (c.n > 0 && !acc) return fail(c, HFMM_ERR_ARG, "null acceleration pointer");
+  if (c.n == 0) return HFMM_OK;
+  cudaStream_t st = S(stream);
+  cudaError_t e;
+  size_t eb = (size_t)c.nnodes * c.nc * sizeof(float);
+  if ((e = ensure(c.M, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc M");
+  if ((e = ensure(c.L, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc L");
+  if ((e = cudaMemsetAsync(c.L.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset L");
+  bool prof = c.prm.profile != 0;
+  if (prof) cudaEventRecord(c.ev[3], st);
+  if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
+  if (prof) cudaEventRecord(c.ev[4], st);
+  e = traverse(c, st);
+  if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "traversal frontier above 2^32 entries");
+  if (e != cudaSuccess) return cuda_fail(c, e, "traverse");
+  if (prof) cudaEventRecord(c.ev[5], st);
+  if ((e = sort_lists(c, st)) != cudaSuccess) return cuda_fail(c, e, "sort_lists");
+  if (prof) cudaEventRecord(c.ev[6], st);
+  if ((e = m2l_pass(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l");
+  if (prof) cudaEventRecord(c.ev[7], st);
+  if ((e = l2l_pass(c, st)) != cudaSuccess) return cuda_fail(c, e, "l2l");
+  if (prof) cudaEventRecord(c.ev[8], st);
+  if ((e = p2p_l2p(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "p2p_l2p");
+  if (prof) cudaEventRecord(c.ev[9], st);
+  return HFMM_OK;
+}
+
+int hfmm_short_range_forces_host(hfmm_ctx *h, const double *pos, const float *mass, int64_t n, float *acc,
+                                 void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (n < 0 || n > (int64_t)0x7fffffff) return fail(c, HFMM_ERR_ARG, "n must be in [0, 2^31)");
+  if (n > 0 && (!pos || !mass || !acc)) return fail(c, HFMM_ERR_ARG, "null host pointer");
+  cudaStream_t st = S(stream);
+  cudaError_t e;
+  if ((e = ensure(c.hpos, (size_t)(n ? n : 1) * 24)) != cudaSuccess) return cuda_fail(c, e, "alloc pos");
+  if ((e = ensure(c.hmass, (size_t)(n ? n : 1) * 4)) != cudaSuccess) return cuda_fail(c, e, "alloc mass");
+  if ((e = ensure(c.hacc, (size_t)(n ? n : 1) * 12)) != cudaSuccess) return cuda_fail(c, e, "alloc acc");
+  if (n > 0) {
+    if ((e = cudaMemcpyAsync(c.hpos.p, pos, n * 24, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(c, e, "copy pos");
+    if ((e = cudaMemcpyAsync(c.hmass.p, mass, n * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(c, e, "copy mass");
+  }
+  int rc = hfmm_build_tree(h, P<double>(c.hpos), P<float>(c.hmass), n, stream);
+  if (rc != HFMM_OK) return rc;
+  rc = hfmm_short_range_forces(h, P<float>(c.hacc), stream);
+  if (rc != HFMM_OK) return rc;
+  if (n > 0 && (e = cudaMemcpyAsync(acc, c.hacc.p, n * 12, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(c, e, "copy acc");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  return HFMM_OK;
+}
+
+int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
+  if (!h || !o) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  std::memset(o, 0, sizeof(*o));
+  o->n = c.n;
+  o->nnodes = c.nnodes;
+  o->nleaves = c.nleaves;
+  o->nlevels = c.nlevels;
+  o->traverse_iters = c.traverse_iters;
+  o->np2p = c.np2p;
+  o->nm2l = c.nm2l;
+  o->p2p_particle_pairs = c.p2p_particle_pairs;
+  float *t[] = {&o->t_keys_sort, &o->t_tree, &o->t_upward, &o->t_traverse, &o->t_lists, &o->t_m2l, &o->t_l2l,
+                &o->t_p2p};
+  const int ev_pairs[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};
+  for (int i = 0; i < 8; ++i) {
+    *t[i] = -1.f;
+    if (c.prm.profile && c.n > 0) {
+      float ms = -1.f;
+      if (cudaEventElapsedTime(&ms, c.ev[ev_pairs[i][0]], c.ev[ev_pairs[i][1]]) == cudaSuccess) *t[i] = ms;
+    }
+  }
+  cudaGetLastError();
+  return HFMM_OK;
+}
+
+int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
+  if (!h || !bytes) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "nothing to export before build_tree");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  size_t need = 0;
+  switch (what) {
+    case HFMM_EXPORT_KEYS: need = c.n * 8; break;
+    case HFMM_EXPORT_PERM: need = c.n * 4; break;
+    case HFMM_EXPORT_NODES: need = c.nnodes * 64; break;
+    case HFMM_EXPORT_P2P: need = c.np2p * 24; break;
+    case HFMM_EXPORT_M2L: need = c.nm2l * 24; break;
+    case HFMM_EXPORT_MULTIPOLES:
+    case HFMM_EXPORT_LOCALS: need = (size_t)c.nnodes * c.nc * 4; break;
+    default: return fail(c, HFMM_ERR_ARG, "unknown export");
+  }
+  if (!buf) {
+    *bytes = need;
+    return HFMM_OK;
+  }
+  if (*bytes < need) return fail(c, HFMM_ERR_ARG, "export buffer too small");
+  *bytes = need;
+  if (need == 0) return HFMM_OK;
+  switch (what) {
+    case HFMM_EXPORT_KEYS: e = cudaMemcpy(buf, c.key.p, need, cudaMemcpyDeviceToHost); break;
+    case HFMM_EXPORT_PERM: e = cudaMemcpy(buf, c.idx.p, need, cudaMemcpyDeviceToHost); break;
+    case HFMM_EXPORT_MULTIPOLES: e = cudaMemcpy(buf, c.M.p, need, cudaMemcpyDeviceToHost); break;
+    case HFMM_EXPORT_LOCALS: e = cudaMemcpy(buf, c.L.p, need, cudaMemcpyDeviceToHost); break;
+    case HFMM_EXPORT_NODES: {
+      std::vector<uint4> cell(c.nnodes);
+      std::vector<uint2> range(c.nnodes);
+      std::vector<int2> kids(c.nnodes);
+      e = cudaMemcpy(cell.data(), c.cell.p, c.nnodes * sizeof(uint4), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(range.data(), c.range.p, c.nnodes * sizeof(uint2), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(kids.data(), c.kids.p, c.nnodes * sizeof(int2), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      int64_t *o = static_cast<int64_t *>(buf);
+      for (int64_t k = 0; k < c.nnodes; ++k) {
+        int64_t *r = o + 8 * k;
+        r[0] = cell[k].w; r[1] = cell[k].x; r[2] = cell[k].y; r[3] = cell[k].z;
+        r[4] = range[k].x; r[5] = range[k].y;
+        r[6] = kids[k].y ? kids[k].x : -1;
+        r[7] = kids[k].y;
+      }
+      break;
+    }
+    case HFMM_EXPORT_P2P:
+    case HFMM_EXPORT_M2L: {
+      int64_t cnt = what == HFMM_EXPORT_P2P ? c.np2p : c.nm2l;
+      std::vector<uint64_t> v(cnt);
+      e = cudaMemcpy(v.data(), (what == HFMM_EXPORT_P2P ? c.p2p : c.m2l).p, cnt * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      int64_t *o = static_cast<int64_t *>(buf);
+      for (int64_t t = 0; t < cnt; ++t) {
+        o[3 * t] = pair_sink(v[t]);
+        o[3 * t + 1] = pair_src(v[t]);
+        o[3 * t + 2] = pair_shift(v[t]);
+      }
+      break;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "export copy");
+  return HFMM_OK;
+}
+
+}  // extern "C"

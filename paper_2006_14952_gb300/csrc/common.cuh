@@ -1,0 +1,164 @@
+// Shared definitions of libhfmm: context, device buffers, multi-index helpers,
+// packed list entries and the integer cell geometry used by the traversal.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/hfmm.h"
+
+namespace hfmm {
+
+constexpr int kDepth = 21;           // finest octree level (2^21 cells per side)
+constexpr int kPMax = 8;             // highest supported expansion order
+constexpr int kNCMax = 165;          // ncoef(kPMax)
+constexpr int64_t kHalfBox = 1ll << 22;  // box side in half units (L / 2^22)
+
+__host__ __device__ constexpr int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// Graded multi-index order: k = |n| ascending, nx descending, ny descending.
+__host__ __device__ inline int midx(int nx, int ny, int nz) {
+  int k = nx + ny + nz, j = k - nx;
+  return k * (k + 1) * (k + 2) / 6 + j * (j + 1) / 2 + (j - ny);
+}
+
+// Inverse of midx.
+__host__ __device__ inline void mdecode(int c, int &nx, int &ny, int &nz) {
+  int k = 0;
+  while (ncoef(k) <= c) ++k;
+  int r = c - (k ? ncoef(k - 1) : 0);
+  int j = 0;
+  while ((j + 1) * (j + 2) / 2 <= r) ++j;
+  nx = k - j;
+  ny = j - (r - j * (j + 1) / 2);
+  nz = k - nx - ny;
+}
+
+// ---------------------------------------------------------------- lists
+// Packed (sink node, source node, shift index) entry: sink in bits 37..63,
+// source in bits 5..36, periodic shift index (0..26) in bits 0..4.
+constexpr int kSinkShift = 37;
+constexpr int kSinkBits = 27;
+__host__ __device__ inline uint64_t pack_pair(uint32_t sink, uint32_t src, uint32_t s) {
+  return ((uint64_t)sink << kSinkShift) | ((uint64_t)src << 5) | (uint64_t)s;
+}
+__host__ __device__ inline uint32_t pair_sink(uint64_t e) { return (uint32_t)(e >> kSinkShift); }
+__host__ __device__ inline uint32_t pair_src(uint64_t e) { return (uint32_t)((e >> 5) & 0xffffffffull); }
+__host__ __device__ inline uint32_t pair_shift(uint64_t e) { return (uint32_t)(e & 31ull); }
+
+// ---------------------------------------------------------------- cells
+// cell = {ix, iy, iz, level}; half-unit centre 2*ix*w + w with w = 2^(21-level).
+__host__ __device__ inline int64_t half_width(uint32_t level) { return (int64_t)1 << (kDepth - level); }
+__host__ __device__ inline int64_t half_centre(uint32_t i, uint32_t level) {
+  int64_t w = half_width(level);
+  return 2 * (int64_t)i * w + w;
+}
+__host__ __device__ inline int shift_component(uint32_t s, int d) {
+  return d == 0 ? (int)(s / 9) - 1 : d == 1 ? (int)((s / 3) % 3) - 1 : (int)(s % 3) - 1;
+}
+// Source centre (displaced by the periodic shift) minus sink centre, half units.
+__host__ __device__ inline void half_delta(uint4 sink, uint4 src, uint32_t s, int64_t *dd) {
+  dd[0] = half_centre(src.x, src.w) + shift_component(s, 0) * kHalfBox - half_centre(sink.x, sink.w);
+  dd[1] = half_centre(src.y, src.w) + shift_component(s, 1) * kHalfBox - half_centre(sink.y, sink.w);
+  dd[2] = half_centre(src.z, src.w) + shift_component(s, 2) * kHalfBox - half_centre(sink.z, sink.w);
+}
+
+// ---------------------------------------------------------------- buffers
+struct DBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+// Grow b to at least `bytes` (contents not kept).
+cudaError_t ensure(DBuf &b, size_t bytes);
+// Grow b to at least `bytes`, keeping the first `keep` bytes (stream-ordered copy).
+cudaError_t ensure_keep(DBuf &b, size_t bytes, size_t keep, cudaStream_t st);
+void release(DBuf &b);
+
+template <class T>
+inline T *P(DBuf &b) {
+  return static_cast<T *>(b.p);
+}
+
+// ---------------------------------------------------------------- scan / sort
+// Exclusive prefix sum of n uint32 values; *total (device, uint64) receives the sum.
+// `tmp` is scratch grown as needed.
+cudaError_t scan_u32(const uint32_t *in, uint32_t *out, uint64_t *total, size_t n, DBuf &tmp, cudaStream_t st);
+
+// Stable LSD radix sort of uint64 keys on bits [bit_lo, bit_hi), optionally
+// carrying uint32 values.  Ping-pongs between (keys, vals) and (keys_alt,
+// vals_alt); returns in *in_alt whether the result ended in the alt buffers.
+cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
+                           int bit_lo, int bit_hi, bool *in_alt, DBuf &tmp, cudaStream_t st);
+
+// ---------------------------------------------------------------- context
+struct Ctx {
+  hfmm_params prm{};
+  double rs = 0, rc = 0;        // split scale and cut-off radius
+  double rc2h = 0, theta2 = 0;  // MAC thresholds (half units squared; theta^2)
+  int p = 4, nc = 35;
+  std::string err;
+
+  // particles
+  int64_t n = 0;
+  bool have_tree = false;
+  DBuf key, key_alt, idx, idx_alt;  // u64 keys, u32 input indices
+  DBuf xs;                          // f64 [3][n] sorted wrapped positions
+  DBuf pm4;                         // float4 [n] (offset from leaf centre, mass)
+  DBuf perm;                        // u32 [n] input index per sorted particle (alias of idx result)
+
+  // nodes (breadth-first)
+  int64_t nnodes = 0, nleaves = 0;
+  int nlevels = 0;
+  int64_t level_start[kDepth + 3] = {0};
+  DBuf cell;    // uint4 {ix, iy, iz, level}
+  DBuf range;   // uint2 {first, count}
+  DBuf kids;    // int2 {first child or -1, child count}
+  DBuf leaves;  // u32 [nleaves] node index of each leaf
+  DBuf bounds, nkids, koff;  // build scratch
+
+  // traversal
+  DBuf front, front_next, cls, counts, offs;
+  DBuf m2l, m2l_alt, p2p, p2p_alt;  // packed u64 entries
+  int64_t nm2l = 0, np2p = 0;
+  int traverse_iters = 0;
+  DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
+
+  // expansions (scaled): M~ = M / h^|m|, L~ = L h^(|n|+1)
+  DBuf M, L;
+
+  // host-visible scratch
+  DBuf tmp, tmp2;
+  uint64_t *h_pinned = nullptr;  // small pinned host buffer for counters
+  DBuf d_small;                  // small device buffer for counters
+
+  // host-buffer entry point
+  DBuf hpos, hmass, hacc;
+
+  // stats
+  int64_t p2p_particle_pairs = -1;
+  cudaEvent_t ev[16] = {};
+  bool ev_ready = false;
+  float t_keys_sort = -1, t_tree = -1, t_upward = -1, t_traverse = -1, t_lists = -1, t_m2l = -1, t_l2l = -1,
+        t_p2p = -1;
+};
+
+// Phase implementations (each returns a CUDA error; the ABI maps it).
+cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st);
+cudaError_t traverse(Ctx &c, cudaStream_t st);
+cudaError_t sort_lists(Ctx &c, cudaStream_t st);
+cudaError_t upward(Ctx &c, cudaStream_t st);
+cudaError_t m2l_pass(Ctx &c, cudaStream_t st);
+cudaError_t l2l_pass(Ctx &c, cudaStream_t st);
+cudaError_t p2p_l2p(Ctx &c, float *acc, cudaStream_t st);
+
+inline unsigned blocks_for(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace hfmm
+
+struct hfmm_ctx {
+  hfmm::Ctx c;
+};

@@ -1,0 +1,200 @@
+"""ctypes binding of libhfmm.so (include/hfmm.h).
+
+Argument marshalling only: torch tensors supply device memory and the current
+CUDA stream; every step of the solver runs in the library's CUDA kernels.
+There is no CPU fallback: if the library has not been built, or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+HFMM_OK = 0
+ERRORS = {-1: "HFMM_ERR_ARG", -2: "HFMM_ERR_OOM", -3: "HFMM_ERR_CUDA", -4: "HFMM_ERR_CAPACITY",
+          -5: "HFMM_ERR_STATE", -6: "HFMM_ERR_TIMEOUT"}
+EXPORT = {"keys": 0, "perm": 1, "nodes": 2, "p2p": 3, "m2l": 4, "multipoles": 5, "locals": 6}
+
+# Every symbol include/hfmm.h declares.
+SYMBOLS = ["hfmm_default_params", "hfmm_create", "hfmm_destroy", "hfmm_last_error", "hfmm_build_tree",
+           "hfmm_short_range_forces", "hfmm_short_range_forces_host", "hfmm_get_stats", "hfmm_export"]
+
+
+class Params(C.Structure):
+    _fields_ = [("box", C.c_double), ("pm_grid", C.c_int), ("rs_cells", C.c_double), ("rcut_rs", C.c_double),
+                ("G", C.c_double), ("theta", C.c_double), ("order", C.c_int), ("leaf_max", C.c_int),
+                ("mac_mode", C.c_int), ("transition_rule", C.c_int), ("size_rule", C.c_int),
+                ("m2l_precision", C.c_int), ("profile", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnodes", C.c_int64), ("nleaves", C.c_int64), ("nlevels", C.c_int32),
+                ("traverse_iters", C.c_int32), ("np2p", C.c_int64), ("nm2l", C.c_int64),
+                ("p2p_particle_pairs", C.c_int64), ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
+                ("t_upward", C.c_float), ("t_traverse", C.c_float), ("t_lists", C.c_float), ("t_m2l", C.c_float),
+                ("t_l2l", C.c_float), ("t_p2p", C.c_float)]
+
+
+class HfmmError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libhfmm.so (building it first if asked and needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise HfmmError(f"{path} is missing: build it with paper_2006_14952_gb300.build.build()")
+            _build.build()
+        L = C.CDLL(path)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+        L.hfmm_default_params.argtypes = [C.POINTER(Params)]
+        L.hfmm_default_params.restype = None
+        L.hfmm_create.argtypes = [C.POINTER(Params), C.POINTER(vp)]
+        L.hfmm_create.restype = i32
+        L.hfmm_destroy.argtypes = [vp]
+        L.hfmm_destroy.restype = None
+        L.hfmm_last_error.argtypes = [vp]
+        L.hfmm_last_error.restype = C.c_char_p
+        L.hfmm_build_tree.argtypes = [vp, vp, vp, i64, vp]
+        L.hfmm_build_tree.restype = i32
+        L.hfmm_short_range_forces.argtypes = [vp, vp, vp]
+        L.hfmm_short_range_forces.restype = i32
+        L.hfmm_short_range_forces_host.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.hfmm_short_range_forces_host.restype = i32
+        L.hfmm_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.hfmm_get_stats.restype = i32
+        L.hfmm_export.argtypes = [vp, i32, vp, C.POINTER(C.c_size_t)]
+        L.hfmm_export.restype = i32
+        _lib = L
+        return L
+
+
+def default_params() -> Params:
+    p = Params()
+    load().hfmm_default_params(C.byref(p))
+    return p
+
+
+def _stream_handle(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """One hfmm context: build_tree, short_range_forces, get_stats, export."""
+
+    def __init__(self, **kw):
+        self._lib = load()
+        p = default_params()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        h = C.c_void_p()
+        rc = self._lib.hfmm_create(C.byref(p), C.byref(h))
+        if rc != HFMM_OK:
+            raise HfmmError(f"hfmm_create: {ERRORS.get(rc, rc)}: {self._lib.hfmm_last_error(None).decode()}")
+        self._h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hfmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != HFMM_OK:
+            msg = self._lib.hfmm_last_error(self._h).decode()
+            raise HfmmError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+
+    @property
+    def rs(self) -> float:
+        p = self.params
+        return p.rs_cells * (p.box / p.pm_grid)
+
+    @property
+    def rc(self) -> float:
+        return self.params.rcut_rs * self.rs
+
+    def build_tree(self, pos, mass, stream=None):
+        """pos: CUDA float64 [3][n] contiguous; mass: CUDA float32 [n]."""
+        import torch
+
+        assert pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous() and pos.shape[0] == 3
+        assert mass.is_cuda and mass.dtype == torch.float32 and mass.is_contiguous()
+        n = pos.shape[1]
+        assert mass.shape[0] == n
+        self.n = n
+        self._check(self._lib.hfmm_build_tree(self._h, C.c_void_p(pos.data_ptr()), C.c_void_p(mass.data_ptr()), n,
+                                              _stream_handle(stream)), "hfmm_build_tree")
+
+    def short_range_forces(self, acc=None, stream=None):
+        """Returns (or fills) a CUDA float32 [3][n] tensor of accelerations."""
+        import torch
+
+        if acc is None:
+            acc = torch.empty((3, self.n), dtype=torch.float32, device="cuda")
+        assert acc.is_cuda and acc.dtype == torch.float32 and acc.is_contiguous()
+        self._check(self._lib.hfmm_short_range_forces(self._h, C.c_void_p(acc.data_ptr()), _stream_handle(stream)),
+                    "hfmm_short_range_forces")
+        return acc
+
+    def short_range_forces_host(self, pos, mass, acc=None, stream=None):
+        """Host numpy (or pinned CPU torch) buffers in and out."""
+        n = pos.shape[1]
+        if acc is None:
+            acc = np.empty((3, n), dtype=np.float32)
+        ptr = (lambda a: C.c_void_p(a.data_ptr())) if hasattr(pos, "data_ptr") else (
+            lambda a: a.ctypes.data_as(C.c_void_p))
+        self.n = n
+        self._check(self._lib.hfmm_short_range_forces_host(self._h, ptr(pos), ptr(mass), n, ptr(acc),
+                                                           _stream_handle(stream)), "hfmm_short_range_forces_host")
+        return acc
+
+    def get_stats(self) -> dict:
+        s = Stats()
+        self._check(self._lib.hfmm_get_stats(self._h, C.byref(s)), "hfmm_get_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def export(self, what: str) -> np.ndarray:
+        code = EXPORT[what]
+        nb = C.c_size_t(0)
+        self._check(self._lib.hfmm_export(self._h, code, None, C.byref(nb)), "hfmm_export")
+        dtype, cols = {"keys": (np.uint64, 0), "perm": (np.uint32, 0), "nodes": (np.int64, 8), "p2p": (np.int64, 3),
+                       "m2l": (np.int64, 3), "multipoles": (np.float32, -1), "locals": (np.float32, -1)}[what]
+        out = np.empty(nb.value // np.dtype(dtype).itemsize, dtype=dtype)
+        if nb.value:
+            self._check(self._lib.hfmm_export(self._h, code, out.ctypes.data_as(C.c_void_p), C.byref(nb)),
+                        "hfmm_export")
+        if cols > 0:
+            out = out.reshape(-1, cols)
+        elif cols < 0:
+            nc = (self.params.order + 1) * (self.params.order + 2) * (self.params.order + 3) // 6
+            out = out.reshape(-1, nc)
+        return out

@@ -181,7 +181,7 @@ def zeldovich(n_side: int, seed: int, box: float = 1.0, rms_spacing: float = 0.3
     disp = []
     for kk in (kx, ky, kz):
         psi_k = 1j * kk * dk / k2
-        disp.append(np.fft.irfftn(psi_k, s=(n_side,) * 3).astype(np.float64).ravel())
+        disp.append(np.fft.irfftn(psi_k, s=(n_side,) * 3, axes=(0, 1, 2)).astype(np.float64).ravel())
         del psi_k
     disp = np.stack(disp)
     rms = np.sqrt((disp ** 2).sum(axis=0).mean())

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry
+point that include/*.h declares (no compute call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(hfmm_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2006_14952_gb300 import build, hfmm
+
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    decl = declared_functions()
+    assert len(decl) >= 9
+    missing = [s for s in decl if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(hfmm.SYMBOLS) <= set(decl)
+
+
+def test_parameter_validation_needs_no_gpu():
+    from paper_2006_14952_gb300 import hfmm
+
+    L = hfmm.load()
+    p = hfmm.default_params()
+    assert p.order == 4 and p.leaf_max == 16 and p.transition_rule == 1 and p.size_rule == 1
+    h = ctypes.c_void_p()
+    p.order = 99
+    assert L.hfmm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert b"order" in L.hfmm_last_error(None)
+    p.order = 4
+    p.rcut_rs = 1000.0
+    assert L.hfmm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert L.hfmm_create(None, ctypes.byref(h)) == -1
+
+
+def test_struct_layout_matches_header():
+    """The ctypes mirrors have the sizes the C compiler gives the header structs."""
+    import subprocess
+    import tempfile
+
+    from paper_2006_14952_gb300 import hfmm
+
+    src = '#include <stdio.h>\n#include "hfmm.h"\nint main(){printf("%zu %zu\\n", sizeof(hfmm_params), sizeof(hfmm_stats));return 0;}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        a, b = map(int, subprocess.check_output([exe]).split())
+    assert a == ctypes.sizeof(hfmm.Params) and b == ctypes.sizeof(hfmm.Stats)

@@ -1,0 +1,167 @@
+"""GPU parity against the FP64 oracle, through the C ABI.
+
+Bit-exact: Morton keys, sort permutation, tree nodes, and the P2P / M2L lists
+(compared as sorted sets).  Forces: FP32 GPU vs FP64 oracle FMM on identical
+lists within 1e-5 relative RMS (the stated tolerance); theta = 0 (all P2P)
+vs the FP64 direct truncated sum within the same bound.  Sizes span several
+sort tiles (2048 keys) with a ragged tail; edge cases: N = 0, 1, coincident
+particles (depth cap), positions outside the box.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_14952_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5  # relative RMS, FP32 vs FP64 on identical lists
+
+
+def solver(**kw):
+    from paper_2006_14952_gb300 import hfmm
+
+    return hfmm.Solver(**kw)
+
+
+def run_gpu(pos, mass, **kw):
+    import torch
+
+    s = solver(**kw)
+    s.build_tree(torch.from_numpy(np.ascontiguousarray(pos)).cuda(), torch.from_numpy(mass).cuda())
+    acc = s.short_range_forces()
+    torch.cuda.synchronize()
+    return s, acc.cpu().numpy().astype(np.float64)
+
+
+def run_oracle(pos, mass, s, traverse=True):
+    p = s.params
+    f = oracle.FMM(box=p.box, rs=s.rs, rc=s.rc, G=p.G, theta=p.theta, order=p.order, leaf_max=p.leaf_max,
+                   transition_rule=p.transition_rule, size_rule=p.size_rule)
+    f.build_tree(pos, mass)
+    return f
+
+
+def rel_rms(a, ref):
+    return math.sqrt(((a - ref) ** 2).sum() / max((ref ** 2).sum(), 1e-300))
+
+
+def sorted_rows(a):
+    a = np.asarray(a, dtype=np.int64).reshape(-1, 3)
+    return a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+
+
+CASES = {
+    "uniform-50000": lambda: W.uniform(50000, 11),
+    "nfw-50000": lambda: W.nfw_clustered(50000, 60, 0.7, 12),
+    "zeldovich-32768": lambda: W.zeldovich(32, 13, halo_count=20, halo_frac=0.4),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_keys_perm_nodes_bit_exact(case):
+    pos, mass = CASES[case]()
+    pos = pos.copy()
+    pos[:, :4] = [[-0.3, 1.0, 1.7, 0.5], [2.2, -1e-17, 0.25, 0.5], [0.999999999999, 0.5, -2.0, 0.5]]
+    s, _ = run_gpu(pos, mass, pm_grid=32)
+    f = run_oracle(pos, mass, s)
+    key, perm, _ = f.particles()
+    np.testing.assert_array_equal(s.export("keys"), key)
+    np.testing.assert_array_equal(s.export("perm").astype(np.int64), perm)
+    np.testing.assert_array_equal(s.export("nodes"), f.nodes())
+
+
+@pytest.mark.parametrize("rule,size_rule,theta,leaf", [(1, 1, 0.5, 16), (0, 1, 0.5, 16), (1, 0, 0.5, 16),
+                                                        (1, 1, 0.3, 8), (1, 1, 0.7, 1), (1, 1, 0.0, 16)])
+def test_interaction_lists_bit_exact(rule, size_rule, theta, leaf):
+    pos, mass = W.nfw_clustered(20000 if leaf > 1 else 4000, 30, 0.7, 21)
+    s, _ = run_gpu(pos, mass, pm_grid=32, theta=theta, leaf_max=leaf, transition_rule=rule, size_rule=size_rule,
+                   order=2)
+    f = run_oracle(pos, mass, s)
+    f.traverse()
+    p2p, m2l = f.lists()
+    np.testing.assert_array_equal(sorted_rows(s.export("p2p")), sorted_rows(p2p))
+    np.testing.assert_array_equal(sorted_rows(s.export("m2l")), sorted_rows(m2l))
+    st = s.get_stats()
+    assert st["np2p"] == len(p2p) and st["nm2l"] == len(m2l)
+
+
+@pytest.mark.parametrize("case,order", [("uniform-50000", 4), ("nfw-50000", 2), ("nfw-50000", 4),
+                                        ("nfw-50000", 6), ("nfw-50000", 8), ("zeldovich-32768", 5)])
+def test_forces_match_fp64_fmm_on_identical_lists(case, order):
+    pos, mass = CASES[case]()
+    s, acc = run_gpu(pos, mass, pm_grid=32, order=order)
+    f = run_oracle(pos, mass, s)
+    ref = f.forces()
+    assert f.size("m2l") > 0
+    err = rel_rms(acc, ref)
+    assert err < FORCE_TOL, err
+
+
+def test_expansions_match_oracle():
+    pos, mass = CASES["nfw-50000"]()
+    s, _ = run_gpu(pos, mass, pm_grid=32, order=4)
+    f = run_oracle(pos, mass, s)
+    f.forces()
+    nodes = f.nodes()
+    h = 1.0 / 2.0 ** nodes[:, 0]
+    mi = oracle.multi_indices(4)
+    deg = mi.sum(axis=1)
+    Mg = s.export("multipoles").astype(np.float64) * h[:, None] ** deg[None, :]
+    Lg = s.export("locals").astype(np.float64) / h[:, None] ** (deg[None, :] + 1)
+    Mo, Lo = f.expansions("M"), f.expansions("L")
+    for g, o in ((Mg, Mo), (Lg, Lo)):
+        # per-degree relative error over all cells
+        for k in range(5):
+            sel = deg == k
+            err = np.sqrt(((g[:, sel] - o[:, sel]) ** 2).sum() / max((o[:, sel] ** 2).sum(), 1e-300))
+            assert err < 1e-5, (k, err)
+
+
+def test_theta_zero_equals_direct_sum_at_full_uniform_size():
+    pos, mass = W.make(W.CONFIGS["uniform-32k"])
+    s, acc = run_gpu(pos, mass, pm_grid=32, theta=0.0)
+    assert s.get_stats()["nm2l"] == 0
+    ref = oracle.direct_sr(pos, mass, 1.0, s.rs, s.rc)
+    assert rel_rms(acc, ref) < FORCE_TOL
+
+
+def test_edge_cases_empty_single_coincident():
+    import torch
+
+    s = solver()
+    s.build_tree(torch.zeros((3, 0), dtype=torch.float64, device="cuda"), torch.zeros(0, device="cuda"))
+    assert s.short_range_forces().shape == (3, 0)
+    one = torch.tensor([[0.3], [0.4], [0.5]], dtype=torch.float64, device="cuda")
+    s.build_tree(one, torch.ones(1, device="cuda"))
+    assert torch.all(s.short_range_forces() == 0)
+    # 40 coincident particles plus two neighbours: depth cap, zero self force
+    pos = np.full((3, 42), 0.3)
+    pos[0, 40] = 0.31
+    pos[0, 41] = 0.29
+    mass = np.full(42, 1 / 42, dtype=np.float32)
+    s2, acc = run_gpu(pos, mass, pm_grid=32)
+    nodes = s2.export("nodes")
+    assert nodes[:, 0].max() == 21
+    ref = oracle.direct_sr(pos, mass, 1.0, s2.rs, s2.rc)
+    assert rel_rms(acc, ref) < FORCE_TOL
+
+
+def test_state_and_argument_errors():
+    import torch
+
+    from paper_2006_14952_gb300 import hfmm
+
+    s = solver()
+    with pytest.raises(hfmm.HfmmError, match="STATE"):
+        s.short_range_forces(torch.empty((3, 1), device="cuda"))
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    pos, mass = CASES["nfw-50000"]()
+    s, acc = run_gpu(pos, mass, pm_grid=32)
+    s2 = solver(pm_grid=32)
+    acc2 = s2.short_range_forces_host(np.ascontiguousarray(pos), mass)
+    np.testing.assert_array_equal(acc2, acc.astype(np.float32))
