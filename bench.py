@@ -1,0 +1,358 @@
+"""Benchmark: short-range forces/s of the truncated FMM on the clustered
+N = 128^3 set (70% of the particles in 2000 NFW haloes, 30% uniform; PM 128^3,
+r_s = 1.25 cells, R_c = 4.5 r_s, leaves <= 16), one GB300.
+
+One step = one pass of the whole short-range path over the resident particle
+set: wrap + Morton keys, sort, octree, P2M/M2M, traversal, list grouping, M2L,
+L2L, L2P + P2P, accelerations in input order.  L2 is flushed (a 512 MB write)
+before every timed step.  `value` counts particles with forces per second of
+device time (CUDA events on the launching stream); `e2e` repeats the step
+through the host-buffer C entry point with the copies inside the timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "short-range forces/s, N=2M clustered, rms err≤1e-4: learned+TF32 vs plain"
+UNIT = "forces/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+# Algorithmic FP32 work of one P2P pair inside the cut-off: separation (3),
+# r^2 (5: 1 mul + 2 fma), rsqrt (1), r (1), x = r/r_s (1), the truncation factor
+# S(x) = erfc(x/2) + x e^(-x^2/4)/sqrt(pi) (exp 1, polynomial 2 x 6 fma = 12,
+# 2 mul + 1 fma = 4 for assembling it), 1/r^3 and mass (3), accumulation (6).
+P2P_FLOPS_PER_PAIR = 37
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nfw-2m")
+    ap.add_argument("--theta", type=float, default=0.3)
+    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--accuracy-sinks", type=int, default=20000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_desc(cfg):
+    if cfg.kind == "nfw":
+        return (f"{cfg.name}: N={cfg.n} in L=1, {int(cfg.halo_frac * 100)}% in {cfg.halo_count} NFW haloes "
+                f"(dN/dM~M^-1.9 over 3 decades, c~U[5,15], truncated at r_200), rest uniform; PM {cfg.pm_grid}^3, "
+                f"r_s={cfg.rs_cells} cells, R_c={cfg.rcut_rs} r_s")
+    return f"{cfg.name}: N={cfg.n}, kind={cfg.kind}, PM {cfg.pm_grid}^3"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [int(r[1]) for r in rows]
+        smax = max(int(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7):
+    """Direct FP64 truncated sum (the oracle) on a bounded random sink sample."""
+    import oracle
+
+    oracle.build()
+    n = pos.shape[1]
+    probe = np.sort(np.random.default_rng(seed).choice(n, size=min(500, n), replace=False))
+    t0 = time.perf_counter()
+    oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(n, max(500, 500 * target_s / dt)))
+    sinks = np.sort(np.random.default_rng(seed + 1).choice(n, size=k, replace=False))
+    t0 = time.perf_counter()
+    oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks)
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 direct truncated sum (oracle) for {k} random sinks against all {n} sources, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, cfg):
+    """The oracle as the reference arm: each step is a bounded sink sample."""
+    from paper_2006_14952_gb300 import workloads as W
+    import oracle
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    pos, mass = W.make(cfg)
+    n = pos.shape[1]
+    k = 2000
+    rng = np.random.default_rng(99)
+    for _ in range(args.warmup):
+        oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=np.sort(rng.choice(n, 200, replace=False)))
+    tot = 0.0
+    for _ in range(args.steps):
+        sinks = np.sort(rng.choice(n, k, replace=False))
+        t0 = time.perf_counter()
+        oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks)
+        tot += time.perf_counter() - t0
+    v = k * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(cfg), "reference": "FP64 CPU oracle, direct truncated sum"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{k} random sinks per step against all {n} sources"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def src_sha(name):
+    p = os.path.join(ROOT, "paper_2006_14952_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_traffic(kernel, src):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        e = d.get(kernel)
+        if e and e.get("src_sha") == src_sha(src):
+            return e["bytes_per_launch_full"]
+    except Exception:
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    from paper_2006_14952_gb300 import workloads as W
+
+    cfg = W.CONFIGS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2006_14952_gb300 import hfmm
+
+    # replicas: every rank solves its own seeded copy of the workload (weak scaling)
+    cfg_r = W.dataclasses.replace(cfg, seed=cfg.seed + rank) if ws > 1 else cfg
+    pos, mass = W.make(cfg_r)
+    n = pos.shape[1]
+    s = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
+                    order=args.order, leaf_max=cfg.leaf_max, profile=1)
+    dpos = torch.from_numpy(pos).to(dev)
+    dmass = torch.from_numpy(mass).to(dev)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.build_tree(dpos, dmass)
+        s.short_range_forces(acc)
+
+    for _ in range(max(args.warmup, 3 if args.warmup >= 3 else args.warmup)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+
+    # accuracy of this configuration against the FP64 direct sum (rank 0, untimed)
+    accuracy = None
+    if rank == 0 and args.accuracy_sinks > 0:
+        import oracle
+
+        oracle.build()
+        sinks = W.subsample(n, args.accuracy_sinks, 2024)
+        ref = oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks)
+        a = acc.cpu().numpy()[:, sinks].astype(np.float64)
+        e = np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        accuracy = {"rms_rel": float(math.sqrt((e ** 2).mean())), "p99_rel": float(np.percentile(e, 99)),
+                    "max_rel": float(e.max()), "sinks": int(len(sinks)), "against": "FP64 direct truncated sum"}
+
+    # timed region
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = s.get_stats()["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            phases.append(s.get_stats())  # synchronises; outside the events
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    l1 = s.get_stats()["launches"]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        tot_ms = float(t.item())
+    value = ws * n * args.steps / (tot_ms / 1e3)
+
+    # end to end through the host-buffer entry point, copies included
+    pin_pos = torch.from_numpy(pos).pin_memory()
+    pin_mass = torch.from_numpy(mass).pin_memory()
+    pin_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    s2 = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
+                     order=args.order, leaf_max=cfg.leaf_max)
+    for _ in range(2):
+        s2.short_range_forces_host(pin_pos, pin_mass, pin_acc)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2.short_range_forces_host(pin_pos, pin_mass, pin_acc)
+        e2e_s += time.perf_counter() - t0
+    e2e_v = ws * n * args.steps / e2e_s if ws == 1 else None
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_v = ws * n * args.steps / float(t.item())
+
+    # phase breakdown (mean over timed steps) and the dominant kernel's roofline
+    keys = ["t_keys_sort", "t_tree", "t_upward", "t_traverse", "t_lists", "t_m2l", "t_l2l", "t_p2p"]
+    mean = {k: statistics.mean(p[k] for p in phases) for k in keys}
+    st = phases[-1]
+    peak_fp32 = N_SM * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    if mean["t_p2p"] >= mean["t_m2l"]:
+        flops = st["p2p_useful_pairs"] * P2P_FLOPS_PER_PAIR
+        achieved = flops / (mean["t_p2p"] / 1e3) / 1e12
+        roof = {"kernel": "k_p2p_l2p (P2P + L2P)", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
+                "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": measured_traffic("k_p2p_l2p", "p2p.cu"),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "algorithmic": f"{st['p2p_useful_pairs']} pairs inside R_c x {P2P_FLOPS_PER_PAIR} flop"}
+    else:
+        p = args.order
+        fl_pair = 2 * math.comb(p + 6, 6)
+        achieved = st["nm2l"] * fl_pair / (mean["t_m2l"] / 1e3) / 1e12
+        roof = {"kernel": "k_m2l_generic", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
+                "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+                "traffic": measured_traffic("k_m2l_generic", "expansions.cu"),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "algorithmic": f"{st['nm2l']} M2L pairs x {fl_pair} flop (2 C(p+6,6))"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(pos, mass, cfg, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(cfg), "path": "plain FP32 geometric acceptance",
+                       "theta": args.theta, "order": args.order, "leaf_max": cfg.leaf_max,
+                       "transition_rule": 1, "size_rule": 1, "l2": "flushed (512 MB write) before every step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "accuracy": accuracy,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 4), "d2h_bytes_per_step": n * 12},
+            "gpu_launches": int(l1 - l0 - 0),
+            "clocks": clocks,
+            "breakdown_ms": {k[2:]: round(v, 4) for k, v in mean.items()},
+            "counts": {"nodes": st["nnodes"], "leaves": st["nleaves"], "levels": st["nlevels"],
+                       "traverse_iters": st["traverse_iters"], "p2p_leaf_pairs": st["np2p"],
+                       "m2l_pairs": st["nm2l"], "p2p_pairs_evaluated": st["p2p_particle_pairs"],
+                       "p2p_pairs_useful": st["p2p_useful_pairs"]},
+            "step_ms": [round(x, 4) for x in step_ms],
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

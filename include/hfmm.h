@@ -77,6 +77,8 @@ typedef struct {
   int64_t np2p;           /* P2P leaf pairs */
   int64_t nm2l;           /* M2L cell pairs */
   int64_t p2p_particle_pairs; /* particle pairs evaluated by P2P (incl. masked) */
+  int64_t p2p_useful_pairs;   /* pairs with 0 < r < R_c (params.profile = 1, else -1) */
+  int64_t launches;           /* kernels launched by this library in this process so far */
   /* milliseconds, filled when params.profile = 1 (else -1) */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
 } hfmm_stats;

@@ -150,6 +150,8 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if ((e = ensure(c.L, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc L");
   if ((e = cudaMemsetAsync(c.L.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset L");
   bool prof = c.prm.profile != 0;
+  if (prof && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 2, 0, 8, st)) != cudaSuccess)
+    return cuda_fail(c, e, "memset counter");
   if (prof) cudaEventRecord(c.ev[3], st);
   if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
   if (prof) cudaEventRecord(c.ev[4], st);
@@ -209,6 +211,13 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->np2p = c.np2p;
   o->nm2l = c.nm2l;
   o->p2p_particle_pairs = c.p2p_particle_pairs;
+  o->p2p_useful_pairs = -1;
+  if (c.prm.profile && c.n > 0) {
+    unsigned long long u = 0;
+    if (cudaMemcpy(&u, P<uint64_t>(c.d_small) + 2, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
+      o->p2p_useful_pairs = (int64_t)u;
+  }
+  o->launches = (int64_t)g_launches.load();
   float *t[] = {&o->t_keys_sort, &o->t_tree, &o->t_upward, &o->t_traverse, &o->t_lists, &o->t_m2l, &o->t_l2l,
                 &o->t_p2p};
   const int ev_pairs[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};

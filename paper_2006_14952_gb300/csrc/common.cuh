@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -139,7 +140,7 @@ struct Ctx {
   DBuf hpos, hmass, hacc;
 
   // stats
-  int64_t p2p_particle_pairs = -1;
+  int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1;
   cudaEvent_t ev[16] = {};
   bool ev_ready = false;
   float t_keys_sort = -1, t_tree = -1, t_upward = -1, t_traverse = -1, t_lists = -1, t_m2l = -1, t_l2l = -1,
@@ -156,6 +157,10 @@ cudaError_t l2l_pass(Ctx &c, cudaStream_t st);
 cudaError_t p2p_l2p(Ctx &c, float *acc, cudaStream_t st);
 
 inline unsigned blocks_for(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+// Process-wide count of kernels launched by this library (reported in stats).
+extern std::atomic<long long> g_launches;
+inline void note_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 }  // namespace hfmm
 

@@ -218,11 +218,13 @@ cudaError_t upward(Ctx &c, cudaStream_t st) {
   if (g > 152 * 64) g = 152 * 64;
   k_p2m<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<float4>(c.pm4), box,
                          c.nc, P<float>(c.M));
+  note_launch();
   for (int l = c.nlevels - 2; l >= 0; --l) {
     int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
     unsigned gl = blocks_for(cnt, 8);
     if (gl > 152 * 64) gl = 152 * 64;
     k_m2m<<<gl, T, 0, st>>>(lo, cnt, P<uint4>(c.cell), P<int2>(c.kids), c.nc, P<float>(c.M));
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -235,6 +237,7 @@ cudaError_t m2l_pass(Ctx &c, cudaStream_t st) {
   k_m2l_generic<<<g, T, 0, st>>>(c.nnodes, P<uint4>(c.cell), P<uint32_t>(c.m2l_beg), P<uint32_t>(c.m2l_end),
                                  P<uint64_t>(c.m2l), P<float>(c.M), P<float>(c.L), c.p, c.nc,
                                  (float)(c.rs / c.prm.box));
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -245,6 +248,7 @@ cudaError_t l2l_pass(Ctx &c, cudaStream_t st) {
     unsigned gl = blocks_for(cnt, 8);
     if (gl > 152 * 64) gl = 152 * 64;
     k_l2l<<<gl, T, 0, st>>>(lo, cnt, P<uint4>(c.cell), P<int2>(c.kids), c.p, c.nc, P<float>(c.L));
+    note_launch();
   }
   return cudaGetLastError();
 }

@@ -24,14 +24,17 @@ __device__ __forceinline__ float powi(float x, int e) {
   return r;
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ leaves, int64_t nl,
                                                  const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
                                                  const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
                                                  const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
                                                  const float *__restrict__ L, const uint32_t *__restrict__ perm,
                                                  int64_t n, int p, int nc, float box, float inv_rs, float rc2, float G,
-                                                 float *__restrict__ acc_out) {
+                                                 float *__restrict__ acc_out,
+                                                 unsigned long long *__restrict__ useful) {
   __shared__ uchar4 mi[kNCMax];
+  uint32_t n_in = 0;  // pairs inside the cut-off (profile mode only)
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     int x, y, z;
     mdecode(c, x, y, z);
@@ -70,6 +73,7 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ le
           float dx = sx - xj.x, dy = sy - xj.y, dz = sz - xj.z;
           float r2 = dx * dx + dy * dy + dz * dz;
           bool in = r2 > 0.f && r2 < rc2;
+          if (kCount) n_in += (in && vi);
           float r2s = in ? r2 : 1.f;
           float rinv = rsqrtf(r2s);
           float rr = r2s * rinv;
@@ -104,6 +108,11 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ le
       }
     }
   }
+  if (kCount) {
+    unsigned long long v = n_in;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(useful, v);
+  }
 }
 
 }  // namespace
@@ -113,10 +122,14 @@ cudaError_t p2p_l2p(Ctx &c, float *acc, cudaStream_t st) {
   const int T = 256;
   unsigned g = blocks_for(c.nleaves, 8);
   if (g > 152 * 16) g = 152 * 16;
-  k_p2p_l2p<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range),
-                             P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4),
-                             P<float>(c.L), P<uint32_t>(c.idx), c.n, c.p, c.nc, (float)c.prm.box, (float)(1.0 / c.rs),
-                             (float)(c.rc * c.rc), (float)c.prm.G, acc);
+  auto kern = c.prm.profile ? k_p2p_l2p<true> : k_p2p_l2p<false>;
+  // zeroed by hfmm_short_range_forces before the first phase
+  unsigned long long *useful = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 2);
+  kern<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
+                        P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<float>(c.L),
+                        P<uint32_t>(c.idx), c.n, c.p, c.nc, (float)c.prm.box, (float)(1.0 / c.rs), (float)(c.rc * c.rc),
+                        (float)c.prm.G, acc, useful);
+  note_launch();
   return cudaGetLastError();
 }
 

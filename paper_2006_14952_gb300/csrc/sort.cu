@@ -4,6 +4,8 @@
 
 namespace hfmm {
 
+std::atomic<long long> g_launches{0};
+
 cudaError_t ensure(DBuf &b, size_t bytes) {
   if (bytes <= b.cap) return cudaSuccess;
   size_t want = bytes + bytes / 4 + 256;
@@ -158,8 +160,11 @@ cudaError_t scan_u32(const uint32_t *in, uint32_t *out, uint64_t *total, size_t 
   uint64_t *bsum = P<uint64_t>(tmp);
   if (n == 0) return cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum);
+  note_launch();
   k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, total);
+  note_launch();
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, bsum);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -263,12 +268,14 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
     int bits = bit_hi - sh < 8 ? bit_hi - sh : 8;
     uint32_t mask = (1u << bits) - 1u;
     k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, sh, mask, counts, ntiles);
+    note_launch();
     e = scan_u32(counts, offs, total, m, scan_tmp, st);
     if (e != cudaSuccess) return e;
     if (vals)
       k_radix_scatter<true><<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, sh, mask, offs, ntiles);
     else
       k_radix_scatter<false><<<ntiles, kSortThreads, 0, st>>>(ka, nullptr, kb, nullptr, n, sh, mask, offs, ntiles);
+    note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint64_t *tk = ka;

@@ -147,6 +147,7 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   int64_t nf = 27;
   TRY(ensure(c.front, 1024 * 8));
   k_init_frontier<<<1, 32, 0, st>>>(P<uint64_t>(c.front));
+  note_launch();
   size_t cap_m2l = c.m2l.cap / 8, cap_p2p = c.p2p.cap / 8;
   uint64_t *d_tot = P<uint64_t>(c.d_small);
   while (nf > 0) {
@@ -155,6 +156,7 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
     TRY(ensure(c.offs, 3 * nf * sizeof(uint32_t)));
     k_mac_count<<<blocks_for(nf, T), T, 0, st>>>(P<uint64_t>(c.front), nf, P<uint4>(c.cell), P<int2>(c.kids), m,
                                                  P<uint8_t>(c.cls), P<uint32_t>(c.counts));
+    note_launch();
     TRY(scan_u32(P<uint32_t>(c.counts), P<uint32_t>(c.offs), d_tot, 3 * nf, c.tmp, st));
     TRY(cudaMemcpyAsync(c.h_pinned, P<uint32_t>(c.offs) + nf, 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(reinterpret_cast<uint32_t *>(c.h_pinned) + 1, P<uint32_t>(c.offs) + 2 * nf, 4,
@@ -178,6 +180,7 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
     k_mac_emit<<<blocks_for(nf, T), T, 0, st>>>(P<uint64_t>(c.front), nf, P<uint8_t>(c.cls), P<uint32_t>(c.offs),
                                                 P<int2>(c.kids), P<uint64_t>(c.m2l) + c.nm2l,
                                                 P<uint64_t>(c.p2p) + c.np2p, P<uint64_t>(c.front_next));
+    note_launch();
     TRY(cudaGetLastError());
     c.nm2l += add_m2l;
     c.np2p += add_p2p;
@@ -222,12 +225,14 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
     if (alt) std::swap(L, A);
     k_list_bounds<<<blocks_for(n, T), T, 0, st>>>(P<uint64_t>(L), n, P<uint32_t>(which ? c.p2p_beg : c.m2l_beg),
                                                   P<uint32_t>(which ? c.p2p_end : c.m2l_end));
+    note_launch();
     TRY(cudaGetLastError());
   }
   if (c.np2p > 0) {
     TRY(cudaMemsetAsync(c.d_small.p, 0, 8, st));
     k_pairs_in_list<<<blocks_for(c.np2p, T), T, 0, st>>>(P<uint64_t>(c.p2p), c.np2p, P<uint2>(c.range),
                                                          reinterpret_cast<unsigned long long *>(c.d_small.p));
+    note_launch();
     TRY(cudaMemcpyAsync(c.h_pinned, c.d_small.p, 8, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     c.p2p_particle_pairs = (int64_t)c.h_pinned[0];

@@ -172,6 +172,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   TRY(ensure(c.d_small, 256));
   if (c.prm.profile) cudaEventRecord(c.ev[0], st);
   k_keys<<<blocks_for(n, T), T, 0, st>>>(pos, n, c.prm.box, P<uint64_t>(c.key), P<uint32_t>(c.idx));
+  note_launch();
   bool alt = false;
   TRY(radix_sort_u64(P<uint64_t>(c.key), P<uint32_t>(c.idx), P<uint64_t>(c.key_alt), P<uint32_t>(c.idx_alt), n, 0,
                      63, &alt, c.tmp, st));
@@ -183,6 +184,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   uint32_t *perm = P<uint32_t>(c.idx);
   if (c.prm.profile) cudaEventRecord(c.ev[1], st);
   k_gather<<<blocks_for(n, T), T, 0, st>>>(pos, perm, n, c.prm.box, P<double>(c.xs));
+  note_launch();
 
   // level-synchronous node build
   size_t cap_nodes = (size_t)(2 * n / (c.prm.leaf_max > 1 ? c.prm.leaf_max : 1) + 64);
@@ -190,6 +192,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   TRY(ensure(c.range, cap_nodes * sizeof(uint2)));
   TRY(ensure(c.kids, cap_nodes * sizeof(int2)));
   k_root<<<1, 1, 0, st>>>(P<uint4>(c.cell), P<uint2>(c.range), n);
+  note_launch();
   int64_t lo = 0, cnt = 1, total = 1;
   int level = 0;
   c.level_start[0] = 0;
@@ -200,6 +203,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
     TRY(ensure(c.koff, cnt * sizeof(uint32_t)));
     k_split_count<<<blocks_for(cnt, T), T, 0, st>>>(P<uint2>(c.range), lo, cnt, level, c.prm.leaf_max, key,
                                                     P<uint32_t>(c.bounds), P<uint32_t>(c.nkids));
+    note_launch();
     TRY(scan_u32(P<uint32_t>(c.nkids), P<uint32_t>(c.koff), d_tot, cnt, c.tmp2, st));
     TRY(cudaMemcpyAsync(c.h_pinned, d_tot, 8, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
@@ -214,6 +218,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
     k_emit_children<<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, total, P<uint32_t>(c.bounds), P<uint32_t>(c.nkids),
                                                       P<uint32_t>(c.koff), P<uint4>(c.cell), P<uint2>(c.range),
                                                       P<int2>(c.kids));
+    note_launch();
     TRY(cudaGetLastError());
     ++level;
     if (nxt == 0) break;
@@ -231,6 +236,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   TRY(ensure(c.nkids, total * sizeof(uint32_t)));
   TRY(ensure(c.koff, total * sizeof(uint32_t)));
   k_leaf_flags<<<blocks_for(total, T), T, 0, st>>>(P<int2>(c.kids), total, P<uint32_t>(c.nkids));
+  note_launch();
   TRY(scan_u32(P<uint32_t>(c.nkids), P<uint32_t>(c.koff), d_tot, total, c.tmp2, st));
   TRY(cudaMemcpyAsync(c.h_pinned, d_tot, 8, cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
@@ -238,9 +244,11 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   TRY(ensure(c.leaves, c.nleaves * sizeof(uint32_t)));
   k_leaf_list<<<blocks_for(total, T), T, 0, st>>>(P<uint32_t>(c.nkids), P<uint32_t>(c.koff), total,
                                                   P<uint32_t>(c.leaves));
+  note_launch();
   k_leaf_offsets<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell),
                                                          P<uint2>(c.range), P<double>(c.xs), mass, perm, n,
                                                          c.prm.box, P<float4>(c.pm4));
+  note_launch();
   TRY(cudaGetLastError());
   if (c.prm.profile) cudaEventRecord(c.ev[2], st);
   c.have_tree = true;

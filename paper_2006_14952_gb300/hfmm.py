@@ -38,7 +38,8 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnodes", C.c_int64), ("nleaves", C.c_int64), ("nlevels", C.c_int32),
                 ("traverse_iters", C.c_int32), ("np2p", C.c_int64), ("nm2l", C.c_int64),
-                ("p2p_particle_pairs", C.c_int64), ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
+                ("p2p_particle_pairs", C.c_int64), ("p2p_useful_pairs", C.c_int64), ("launches", C.c_int64),
+                ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
                 ("t_upward", C.c_float), ("t_traverse", C.c_float), ("t_lists", C.c_float), ("t_m2l", C.c_float),
                 ("t_l2l", C.c_float), ("t_p2p", C.c_float)]
 
