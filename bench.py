@@ -34,11 +34,11 @@ METRIC = "short-range forces/s, N=2M clustered, rms err≤1e-4: learned+TF32 vs 
 UNIT = "forces/s"
 FP32_LANES_PER_SM = 128
 N_SM = 152
-# Algorithmic FP32 work of one P2P pair inside the cut-off: separation (3),
-# r^2 (5: 1 mul + 2 fma), rsqrt (1), r (1), x = r/r_s (1), the truncation factor
-# S(x) = erfc(x/2) + x e^(-x^2/4)/sqrt(pi) (exp 1, polynomial 2 x 6 fma = 12,
-# 2 mul + 1 fma = 4 for assembling it), 1/r^3 and mass (3), accumulation (6).
-P2P_FLOPS_PER_PAIR = 37
+# FP32 work of one P2P pair inside the cut-off (FMA = 2 flop): separation (3),
+# r^2 (1 mul + 2 fma = 5), rsqrt (1), t = r / R_c (2), the truncation factor
+# S = exp2(r^2 k) Q(t) with Q of degree 9 (exponent 1 + exp2 1 + 9 fma 18 +
+# product 1 = 21), -S m / r^3 (4), accumulation (3 fma = 6).
+P2P_FLOPS_PER_PAIR = 42
 
 
 def parse():
@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nfw-2m")
+    ap.add_argument("--n", type=int, default=0, help="same kind of set at another N (profiling only)")
     ap.add_argument("--theta", type=float, default=0.3)
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--accuracy-sinks", type=int, default=20000)
@@ -202,6 +203,8 @@ def main():
     from paper_2006_14952_gb300 import workloads as W
 
     cfg = W.CONFIGS[args.workload]
+    if args.n:
+        cfg = W.scaled(cfg, args.n)
     if args.impl == "reference":
         run_reference(args, cfg)
         return

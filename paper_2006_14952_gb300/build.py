@@ -34,12 +34,21 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+GENERATED = os.path.join(CSRC, "m2l_body.cuh")
+
+
+def _generate():
+    """Straight-line M2L bodies (gen_m2l.py); rewritten only when they change."""
+    subprocess.check_call([sys.executable, os.path.join(CSRC, "gen_m2l.py"), GENERATED])
+
+
 def _inputs():
-    return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) +
+            [os.path.join(CSRC, "gen_m2l.py")])
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(GENERATED):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(s) <= t for s in _inputs())
@@ -62,6 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     if not force and up_to_date():
         return LIB
+    _generate()
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))

@@ -1,5 +1,6 @@
 // C ABI of libhfmm (declared in include/hfmm.h): context lifecycle, argument
 // checks, error mapping, phase orchestration, statistics and exports.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -45,6 +46,44 @@ bool valid_params(const hfmm_params &p, std::string &why) {
 }
 
 }  // namespace
+
+namespace hfmm {
+
+PairFit fit_pair_factor(double rs, double rc) {
+  constexpr int N = 10;
+  const double pi = 3.14159265358979323846;
+  const double xc = rc / rs;
+  double fk[N], cj[N], T[N + 1][N], mono[N];
+  for (int k = 0; k < N; ++k) {
+    double t = 0.5 * (1.0 + std::cos(pi * (k + 0.5) / N));
+    double x = xc * t;
+    fk[k] = std::exp(0.25 * x * x) * std::erfc(0.5 * x) + x / std::sqrt(pi);
+  }
+  for (int j = 0; j < N; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += fk[k] * std::cos(pi * j * (k + 0.5) / N);
+    cj[j] = (j == 0 ? 1.0 : 2.0) * s / N;
+  }
+  // T_j(2t - 1) as monomial coefficients in t
+  std::memset(T, 0, sizeof(T));
+  T[0][0] = 1.0;
+  T[1][0] = -1.0;
+  T[1][1] = 2.0;
+  for (int j = 1; j + 1 < N; ++j)
+    for (int i = 0; i < N; ++i) T[j + 1][i] = (i ? 4.0 * T[j][i - 1] : 0.0) - 2.0 * T[j][i] - T[j - 1][i];
+  for (int i = 0; i < N; ++i) {
+    mono[i] = 0.0;
+    for (int j = 0; j < N; ++j) mono[i] += cj[j] * T[j][i];
+  }
+  PairFit f;
+  for (int i = 0; i < N; ++i) f.c[i] = (float)mono[i];
+  f.inv_rc = (float)(1.0 / rc);
+  f.rc2 = (float)(rc * rc);
+  f.kexp = (float)(-1.4426950408889634 / (4.0 * rs * rs));
+  return f;
+}
+
+}  // namespace hfmm
 
 extern "C" {
 
@@ -92,6 +131,7 @@ int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
   c.theta2 = params->theta * params->theta;
   c.p = params->order;
   c.nc = ncoef(c.p);
+  c.fit = fit_pair_factor(c.rs, c.rc);
   cudaError_t e = cudaMallocHost(&c.h_pinned, 64);
   if (e == cudaSuccess) e = ensure(c.d_small, 256);
   for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&c.ev[i]);
@@ -150,7 +190,7 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if ((e = ensure(c.L, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc L");
   if ((e = cudaMemsetAsync(c.L.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset L");
   bool prof = c.prm.profile != 0;
-  if (prof && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 2, 0, 8, st)) != cudaSuccess)
+  if (prof && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "memset counter");
   if (prof) cudaEventRecord(c.ev[3], st);
   if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
@@ -214,7 +254,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->p2p_useful_pairs = -1;
   if (c.prm.profile && c.n > 0) {
     unsigned long long u = 0;
-    if (cudaMemcpy(&u, P<uint64_t>(c.d_small) + 2, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
+    if (cudaMemcpy(&u, P<uint64_t>(c.d_small) + 4, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
       o->p2p_useful_pairs = (int64_t)u;
   }
   o->launches = (int64_t)g_launches.load();

@@ -95,11 +95,22 @@ cudaError_t scan_u32(const uint32_t *in, uint32_t *out, uint64_t *total, size_t 
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
                            int bit_lo, int bit_hi, bool *in_alt, DBuf &tmp, cudaStream_t st);
 
+// ---------------------------------------------------------------- pair force
+// S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi) = exp2(r^2 kexp) Q(r / R_c),
+// Q(t) = sum_j c[j] t^j (degree 9), kexp = -log2(e) / (4 r_s^2).
+struct PairFit {
+  float c[10];
+  float inv_rc, rc2, kexp;
+};
+// Chebyshev interpolation (10 nodes on [0, R_c]) of e^(x^2/4) erfc(x/2) + x/sqrt(pi), in FP64.
+PairFit fit_pair_factor(double rs, double rc);
+
 // ---------------------------------------------------------------- context
 struct Ctx {
   hfmm_params prm{};
   double rs = 0, rc = 0;        // split scale and cut-off radius
   double rc2h = 0, theta2 = 0;  // MAC thresholds (half units squared; theta^2)
+  PairFit fit{};
   int p = 4, nc = 35;
   std::string err;
 

@@ -1,8 +1,8 @@
-// Expansion passes in scaled Cartesian form (Sec. 2.1, Eqs. p2m, m2m, m2l, l2l):
+// Upward and downward translation passes in scaled Cartesian form (Sec. 2.1,
+// Eqs. p2m, m2m, l2l):
 //   M~_m = M_m / h^|m|,   L~_n = L_n h^(|n|+1),   h = side of the cell.
-// With this scaling the M2M and L2L operators are the same on every level and
-// the M2L kernel is a contraction with the derivative tensor of the truncated
-// potential erfc(r / 2r_s) / r evaluated in units of the larger cell side.
+// With this scaling the M2M and L2L operators are the same on every level.
+// (M2L is in m2l.cu.)
 #include "common.cuh"
 
 namespace hfmm {
@@ -119,95 +119,6 @@ __global__ void k_l2l(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, c
   }
 }
 
-// n! / (2^k k! (n-2k)!)
-__device__ __forceinline__ float hcoef(int n, int k) { return factf(n) / (ldexpf(1.f, k) * factf(k) * factf(n - 2 * k)); }
-
-// Generic M2L on CUDA cores, one warp per sink cell, FP32:
-//   L~_n(A) += (h_A/h)^(|n|+1) sum_m (h_B/h)^|m| M~_m(B) D^_{n+m}(R / h),   h = max(h_A, h_B),
-// with D^ the derivative tensor of erfc(r / 2(r_s/h)) / r (radial form).
-__global__ void k_m2l_generic(int64_t nn, const uint4 *__restrict__ cell, const uint32_t *__restrict__ beg,
-                              const uint32_t *__restrict__ end, const uint64_t *__restrict__ lst,
-                              const float *__restrict__ M, float *__restrict__ L, int p, int nc, float rs_over_box) {
-  __shared__ uchar4 mi[kNCMax];
-  __shared__ float sM[8][kNCMax];
-  __shared__ float sD[8][kNCMax];
-  build_mi(mi, nc);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const float kInvSqrtPi = 0.56418958354775628f;
-  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; k < nn; k += nw) {
-    uint32_t tb = beg[k], te = end[k];
-    if (tb == te) continue;
-    uint4 ca = cell[k];
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (uint32_t t = tb; t < te; ++t) {
-      uint64_t e = lst[t];
-      uint32_t b = pair_src(e), s = pair_shift(e);
-      uint4 cb = cell[b];
-      int64_t dd[3];
-      half_delta(ca, cb, s, dd);
-      uint32_t lr = ca.w < cb.w ? ca.w : cb.w;  // level of the larger cell
-      float inv2w = 1.f / (float)(2 * half_width(lr));
-      float R[3] = {-(float)dd[0] * inv2w, -(float)dd[1] * inv2w, -(float)dd[2] * inv2w};
-      float sa = ldexpf(1.f, (int)lr - (int)ca.w), sb = ldexpf(1.f, (int)lr - (int)cb.w);
-      float rsh = rs_over_box * (float)(1u << lr);
-      float r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
-      float r = sqrtf(r2), x = r / rsh;
-      float f[kPMax + 1];
-      f[0] = erfcf(0.5f * x) / r;
-      float tk = -expf(-0.25f * x * x) * kInvSqrtPi / rsh;
-      float inv2rs2 = 0.5f / (rsh * rsh);
-#pragma unroll
-      for (int q = 0; q < kPMax; ++q) {
-        if (q < p) {
-          f[q + 1] = (-(float)(2 * q + 1) * f[q] + tk) / r2;
-          tk = -tk * inv2rs2;
-        }
-      }
-      for (int c = lane; c < nc; c += 32) {
-        uchar4 n = mi[c];
-        float sum = 0.f;
-        for (int kx = 0; 2 * kx <= n.x; ++kx)
-          for (int ky = 0; 2 * ky <= n.y; ++ky)
-            for (int kz = 0; 2 * kz <= n.z; ++kz) {
-              float cf = hcoef(n.x, kx) * hcoef(n.y, ky) * hcoef(n.z, kz) * powi(R[0], n.x - 2 * kx) *
-                         powi(R[1], n.y - 2 * ky) * powi(R[2], n.z - 2 * kz);
-              int o = n.w - kx - ky - kz;
-              float fo = f[0];
-#pragma unroll
-              for (int q = 1; q <= kPMax; ++q)
-                if (q == o) fo = f[q];
-              sum += cf * fo;
-            }
-        sD[w][c] = sum;
-        sM[w][c] = M[(size_t)b * nc + c] * powi(sb, n.w);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        int c = lane + 32 * q;
-        if (c < nc) {
-          uchar4 n = mi[c];
-          int rem = p - n.w;
-          float sum = 0.f;
-          for (int e2 = 0; e2 < ncoef(rem); ++e2) {
-            uchar4 m = mi[e2];
-            sum += sM[w][e2] * sD[w][midx(n.x + m.x, n.y + m.y, n.z + m.z)];
-          }
-          acc[q] += sum * powi(sa, n.w + 1);
-        }
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      int c = lane + 32 * q;
-      if (c < nc) L[(size_t)k * nc + c] += acc[q];
-    }
-  }
-}
-
 }  // namespace
 
 cudaError_t upward(Ctx &c, cudaStream_t st) {
@@ -226,18 +137,6 @@ cudaError_t upward(Ctx &c, cudaStream_t st) {
     k_m2m<<<gl, T, 0, st>>>(lo, cnt, P<uint4>(c.cell), P<int2>(c.kids), c.nc, P<float>(c.M));
     note_launch();
   }
-  return cudaGetLastError();
-}
-
-cudaError_t m2l_pass(Ctx &c, cudaStream_t st) {
-  if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
-  const int T = 256;
-  unsigned g = blocks_for(c.nnodes, 8);
-  if (g > 152 * 32) g = 152 * 32;
-  k_m2l_generic<<<g, T, 0, st>>>(c.nnodes, P<uint4>(c.cell), P<uint32_t>(c.m2l_beg), P<uint32_t>(c.m2l_end),
-                                 P<uint64_t>(c.m2l), P<float>(c.M), P<float>(c.L), c.p, c.nc,
-                                 (float)(c.rs / c.prm.box));
-  note_launch();
   return cudaGetLastError();
 }
 

@@ -1,0 +1,158 @@
+// M2L on CUDA cores (Eq. m2l with the truncated derivative tensors of Sec. 2.2):
+//   L~_n(A) += sum_m M~_m(B) h_B^|m| h_A^(|n|+1) D_{n+m}(R),   R = z_A - z_B',
+// evaluated per pair in units of r = |R|:  D_c(R) = r^-(|c|+1) D^_c(R / r), so
+//   L~_n(A) += u^(|n|+1) sum_m (v^|m| M~_m(B)) D^_{n+m}(R^),  u = h_A / r, v = h_B / r,
+// with |R^| = 1 and u, v <= theta: every factor is O(1) or smaller for any pair
+// of levels.  D^ is the derivative tensor of erfc(x r^ / 2) / r^ at r^ = 1,
+// x = r / r_s, from the radial prefactors f_(k) = ((1/r) d/dr)^k psi:
+//   D^_c = sum_{k_d <= c_d/2} prod_d [c_d! / (2^k_d k_d! (c_d - 2k_d)!)] R^_d^(c_d-2k_d) f_(|c|-|k|).
+//
+// One lane per (sink, source) pair; a warp walks the pairs of one sink (lists
+// are grouped by sink), keeps its partial local expansion in registers and
+// reduces it across the warp at the end, so no atomics are used and the
+// result is deterministic.  The expansion order is a template parameter: all
+// index arithmetic is literal in the generated straight-line bodies
+// (gen_m2l.py -> m2l_body.cuh).  For p >= 6 the output coefficients are split
+// over G warps (slice g owns the outputs with index = g mod G); for p >= 7 the
+// scaled source multipoles of each lane's pair are staged in shared memory.
+#include "common.cuh"
+#include "m2l_body.cuh"
+
+namespace hfmm {
+namespace {
+
+template <int P, int G, int g>
+__device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, const uint4 *__restrict__ cell,
+                                         const uint64_t *__restrict__ lst, const float *__restrict__ M,
+                                         float *__restrict__ L, int ldm, float inv_rs, float *__restrict__ wsm) {
+  constexpr int NC = ncoef(P);
+  constexpr int NS = (NC + G - 1) / G;
+  constexpr bool kSmem = M2LSlices<P>::kSmem;
+  const int lane = threadIdx.x & 31;
+  const float kInvSqrtPi = 0.56418958354775628f;
+  const uint4 ca = cell[k];
+  float acc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = 0.f;
+  for (uint32_t t = tb + lane; t < te; t += 32) {
+    const uint64_t e = lst[t];
+    const uint32_t b = pair_src(e), sh = pair_shift(e);
+    const uint4 cb = cell[b];
+    int64_t dd[3];
+    half_delta(ca, cb, sh, dd);
+    // R = z_A - z_B' in half units (exact integers below 2^24)
+    const float Rx = -(float)dd[0], Ry = -(float)dd[1], Rz = -(float)dd[2];
+    const float r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+    const float rinv = rsqrtf(r2);
+    const float x = r2 * rinv * inv_rs;  // r / r_s
+    const float u = (float)(2 * half_width(ca.w)) * rinv, v = (float)(2 * half_width(cb.w)) * rinv;
+    float f[P + 1];
+    f[0] = erfcf(0.5f * x);
+    float tk = -x * kInvSqrtPi * __expf(-0.25f * x * x);
+    const float hx2 = 0.5f * x * x;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      f[q + 1] = -(float)(2 * q + 1) * f[q] + tk;
+      tk = -tk * hx2;
+    }
+    float U[P + 1];
+    U[0] = u;
+#pragma unroll
+    for (int q = 1; q <= P; ++q) U[q] = U[q - 1] * u;
+    const float *Mb = M + (size_t)b * ldm;
+    if constexpr (kSmem) {
+      float *col = wsm + lane;
+      M2LLoad<P>::template run<32>(Mb, v, col);
+      M2LBody<P, G, g>::run(Rx * rinv, Ry * rinv, Rz * rinv, f, U, col, acc);
+    } else {
+      float Mp[NC];
+      M2LLoad<P>::template run<1>(Mb, v, Mp);
+      M2LBody<P, G, g>::run(Rx * rinv, Ry * rinv, Rz * rinv, f, U, Mp, acc);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    float a = acc[s];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    const int n = s * G + g;
+    if (lane == 0 && n < NC) L[(size_t)k * ldm + n] = a;
+  }
+}
+
+template <int P, int G>
+__global__ void __launch_bounds__(128) k_m2l(int64_t nn, const uint4 *__restrict__ cell,
+                                             const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
+                                             const uint64_t *__restrict__ lst, const float *__restrict__ M,
+                                             float *__restrict__ L, int ldm, float inv_rs) {
+  extern __shared__ float sm[];
+  float *wsm = sm + (threadIdx.x >> 5) * (M2LSlices<P>::kSmem ? ncoef(P) * 32 : 0);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nn * G; w += nw) {
+    const uint32_t k = (uint32_t)(w / G);
+    const int g = (int)(w % G);
+    const uint32_t tb = beg[k], te = end[k];
+    if (tb == te) continue;
+    if constexpr (G == 1) {
+      m2l_sink<P, 1, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+    } else if constexpr (G == 2) {
+      if (g == 0) m2l_sink<P, 2, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else m2l_sink<P, 2, 1>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+    } else if constexpr (G == 4) {
+      if (g == 0) m2l_sink<P, 4, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else if (g == 1) m2l_sink<P, 4, 1>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else if (g == 2) m2l_sink<P, 4, 2>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else m2l_sink<P, 4, 3>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+    } else {
+      static_assert(G == 8, "slices");
+      switch (g) {
+        case 0: m2l_sink<P, 8, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 1: m2l_sink<P, 8, 1>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 2: m2l_sink<P, 8, 2>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 3: m2l_sink<P, 8, 3>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 4: m2l_sink<P, 8, 4>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 5: m2l_sink<P, 8, 5>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 6: m2l_sink<P, 8, 6>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        default: m2l_sink<P, 8, 7>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+      }
+    }
+  }
+}
+
+template <int P>
+cudaError_t launch(Ctx &c, cudaStream_t st) {
+  constexpr int G = M2LSlices<P>::G;
+  unsigned g = blocks_for((size_t)c.nnodes * G, 4);
+  if (g > 152 * 64) g = 152 * 64;
+  // r / r_s with r in half units: x = r_half * (L / 2^22) / r_s
+  const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
+  size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float) : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_m2l<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_m2l<P, G><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_beg),
+                                    hfmm::P<uint32_t>(c.m2l_end), hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M),
+                                    hfmm::P<float>(c.L), c.nc, inv_rs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t m2l_pass(Ctx &c, cudaStream_t st) {
+  if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
+  switch (c.p) {
+    case 1: return launch<1>(c, st);
+    case 2: return launch<2>(c, st);
+    case 3: return launch<3>(c, st);
+    case 4: return launch<4>(c, st);
+    case 5: return launch<5>(c, st);
+    case 6: return launch<6>(c, st);
+    case 7: return launch<7>(c, st);
+    case 8: return launch<8>(c, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hfmm

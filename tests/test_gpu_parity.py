@@ -165,3 +165,32 @@ def test_host_buffer_entry_point_matches_device_path():
     s2 = solver(pm_grid=32)
     acc2 = s2.short_range_forces_host(np.ascontiguousarray(pos), mass)
     np.testing.assert_array_equal(acc2, acc.astype(np.float32))
+
+
+def test_pair_force_law_across_the_cutoff_range():
+    """1000 isolated pairs, separations log-spaced over (0.03, 1) R_c, against the
+    FP64 direct sum (the closed-form g(r)).  Error budget per pair: 3e-6 for the
+    FP32 evaluation (interpolant 1.2e-6, Horner rounding with alternating
+    coefficients ~1e-6, exp2 and rsqrt a few ulp), plus the rounding of the two
+    FP32 offsets from their leaf centres, 4 * 2^-24 * sqrt(3) h_leaf / r."""
+    rng = np.random.default_rng(5)
+    g = (np.arange(10) + 0.5) / 10.0
+    cx, cy, cz = np.meshgrid(g, g, g, indexing="ij")
+    centres = np.stack([cx.ravel(), cy.ravel(), cz.ravel()])
+    s = solver(pm_grid=128)
+    rc = s.rc
+    r = rc * np.logspace(-1.5, np.log10(0.9999), 1000)
+    d = rng.standard_normal((3, 1000))
+    d /= np.linalg.norm(d, axis=0)
+    pos = np.concatenate([centres, centres + r * d], axis=1)
+    mass = np.full(2000, 1 / 2000, dtype=np.float32)
+    s, acc = run_gpu(pos, mass, pm_grid=128)
+    ref = oracle.direct_sr(pos, mass, 1.0, s.rs, s.rc)
+    e = np.linalg.norm(acc - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    nodes = s.export("nodes")
+    h_leaf = (1.0 / 2.0 ** nodes[nodes[:, 7] == 0, 0]).max()
+    rr = np.concatenate([r, r])
+    bound = 3e-6 + 4 * 2.0 ** -24 * np.sqrt(3) * h_leaf / rr
+    w = int(np.argmax(e / bound))
+    assert np.all(e < bound), f"worst r/R_c {rr[w] / rc:.4f}: err {e[w]:.3e} > bound {bound[w]:.3e}"
+    assert np.median(e) < 1e-6
