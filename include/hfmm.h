@@ -159,6 +159,33 @@ enum {
 };
 int hfmm_export(hfmm_ctx *ctx, int what, void *host_buf, size_t *bytes);
 
+/*
+ * Allocation-free Morton keys + sort.  The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory at the point of
+ * the call - for example a host runtime that plans all GPU memory up front and
+ * forbids further cudaMalloc, or code that must not risk the implicit device
+ * synchronisation cudaMalloc/cudaFree can cause.  It computes what the first
+ * steps of hfmm_build_tree compute: wrap into [0, box), 63-bit Morton keys on a
+ * 2^21 grid per side, stable sort by (key, input index).
+ *  pos_soa  device FP64 [3][n] (caller's)       keys_out device uint64 [n] (caller's)
+ *  perm_out device uint32 [n]: input index of each sorted key (caller's)
+ * Scratch: one file-scope device array of fixed size (about 6.5 MB, enough for
+ * HFMM_NOALLOC_MAX_N particles) that every GPU loading the library holds until
+ * the process exits.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current, so make the first call on a
+ * device before any stream capture.  Every call on a device shares the array:
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  Nothing in the array is
+ * assumed to start at zero: each call writes every word before reading it.
+ * Returns HFMM_OK; HFMM_ERR_CAPACITY if n > HFMM_NOALLOC_MAX_N; HFMM_ERR_ARG
+ * for n < 0, box <= 0 or a null pointer with n > 0; HFMM_ERR_CUDA if a launch
+ * fails.  Work is enqueued on `stream`; the call does not synchronise.
+ */
+#define HFMM_NOALLOC_MAX_N 524288
+int hfmm_morton_sort_noalloc(const double *pos_soa, int64_t n, double box, uint64_t *keys_out, uint32_t *perm_out,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

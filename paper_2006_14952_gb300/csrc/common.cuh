@@ -95,6 +95,13 @@ cudaError_t scan_u32(const uint32_t *in, uint32_t *out, uint64_t *total, size_t 
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
                            int bit_lo, int bit_hi, bool *in_alt, DBuf &tmp, cudaStream_t st);
 
+// The same sort with all scratch in a caller-provided region (no allocation);
+// radix_sort_scratch_bytes(n) is the size that region needs.
+size_t radix_sort_scratch_bytes(size_t n);
+cudaError_t radix_sort_u64_into(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
+                                int bit_lo, int bit_hi, bool *in_alt, void *scratch, size_t scratch_bytes,
+                                cudaStream_t st);
+
 // ---------------------------------------------------------------- pair force
 // S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi) = exp2(r^2 kexp) Q(r / R_c),
 // Q(t) = sum_j c[j] t^j (degree 9), kexp = -log2(e) / (4 r_s^2).

@@ -291,3 +291,60 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
 }
 
 }  // namespace hfmm
+
+namespace hfmm {
+
+// ------------------------------------------------------------------ caller-provided scratch
+// The same scan and sort as above, with every scratch word taken from a
+// caller-provided region instead of a growable buffer (nothing is allocated).
+
+size_t radix_sort_scratch_bytes(size_t n) {
+  size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  size_t m = 256 * ntiles;
+  size_t nb = (m + kScanTile - 1) / kScanTile;
+  return 2 * m * sizeof(uint32_t) + (nb + 2) * sizeof(uint64_t) + 64;
+}
+
+cudaError_t radix_sort_u64_into(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, size_t n,
+                                int bit_lo, int bit_hi, bool *in_alt, void *scratch, size_t scratch_bytes,
+                                cudaStream_t st) {
+  *in_alt = false;
+  if (n <= 1 || bit_hi <= bit_lo) return cudaSuccess;
+  if (radix_sort_scratch_bytes(n) > scratch_bytes) return cudaErrorInvalidValue;
+  unsigned ntiles = (unsigned)((n + kSortTile - 1) / kSortTile);
+  size_t m = (size_t)256 * ntiles;
+  size_t nb = (m + kScanTile - 1) / kScanTile;
+  uint32_t *counts = static_cast<uint32_t *>(scratch);
+  uint32_t *offs = counts + m;
+  uint64_t *total = reinterpret_cast<uint64_t *>(offs + m + (m & 1));
+  uint64_t *bsum = total + 1;
+  uint64_t *ka = keys, *kb = keys_alt;
+  uint32_t *va = vals, *vb = vals_alt;
+  bool alt = false;
+  for (int sh = bit_lo; sh < bit_hi; sh += 8) {
+    int bits = bit_hi - sh < 8 ? bit_hi - sh : 8;
+    uint32_t mask = (1u << bits) - 1u;
+    k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, sh, mask, counts, ntiles);
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(counts, m, bsum);
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, total);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(counts, offs, m, bsum);
+    if (vals)
+      k_radix_scatter<true><<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, sh, mask, offs, ntiles);
+    else
+      k_radix_scatter<false><<<ntiles, kSortThreads, 0, st>>>(ka, nullptr, kb, nullptr, n, sh, mask, offs, ntiles);
+    note_launch(5);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint64_t *tk = ka;
+    ka = kb;
+    kb = tk;
+    uint32_t *tv = va;
+    va = vb;
+    vb = tv;
+    alt = !alt;
+  }
+  *in_alt = alt;
+  return cudaSuccess;
+}
+
+}  // namespace hfmm
