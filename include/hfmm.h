@@ -67,7 +67,8 @@ typedef struct {
   int size_rule;       /* L in theta = L / S_c: 0 = side of the source cell (as printed),
                           1 = larger side of the two cells */
   int m2l_precision;   /* 0 = FP32 CUDA cores */
-  int profile;         /* 1 = record per-phase CUDA-event timings (hfmm_get_stats) */
+  int profile;         /* bit 0: record per-phase CUDA-event timings; bit 1: count P2P
+                          particle pairs (extra work; for statistics runs only) */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */
@@ -76,10 +77,10 @@ typedef struct {
   int32_t nlevels, traverse_iters;
   int64_t np2p;           /* P2P leaf pairs */
   int64_t nm2l;           /* M2L cell pairs */
-  int64_t p2p_particle_pairs; /* particle pairs evaluated by P2P (incl. masked) */
-  int64_t p2p_useful_pairs;   /* pairs with 0 < r < R_c (params.profile = 1, else -1) */
+  int64_t p2p_particle_pairs; /* particle pairs evaluated by P2P incl. masked (profile bit 1, else -1) */
+  int64_t p2p_useful_pairs;   /* pairs with 0 < r < R_c (profile bit 1, else -1) */
   int64_t launches;           /* kernels launched by this library in this process so far */
-  /* milliseconds, filled when params.profile = 1 (else -1) */
+  /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
 } hfmm_stats;
 

@@ -34,17 +34,17 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-GENERATED = os.path.join(CSRC, "m2l_body.cuh")
+GENERATED = os.path.join(CSRC, "gen_bodies.cuh")
 
 
 def _generate():
-    """Straight-line M2L bodies (gen_m2l.py); rewritten only when they change."""
-    subprocess.check_call([sys.executable, os.path.join(CSRC, "gen_m2l.py"), GENERATED])
+    """Straight-line expansion bodies (gen_bodies.py); rewritten only when they change."""
+    subprocess.check_call([sys.executable, os.path.join(CSRC, "gen_bodies.py"), GENERATED])
 
 
 def _inputs():
     return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) +
-            [os.path.join(CSRC, "gen_m2l.py")])
+            [os.path.join(CSRC, "gen_bodies.py")])
 
 
 def up_to_date() -> bool:

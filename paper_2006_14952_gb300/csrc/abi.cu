@@ -39,6 +39,7 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.transition_rule != 0 && p.transition_rule != 1) return why = "transition_rule must be 0 or 1", false;
   if (p.size_rule != 0 && p.size_rule != 1) return why = "size_rule must be 0 or 1", false;
   if (p.m2l_precision != 0) return why = "m2l_precision must be 0", false;
+  if (p.profile < 0 || p.profile > 3) return why = "profile must be 0..3", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
@@ -189,8 +190,8 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if ((e = ensure(c.M, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc M");
   if ((e = ensure(c.L, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc L");
   if ((e = cudaMemsetAsync(c.L.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset L");
-  bool prof = c.prm.profile != 0;
-  if (prof && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
+  bool prof = (c.prm.profile & 1) != 0;
+  if ((c.prm.profile & 2) && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "memset counter");
   if (prof) cudaEventRecord(c.ev[3], st);
   if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
@@ -203,9 +204,9 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (prof) cudaEventRecord(c.ev[6], st);
   if ((e = m2l_pass(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l");
   if (prof) cudaEventRecord(c.ev[7], st);
-  if ((e = l2l_pass(c, st)) != cudaSuccess) return cuda_fail(c, e, "l2l");
+  if ((e = downward(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "l2l/l2p");
   if (prof) cudaEventRecord(c.ev[8], st);
-  if ((e = p2p_l2p(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "p2p_l2p");
+  if ((e = p2p_pass(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "p2p");
   if (prof) cudaEventRecord(c.ev[9], st);
   return HFMM_OK;
 }
@@ -252,7 +253,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->nm2l = c.nm2l;
   o->p2p_particle_pairs = c.p2p_particle_pairs;
   o->p2p_useful_pairs = -1;
-  if (c.prm.profile && c.n > 0) {
+  if ((c.prm.profile & 2) && c.n > 0) {
     unsigned long long u = 0;
     if (cudaMemcpy(&u, P<uint64_t>(c.d_small) + 4, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
       o->p2p_useful_pairs = (int64_t)u;
@@ -263,7 +264,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   const int ev_pairs[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};
   for (int i = 0; i < 8; ++i) {
     *t[i] = -1.f;
-    if (c.prm.profile && c.n > 0) {
+    if ((c.prm.profile & 1) && c.n > 0) {
       float ms = -1.f;
       if (cudaEventElapsedTime(&ms, c.ev[ev_pairs[i][0]], c.ev[ev_pairs[i][1]]) == cudaSuccess) *t[i] = ms;
     }

@@ -171,8 +171,10 @@ cudaError_t traverse(Ctx &c, cudaStream_t st);
 cudaError_t sort_lists(Ctx &c, cudaStream_t st);
 cudaError_t upward(Ctx &c, cudaStream_t st);
 cudaError_t m2l_pass(Ctx &c, cudaStream_t st);
-cudaError_t l2l_pass(Ctx &c, cudaStream_t st);
-cudaError_t p2p_l2p(Ctx &c, float *acc, cudaStream_t st);
+// L2L top-down, then L2P writing the far-field accelerations in input order.
+cudaError_t downward(Ctx &c, float *acc, cudaStream_t st);
+// Cut-off P2P, added to the accelerations written by downward().
+cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st);
 
 inline unsigned blocks_for(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 

@@ -4,152 +4,169 @@
 // With this scaling the M2M and L2L operators are the same on every level.
 // (M2L is in m2l.cu.)
 #include "common.cuh"
+#include "gen_bodies.cuh"
 
 namespace hfmm {
 namespace {
 
-__device__ __forceinline__ float factf(int k) {
-  float f = 1.f;
-  for (int i = 2; i <= k; ++i) f *= (float)i;
-  return f;
-}
-
-__device__ __forceinline__ float powi(float x, int e) {
-  float r = 1.f;
-  for (int i = 0; i < e; ++i) r *= x;
-  return r;
-}
-
-// multi-index table in shared memory: {nx, ny, nz, |n|}
-__device__ __forceinline__ void build_mi(uchar4 *mi, int nc) {
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    int x, y, z;
-    mdecode(c, x, y, z);
-    mi[c] = make_uchar4((unsigned char)x, (unsigned char)y, (unsigned char)z, (unsigned char)(x + y + z));
-  }
-}
-
+// P2M, one thread per leaf: M~_m = sum_a mu_a (-1)^|m| / m! (u_a)^m, u = (x - z) / h.
+template <int P>
 __global__ void k_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
-                      const uint2 *__restrict__ range, const float4 *__restrict__ pm4, float box, int nc,
+                      const uint2 *__restrict__ range, const float4 *__restrict__ pm4, float box, int ldm,
                       float *__restrict__ M) {
-  __shared__ uchar4 mi[kNCMax];
-  build_mi(mi, nc);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nl; t += nw) {
-    uint32_t k = leaves[t];
-    uint2 r = range[k];
-    float inv_h = (float)(1u << cell[k].w) / box;
-    for (int c = lane; c < nc; c += 32) {
-      uchar4 m = mi[c];
-      float s = 0.f;
-      for (uint32_t i = r.x; i < r.x + r.y; ++i) {
-        float4 q = pm4[i];
-        s += q.w * powi(q.x * inv_h, m.x) * powi(q.y * inv_h, m.y) * powi(q.z * inv_h, m.z);
-      }
-      float coef = ((m.w & 1) ? -1.f : 1.f) / (factf(m.x) * factf(m.y) * factf(m.z));
-      M[(size_t)k * nc + c] = coef * s;
-    }
+  constexpr int NC = ncoef(P);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const uint32_t k = leaves[t];
+  const uint2 r = range[k];
+  const float inv_h = (float)(1u << cell[k].w) / box;
+  float acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.f;
+  for (uint32_t i = r.x; i < r.x + r.y; ++i) {
+    const float4 q = pm4[i];
+    P2MBody<P>::run(q.x * inv_h, q.y * inv_h, q.z * inv_h, q.w, acc);
+  }
+  P2MBody<P>::finish(acc);
+  float *o = M + (size_t)k * ldm;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) o[c] = acc[c];
+}
+
+// M2M, one thread per cell of one level: sum of its children's shifted multipoles.
+template <int P>
+__global__ void k_m2m(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int ldm,
+                      float *__restrict__ M) {
+  constexpr int NC = ncoef(P);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t k = lo + t;
+  const int2 kd = kids[k];
+  if (kd.y == 0) return;
+  float o[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) o[c] = 0.f;
+  for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
+    const uint4 cc = cell[ch];
+    // (z_P - z_C) / H = +1/4 for the lower half of an axis, -1/4 for the upper
+    M2MBody<P>::run((cc.x & 1u) ? -1.f : 1.f, (cc.y & 1u) ? -1.f : 1.f, (cc.z & 1u) ? -1.f : 1.f,
+                    M + (size_t)ch * ldm, o);
+  }
+  float *dst = M + (size_t)k * ldm;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) dst[c] = o[c];
+}
+
+// L2L, one thread per cell of one level: add its local expansion to each child's.
+template <int P>
+__global__ void k_l2l(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int ldm,
+                      float *__restrict__ L) {
+  constexpr int NC = ncoef(P);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t k = lo + t;
+  const int2 kd = kids[k];
+  if (kd.y == 0) return;
+  float pl[NC];
+  const float *src = L + (size_t)k * ldm;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) pl[c] = src[c];
+  for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
+    const uint4 cc = cell[ch];
+    // (z_C - z_P) / H = -1/4 for the lower half of an axis, +1/4 for the upper
+    L2LBody<P>::run((cc.x & 1u) ? 1.f : -1.f, (cc.y & 1u) ? 1.f : -1.f, (cc.z & 1u) ? 1.f : -1.f, pl,
+                    L + (size_t)ch * ldm);
   }
 }
 
-// M~_m(P) = sum_children sum_{n <= m} (x/H)^n / n! 2^-(|m|-|n|) M~_{m-n}(C),
-// x = z_P - z_C = +-H/4 per axis.
-__global__ void k_m2m(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int nc,
-                      float *__restrict__ M) {
-  __shared__ uchar4 mi[kNCMax];
-  build_mi(mi, nc);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < cnt; t += nw) {
-    int64_t k = lo + t;
-    int2 kd = kids[k];
-    if (kd.y == 0) continue;
-    for (int c = lane; c < nc; c += 32) {
-      uchar4 m = mi[c];
-      float acc = 0.f;
-      for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
-        uint4 cc = cell[ch];
-        float xh[3] = {(cc.x & 1u) ? -0.25f : 0.25f, (cc.y & 1u) ? -0.25f : 0.25f, (cc.z & 1u) ? -0.25f : 0.25f};
-        const float *Mc = M + (size_t)ch * nc;
-        for (int a = 0; a <= m.x; ++a)
-          for (int b = 0; b <= m.y; ++b)
-            for (int d = 0; d <= m.z; ++d) {
-              int rest = m.w - a - b - d;
-              float term = powi(xh[0], a) * powi(xh[1], b) * powi(xh[2], d) /
-                           (factf(a) * factf(b) * factf(d)) * ldexpf(1.f, -rest);
-              acc += term * Mc[midx(m.x - a, m.y - b, m.z - d)];
-            }
-      }
-      M[(size_t)k * nc + c] = acc;
-    }
+// L2P, one thread per leaf: a = G h^-2 sum L~_{n+e_d} u^n / n!, written in input order.
+template <int P>
+__global__ void k_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
+                      const uint2 *__restrict__ range, const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm,
+                      int64_t n, float box, float G, int ldm, const float *__restrict__ L, float *__restrict__ acc) {
+  constexpr int NC = ncoef(P);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const uint32_t k = leaves[t];
+  const uint2 r = range[k];
+  const float inv_h = (float)(1u << cell[k].w) / box;
+  const float s = G * inv_h * inv_h;
+  float l[NC];
+  const float *src = L + (size_t)k * ldm;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) l[c] = src[c];
+  for (uint32_t i = r.x; i < r.x + r.y; ++i) {
+    const float4 q = pm4[i];
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    L2PBody<P>::run(q.x * inv_h, q.y * inv_h, q.z * inv_h, l, ax, ay, az);
+    const uint32_t o = perm[i];
+    acc[o] = s * ax;
+    acc[n + o] = s * ay;
+    acc[2 * n + o] = s * az;
   }
 }
 
-// L~_n(C) += 2^-(|n|+1) sum_{|m| <= p-|n|} (x/H)^m / m! L~_{m+n}(P),  x = z_C - z_P = +-H/4.
-__global__ void k_l2l(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int p,
-                      int nc, float *__restrict__ L) {
-  __shared__ uchar4 mi[kNCMax];
-  build_mi(mi, nc);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < cnt; t += nw) {
-    int64_t k = lo + t;
-    int2 kd = kids[k];
-    if (kd.y == 0) continue;
-    const float *Lp = L + (size_t)k * nc;
-    for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
-      uint4 cc = cell[ch];
-      float xh[3] = {(cc.x & 1u) ? 0.25f : -0.25f, (cc.y & 1u) ? 0.25f : -0.25f, (cc.z & 1u) ? 0.25f : -0.25f};
-      for (int c = lane; c < nc; c += 32) {
-        uchar4 n = mi[c];
-        int rem = p - n.w;
-        float s = 0.f;
-        for (int e = 0; e < ncoef(rem); ++e) {
-          uchar4 m = mi[e];
-          s += powi(xh[0], m.x) * powi(xh[1], m.y) * powi(xh[2], m.z) / (factf(m.x) * factf(m.y) * factf(m.z)) *
-               Lp[midx(n.x + m.x, n.y + m.y, n.z + m.z)];
-        }
-        L[(size_t)ch * nc + c] += ldexpf(s, -(n.w + 1));
-      }
-    }
+template <int P>
+cudaError_t upward_p(Ctx &c, cudaStream_t st) {
+  const int T = 128;
+  const float box = (float)c.prm.box;
+  k_p2m<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell), hfmm::P<uint2>(c.range),
+                                                   hfmm::P<float4>(c.pm4), box, c.nc, hfmm::P<float>(c.M));
+  note_launch();
+  for (int l = c.nlevels - 2; l >= 0; --l) {
+    int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
+    k_m2m<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.nc, hfmm::P<float>(c.M));
+    note_launch();
   }
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st) {
+  const int T = 128;
+  for (int l = 0; l + 1 < c.nlevels; ++l) {
+    int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
+    k_l2l<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.nc, hfmm::P<float>(c.L));
+    note_launch();
+  }
+  k_l2p<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell),
+                                                   hfmm::P<uint2>(c.range), hfmm::P<float4>(c.pm4), hfmm::P<uint32_t>(c.idx), c.n,
+                                                   (float)c.prm.box, (float)c.prm.G, c.nc, hfmm::P<float>(c.L), acc);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t upward(Ctx &c, cudaStream_t st) {
-  const int T = 256;
-  const float box = (float)c.prm.box;
   if (c.nleaves == 0) return cudaSuccess;
-  unsigned g = blocks_for(c.nleaves, 8);
-  if (g > 152 * 64) g = 152 * 64;
-  k_p2m<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<float4>(c.pm4), box,
-                         c.nc, P<float>(c.M));
-  note_launch();
-  for (int l = c.nlevels - 2; l >= 0; --l) {
-    int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    unsigned gl = blocks_for(cnt, 8);
-    if (gl > 152 * 64) gl = 152 * 64;
-    k_m2m<<<gl, T, 0, st>>>(lo, cnt, P<uint4>(c.cell), P<int2>(c.kids), c.nc, P<float>(c.M));
-    note_launch();
+  switch (c.p) {
+    case 1: return upward_p<1>(c, st);
+    case 2: return upward_p<2>(c, st);
+    case 3: return upward_p<3>(c, st);
+    case 4: return upward_p<4>(c, st);
+    case 5: return upward_p<5>(c, st);
+    case 6: return upward_p<6>(c, st);
+    case 7: return upward_p<7>(c, st);
+    case 8: return upward_p<8>(c, st);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t l2l_pass(Ctx &c, cudaStream_t st) {
-  const int T = 256;
-  for (int l = 0; l + 1 < c.nlevels; ++l) {
-    int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    unsigned gl = blocks_for(cnt, 8);
-    if (gl > 152 * 64) gl = 152 * 64;
-    k_l2l<<<gl, T, 0, st>>>(lo, cnt, P<uint4>(c.cell), P<int2>(c.kids), c.p, c.nc, P<float>(c.L));
-    note_launch();
+// L2L top-down, then L2P (overwrites acc in input order; P2P adds to it).
+cudaError_t downward(Ctx &c, float *acc, cudaStream_t st) {
+  if (c.nleaves == 0) return cudaSuccess;
+  switch (c.p) {
+    case 1: return downward_p<1>(c, acc, st);
+    case 2: return downward_p<2>(c, acc, st);
+    case 3: return downward_p<3>(c, acc, st);
+    case 4: return downward_p<4>(c, acc, st);
+    case 5: return downward_p<5>(c, acc, st);
+    case 6: return downward_p<6>(c, acc, st);
+    case 7: return downward_p<7>(c, acc, st);
+    case 8: return downward_p<8>(c, acc, st);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace hfmm

@@ -1,4 +1,7 @@
-"""Write m2l_body.cuh: straight-line M2L contraction code for orders 1..8.
+"""Write gen_bodies.cuh: straight-line expansion code for orders 1..8.
+
+M2L (M2LBody, M2LLoad, M2LSlices) is described first; P2M, M2M, L2L and L2P
+bodies follow at the end of this docstring.
 
 For each order P and output slice g of G, the generated device function takes,
 for one (sink, source) pair, the unit separation vector R^ (rx, ry, rz), the
@@ -10,7 +13,15 @@ with D^_c = sum_{k_d <= c_d/2} prod_d [c_d!/(2^k_d k_d! (c_d-2k_d)!)] R^^(c-2k) 
 index is a literal, so the arrays live in registers.  Multi-index order: graded,
 nx descending, ny descending.
 
-Run by build.py before nvcc (python3 gen_m2l.py <out>).
+P2MBody<P>:  acc[c] += m u^c for one particle (u = offset / h); finish() applies
+             (-1)^|c| / c!  (Eq. p2m, scaled M~ = M / h^|m|).
+M2MBody<P>:  out[m] += sum_{n <= m} (x/H)^n / n! 2^-(|m|-|n|) in[m-n] for one
+             child, x/H = (sx, sy, sz) / 4, s = +-1 (Eq. m2m, scaled).
+L2LBody<P>:  out[n] = 2^-(|n|+1) sum_{|m| <= P-|n|} (x/H)^m / m! Lp[m+n] for one
+             child, x/H = (sx, sy, sz) / 4 (Eq. l2l, scaled L~ = L h^(|n|+1)).
+L2PBody<P>:  a_d += sum_{|n| <= P-1} Lk[n+e_d] u^n / n! (Eq. l2p gradient).
+
+Run by build.py before nvcc (python3 gen_bodies.py <out>).
 """
 from __future__ import annotations
 
@@ -129,9 +140,117 @@ def gen_body(P, G, g):
     return "\n".join(L)
 
 
+def _monomials(P, var, L, prefix="u", include_fact=False):
+    """Emit u^a (or u^a / a!) for all |a| <= P as named floats; returns name(a)."""
+    names = {}
+    for a in multi(P):
+        nm = f"{prefix}_{a[0]}_{a[1]}_{a[2]}"
+        if a == (0, 0, 0):
+            names[a] = "1.f"
+            continue
+        if a[2] > 0:
+            p, v, k = (a[0], a[1], a[2] - 1), var[2], a[2]
+        elif a[1] > 0:
+            p, v, k = (a[0], a[1] - 1, a[2]), var[1], a[1]
+        else:
+            p, v, k = (a[0] - 1, a[1], a[2]), var[0], a[0]
+        src = names[p]
+        if include_fact:
+            L.append(f"    const float {nm} = {src} * {v} * {1.0 / k!r}f;")
+        else:
+            L.append(f"    const float {nm} = {src} * {v};" if src != "1.f" else f"    const float {nm} = {v};")
+        names[a] = nm
+    return names
+
+
+def gen_passes(P):
+    NC = ncoef(P)
+    ms = multi(P)
+    out = []
+    # ---- P2M
+    L = [f"template <> struct P2MBody<{P}> {{",
+         f"  static __device__ __forceinline__ void run(float ux, float uy, float uz, float m, float (&acc)[{NC}]) {{"]
+    nm = _monomials(P, ("ux", "uy", "uz"), L)
+    for a in ms:
+        c = idx(a)
+        L.append(f"    acc[{c}] = fmaf(m, {nm[a]}, acc[{c}]);" if a != (0, 0, 0) else f"    acc[{c}] += m;")
+    L.append("  }")
+    L.append(f"  static __device__ __forceinline__ void finish(float (&acc)[{NC}]) {{")
+    for a in ms:
+        co = (-1) ** sum(a) / (factorial(a[0]) * factorial(a[1]) * factorial(a[2]))
+        if co != 1.0:
+            L.append(f"    acc[{idx(a)}] *= {co!r}f;")
+    L.append("  }")
+    L.append("};")
+    out.append("\n".join(L))
+    # ---- M2M
+    L = [f"template <> struct M2MBody<{P}> {{",
+         f"  static __device__ __forceinline__ void run(float sx, float sy, float sz, const float *__restrict__ in,"
+         f" float (&o)[{NC}]) {{"]
+    for a in ms:
+        k = idx(a)
+        L.append(f"    const float i{k} = __ldg(in + {k}) * {2.0 ** -sum(a)!r}f;")
+    for a in ms:
+        if a == (0, 0, 0):
+            continue
+        co = 0.25 ** sum(a) / (factorial(a[0]) * factorial(a[1]) * factorial(a[2]))
+        sg = "".join(f" * {v}" for v, e in zip(("sx", "sy", "sz"), a) if e % 2)
+        L.append(f"    const float w{idx(a)} = {co!r}f{sg};")
+    for m in ms:
+        terms = []
+        for n in ms:
+            if all(n[d] <= m[d] for d in range(3)):
+                r = (m[0] - n[0], m[1] - n[1], m[2] - n[2])
+                terms.append(f"i{idx(r)}" if n == (0, 0, 0) else f"w{idx(n)} * i{idx(r)}")
+        L.append(f"    o[{idx(m)}] += " + " + ".join(terms) + ";")
+    L.append("  }")
+    L.append("};")
+    out.append("\n".join(L))
+    # ---- L2L
+    L = [f"template <> struct L2LBody<{P}> {{",
+         f"  static __device__ __forceinline__ void run(float sx, float sy, float sz, const float (&p)[{NC}],"
+         f" float *__restrict__ child) {{"]
+    for a in ms:
+        if a == (0, 0, 0):
+            continue
+        co = 0.25 ** sum(a) / (factorial(a[0]) * factorial(a[1]) * factorial(a[2]))
+        sg = "".join(f" * {v}" for v, e in zip(("sx", "sy", "sz"), a) if e % 2)
+        L.append(f"    const float w{idx(a)} = {co!r}f{sg};")
+    for n in ms:
+        terms = []
+        for m in ms:
+            if sum(m) + sum(n) <= P:
+                q = (m[0] + n[0], m[1] + n[1], m[2] + n[2])
+                terms.append(f"p[{idx(q)}]" if m == (0, 0, 0) else f"w{idx(m)} * p[{idx(q)}]")
+        L.append(f"    child[{idx(n)}] += {2.0 ** -(sum(n) + 1)!r}f * (" + " + ".join(terms) + ");")
+    L.append("  }")
+    L.append("};")
+    out.append("\n".join(L))
+    # ---- L2P
+    L = [f"template <> struct L2PBody<{P}> {{",
+         f"  static __device__ __forceinline__ void run(float ux, float uy, float uz, const float (&l)[{NC}],"
+         f" float &ax, float &ay, float &az) {{"]
+    nm = _monomials(P - 1, ("ux", "uy", "uz"), L, prefix="t", include_fact=True) if P >= 1 else {}
+    tx, ty, tz = [], [], []
+    for a in multi(P - 1):
+        t = nm[a]
+        tx.append(f"{t} * l[{idx((a[0] + 1, a[1], a[2]))}]")
+        ty.append(f"{t} * l[{idx((a[0], a[1] + 1, a[2]))}]")
+        tz.append(f"{t} * l[{idx((a[0], a[1], a[2] + 1))}]")
+    L.append("    ax += " + " + ".join(tx) + ";")
+    L.append("    ay += " + " + ".join(ty) + ";")
+    L.append("    az += " + " + ".join(tz) + ";")
+    L.append("  }")
+    L.append("};")
+    out.append("\n".join(L))
+    return "\n\n".join(out)
+
+
 def main(out):
-    parts = ["// Generated by gen_m2l.py: do not edit.", "#pragma once", "",
-             "template <int P, int G, int g> struct M2LBody;", "template <int P> struct M2LLoad;", ""]
+    parts = ["// Generated by gen_bodies.py: do not edit.", "#pragma once", "",
+             "template <int P, int G, int g> struct M2LBody;", "template <int P> struct M2LLoad;",
+             "template <int P> struct P2MBody;", "template <int P> struct M2MBody;", "template <int P> struct L2LBody;",
+             "template <int P> struct L2PBody;", ""]
     for P in range(1, 9):
         G = SLICES[P]
         for g in range(G):
@@ -154,6 +273,9 @@ def main(out):
         parts.append("  }")
         parts.append("};")
         parts.append("")
+    for P in range(1, 9):
+        parts.append(gen_passes(P))
+        parts.append("")
     parts.append("template <int P> struct M2LSlices { static constexpr int G = " +
                  "(P == 6 ? 2 : (P == 7 ? 4 : (P == 8 ? 8 : 1))); static constexpr bool kSmem = (P >= 7); };")
     text = "\n".join(parts) + "\n"
@@ -167,4 +289,4 @@ def main(out):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "m2l_body.cuh")
+    main(sys.argv[1] if len(sys.argv) > 1 else "gen_bodies.cuh")

@@ -12,11 +12,11 @@
 // reduces it across the warp at the end, so no atomics are used and the
 // result is deterministic.  The expansion order is a template parameter: all
 // index arithmetic is literal in the generated straight-line bodies
-// (gen_m2l.py -> m2l_body.cuh).  For p >= 6 the output coefficients are split
+// (gen_bodies.py -> gen_bodies.cuh).  For p >= 6 the output coefficients are split
 // over G warps (slice g owns the outputs with index = g mod G); for p >= 7 the
 // scaled source multipoles of each lane's pair are staged in shared memory.
 #include "common.cuh"
-#include "m2l_body.cuh"
+#include "gen_bodies.cuh"
 
 namespace hfmm {
 namespace {

@@ -1,7 +1,6 @@
-// Fused leaf kernel: cut-off P2P over the sink leaf's P2P list (Sec. 2.1, the
-// pair force f_(1)(r) r of Sec. 2.2, kept for 0 < r < R_c), plus L2P of the
-// leaf's local expansion (Eq. l2p), written straight to the caller's particle
-// order (the un-permute).
+// Cut-off P2P over each sink leaf's P2P list (Sec. 2.1, the pair force
+// f_(1)(r) r of Sec. 2.2, kept for 0 < r < R_c), added to the L2P accelerations
+// already in the caller's particle order (the un-permute).
 //
 // One warp per sink leaf (taken from a global work counter).  The source
 // particles of all leaves on the sink's list are streamed through a per-warp
@@ -22,38 +21,18 @@ namespace {
 
 constexpr int kCap = 256;  // staged source particles per warp
 
-__device__ __forceinline__ float factf(int k) {
-  float f = 1.f;
-  for (int i = 2; i <= k; ++i) f *= (float)i;
-  return f;
-}
-
-__device__ __forceinline__ float powi(float x, int e) {
-  float r = 1.f;
-  for (int i = 0; i < e; ++i) r *= x;
-  return r;
-}
-
 template <bool kCount>
-__global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ leaves, int64_t nl,
-                                                 const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
-                                                 const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
-                                                 const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
-                                                 const float *__restrict__ L, const uint32_t *__restrict__ perm,
-                                                 int64_t n, int p, int nc, float box, PairFit fit, float G,
-                                                 float *__restrict__ acc_out, unsigned long long *__restrict__ ctr) {
+__global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
+                                             const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
+                                             const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
+                                             const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
+                                             const uint32_t *__restrict__ perm, int64_t n, float box, PairFit fit,
+                                             float G, float *__restrict__ acc_out,
+                                             unsigned long long *__restrict__ ctr) {
   __shared__ float4 sbuf[8][kCap];
-  __shared__ uchar4 mi[kNCMax];
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    int x, y, z;
-    mdecode(c, x, y, z);
-    mi[c] = make_uchar4((unsigned char)x, (unsigned char)y, (unsigned char)z, (unsigned char)(x + y + z));
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   float4 *buf = sbuf[threadIdx.x >> 5];
   const float half_unit = box / (float)kHalfBox;
-  const int ncl = p >= 1 ? ncoef(p - 1) : 0;
   uint32_t n_in = 0;  // pairs inside the cut-off (profile mode only)
   for (;;) {
     unsigned long long t = 0;
@@ -64,7 +43,6 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ le
     const uint4 ca = cell[k];
     const uint2 r = range[k];
     const uint32_t tb = beg[k], te = end[k];
-    const float inv_h = (float)(1u << ca.w) / box;
     for (uint32_t cbase = r.x; cbase < r.x + r.y; cbase += 32) {
       const uint32_t rem = r.x + r.y - cbase;
       const int cs = rem < 32 ? (int)rem : 32;
@@ -125,13 +103,13 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ le
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const bool in = (r2 < fit.rc2) && (r2 > 0.f);
             if (kCount) n_in += in;
-            const float r2s = in ? r2 : fit.rc2;
-            const float rinv = rsqrtf(r2s);
-            const float tt = r2s * rinv * fit.inv_rc;
+            // outside (0, R_c) the value below may be inf/NaN; the select discards it
+            const float rinv = rsqrtf(r2);
+            const float tt = r2 * rinv * fit.inv_rc;
             float qv = fit.c[9];
 #pragma unroll
             for (int j = 8; j >= 0; --j) qv = fmaf(qv, tt, fit.c[j]);
-            const float sfac = exp2f(r2s * fit.kexp) * qv;
+            const float sfac = exp2f(r2 * fit.kexp) * qv;
             const float f = in ? -(sfac * rinv * rinv * rinv) * s4.w : 0.f;
             ax = fmaf(f, dx, ax);
             ay = fmaf(f, dy, ay);
@@ -151,22 +129,10 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ le
           sy += v.y;
           sz += v.z;
         }
-        // L2P: a_d = h^-2 sum_{|n| <= p-1} L~_{n+e_d} u^n / n!, u = offset / h
-        const float *Lk = L + (size_t)k * nc;
-        const float ux = xi.x * inv_h, uy = xi.y * inv_h, uz = xi.z * inv_h;
-        float lx = 0.f, ly = 0.f, lz = 0.f;
-        for (int c = 0; c < ncl; ++c) {
-          const uchar4 m = mi[c];
-          const float mono = powi(ux, m.x) * powi(uy, m.y) * powi(uz, m.z) / (factf(m.x) * factf(m.y) * factf(m.z));
-          lx = fmaf(Lk[midx(m.x + 1, m.y, m.z)], mono, lx);
-          ly = fmaf(Lk[midx(m.x, m.y + 1, m.z)], mono, ly);
-          lz = fmaf(Lk[midx(m.x, m.y, m.z + 1)], mono, lz);
-        }
-        const float ih2 = inv_h * inv_h;
         const uint32_t o = perm[cbase + lane];
-        acc_out[o] = G * (sx + lx * ih2);
-        acc_out[n + o] = G * (sy + ly * ih2);
-        acc_out[2 * n + o] = G * (sz + lz * ih2);
+        acc_out[o] += G * sx;
+        acc_out[n + o] += G * sy;
+        acc_out[2 * n + o] += G * sz;
       }
       __syncwarp();
     }
@@ -180,19 +146,19 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(const uint32_t *__restrict__ le
 
 }  // namespace
 
-cudaError_t p2p_l2p(Ctx &c, float *acc, cudaStream_t st) {
+cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   if (c.nleaves == 0) return cudaSuccess;
   const int T = 256;
   unsigned g = 152 * 8;
   if ((size_t)g * 8 > (size_t)c.nleaves) g = blocks_for(c.nleaves, 8);
-  auto kern = c.prm.profile ? k_p2p_l2p<true> : k_p2p_l2p<false>;
+  auto kern = (c.prm.profile & 2) ? k_p2p<true> : k_p2p<false>;
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
   cudaError_t e = cudaMemsetAsync(ctr, 0, 8, st);
   if (e != cudaSuccess) return e;
   kern<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
-                        P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<float>(c.L),
-                        P<uint32_t>(c.idx), c.n, c.p, c.nc, (float)c.prm.box, c.fit, (float)c.prm.G, acc, ctr);
+                        P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
+                        (float)c.prm.box, c.fit, (float)c.prm.G, acc, ctr);
   note_launch();
   return cudaGetLastError();
 }

@@ -228,7 +228,8 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
     note_launch();
     TRY(cudaGetLastError());
   }
-  if (c.np2p > 0) {
+  c.p2p_particle_pairs = -1;
+  if ((c.prm.profile & 2) && c.np2p > 0) {
     TRY(cudaMemsetAsync(c.d_small.p, 0, 8, st));
     k_pairs_in_list<<<blocks_for(c.np2p, T), T, 0, st>>>(P<uint64_t>(c.p2p), c.np2p, P<uint2>(c.range),
                                                          reinterpret_cast<unsigned long long *>(c.d_small.p));
@@ -236,8 +237,6 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
     TRY(cudaMemcpyAsync(c.h_pinned, c.d_small.p, 8, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     c.p2p_particle_pairs = (int64_t)c.h_pinned[0];
-  } else {
-    c.p2p_particle_pairs = 0;
   }
   return cudaSuccess;
 #undef TRY

@@ -170,7 +170,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   TRY(ensure(c.xs, n * 24));
   TRY(ensure(c.pm4, n * 16));
   TRY(ensure(c.d_small, 256));
-  if (c.prm.profile) cudaEventRecord(c.ev[0], st);
+  if (c.prm.profile & 1) cudaEventRecord(c.ev[0], st);
   k_keys<<<blocks_for(n, T), T, 0, st>>>(pos, n, c.prm.box, P<uint64_t>(c.key), P<uint32_t>(c.idx));
   note_launch();
   bool alt = false;
@@ -182,7 +182,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   }
   uint64_t *key = P<uint64_t>(c.key);
   uint32_t *perm = P<uint32_t>(c.idx);
-  if (c.prm.profile) cudaEventRecord(c.ev[1], st);
+  if (c.prm.profile & 1) cudaEventRecord(c.ev[1], st);
   k_gather<<<blocks_for(n, T), T, 0, st>>>(pos, perm, n, c.prm.box, P<double>(c.xs));
   note_launch();
 
@@ -250,7 +250,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
                                                          c.prm.box, P<float4>(c.pm4));
   note_launch();
   TRY(cudaGetLastError());
-  if (c.prm.profile) cudaEventRecord(c.ev[2], st);
+  if (c.prm.profile & 1) cudaEventRecord(c.ev[2], st);
   c.have_tree = true;
   return cudaSuccess;
 #undef TRY
