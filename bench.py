@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="same kind of set at another N (profiling only)")
     ap.add_argument("--theta", type=float, default=0.3)
     ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
     ap.add_argument("--accuracy-sinks", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=25.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -230,7 +231,7 @@ def main():
     # timed solver: phase events only (profile bit 0); the pair counts come from
     # one untimed run of a second context with counting on (bit 1)
     s = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                    order=args.order, leaf_max=cfg.leaf_max, profile=1)
+                    order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=1)
     dpos = torch.from_numpy(pos).to(dev)
     dmass = torch.from_numpy(mass).to(dev)
     acc = torch.empty((3, n), dtype=torch.float32, device=dev)
@@ -246,7 +247,7 @@ def main():
         step()
     torch.cuda.synchronize()
     sc = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, profile=3)
+                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=3)
     sc.build_tree(dpos, dmass)
     sc.short_range_forces(torch.empty_like(acc))
     counts = sc.get_stats()
@@ -297,7 +298,7 @@ def main():
     pin_mass = torch.from_numpy(mass).pin_memory()
     pin_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
     s2 = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max)
+                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision)
     for _ in range(2):
         s2.short_range_forces_host(pin_pos, pin_mass, pin_acc)
     e2e_s = 0.0
@@ -344,7 +345,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(cfg), "path": "plain FP32 geometric acceptance",
+            "config": {"workload": workload_desc(cfg),
+                       "path": "geometric acceptance, " + ("3xTF32 tensor-core M2L" if args.m2l_precision == 1
+                                                           else "FP32 CUDA-core M2L"),
                        "theta": args.theta, "order": args.order, "leaf_max": cfg.leaf_max,
                        "transition_rule": 1, "size_rule": 1, "l2": "flushed (512 MB write) before every step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},

@@ -66,7 +66,8 @@ typedef struct {
                           1: open iff S_max > R_c >= S_m (every M2L pair lies within R_c) */
   int size_rule;       /* L in theta = L / S_c: 0 = side of the source cell (as printed),
                           1 = larger side of the two cells */
-  int m2l_precision;   /* 0 = FP32 CUDA cores */
+  int m2l_precision;   /* 0 = FP32 on CUDA cores; 1 = 3xTF32 split products on the tcgen05
+                          tensor cores with FP32 accumulation in tensor memory (orders 1..6) */
   int profile;         /* bit 0: record per-phase CUDA-event timings; bit 1: count P2P
                           particle pairs (extra work; for statistics runs only) */
 } hfmm_params;

@@ -38,7 +38,9 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.mac_mode != 0) return why = "mac_mode must be 0 (geometric)", false;
   if (p.transition_rule != 0 && p.transition_rule != 1) return why = "transition_rule must be 0 or 1", false;
   if (p.size_rule != 0 && p.size_rule != 1) return why = "size_rule must be 0 or 1", false;
-  if (p.m2l_precision != 0) return why = "m2l_precision must be 0", false;
+  if (p.m2l_precision != 0 && p.m2l_precision != 1) return why = "m2l_precision must be 0 or 1", false;
+  if (p.m2l_precision == 1 && !m2l_tc_supported(p.order))
+    return why = "m2l_precision 1 (3xTF32 tensor cores) supports orders 1..6", false;
   if (p.profile < 0 || p.profile > 3) return why = "profile must be 0..3", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
@@ -202,7 +204,19 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (prof) cudaEventRecord(c.ev[5], st);
   if ((e = sort_lists(c, st)) != cudaSuccess) return cuda_fail(c, e, "sort_lists");
   if (prof) cudaEventRecord(c.ev[6], st);
-  if ((e = m2l_pass(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l");
+  if (c.prm.m2l_precision == 1) {
+    if ((e = m2l_pass_tc(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l (tensor cores)");
+    int *status = reinterpret_cast<int *>(P<uint64_t>(c.d_small) + 6);
+    if (c.nm2l > 0) {
+      if ((e = cudaMemcpyAsync(c.h_pinned + 7, status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "m2l status");
+      if (*reinterpret_cast<int *>(c.h_pinned + 7) != 0)
+        return fail(c, HFMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait for MMA completion gave up");
+    }
+  } else if ((e = m2l_pass(c, st)) != cudaSuccess) {
+    return cuda_fail(c, e, "m2l");
+  }
   if (prof) cudaEventRecord(c.ev[7], st);
   if ((e = downward(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "l2l/l2p");
   if (prof) cudaEventRecord(c.ev[8], st);

@@ -171,6 +171,10 @@ cudaError_t traverse(Ctx &c, cudaStream_t st);
 cudaError_t sort_lists(Ctx &c, cudaStream_t st);
 cudaError_t upward(Ctx &c, cudaStream_t st);
 cudaError_t m2l_pass(Ctx &c, cudaStream_t st);
+// Split-precision (3xTF32) M2L on tcgen05 tensor cores; orders 1..6.  The
+// kernel's status word (d_small[6]) is 1 after a timed-out wait.
+bool m2l_tc_supported(int p);
+cudaError_t m2l_pass_tc(Ctx &c, cudaStream_t st);
 // L2L top-down, then L2P writing the far-field accelerations in input order.
 cudaError_t downward(Ctx &c, float *acc, cudaStream_t st);
 // Cut-off P2P, added to the accelerations written by downward().

@@ -20,6 +20,10 @@ M2MBody<P>:  out[m] += sum_{n <= m} (x/H)^n / n! 2^-(|m|-|n|) in[m-n] for one
 L2LBody<P>:  out[n] = 2^-(|n|+1) sum_{|m| <= P-|n|} (x/H)^m / m! Lp[m+n] for one
              child, x/H = (sx, sy, sz) / 4 (Eq. l2l, scaled L~ = L h^(|n|+1)).
 L2PBody<P>:  a_d += sum_{|n| <= P-1} Lk[n+e_d] u^n / n! (Eq. l2p gradient).
+TCStore<P>:  tensor-core M2L operands for one pair: D'_c = u^(|c|+1) D^_c(R^) and
+             M'_m = s (v/u)^|m| M~_m, each split x = hi + lo (hi = TF32 rounding),
+             stored at row c (or m), column k of K-major 128-byte-swizzled tiles
+             (xo[j] = float offset of column k in a row with (row mod 8) = j).
 
 Run by build.py before nvcc (python3 gen_bodies.py <out>).
 """
@@ -246,11 +250,70 @@ def gen_passes(P):
     return "\n\n".join(out)
 
 
+def gen_tc(P):
+    NC = ncoef(P)
+    ms = multi(P)
+    L = [f"template <> struct TCStore<{P}> {{",
+         f"  static __device__ __forceinline__ void store_d(float rx, float ry, float rz, const float (&f)[{P + 1}],"
+         f" const float (&U)[{P + 1}], float *__restrict__ hi, float *__restrict__ lo, const int (&xo)[8]) {{"]
+    nm = {}
+    for a in ms:
+        if a == (0, 0, 0):
+            nm[a] = "1.f"
+            continue
+        if a[2] > 0:
+            p, v = (a[0], a[1], a[2] - 1), "rz"
+        elif a[1] > 0:
+            p, v = (a[0], a[1] - 1, a[2]), "ry"
+        else:
+            p, v = (a[0] - 1, a[1], a[2]), "rx"
+        name = "m_%d_%d_%d" % a
+        L.append(f"    const float {name} = {nm[p]} * {v};" if nm[p] != "1.f" else f"    const float {name} = {v};")
+        nm[a] = name
+    for c in ms:
+        ci = idx(c)
+        cn = sum(c)
+        parts = []
+        for kx in range(c[0] // 2 + 1):
+            for ky in range(c[1] // 2 + 1):
+                for kz in range(c[2] // 2 + 1):
+                    co = hco(c[0], kx) * hco(c[1], ky) * hco(c[2], kz)
+                    a = (c[0] - 2 * kx, c[1] - 2 * ky, c[2] - 2 * kz)
+                    o = cn - kx - ky - kz
+                    t = f"f[{o}]" if a == (0, 0, 0) else f"{nm[a]} * f[{o}]"
+                    parts.append(t if co == 1 else f"{float(co)}f * {t}")
+        off = (ci >> 3) * 256 + (ci & 7) * 32
+        L.append(f"    {{ const float d = U[{cn}] * ({' + '.join(parts)}); const float h = tf32_round(d);"
+                 f" hi[{off} + xo[{ci & 7}]] = h; lo[{off} + xo[{ci & 7}]] = d - h; }}")
+    L.append("  }")
+    L.append(f"  static __device__ __forceinline__ void store_m(const float *__restrict__ Mb, float vr, float s,"
+             f" float *__restrict__ hi, float *__restrict__ lo, const int (&xo)[8]) {{")
+    L.append("    float q = s;")
+    for k in range(P + 1):
+        if k:
+            L.append("    q *= vr;")
+        for a in ms:
+            if sum(a) != k:
+                continue
+            ci = idx(a)
+            off = (ci >> 3) * 256 + (ci & 7) * 32
+            L.append(f"    {{ const float x = __ldg(Mb + {ci}) * q; const float h = tf32_round(x);"
+                     f" hi[{off} + xo[{ci & 7}]] = h; lo[{off} + xo[{ci & 7}]] = x - h; }}")
+    L.append("  }")
+    L.append("};")
+    return "\n".join(L)
+
+
 def main(out):
     parts = ["// Generated by gen_bodies.py: do not edit.", "#pragma once", "",
              "template <int P, int G, int g> struct M2LBody;", "template <int P> struct M2LLoad;",
              "template <int P> struct P2MBody;", "template <int P> struct M2MBody;", "template <int P> struct L2LBody;",
-             "template <int P> struct L2PBody;", ""]
+             "template <int P> struct L2PBody;", "template <int P> struct TCStore;", "",
+             "__device__ __forceinline__ float tf32_round(float x) {",
+             "  uint32_t r;",
+             "  asm(\"cvt.rna.tf32.f32 %0, %1;\" : \"=r\"(r) : \"f\"(x));",
+             "  return __uint_as_float(r);",
+             "}", ""]
     for P in range(1, 9):
         G = SLICES[P]
         for g in range(G):
@@ -275,6 +338,9 @@ def main(out):
         parts.append("")
     for P in range(1, 9):
         parts.append(gen_passes(P))
+        parts.append("")
+    for P in range(1, 7):
+        parts.append(gen_tc(P))
         parts.append("")
     parts.append("template <int P> struct M2LSlices { static constexpr int G = " +
                  "(P == 6 ? 2 : (P == 7 ? 4 : (P == 8 ? 8 : 1))); static constexpr bool kSmem = (P >= 7); };")
