@@ -61,7 +61,11 @@ typedef struct {
   double theta;        /* opening angle theta_MAC of Sec. 2.3 (0 = never accept M2L) */
   int order;           /* expansion order p, 1..8 (total order |n| + |m| <= p) */
   int leaf_max;        /* a cell is split while it holds more than leaf_max particles (1..64) */
-  int mac_mode;        /* 0 = geometric acceptance (Sec. 2.3) */
+  int mac_mode;        /* 0 = geometric acceptance (Sec. 2.3); 1 = learned acceptance: rules 1
+                          and 3 of Sec. 2.3 unchanged, and in place of rule 2 a network chooses,
+                          for each pair with L / S_c <= theta (theta is then a safety bound),
+                          between opening the pair and M2L at an order q in 2..order
+                          (needs hfmm_load_mlp; order 8 recommended) */
   int transition_rule; /* 0: open iff S_c > R_c >= S_m (Sec. 2.3 as printed);
                           1: open iff S_max > R_c >= S_m (every M2L pair lies within R_c) */
   int size_rule;       /* L in theta = L / S_c: 0 = side of the source cell (as printed),
@@ -157,9 +161,56 @@ enum {
   HFMM_EXPORT_P2P = 3,
   HFMM_EXPORT_M2L = 4,
   HFMM_EXPORT_MULTIPOLES = 5,
-  HFMM_EXPORT_LOCALS = 6
+  HFMM_EXPORT_LOCALS = 6,
+  HFMM_EXPORT_M2L_ORDER = 7, /* int64 [nm2l] expansion order of each M2L entry, list order */
+  HFMM_EXPORT_CANDIDATES = 8 /* int64 [n][3] pairs of the last hfmm_collect_training_pairs (row order) */
 };
 int hfmm_export(hfmm_ctx *ctx, int what, void *host_buf, size_t *bytes);
+
+/*
+ * Learned acceptance (an addition to the paper's Sec. 2.3 criterion).
+ * The network maps 12 pair features to 8 classes {open, M2L at order 2..8}:
+ * 12 -> 64 -> ReLU -> 64 -> ReLU -> 8, BF16 weights, FP32 accumulation.
+ * Weight blob: 5512 BF16 values, W1[64][12], b1[64], W2[64][64], b2[64],
+ * W3[8][64], b3[8].  Features (half units; all dimensionless): S_c/r_s,
+ * S_m/r_s, S_max/R_c, h_A/S_c, h_B/S_c, max(h_A,h_B)/S_c, (level_A-level_B)/8,
+ * log2(1+n_A)/16, log2(1+n_B)/16, |dipole of B|/|M_0|, |quadrupole of B|/|M_0|
+ * (scaled multipoles), S_c/R_c.
+ */
+/* Copy the network's weights (host pointer, 11024 bytes) to the context. */
+int hfmm_load_mlp(hfmm_ctx *ctx, const void *weights_bf16, size_t bytes);
+
+/*
+ * Training data, measured by the method itself: after hfmm_build_tree on an
+ * order-8 context, visit every cell pair (every pair opened), and for a
+ * hash-sampled 1/sample_mod of the candidate pairs (rules 1 and 3 passed,
+ * L / S_c <= theta) write the 12 features (device FP32 [n][12]) and the error
+ * of M2L at orders 2..8 against the pair's own direct sum, measured on up to
+ * 32 particles of the sink cell (device FP32 [n][7]:
+ * |a_M2L - a_direct|_2 / |a_direct|_2).  At most max_pairs rows; *count
+ * receives n.  Synchronises the stream.
+ */
+int hfmm_collect_training_pairs(hfmm_ctx *ctx, int64_t max_pairs, uint32_t sample_mod, float *features,
+                                float *errors, int64_t *count, void *stream);
+
+/* Network inference on the tensor cores (device pointers): logits [n][8]
+ * and/or classes [n] (argmax, ties to the lower class); either may be NULL. */
+int hfmm_mlp_infer(const void *weights_bf16, const float *features, int64_t n, float *logits, int32_t *classes,
+                   void *stream);
+
+/*
+ * Mean softmax cross-entropy over n samples and its gradient (device
+ * pointers): weights = FP32 master copy [5512] (rounded to BF16 in the
+ * forward pass, as the inference does), labels [n] in 0..7, class_weights
+ * [8] or NULL; grad [5512] and loss [1] are written.  Uses ctx's scratch.
+ */
+int hfmm_mlp_grad(hfmm_ctx *ctx, const float *weights, const float *features, const int32_t *labels,
+                  const float *class_weights, int64_t n, float *grad, float *loss, void *stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected at `step` >= 1)
+ * on the FP32 master weights; writes the BF16 copy when weights_bf16 != NULL. */
+int hfmm_mlp_adam(const float *grad, float lr, int step, float *weights, float *m1, float *m2, void *weights_bf16,
+                  void *stream);
 
 /*
  * Allocation-free Morton keys + sort.  The paper has no counterpart: this is

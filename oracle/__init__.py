@@ -81,6 +81,16 @@ def lib():
             L.orc_export_list.argtypes = [P, i32, P]
             L.orc_export_expansions.argtypes = [P, i32, P]
             L.orc_num_threads.restype = i32
+            L.orc_bf16.argtypes = [d]
+            L.orc_bf16.restype = d
+            L.orc_mlp_forward.argtypes = [P, P, i64, i32, P]
+            L.orc_mlp_loss_grad.argtypes = [P, P, P, P, i64, i32, P, P]
+            L.orc_set_lists.argtypes = [P, P, i64, P, P, i64]
+            L.orc_fmm_forces_given_lists.argtypes = [P, P]
+            L.orc_pair_error.argtypes = [P, i64, i64, i32, i32]
+            L.orc_pair_error.restype = d
+            L.orc_find_node.argtypes = [P, i32, C.c_uint32, C.c_uint32, C.c_uint32]
+            L.orc_find_node.restype = i64
             _lib = L
     return _lib
 
@@ -184,6 +194,35 @@ def direct_sr(pos, mass, box, rs, rc, G=1.0, sinks=None) -> np.ndarray:
     return acc
 
 
+# ---------------------------------------------------------------- network
+MLP_WEIGHTS = 5512
+
+
+def bf16(x: float) -> float:
+    return float(lib().orc_bf16(float(x)))
+
+
+def mlp_forward(w, x, rnd=1) -> np.ndarray:
+    """Logits [n][8] of the learned-acceptance network (weights as doubles, blob order)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 12)
+    out = np.zeros((x.shape[0], 8))
+    _check(lib().orc_mlp_forward(_p(w), _p(x), x.shape[0], int(rnd), _p(out)), "mlp_forward")
+    return out
+
+
+def mlp_loss_grad(w, x, labels, class_weights=None, rnd=1):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 12)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    cw = None if class_weights is None else np.ascontiguousarray(class_weights, dtype=np.float64)
+    g = np.zeros(MLP_WEIGHTS)
+    loss = np.zeros(1)
+    _check(lib().orc_mlp_loss_grad(_p(w), _p(x), _p(lab), _p(cw), x.shape[0], int(rnd), _p(g), _p(loss)),
+           "mlp_loss_grad")
+    return float(loss[0]), g
+
+
 # ---------------------------------------------------------------- FMM
 class FMM:
     """FP64 truncated FMM with the same tree, MAC and lists as the GPU library."""
@@ -244,6 +283,22 @@ class FMM:
         out = np.zeros((self.size("nodes"), ncoef(self.order)))
         _check(lib().orc_export_expansions(self._c, {"M": 0, "L": 1}[which], _p(out)), "export_expansions")
         return out
+
+    def forces_given_lists(self, p2p, m2l, orders=None):
+        """FMM forces on the given lists (P2P and M2L rows: sink, source, shift; optional order per M2L row)."""
+        p2p = np.ascontiguousarray(p2p, dtype=np.int64).reshape(-1, 3)
+        m2l = np.ascontiguousarray(m2l, dtype=np.int64).reshape(-1, 3)
+        o = None if orders is None else np.ascontiguousarray(orders, dtype=np.int64)
+        _check(lib().orc_set_lists(self._c, _p(p2p), len(p2p), _p(m2l), _p(o), len(m2l)), "set_lists")
+        acc = np.zeros((3, self.n))
+        _check(lib().orc_fmm_forces_given_lists(self._c, _p(acc)), "fmm_forces_given_lists")
+        return acc
+
+    def pair_error(self, a, b, s, q):
+        return float(lib().orc_pair_error(self._c, int(a), int(b), int(s), int(q)))
+
+    def find_node(self, lev, ix, iy, iz):
+        return int(lib().orc_find_node(self._c, int(lev), int(ix), int(iy), int(iz)))
 
     # phase-by-phase access for the tests
     def upward(self):

@@ -821,3 +821,242 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned acceptance: network reference and FMM on given lists.             */
+/* ------------------------------------------------------------------------ */
+
+/* FP32 value rounded to the nearest BF16 (ties to even), returned as double. */
+double orc_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+#define MLP_IN 12
+#define MLP_H 64
+#define MLP_OUT 8
+#define OFF_W1 0
+#define OFF_B1 (OFF_W1 + MLP_H * MLP_IN)
+#define OFF_W2 (OFF_B1 + MLP_H)
+#define OFF_B2 (OFF_W2 + MLP_H * MLP_H)
+#define OFF_W3 (OFF_B2 + MLP_H)
+#define OFF_B3 (OFF_W3 + MLP_OUT * MLP_H)
+#define MLP_W (OFF_B3 + MLP_OUT)
+
+/* one sample: z1, h1, z2, h2 (hidden) and logits; rnd = 1 rounds inputs and hidden activations to BF16 */
+static void mlp_fwd1(const double *w, const double *x, int rnd, double *z1, double *h1, double *z2, double *h2,
+                     double *lo) {
+  double xi[MLP_IN];
+  for (int k = 0; k < MLP_IN; ++k) xi[k] = rnd ? orc_bf16(x[k]) : x[k];
+  for (int u = 0; u < MLP_H; ++u) {
+    double z = w[OFF_B1 + u];
+    for (int k = 0; k < MLP_IN; ++k) z += w[OFF_W1 + u * MLP_IN + k] * xi[k];
+    z1[u] = z;
+    h1[u] = z > 0 ? (rnd ? orc_bf16(z) : z) : 0.0;
+  }
+  for (int u = 0; u < MLP_H; ++u) {
+    double z = w[OFF_B2 + u];
+    for (int k = 0; k < MLP_H; ++k) z += w[OFF_W2 + u * MLP_H + k] * h1[k];
+    z2[u] = z;
+    h2[u] = z > 0 ? (rnd ? orc_bf16(z) : z) : 0.0;
+  }
+  for (int o = 0; o < MLP_OUT; ++o) {
+    double z = w[OFF_B3 + o];
+    for (int k = 0; k < MLP_H; ++k) z += w[OFF_W3 + o * MLP_H + k] * h2[k];
+    lo[o] = z;
+  }
+}
+
+/* Network 12 -> 64 -> ReLU -> 64 -> ReLU -> 8 (the weight blob order of include/hfmm.h). */
+int orc_mlp_forward(const double *w, const double *x, int64_t n, int rnd, double *logits) {
+  for (int64_t i = 0; i < n; ++i) {
+    double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H];
+    mlp_fwd1(w, x + i * MLP_IN, rnd, z1, h1, z2, h2, logits + i * MLP_OUT);
+  }
+  return 0;
+}
+
+/* Mean (class-weighted) softmax cross-entropy and its gradient; the BF16
+ * rounding (rnd = 1) is treated as the identity in the backward pass. */
+int orc_mlp_loss_grad(const double *w, const double *x, const int32_t *lab, const double *cw, int64_t n, int rnd,
+                      double *grad, double *loss) {
+  for (int i = 0; i < MLP_W; ++i) grad[i] = 0.0;
+  double L = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H], lo[MLP_OUT], xi[MLP_IN];
+    const double *x0 = x + s * MLP_IN;
+    for (int k = 0; k < MLP_IN; ++k) xi[k] = rnd ? orc_bf16(x0[k]) : x0[k];
+    mlp_fwd1(w, x0, rnd, z1, h1, z2, h2, lo);
+    double mx = lo[0];
+    for (int o = 1; o < MLP_OUT; ++o) mx = lo[o] > mx ? lo[o] : mx;
+    double se = 0.0, pr[MLP_OUT];
+    for (int o = 0; o < MLP_OUT; ++o) se += exp(lo[o] - mx);
+    for (int o = 0; o < MLP_OUT; ++o) pr[o] = exp(lo[o] - mx) / se;
+    const int y = lab[s];
+    const double wt = cw ? cw[y] : 1.0;
+    L += -wt * log(pr[y]);
+    double d3[MLP_OUT], d2[MLP_H], d1[MLP_H];
+    for (int o = 0; o < MLP_OUT; ++o) d3[o] = wt * (pr[o] - (o == y ? 1.0 : 0.0));
+    for (int o = 0; o < MLP_OUT; ++o) {
+      grad[OFF_B3 + o] += d3[o];
+      for (int k = 0; k < MLP_H; ++k) grad[OFF_W3 + o * MLP_H + k] += d3[o] * h2[k];
+    }
+    for (int k = 0; k < MLP_H; ++k) {
+      double dh = 0.0;
+      for (int o = 0; o < MLP_OUT; ++o) dh += w[OFF_W3 + o * MLP_H + k] * d3[o];
+      d2[k] = z2[k] > 0 ? dh : 0.0;
+    }
+    for (int u = 0; u < MLP_H; ++u) {
+      grad[OFF_B2 + u] += d2[u];
+      for (int k = 0; k < MLP_H; ++k) grad[OFF_W2 + u * MLP_H + k] += d2[u] * h1[k];
+    }
+    for (int k = 0; k < MLP_H; ++k) {
+      double dh = 0.0;
+      for (int u = 0; u < MLP_H; ++u) dh += w[OFF_W2 + u * MLP_H + k] * d2[u];
+      d1[k] = z1[k] > 0 ? dh : 0.0;
+    }
+    for (int u = 0; u < MLP_H; ++u) {
+      grad[OFF_B1 + u] += d1[u];
+      for (int k = 0; k < MLP_IN; ++k) grad[OFF_W1 + u * MLP_IN + k] += d1[u] * xi[k];
+    }
+  }
+  for (int i = 0; i < MLP_W; ++i) grad[i] /= (double)n;
+  if (loss) *loss = L / (double)n;
+  return 0;
+}
+
+/*
+ * Replace the context's lists (sink, source, shift index per row) and give
+ * each M2L pair its own order q <= p (Eq. m2l truncated at |n| + |m| <= q).
+ */
+int orc_set_lists(orc_ctx *c, const int64_t *p2p, int64_t np2p, const int64_t *m2l, const int64_t *orders,
+                  int64_t nm2l) {
+  if (!c) return -1;
+  free(c->p2p);
+  free(c->m2l);
+  c->p2p = (int64_t *)malloc(sizeof(int64_t) * 3 * (np2p ? np2p : 1));
+  c->m2l = (int64_t *)malloc(sizeof(int64_t) * 4 * (nm2l ? nm2l : 1));
+  memcpy(c->p2p, p2p, sizeof(int64_t) * 3 * np2p);
+  c->np2p = c->cap_p2p = np2p;
+  /* the M2L rows keep (sink, source, shift) in the first three columns and the order in the fourth */
+  for (int64_t t = 0; t < nm2l; ++t) {
+    c->m2l[4 * t] = m2l[3 * t];
+    c->m2l[4 * t + 1] = m2l[3 * t + 1];
+    c->m2l[4 * t + 2] = m2l[3 * t + 2];
+    c->m2l[4 * t + 3] = orders ? orders[t] : c->p;
+  }
+  c->nm2l = nm2l;
+  c->cap_m2l = nm2l;
+  return 0;
+}
+
+static int cmp_quad(const void *a, const void *b) {
+  const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+  for (int i = 0; i < 4; ++i)
+    if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+  return 0;
+}
+
+/* FMM forces on the lists given to orc_set_lists (order per M2L pair). */
+int orc_fmm_forces_given_lists(orc_ctx *c, double *acc) {
+  if (!c) return -1;
+  int64_t n = c->n;
+  if (n == 0) return 0;
+  int nc = orc_ncoef(c->p);
+  double *as = (double *)calloc((size_t)3 * n, sizeof(double));
+  int rc = orc_upward(c);
+  if (!rc) {
+    free(c->L);
+    c->L = (double *)calloc((size_t)(c->nnodes ? c->nnodes : 1) * nc, sizeof(double));
+    qsort(c->m2l, (size_t)c->nm2l, 4 * sizeof(int64_t), cmp_quad);
+    int64_t *off = (int64_t *)calloc((size_t)c->nnodes + 1, sizeof(int64_t));
+    for (int64_t t = 0; t < c->nm2l; ++t) off[c->m2l[4 * t] + 1]++;
+    for (int64_t k = 0; k < c->nnodes; ++k) off[k + 1] += off[k];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t a = 0; a < c->nnodes; ++a) {
+      double za[3];
+      node_centre(c, a, za);
+      for (int64_t t = off[a]; t < off[a + 1]; ++t) {
+        int64_t b = c->m2l[4 * t + 1];
+        int s = (int)c->m2l[4 * t + 2], q = (int)c->m2l[4 * t + 3];
+        double zb[3], sv[3], R[3], Lq[ORC_NCMAX];
+        node_centre(c, b, zb);
+        shift_vec(s, c->box, sv);
+        for (int d = 0; d < 3; ++d) R[d] = za[d] - (zb[d] + sv[d]);
+        for (int e = 0; e < orc_ncoef(q); ++e) Lq[e] = 0.0;
+        orc_m2l(c->M + b * nc, R, c->rs, q, Lq);
+        for (int e = 0; e < orc_ncoef(q); ++e) c->L[a * nc + e] += Lq[e];
+      }
+    }
+    free(off);
+    /* keep the list in the three-column layout the rest of the oracle uses */
+    for (int64_t t = 0; t < c->nm2l; ++t)
+      for (int j = 0; j < 3; ++j) c->m2l[3 * t + j] = c->m2l[4 * t + j];
+  }
+  if (!rc) rc = orc_downward(c, as);
+  if (!rc) rc = orc_p2p_pass(c, as);
+  if (!rc)
+    for (int64_t s = 0; s < n; ++s)
+      for (int d = 0; d < 3; ++d) acc[d * n + c->perm[s]] = as[3 * s + d];
+  free(as);
+  return rc;
+}
+
+/*
+ * Error of accepting the pair (a, b, shift) with M2L at order q: up to 32
+ * evenly strided particles of a, direct sum over b's particles vs
+ * P2M(b, order q) -> M2L(order q) -> L2P (all FP64).  Returns
+ * sqrt(sum |a_q - a|^2) / sqrt(sum |a|^2).
+ */
+double orc_pair_error(orc_ctx *c, int64_t a, int64_t b, int s, int q) {
+  double za[3], zb[3], sv[3], R[3];
+  node_centre(c, a, za);
+  node_centre(c, b, zb);
+  shift_vec(s, c->box, sv);
+  for (int d = 0; d < 3; ++d) R[d] = za[d] - (zb[d] + sv[d]);
+  double M[ORC_NCMAX], L[ORC_NCMAX];
+  int64_t nb = c->count[b];
+  double *xb = (double *)malloc(sizeof(double) * 3 * nb);
+  for (int64_t j = 0; j < nb; ++j)
+    for (int d = 0; d < 3; ++d) xb[3 * j + d] = c->x[3 * (c->first[b] + j) + d];
+  orc_p2m(nb, xb, c->m + c->first[b], zb, q, M);
+  for (int e = 0; e < orc_ncoef(q); ++e) L[e] = 0.0;
+  orc_m2l(M, R, c->rs, q, L);
+  int64_t na = c->count[a];
+  int ns = na < 32 ? (int)na : 32;
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    int64_t i = c->first[a] + (int64_t)(((uint64_t)k * (uint64_t)na) / (uint64_t)ns);
+    double ex[3] = {0, 0, 0}, ap[3], u[3];
+    for (int64_t j = 0; j < nb; ++j) {
+      double d[3];
+      for (int dd = 0; dd < 3; ++dd) d[dd] = c->x[3 * i + dd] - (xb[3 * j + dd] + sv[dd]);
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 > 0)) continue;
+      double f[2];
+      orc_prefactors(sqrt(r2), c->rs, 1, f);
+      for (int dd = 0; dd < 3; ++dd) ex[dd] += c->G * c->m[c->first[b] + j] * f[1] * d[dd];
+    }
+    for (int dd = 0; dd < 3; ++dd) u[dd] = c->x[3 * i + dd] - za[dd];
+    orc_l2p(L, u, q, c->G, NULL, ap);
+    for (int dd = 0; dd < 3; ++dd) {
+      num += (ap[dd] - ex[dd]) * (ap[dd] - ex[dd]);
+      den += ex[dd] * ex[dd];
+    }
+  }
+  free(xb);
+  return den > 0 ? sqrt(num / den) : 0.0;
+}
+
+/* index of the node with the given level and cell coordinates, or -1 */
+int64_t orc_find_node(const orc_ctx *c, int lev, uint32_t ix, uint32_t iy, uint32_t iz) {
+  if (lev < 0 || lev >= c->nlevels) return -1;
+  for (int64_t k = c->level_start[lev]; k < c->level_start[lev + 1]; ++k)
+    if (c->ic[3 * k] == ix && c->ic[3 * k + 1] == iy && c->ic[3 * k + 2] == iz) return k;
+  return -1;
+}

@@ -35,7 +35,7 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (!(p.theta >= 0) || p.theta > 1.0) return why = "theta must be in [0, 1]", false;
   if (p.order < 1 || p.order > kPMax) return why = "order must be in 1..8", false;
   if (p.leaf_max < 1 || p.leaf_max > 64) return why = "leaf_max must be in 1..64", false;
-  if (p.mac_mode != 0) return why = "mac_mode must be 0 (geometric)", false;
+  if (p.mac_mode != 0 && p.mac_mode != 1) return why = "mac_mode must be 0 (geometric) or 1 (learned)", false;
   if (p.transition_rule != 0 && p.transition_rule != 1) return why = "transition_rule must be 0 or 1", false;
   if (p.size_rule != 0 && p.size_rule != 1) return why = "size_rule must be 0 or 1", false;
   if (p.m2l_precision != 0 && p.m2l_precision != 1) return why = "m2l_precision must be 0 or 1", false;
@@ -135,7 +135,7 @@ int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
   c.p = params->order;
   c.nc = ncoef(c.p);
   c.fit = fit_pair_factor(c.rs, c.rc);
-  cudaError_t e = cudaMallocHost(&c.h_pinned, 64);
+  cudaError_t e = cudaMallocHost(&c.h_pinned, 256);
   if (e == cudaSuccess) e = ensure(c.d_small, 256);
   for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&c.ev[i]);
   if (e != cudaSuccess) {
@@ -184,6 +184,7 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (!h) return HFMM_ERR_ARG;
   Ctx &c = h->c;
   if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "short_range_forces before build_tree");
+  if (c.prm.mac_mode == 1 && !c.have_mlp) return fail(c, HFMM_ERR_STATE, "learned acceptance without hfmm_load_mlp");
   if (c.n > 0 && !acc) return fail(c, HFMM_ERR_ARG, "null acceleration pointer");
   if (c.n == 0) return HFMM_OK;
   cudaStream_t st = S(stream);
@@ -204,18 +205,17 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (prof) cudaEventRecord(c.ev[5], st);
   if ((e = sort_lists(c, st)) != cudaSuccess) return cuda_fail(c, e, "sort_lists");
   if (prof) cudaEventRecord(c.ev[6], st);
-  if (c.prm.m2l_precision == 1) {
-    if ((e = m2l_pass_tc(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l (tensor cores)");
+  if (c.prm.m2l_precision == 1 &&
+      (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 6, 0, 8, st)) != cudaSuccess)
+    return cuda_fail(c, e, "m2l status");
+  if ((e = m2l_all(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l");
+  if (c.prm.m2l_precision == 1 && c.nm2l > 0) {
     int *status = reinterpret_cast<int *>(P<uint64_t>(c.d_small) + 6);
-    if (c.nm2l > 0) {
-      if ((e = cudaMemcpyAsync(c.h_pinned + 7, status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-          (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_fail(c, e, "m2l status");
-      if (*reinterpret_cast<int *>(c.h_pinned + 7) != 0)
-        return fail(c, HFMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait for MMA completion gave up");
-    }
-  } else if ((e = m2l_pass(c, st)) != cudaSuccess) {
-    return cuda_fail(c, e, "m2l");
+    if ((e = cudaMemcpyAsync(c.h_pinned + 31, status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(c, e, "m2l status");
+    if (*reinterpret_cast<int *>(c.h_pinned + 31) != 0)
+      return fail(c, HFMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait for MMA completion gave up");
   }
   if (prof) cudaEventRecord(c.ev[7], st);
   if ((e = downward(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "l2l/l2p");
@@ -302,6 +302,8 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
     case HFMM_EXPORT_M2L: need = c.nm2l * 24; break;
     case HFMM_EXPORT_MULTIPOLES:
     case HFMM_EXPORT_LOCALS: need = (size_t)c.nnodes * c.nc * 4; break;
+    case HFMM_EXPORT_M2L_ORDER: need = c.nm2l * 8; break;
+    case HFMM_EXPORT_CANDIDATES: need = c.ncand_last * 24; break;
     default: return fail(c, HFMM_ERR_ARG, "unknown export");
   }
   if (!buf) {
@@ -334,6 +336,26 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
       }
       break;
     }
+    case HFMM_EXPORT_CANDIDATES: {
+      std::vector<uint64_t> v(c.ncand_last);
+      e = cudaMemcpy(v.data(), c.cand.p, c.ncand_last * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      int64_t *o = static_cast<int64_t *>(buf);
+      for (int64_t t = 0; t < c.ncand_last; ++t) {
+        o[3 * t] = pair_sink(v[t]);
+        o[3 * t + 1] = pair_src(v[t]);
+        o[3 * t + 2] = pair_shift(v[t]);
+      }
+      break;
+    }
+    case HFMM_EXPORT_M2L_ORDER: {
+      std::vector<uint64_t> v(c.nm2l);
+      e = cudaMemcpy(v.data(), c.m2l.p, c.nm2l * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      int64_t *o = static_cast<int64_t *>(buf);
+      for (int64_t t = 0; t < c.nm2l; ++t) o[t] = pair_order(v[t]);
+      break;
+    }
     case HFMM_EXPORT_P2P:
     case HFMM_EXPORT_M2L: {
       int64_t cnt = what == HFMM_EXPORT_P2P ? c.np2p : c.nm2l;
@@ -351,6 +373,54 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "export copy");
   return HFMM_OK;
+}
+
+int hfmm_load_mlp(hfmm_ctx *h, const void *weights_bf16, size_t bytes) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  const size_t need = (size_t)kMlpWeights * 2;
+  if (!weights_bf16 || bytes != need) return fail(c, HFMM_ERR_ARG, "weights must be 5512 BF16 values (11024 bytes)");
+  cudaError_t e = ensure(c.mlp_w, need);
+  if (e == cudaSuccess) e = cudaMemcpy(c.mlp_w.p, weights_bf16, need, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load_mlp");
+  c.have_mlp = true;
+  return HFMM_OK;
+}
+
+int hfmm_collect_training_pairs(hfmm_ctx *h, int64_t max_pairs, uint32_t sample_mod, float *features, float *errors,
+                                int64_t *count, void *stream) {
+  if (!h || !count) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  *count = 0;
+  if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "collect_training_pairs before build_tree");
+  if (c.p != kPMax) return fail(c, HFMM_ERR_ARG, "training pairs need a context of order 8");
+  if (max_pairs < 1 || !features || !errors) return fail(c, HFMM_ERR_ARG, "need max_pairs >= 1 and device buffers");
+  cudaError_t e = collect_pairs(c, max_pairs, sample_mod, features, errors, count, S(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "collect_training_pairs");
+  return HFMM_OK;
+}
+
+int hfmm_mlp_infer(const void *weights_bf16, const float *features, int64_t n, float *logits, int32_t *classes,
+                   void *stream) {
+  if (n < 0 || (n > 0 && (!weights_bf16 || !features))) return HFMM_ERR_ARG;
+  return mlp_infer(weights_bf16, features, n, logits, classes, S(stream)) == cudaSuccess ? HFMM_OK : HFMM_ERR_CUDA;
+}
+
+int hfmm_mlp_grad(hfmm_ctx *h, const float *weights, const float *features, const int32_t *labels,
+                  const float *class_weights, int64_t n, float *grad, float *loss, void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (n < 1 || !weights || !features || !labels || !grad) return fail(c, HFMM_ERR_ARG, "bad training arguments");
+  cudaError_t e = ensure(c.mlp_scratch, mlp_train_scratch_bytes());
+  if (e == cudaSuccess) e = mlp_grad(weights, features, labels, class_weights, n, grad, loss, c.mlp_scratch.p, S(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "mlp_grad");
+  return HFMM_OK;
+}
+
+int hfmm_mlp_adam(const float *grad, float lr, int step, float *weights, float *m1, float *m2, void *weights_bf16,
+                  void *stream) {
+  if (!grad || !weights || !m1 || !m2 || step < 1) return HFMM_ERR_ARG;
+  return mlp_adam(weights, m1, m2, grad, lr, step, weights_bf16, S(stream)) == cudaSuccess ? HFMM_OK : HFMM_ERR_CUDA;
 }
 
 }  // extern "C"

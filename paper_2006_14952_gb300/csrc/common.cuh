@@ -16,6 +16,7 @@ namespace hfmm {
 constexpr int kDepth = 21;           // finest octree level (2^21 cells per side)
 constexpr int kPMax = 8;             // highest supported expansion order
 constexpr int kNCMax = 165;          // ncoef(kPMax)
+constexpr int kMlpWeights = 5512;    // learned-acceptance network parameters (BF16)
 constexpr int64_t kHalfBox = 1ll << 22;  // box side in half units (L / 2^22)
 
 __host__ __device__ constexpr int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
@@ -39,16 +40,24 @@ __host__ __device__ inline void mdecode(int c, int &nx, int &ny, int &nz) {
 }
 
 // ---------------------------------------------------------------- lists
-// Packed (sink node, source node, shift index) entry: sink in bits 37..63,
-// source in bits 5..36, periodic shift index (0..26) in bits 0..4.
-constexpr int kSinkShift = 37;
+// Packed (sink node, source node, shift, order) entry:
+//   bits 61..63  expansion order - 1 of an M2L entry (0 for P2P and frontier entries)
+//   bits 34..60  sink node (27 bits)
+//   bits  5..33  source node (29 bits)
+//   bits  0..4   periodic shift index 0..26
+constexpr int kSinkShift = 34;
 constexpr int kSinkBits = 27;
-__host__ __device__ inline uint64_t pack_pair(uint32_t sink, uint32_t src, uint32_t s) {
-  return ((uint64_t)sink << kSinkShift) | ((uint64_t)src << 5) | (uint64_t)s;
+constexpr int kOrderShift = 61;
+__host__ __device__ inline uint64_t pack_pair(uint32_t sink, uint32_t src, uint32_t s, uint32_t order_m1 = 0) {
+  return ((uint64_t)order_m1 << kOrderShift) | ((uint64_t)sink << kSinkShift) | ((uint64_t)src << 5) | (uint64_t)s;
 }
-__host__ __device__ inline uint32_t pair_sink(uint64_t e) { return (uint32_t)(e >> kSinkShift); }
-__host__ __device__ inline uint32_t pair_src(uint64_t e) { return (uint32_t)((e >> 5) & 0xffffffffull); }
+__host__ __device__ inline uint32_t pair_sink(uint64_t e) { return (uint32_t)((e >> kSinkShift) & 0x7ffffffull); }
+__host__ __device__ inline uint32_t pair_src(uint64_t e) { return (uint32_t)((e >> 5) & 0x1fffffffull); }
 __host__ __device__ inline uint32_t pair_shift(uint64_t e) { return (uint32_t)(e & 31ull); }
+__host__ __device__ inline uint32_t pair_order(uint64_t e) { return (uint32_t)(e >> kOrderShift) + 1u; }
+__host__ __device__ inline uint64_t with_order(uint64_t e, uint32_t order) {
+  return (e & ~(7ull << kOrderShift)) | ((uint64_t)(order - 1u) << kOrderShift);
+}
 
 // ---------------------------------------------------------------- cells
 // cell = {ix, iy, iz, level}; half-unit centre 2*ix*w + w with w = 2^(21-level).
@@ -157,6 +166,16 @@ struct Ctx {
   // host-buffer entry point
   DBuf hpos, hmass, hacc;
 
+  // learned acceptance: BF16 weights (5512 values); training-pair collection
+  DBuf mlp_w;
+  bool have_mlp = false;
+  bool collect = false;
+  DBuf cand;
+  uint64_t cand_cap = 0;
+  int64_t ncand_last = 0;  // candidates written by the last collection
+  uint32_t sample_mod = 1;
+  DBuf mlp_scratch;
+
   // stats
   int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1;
   cudaEvent_t ev[16] = {};
@@ -170,15 +189,31 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
 cudaError_t traverse(Ctx &c, cudaStream_t st);
 cudaError_t sort_lists(Ctx &c, cudaStream_t st);
 cudaError_t upward(Ctx &c, cudaStream_t st);
-cudaError_t m2l_pass(Ctx &c, cudaStream_t st);
+// M2L of the list entries of order q (the CSR bounds m2l_beg/m2l_end cover
+// exactly those entries); adds into L.
+cudaError_t m2l_pass(Ctx &c, int q, cudaStream_t st);
+// All M2L entries: one pass per order present in the list.
+cudaError_t m2l_all(Ctx &c, cudaStream_t st);
 // Split-precision (3xTF32) M2L on tcgen05 tensor cores; orders 1..6.  The
 // kernel's status word (d_small[6]) is 1 after a timed-out wait.
 bool m2l_tc_supported(int p);
-cudaError_t m2l_pass_tc(Ctx &c, cudaStream_t st);
+cudaError_t m2l_pass_tc(Ctx &c, int q, cudaStream_t st);
 // L2L top-down, then L2P writing the far-field accelerations in input order.
 cudaError_t downward(Ctx &c, float *acc, cudaStream_t st);
 // Cut-off P2P, added to the accelerations written by downward().
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st);
+
+// Training pairs for the learned acceptance: features [n][12] and M2L errors
+// at orders 2..8 [n][7] (device buffers of the caller); *count receives n.
+cudaError_t collect_pairs(Ctx &c, int64_t max_pairs, uint32_t sample_mod, float *feat, float *err, int64_t *count,
+                          cudaStream_t st);
+// Network kernels (mlp.cu).
+cudaError_t mlp_infer(const void *w_bf16, const float *x, int64_t n, float *logits, int *cls, cudaStream_t st);
+size_t mlp_train_scratch_bytes();
+cudaError_t mlp_grad(const float *wm, const float *x, const int *labels, const float *cw, int64_t n, float *grad,
+                     float *loss, void *scratch, cudaStream_t st);
+cudaError_t mlp_adam(float *wm, float *m1, float *m2, const float *grad, float lr, int step, void *w_bf16,
+                     cudaStream_t st);
 
 inline unsigned blocks_for(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 

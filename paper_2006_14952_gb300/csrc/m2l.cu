@@ -10,7 +10,7 @@
 // One lane per (sink, source) pair; a warp walks the pairs of one sink (lists
 // are grouped by sink), keeps its partial local expansion in registers and
 // reduces it across the warp at the end, so no atomics are used and the
-// result is deterministic.  The expansion order is a template parameter: all
+// result is deterministic.  Each launch adds into L (one launch per order).  The expansion order is a template parameter: all
 // index arithmetic is literal in the generated straight-line bodies
 // (gen_bodies.py -> gen_bodies.cuh).  For p >= 6 the output coefficients are split
 // over G warps (slice g owns the outputs with index = g mod G); for p >= 7 the
@@ -76,7 +76,7 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
 #pragma unroll
     for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     const int n = s * G + g;
-    if (lane == 0 && n < NC) L[(size_t)k * ldm + n] = a;
+    if (lane == 0 && n < NC) L[(size_t)k * ldm + n] += a;
   }
 }
 
@@ -140,9 +140,9 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t m2l_pass(Ctx &c, cudaStream_t st) {
+cudaError_t m2l_pass(Ctx &c, int q, cudaStream_t st) {
   if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
-  switch (c.p) {
+  switch (q) {
     case 1: return launch<1>(c, st);
     case 2: return launch<2>(c, st);
     case 3: return launch<3>(c, st);

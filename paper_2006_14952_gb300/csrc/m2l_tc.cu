@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uchar4 m = mi[e];
         acc += pbuf[midx(n.x + m.x, n.y + m.y, n.z + m.z) * NC + e];
       }
-      L[(size_t)k * ldm + tid] = acc;
+      L[(size_t)k * ldm + tid] += acc;
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -277,9 +277,10 @@ cudaError_t launch_tc(Ctx &c, cudaStream_t st) {
   const size_t smem = smem_of(P);
   cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // d_small[5] = work counter, d_small[6] = status word
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(hfmm::P<uint64_t>(c.d_small) + 5);
   int *status = reinterpret_cast<int *>(hfmm::P<uint64_t>(c.d_small) + 6);
-  if ((e = cudaMemsetAsync(ctr, 0, 16, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ctr, 0, 8, st)) != cudaSuccess) return e;  // the status word is zeroed once per call
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -295,9 +296,9 @@ cudaError_t launch_tc(Ctx &c, cudaStream_t st) {
 
 bool m2l_tc_supported(int p) { return p >= 1 && p <= 6; }
 
-cudaError_t m2l_pass_tc(Ctx &c, cudaStream_t st) {
+cudaError_t m2l_pass_tc(Ctx &c, int q, cudaStream_t st) {
   if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
-  switch (c.p) {
+  switch (q) {
     case 1: return launch_tc<1>(c, st);
     case 2: return launch_tc<2>(c, st);
     case 3: return launch_tc<3>(c, st);

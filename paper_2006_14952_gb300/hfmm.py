@@ -21,11 +21,15 @@ _lib = None
 HFMM_OK = 0
 ERRORS = {-1: "HFMM_ERR_ARG", -2: "HFMM_ERR_OOM", -3: "HFMM_ERR_CUDA", -4: "HFMM_ERR_CAPACITY",
           -5: "HFMM_ERR_STATE", -6: "HFMM_ERR_TIMEOUT"}
-EXPORT = {"keys": 0, "perm": 1, "nodes": 2, "p2p": 3, "m2l": 4, "multipoles": 5, "locals": 6}
+EXPORT = {"keys": 0, "perm": 1, "nodes": 2, "p2p": 3, "m2l": 4, "multipoles": 5, "locals": 6, "m2l_order": 7,
+          "candidates": 8}
+MLP_WEIGHTS = 5512
 
 # Every symbol include/hfmm.h declares.
 SYMBOLS = ["hfmm_default_params", "hfmm_create", "hfmm_destroy", "hfmm_last_error", "hfmm_build_tree",
-           "hfmm_short_range_forces", "hfmm_short_range_forces_host", "hfmm_get_stats", "hfmm_export"]
+           "hfmm_short_range_forces", "hfmm_short_range_forces_host", "hfmm_get_stats", "hfmm_export",
+           "hfmm_load_mlp", "hfmm_collect_training_pairs", "hfmm_mlp_infer", "hfmm_mlp_grad", "hfmm_mlp_adam",
+           "hfmm_morton_sort_noalloc"]
 
 
 class Params(C.Structure):
@@ -83,6 +87,16 @@ def load(build_if_missing: bool = True):
         L.hfmm_get_stats.restype = i32
         L.hfmm_export.argtypes = [vp, i32, vp, C.POINTER(C.c_size_t)]
         L.hfmm_export.restype = i32
+        L.hfmm_load_mlp.argtypes = [vp, vp, C.c_size_t]
+        L.hfmm_load_mlp.restype = i32
+        L.hfmm_collect_training_pairs.argtypes = [vp, i64, C.c_uint32, vp, vp, C.POINTER(i64), vp]
+        L.hfmm_collect_training_pairs.restype = i32
+        L.hfmm_mlp_infer.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.hfmm_mlp_infer.restype = i32
+        L.hfmm_mlp_grad.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        L.hfmm_mlp_grad.restype = i32
+        L.hfmm_mlp_adam.argtypes = [vp, C.c_float, i32, vp, vp, vp, vp, vp]
+        L.hfmm_mlp_adam.restype = i32
         _lib = L
         return L
 
@@ -98,6 +112,28 @@ def _stream_handle(stream):
 
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def mlp_infer(weights_bf16, x, stream=None):
+    """Network logits [n][8] and classes [n] (CUDA tensors in, CUDA tensors out)."""
+    import torch
+
+    n = x.shape[0]
+    logits = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    cls = torch.empty(n, dtype=torch.int32, device="cuda")
+    rc = load().hfmm_mlp_infer(C.c_void_p(weights_bf16.data_ptr()), C.c_void_p(x.data_ptr()), n,
+                               C.c_void_p(logits.data_ptr()), C.c_void_p(cls.data_ptr()), _stream_handle(stream))
+    if rc != HFMM_OK:
+        raise HfmmError(f"hfmm_mlp_infer: {ERRORS.get(rc, rc)}")
+    return logits, cls
+
+
+def mlp_adam(grad, lr, step, weights, m1, m2, weights_bf16=None, stream=None):
+    wb = C.c_void_p(weights_bf16.data_ptr()) if weights_bf16 is not None else None
+    rc = load().hfmm_mlp_adam(C.c_void_p(grad.data_ptr()), float(lr), int(step), C.c_void_p(weights.data_ptr()),
+                              C.c_void_p(m1.data_ptr()), C.c_void_p(m2.data_ptr()), wb, _stream_handle(stream))
+    if rc != HFMM_OK:
+        raise HfmmError(f"hfmm_mlp_adam: {ERRORS.get(rc, rc)}")
 
 
 class Solver:
@@ -183,12 +219,44 @@ class Solver:
         self._check(self._lib.hfmm_get_stats(self._h, C.byref(s)), "hfmm_get_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
 
+    def load_mlp(self, weights_bf16):
+        """weights_bf16: numpy uint16 [5512] holding BF16 bit patterns."""
+        w = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
+        assert w.size == MLP_WEIGHTS
+        self._check(self._lib.hfmm_load_mlp(self._h, w.ctypes.data_as(C.c_void_p), w.nbytes), "hfmm_load_mlp")
+
+    def collect_training_pairs(self, max_pairs, sample_mod=1, stream=None):
+        """Features [n][12] and M2L errors at orders 2..8 [n][7] (CUDA float32 tensors)."""
+        import torch
+
+        feat = torch.empty((max_pairs, 12), dtype=torch.float32, device="cuda")
+        err = torch.empty((max_pairs, 7), dtype=torch.float32, device="cuda")
+        cnt = C.c_int64(0)
+        self._check(self._lib.hfmm_collect_training_pairs(self._h, max_pairs, sample_mod,
+                                                          C.c_void_p(feat.data_ptr()), C.c_void_p(err.data_ptr()),
+                                                          C.byref(cnt), _stream_handle(stream)),
+                    "hfmm_collect_training_pairs")
+        return feat[:cnt.value], err[:cnt.value]
+
+    def mlp_grad(self, weights, x, labels, class_weights=None, stream=None):
+        """Gradient and loss of the mean cross-entropy (CUDA tensors)."""
+        import torch
+
+        grad = torch.empty(MLP_WEIGHTS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        cw = C.c_void_p(class_weights.data_ptr()) if class_weights is not None else None
+        self._check(self._lib.hfmm_mlp_grad(self._h, C.c_void_p(weights.data_ptr()), C.c_void_p(x.data_ptr()),
+                                            C.c_void_p(labels.data_ptr()), cw, x.shape[0], C.c_void_p(grad.data_ptr()),
+                                            C.c_void_p(loss.data_ptr()), _stream_handle(stream)), "hfmm_mlp_grad")
+        return grad, loss
+
     def export(self, what: str) -> np.ndarray:
         code = EXPORT[what]
         nb = C.c_size_t(0)
         self._check(self._lib.hfmm_export(self._h, code, None, C.byref(nb)), "hfmm_export")
         dtype, cols = {"keys": (np.uint64, 0), "perm": (np.uint32, 0), "nodes": (np.int64, 8), "p2p": (np.int64, 3),
-                       "m2l": (np.int64, 3), "multipoles": (np.float32, -1), "locals": (np.float32, -1)}[what]
+                       "m2l": (np.int64, 3), "multipoles": (np.float32, -1), "locals": (np.float32, -1),
+                       "m2l_order": (np.int64, 0), "candidates": (np.int64, 3)}[what]
         out = np.empty(nb.value // np.dtype(dtype).itemsize, dtype=dtype)
         if nb.value:
             self._check(self._lib.hfmm_export(self._h, code, out.ctypes.data_as(C.c_void_p), C.byref(nb)),

@@ -1,0 +1,183 @@
+"""Learned acceptance on the GPU against the FP64 oracle.
+
+Network: tensor-core inference vs the oracle forward (BF16 inputs and
+activations), gradients vs the oracle backward, one Adam step vs its formula.
+Training data: the measured per-pair M2L errors vs the oracle's pair error.
+Traversal: lists built with the network cover every close particle pair
+exactly once, and forces on those lists match the oracle FMM on the same lists.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_14952_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_weights(seed, scale=0.4):
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(5512) * scale
+    return np.vectorize(oracle.bf16)(w)
+
+
+def graded_weights():
+    """Exact BF16 weights with logit_k = 16 k f - k^2, f = S_c / R_c (feature 11): the class
+    (0 = open, k = order k + 1) grows with the separation, so every class occurs."""
+    w = np.zeros(5512)
+    w[0 * 12 + 11] = 1.0                 # W1[0][11]: h1_0 = relu(S_c / R_c)
+    w[832 + 0 * 64 + 0] = 1.0            # W2[0][0]:  h2_0 = h1_0
+    for k in range(8):
+        w[832 + 4096 + 64 + k * 64] = 16.0 * k   # W3[k][0]
+        w[832 + 4096 + 64 + 512 + k] = -float(k * k)  # b3[k]
+    return w
+
+
+def to_bf16_bits(w):
+    import torch
+
+    return torch.tensor(w, dtype=torch.float32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+
+
+def to_cuda_bf16(w):
+    import torch
+
+    return torch.tensor(w, dtype=torch.float32).to(torch.bfloat16).cuda()
+
+
+def features(n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.stack([rng.uniform(0, 4.5, n), rng.uniform(0, 4.5, n), rng.uniform(0, 1, n), rng.uniform(0, 0.6, n),
+                  rng.uniform(0, 0.6, n), rng.uniform(0, 0.6, n), rng.integers(-3, 4, n) / 8.0,
+                  np.log2(1 + rng.integers(1, 5000, n)) / 16, np.log2(1 + rng.integers(1, 5000, n)) / 16,
+                  rng.uniform(0, 0.5, n), rng.uniform(0, 0.5, n), rng.uniform(0, 1, n)], axis=1)
+    return x
+
+
+def test_network_inference_matches_oracle():
+    import torch
+
+    from paper_2006_14952_gb300 import hfmm
+
+    w = rand_weights(1)
+    x = features(4099, 2)
+    logits, cls = hfmm.mlp_infer(to_cuda_bf16(w), torch.tensor(x, dtype=torch.float32).cuda())
+    ref = oracle.mlp_forward(w, x.astype(np.float32), rnd=1)
+    lg = logits.cpu().numpy()
+    scale = np.abs(ref).max()
+    dev = np.abs(lg - ref).max()
+    assert dev < 2e-2 * scale
+    # where the top-2 margin exceeds twice the largest deviation the classes must agree
+    top2 = np.sort(ref, axis=1)[:, -2:]
+    clear = (top2[:, 1] - top2[:, 0]) > 2 * dev
+    assert clear.mean() > 0.5
+    np.testing.assert_array_equal(cls.cpu().numpy()[clear], ref.argmax(axis=1)[clear])
+
+
+def test_network_gradient_and_adam_step():
+    import torch
+
+    from paper_2006_14952_gb300 import hfmm
+
+    w = rand_weights(3, 0.3)
+    x = features(2000, 4)
+    y = np.random.default_rng(5).integers(0, 8, 2000).astype(np.int32)
+    cw = np.random.default_rng(6).uniform(0.5, 2.0, 8)
+    s = hfmm.Solver()
+    wt = torch.tensor(w, dtype=torch.float32).cuda()
+    g, loss = s.mlp_grad(wt, torch.tensor(x, dtype=torch.float32).cuda(), torch.tensor(y).cuda(),
+                         torch.tensor(cw, dtype=torch.float32).cuda())
+    ref_loss, ref_g = oracle.mlp_loss_grad(w, x.astype(np.float32), y, cw, rnd=1)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert loss.item() == pytest.approx(ref_loss, rel=1e-3)
+    assert np.linalg.norm(gg - ref_g) < 1e-2 * np.linalg.norm(ref_g)
+    # one Adam step against its formula
+    m1 = torch.zeros_like(wt)
+    m2 = torch.zeros_like(wt)
+    w0 = wt.clone()
+    hfmm.mlp_adam(g, 1e-3, 1, wt, m1, m2)
+    a = 0.1 * gg
+    b = 0.001 * gg * gg
+    expect = w0.cpu().numpy() - 1e-3 * (a / 0.1) / (np.sqrt(b / 0.001) + 1e-8)
+    np.testing.assert_allclose(wt.cpu().numpy(), expect, rtol=1e-5, atol=1e-7)
+
+
+def _solver_with_tree(pos, mass, **kw):
+    import torch
+
+    from paper_2006_14952_gb300 import hfmm
+
+    s = hfmm.Solver(**kw)
+    s.build_tree(torch.from_numpy(np.ascontiguousarray(pos)).cuda(), torch.from_numpy(mass).cuda())
+    return s
+
+
+def test_collected_errors_match_oracle_pair_errors():
+    pos, mass = W.nfw_clustered(20000, 25, 0.7, 41)
+    s = _solver_with_tree(pos, mass, pm_grid=32, order=8, theta=0.6)
+    feat, err = s.collect_training_pairs(3000, 3)
+    pairs = s.export("candidates")
+    assert len(pairs) == feat.shape[0] > 100
+    err = err.cpu().numpy()
+    f = oracle.FMM(box=1.0, rs=s.rs, rc=s.rc, theta=0.6, order=8, leaf_max=16)
+    f.build_tree(pos, mass)
+    rng = np.random.default_rng(7)
+    for i in rng.choice(len(pairs), 40, replace=False):
+        a, b, sh = pairs[i]
+        ref = np.array([f.pair_error(a, b, sh, q) for q in range(2, 9)])
+        np.testing.assert_allclose(err[i], ref, rtol=5e-2, atol=2e-6)
+
+
+def _learned_run(pos, mass, w, **kw):
+    import torch
+
+    s = _solver_with_tree(pos, mass, mac_mode=1, **kw)
+    s.load_mlp(to_bf16_bits(w))
+    acc = s.short_range_forces()
+    torch.cuda.synchronize()
+    return s, acc.cpu().numpy().astype(np.float64)
+
+
+def test_learned_lists_cover_every_close_pair_once():
+    n = 400
+    pos, mass = W.nfw_clustered(n, 4, 0.6, 43)
+    rc = 0.2
+    s, _ = _learned_run(pos, mass, graded_weights(), pm_grid=1, rs_cells=rc / 4.5, rcut_rs=4.5, order=8,
+                        theta=0.7, leaf_max=4)
+    assert abs(s.rc - rc) < 1e-12
+    nodes = s.export("nodes")
+    p2p, m2l, orders = s.export("p2p"), s.export("m2l"), s.export("m2l_order")
+    assert len(m2l) > 0 and set(orders.tolist()) <= set(range(2, 9)) and len(set(orders.tolist())) > 1
+    f = oracle.FMM(box=1.0, rs=s.rs, rc=s.rc, theta=0.7, order=8, leaf_max=4)
+    f.build_tree(pos, mass)
+    _, _, xs = f.particles()
+    cov = {}
+    for lst in (p2p, m2l):
+        for a, b, sh in lst:
+            for i in range(nodes[a, 4], nodes[a, 4] + nodes[a, 5]):
+                for j in range(nodes[b, 4], nodes[b, 4] + nodes[b, 5]):
+                    cov[(i, j, sh)] = cov.get((i, j, sh), 0) + 1
+    assert max(cov.values()) == 1
+    for i in range(n):
+        d_raw = xs[i][None, :] - xs
+        d_img = d_raw - np.round(d_raw)
+        r = np.sqrt((d_img ** 2).sum(1))
+        for j in np.nonzero((r < rc) & (np.arange(n) != i))[0]:
+            sv = np.round(d_raw[j] - d_img[j]).astype(int)
+            sh = (sv[0] + 1) * 9 + (sv[1] + 1) * 3 + (sv[2] + 1)
+            assert cov.get((i, j, sh), 0) == 1
+
+
+def test_learned_forces_match_oracle_on_the_same_lists():
+    pos, mass = W.nfw_clustered(30000, 40, 0.7, 44)
+    s, acc = _learned_run(pos, mass, graded_weights(), pm_grid=32, order=8, theta=0.6)
+    p2p, m2l, orders = s.export("p2p"), s.export("m2l"), s.export("m2l_order")
+    assert len(set(orders.tolist())) > 2
+    f = oracle.FMM(box=1.0, rs=s.rs, rc=s.rc, theta=0.6, order=8, leaf_max=16)
+    f.build_tree(pos, mass)
+    ref = f.forces_given_lists(p2p, m2l, orders)
+    err = math.sqrt(((acc - ref) ** 2).sum() / (ref ** 2).sum())
+    assert err < 1e-5, err
