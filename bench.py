@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.3)
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
+    ap.add_argument("--mac", default="geometric", choices=["geometric", "learned"])
+    ap.add_argument("--mlp-weights", default=os.path.join(ROOT, "paper_2006_14952_gb300", "weights", "mac_weights.bin"))
     ap.add_argument("--accuracy-sinks", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=25.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -230,8 +232,13 @@ def main():
     n = pos.shape[1]
     # timed solver: phase events only (profile bit 0); the pair counts come from
     # one untimed run of a second context with counting on (bit 1)
+    learned = args.mac == "learned"
+    mac_kw = dict(mac_mode=1) if learned else {}
+    wts = np.fromfile(args.mlp_weights, dtype=np.uint16) if learned else None
     s = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                    order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=1)
+                    order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=1, **mac_kw)
+    if learned:
+        s.load_mlp(wts)
     dpos = torch.from_numpy(pos).to(dev)
     dmass = torch.from_numpy(mass).to(dev)
     acc = torch.empty((3, n), dtype=torch.float32, device=dev)
@@ -247,7 +254,9 @@ def main():
         step()
     torch.cuda.synchronize()
     sc = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=3)
+                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=3, **mac_kw)
+    if learned:
+        sc.load_mlp(wts)
     sc.build_tree(dpos, dmass)
     sc.short_range_forces(torch.empty_like(acc))
     counts = sc.get_stats()
@@ -298,7 +307,9 @@ def main():
     pin_mass = torch.from_numpy(mass).pin_memory()
     pin_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
     s2 = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision)
+                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, **mac_kw)
+    if learned:
+        s2.load_mlp(wts)
     for _ in range(2):
         s2.short_range_forces_host(pin_pos, pin_mass, pin_acc)
     e2e_s = 0.0
@@ -328,7 +339,7 @@ def main():
                 "algorithmic": f"{st['p2p_useful_pairs']} pairs inside R_c x {P2P_FLOPS_PER_PAIR} flop"}
     else:
         p = args.order
-        fl_pair = 2 * math.comb(p + 6, 6)
+        fl_pair = 2 * math.comb(p + 6, 6)  # for the learned path: counted at the largest order (an upper bound)
         achieved = st["nm2l"] * fl_pair / (mean["t_m2l"] / 1e3) / 1e12
         roof = {"kernel": f"k_m2l<{p}> (CUDA cores)", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
                 "unit": "TFLOP/s", "frac": achieved / peak_fp32,
@@ -346,8 +357,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg),
-                       "path": "geometric acceptance, " + ("3xTF32 tensor-core M2L" if args.m2l_precision == 1
-                                                           else "FP32 CUDA-core M2L"),
+                       "path": ("learned acceptance (network, safety bound theta), " if learned else
+                                "geometric acceptance, ") + ("3xTF32 tensor-core M2L" if args.m2l_precision == 1
+                                                             else "FP32 CUDA-core M2L"),
                        "theta": args.theta, "order": args.order, "leaf_max": cfg.leaf_max,
                        "transition_rule": 1, "size_rule": 1, "l2": "flushed (512 MB write) before every step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},

@@ -12,7 +12,8 @@ Pipeline (all on the GPU through the C ABI):
 The BF16 weights go to mac_weights.bin (5512 little-endian uint16) with a
 JSON summary beside them.
 
-    python -m paper_2006_14952_gb300.train_mac [--eps 2e-5] [--steps 600] [--out DIR]
+    python -m paper_2006_14952_gb300.train_mac [--eps 3e-4] [--theta-safety 0.35] [--max-order 6]
+                                               [--steps 500] [--out DIR]
 """
 from __future__ import annotations
 
@@ -50,10 +51,10 @@ def collect(cfg, theta_safety: float, max_pairs: int, sample_mod: int):
     return feat.clone(), err.clone()
 
 
-def make_labels(err, eps: float):
+def make_labels(err, eps: float, max_order: int = 8):
     import torch
 
-    ok = err <= eps  # [n][7], orders 2..8
+    ok = err[:, : max_order - 1] <= eps  # [n][max_order - 1], orders 2..max_order
     first = torch.where(ok.any(dim=1), ok.float().argmax(dim=1) + 1, torch.zeros_like(ok[:, 0], dtype=torch.long))
     return first.to(torch.int32)  # 0 = open, k = order k + 1
 
@@ -94,9 +95,10 @@ def train(x, y, steps: int, lr: float, seed: int = 7, log=None):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--eps", type=float, default=2e-5, help="per-pair relative error budget of an accepted M2L")
-    ap.add_argument("--theta-safety", type=float, default=0.6)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--eps", type=float, default=3e-4, help="per-pair relative error budget of an accepted M2L")
+    ap.add_argument("--theta-safety", type=float, default=0.35)
+    ap.add_argument("--max-order", type=int, default=6, help="largest order a label may choose")
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--max-pairs", type=int, default=200000)
     ap.add_argument("--sample-mod", type=int, default=7)
@@ -115,7 +117,7 @@ def main():
         print(f"{cfg.name}: {f.shape[0]} pairs", flush=True)
     x = torch.cat(xs).contiguous()
     err = torch.cat(es).contiguous()
-    y = make_labels(err, args.eps).contiguous()
+    y = make_labels(err, args.eps, args.max_order).contiguous()
     hist = torch.bincount(y.long(), minlength=8).tolist()
     print("label histogram (open, q=2..8):", hist, flush=True)
     w, wb, losses, cw = train(x, y, args.steps, args.lr, log=lambda s: print(s, flush=True))
@@ -123,10 +125,12 @@ def main():
     acc = float((cls == y).float().mean().item())
     # a decision is safe when it opens, or accepts an order whose measured error is within budget
     q = cls.long()
+    q = q.clamp(max=args.max_order - 1)
     safe = (q == 0) | (err.gather(1, (q - 1).clamp(min=0).unsqueeze(1)).squeeze(1) <= args.eps)
     os.makedirs(args.out, exist_ok=True)
     wb.cpu().view(torch.int16).numpy().astype(np.int16).view(np.uint16).tofile(os.path.join(args.out, "mac_weights.bin"))
-    meta = {"eps": args.eps, "theta_safety": args.theta_safety, "pairs": int(x.shape[0]), "labels": hist,
+    meta = {"eps": args.eps, "theta_safety": args.theta_safety, "max_order": args.max_order,
+            "pairs": int(x.shape[0]), "labels": hist,
             "train_accuracy": acc, "safe_fraction": float(safe.float().mean().item()), "losses": losses,
             "class_weights": cw.cpu().tolist(), "steps": args.steps, "lr": args.lr, "seconds": time.time() - t0,
             "sets": [c.name for c in make_sets()]}

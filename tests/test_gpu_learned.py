@@ -181,3 +181,43 @@ def test_learned_forces_match_oracle_on_the_same_lists():
     ref = f.forces_given_lists(p2p, m2l, orders)
     err = math.sqrt(((acc - ref) ** 2).sum() / (ref ** 2).sum())
     assert err < 1e-5, err
+
+
+def _m2l_flops(s):
+    orders = s.export("m2l_order")
+    return int(sum(2 * math.comb(int(q) + 6, 6) for q in orders))
+
+
+def test_trained_network_gains_over_geometric_rule():
+    """The committed network (trained by train_mac.py) against the geometric rule with the
+    same safety bound (theta 0.35) and largest order (6): the same accuracy class
+    (RMS <= 1e-4 against the FP64 direct sum) for less M2L work."""
+    import os
+
+    import torch
+
+    from paper_2006_14952_gb300 import hfmm
+
+    wpath = os.path.join(os.path.dirname(hfmm.__file__), "weights", "mac_weights.bin")
+    w = np.fromfile(wpath, dtype=np.uint16)
+    cfg = W.scaled(W.CONFIGS["nfw-2m"], 262144, halo_count=250, seed=3001)
+    pos, mass = W.make(cfg)
+    sinks = W.subsample(cfg.n, 4000, 5)
+    ref = oracle.direct_sr(pos, mass, 1.0, cfg.rs, cfg.rc, sinks=sinks)
+
+    def run(**kw):
+        s = _solver_with_tree(pos, mass, pm_grid=cfg.pm_grid, order=6, theta=0.35, **kw)
+        if kw.get("mac_mode") == 1:
+            s.load_mlp(w)
+        acc = s.short_range_forces()
+        torch.cuda.synchronize()
+        a = acc.cpu().numpy().astype(np.float64)[:, sinks]
+        e = np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        return s, math.sqrt((e ** 2).mean())
+
+    sg, eg = run()
+    sl, el = run(mac_mode=1)
+    fg, fl = _m2l_flops(sg), _m2l_flops(sl)
+    print(f"geometric: rms {eg:.2e}, M2L {fg:.3e} flop; learned: rms {el:.2e}, M2L {fl:.3e} flop")
+    assert el <= 1e-4 and eg <= 1e-4
+    assert fl < fg
