@@ -153,6 +153,7 @@ struct Ctx {
   DBuf m2l, m2l_alt, p2p, p2p_alt;  // packed u64 entries
   int64_t nm2l = 0, np2p = 0;
   int traverse_iters = 0;
+  uint64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;  // traversal capacities (entries)
   DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
 
   // expansions (scaled): M~ = M / h^|m|, L~ = L h^(|n|+1)

@@ -19,7 +19,13 @@
 // class chooses between opening the pair and M2L at an order q = 2..p.
 // Collection mode records a hash-sampled subset of candidates while opening
 // every pair (training data for the network).
+#include <cooperative_groups.h>
+
+#include <cstring>
+
 #include "mlp.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hfmm {
 namespace {
@@ -84,26 +90,19 @@ __device__ __forceinline__ uint8_t classify(uint4 ca, uint4 cb, uint32_t s, int2
   return open_rule(ca, cb, ka, kb);
 }
 
-__global__ void k_init_frontier(uint64_t *f) {
-  int s = threadIdx.x;
-  if (s < 27) f[s] = pack_pair(0, 0, (uint32_t)s);
-}
+// One frontier pair: its class (bits 0..2) and M2L order (bits 3..6), and the
+// number of M2L entries, P2P entries and child pairs it produces.  Called by
+// all 32 lanes of a warp (the network runs on warp batches of candidates).
+struct Item {
+  uint8_t cls;
+  uint32_t nm, np, nch;
+};
 
-// counts layout [3][nf]: M2L flags, P2P flags, child-pair counts.
-// cls: bits 0..2 the class, bits 3..6 the M2L order.
-__global__ void __launch_bounds__(256) k_mac_count(const uint64_t *__restrict__ f, int64_t nf,
-                                                   const uint4 *__restrict__ cell, const int2 *__restrict__ kids,
-                                                   Mac m, uint8_t *__restrict__ cls, uint32_t *__restrict__ counts) {
-  __shared__ uint32_t sw[kMlpSmemWords];
-  __shared__ __align__(16) __nv_bfloat16 xs[8][32 * 16];
-  __shared__ uint8_t dec[8][32];
-  if (m.mode == 1) {
-    mlp_stage(m.w, sw);
-    __syncthreads();
-  }
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = t < nf;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+template <bool kNet>
+__device__ __forceinline__ Item mac_item(const uint64_t *__restrict__ f, int64_t t, bool valid,
+                                         const uint4 *__restrict__ cell, const int2 *__restrict__ kids, const Mac &m,
+                                         const uint32_t *sw, __nv_bfloat16 *xs, uint8_t *dec) {
+  const int lane = threadIdx.x & 31;
   uint64_t e = 0;
   uint32_t a = 0, b = 0, s = 0;
   int2 ka = make_int2(-1, 0), kb = make_int2(-1, 0);
@@ -128,11 +127,11 @@ __global__ void __launch_bounds__(256) k_mac_count(const uint64_t *__restrict__ 
     }
     c = open_rule(ca, cb, ka, kb);
   }
-  if (m.mode == 1) {  // warp-batched network decisions for the candidates
+  if (kNet && m.mode == 1) {  // warp-batched network decisions for the candidates
     const unsigned want = __ballot_sync(0xffffffffu, c == kCandidate);
     if (want) {
       const int slot = __popc(want & ((1u << lane) - 1u)), nc = __popc(want);
-      __nv_bfloat16 *row = xs[wp] + slot * 16;
+      __nv_bfloat16 *row = xs + slot * 16;
       if (c == kCandidate) {
         float ft[kMlpIn];
         pair_features(ca, cb, s, m.range[a].y, m.range[b].y, m.M + (size_t)b * m.ldm, m.inv_rs_h, m.inv_rc_h, ft);
@@ -141,21 +140,21 @@ __global__ void __launch_bounds__(256) k_mac_count(const uint64_t *__restrict__ 
       }
       for (int r = nc + lane; r < ((nc + 15) & ~15); r += 32)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) xs[wp][r * 16 + k] = __float2bfloat16_rn(0.f);
+        for (int k = 0; k < 16; ++k) xs[r * 16 + k] = __float2bfloat16_rn(0.f);
       __syncwarp();
       for (int bt = 0; bt < nc; bt += 16) {
         float l[4];
-        mlp_logits16(sw, xs[wp] + bt * 16, l);
+        mlp_logits16(sw, xs + bt * 16, l);
         int c0, c8;
         mlp_argmax16(l, c0, c8);
         if ((lane & 3) == 0) {
-          dec[wp][bt + (lane >> 2)] = (uint8_t)c0;
-          dec[wp][bt + (lane >> 2) + 8] = (uint8_t)c8;
+          dec[bt + (lane >> 2)] = (uint8_t)c0;
+          dec[bt + (lane >> 2) + 8] = (uint8_t)c8;
         }
       }
       __syncwarp();
       if (c == kCandidate) {
-        const int k = dec[wp][slot];
+        const int k = dec[slot];
         if (k == 0) {
           c = open_rule(ca, cb, ka, kb);
         } else {
@@ -163,51 +162,182 @@ __global__ void __launch_bounds__(256) k_mac_count(const uint64_t *__restrict__ 
           order = (uint32_t)(k + 1) < order ? (uint32_t)(k + 1) : order;
         }
       }
+      __syncwarp();
     }
   }
-  if (!valid) return;
-  cls[t] = (uint8_t)(c | (order << 3));
-  uint32_t nm = c == kM2L, np = c == kP2P, nch = 0;
-  if (c == kOpenA) nch = ka.y;
-  if (c == kOpenB) nch = kb.y;
-  if (c == kOpenAB) nch = ka.y * kb.y;
-  counts[t] = nm;
-  counts[nf + t] = np;
-  counts[2 * nf + t] = nch;
+  Item it;
+  it.cls = (uint8_t)(c | (order << 3));
+  it.nm = c == kM2L;
+  it.np = c == kP2P;
+  it.nch = c == kOpenA ? (uint32_t)ka.y : c == kOpenB ? (uint32_t)kb.y : c == kOpenAB ? (uint32_t)(ka.y * kb.y) : 0u;
+  return it;
 }
 
-__global__ void k_mac_emit(const uint64_t *__restrict__ f, int64_t nf, const uint8_t *__restrict__ cls,
-                           const uint32_t *__restrict__ offs, const int2 *__restrict__ kids,
-                           uint64_t *__restrict__ m2l, uint64_t *__restrict__ p2p, uint64_t *__restrict__ next) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nf) return;
-  const uint8_t cc = cls[t];
-  const uint8_t c = cc & 7;
-  if (c == kSkip) return;
-  uint64_t e = f[t];
-  if (c == kM2L) {
-    m2l[offs[t]] = with_order(e, cc >> 3);
-    return;
+struct TravState {
+  unsigned long long nm2l, np2p, nf;
+  int iters, overflow;
+};
+
+constexpr int kTT = 256;  // threads of the traversal kernel
+
+// Persistent level-synchronous traversal: one cooperative launch processes
+// every level.  Per level each block classifies a contiguous chunk of the
+// frontier and publishes its counts; after a grid barrier every block forms
+// its output offsets from the counts of the blocks before it and writes its
+// M2L entries, P2P entries and child pairs in frontier order (the same order
+// as a serial pass, so the lists are deterministic).  Outputs beyond the
+// given capacities set st->overflow and stop the walk; the host grows the
+// buffers and runs it again.
+template <bool kNet>
+__global__ void __launch_bounds__(kTT, kNet ? 2 : 4) k_traverse(const uint4 *__restrict__ cell,
+                                                  const int2 *__restrict__ kids, Mac m,
+                                                  uint64_t *fa, uint64_t *fb, unsigned long long capF,
+                                                  uint8_t *__restrict__ cls, uint64_t *__restrict__ m2l,
+                                                  unsigned long long capM, uint64_t *__restrict__ p2p,
+                                                  unsigned long long capP, uint32_t *__restrict__ btot,
+                                                  TravState *__restrict__ st, int max_iters) {
+  cg::grid_group grid = cg::this_grid();
+  constexpr int kSw = kNet ? kMlpSmemWords : 1, kXs = kNet ? 32 * 16 : 1, kDec = kNet ? 32 : 1;
+  __shared__ uint32_t sw[kSw];
+  __shared__ __align__(16) __nv_bfloat16 xs[kTT / 32][kXs];
+  __shared__ uint8_t dec[kTT / 32][kDec];
+  __shared__ uint32_t ws[kTT / 32][3];
+  __shared__ unsigned long long pre[3], sums[3];
+  if (kNet) mlp_stage(m.w, sw);
+  const int tid = threadIdx.x, wp = tid >> 5;
+  const unsigned nb = gridDim.x, bid = blockIdx.x;
+  if (bid == 0 && tid < 27) fa[tid] = pack_pair(0, 0, (uint32_t)tid);
+  __syncthreads();
+  grid.sync();
+  uint64_t *cur = fa, *nxt = fb;
+  unsigned long long nf = 27, nm = 0, np = 0;
+  const int lane = tid & 31;
+  constexpr int kW = kTT / 32;
+  int iter = 0;
+  for (; iter < max_iters && nf > 0; ++iter) {
+    // block range, then one contiguous sub-range per warp
+    const unsigned long long chunk = (nf + nb - 1) / nb;
+    const unsigned long long lo = chunk * bid < nf ? chunk * bid : nf;
+    const unsigned long long hi = lo + chunk < nf ? lo + chunk : nf;
+    const unsigned long long wch = (hi - lo + kW - 1) / kW;
+    const unsigned long long wlo = lo + wch * wp < hi ? lo + wch * wp : hi;
+    const unsigned long long whi = wlo + wch < hi ? wlo + wch : hi;
+    uint32_t cnt[3] = {0, 0, 0};
+    for (unsigned long long base = wlo; base < whi; base += 32) {
+      const unsigned long long t = base + lane;
+      const bool valid = t < whi;
+      const Item it = mac_item<kNet>(cur, (int64_t)t, valid, cell, kids, m, sw, xs[wp], dec[wp]);
+      if (valid) {
+        cls[t] = it.cls;
+        cnt[0] += it.nm;
+        cnt[1] += it.np;
+        cnt[2] += it.nch;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o; o >>= 1) cnt[k] += __shfl_xor_sync(0xffffffffu, cnt[k], o);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ws[wp][k] = cnt[k];
+    __syncthreads();
+    if (tid < 3) {
+      uint32_t t = 0;
+      for (int q = 0; q < kW; ++q) t += ws[q][tid];
+      btot[3 * bid + tid] = t;
+    }
+    __threadfence();
+    grid.sync();
+    if (tid < 3) {
+      unsigned long long before = 0, all = 0;
+      for (unsigned q = 0; q < nb; ++q) {
+        const unsigned long long v = btot[3 * q + tid];
+        if (q < bid) before += v;
+        all += v;
+      }
+      pre[tid] = before;
+      sums[tid] = all;
+    }
+    __syncthreads();
+    const unsigned long long Tm = sums[0], Tp = sums[1], Tc = sums[2];
+    if (nm + Tm > capM || np + Tp > capP || Tc > capF) {
+      if (bid == 0 && tid == 0) st->overflow = 1;
+      break;  // every block takes the same decision
+    }
+    // this warp's offsets: the block's offsets plus the counts of the warps before it
+    unsigned long long om = nm + pre[0], op = np + pre[1], oc = pre[2];
+    for (int q = 0; q < wp; ++q) {
+      om += ws[q][0];
+      op += ws[q][1];
+      oc += ws[q][2];
+    }
+    for (unsigned long long base = wlo; base < whi; base += 32) {
+      const unsigned long long t = base + lane;
+      const bool valid = t < whi;
+      uint8_t cc = 0;
+      uint64_t e = 0;
+      int2 ka = make_int2(-1, 0), kb = make_int2(-1, 0);
+      uint32_t v[3] = {0, 0, 0};
+      if (valid) {
+        cc = cls[t];
+        e = cur[t];
+        const uint8_t c = cc & 7;
+        if (c == kM2L) v[0] = 1;
+        if (c == kP2P) v[1] = 1;
+        if (c == kOpenA || c == kOpenB || c == kOpenAB) {
+          ka = kids[pair_sink(e)];
+          kb = kids[pair_src(e)];
+          v[2] = c == kOpenA ? ka.y : c == kOpenB ? kb.y : ka.y * kb.y;
+        }
+      }
+      uint32_t x[3] = {v[0], v[1], v[2]};
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
+          if (lane >= o) x[k] += y;
+        }
+      if (valid) {
+        const uint8_t c = cc & 7;
+        if (c == kM2L) m2l[om + x[0] - v[0]] = with_order(e, cc >> 3);
+        if (c == kP2P) p2p[op + x[1] - v[1]] = e;
+        if (c == kOpenA || c == kOpenB || c == kOpenAB) {
+          const uint32_t a = pair_sink(e), b = pair_src(e), s = pair_shift(e);
+          uint32_t a0 = a, na = 1, b0 = b, nbb = 1;
+          if (c == kOpenA || c == kOpenAB) {
+            a0 = (uint32_t)ka.x;
+            na = (uint32_t)ka.y;
+          }
+          if (c == kOpenB || c == kOpenAB) {
+            b0 = (uint32_t)kb.x;
+            nbb = (uint32_t)kb.y;
+          }
+          uint64_t *o = nxt + oc + x[2] - v[2];
+          for (uint32_t xx = 0; xx < na; ++xx)
+            for (uint32_t y = 0; y < nbb; ++y) *o++ = pack_pair(a0 + xx, b0 + y, s);
+        }
+      }
+      om += __shfl_sync(0xffffffffu, x[0], 31);
+      op += __shfl_sync(0xffffffffu, x[1], 31);
+      oc += __shfl_sync(0xffffffffu, x[2], 31);
+    }
+    nm += Tm;
+    np += Tp;
+    nf = Tc;
+    uint64_t *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    __threadfence();
+    __syncthreads();  // ws is rewritten by the next level
+    grid.sync();
   }
-  uint32_t base1 = offs[nf], base2 = offs[2 * nf];
-  if (c == kP2P) {
-    p2p[offs[nf + t] - base1] = e;
-    return;
+  if (bid == 0 && tid == 0) {
+    st->nm2l = nm;
+    st->np2p = np;
+    st->nf = nf;
+    st->iters = iter;
   }
-  uint32_t a = pair_sink(e), b = pair_src(e), s = pair_shift(e);
-  int2 ka = kids[a], kb = kids[b];
-  uint32_t a0 = a, na = 1, b0 = b, nb = 1;
-  if (c == kOpenA || c == kOpenAB) {
-    a0 = (uint32_t)ka.x;
-    na = (uint32_t)ka.y;
-  }
-  if (c == kOpenB || c == kOpenAB) {
-    b0 = (uint32_t)kb.x;
-    nb = (uint32_t)kb.y;
-  }
-  uint64_t *o = next + (offs[2 * nf + t] - base2);
-  for (uint32_t x = 0; x < na; ++x)
-    for (uint32_t y = 0; y < nb; ++y) *o++ = pack_pair(a0 + x, b0 + y, s);
 }
 
 // CSR bounds of the entries [lo, hi) of a list sorted by sink: beg[k] .. end[k].
@@ -253,7 +383,6 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
     e = (x);                        \
     if (e != cudaSuccess) return e; \
   } while (0)
-  const int T = 256;
   c.nm2l = c.np2p = 0;
   c.traverse_iters = 0;
   if (c.n == 0) return cudaSuccess;
@@ -274,51 +403,57 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   m.ncand = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 7);
   m.cand_cap = c.cand_cap;
   m.sample_mod = c.sample_mod ? c.sample_mod : 1u;
-  int64_t nf = 27;
-  TRY(ensure(c.front, 1024 * 8));
-  k_init_frontier<<<1, 32, 0, st>>>(P<uint64_t>(c.front));
-  note_launch();
-  size_t cap_m2l = c.m2l.cap / 8, cap_p2p = c.p2p.cap / 8;
-  uint64_t *d_tot = P<uint64_t>(c.d_small);
-  while (nf > 0) {
-    TRY(ensure(c.cls, nf));
-    TRY(ensure(c.counts, 3 * nf * sizeof(uint32_t)));
-    TRY(ensure(c.offs, 3 * nf * sizeof(uint32_t)));
-    k_mac_count<<<blocks_for(nf, T), T, 0, st>>>(P<uint64_t>(c.front), nf, P<uint4>(c.cell), P<int2>(c.kids), m,
-                                                 P<uint8_t>(c.cls), P<uint32_t>(c.counts));
+
+  int dev = 0, nsm = 0, per_sm = 0;
+  TRY(cudaGetDevice(&dev));
+  TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const bool net = m.mode == 1;
+  const void *kern = net ? (const void *)k_traverse<true> : (const void *)k_traverse<false>;
+  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, net ? k_traverse<true> : k_traverse<false>, kTT, 0));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const unsigned nb = (unsigned)(nsm * (per_sm < 4 ? per_sm : 4));
+  TRY(ensure(c.counts, (size_t)nb * 3 * sizeof(uint32_t)));
+  // capacities: the last call's sizes with head-room, at least a few per node
+  auto grow = [](uint64_t want) { return want + want / 4 + 1024; };
+  if (c.cap_front < (uint64_t)(4 * c.nnodes + 1024)) c.cap_front = 4 * c.nnodes + 1024;
+  if (c.cap_m2l < (uint64_t)(8 * c.nnodes + 1024)) c.cap_m2l = 8 * c.nnodes + 1024;
+  if (c.cap_p2p < (uint64_t)(16 * c.nleaves + 1024)) c.cap_p2p = 16 * c.nleaves + 1024;
+  TravState *dst = reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    TRY(ensure(c.front, c.cap_front * 8));
+    TRY(ensure(c.front_next, c.cap_front * 8));
+    TRY(ensure(c.cls, c.cap_front));
+    TRY(ensure(c.m2l, c.cap_m2l * 8));
+    TRY(ensure(c.p2p, c.cap_p2p * 8));
+    TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), st));
+    uint64_t *fa = P<uint64_t>(c.front), *fb = P<uint64_t>(c.front_next);
+    uint8_t *cl = P<uint8_t>(c.cls);
+    uint64_t *ml = P<uint64_t>(c.m2l), *pl = P<uint64_t>(c.p2p);
+    unsigned long long capF = c.cap_front, capM = c.cap_m2l, capP = c.cap_p2p;
+    uint32_t *bt = P<uint32_t>(c.counts);
+    int max_iters = 2 * kDepth + 6;
+    void *args[] = {(void *)&c.cell.p, (void *)&c.kids.p, (void *)&m, (void *)&fa, (void *)&fb, (void *)&capF,
+                    (void *)&cl, (void *)&ml, (void *)&capM, (void *)&pl, (void *)&capP, (void *)&bt,
+                    (void *)&dst, (void *)&max_iters};
+    TRY(cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kTT), args, 0, st));
     note_launch();
-    TRY(scan_u32(P<uint32_t>(c.counts), P<uint32_t>(c.offs), d_tot, 3 * nf, c.tmp, st));
-    TRY(cudaMemcpyAsync(c.h_pinned, P<uint32_t>(c.offs) + nf, 4, cudaMemcpyDeviceToHost, st));
-    TRY(cudaMemcpyAsync(reinterpret_cast<uint32_t *>(c.h_pinned) + 1, P<uint32_t>(c.offs) + 2 * nf, 4,
-                        cudaMemcpyDeviceToHost, st));
-    TRY(cudaMemcpyAsync(c.h_pinned + 1, d_tot, 8, cudaMemcpyDeviceToHost, st));
+    TravState hs;
+    TRY(cudaMemcpyAsync(c.h_pinned, dst, sizeof(TravState), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    uint64_t s0 = reinterpret_cast<uint32_t *>(c.h_pinned)[0];
-    uint64_t s01 = reinterpret_cast<uint32_t *>(c.h_pinned)[1];
-    uint64_t tot = c.h_pinned[1];
-    if (tot >= 0xffffffffull) return cudaErrorInvalidValue;
-    int64_t add_m2l = (int64_t)s0, add_p2p = (int64_t)(s01 - s0), nch = (int64_t)(tot - s01);
-    if ((size_t)(c.nm2l + add_m2l) > cap_m2l) {
-      TRY(ensure_keep(c.m2l, (c.nm2l + add_m2l) * 8 * 2, c.nm2l * 8, st));
-      cap_m2l = c.m2l.cap / 8;
+    std::memcpy(&hs, c.h_pinned, sizeof(TravState));
+    if (!hs.overflow) {
+      if (hs.nf != 0) return cudaErrorInvalidValue;  // more levels than any octree can have
+      c.nm2l = (int64_t)hs.nm2l;
+      c.np2p = (int64_t)hs.np2p;
+      c.traverse_iters = hs.iters;
+      return cudaSuccess;
     }
-    if ((size_t)(c.np2p + add_p2p) > cap_p2p) {
-      TRY(ensure_keep(c.p2p, (c.np2p + add_p2p) * 8 * 2, c.np2p * 8, st));
-      cap_p2p = c.p2p.cap / 8;
-    }
-    TRY(ensure(c.front_next, (nch > 0 ? nch : 1) * 8));
-    k_mac_emit<<<blocks_for(nf, T), T, 0, st>>>(P<uint64_t>(c.front), nf, P<uint8_t>(c.cls), P<uint32_t>(c.offs),
-                                                P<int2>(c.kids), P<uint64_t>(c.m2l) + c.nm2l,
-                                                P<uint64_t>(c.p2p) + c.np2p, P<uint64_t>(c.front_next));
-    note_launch();
-    TRY(cudaGetLastError());
-    c.nm2l += add_m2l;
-    c.np2p += add_p2p;
-    std::swap(c.front, c.front_next);
-    nf = nch;
-    ++c.traverse_iters;
+    // grow every list (the walk stopped at the first overflow, so the sizes seen are lower bounds)
+    c.cap_front = grow(c.cap_front * 2);
+    c.cap_m2l = grow(c.cap_m2l * 2);
+    c.cap_p2p = grow(c.cap_p2p * 2);
   }
-  return cudaSuccess;
+  return cudaErrorInvalidValue;
 #undef TRY
 }
 
