@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.3)
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
+    ap.add_argument("--m2l-tables", type=int, default=0, help="1: same-level M2L operators from the (level, offset) table")
     ap.add_argument("--mac", default="geometric", choices=["geometric", "learned"])
     ap.add_argument("--mlp-weights", default=os.path.join(ROOT, "paper_2006_14952_gb300", "weights", "mac_weights.bin"))
     ap.add_argument("--accuracy-sinks", type=int, default=20000)
@@ -236,7 +237,7 @@ def main():
     mac_kw = dict(mac_mode=1) if learned else {}
     wts = np.fromfile(args.mlp_weights, dtype=np.uint16) if learned else None
     s = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                    order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=1, **mac_kw)
+                    order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, m2l_tables=args.m2l_tables, profile=1, **mac_kw)
     if learned:
         s.load_mlp(wts)
     dpos = torch.from_numpy(pos).to(dev)
@@ -254,7 +255,7 @@ def main():
         step()
     torch.cuda.synchronize()
     sc = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, profile=3, **mac_kw)
+                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, m2l_tables=args.m2l_tables, profile=3, **mac_kw)
     if learned:
         sc.load_mlp(wts)
     sc.build_tree(dpos, dmass)
@@ -307,7 +308,7 @@ def main():
     pin_mass = torch.from_numpy(mass).pin_memory()
     pin_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
     s2 = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, **mac_kw)
+                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, m2l_tables=args.m2l_tables, **mac_kw)
     if learned:
         s2.load_mlp(wts)
     for _ in range(2):
@@ -359,7 +360,9 @@ def main():
             "config": {"workload": workload_desc(cfg),
                        "path": ("learned acceptance (network, safety bound theta), " if learned else
                                 "geometric acceptance, ") + ("3xTF32 tensor-core M2L" if args.m2l_precision == 1
-                                                             else "FP32 CUDA-core M2L"),
+                                                             else "FP32 CUDA-core M2L" +
+                                                             (" with (level, offset) operator tables"
+                                                              if args.m2l_tables else "")),
                        "theta": args.theta, "order": args.order, "leaf_max": cfg.leaf_max,
                        "transition_rule": 1, "size_rule": 1, "l2": "flushed (512 MB write) before every step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
@@ -372,7 +375,8 @@ def main():
             "breakdown_ms": {k[2:]: round(v, 4) for k, v in mean.items()},
             "counts": {"nodes": st["nnodes"], "leaves": st["nleaves"], "levels": st["nlevels"],
                        "traverse_iters": st["traverse_iters"], "p2p_leaf_pairs": st["np2p"],
-                       "m2l_pairs": st["nm2l"], "p2p_pairs_evaluated": st["p2p_particle_pairs"],
+                       "m2l_pairs": st["nm2l"], "m2l_pairs_table": st["nm2l_table"],
+                       "p2p_pairs_evaluated": st["p2p_particle_pairs"],
                        "p2p_pairs_useful": st["p2p_useful_pairs"]},
             "step_ms": [round(x, 4) for x in step_ms],
         }

@@ -74,6 +74,14 @@ typedef struct {
                           tensor cores with FP32 accumulation in tensor memory (orders 1..6) */
   int profile;         /* bit 0: record per-phase CUDA-event timings; bit 1: count P2P
                           particle pairs (extra work; for statistics runs only) */
+  int m2l_tables;      /* 1 = same-level M2L pairs whose integer cell offset o satisfies
+                          |o_d| <= 2 floor(1/theta) + 1 read their translation operator
+                          T_c = D_c(-o h) h^(|c|+1) (Eq. m2l with the truncated D of Sec. 2.2)
+                          from a per-(level, offset) table built once in FP64 on the device;
+                          other pairs evaluate D per pair.  0 (default) = every pair
+                          evaluates D: on the 2M-particle clustered set the 224-byte table
+                          row per pair costs more than evaluating D (7.1 vs 6.6 ms of M2L).
+                          Used by m2l_precision 0 only. */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */
@@ -87,6 +95,7 @@ typedef struct {
   int64_t launches;           /* kernels launched by this library in this process so far */
   /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
+  int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
 } hfmm_stats;
 
 typedef struct hfmm_ctx hfmm_ctx;

@@ -42,6 +42,7 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.m2l_precision == 1 && !m2l_tc_supported(p.order))
     return why = "m2l_precision 1 (3xTF32 tensor cores) supports orders 1..6", false;
   if (p.profile < 0 || p.profile > 3) return why = "profile must be 0..3", false;
+  if (p.m2l_tables != 0 && p.m2l_tables != 1) return why = "m2l_tables must be 0 or 1", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
@@ -106,6 +107,7 @@ void hfmm_default_params(hfmm_params *o) {
   o->size_rule = 1;
   o->m2l_precision = 0;
   o->profile = 0;
+  o->m2l_tables = 0;
 }
 
 int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
@@ -134,7 +136,9 @@ int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
   c.theta2 = params->theta * params->theta;
   c.p = params->order;
   c.nc = ncoef(c.p);
+  c.ldm = (c.nc + 3) & ~3;
   c.fit = fit_pair_factor(c.rs, c.rc);
+  c.tab_k = m2l_table_extent(*params);
   cudaError_t e = cudaMallocHost(&c.h_pinned, 256);
   if (e == cudaSuccess) e = ensure(c.d_small, 256);
   for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&c.ev[i]);
@@ -189,10 +193,12 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (c.n == 0) return HFMM_OK;
   cudaStream_t st = S(stream);
   cudaError_t e;
-  size_t eb = (size_t)c.nnodes * c.nc * sizeof(float);
+  size_t eb = (size_t)c.nnodes * c.ldm * sizeof(float);
   if ((e = ensure(c.M, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc M");
   if ((e = ensure(c.L, eb)) != cudaSuccess) return cuda_fail(c, e, "alloc L");
   if ((e = cudaMemsetAsync(c.L.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset L");
+  // the padding of each multipole row is read (as part of a float4) but never used: keep it finite
+  if (c.ldm != c.nc && (e = cudaMemsetAsync(c.M.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset M");
   bool prof = (c.prm.profile & 1) != 0;
   if ((c.prm.profile & 2) && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "memset counter");
@@ -266,6 +272,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->np2p = c.np2p;
   o->nm2l = c.nm2l;
   o->p2p_particle_pairs = c.p2p_particle_pairs;
+  o->nm2l_table = c.nm2l_table;
   o->p2p_useful_pairs = -1;
   if ((c.prm.profile & 2) && c.n > 0) {
     unsigned long long u = 0;
@@ -316,8 +323,11 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
   switch (what) {
     case HFMM_EXPORT_KEYS: e = cudaMemcpy(buf, c.key.p, need, cudaMemcpyDeviceToHost); break;
     case HFMM_EXPORT_PERM: e = cudaMemcpy(buf, c.idx.p, need, cudaMemcpyDeviceToHost); break;
-    case HFMM_EXPORT_MULTIPOLES: e = cudaMemcpy(buf, c.M.p, need, cudaMemcpyDeviceToHost); break;
-    case HFMM_EXPORT_LOCALS: e = cudaMemcpy(buf, c.L.p, need, cudaMemcpyDeviceToHost); break;
+    case HFMM_EXPORT_MULTIPOLES:
+    case HFMM_EXPORT_LOCALS:  // rows of nc values out of the padded device rows
+      e = cudaMemcpy2D(buf, c.nc * sizeof(float), (what == HFMM_EXPORT_LOCALS ? c.L : c.M).p, c.ldm * sizeof(float),
+                       c.nc * sizeof(float), c.nnodes, cudaMemcpyDeviceToHost);
+      break;
     case HFMM_EXPORT_NODES: {
       std::vector<uint4> cell(c.nnodes);
       std::vector<uint2> range(c.nnodes);

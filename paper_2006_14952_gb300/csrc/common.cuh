@@ -43,7 +43,10 @@ __host__ __device__ inline void mdecode(int c, int &nx, int &ny, int &nz) {
 // Packed (sink node, source node, shift, order) entry:
 //   bits 61..63  expansion order - 1 of an M2L entry (0 for P2P and frontier entries)
 //   bits 34..60  sink node (27 bits)
-//   bits  5..33  source node (29 bits)
+//   bit  33      M2L entries: 1 = the operator is evaluated per pair, 0 = it is read
+//                from the (level, offset) table (sorting on bits 33.. puts a sink's
+//                table pairs first)
+//   bits  5..32  source node (28 bits)
 //   bits  0..4   periodic shift index 0..26
 constexpr int kSinkShift = 34;
 constexpr int kSinkBits = 27;
@@ -52,7 +55,9 @@ __host__ __device__ inline uint64_t pack_pair(uint32_t sink, uint32_t src, uint3
   return ((uint64_t)order_m1 << kOrderShift) | ((uint64_t)sink << kSinkShift) | ((uint64_t)src << 5) | (uint64_t)s;
 }
 __host__ __device__ inline uint32_t pair_sink(uint64_t e) { return (uint32_t)((e >> kSinkShift) & 0x7ffffffull); }
-__host__ __device__ inline uint32_t pair_src(uint64_t e) { return (uint32_t)((e >> 5) & 0x1fffffffull); }
+__host__ __device__ inline uint32_t pair_src(uint64_t e) { return (uint32_t)((e >> 5) & 0xfffffffull); }
+constexpr int kGenericBit = 33;
+__host__ __device__ inline bool pair_generic(uint64_t e) { return (e >> kGenericBit) & 1ull; }
 __host__ __device__ inline uint32_t pair_shift(uint64_t e) { return (uint32_t)(e & 31ull); }
 __host__ __device__ inline uint32_t pair_order(uint64_t e) { return (uint32_t)(e >> kOrderShift) + 1u; }
 __host__ __device__ inline uint64_t with_order(uint64_t e, uint32_t order) {
@@ -128,6 +133,7 @@ struct Ctx {
   double rc2h = 0, theta2 = 0;  // MAC thresholds (half units squared; theta^2)
   PairFit fit{};
   int p = 4, nc = 35;
+  int ldm = 36;  // row stride of the expansion arrays: nc rounded up to a multiple of 4 (float4 rows)
   std::string err;
 
   // particles
@@ -155,6 +161,12 @@ struct Ctx {
   int traverse_iters = 0;
   uint64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;  // traversal capacities (entries)
   DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
+  DBuf m2l_mid;  // u32 [nnodes]: [beg, mid) table pairs, [mid, end) per-pair operator
+
+  // M2L operator table: T[level][ox][oy][oz][c], |o_d| <= tab_k, c < ncoef(p) padded to tab_ld
+  DBuf tab;
+  int tab_k = 0, tab_ld = 0;
+  bool tab_ready = false;
 
   // expansions (scaled): M~ = M / h^|m|, L~ = L h^(|n|+1)
   DBuf M, L;
@@ -178,7 +190,7 @@ struct Ctx {
   DBuf mlp_scratch;
 
   // stats
-  int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1;
+  int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1, nm2l_table = -1;
   cudaEvent_t ev[16] = {};
   bool ev_ready = false;
   float t_keys_sort = -1, t_tree = -1, t_upward = -1, t_traverse = -1, t_lists = -1, t_m2l = -1, t_l2l = -1,
@@ -195,6 +207,12 @@ cudaError_t upward(Ctx &c, cudaStream_t st);
 cudaError_t m2l_pass(Ctx &c, int q, cudaStream_t st);
 // All M2L entries: one pass per order present in the list.
 cudaError_t m2l_all(Ctx &c, cudaStream_t st);
+// Table half-extent K for opening angle theta (0: no table).
+int m2l_table_extent(const hfmm_params &p);
+// Build the (level, offset) operator table once per context (FP64, rounded to FP32).
+cudaError_t m2l_table_build(Ctx &c, cudaStream_t st);
+// M2L of the table pairs [beg, mid) of order q; adds into L.
+cudaError_t m2l_pass_table(Ctx &c, int q, cudaStream_t st);
 // Split-precision (3xTF32) M2L on tcgen05 tensor cores; orders 1..6.  The
 // kernel's status word (d_small[6]) is 1 after a timed-out wait.
 bool m2l_tc_supported(int p);

@@ -111,11 +111,11 @@ cudaError_t upward_p(Ctx &c, cudaStream_t st) {
   const int T = 128;
   const float box = (float)c.prm.box;
   k_p2m<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell), hfmm::P<uint2>(c.range),
-                                                   hfmm::P<float4>(c.pm4), box, c.nc, hfmm::P<float>(c.M));
+                                                   hfmm::P<float4>(c.pm4), box, c.ldm, hfmm::P<float>(c.M));
   note_launch();
   for (int l = c.nlevels - 2; l >= 0; --l) {
     int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    k_m2m<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.nc, hfmm::P<float>(c.M));
+    k_m2m<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm, hfmm::P<float>(c.M));
     note_launch();
   }
   return cudaGetLastError();
@@ -126,12 +126,12 @@ cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st) {
   const int T = 128;
   for (int l = 0; l + 1 < c.nlevels; ++l) {
     int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    k_l2l<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.nc, hfmm::P<float>(c.L));
+    k_l2l<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm, hfmm::P<float>(c.L));
     note_launch();
   }
   k_l2p<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell),
                                                    hfmm::P<uint2>(c.range), hfmm::P<float4>(c.pm4), hfmm::P<uint32_t>(c.idx), c.n,
-                                                   (float)c.prm.box, (float)c.prm.G, c.nc, hfmm::P<float>(c.L), acc);
+                                                   (float)c.prm.box, (float)c.prm.G, c.ldm, hfmm::P<float>(c.L), acc);
   note_launch();
   return cudaGetLastError();
 }

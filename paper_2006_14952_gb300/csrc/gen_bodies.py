@@ -20,6 +20,8 @@ M2MBody<P>:  out[m] += sum_{n <= m} (x/H)^n / n! 2^-(|m|-|n|) in[m-n] for one
 L2LBody<P>:  out[n] = 2^-(|n|+1) sum_{|m| <= P-|n|} (x/H)^m / m! Lp[m+n] for one
              child, x/H = (sx, sy, sz) / 4 (Eq. l2l, scaled L~ = L h^(|n|+1)).
 L2PBody<P>:  a_d += sum_{|n| <= P-1} Lk[n+e_d] u^n / n! (Eq. l2p gradient).
+M2LTabBody<P, G, g>: acc[n / G] += sum_m T[n+m] Mp[m] for one pair whose scaled
+             operator T_c = D_c h^(|c|+1) comes from the (level, offset) table.
 TCStore<P>:  tensor-core M2L operands for one pair: D'_c = u^(|c|+1) D^_c(R^) and
              M'_m = s (v/u)^|m| M~_m, each split x = hi + lo (hi = TF32 rounding),
              stored at row c (or m), column k of K-major 128-byte-swizzled tiles
@@ -250,6 +252,36 @@ def gen_passes(P):
     return "\n\n".join(out)
 
 
+def gen_tab_body(P, G, g):
+    """M2LTabBody<P, G, g>: acc[n / G] += sum_m T[n + m] Mp[m] for the outputs n = g mod G,
+    with T one row of the (level, offset) operator table (16-byte aligned, read as float4)."""
+    smem = P in MP_IN_SMEM
+    mp = (lambda e: f"Mp[{e} * 32]") if smem else (lambda e: f"Mp[{e}]")
+    sig_mp = "const float *__restrict__ Mp" if smem else f"const float (&Mp)[{ncoef(P)}]"
+    L = [f"template <> struct M2LTabBody<{P}, {G}, {g}> {{",
+         f"  static __device__ __forceinline__ void run(const float4 *__restrict__ T4, {sig_mp},"
+         f" float (&acc)[{(ncoef(P) + G - 1) // G}]) {{"]
+    ms = multi(P)
+    outs = [n for n in ms if idx(n) % G == g]
+    need_c = [c for c in ms if any(all(n[d] <= c[d] for d in range(3)) for n in outs)]
+    loaded = set()
+    for c in need_c:
+        ci = idx(c)
+        q = ci // 4
+        if q not in loaded:
+            L.append(f"    const float4 q{q} = __ldg(T4 + {q});")
+            loaded.add(q)
+        comp = "xyzw"[ci % 4]
+        for n in outs:
+            if all(n[d] <= c[d] for d in range(3)):
+                m = (c[0] - n[0], c[1] - n[1], c[2] - n[2])
+                a = idx(n) // G
+                L.append(f"    acc[{a}] = fmaf(q{q}.{comp}, {mp(idx(m))}, acc[{a}]);")
+    L.append("  }")
+    L.append("};")
+    return "\n".join(L)
+
+
 def gen_tc(P):
     NC = ncoef(P)
     ms = multi(P)
@@ -307,6 +339,7 @@ def gen_tc(P):
 def main(out):
     parts = ["// Generated by gen_bodies.py: do not edit.", "#pragma once", "",
              "template <int P, int G, int g> struct M2LBody;", "template <int P> struct M2LLoad;",
+             "template <int P, int G, int g> struct M2LTabBody;",
              "template <int P> struct P2MBody;", "template <int P> struct M2MBody;", "template <int P> struct L2LBody;",
              "template <int P> struct L2PBody;", "template <int P> struct TCStore;", "",
              "__device__ __forceinline__ float tf32_round(float x) {",
@@ -319,20 +352,24 @@ def main(out):
         for g in range(G):
             parts.append(gen_body(P, G, g))
             parts.append("")
+            parts.append(gen_tab_body(P, G, g))
+            parts.append("")
     for P in range(1, 9):
         NC = ncoef(P)
         parts.append(f"template <> struct M2LLoad<{P}> {{")
-        parts.append(f"  // dst[c * S] = Mb[c] * v^|c|")
+        parts.append(f"  // dst[c * S] = Mb[c] * v^|c|; Mb is a 16-byte aligned row (float4 loads)")
         parts.append(f"  template <int S, class T> static __device__ __forceinline__ void run(const float *__restrict__ Mb,"
                      f" float v, T &dst) {{")
-        parts.append("    float vq = 1.f;")
-        c = 0
-        for k in range(P + 1):
-            if k:
-                parts.append("    vq *= v;")
-            for _ in range((k + 1) * (k + 2) // 2):
-                parts.append(f"    dst[{c} * S] = __ldg(Mb + {c}) * vq;")
-                c += 1
+        parts.append("    const float4 *M4 = reinterpret_cast<const float4 *>(Mb);")
+        parts.append("    const float v1 = v;")
+        for k in range(2, P + 1):
+            parts.append(f"    const float v{k} = v{k - 1} * v;")
+        deg = [sum(a) for a in multi(P)]
+        for j in range((NC + 3) // 4):
+            parts.append(f"    const float4 q{j} = __ldg(M4 + {j});")
+        for c in range(NC):
+            comp = "q%d.%s" % (c // 4, "xyzw"[c % 4])
+            parts.append(f"    dst[{c} * S] = {comp};" if deg[c] == 0 else f"    dst[{c} * S] = {comp} * v{deg[c]};")
         parts.append("  }")
         parts.append("};")
         parts.append("")

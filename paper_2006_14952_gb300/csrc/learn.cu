@@ -185,7 +185,7 @@ cudaError_t collect_pairs(Ctx &c, int64_t max_pairs, uint32_t sample_mod, float 
   c.cand_cap = (uint64_t)max_pairs;
   c.sample_mod = sample_mod ? sample_mod : 1u;
   if ((e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 7, 0, 8, st)) != cudaSuccess) return e;
-  size_t eb = (size_t)c.nnodes * c.nc * sizeof(float);
+  size_t eb = (size_t)c.nnodes * c.ldm * sizeof(float);
   if ((e = ensure(c.M, eb)) != cudaSuccess) return e;
   if ((e = upward(c, st)) != cudaSuccess) return e;
   c.collect = true;
@@ -202,7 +202,7 @@ cudaError_t collect_pairs(Ctx &c, int64_t max_pairs, uint32_t sample_mod, float 
   if (nc == 0) return cudaSuccess;
   const double hu = c.prm.box / (double)kHalfBox;
   k_pair_errors<<<152 * 8, kLT, 0, st>>>(P<uint64_t>(c.cand), nc, P<uint4>(c.cell), P<uint2>(c.range),
-                                         P<double>(c.xs), P<float4>(c.pm4), c.n, P<float>(c.M), c.nc, c.prm.box,
+                                         P<double>(c.xs), P<float4>(c.pm4), c.n, P<float>(c.M), c.ldm, c.prm.box,
                                          (float)c.rs, (float)(hu / c.rs), (float)(hu / c.rc), (float)c.prm.G, feat,
                                          err);
   note_launch();

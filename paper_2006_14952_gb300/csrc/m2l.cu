@@ -131,9 +131,10 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_m2l<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_m2l<P, G><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_beg),
+  // the entries [mid, end) of each sink: pairs outside the operator table
+  k_m2l<P, G><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_mid),
                                     hfmm::P<uint32_t>(c.m2l_end), hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M),
-                                    hfmm::P<float>(c.L), c.nc, inv_rs);
+                                    hfmm::P<float>(c.L), c.ldm, inv_rs);
   note_launch();
   return cudaGetLastError();
 }

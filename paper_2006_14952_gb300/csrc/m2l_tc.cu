@@ -287,7 +287,7 @@ cudaError_t launch_tc(Ctx &c, cudaStream_t st) {
   const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
   k_m2l_tc<P><<<nsm > 0 ? nsm : 152, kThreads, smem, st>>>(
       c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_beg), hfmm::P<uint32_t>(c.m2l_end),
-      hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.nc, inv_rs, ctr, status);
+      hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.ldm, inv_rs, ctr, status);
   note_launch();
   return cudaGetLastError();
 }

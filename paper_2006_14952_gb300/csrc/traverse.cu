@@ -38,6 +38,7 @@ struct Mac {
   int rule, size_rule;
   int mode;   // 0 geometric, 1 learned, 2 collect
   int order;  // p (geometric M2L order, and the largest learned order)
+  int tab_k;  // operator-table half extent (0: no table)
   // learned / collect
   const __nv_bfloat16 *w;
   const float *M;
@@ -97,6 +98,16 @@ struct Item {
   uint8_t cls;
   uint32_t nm, np, nch;
 };
+
+// An M2L pair outside the operator table: cells of different levels, or a
+// cell offset beyond the table's extent in some axis.
+__device__ __forceinline__ bool table_miss(uint4 ca, uint4 cb, uint32_t s, int k) {
+  if (k == 0 || ca.w != cb.w) return true;
+  int64_t dd[3];
+  half_delta(ca, cb, s, dd);
+  const int64_t lim = 2 * half_width(ca.w) * k;  // k cell sides
+  return dd[0] > lim || dd[0] < -lim || dd[1] > lim || dd[1] < -lim || dd[2] > lim || dd[2] < -lim;
+}
 
 template <bool kNet>
 __device__ __forceinline__ Item mac_item(const uint64_t *__restrict__ f, int64_t t, bool valid,
@@ -166,7 +177,8 @@ __device__ __forceinline__ Item mac_item(const uint64_t *__restrict__ f, int64_t
     }
   }
   Item it;
-  it.cls = (uint8_t)(c | (order << 3));
+  const uint32_t miss = (c == kM2L && table_miss(ca, cb, s, m.tab_k)) ? 1u : 0u;
+  it.cls = (uint8_t)(c | (order << 3) | (miss << 7));
   it.nm = c == kM2L;
   it.np = c == kP2P;
   it.nch = c == kOpenA ? (uint32_t)ka.y : c == kOpenB ? (uint32_t)kb.y : c == kOpenAB ? (uint32_t)(ka.y * kb.y) : 0u;
@@ -300,7 +312,7 @@ __global__ void __launch_bounds__(kTT, kNet ? 2 : 4) k_traverse(const uint4 *__r
         }
       if (valid) {
         const uint8_t c = cc & 7;
-        if (c == kM2L) m2l[om + x[0] - v[0]] = with_order(e, cc >> 3);
+        if (c == kM2L) m2l[om + x[0] - v[0]] = with_order(e, (cc >> 3) & 15) | ((uint64_t)(cc >> 7) << kGenericBit);
         if (c == kP2P) p2p[op + x[1] - v[1]] = e;
         if (c == kOpenA || c == kOpenB || c == kOpenAB) {
           const uint32_t a = pair_sink(e), b = pair_src(e), s = pair_shift(e);
@@ -340,14 +352,24 @@ __global__ void __launch_bounds__(kTT, kNet ? 2 : 4) k_traverse(const uint4 *__r
   }
 }
 
-// CSR bounds of the entries [lo, hi) of a list sorted by sink: beg[k] .. end[k].
+// CSR bounds of the entries [lo, hi) of a list sorted by (sink, generic bit):
+// beg[k] .. end[k]; with mid != null also mid[k], the first entry of sink k
+// whose operator is evaluated per pair (end[k] when there is none).
 __global__ void k_list_bounds(const uint64_t *__restrict__ lst, int64_t lo, int64_t hi, uint32_t *__restrict__ beg,
-                              uint32_t *__restrict__ end) {
+                              uint32_t *__restrict__ end, uint32_t *__restrict__ mid) {
   int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= hi) return;
-  uint32_t s = pair_sink(lst[t]);
-  if (t == lo || pair_sink(lst[t - 1]) != s) beg[s] = (uint32_t)t;
-  if (t == hi - 1 || pair_sink(lst[t + 1]) != s) end[s] = (uint32_t)(t + 1);
+  const uint64_t e = lst[t];
+  const uint32_t s = pair_sink(e);
+  const bool first = t == lo || pair_sink(lst[t - 1]) != s;
+  const bool last = t == hi - 1 || pair_sink(lst[t + 1]) != s;
+  if (first) beg[s] = (uint32_t)t;
+  if (last) end[s] = (uint32_t)(t + 1);
+  if (mid) {
+    const bool g = pair_generic(e);
+    if (g && (first || !pair_generic(lst[t - 1]))) mid[s] = (uint32_t)t;
+    if (!g && last) mid[s] = (uint32_t)(t + 1);
+  }
 }
 
 // first[q] = index of the first entry with order >= q (q = 0..9) in a list sorted by (order, sink)
@@ -374,6 +396,13 @@ __global__ void k_pairs_in_list(const uint64_t *__restrict__ lst, int64_t n, con
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
 }
 
+__global__ void k_count_table(const uint64_t *__restrict__ lst, int64_t n, unsigned long long *__restrict__ acc) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = (t < n && !pair_generic(lst[t])) ? 1ull : 0ull;
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
 }  // namespace
 
 cudaError_t traverse(Ctx &c, cudaStream_t st) {
@@ -393,10 +422,11 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   m.size_rule = c.prm.size_rule;
   m.mode = c.collect ? 2 : c.prm.mac_mode;
   m.order = c.p;
+  m.tab_k = (c.prm.m2l_precision == 0 && c.prm.m2l_tables) ? c.tab_k : 0;
   m.w = static_cast<const __nv_bfloat16 *>(c.mlp_w.p);
   m.M = P<float>(c.M);
   m.range = P<uint2>(c.range);
-  m.ldm = c.nc;
+  m.ldm = c.ldm;
   m.inv_rs_h = (float)(c.prm.box / (double)kHalfBox / c.rs);
   m.inv_rc_h = (float)(c.prm.box / (double)kHalfBox / c.rc);
   m.cand = P<uint64_t>(c.cand);
@@ -472,6 +502,8 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   TRY(ensure(c.m2l_end, nn * 4));
   TRY(ensure(c.p2p_beg, nn * 4));
   TRY(ensure(c.p2p_end, nn * 4));
+  TRY(ensure(c.m2l_mid, nn * 4));
+  TRY(cudaMemsetAsync(c.m2l_mid.p, 0, nn * 4, st));
   TRY(cudaMemsetAsync(c.m2l_beg.p, 0, nn * 4, st));
   TRY(cudaMemsetAsync(c.m2l_end.p, 0, nn * 4, st));
   TRY(cudaMemsetAsync(c.p2p_beg.p, 0, nn * 4, st));
@@ -485,26 +517,38 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
     if (n == 0) continue;
     TRY(ensure(A, n * 8));
     bool alt = false;
-    // learned M2L entries carry their order in the top bits: group by (order, sink)
+    // learned M2L entries carry their order in the top bits: group by (order, sink);
+    // M2L entries are also ordered by the generic bit (table pairs first in each sink)
     const int hi_bit = (!which && c.prm.mac_mode == 1) ? 64 : kSinkShift + sink_bits;
-    TRY(radix_sort_u64(P<uint64_t>(L), nullptr, P<uint64_t>(A), nullptr, n, kSinkShift, hi_bit, &alt, c.tmp, st));
+    const int lo_bit = which ? kSinkShift : kGenericBit;
+    TRY(radix_sort_u64(P<uint64_t>(L), nullptr, P<uint64_t>(A), nullptr, n, lo_bit, hi_bit, &alt, c.tmp, st));
     if (alt) std::swap(L, A);
     if (which || c.prm.mac_mode != 1) {
       k_list_bounds<<<blocks_for(n, T), T, 0, st>>>(P<uint64_t>(L), 0, n, P<uint32_t>(which ? c.p2p_beg : c.m2l_beg),
-                                                    P<uint32_t>(which ? c.p2p_end : c.m2l_end));
+                                                    P<uint32_t>(which ? c.p2p_end : c.m2l_end),
+                                                    which ? nullptr : P<uint32_t>(c.m2l_mid));
       note_launch();
       TRY(cudaGetLastError());
     }
   }
   c.p2p_particle_pairs = -1;
-  if ((c.prm.profile & 2) && c.np2p > 0) {
-    TRY(cudaMemsetAsync(c.d_small.p, 0, 8, st));
-    k_pairs_in_list<<<blocks_for(c.np2p, T), T, 0, st>>>(P<uint64_t>(c.p2p), c.np2p, P<uint2>(c.range),
-                                                         reinterpret_cast<unsigned long long *>(c.d_small.p));
-    note_launch();
-    TRY(cudaMemcpyAsync(c.h_pinned, c.d_small.p, 8, cudaMemcpyDeviceToHost, st));
+  c.nm2l_table = -1;
+  if (c.prm.profile & 2) {
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c.d_small.p);
+    TRY(cudaMemsetAsync(cnt, 0, 16, st));
+    if (c.np2p > 0) {
+      k_pairs_in_list<<<blocks_for(c.np2p, T), T, 0, st>>>(P<uint64_t>(c.p2p), c.np2p, P<uint2>(c.range), cnt);
+      note_launch();
+    }
+    if (c.nm2l > 0) {
+      k_count_table<<<blocks_for(c.nm2l, T), T, 0, st>>>(P<uint64_t>(c.m2l), c.nm2l, cnt + 1);
+      note_launch();
+    }
+    TRY(cudaGetLastError());
+    TRY(cudaMemcpyAsync(c.h_pinned, c.d_small.p, 16, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     c.p2p_particle_pairs = (int64_t)c.h_pinned[0];
+    c.nm2l_table = (int64_t)c.h_pinned[1];
   }
   return cudaSuccess;
 #undef TRY
@@ -512,8 +556,17 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
 
 cudaError_t m2l_all(Ctx &c, cudaStream_t st) {
   if (c.nm2l == 0) return cudaSuccess;
+  const bool tab = c.prm.m2l_precision == 0 && c.prm.m2l_tables && c.tab_k > 0;
+  if (tab && !c.tab_ready) {
+    cudaError_t e = m2l_table_build(c, st);
+    if (e != cudaSuccess) return e;
+  }
   auto run = [&](int q) -> cudaError_t {
     if (c.prm.m2l_precision == 1 && m2l_tc_supported(q)) return m2l_pass_tc(c, q, st);
+    if (tab) {
+      cudaError_t e = m2l_pass_table(c, q, st);
+      if (e != cudaSuccess) return e;
+    }
     return m2l_pass(c, q, st);
   };
   if (c.prm.mac_mode != 1) return run(c.p);
@@ -532,8 +585,9 @@ cudaError_t m2l_all(Ctx &c, cudaStream_t st) {
     if (hi <= lo) continue;
     if ((e = cudaMemsetAsync(c.m2l_beg.p, 0, nn * 4, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c.m2l_end.p, 0, nn * 4, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c.m2l_mid.p, 0, nn * 4, st)) != cudaSuccess) return e;
     k_list_bounds<<<blocks_for(hi - lo, T), T, 0, st>>>(P<uint64_t>(c.m2l), lo, hi, P<uint32_t>(c.m2l_beg),
-                                                        P<uint32_t>(c.m2l_end));
+                                                        P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid));
     note_launch();
     if ((e = run(q)) != cudaSuccess) return e;
   }

@@ -36,7 +36,7 @@ class Params(C.Structure):
     _fields_ = [("box", C.c_double), ("pm_grid", C.c_int), ("rs_cells", C.c_double), ("rcut_rs", C.c_double),
                 ("G", C.c_double), ("theta", C.c_double), ("order", C.c_int), ("leaf_max", C.c_int),
                 ("mac_mode", C.c_int), ("transition_rule", C.c_int), ("size_rule", C.c_int),
-                ("m2l_precision", C.c_int), ("profile", C.c_int)]
+                ("m2l_precision", C.c_int), ("profile", C.c_int), ("m2l_tables", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -45,7 +45,7 @@ class Stats(C.Structure):
                 ("p2p_particle_pairs", C.c_int64), ("p2p_useful_pairs", C.c_int64), ("launches", C.c_int64),
                 ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
                 ("t_upward", C.c_float), ("t_traverse", C.c_float), ("t_lists", C.c_float), ("t_m2l", C.c_float),
-                ("t_l2l", C.c_float), ("t_p2p", C.c_float)]
+                ("t_l2l", C.c_float), ("t_p2p", C.c_float), ("nm2l_table", C.c_int64)]
 
 
 class HfmmError(RuntimeError):
