@@ -144,6 +144,36 @@ int hfmm_short_range_forces(hfmm_ctx *ctx, float *acc_soa, void *stream);
 int hfmm_short_range_forces_host(hfmm_ctx *ctx, const double *pos_soa, const float *mass, int64_t n,
                                  float *acc_soa, void *stream);
 
+/*
+ * Long-range accelerations of the force split (Sec. 2.2: 1/r = erfc(r/2r_s)/r +
+ * erf(r/2r_s)/r; the erf part on the PM mesh of the same section), ADDED to acc_soa
+ * (device float32 [3][n], input order) for the particles of the last
+ * hfmm_build_tree.  Mesh: pm_grid^3 points x_g = g L / pm_grid; cloud-in-cell
+ * assignment and interpolation; cuFFT; Green function 4 pi G exp(-k^2 r_s^2) / k^2
+ * divided by the squared CIC window; spectral gradient i k with the Nyquist plane
+ * of each component set to zero; k = 0 dropped.  The mass mesh is accumulated in
+ * 64-bit fixed point, so the result does not depend on the order of the atomic
+ * additions.  Library-owned mesh buffers (about 24 pm_grid^3 bytes) are kept
+ * between calls.  pm_grid must be in 2..1024.  Errors: HFMM_ERR_STATE before
+ * hfmm_build_tree, HFMM_ERR_ARG for a null acc_soa or a pm_grid outside 2..1024,
+ * HFMM_ERR_CUDA for a failed launch or transform.
+ */
+int hfmm_pm_long_range(hfmm_ctx *ctx, float *acc_soa, void *stream);
+
+/*
+ * One kick-drift-kick leapfrog step of length dt in a static periodic box
+ * (the synchronised global step of Sec. 4, without cosmological
+ * factors), for the particles and masses of the last hfmm_build_tree:
+ *   vel += acc dt/2;  pos += vel dt, wrapped into [0, L);  hfmm_build_tree(pos);
+ *   acc = short range + long range at the new positions;  vel += acc dt/2.
+ * pos_soa (device float64 [3][n]), vel_soa and acc_soa (device float32 [3][n])
+ * are the caller's and are updated in place; on entry acc_soa must hold the
+ * total acceleration at pos_soa (hfmm_short_range_forces then
+ * hfmm_pm_long_range, or the previous step).  The mass array given to
+ * hfmm_build_tree must stay valid.  Errors as for the calls it makes.
+ */
+int hfmm_step(hfmm_ctx *ctx, double *pos_soa, float *vel_soa, float *acc_soa, double dt, void *stream);
+
 /* Counters and timings of the last calls (synchronises the context's work). */
 int hfmm_get_stats(hfmm_ctx *ctx, hfmm_stats *out);
 

@@ -158,8 +158,10 @@ void hfmm_destroy(hfmm_ctx *h) {
   DBuf *bufs[] = {&c.key, &c.key_alt, &c.idx, &c.idx_alt, &c.xs, &c.pm4, &c.perm, &c.cell, &c.range, &c.kids,
                   &c.leaves, &c.bounds, &c.nkids, &c.koff, &c.front, &c.front_next, &c.cls, &c.counts, &c.offs,
                   &c.m2l, &c.m2l_alt, &c.p2p, &c.p2p_alt, &c.m2l_beg, &c.m2l_end, &c.p2p_beg, &c.p2p_end, &c.M,
-                  &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc};
+                  &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc, &c.m2l_mid, &c.tab,
+                  &c.mlp_w, &c.cand, &c.mlp_scratch};
   for (DBuf *b : bufs) release(*b);
+  pm_release(c);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
   for (int i = 0; i < 16; ++i)
     if (c.ev[i]) cudaEventDestroy(c.ev[i]);
@@ -177,6 +179,7 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
   c.have_tree = false;
   if (n < 0 || n > (int64_t)0x7fffffff) return fail(c, HFMM_ERR_ARG, "n must be in [0, 2^31)");
   if (n > 0 && (!pos || !mass)) return fail(c, HFMM_ERR_ARG, "null position or mass pointer");
+  c.mass_ref = mass;
   cudaError_t e = build_tree(c, pos, mass, n, S(stream));
   if (e == cudaErrorInvalidValue && c.nnodes >= ((int64_t)1 << kSinkBits))
     return fail(c, HFMM_ERR_CAPACITY, "more than 2^27 tree nodes");
@@ -228,6 +231,36 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (prof) cudaEventRecord(c.ev[8], st);
   if ((e = p2p_pass(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "p2p");
   if (prof) cudaEventRecord(c.ev[9], st);
+  return HFMM_OK;
+}
+
+int hfmm_pm_long_range(hfmm_ctx *h, float *acc, void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "pm_long_range before build_tree");
+  if (c.n > 0 && !acc) return fail(c, HFMM_ERR_ARG, "null acceleration pointer");
+  if (c.prm.pm_grid < 2 || c.prm.pm_grid > 1024) return fail(c, HFMM_ERR_ARG, "pm_grid must be in 2..1024");
+  cudaError_t e = pm_long_range(c, acc, S(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "pm_long_range");
+  return HFMM_OK;
+}
+
+int hfmm_step(hfmm_ctx *h, double *pos, float *vel, float *acc, double dt, void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "step before build_tree");
+  if (c.n > 0 && (!pos || !vel || !acc || !c.mass_ref)) return fail(c, HFMM_ERR_ARG, "null particle array");
+  if (!std::isfinite(dt)) return fail(c, HFMM_ERR_ARG, "dt must be finite");
+  cudaStream_t st = S(stream);
+  const int64_t n = c.n;
+  cudaError_t e;
+  if ((e = kick(vel, acc, n, 0.5 * dt, st)) != cudaSuccess) return cuda_fail(c, e, "kick");
+  if ((e = drift(pos, vel, n, dt, c.prm.box, st)) != cudaSuccess) return cuda_fail(c, e, "drift");
+  int rc = hfmm_build_tree(h, pos, c.mass_ref, n, stream);
+  if (rc != HFMM_OK) return rc;
+  if ((rc = hfmm_short_range_forces(h, acc, stream)) != HFMM_OK) return rc;
+  if ((rc = hfmm_pm_long_range(h, acc, stream)) != HFMM_OK) return rc;
+  if ((e = kick(vel, acc, n, 0.5 * dt, st)) != cudaSuccess) return cuda_fail(c, e, "kick");
   return HFMM_OK;
 }
 

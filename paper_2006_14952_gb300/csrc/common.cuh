@@ -189,6 +189,11 @@ struct Ctx {
   uint32_t sample_mod = 1;
   DBuf mlp_scratch;
 
+  // PM long range (cuFFT plans made on first use; -1 = none) and the step
+  DBuf pm_q, pm_rho, pm_mk, pm_ak, pm_a;
+  int pm_plan_r2c = -1, pm_plan_c2r = -1;
+  const float *mass_ref = nullptr;  // the mass array of the last build_tree
+
   // stats
   int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1, nm2l_table = -1;
   cudaEvent_t ev[16] = {};
@@ -219,6 +224,13 @@ bool m2l_tc_supported(int p);
 cudaError_t m2l_pass_tc(Ctx &c, int q, cudaStream_t st);
 // L2L top-down, then L2P writing the far-field accelerations in input order.
 cudaError_t downward(Ctx &c, float *acc, cudaStream_t st);
+// Long-range PM accelerations added to acc (input order); mesh buffers and
+// FFT plans are kept in the context (pm_release frees them).
+cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st);
+void pm_release(Ctx &c);
+// vel += h acc and pos += dt vel (wrapped), [3][n] arrays.
+cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t st);
+cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st);
 // Cut-off P2P, added to the accelerations written by downward().
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st);
 

@@ -1,0 +1,255 @@
+// Long-range (PM) accelerations of the force split of Sec. 2.2, and the
+// kick-drift-kick step (the synchronised global step of Sec. 4).
+//
+// The long-range pair potential erf(r / 2r_s) / r has the Fourier transform
+// 4 pi exp(-k^2 r_s^2) / k^2.  With the mass m_g assigned to the mesh points
+// x_g = g L / N_g by cloud-in-cell (CIC) weights:
+//   a(k) = i k G 4 pi exp(-k^2 r_s^2) / (k^2 W(k)^2) m(k) / L^3,
+//   W(k) = prod_d sinc^2(k_d L / 2N_g)   (the CIC window of the assignment and
+//                                         of the interpolation, divided out),
+// zero at k = 0 and on the Nyquist plane of each gradient component; the mesh
+// acceleration is the inverse transform (the Fourier series sums the modes, so
+// the unnormalised inverse FFT is the right scaling) and is interpolated back to
+// the particles with the same CIC weights.  Sign convention: a = G grad Phi,
+// Phi = sum_j m_j psi(x - x_j), as for the short-range pair force.
+//
+// The mass assignment accumulates 64-bit fixed-point integers (mass * weight *
+// 2^s, s chosen from N * max|m| so no sum can overflow), so the mesh, and with
+// it every acceleration, is the same on every run whatever order the atomics
+// land in.  Mesh transforms use cuFFT (FP32, one R2C and a batch of three C2R).
+#include <cufft.h>
+
+#include <cmath>
+
+#include "common.cuh"
+
+namespace hfmm {
+namespace {
+
+__global__ void k_mass_absmax(const float4 *__restrict__ pm4, int64_t n, unsigned *__restrict__ out) {
+  unsigned v = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v = max(v, __float_as_uint(fabsf(pm4[i].w)));  // non-negative floats order like their bit patterns
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
+}
+
+// Fixed-point scale 2^s with N * max|m| * 2^s <= 2^61.
+__device__ __forceinline__ double fixed_scale(const unsigned *mmax_bits, int64_t n) {
+  const double bound = (double)__uint_as_float(*mmax_bits) * (double)n;
+  if (!(bound > 0)) return 1.0;
+  int e;
+  frexp(bound, &e);  // bound < 2^e
+  return ldexp(1.0, 61 - e);
+}
+
+__device__ __forceinline__ void cic_setup(const double *__restrict__ xs, int64_t n, int64_t i, double to_mesh,
+                                          int ng, int (&i0)[3], double (&d)[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double u = xs[k * n + i] * to_mesh;  // wrapped positions: u in [0, ng]
+    double f = floor(u);
+    d[k] = u - f;
+    int c = (int)f;
+    if (c >= ng) c -= ng;
+    if (c < 0) c += ng;
+    i0[k] = c;
+  }
+}
+
+__global__ void k_deposit(const double *__restrict__ xs, const float4 *__restrict__ pm4, int64_t n, double to_mesh,
+                          int ng, const unsigned *__restrict__ mmax, unsigned long long *__restrict__ q) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double S = fixed_scale(mmax, n);
+  int i0[3];
+  double d[3];
+  cic_setup(xs, n, i, to_mesh, ng, i0, d);
+  const double m = (double)pm4[i].w * S;
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox) {
+    const double wx = ox ? d[0] : 1.0 - d[0];
+    const int gx = i0[0] + ox == ng ? 0 : i0[0] + ox;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const double wy = oy ? d[1] : 1.0 - d[1];
+      const int gy = i0[1] + oy == ng ? 0 : i0[1] + oy;
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const double wz = oz ? d[2] : 1.0 - d[2];
+        const int gz = i0[2] + oz == ng ? 0 : i0[2] + oz;
+        const long long v = __double2ll_rn(m * wx * wy * wz);
+        atomicAdd(q + ((int64_t)gx * ng + gy) * ng + gz, (unsigned long long)v);
+      }
+    }
+  }
+}
+
+__global__ void k_fixed_to_real(const unsigned long long *__restrict__ q, int64_t cells, const unsigned *mmax,
+                                int64_t n, float *__restrict__ rho) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cells) return;
+  rho[g] = (float)((double)(long long)q[g] / fixed_scale(mmax, n));
+}
+
+__device__ __forceinline__ float sincf_(float x) { return fabsf(x) < 1e-4f ? 1.f - x * x / 6.f : sinf(x) / x; }
+
+// m(k) -> the three gradient components i k_d G(k) m(k) / L^3 (R2C layout [ng][ng][ng/2+1]).
+__global__ void k_green(const cufftComplex *__restrict__ mk, int ng, float box, float rs, float G,
+                        cufftComplex *__restrict__ ak) {
+  const int nz = ng / 2 + 1;
+  const int64_t total = (int64_t)ng * ng * nz;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int iz = (int)(t % nz), iy = (int)((t / nz) % ng), ix = (int)(t / ((int64_t)nz * ng));
+  const float kf = 2.f * 3.14159265358979f / box;
+  const float kx = kf * (float)(ix <= ng / 2 ? ix : ix - ng);
+  const float ky = kf * (float)(iy <= ng / 2 ? iy : iy - ng);
+  const float kz = kf * (float)iz;
+  const float k2 = kx * kx + ky * ky + kz * kz;
+  float g = 0.f;
+  if (k2 > 0.f) {
+    const float hh = 0.5f * box / (float)ng;
+    const float w = sincf_(kx * hh) * sincf_(ky * hh) * sincf_(kz * hh);
+    const float w2 = w * w;  // W(k) = (product of sincs)^2, divided out twice
+    g = 4.f * 3.14159265358979f * G * expf(-k2 * rs * rs) / (k2 * w2 * w2) / (box * box * box);
+  }
+  const bool even = (ng & 1) == 0;
+  const float kd[3] = {(even && ix == ng / 2) ? 0.f : kx, (even && iy == ng / 2) ? 0.f : ky,
+                       (even && iz == ng / 2) ? 0.f : kz};
+  const cufftComplex m = mk[t];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float s = kd[d] * g;  // i s (re + i im) = -s im + i s re
+    ak[d * total + t] = make_float2(-s * m.y, s * m.x);
+  }
+}
+
+__global__ void k_interpolate(const double *__restrict__ xs, const uint32_t *__restrict__ perm, int64_t n,
+                              double to_mesh, int ng, const float *__restrict__ a, float *__restrict__ acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int i0[3];
+  double d[3];
+  cic_setup(xs, n, i, to_mesh, ng, i0, d);
+  const int64_t cells = (int64_t)ng * ng * ng;
+  float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox) {
+    const float wx = (float)(ox ? d[0] : 1.0 - d[0]);
+    const int gx = i0[0] + ox == ng ? 0 : i0[0] + ox;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const float wy = (float)(oy ? d[1] : 1.0 - d[1]);
+      const int gy = i0[1] + oy == ng ? 0 : i0[1] + oy;
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const float wz = (float)(oz ? d[2] : 1.0 - d[2]);
+        const int gz = i0[2] + oz == ng ? 0 : i0[2] + oz;
+        const int64_t g = ((int64_t)gx * ng + gy) * ng + gz;
+        const float w = wx * wy * wz;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s[k] = fmaf(w, a[k * cells + g], s[k]);
+      }
+    }
+  }
+  const uint32_t o = perm[i];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) acc[k * n + o] += s[k];
+}
+
+__global__ void k_kick(float *__restrict__ vel, const float *__restrict__ acc, int64_t n3, float h) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n3) vel[i] = fmaf(h, acc[i], vel[i]);
+}
+
+__global__ void k_drift(double *__restrict__ pos, const float *__restrict__ vel, int64_t n3, double dt, double box) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double x = pos[i] + dt * (double)vel[i];
+  x -= box * floor(x / box);
+  if (x >= box) x -= box;  // rounding of a value just below 0
+  pos[i] = x;
+}
+
+cudaError_t fft_error(cufftResult r) { return r == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown; }
+
+}  // namespace
+
+void pm_release(Ctx &c) {
+  if (c.pm_plan_r2c >= 0) cufftDestroy(c.pm_plan_r2c);
+  if (c.pm_plan_c2r >= 0) cufftDestroy(c.pm_plan_c2r);
+  c.pm_plan_r2c = c.pm_plan_c2r = -1;
+  release(c.pm_q);
+  release(c.pm_rho);
+  release(c.pm_mk);
+  release(c.pm_ak);
+  release(c.pm_a);
+}
+
+cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  const int ng = c.prm.pm_grid;
+  const int64_t cells = (int64_t)ng * ng * ng, kcells = (int64_t)ng * ng * (ng / 2 + 1);
+  cudaError_t e;
+  if ((e = ensure(c.pm_q, cells * 8)) != cudaSuccess) return e;
+  if ((e = ensure(c.pm_rho, cells * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.pm_mk, kcells * sizeof(cufftComplex))) != cudaSuccess) return e;
+  if ((e = ensure(c.pm_ak, 3 * kcells * sizeof(cufftComplex))) != cudaSuccess) return e;
+  if ((e = ensure(c.pm_a, 3 * cells * 4)) != cudaSuccess) return e;
+  if (c.pm_plan_r2c < 0) {
+    cufftHandle p;
+    if ((e = fft_error(cufftPlan3d(&p, ng, ng, ng, CUFFT_R2C))) != cudaSuccess) return e;
+    c.pm_plan_r2c = p;
+    int dims[3] = {ng, ng, ng};
+    if ((e = fft_error(cufftPlanMany(&p, 3, dims, nullptr, 1, (int)kcells, nullptr, 1, (int)cells, CUFFT_C2R, 3))) !=
+        cudaSuccess)
+      return e;
+    c.pm_plan_c2r = p;
+  }
+  if ((e = fft_error(cufftSetStream(c.pm_plan_r2c, st))) != cudaSuccess) return e;
+  if ((e = fft_error(cufftSetStream(c.pm_plan_c2r, st))) != cudaSuccess) return e;
+
+  unsigned *mmax = reinterpret_cast<unsigned *>(P<uint64_t>(c.d_small) + 2);
+  if ((e = cudaMemsetAsync(mmax, 0, 8, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c.pm_q.p, 0, cells * 8, st)) != cudaSuccess) return e;
+  const int T = 256;
+  const double to_mesh = (double)ng / c.prm.box;
+  unsigned gm = blocks_for(c.n, T);
+  if (gm > 152 * 16) gm = 152 * 16;
+  k_mass_absmax<<<gm, T, 0, st>>>(P<float4>(c.pm4), c.n, mmax);
+  k_deposit<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<float4>(c.pm4), c.n, to_mesh, ng, mmax,
+                                              P<unsigned long long>(c.pm_q));
+  k_fixed_to_real<<<blocks_for(cells, T), T, 0, st>>>(P<unsigned long long>(c.pm_q), cells, mmax, c.n,
+                                                      P<float>(c.pm_rho));
+  note_launch(3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = fft_error(cufftExecR2C(c.pm_plan_r2c, P<cufftReal>(c.pm_rho), P<cufftComplex>(c.pm_mk)))) != cudaSuccess)
+    return e;
+  k_green<<<blocks_for(kcells, T), T, 0, st>>>(P<cufftComplex>(c.pm_mk), ng, (float)c.prm.box, (float)c.rs,
+                                               (float)c.prm.G, P<cufftComplex>(c.pm_ak));
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = fft_error(cufftExecC2R(c.pm_plan_c2r, P<cufftComplex>(c.pm_ak), P<cufftReal>(c.pm_a)))) != cudaSuccess)
+    return e;
+  k_interpolate<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<uint32_t>(c.idx), c.n, to_mesh, ng,
+                                                  P<float>(c.pm_a), acc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_kick<<<blocks_for(3 * n, 256), 256, 0, st>>>(vel, acc, 3 * n, (float)h);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_drift<<<blocks_for(3 * n, 256), 256, 0, st>>>(pos, vel, 3 * n, dt, box);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hfmm

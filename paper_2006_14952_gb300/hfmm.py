@@ -29,7 +29,7 @@ MLP_WEIGHTS = 5512
 SYMBOLS = ["hfmm_default_params", "hfmm_create", "hfmm_destroy", "hfmm_last_error", "hfmm_build_tree",
            "hfmm_short_range_forces", "hfmm_short_range_forces_host", "hfmm_get_stats", "hfmm_export",
            "hfmm_load_mlp", "hfmm_collect_training_pairs", "hfmm_mlp_infer", "hfmm_mlp_grad", "hfmm_mlp_adam",
-           "hfmm_morton_sort_noalloc"]
+           "hfmm_morton_sort_noalloc", "hfmm_pm_long_range", "hfmm_step"]
 
 
 class Params(C.Structure):
@@ -83,6 +83,10 @@ def load(build_if_missing: bool = True):
         L.hfmm_short_range_forces.restype = i32
         L.hfmm_short_range_forces_host.argtypes = [vp, vp, vp, i64, vp, vp]
         L.hfmm_short_range_forces_host.restype = i32
+        L.hfmm_pm_long_range.argtypes = [vp, vp, vp]
+        L.hfmm_pm_long_range.restype = i32
+        L.hfmm_step.argtypes = [vp, vp, vp, vp, C.c_double, vp]
+        L.hfmm_step.restype = i32
         L.hfmm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.hfmm_get_stats.restype = i32
         L.hfmm_export.argtypes = [vp, i32, vp, C.POINTER(C.c_size_t)]
@@ -201,6 +205,28 @@ class Solver:
         self._check(self._lib.hfmm_short_range_forces(self._h, C.c_void_p(acc.data_ptr()), _stream_handle(stream)),
                     "hfmm_short_range_forces")
         return acc
+
+    def pm_long_range(self, acc=None, stream=None):
+        """Adds the long-range (PM) accelerations into a CUDA float32 [3][n] tensor (zeros if None)."""
+        import torch
+
+        if acc is None:
+            acc = torch.zeros((3, self.n), dtype=torch.float32, device="cuda")
+        assert acc.is_cuda and acc.dtype == torch.float32 and acc.is_contiguous()
+        self._check(self._lib.hfmm_pm_long_range(self._h, C.c_void_p(acc.data_ptr()), _stream_handle(stream)),
+                    "hfmm_pm_long_range")
+        return acc
+
+    def step(self, pos, vel, acc, dt, stream=None):
+        """One KDK step in place: pos CUDA float64 [3][n]; vel, acc CUDA float32 [3][n]
+        (acc must hold the total acceleration at pos on entry)."""
+        import torch
+
+        assert pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()
+        for t in (vel, acc):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.shape == pos.shape
+        self._check(self._lib.hfmm_step(self._h, C.c_void_p(pos.data_ptr()), C.c_void_p(vel.data_ptr()),
+                                        C.c_void_p(acc.data_ptr()), float(dt), _stream_handle(stream)), "hfmm_step")
 
     def short_range_forces_host(self, pos, mass, acc=None, stream=None):
         """Host numpy (or pinned CPU torch) buffers in and out."""
