@@ -53,6 +53,26 @@ bool valid_params(const hfmm_params &p, std::string &why) {
 
 namespace hfmm {
 
+// Integer forms of the acceptance tests (see Ctx::rc2i and Ctx::acc_thr).  The
+// squared distances the traversal forms stay below 3 * 2^48, exact in FP64, so
+// comparing the integers against these thresholds takes the FP64 decisions.
+void mac_integer_thresholds(Ctx &c) {
+  c.rc2i = (int64_t)std::floor(c.rc2h);
+  const double smax = 3.0 * std::ldexp(1.0, 48);
+  for (int l = 0; l <= kDepth; ++l) {
+    const double w = std::ldexp(1.0, 44 - 2 * l);  // 4 w_l^2
+    int64_t t = INT64_MAX;
+    if (c.theta2 > 0 && w / c.theta2 < smax) {
+      double x = std::ceil(w / c.theta2);
+      // fl(theta2 * x) is non-decreasing in x: walk to the least x with fl(theta2 * x) >= w
+      while (x > 0 && c.theta2 * (x - 1) >= w) x -= 1;
+      while (c.theta2 * x < w) x += 1;
+      t = (int64_t)x;
+    }
+    c.acc_thr[l] = t;
+  }
+}
+
 PairFit fit_pair_factor(double rs, double rc) {
   constexpr int N = 10;
   const double pi = 3.14159265358979323846;
@@ -134,6 +154,7 @@ int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
   t = t / params->box;
   c.rc2h = t * t;
   c.theta2 = params->theta * params->theta;
+  mac_integer_thresholds(c);
   c.p = params->order;
   c.nc = ncoef(c.p);
   c.ldm = (c.nc + 3) & ~3;

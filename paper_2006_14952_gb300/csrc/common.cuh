@@ -125,12 +125,19 @@ struct PairFit {
 };
 // Chebyshev interpolation (10 nodes on [0, R_c]) of e^(x^2/4) erfc(x/2) + x/sqrt(pi), in FP64.
 PairFit fit_pair_factor(double rs, double rc);
+struct Ctx;
+void mac_integer_thresholds(Ctx &c);
 
 // ---------------------------------------------------------------- context
 struct Ctx {
   hfmm_params prm{};
   double rs = 0, rc = 0;        // split scale and cut-off radius
   double rc2h = 0, theta2 = 0;  // MAC thresholds (half units squared; theta^2)
+  // The same tests on integer squared distances (decisions identical to the FP64 ones):
+  //   (double)s > rc2h          <=>  s > rc2i = floor(rc2h)
+  //   4 w_l^2 <= fl(theta2 * s)  <=>  s >= acc_thr[l]   (w_l = 2^(21-l) half units)
+  int64_t rc2i = 0;
+  int64_t acc_thr[kDepth + 1] = {};
   PairFit fit{};
   int p = 4, nc = 35;
   int ldm = 36;  // row stride of the expansion arrays: nc rounded up to a multiple of 4 (float4 rows)

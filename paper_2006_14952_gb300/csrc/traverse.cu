@@ -34,7 +34,8 @@ enum : uint8_t { kSkip = 0, kM2L = 1, kP2P = 2, kOpenA = 3, kOpenB = 4, kOpenAB 
 constexpr uint8_t kCandidate = 6;  // internal: needs the network's decision
 
 struct Mac {
-  double rc2h, theta2;
+  int64_t rc2i;                 // floor of (R_c in half units)^2
+  int64_t acc_thr[kDepth + 1];  // accept iff S_c^2 >= acc_thr[level of the larger cell]
   int rule, size_rule;
   int mode;   // 0 geometric, 1 learned, 2 collect
   int order;  // p (geometric M2L order, and the largest learned order)
@@ -69,25 +70,33 @@ __device__ __forceinline__ uint8_t open_rule(uint4 ca, uint4 cb, int2 ka, int2 k
   return kOpenAB;
 }
 
+// Source centre (with the periodic shift) minus sink centre in half units; every
+// quantity fits 32 bits: centres are below 2^22, the shift is +-2^22.
+__device__ __forceinline__ void half_delta32(uint4 sink, uint4 src, uint32_t s, int (&dd)[3]) {
+  const uint32_t la = kDepth - sink.w, lb = kDepth - src.w;  // log2 of the half widths
+  dd[0] = (int)(((2u * src.x + 1u) << lb) - ((2u * sink.x + 1u) << la)) + shift_component(s, 0) * (int)kHalfBox;
+  dd[1] = (int)(((2u * src.y + 1u) << lb) - ((2u * sink.y + 1u) << la)) + shift_component(s, 1) * (int)kHalfBox;
+  dd[2] = (int)(((2u * src.z + 1u) << lb) - ((2u * sink.z + 1u) << la)) + shift_component(s, 2) * (int)kHalfBox;
+}
+
 __device__ __forceinline__ uint8_t classify(uint4 ca, uint4 cb, uint32_t s, int2 ka, int2 kb, const Mac &m) {
-  int64_t dd[3];
-  half_delta(ca, cb, s, dd);
-  const int64_t wa = half_width(ca.w), wb = half_width(cb.w), ext = wa + wb;
+  int dd[3];
+  half_delta32(ca, cb, s, dd);
+  const int ext = (1 << (kDepth - ca.w)) + (1 << (kDepth - cb.w));
   int64_t sc2 = 0, sm2 = 0, sx2 = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    int64_t a = dd[d] < 0 ? -dd[d] : dd[d];
-    int64_t g = a - ext > 0 ? a - ext : 0;
-    int64_t f = a + ext;
-    sc2 += a * a;
-    sm2 += g * g;
-    sx2 += f * f;
+    const int a = dd[d] < 0 ? -dd[d] : dd[d];
+    const int g = a - ext > 0 ? a - ext : 0;
+    const int f = a + ext;
+    sc2 += (int64_t)a * a;
+    sm2 += (int64_t)g * g;
+    sx2 += (int64_t)f * f;
   }
-  if ((double)sm2 > m.rc2h) return kSkip;
-  bool trans = m.rule == 0 ? ((double)sc2 > m.rc2h) : ((double)sx2 > m.rc2h);
-  int64_t wl = m.size_rule == 0 ? wb : (wa > wb ? wa : wb);
-  if (!trans && (double)(4 * wl * wl) <= __dmul_rn(m.theta2, (double)sc2))
-    return m.mode == 0 ? kM2L : kCandidate;  // sc2 = 0 (a self pair) never passes
+  if (sm2 > m.rc2i) return kSkip;
+  const bool trans = m.rule == 0 ? sc2 > m.rc2i : sx2 > m.rc2i;
+  const uint32_t lv = m.size_rule == 0 ? cb.w : (ca.w < cb.w ? ca.w : cb.w);  // level of the cell setting L
+  if (!trans && sc2 >= m.acc_thr[lv]) return m.mode == 0 ? kM2L : kCandidate;  // acc_thr >= 1: self pairs open
   return open_rule(ca, cb, ka, kb);
 }
 
@@ -103,9 +112,9 @@ struct Item {
 // cell offset beyond the table's extent in some axis.
 __device__ __forceinline__ bool table_miss(uint4 ca, uint4 cb, uint32_t s, int k) {
   if (k == 0 || ca.w != cb.w) return true;
-  int64_t dd[3];
-  half_delta(ca, cb, s, dd);
-  const int64_t lim = 2 * half_width(ca.w) * k;  // k cell sides
+  int dd[3];
+  half_delta32(ca, cb, s, dd);
+  const int lim = (2 << (kDepth - ca.w)) * k;  // k cell sides
   return dd[0] > lim || dd[0] < -lim || dd[1] > lim || dd[1] < -lim || dd[2] > lim || dd[2] < -lim;
 }
 
@@ -416,8 +425,8 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   c.traverse_iters = 0;
   if (c.n == 0) return cudaSuccess;
   Mac m{};
-  m.rc2h = c.rc2h;
-  m.theta2 = c.theta2;
+  m.rc2i = c.rc2i;
+  for (int l = 0; l <= kDepth; ++l) m.acc_thr[l] = c.acc_thr[l];
   m.rule = c.prm.transition_rule;
   m.size_rule = c.prm.size_rule;
   m.mode = c.collect ? 2 : c.prm.mac_mode;
