@@ -81,6 +81,15 @@ __host__ __device__ inline void half_delta(uint4 sink, uint4 src, uint32_t s, in
   dd[2] = half_centre(src.z, src.w) + shift_component(s, 2) * kHalfBox - half_centre(sink.z, sink.w);
 }
 
+// Source centre (with the periodic shift) minus sink centre in half units; every
+// quantity fits 32 bits: centres are below 2^22, the shift is +-2^22.
+__host__ __device__ inline void half_delta32(uint4 sink, uint4 src, uint32_t s, int (&dd)[3]) {
+  const uint32_t la = kDepth - sink.w, lb = kDepth - src.w;  // log2 of the half widths
+  dd[0] = (int)(((2u * src.x + 1u) << lb) - ((2u * sink.x + 1u) << la)) + shift_component(s, 0) * (int)kHalfBox;
+  dd[1] = (int)(((2u * src.y + 1u) << lb) - ((2u * sink.y + 1u) << la)) + shift_component(s, 1) * (int)kHalfBox;
+  dd[2] = (int)(((2u * src.z + 1u) << lb) - ((2u * sink.z + 1u) << la)) + shift_component(s, 2) * (int)kHalfBox;
+}
+
 // ---------------------------------------------------------------- buffers
 struct DBuf {
   void *p = nullptr;

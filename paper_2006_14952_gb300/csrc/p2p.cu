@@ -10,6 +10,12 @@
 // the buffer, so small leaves still keep the warp busy; the streams are added
 // in a fixed order at the end (deterministic).
 //
+// The buffer holds sources in pairs, {-x0, -x1, -y0, -y1} {-z0, -z1, -w0, -w1}
+// (w = mass), so each lane evaluates two pairs per step with the packed FP32x2
+// add / multiply / fma of sm_100+ (half the FP32 instructions; rsqrt and exp2
+// stay per element).  An odd tail is padded with a massless source far outside
+// the cut-off.
+//
 // Pair force: a = -m S(x) r / r^3, S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi),
 // x = r / r_s, evaluated as S = exp2(-x^2 log2(e) / 4) * Q(r / R_c) with Q a
 // degree-9 polynomial interpolating e^(x^2/4) erfc(x/2) + x / sqrt(pi) at
@@ -19,7 +25,22 @@
 namespace hfmm {
 namespace {
 
-constexpr int kCap = 256;  // staged source particles per warp
+constexpr int kCap = 256;  // staged source particles per warp (even)
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// One MUFU instruction each (relative error about 2^-22); the arguments here are
+// never denormal: r^2 > 0 in the cut-off range, and the exponent is -r^2 log2(e) / 4r_s^2 >= -7.3.
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float exp2_mufu(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 template <bool kCount>
 __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
@@ -29,9 +50,14 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
                                              const uint32_t *__restrict__ perm, int64_t n, float box, PairFit fit,
                                              float G, float *__restrict__ acc_out,
                                              unsigned long long *__restrict__ ctr) {
-  __shared__ float4 sbuf[8][kCap];
-  const int lane = threadIdx.x & 31;
-  float4 *buf = sbuf[threadIdx.x >> 5];
+  __shared__ float4 sbuf[8][kCap];  // kCap / 2 source pairs, two float4 each
+  // per warp: the 32 list entries of one fill step (first staged particle,
+  // exclusive slot offset, leaf-centre offset in the sink's frame)
+  __shared__ uint32_t e_src[8][32], e_excl[8][32];
+  __shared__ float e_off[8][3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float4 *buf = sbuf[wid];
+  float *bf = reinterpret_cast<float *>(buf);
   const float half_unit = box / (float)kHalfBox;
   uint32_t n_in = 0;  // pairs inside the cut-off (profile mode only)
   for (;;) {
@@ -49,7 +75,8 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
       const int S = 32 / cs, stream = lane / cs, il = lane % cs;
       const bool active = stream < S;
       const float4 xi = pm4[cbase + il];
-      float ax = 0.f, ay = 0.f, az = 0.f;
+      const float2 xx = f2(xi.x), xy = f2(xi.y), xz = f2(xi.z);
+      float2 ax = f2(0.f), ay = f2(0.f), az = f2(0.f);
       uint32_t q = tb, jq = 0;
       while (q < te) {
         int fill = 0;
@@ -62,8 +89,8 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
             const uint64_t e = lst[qi];
             const uint32_t b = pair_src(e);
             const uint2 rb = range[b];
-            int64_t dd[3];
-            half_delta(ca, cell[b], pair_shift(e), dd);
+            int dd[3];
+            half_delta32(ca, cell[b], pair_shift(e), dd);
             dx = (float)dd[0] * half_unit;
             dy = (float)dd[1] * half_unit;
             dz = (float)dd[2] * half_unit;
@@ -80,11 +107,32 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
           }
           const uint32_t excl = incl - avail;
           const uint32_t room = (uint32_t)(kCap - fill);
-          const uint32_t take = excl >= room ? 0u : min(avail, room - excl);
-          for (uint32_t j = 0; j < take; ++j) {
-            const float4 s4 = pm4[first + start + j];
-            buf[fill + excl + j] = make_float4(s4.x + dx, s4.y + dy, s4.z + dz, s4.w);
+          e_src[wid][lane] = first + start;
+          e_excl[wid][lane] = excl;  // non-decreasing in the lane index
+          e_off[wid][0][lane] = dx;
+          e_off[wid][1][lane] = dy;
+          e_off[wid][2][lane] = dz;
+          __syncwarp();
+          {
+            // stage slots [0, min(total, room)) of this step, one slot per lane:
+            // slot p belongs to the last entry whose offset is <= p
+            const uint32_t all = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t tot = all < room ? all : room;
+            for (uint32_t p = lane; p < tot; p += 32) {
+              int o = 0;
+#pragma unroll
+              for (int step = 16; step; step >>= 1)
+                if (e_excl[wid][o + step] <= p) o += step;
+              const float4 s4 = pm4[e_src[wid][o] + (p - e_excl[wid][o])];
+              const uint32_t slot = (uint32_t)fill + p;
+              float *a = bf + (slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
+              a[0] = -(s4.x + e_off[wid][0][o]);
+              a[2] = -(s4.y + e_off[wid][1][o]);
+              a[4] = -(s4.z + e_off[wid][2][o]);
+              a[6] = -s4.w;
+            }
           }
+          __syncwarp();  // the entry table is rewritten by the next step
           const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
           const unsigned full = __ballot_sync(0xffffffffu, valid && incl <= room);
           const int nfull = __popc(full);
@@ -95,31 +143,46 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
           q += nfull;
           fill += (int)(total < room ? total : room);
         }
+        if ((fill & 1) && lane == 0) {  // pad: massless, far beyond the cut-off
+          float *a = bf + (fill >> 1) * 8 + 1;
+          a[0] = -1e18f;
+          a[2] = -1e18f;
+          a[4] = -1e18f;
+          a[6] = 0.f;
+        }
         __syncwarp();
         if (active) {
-          for (int kk = stream; kk < fill; kk += S) {
-            const float4 s4 = buf[kk];
-            const float dx = xi.x - s4.x, dy = xi.y - s4.y, dz = xi.z - s4.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool in = (r2 < fit.rc2) && (r2 > 0.f);
-            if (kCount) n_in += in;
-            // outside (0, R_c) the value below may be inf/NaN; the select discards it
-            const float rinv = rsqrtf(r2);
-            const float tt = r2 * rinv * fit.inv_rc;
-            float qv = fit.c[9];
+          const int np = (fill + 1) >> 1;
+          for (int kk = stream; kk < np; kk += S) {
+            const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
+            const float2 dx = __fadd2_rn(xx, make_float2(A.x, A.y));
+            const float2 dy = __fadd2_rn(xy, make_float2(A.z, A.w));
+            const float2 dz = __fadd2_rn(xz, make_float2(B.x, B.y));
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const bool in0 = (r2.x < fit.rc2) && (r2.x > 0.f);
+            const bool in1 = (r2.y < fit.rc2) && (r2.y > 0.f);
+            if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
+            // outside (0, R_c) the values below may be inf/NaN; the selects discard them
+            const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            const float2 tt = __fmul2_rn(__fmul2_rn(r2, rinv), f2(fit.inv_rc));
+            float2 qv = f2(fit.c[9]);
 #pragma unroll
-            for (int j = 8; j >= 0; --j) qv = fmaf(qv, tt, fit.c[j]);
-            const float sfac = exp2f(r2 * fit.kexp) * qv;
-            const float f = in ? -(sfac * rinv * rinv * rinv) * s4.w : 0.f;
-            ax = fmaf(f, dx, ax);
-            ay = fmaf(f, dy, ay);
-            az = fmaf(f, dz, az);
+            for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, f2(fit.c[j]));
+            const float2 ea = __fmul2_rn(r2, f2(fit.kexp));
+            const float2 sfac = __fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv);
+            const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+            float2 f = __fmul2_rn(__fmul2_rn(sfac, r3), make_float2(B.z, B.w));  // -S m / r^3
+            f.x = in0 ? f.x : 0.f;
+            f.y = in1 ? f.y : 0.f;
+            ax = __ffma2_rn(f, dx, ax);
+            ay = __ffma2_rn(f, dy, ay);
+            az = __ffma2_rn(f, dz, az);
           }
         }
         __syncwarp();
       }
       // add the streams of each sink in a fixed order
-      buf[lane] = make_float4(ax, ay, az, 0.f);
+      buf[lane] = make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, 0.f);
       __syncwarp();
       if (lane < cs) {
         float sx = 0.f, sy = 0.f, sz = 0.f;

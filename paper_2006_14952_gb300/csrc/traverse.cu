@@ -70,15 +70,6 @@ __device__ __forceinline__ uint8_t open_rule(uint4 ca, uint4 cb, int2 ka, int2 k
   return kOpenAB;
 }
 
-// Source centre (with the periodic shift) minus sink centre in half units; every
-// quantity fits 32 bits: centres are below 2^22, the shift is +-2^22.
-__device__ __forceinline__ void half_delta32(uint4 sink, uint4 src, uint32_t s, int (&dd)[3]) {
-  const uint32_t la = kDepth - sink.w, lb = kDepth - src.w;  // log2 of the half widths
-  dd[0] = (int)(((2u * src.x + 1u) << lb) - ((2u * sink.x + 1u) << la)) + shift_component(s, 0) * (int)kHalfBox;
-  dd[1] = (int)(((2u * src.y + 1u) << lb) - ((2u * sink.y + 1u) << la)) + shift_component(s, 1) * (int)kHalfBox;
-  dd[2] = (int)(((2u * src.z + 1u) << lb) - ((2u * sink.z + 1u) << la)) + shift_component(s, 2) * (int)kHalfBox;
-}
-
 __device__ __forceinline__ uint8_t classify(uint4 ca, uint4 cb, uint32_t s, int2 ka, int2 kb, const Mac &m) {
   int dd[3];
   half_delta32(ca, cb, s, dd);
