@@ -375,7 +375,7 @@ def main():
             "breakdown_ms": {k[2:]: round(v, 4) for k, v in mean.items()},
             "counts": {"nodes": st["nnodes"], "leaves": st["nleaves"], "levels": st["nlevels"],
                        "traverse_iters": st["traverse_iters"], "p2p_leaf_pairs": st["np2p"],
-                       "m2l_pairs": st["nm2l"], "m2l_pairs_table": st["nm2l_table"],
+                       "m2l_pairs": st["nm2l"], "m2l_pairs_table": st["nm2l_table"], "frontier_pairs": st["frontier_pairs"],
                        "p2p_pairs_evaluated": st["p2p_particle_pairs"],
                        "p2p_pairs_useful": st["p2p_useful_pairs"]},
             "step_ms": [round(x, 4) for x in step_ms],

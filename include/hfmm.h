@@ -96,6 +96,7 @@ typedef struct {
   /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
   int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
+  int64_t frontier_pairs;     /* cell pairs the traversal classified, over all levels */
 } hfmm_stats;
 
 typedef struct hfmm_ctx hfmm_ctx;

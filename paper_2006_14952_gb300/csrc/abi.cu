@@ -180,7 +180,9 @@ void hfmm_destroy(hfmm_ctx *h) {
                   &c.leaves, &c.bounds, &c.nkids, &c.koff, &c.front, &c.front_next, &c.cls, &c.counts, &c.offs,
                   &c.m2l, &c.m2l_alt, &c.p2p, &c.p2p_alt, &c.m2l_beg, &c.m2l_end, &c.p2p_beg, &c.p2p_end, &c.M,
                   &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc, &c.m2l_mid, &c.tab,
-                  &c.mlp_w, &c.cand, &c.mlp_scratch};
+                  &c.mlp_w, &c.cand, &c.mlp_scratch, &c.fseg, &c.fseg_next, &c.seg_a, &c.seg_b, &c.acc_a,
+                  &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
+                  &c.rp_cnt, &c.segpre, &c.ctot};
   for (DBuf *b : bufs) release(*b);
   pm_release(c);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
@@ -327,6 +329,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->nm2l = c.nm2l;
   o->p2p_particle_pairs = c.p2p_particle_pairs;
   o->nm2l_table = c.nm2l_table;
+  o->frontier_pairs = c.frontier_items;
   o->p2p_useful_pairs = -1;
   if ((c.prm.profile & 2) && c.n > 0) {
     unsigned long long u = 0;

@@ -172,6 +172,12 @@ struct Ctx {
 
   // traversal
   DBuf front, front_next, cls, counts, offs;
+  // sink-major walk: segment of each sink cell (per level), segment sinks and totals,
+  // segment bases, runs of M2L / P2P entries per (sink, level)
+  DBuf fseg, fseg_next, seg_a, seg_b, acc_a, acc_b, segbase, btot2, segpre, ctot;
+  DBuf rm_key, rm_beg, rm_cnt, rp_key, rp_beg, rp_cnt;
+  uint64_t cap_seg = 0, cap_run = 0;
+  int64_t nrun_m = 0, nrun_p = 0, frontier_items = 0;
   DBuf m2l, m2l_alt, p2p, p2p_alt;  // packed u64 entries
   int64_t nm2l = 0, np2p = 0;
   int traverse_iters = 0;

@@ -96,7 +96,8 @@ __device__ __forceinline__ uint8_t classify(uint4 ca, uint4 cb, uint32_t s, int2
 // all 32 lanes of a warp (the network runs on warp batches of candidates).
 struct Item {
   uint8_t cls;
-  uint32_t nm, np, nch;
+  uint32_t nm, np, nchB;  // M2L entry, P2P entry, children of the source cell
+  uint32_t sink;
 };
 
 // An M2L pair outside the operator table: cells of different levels, or a
@@ -181,167 +182,414 @@ __device__ __forceinline__ Item mac_item(const uint64_t *__restrict__ f, int64_t
   it.cls = (uint8_t)(c | (order << 3) | (miss << 7));
   it.nm = c == kM2L;
   it.np = c == kP2P;
-  it.nch = c == kOpenA ? (uint32_t)ka.y : c == kOpenB ? (uint32_t)kb.y : c == kOpenAB ? (uint32_t)(ka.y * kb.y) : 0u;
+  it.nchB = kb.y > 0 ? (uint32_t)kb.y : 0u;
+  it.sink = a;
   return it;
 }
 
 struct TravState {
   unsigned long long nm2l, np2p, nf;
   int iters, overflow;
+  unsigned long long items;           // frontier pairs classified over all levels
+  unsigned long long nrun_m, nrun_p;  // M2L / P2P runs recorded
+};
+
+// Per-segment bases of one level: first output item (next frontier), the
+// item prefix of the children-per-sink-child counts at the segment start, the
+// first next-level segment, and the segment's children-per-sink-child total.
+struct SegBase {
+  unsigned long long o, c;
+  uint32_t s, C;
+};
+
+// Frontier and output buffers of the walk (device pointers and capacities).
+struct TravBufs {
+  uint64_t *fa, *fb;                    // frontier pairs (ping-pong)
+  uint32_t *map_a, *map_b;              // segment of each sink cell at this level (a sink has one)
+  uint8_t *cls;                         // class of each frontier pair
+  uint32_t *seg_a, *seg_b;              // sink of each segment (ping-pong)
+  unsigned long long *st_a, *st_b;      // first frontier pair of each segment (ping-pong)
+  unsigned long long *spre;             // per segment: pair prefixes (C, M, P) at its start
+  SegBase *base;                        // bases of the current level's segments
+  uint8_t *cc;                          // child pairs per child of the sink, per frontier pair
+  unsigned long long *ctot;             // per 32-pair chunk: totals (C, M, P), then exclusive prefixes
+  uint64_t *m2l, *p2p;                  // outputs
+  uint64_t *rm_key, *rp_key;            // runs: (sink << 8 | level)
+  uint64_t *rm_beg, *rp_beg;            // runs: first output entry
+  uint32_t *rm_cnt, *rp_cnt;            // runs: entries
+  unsigned long long *btot;             // per-block partial sums (4 per block)
+  unsigned long long capF, capS, capM, capP, capR;
 };
 
 constexpr int kTT = 256;  // threads of the traversal kernel
+constexpr int kTW = kTT / 32;
 
-// Persistent level-synchronous traversal: one cooperative launch processes
-// every level.  Per level each block classifies a contiguous chunk of the
-// frontier and publishes its counts; after a grid barrier every block forms
-// its output offsets from the counts of the blocks before it and writes its
-// M2L entries, P2P entries and child pairs in frontier order (the same order
-// as a serial pass, so the lists are deterministic).  Outputs beyond the
-// given capacities set st->overflow and stop the walk; the host grows the
-// buffers and runs it again.
+// Exclusive block-wide prefix of one value per thread (all threads call it);
+// returns the exclusive prefix, *tot receives the block total.
+__device__ __forceinline__ unsigned long long block_exscan(unsigned long long v, unsigned long long *wsum,
+                                                           unsigned long long *tot) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wp] = x;
+  __syncthreads();
+  unsigned long long before = 0, all = 0;
+#pragma unroll
+  for (int q = 0; q < kTW; ++q) {
+    const unsigned long long w = wsum[q];
+    if (q < wp) before += w;
+    all += w;
+  }
+  __syncthreads();
+  *tot = all;
+  return before + x - v;
+}
+
+// Block-wide sum of one value per thread (all threads call it).
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, unsigned long long *wsum) {
+  unsigned long long tot;
+  (void)block_exscan(v, wsum, &tot);
+  return tot;
+}
+
+// Prefix over the blocks before this one of column k of the per-block partials.
+__device__ __forceinline__ void block_prefixes(const unsigned long long *btot, int ncol, unsigned long long *pre,
+                                               unsigned long long *all) {
+  const unsigned nb = gridDim.x, bid = blockIdx.x;
+  if ((int)threadIdx.x < ncol) {
+    unsigned long long b = 0, a = 0;
+    for (unsigned q = 0; q < nb; ++q) {
+      const unsigned long long v = btot[4 * q + threadIdx.x];
+      if (q < bid) b += v;
+      a += v;
+    }
+    pre[threadIdx.x] = b;
+    all[threadIdx.x] = a;
+  }
+  __syncthreads();
+}
+
+// Persistent level-synchronous traversal, sink-major: one cooperative launch
+// processes every level.  The frontier is kept in segments, one per sink cell,
+// each holding that sink's pairs contiguously.  Per level:
+//   1. every warp classifies interleaved 32-pair chunks (the acceptance rules
+//      of Sec. 2.3; interleaving spreads dense regions over all warps) and
+//      records per chunk the number of child pairs given to each child of the
+//      sink (C), of M2L entries (M) and of P2P entries (P);
+//   2. a scan over the chunks gives every chunk its exclusive prefixes; the
+//      prefixes at the segment starts give each segment its totals; a scan
+//      over the segments gives each its next-frontier base, writes the next
+//      level's segments (one per child of an opened sink, or the sink itself
+//      when it is a leaf whose partners open) and records the runs of M2L and
+//      P2P entries each sink received at this level;
+//   3. every warp emits its chunks again: M2L / P2P entries in pair order (so
+//      grouped by sink within the level), child pairs at
+//      base + child * C + (prefix within the segment), so that every child's
+//      pairs are contiguous in the next frontier.
+// A non-leaf sink only ever opens itself (open A or both): the larger cell is
+// opened, and a pair with a larger source arises only when the sink is a leaf.
+// Outputs beyond the given capacities set st->overflow and stop the walk; the
+// host grows the buffers and runs it again.
 template <bool kNet>
 __global__ void __launch_bounds__(kTT, kNet ? 2 : 4) k_traverse(const uint4 *__restrict__ cell,
-                                                  const int2 *__restrict__ kids, Mac m,
-                                                  uint64_t *fa, uint64_t *fb, unsigned long long capF,
-                                                  uint8_t *__restrict__ cls, uint64_t *__restrict__ m2l,
-                                                  unsigned long long capM, uint64_t *__restrict__ p2p,
-                                                  unsigned long long capP, uint32_t *__restrict__ btot,
-                                                  TravState *__restrict__ st, int max_iters) {
+                                                                const int2 *__restrict__ kids, Mac m, TravBufs B,
+                                                                TravState *__restrict__ st, int max_iters) {
   cg::grid_group grid = cg::this_grid();
   constexpr int kSw = kNet ? kMlpSmemWords : 1, kXs = kNet ? 32 * 16 : 1, kDec = kNet ? 32 : 1;
   __shared__ uint32_t sw[kSw];
-  __shared__ __align__(16) __nv_bfloat16 xs[kTT / 32][kXs];
-  __shared__ uint8_t dec[kTT / 32][kDec];
-  __shared__ uint32_t ws[kTT / 32][3];
-  __shared__ unsigned long long pre[3], sums[3];
+  __shared__ __align__(16) __nv_bfloat16 xs[kTW][kXs];
+  __shared__ uint8_t dec[kTW][kDec];
+  __shared__ unsigned long long wsum[kTW], pre[4], all[4], run[4];
+  // level state, uniform over the grid (kept in shared memory, out of the registers)
+  __shared__ uint64_t *cur, *nxt;
+  __shared__ uint32_t *cmap, *nmap, *segs, *nsegs;
+  __shared__ unsigned long long *sst, *nsst;
+  __shared__ unsigned long long nf, nseg, nm, np, nrm, nrp, items;
   if (kNet) mlp_stage(m.w, sw);
-  const int tid = threadIdx.x, wp = tid >> 5;
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
   const unsigned nb = gridDim.x, bid = blockIdx.x;
-  if (bid == 0 && tid < 27) fa[tid] = pack_pair(0, 0, (uint32_t)tid);
+  const unsigned long long gw = (unsigned long long)bid * kTW + wp, nw = (unsigned long long)nb * kTW;
+  if (bid == 0 && tid < 27) B.fa[tid] = pack_pair(0, 0, (uint32_t)tid);
+  if (bid == 0 && tid == 0) {
+    B.map_a[0] = 0;
+    B.seg_a[0] = 0;
+    B.st_a[0] = 0;
+  }
+  if (tid == 0) {
+    cur = B.fa;
+    nxt = B.fb;
+    cmap = B.map_a;
+    nmap = B.map_b;
+    segs = B.seg_a;
+    nsegs = B.seg_b;
+    sst = B.st_a;
+    nsst = B.st_b;
+    nf = 27;
+    nseg = 1;
+    nm = np = nrm = nrp = items = 0;
+  }
   __syncthreads();
   grid.sync();
-  uint64_t *cur = fa, *nxt = fb;
-  unsigned long long nf = 27, nm = 0, np = 0;
-  const int lane = tid & 31;
-  constexpr int kW = kTT / 32;
   int iter = 0;
   for (; iter < max_iters && nf > 0; ++iter) {
-    // block range, then one contiguous sub-range per warp
-    const unsigned long long chunk = (nf + nb - 1) / nb;
-    const unsigned long long lo = chunk * bid < nf ? chunk * bid : nf;
-    const unsigned long long hi = lo + chunk < nf ? lo + chunk : nf;
-    const unsigned long long wch = (hi - lo + kW - 1) / kW;
-    const unsigned long long wlo = lo + wch * wp < hi ? lo + wch * wp : hi;
-    const unsigned long long whi = wlo + wch < hi ? wlo + wch : hi;
-    uint32_t cnt[3] = {0, 0, 0};
-    for (unsigned long long base = wlo; base < whi; base += 32) {
-      const unsigned long long t = base + lane;
-      const bool valid = t < whi;
+    const unsigned long long NF = nf, K = (NF + 31) / 32;  // 32-pair chunks
+    // ---- 1. classify interleaved chunks; chunk totals (C, M, P)
+    for (unsigned long long k = gw; k < K; k += nw) {
+      const unsigned long long t = 32 * k + lane;
+      const bool valid = t < NF;
       const Item it = mac_item<kNet>(cur, (int64_t)t, valid, cell, kids, m, sw, xs[wp], dec[wp]);
+      uint32_t v[3] = {0, 0, 0};
       if (valid) {
-        cls[t] = it.cls;
-        cnt[0] += it.nm;
-        cnt[1] += it.np;
-        cnt[2] += it.nch;
+        const uint8_t c = it.cls & 7;
+        v[0] = c == kOpenA ? 1u : (c == kOpenAB || c == kOpenB) ? it.nchB : 0u;
+        v[1] = it.nm;
+        v[2] = it.np;
+        B.cls[t] = it.cls;
+        B.cc[t] = (uint8_t)v[0];
       }
-    }
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      for (int o = 16; o; o >>= 1) cnt[k] += __shfl_xor_sync(0xffffffffu, cnt[k], o);
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) ws[wp][k] = cnt[k];
-    __syncthreads();
-    if (tid < 3) {
-      uint32_t t = 0;
-      for (int q = 0; q < kW; ++q) t += ws[q][tid];
-      btot[3 * bid + tid] = t;
+      for (int q = 0; q < 3; ++q) v[q] = __reduce_add_sync(0xffffffffu, v[q]);
+      if (lane < 3) B.ctot[3 * k + lane] = v[lane];
     }
     __threadfence();
     grid.sync();
-    if (tid < 3) {
-      unsigned long long before = 0, all = 0;
-      for (unsigned q = 0; q < nb; ++q) {
-        const unsigned long long v = btot[3 * q + tid];
-        if (q < bid) before += v;
-        all += v;
-      }
-      pre[tid] = before;
-      sums[tid] = all;
+    // ---- 2a. chunk scan: block partials over contiguous chunk ranges
+    const unsigned long long kch = (K + nb - 1) / nb;
+    const unsigned long long klo = kch * bid < K ? kch * bid : K, khi = klo + kch < K ? klo + kch : K;
+    for (int q = 0; q < 3; ++q) {
+      unsigned long long loc = 0;
+      for (unsigned long long k = klo + tid; k < khi; k += kTT) loc += B.ctot[3 * k + q];
+      const unsigned long long tot = block_sum(loc, wsum);
+      if (tid == 0) B.btot[4 * bid + q] = tot;
     }
+    __threadfence();
+    grid.sync();
+    // ---- 2b. chunk scan: exclusive prefixes in place
+    block_prefixes(B.btot, 3, pre, all);
+    const unsigned long long Tc = all[0], Tm = all[1], Tp = all[2];
+    if (tid < 3) run[tid] = pre[tid];
     __syncthreads();
-    const unsigned long long Tm = sums[0], Tp = sums[1], Tc = sums[2];
-    if (nm + Tm > capM || np + Tp > capP || Tc > capF) {
+    for (unsigned long long kb = klo; kb < khi; kb += kTT) {
+      const unsigned long long k = kb + tid;
+      const bool valid = k < khi;
+      for (int q = 0; q < 3; ++q) {
+        const unsigned long long v = valid ? B.ctot[3 * k + q] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_exscan(v, wsum, &tot);
+        if (valid) B.ctot[3 * k + q] = run[q] + ex;
+        __syncthreads();
+        if (tid == 0) run[q] += tot;
+        __syncthreads();
+      }
+    }
+    __threadfence();
+    grid.sync();
+    // ---- 2c. segment prefixes at their starts, totals by differences; block partials of
+    //          (next items, next segments, M2L runs, P2P runs)
+    const unsigned long long NS = nseg;
+    const unsigned long long sch = (NS + nb - 1) / nb;
+    const unsigned long long slo = sch * bid < NS ? sch * bid : NS, shi = slo + sch < NS ? slo + sch : NS;
+    // prefix (C, M, P) of the pairs before frontier position t
+    auto prefix_at = [&](unsigned long long t, unsigned long long (&pv)[3]) {
+      if (t >= NF) {
+        pv[0] = Tc;
+        pv[1] = Tm;
+        pv[2] = Tp;
+        return;
+      }
+      const unsigned long long k = t / 32;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) pv[q] = B.ctot[3 * k + q];
+      for (unsigned long long j = 32 * k; j < t; ++j) {
+        const uint8_t c = B.cls[j] & 7;
+        pv[0] += B.cc[j];
+        pv[1] += c == kM2L;
+        pv[2] += c == kP2P;
+      }
+    };
+    auto seg_prefix = [&](unsigned long long s, unsigned long long (&pv)[3]) { prefix_at(s < NS ? sst[s] : NF, pv); };
+    {
+      unsigned long long loc[4] = {0, 0, 0, 0};
+      for (unsigned long long s = slo + tid; s < shi; s += kTT) {
+        unsigned long long pv[3], pn[3];
+        seg_prefix(s, pv);
+        seg_prefix(s + 1, pn);
+        const int2 kk = kids[segs[s]];
+        const unsigned long long mult = kk.y > 0 ? (unsigned long long)kk.y : 1ull, C = pn[0] - pv[0];
+        loc[0] += mult * C;
+        loc[1] += C > 0 ? mult : 0;
+        loc[2] += pn[1] > pv[1];
+        loc[3] += pn[2] > pv[2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) B.spre[3 * s + q] = pv[q];
+      }
+      for (int q = 0; q < 4; ++q) {
+        const unsigned long long tot = block_sum(loc[q], wsum);
+        if (tid == 0) B.btot[4 * bid + q] = tot;
+      }
+    }
+    __threadfence();
+    grid.sync();
+    // ---- 2d. segment scan: bases, next-level segments, runs
+    block_prefixes(B.btot, 4, pre, all);
+    const unsigned long long To = all[0], Ts = all[1], Trm = all[2], Trp = all[3];
+    if (nm + Tm > B.capM || np + Tp > B.capP || To > B.capF || Ts > B.capS || nrm + Trm > B.capR ||
+        nrp + Trp > B.capR) {
       if (bid == 0 && tid == 0) st->overflow = 1;
       break;  // every block takes the same decision
     }
-    // this warp's offsets: the block's offsets plus the counts of the warps before it
-    unsigned long long om = nm + pre[0], op = np + pre[1], oc = pre[2];
-    for (int q = 0; q < wp; ++q) {
-      om += ws[q][0];
-      op += ws[q][1];
-      oc += ws[q][2];
+    if (tid < 4) run[tid] = pre[tid];
+    __syncthreads();
+    for (unsigned long long sb0 = slo; sb0 < shi; sb0 += kTT) {
+      const unsigned long long s = sb0 + tid;
+      const bool valid = s < shi;
+      unsigned long long tv[3] = {0, 0, 0}, pv[3] = {0, 0, 0};
+      uint32_t sink = 0;
+      int2 kk = make_int2(-1, 0);
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) pv[q] = B.spre[3 * s + q];
+        if (s + 1 < NS) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) tv[q] = B.spre[3 * (s + 1) + q] - pv[q];
+        } else {
+          tv[0] = Tc - pv[0];
+          tv[1] = Tm - pv[1];
+          tv[2] = Tp - pv[2];
+        }
+        sink = segs[s];
+        kk = kids[sink];
+      }
+      const unsigned long long mult = kk.y > 0 ? (unsigned long long)kk.y : 1ull;
+      unsigned long long ex[4], tot[4];
+      ex[0] = block_exscan(valid ? mult * tv[0] : 0ull, wsum, &tot[0]);
+      ex[1] = block_exscan(valid && tv[0] > 0 ? mult : 0ull, wsum, &tot[1]);
+      ex[2] = block_exscan(valid && tv[1] > 0 ? 1ull : 0ull, wsum, &tot[2]);
+      ex[3] = block_exscan(valid && tv[2] > 0 ? 1ull : 0ull, wsum, &tot[3]);
+      if (valid) {
+        const unsigned long long o = run[0] + ex[0], sn = run[1] + ex[1];
+        SegBase sbv;
+        sbv.o = o;
+        sbv.s = (uint32_t)sn;
+        sbv.c = pv[0];
+        sbv.C = (uint32_t)tv[0];
+        B.base[s] = sbv;
+        if (tv[0] > 0) {  // next-level segments: the sink itself (leaf) or each of its children
+          if (kk.y > 0) {
+            for (int i = 0; i < kk.y; ++i) {
+              nsegs[sn + i] = (uint32_t)kk.x + (uint32_t)i;
+              nmap[(uint32_t)kk.x + (uint32_t)i] = (uint32_t)(sn + i);
+              nsst[sn + i] = o + (unsigned long long)i * tv[0];
+            }
+          } else {
+            nsegs[sn] = sink;
+            nmap[sink] = (uint32_t)sn;
+            nsst[sn] = o;
+          }
+        }
+        if (tv[1] > 0) {
+          const unsigned long long r = nrm + run[2] + ex[2];
+          B.rm_key[r] = ((unsigned long long)sink << 8) | (unsigned)iter;
+          B.rm_beg[r] = nm + pv[1];
+          B.rm_cnt[r] = (uint32_t)tv[1];
+        }
+        if (tv[2] > 0) {
+          const unsigned long long r = nrp + run[3] + ex[3];
+          B.rp_key[r] = ((unsigned long long)sink << 8) | (unsigned)iter;
+          B.rp_beg[r] = np + pv[2];
+          B.rp_cnt[r] = (uint32_t)tv[2];
+        }
+      }
+      __syncthreads();
+      if (tid < 4) run[tid] += tot[tid];
+      __syncthreads();
     }
-    for (unsigned long long base = wlo; base < whi; base += 32) {
-      const unsigned long long t = base + lane;
-      const bool valid = t < whi;
+    __threadfence();
+    grid.sync();
+    // ---- 3. emit interleaved chunks
+    for (unsigned long long k = gw; k < K; k += nw) {
+      const unsigned long long t = 32 * k + lane;
+      const bool valid = t < NF;
       uint8_t cc = 0;
       uint64_t e = 0;
       int2 ka = make_int2(-1, 0), kb = make_int2(-1, 0);
       uint32_t v[3] = {0, 0, 0};
       if (valid) {
-        cc = cls[t];
+        cc = B.cls[t];
         e = cur[t];
         const uint8_t c = cc & 7;
-        if (c == kM2L) v[0] = 1;
-        if (c == kP2P) v[1] = 1;
+        if (c == kM2L) v[1] = 1;
+        if (c == kP2P) v[2] = 1;
         if (c == kOpenA || c == kOpenB || c == kOpenAB) {
           ka = kids[pair_sink(e)];
           kb = kids[pair_src(e)];
-          v[2] = c == kOpenA ? ka.y : c == kOpenB ? kb.y : ka.y * kb.y;
+          v[0] = c == kOpenA ? 1u : (uint32_t)kb.y;
         }
       }
       uint32_t x[3] = {v[0], v[1], v[2]};
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
-          if (lane >= o) x[k] += y;
+        for (int q = 0; q < 3; ++q) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x[q], o);
+          if (lane >= o) x[q] += y;
         }
       if (valid) {
         const uint8_t c = cc & 7;
-        if (c == kM2L) m2l[om + x[0] - v[0]] = with_order(e, (cc >> 3) & 15) | ((uint64_t)(cc >> 7) << kGenericBit);
-        if (c == kP2P) p2p[op + x[1] - v[1]] = e;
+        if (c == kM2L)
+          B.m2l[nm + B.ctot[3 * k + 1] + x[1] - v[1]] = with_order(e, (cc >> 3) & 15) | ((uint64_t)(cc >> 7) << kGenericBit);
+        if (c == kP2P) B.p2p[np + B.ctot[3 * k + 2] + x[2] - v[2]] = e;
         if (c == kOpenA || c == kOpenB || c == kOpenAB) {
           const uint32_t a = pair_sink(e), b = pair_src(e), s = pair_shift(e);
-          uint32_t a0 = a, na = 1, b0 = b, nbb = 1;
-          if (c == kOpenA || c == kOpenAB) {
-            a0 = (uint32_t)ka.x;
-            na = (uint32_t)ka.y;
+          const SegBase sb = B.base[cmap[a]];
+          const unsigned long long p0 = sb.o + (B.ctot[3 * k] + x[0] - v[0] - sb.c);
+          // the last slot this item writes; beyond the next frontier means inconsistent bases
+          const unsigned long long last =
+              c == kOpenB ? p0 + kb.y : p0 + (unsigned long long)(ka.y - 1) * sb.C + (c == kOpenA ? 1 : kb.y);
+          const bool bad = (c == kOpenB && ka.y > 0) || last > To;  // cannot happen (see above)
+          if (bad) {
+            st->overflow = 2;  // refuse rather than write out of place
+          } else if (c == kOpenB) {  // the sink is a leaf: one next-level segment
+            for (int q = 0; q < kb.y; ++q) nxt[p0 + q] = pack_pair(a, (uint32_t)kb.x + (uint32_t)q, s);
+          } else {
+            const int nbk = c == kOpenA ? 1 : kb.y;
+            for (int i = 0; i < ka.y; ++i) {
+              const unsigned long long pi = p0 + (unsigned long long)i * sb.C;
+              for (int q = 0; q < nbk; ++q)
+                nxt[pi + q] =
+                    pack_pair((uint32_t)ka.x + (uint32_t)i, c == kOpenA ? b : (uint32_t)kb.x + (uint32_t)q, s);
+            }
           }
-          if (c == kOpenB || c == kOpenAB) {
-            b0 = (uint32_t)kb.x;
-            nbb = (uint32_t)kb.y;
-          }
-          uint64_t *o = nxt + oc + x[2] - v[2];
-          for (uint32_t xx = 0; xx < na; ++xx)
-            for (uint32_t y = 0; y < nbb; ++y) *o++ = pack_pair(a0 + xx, b0 + y, s);
         }
       }
-      om += __shfl_sync(0xffffffffu, x[0], 31);
-      op += __shfl_sync(0xffffffffu, x[1], 31);
-      oc += __shfl_sync(0xffffffffu, x[2], 31);
     }
-    nm += Tm;
-    np += Tp;
-    nf = Tc;
-    uint64_t *tmp = cur;
-    cur = nxt;
-    nxt = tmp;
+    __syncthreads();  // every thread is done with this level's state
+    if (tid == 0) {
+      items += nf;
+      nm += Tm;
+      np += Tp;
+      nrm += Trm;
+      nrp += Trp;
+      nf = To;
+      nseg = Ts;
+      uint64_t *t1 = cur;
+      cur = nxt;
+      nxt = t1;
+      uint32_t *t2 = cmap;
+      cmap = nmap;
+      nmap = t2;
+      uint32_t *t3 = segs;
+      segs = nsegs;
+      nsegs = t3;
+      unsigned long long *t4 = sst;
+      sst = nsst;
+      nsst = t4;
+    }
     __threadfence();
-    __syncthreads();  // ws is rewritten by the next level
     grid.sync();
   }
   if (bid == 0 && tid == 0) {
@@ -349,6 +597,9 @@ __global__ void __launch_bounds__(kTT, kNet ? 2 : 4) k_traverse(const uint4 *__r
     st->np2p = np;
     st->nf = nf;
     st->iters = iter;
+    st->items = items;
+    st->nrun_m = nrm;
+    st->nrun_p = nrp;
   }
 }
 
@@ -442,53 +693,181 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, net ? k_traverse<true> : k_traverse<false>, kTT, 0));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const unsigned nb = (unsigned)(nsm * (per_sm < 4 ? per_sm : 4));
-  TRY(ensure(c.counts, (size_t)nb * 3 * sizeof(uint32_t)));
+  TRY(ensure(c.btot2, (size_t)nb * 4 * sizeof(unsigned long long)));
   // capacities: the last call's sizes with head-room, at least a few per node
   auto grow = [](uint64_t want) { return want + want / 4 + 1024; };
-  if (c.cap_front < (uint64_t)(4 * c.nnodes + 1024)) c.cap_front = 4 * c.nnodes + 1024;
-  if (c.cap_m2l < (uint64_t)(8 * c.nnodes + 1024)) c.cap_m2l = 8 * c.nnodes + 1024;
-  if (c.cap_p2p < (uint64_t)(16 * c.nleaves + 1024)) c.cap_p2p = 16 * c.nleaves + 1024;
+  // (first guesses from the clustered benchmark sets: ~60 frontier pairs, ~50 M2L
+  // and ~115 P2P entries per particle at the largest level / in total)
+  if (c.cap_front < (uint64_t)(64 * c.n + 1024)) c.cap_front = 64 * c.n + 1024;
+  if (c.cap_m2l < (uint64_t)(64 * c.n + 1024)) c.cap_m2l = 64 * c.n + 1024;
+  if (c.cap_p2p < (uint64_t)(128 * c.n + 1024)) c.cap_p2p = 128 * c.n + 1024;
+  if (c.cap_seg < (uint64_t)(2 * c.nnodes + 1024)) c.cap_seg = 2 * c.nnodes + 1024;
+  if (c.cap_run < (uint64_t)(4 * c.nnodes + 1024)) c.cap_run = 4 * c.nnodes + 1024;
   TravState *dst = reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
   for (int attempt = 0; attempt < 8; ++attempt) {
     TRY(ensure(c.front, c.cap_front * 8));
     TRY(ensure(c.front_next, c.cap_front * 8));
-    TRY(ensure(c.cls, c.cap_front));
+    TRY(ensure(c.fseg, c.nnodes * 4 + 64));
+    TRY(ensure(c.fseg_next, c.nnodes * 4 + 64));
+    TRY(ensure(c.cls, c.cap_front * 2));  // class and child count per frontier pair
+    TRY(ensure(c.seg_a, c.cap_seg * 4));
+    TRY(ensure(c.seg_b, c.cap_seg * 4));
+    TRY(ensure(c.acc_a, c.cap_seg * 8));  // segment starts (ping-pong)
+    TRY(ensure(c.acc_b, c.cap_seg * 8));
+    TRY(ensure(c.segpre, c.cap_seg * 24));
+    TRY(ensure(c.segbase, c.cap_seg * sizeof(SegBase)));
+    TRY(ensure(c.ctot, ((c.cap_front + 31) / 32) * 24 + 64));
     TRY(ensure(c.m2l, c.cap_m2l * 8));
     TRY(ensure(c.p2p, c.cap_p2p * 8));
+    TRY(ensure(c.rm_key, c.cap_run * 8));
+    TRY(ensure(c.rm_beg, c.cap_run * 8));
+    TRY(ensure(c.rm_cnt, c.cap_run * 4));
+    TRY(ensure(c.rp_key, c.cap_run * 8));
+    TRY(ensure(c.rp_beg, c.cap_run * 8));
+    TRY(ensure(c.rp_cnt, c.cap_run * 4));
     TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), st));
-    uint64_t *fa = P<uint64_t>(c.front), *fb = P<uint64_t>(c.front_next);
-    uint8_t *cl = P<uint8_t>(c.cls);
-    uint64_t *ml = P<uint64_t>(c.m2l), *pl = P<uint64_t>(c.p2p);
-    unsigned long long capF = c.cap_front, capM = c.cap_m2l, capP = c.cap_p2p;
-    uint32_t *bt = P<uint32_t>(c.counts);
+    TravBufs B;
+    B.fa = P<uint64_t>(c.front);
+    B.fb = P<uint64_t>(c.front_next);
+    B.map_a = P<uint32_t>(c.fseg);
+    B.map_b = P<uint32_t>(c.fseg_next);
+    B.cls = P<uint8_t>(c.cls);
+    B.cc = P<uint8_t>(c.cls) + c.cap_front;
+    B.seg_a = P<uint32_t>(c.seg_a);
+    B.seg_b = P<uint32_t>(c.seg_b);
+    B.st_a = P<unsigned long long>(c.acc_a);
+    B.st_b = P<unsigned long long>(c.acc_b);
+    B.spre = P<unsigned long long>(c.segpre);
+    B.base = P<SegBase>(c.segbase);
+    B.ctot = P<unsigned long long>(c.ctot);
+    B.m2l = P<uint64_t>(c.m2l);
+    B.p2p = P<uint64_t>(c.p2p);
+    B.rm_key = P<uint64_t>(c.rm_key);
+    B.rp_key = P<uint64_t>(c.rp_key);
+    B.rm_beg = P<uint64_t>(c.rm_beg);
+    B.rp_beg = P<uint64_t>(c.rp_beg);
+    B.rm_cnt = P<uint32_t>(c.rm_cnt);
+    B.rp_cnt = P<uint32_t>(c.rp_cnt);
+    B.btot = P<unsigned long long>(c.btot2);
+    B.capF = c.cap_front;
+    B.capS = c.cap_seg;
+    B.capM = c.cap_m2l;
+    B.capP = c.cap_p2p;
+    B.capR = c.cap_run;
     int max_iters = 2 * kDepth + 6;
-    void *args[] = {(void *)&c.cell.p, (void *)&c.kids.p, (void *)&m, (void *)&fa, (void *)&fb, (void *)&capF,
-                    (void *)&cl, (void *)&ml, (void *)&capM, (void *)&pl, (void *)&capP, (void *)&bt,
-                    (void *)&dst, (void *)&max_iters};
+    void *args[] = {(void *)&c.cell.p, (void *)&c.kids.p, (void *)&m, (void *)&B, (void *)&dst, (void *)&max_iters};
     TRY(cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kTT), args, 0, st));
     note_launch();
     TravState hs;
     TRY(cudaMemcpyAsync(c.h_pinned, dst, sizeof(TravState), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     std::memcpy(&hs, c.h_pinned, sizeof(TravState));
+    if (hs.overflow == 2) return cudaErrorInvalidValue;  // a non-leaf sink was asked to open its partner
     if (!hs.overflow) {
       if (hs.nf != 0) return cudaErrorInvalidValue;  // more levels than any octree can have
       c.nm2l = (int64_t)hs.nm2l;
       c.np2p = (int64_t)hs.np2p;
       c.traverse_iters = hs.iters;
+      c.frontier_items = (int64_t)hs.items;
+      c.nrun_m = (int64_t)hs.nrun_m;
+      c.nrun_p = (int64_t)hs.nrun_p;
       return cudaSuccess;
     }
     // grow every list (the walk stopped at the first overflow, so the sizes seen are lower bounds)
     c.cap_front = grow(c.cap_front * 2);
     c.cap_m2l = grow(c.cap_m2l * 2);
     c.cap_p2p = grow(c.cap_p2p * 2);
+    c.cap_seg = grow(c.cap_seg * 2);
+    c.cap_run = grow(c.cap_run * 2);
   }
   return cudaErrorInvalidValue;
 #undef TRY
 }
 
-// Group both lists by sink (stable, so the traversal order is kept within a
-// sink) and build CSR bounds; count the particle pairs P2P evaluates.
+namespace {
+
+__global__ void k_iota(uint32_t *__restrict__ v, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_run_gather(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ cnt,
+                             uint32_t *__restrict__ cnt_s, int64_t nr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nr) cnt_s[i] = cnt[idx[i]];
+}
+
+// One warp per run (runs sorted by (sink, level)): CSR bounds of its sink and a
+// coalesced copy of its entries to their place in the sink-grouped list.
+__global__ void k_run_copy(const uint64_t *__restrict__ key_s, const uint32_t *__restrict__ idx,
+                           const uint64_t *__restrict__ beg, const uint32_t *__restrict__ cnt_s,
+                           const uint32_t *__restrict__ dst, int64_t nr, const uint64_t *__restrict__ src,
+                           uint64_t *__restrict__ out, uint32_t *__restrict__ csr_beg, uint32_t *__restrict__ csr_end,
+                           uint32_t *__restrict__ csr_mid) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nr; i += nw) {
+    const uint32_t sink = (uint32_t)(key_s[i] >> 8);
+    const uint32_t d = dst[i], n = cnt_s[i];
+    if (lane == 0) {
+      if (i == 0 || (uint32_t)(key_s[i - 1] >> 8) != sink) {
+        csr_beg[sink] = d;
+        if (csr_mid) csr_mid[sink] = d;  // no operator-table pairs on this path
+      }
+      if (i == nr - 1 || (uint32_t)(key_s[i + 1] >> 8) != sink) csr_end[sink] = d + n;
+    }
+    const uint64_t b = beg[idx[i]];
+    for (uint32_t j = lane; j < n; j += 32) out[d + j] = src[b + j];
+  }
+}
+
+}  // namespace
+
+// The walk leaves each level's entries grouped by sink; a sink that stays a
+// leaf over several levels has one run per level.  Sort the runs by (sink,
+// level), place them with a prefix sum of their lengths and copy: the list
+// ends up grouped by sink (levels in order, walk order within a level) with
+// CSR bounds.  Cost: a sort of the runs (one per sink and level) and one pass
+// over the entries.
+static cudaError_t merge_runs(Ctx &c, DBuf &L, DBuf &A, int64_t n, DBuf &rkey, DBuf &rbeg, DBuf &rcnt, int64_t nr,
+                              uint32_t *csr_beg, uint32_t *csr_end, uint32_t *csr_mid, int sink_bits,
+                              cudaStream_t st) {
+  cudaError_t e;
+  if (n == 0 || nr == 0) return cudaSuccess;
+  if ((e = ensure(A, n * 8)) != cudaSuccess) return e;
+  // scratch: key_alt u64 | idx u32 | idx_alt u32 | cnt_s u32 | dst u32
+  if ((e = ensure(c.tmp2, (size_t)nr * 24 + 64)) != cudaSuccess) return e;
+  uint64_t *key_alt = P<uint64_t>(c.tmp2);
+  uint32_t *idx = reinterpret_cast<uint32_t *>(key_alt + nr);
+  uint32_t *idx_alt = idx + nr, *cnt_s = idx_alt + nr, *dst = cnt_s + nr;
+  const int T = 256;
+  k_iota<<<blocks_for(nr, T), T, 0, st>>>(idx, nr);
+  note_launch();
+  bool alt = false;
+  uint64_t *keys = P<uint64_t>(rkey);
+  if ((e = radix_sort_u64(keys, idx, key_alt, idx_alt, (size_t)nr, 0, 8 + sink_bits, &alt, c.tmp, st)) !=
+      cudaSuccess)
+    return e;
+  if (alt) {
+    keys = key_alt;
+    idx = idx_alt;
+  }
+  k_run_gather<<<blocks_for(nr, T), T, 0, st>>>(idx, P<uint32_t>(rcnt), cnt_s, nr);
+  note_launch();
+  uint64_t *total = P<uint64_t>(c.d_small) + 1;
+  if ((e = scan_u32(cnt_s, dst, total, (size_t)nr, c.offs, st)) != cudaSuccess) return e;
+  unsigned g = blocks_for((size_t)nr, 8);
+  if (g > 152 * 32) g = 152 * 32;
+  k_run_copy<<<g, T, 0, st>>>(keys, idx, P<uint64_t>(rbeg), cnt_s, dst, nr, P<uint64_t>(L), P<uint64_t>(A), csr_beg,
+                              csr_end, csr_mid);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  std::swap(L, A);
+  return cudaSuccess;
+}
+
+// Group both lists by sink (the walk's order kept within a sink) and build CSR
+// bounds; count the particle pairs P2P evaluates.
 cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   cudaError_t e;
 #define TRY(x)                      \
@@ -510,23 +889,30 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   TRY(cudaMemsetAsync(c.p2p_end.p, 0, nn * 4, st));
   int sink_bits = 1;
   while (((int64_t)1 << sink_bits) < nn) ++sink_bits;
-  for (int which = 0; which < 2; ++which) {
-    DBuf &L = which ? c.p2p : c.m2l;
-    DBuf &A = which ? c.p2p_alt : c.m2l_alt;
-    int64_t n = which ? c.np2p : c.nm2l;
-    if (n == 0) continue;
-    TRY(ensure(A, n * 8));
+  TRY(merge_runs(c, c.p2p, c.p2p_alt, c.np2p, c.rp_key, c.rp_beg, c.rp_cnt, c.nrun_p, P<uint32_t>(c.p2p_beg),
+                 P<uint32_t>(c.p2p_end), nullptr, sink_bits, st));
+  const bool tables = c.prm.m2l_precision == 0 && c.prm.m2l_tables && c.tab_k > 0;
+  if (c.nm2l > 0 && !tables) {
+    TRY(merge_runs(c, c.m2l, c.m2l_alt, c.nm2l, c.rm_key, c.rm_beg, c.rm_cnt, c.nrun_m, P<uint32_t>(c.m2l_beg),
+                   P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid), sink_bits, st));
+    if (c.prm.mac_mode == 1) {  // learned orders: stable pass on the order bits -> (order, sink)
+      bool alt = false;
+      TRY(ensure(c.m2l_alt, c.nm2l * 8));
+      TRY(radix_sort_u64(P<uint64_t>(c.m2l), nullptr, P<uint64_t>(c.m2l_alt), nullptr, c.nm2l, kOrderShift, 64,
+                         &alt, c.tmp, st));
+      if (alt) std::swap(c.m2l, c.m2l_alt);
+    }
+  } else if (c.nm2l > 0) {
+    // operator tables: group by (sink, table bit) (learned: (order, sink, table bit))
+    TRY(ensure(c.m2l_alt, c.nm2l * 8));
     bool alt = false;
-    // learned M2L entries carry their order in the top bits: group by (order, sink);
-    // M2L entries are also ordered by the generic bit (table pairs first in each sink)
-    const int hi_bit = (!which && c.prm.mac_mode == 1) ? 64 : kSinkShift + sink_bits;
-    const int lo_bit = which ? kSinkShift : kGenericBit;
-    TRY(radix_sort_u64(P<uint64_t>(L), nullptr, P<uint64_t>(A), nullptr, n, lo_bit, hi_bit, &alt, c.tmp, st));
-    if (alt) std::swap(L, A);
-    if (which || c.prm.mac_mode != 1) {
-      k_list_bounds<<<blocks_for(n, T), T, 0, st>>>(P<uint64_t>(L), 0, n, P<uint32_t>(which ? c.p2p_beg : c.m2l_beg),
-                                                    P<uint32_t>(which ? c.p2p_end : c.m2l_end),
-                                                    which ? nullptr : P<uint32_t>(c.m2l_mid));
+    const int hi_bit = c.prm.mac_mode == 1 ? 64 : kSinkShift + sink_bits;
+    TRY(radix_sort_u64(P<uint64_t>(c.m2l), nullptr, P<uint64_t>(c.m2l_alt), nullptr, c.nm2l, kGenericBit, hi_bit,
+                       &alt, c.tmp, st));
+    if (alt) std::swap(c.m2l, c.m2l_alt);
+    if (c.prm.mac_mode != 1) {
+      k_list_bounds<<<blocks_for(c.nm2l, T), T, 0, st>>>(P<uint64_t>(c.m2l), 0, c.nm2l, P<uint32_t>(c.m2l_beg),
+                                                         P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid));
       note_launch();
       TRY(cudaGetLastError());
     }

@@ -45,7 +45,7 @@ class Stats(C.Structure):
                 ("p2p_particle_pairs", C.c_int64), ("p2p_useful_pairs", C.c_int64), ("launches", C.c_int64),
                 ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
                 ("t_upward", C.c_float), ("t_traverse", C.c_float), ("t_lists", C.c_float), ("t_m2l", C.c_float),
-                ("t_l2l", C.c_float), ("t_p2p", C.c_float), ("nm2l_table", C.c_int64)]
+                ("t_l2l", C.c_float), ("t_p2p", C.c_float), ("nm2l_table", C.c_int64), ("frontier_pairs", C.c_int64)]
 
 
 class HfmmError(RuntimeError):
