@@ -34,7 +34,8 @@ from __future__ import annotations
 import sys
 from math import factorial
 
-SLICES = {1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 2, 7: 4, 8: 8}
+SLICES = {1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 1, 7: 2, 8: 8}  # per-pair operator (registers: D and the contraction)
+TAB_SLICES = {1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 1, 7: 2, 8: 4}  # table operator (contraction only)
 MP_IN_SMEM = {7, 8}  # source multipoles staged per lane in shared memory (register budget)
 
 
@@ -352,7 +353,8 @@ def main(out):
         for g in range(G):
             parts.append(gen_body(P, G, g))
             parts.append("")
-            parts.append(gen_tab_body(P, G, g))
+        for g in range(TAB_SLICES[P]):
+            parts.append(gen_tab_body(P, TAB_SLICES[P], g))
             parts.append("")
     for P in range(1, 9):
         NC = ncoef(P)
@@ -379,8 +381,18 @@ def main(out):
     for P in range(1, 7):
         parts.append(gen_tc(P))
         parts.append("")
-    parts.append("template <int P> struct M2LSlices { static constexpr int G = " +
-                 "(P == 6 ? 2 : (P == 7 ? 4 : (P == 8 ? 8 : 1))); static constexpr bool kSmem = (P >= 7); };")
+    g_expr = "1"
+    for P in sorted(SLICES, reverse=True):
+        if SLICES[P] != 1:
+            g_expr = f"(P == {P} ? {SLICES[P]} : {g_expr})"
+    s_expr = " || ".join(f"P == {P}" for P in sorted(MP_IN_SMEM)) or "false"
+    parts.append("template <int P> struct M2LSlices { static constexpr int G = " + g_expr +
+                 "; static constexpr bool kSmem = (" + s_expr + "); };")
+    t_expr = "1"
+    for P in sorted(TAB_SLICES, reverse=True):
+        if TAB_SLICES[P] != 1:
+            t_expr = f"(P == {P} ? {TAB_SLICES[P]} : {t_expr})"
+    parts.append("template <int P> struct M2LTabSlices { static constexpr int G = " + t_expr + "; };")
     text = "\n".join(parts) + "\n"
     old = None
     try:

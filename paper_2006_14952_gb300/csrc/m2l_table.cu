@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(128) k_m2l_tab(int64_t nn, const uint4 *__rest
 
 template <int P>
 cudaError_t launch(Ctx &c, cudaStream_t st) {
-  constexpr int G = M2LSlices<P>::G;
+  constexpr int G = M2LTabSlices<P>::G;
   unsigned g = blocks_for((size_t)c.nnodes * G, 4);
   if (g > 152 * 64) g = 152 * 64;
   size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float) : 0;

@@ -295,7 +295,7 @@ __device__ __forceinline__ void block_prefixes(const unsigned long long *btot, i
 // Outputs beyond the given capacities set st->overflow and stop the walk; the
 // host grows the buffers and runs it again.
 template <bool kNet>
-__global__ void __launch_bounds__(kTT, kNet ? 2 : 4) k_traverse(const uint4 *__restrict__ cell,
+__global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ cell,
                                                                 const int2 *__restrict__ kids, Mac m, TravBufs B,
                                                                 TravState *__restrict__ st, int max_iters) {
   cg::grid_group grid = cg::this_grid();
