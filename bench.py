@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.3)
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
+    ap.add_argument("--graph", type=int, default=0, help="1: post-traversal phases as one CUDA graph")
+    ap.add_argument("--tuned", default="", help="autotuner cache (JSON) to take the launch shapes from")
     ap.add_argument("--m2l-tables", type=int, default=0, help="1: same-level M2L operators from the (level, offset) table")
     ap.add_argument("--mac", default="geometric", choices=["geometric", "learned"])
     ap.add_argument("--mlp-weights", default=os.path.join(ROOT, "paper_2006_14952_gb300", "weights", "mac_weights.bin"))
@@ -235,9 +237,20 @@ def main():
     # one untimed run of a second context with counting on (bit 1)
     learned = args.mac == "learned"
     mac_kw = dict(mac_mode=1) if learned else {}
+    tiles = {}
+    if args.tuned:
+        from paper_2006_14952_gb300 import autotune
+
+        key = autotune.cache_key(torch.cuda.get_device_name(dev), cfg.name,
+                                 dict(theta=args.theta, order=args.order, leaf_max=cfg.leaf_max,
+                                      mac_mode=1 if learned else 0, m2l_precision=args.m2l_precision,
+                                      m2l_tables=args.m2l_tables, pm_grid=cfg.pm_grid))
+        tiles = autotune.lookup(args.tuned, key) or {}
+    common = dict(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
+                  order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision,
+                  m2l_tables=args.m2l_tables, use_graph=args.graph, **tiles, **mac_kw)
     wts = np.fromfile(args.mlp_weights, dtype=np.uint16) if learned else None
-    s = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                    order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, m2l_tables=args.m2l_tables, profile=1, **mac_kw)
+    s = hfmm.Solver(profile=1, **common)
     if learned:
         s.load_mlp(wts)
     dpos = torch.from_numpy(pos).to(dev)
@@ -254,8 +267,7 @@ def main():
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize()
-    sc = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, m2l_tables=args.m2l_tables, profile=3, **mac_kw)
+    sc = hfmm.Solver(profile=3, **common)
     if learned:
         sc.load_mlp(wts)
     sc.build_tree(dpos, dmass)
@@ -307,8 +319,7 @@ def main():
     pin_pos = torch.from_numpy(pos).pin_memory()
     pin_mass = torch.from_numpy(mass).pin_memory()
     pin_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
-    s2 = hfmm.Solver(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
-                     order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision, m2l_tables=args.m2l_tables, **mac_kw)
+    s2 = hfmm.Solver(**common)
     if learned:
         s2.load_mlp(wts)
     for _ in range(2):
@@ -331,7 +342,11 @@ def main():
     mean = {k: statistics.mean(p[k] for p in phases) for k in keys}
     st = counts
     peak_fp32 = N_SM * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-    if mean["t_p2p"] >= mean["t_m2l"]:
+    if mean["t_p2p"] < 0:  # graph mode: the post-traversal phases are timed as one graph
+        roof = {"kernel": "post-traversal graph (lists, M2L, L2L/L2P, P2P)", "bound": "alu", "achieved": None,
+                "peak": peak_fp32, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "note": "graph mode times the graph as a whole; run without --graph for the P2P roofline"}
+    elif mean["t_p2p"] >= mean["t_m2l"]:
         flops = st["p2p_useful_pairs"] * P2P_FLOPS_PER_PAIR
         achieved = flops / (mean["t_p2p"] / 1e3) / 1e12
         roof = {"kernel": "k_p2p (cut-off P2P)", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
@@ -365,6 +380,7 @@ def main():
                                                               if args.m2l_tables else "")),
                        "theta": args.theta, "order": args.order, "leaf_max": cfg.leaf_max,
                        "transition_rule": 1, "size_rule": 1, "l2": "flushed (512 MB write) before every step",
+                       "graph": bool(args.graph), "tiles": tiles or "defaults",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "accuracy": accuracy,
             "roofline": roof,

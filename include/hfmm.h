@@ -82,6 +82,19 @@ typedef struct {
                           evaluates D: on the 2M-particle clustered set the 224-byte table
                           row per pair costs more than evaluating D (7.1 vs 6.6 ms of M2L).
                           Used by m2l_precision 0 only. */
+  /* Launch shapes (0 = built-in default; results do not depend on them beyond
+     FP32 summation order).  The autotuner (autotune.py) picks them per GPU and
+     workload and stores them in a JSON cache. */
+  int tile_p2p_stage;  /* P2P source particles staged per warp: 128 or 256 (default 256) */
+  int tile_p2p_blocks; /* P2P resident blocks of 256 threads per SM, 1..8 (default 8) */
+  int tile_m2l_blocks; /* cap on M2L blocks of 128 threads, per SM, 1..64 (default 64) */
+  int tile_trav_blocks;/* traversal blocks of 256 threads per SM, 1..4 (default 4; capped by occupancy) */
+  int use_graph;       /* 1 = after the traversal (the last point where the host reads sizes back),
+                          list grouping, M2L, L2L/L2P and P2P are captured as one CUDA graph on a
+                          library stream and launched on the caller's stream; the executable graph
+                          is updated in place while the launch sequence keeps its shape, else
+                          re-instantiated.  Geometric acceptance, m2l_precision 0, profile bit 1
+                          off; otherwise ignored. */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */
@@ -93,7 +106,9 @@ typedef struct {
   int64_t p2p_particle_pairs; /* particle pairs evaluated by P2P incl. masked (profile bit 1, else -1) */
   int64_t p2p_useful_pairs;   /* pairs with 0 < r < R_c (profile bit 1, else -1) */
   int64_t launches;           /* kernels launched by this library in this process so far */
-  /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P */
+  /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P.
+     After a call in graph mode t_lists covers the whole graph (lists, M2L, L2L/L2P, P2P)
+     and t_m2l, t_l2l, t_p2p are -1. */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
   int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
   int64_t frontier_pairs;     /* cell pairs the traversal classified, over all levels */

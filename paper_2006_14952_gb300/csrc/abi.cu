@@ -43,6 +43,12 @@ bool valid_params(const hfmm_params &p, std::string &why) {
     return why = "m2l_precision 1 (3xTF32 tensor cores) supports orders 1..6", false;
   if (p.profile < 0 || p.profile > 3) return why = "profile must be 0..3", false;
   if (p.m2l_tables != 0 && p.m2l_tables != 1) return why = "m2l_tables must be 0 or 1", false;
+  if (p.tile_p2p_stage != 0 && p.tile_p2p_stage != 128 && p.tile_p2p_stage != 256)
+    return why = "tile_p2p_stage must be 0, 128 or 256", false;
+  if (p.tile_p2p_blocks < 0 || p.tile_p2p_blocks > 8) return why = "tile_p2p_blocks must be in 0..8", false;
+  if (p.tile_m2l_blocks < 0 || p.tile_m2l_blocks > 64) return why = "tile_m2l_blocks must be in 0..64", false;
+  if (p.tile_trav_blocks < 0 || p.tile_trav_blocks > 4) return why = "tile_trav_blocks must be in 0..4", false;
+  if (p.use_graph != 0 && p.use_graph != 1) return why = "use_graph must be 0 or 1", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
@@ -185,6 +191,9 @@ void hfmm_destroy(hfmm_ctx *h) {
                   &c.rp_cnt, &c.segpre, &c.ctot};
   for (DBuf *b : bufs) release(*b);
   pm_release(c);
+  if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  if (c.gstream) cudaStreamDestroy(c.gstream);
+  if (c.gready) cudaEventDestroy(c.gready);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
   for (int i = 0; i < 16; ++i)
     if (c.ev[i]) cudaEventDestroy(c.ev[i]);
@@ -209,6 +218,63 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
   if (e != cudaSuccess) return cuda_fail(c, e, "build_tree");
   return HFMM_OK;
 }
+
+namespace {
+
+// List grouping, M2L, L2L/L2P and P2P (no host round trip once the traversal
+// has fixed the sizes) captured on the context's own stream and replayed on
+// `st` as one graph.  With profiling the graph is timed as a whole.
+cudaError_t post_traversal_graph(Ctx &c, float *acc, cudaStream_t st, bool prof) {
+  cudaError_t e;
+  if (!c.gstream && (e = cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if (!c.gready && (e = cudaEventCreateWithFlags(&c.gready, cudaEventDisableTiming)) != cudaSuccess) return e;
+  std::vector<void *> deferred;
+  g_deferred_free = &deferred;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(c.gstream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t r = sort_lists(c, c.gstream);
+    if (r == cudaSuccess) r = m2l_all(c, c.gstream);
+    if (r == cudaSuccess) r = downward(c, acc, c.gstream);
+    if (r == cudaSuccess) r = p2p_pass(c, acc, c.gstream);
+    e = cudaStreamEndCapture(c.gstream, &graph);
+    if (r != cudaSuccess) e = r;
+  }
+  g_deferred_free = nullptr;
+  for (void *p : deferred) cudaFree(p);  // allocations replaced during the capture
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+  }
+  if (c.gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(c.gexec, graph, &info) == cudaSuccess) {
+      ++c.graph_updates;
+    } else {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(c.gexec);
+      c.gexec = nullptr;
+    }
+  }
+  if (!c.gexec) {
+    e = cudaGraphInstantiate(&c.gexec, graph, 0);
+    if (e != cudaSuccess) {
+      c.gexec = nullptr;
+      cudaGraphDestroy(graph);
+      return e;
+    }
+    ++c.graph_instantiations;
+  }
+  cudaGraphDestroy(graph);
+  if (prof) cudaEventRecord(c.ev[6], st);
+  e = cudaGraphLaunch(c.gexec, st);
+  note_launch();
+  if (prof) cudaEventRecord(c.ev[9], st);
+  c.last_graph = true;
+  return e;
+}
+
+}  // namespace
 
 int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (!h) return HFMM_ERR_ARG;
@@ -235,6 +301,12 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "traversal frontier above 2^32 entries");
   if (e != cudaSuccess) return cuda_fail(c, e, "traverse");
   if (prof) cudaEventRecord(c.ev[5], st);
+  c.last_graph = false;
+  if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2)) {
+    e = post_traversal_graph(c, acc, st, prof);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph");
+    return HFMM_OK;
+  }
   if ((e = sort_lists(c, st)) != cudaSuccess) return cuda_fail(c, e, "sort_lists");
   if (prof) cudaEventRecord(c.ev[6], st);
   if (c.prm.m2l_precision == 1 &&
@@ -340,8 +412,15 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   float *t[] = {&o->t_keys_sort, &o->t_tree, &o->t_upward, &o->t_traverse, &o->t_lists, &o->t_m2l, &o->t_l2l,
                 &o->t_p2p};
   const int ev_pairs[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};
+  const int ev_graph[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {6, 9}, {-1, -1}, {-1, -1}, {-1, -1}};
   for (int i = 0; i < 8; ++i) {
     *t[i] = -1.f;
+    if (c.last_graph && ev_graph[i][0] >= 0 && (c.prm.profile & 1) && c.n > 0) {
+      float ms = -1.f;
+      if (cudaEventElapsedTime(&ms, c.ev[ev_graph[i][0]], c.ev[ev_graph[i][1]]) == cudaSuccess) *t[i] = ms;
+      continue;
+    }
+    if (c.last_graph) continue;
     if ((c.prm.profile & 1) && c.n > 0) {
       float ms = -1.f;
       if (cudaEventElapsedTime(&ms, c.ev[ev_pairs[i][0]], c.ev[ev_pairs[i][1]]) == cudaSuccess) *t[i] = ms;

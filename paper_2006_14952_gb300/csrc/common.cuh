@@ -8,6 +8,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/hfmm.h"
 
@@ -96,8 +97,10 @@ struct DBuf {
   size_t cap = 0;
 };
 
-// Grow b to at least `bytes` (contents not kept).
+// Grow b to at least `bytes` (contents not kept).  While *g_deferred_free is set
+// (a stream capture is in progress) the old allocation is queued there instead of freed.
 cudaError_t ensure(DBuf &b, size_t bytes);
+extern thread_local std::vector<void *> *g_deferred_free;
 // Grow b to at least `bytes`, keeping the first `keep` bytes (stream-ordered copy).
 cudaError_t ensure_keep(DBuf &b, size_t bytes, size_t keep, cudaStream_t st);
 void release(DBuf &b);
@@ -215,6 +218,13 @@ struct Ctx {
   DBuf pm_q, pm_rho, pm_mk, pm_ak, pm_a;
   int pm_plan_r2c = -1, pm_plan_c2r = -1;
   const float *mass_ref = nullptr;  // the mass array of the last build_tree
+
+  // graph mode: the post-traversal sequence captured on gstream, replayed on the caller's stream
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gready = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_updates = 0, graph_instantiations = 0;
+  bool last_graph = false;  // the last short_range_forces ran its post-traversal part as a graph
 
   // stats
   int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1, nm2l_table = -1;

@@ -123,7 +123,8 @@ template <int P>
 cudaError_t launch(Ctx &c, cudaStream_t st) {
   constexpr int G = M2LSlices<P>::G;
   unsigned g = blocks_for((size_t)c.nnodes * G, 4);
-  if (g > 152 * 64) g = 152 * 64;
+  const unsigned cap = 152u * (unsigned)(c.prm.tile_m2l_blocks > 0 ? c.prm.tile_m2l_blocks : 64);
+  if (g > cap) g = cap;
   // r / r_s with r in half units: x = r_half * (L / 2^22) / r_s
   const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
   size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float) : 0;

@@ -182,7 +182,8 @@ template <int P>
 cudaError_t launch(Ctx &c, cudaStream_t st) {
   constexpr int G = M2LTabSlices<P>::G;
   unsigned g = blocks_for((size_t)c.nnodes * G, 4);
-  if (g > 152 * 64) g = 152 * 64;
+  const unsigned cap = 152u * (unsigned)(c.prm.tile_m2l_blocks > 0 ? c.prm.tile_m2l_blocks : 64);
+  if (g > cap) g = cap;
   size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float) : 0;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_m2l_tab<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -25,7 +25,6 @@
 namespace hfmm {
 namespace {
 
-constexpr int kCap = 256;  // staged source particles per warp (even)
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
@@ -42,7 +41,8 @@ __device__ __forceinline__ float exp2_mufu(float x) {
   return y;
 }
 
-template <bool kCount>
+// kCap: staged source particles per warp (even)
+template <bool kCount, int kCap>
 __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
                                              const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
                                              const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
@@ -212,12 +212,18 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   if (c.nleaves == 0) return cudaSuccess;
   const int T = 256;
-  unsigned g = 152 * 8;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int per_sm = c.prm.tile_p2p_blocks > 0 ? c.prm.tile_p2p_blocks : 8;
+  unsigned g = (unsigned)(nsm * per_sm);
   if ((size_t)g * 8 > (size_t)c.nleaves) g = blocks_for(c.nleaves, 8);
-  auto kern = (c.prm.profile & 2) ? k_p2p<true> : k_p2p<false>;
+  const bool small = c.prm.tile_p2p_stage == 128, count = (c.prm.profile & 2) != 0;
+  auto kern = count ? (small ? k_p2p<true, 128> : k_p2p<true, 256>) : (small ? k_p2p<false, 128> : k_p2p<false, 256>);
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
-  cudaError_t e = cudaMemsetAsync(ctr, 0, 8, st);
+  e = cudaMemsetAsync(ctr, 0, 8, st);
   if (e != cudaSuccess) return e;
   kern<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,

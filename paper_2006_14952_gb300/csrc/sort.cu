@@ -1,14 +1,22 @@
 // Device primitives: buffer growth, exclusive scan and a stable LSD radix sort.
 // Used by the tree build (Morton-key sort) and the list grouping by sink.
+#include <vector>
+
 #include "common.cuh"
 
 namespace hfmm {
 
 std::atomic<long long> g_launches{0};
+thread_local std::vector<void *> *g_deferred_free = nullptr;
 
 cudaError_t ensure(DBuf &b, size_t bytes) {
   if (bytes <= b.cap) return cudaSuccess;
   size_t want = bytes + bytes / 4 + 256;
+  if (b.p && g_deferred_free) {  // stream capture in progress: free after it ends
+    g_deferred_free->push_back(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
   if (b.p) {
     cudaError_t e = cudaFree(b.p);
     b.p = nullptr;

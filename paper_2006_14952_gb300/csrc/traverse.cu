@@ -692,7 +692,8 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   const void *kern = net ? (const void *)k_traverse<true> : (const void *)k_traverse<false>;
   TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, net ? k_traverse<true> : k_traverse<false>, kTT, 0));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const unsigned nb = (unsigned)(nsm * (per_sm < 4 ? per_sm : 4));
+  const int want = c.prm.tile_trav_blocks > 0 ? c.prm.tile_trav_blocks : 4;
+  const unsigned nb = (unsigned)(nsm * (per_sm < want ? per_sm : want));
   TRY(ensure(c.btot2, (size_t)nb * 4 * sizeof(unsigned long long)));
   // capacities: the last call's sizes with head-room, at least a few per node
   auto grow = [](uint64_t want) { return want + want / 4 + 1024; };

@@ -36,7 +36,9 @@ class Params(C.Structure):
     _fields_ = [("box", C.c_double), ("pm_grid", C.c_int), ("rs_cells", C.c_double), ("rcut_rs", C.c_double),
                 ("G", C.c_double), ("theta", C.c_double), ("order", C.c_int), ("leaf_max", C.c_int),
                 ("mac_mode", C.c_int), ("transition_rule", C.c_int), ("size_rule", C.c_int),
-                ("m2l_precision", C.c_int), ("profile", C.c_int), ("m2l_tables", C.c_int)]
+                ("m2l_precision", C.c_int), ("profile", C.c_int), ("m2l_tables", C.c_int),
+                ("tile_p2p_stage", C.c_int), ("tile_p2p_blocks", C.c_int), ("tile_m2l_blocks", C.c_int),
+                ("tile_trav_blocks", C.c_int), ("use_graph", C.c_int)]
 
 
 class Stats(C.Structure):
