@@ -543,10 +543,19 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
         if (c == kM2L)
           B.m2l[nm + B.ctot[3 * k + 1] + x[1] - v[1]] = with_order(e, (cc >> 3) & 15) | ((uint64_t)(cc >> 7) << kGenericBit);
         if (c == kP2P) B.p2p[np + B.ctot[3 * k + 2] + x[2] - v[2]] = e;
+      }
+      // child pairs: each open pair's outputs, flattened over the warp so that every
+      // lane writes (the open pairs are a few percent of the frontier)
+      uint32_t nout = 0, nbk = 1, a0 = 0, b0 = 0, shv = 0, Cs = 0;
+      unsigned long long p0 = 0;
+      if (valid) {
+        const uint8_t c = cc & 7;
         if (c == kOpenA || c == kOpenB || c == kOpenAB) {
-          const uint32_t a = pair_sink(e), b = pair_src(e), s = pair_shift(e);
+          const uint32_t a = pair_sink(e), b = pair_src(e);
+          shv = pair_shift(e);
           const SegBase sb = B.base[cmap[a]];
-          const unsigned long long p0 = sb.o + (B.ctot[3 * k] + x[0] - v[0] - sb.c);
+          p0 = sb.o + (B.ctot[3 * k] + x[0] - v[0] - sb.c);
+          Cs = sb.C;
           // the last slot this item writes; beyond the next frontier means inconsistent bases
           const unsigned long long last =
               c == kOpenB ? p0 + kb.y : p0 + (unsigned long long)(ka.y - 1) * sb.C + (c == kOpenA ? 1 : kb.y);
@@ -554,17 +563,52 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
           if (bad) {
             st->overflow = 2;  // refuse rather than write out of place
           } else if (c == kOpenB) {  // the sink is a leaf: one next-level segment
-            for (int q = 0; q < kb.y; ++q) nxt[p0 + q] = pack_pair(a, (uint32_t)kb.x + (uint32_t)q, s);
+            nout = (uint32_t)kb.y;
+            nbk = (uint32_t)kb.y;
+            a0 = a;
+            b0 = (uint32_t)kb.x;
           } else {
-            const int nbk = c == kOpenA ? 1 : kb.y;
-            for (int i = 0; i < ka.y; ++i) {
-              const unsigned long long pi = p0 + (unsigned long long)i * sb.C;
-              for (int q = 0; q < nbk; ++q)
-                nxt[pi + q] =
-                    pack_pair((uint32_t)ka.x + (uint32_t)i, c == kOpenA ? b : (uint32_t)kb.x + (uint32_t)q, s);
-            }
+            nbk = c == kOpenA ? 1u : (uint32_t)kb.y;
+            nout = (uint32_t)ka.y * nbk;
+            a0 = (uint32_t)ka.x;
+            b0 = c == kOpenA ? b : (uint32_t)kb.x;
           }
         }
+      }
+      // many open pairs in the chunk: every lane has work, each writes its own outputs
+      if (__popc(__ballot_sync(0xffffffffu, nout > 0)) > 4) {
+        for (uint32_t r = 0; r < nout; ++r) {
+          const uint32_t i = r / nbk, q = r - i * nbk;
+          nxt[p0 + (unsigned long long)i * Cs + q] = pack_pair(a0 + i, b0 + q, shv);
+        }
+        continue;
+      }
+      // a few open pairs: flatten their outputs over the warp
+      uint32_t oin = nout;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, oin, o);
+        if (lane >= o) oin += y;
+      }
+      const uint32_t oex = oin - nout, ototal = __shfl_sync(0xffffffffu, oin, 31);
+      // 2^16 / nbk rounded up: r / nbk = (r * inv) >> 16 exactly for r < 64, nbk <= 8
+      const uint32_t inv = (65536u + nbk - 1) / nbk;
+      for (uint32_t jb = 0; jb < ototal; jb += 32) {  // uniform trip count: every lane shuffles
+        const uint32_t j = jb + lane;
+        int src = 0;  // the last lane whose outputs start at or before j
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const uint32_t ex = __shfl_sync(0xffffffffu, oex, src + step);
+          if (ex <= j) src += step;
+        }
+        const uint32_t r = j - __shfl_sync(0xffffffffu, oex, src);
+        const uint32_t snbk = __shfl_sync(0xffffffffu, nbk, src), sinv = __shfl_sync(0xffffffffu, inv, src);
+        const uint32_t sa0 = __shfl_sync(0xffffffffu, a0, src), sb0 = __shfl_sync(0xffffffffu, b0, src);
+        const uint32_t ssh = __shfl_sync(0xffffffffu, shv, src), sC = __shfl_sync(0xffffffffu, Cs, src);
+        const unsigned long long sp0 = __shfl_sync(0xffffffffu, p0, src);
+        const uint32_t i = (r * sinv) >> 16, q = r - i * snbk;
+        // open A: b0 fixed, q = 0; open B: i = 0 (one child block); open both: child i, source q
+        if (j < ototal) nxt[sp0 + (unsigned long long)i * sC + q] = pack_pair(sa0 + i, sb0 + q, ssh);
       }
     }
     __syncthreads();  // every thread is done with this level's state
