@@ -118,18 +118,37 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
             // slot p belongs to the last entry whose offset is <= p
             const uint32_t all = __shfl_sync(0xffffffffu, incl, 31);
             const uint32_t tot = all < room ? all : room;
-            for (uint32_t p = lane; p < tot; p += 32) {
-              int o = 0;
+            // four slots per lane per step: the four binary searches first, then four
+            // independent particle loads in flight, then the stores
+            for (uint32_t pb = lane; pb < tot; pb += 128) {
+              int own[4];
+              uint32_t idx[4];
 #pragma unroll
-              for (int step = 16; step; step >>= 1)
-                if (e_excl[wid][o + step] <= p) o += step;
-              const float4 s4 = pm4[e_src[wid][o] + (p - e_excl[wid][o])];
-              const uint32_t slot = (uint32_t)fill + p;
-              float *a = bf + (slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
-              a[0] = -(s4.x + e_off[wid][0][o]);
-              a[2] = -(s4.y + e_off[wid][1][o]);
-              a[4] = -(s4.z + e_off[wid][2][o]);
-              a[6] = -s4.w;
+              for (int u = 0; u < 4; ++u) {
+                const uint32_t p = pb + 32 * u;
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step; step >>= 1)
+                  if (e_excl[wid][o + step] <= p) o += step;
+                own[u] = o;
+                idx[u] = p < tot ? e_src[wid][o] + (p - e_excl[wid][o]) : 0u;
+              }
+              float4 s4[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (pb + 32 * u < tot) s4[u] = pm4[idx[u]];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const uint32_t p = pb + 32 * u;
+                if (p < tot) {
+                  const uint32_t slot = (uint32_t)fill + p;
+                  float *a = bf + (slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
+                  a[0] = -(s4[u].x + e_off[wid][0][own[u]]);
+                  a[2] = -(s4[u].y + e_off[wid][1][own[u]]);
+                  a[4] = -(s4[u].z + e_off[wid][2][own[u]]);
+                  a[6] = -s4[u].w;
+                }
+              }
             }
           }
           __syncwarp();  // the entry table is rewritten by the next step
