@@ -9,6 +9,29 @@
 namespace hfmm {
 namespace {
 
+// Row of NC floats at a 16-byte aligned address (rows are padded to a multiple of 4).
+template <int NC>
+__device__ __forceinline__ void load_row(const float *__restrict__ src, float (&r)[NC]) {
+  const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+  for (int q = 0; q < (NC + 3) / 4; ++q) {
+    const float4 v = __ldg(s4 + q);
+    if (4 * q + 0 < NC) r[4 * q + 0] = v.x;
+    if (4 * q + 1 < NC) r[4 * q + 1] = v.y;
+    if (4 * q + 2 < NC) r[4 * q + 2] = v.z;
+    if (4 * q + 3 < NC) r[4 * q + 3] = v.w;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void store_row(float *__restrict__ dst, const float (&r)[NC]) {
+  float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+  for (int q = 0; q < NC / 4; ++q) d4[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+#pragma unroll
+  for (int c = NC / 4 * 4; c < NC; ++c) dst[c] = r[c];
+}
+
 // P2M, one thread per leaf: M~_m = sum_a mu_a (-1)^|m| / m! (u_a)^m, u = (x - z) / h.
 template <int P>
 __global__ void k_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
@@ -28,9 +51,7 @@ __global__ void k_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uin
     P2MBody<P>::run(q.x * inv_h, q.y * inv_h, q.z * inv_h, q.w, acc);
   }
   P2MBody<P>::finish(acc);
-  float *o = M + (size_t)k * ldm;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) o[c] = acc[c];
+  store_row<NC>(M + (size_t)k * ldm, acc);
 }
 
 // M2M, one thread per cell of one level: sum of its children's shifted multipoles.
@@ -49,34 +70,35 @@ __global__ void k_m2m(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, c
   for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
     const uint4 cc = cell[ch];
     // (z_P - z_C) / H = +1/4 for the lower half of an axis, -1/4 for the upper
-    M2MBody<P>::run((cc.x & 1u) ? -1.f : 1.f, (cc.y & 1u) ? -1.f : 1.f, (cc.z & 1u) ? -1.f : 1.f,
-                    M + (size_t)ch * ldm, o);
+    float ci[NC];
+    load_row<NC>(M + (size_t)ch * ldm, ci);
+    M2MBody<P>::run((cc.x & 1u) ? -1.f : 1.f, (cc.y & 1u) ? -1.f : 1.f, (cc.z & 1u) ? -1.f : 1.f, ci, o);
   }
-  float *dst = M + (size_t)k * ldm;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) dst[c] = o[c];
+  store_row<NC>(M + (size_t)k * ldm, o);
 }
 
-// L2L, one thread per cell of one level: add its local expansion to each child's.
+// L2L, one thread per (cell of one level, child slot): the child's local
+// expansion plus the parent's translated to the child's centre.  The eight
+// siblings of a parent are neighbouring threads (one parent row load, shared).
 template <int P>
 __global__ void k_l2l(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int ldm,
                       float *__restrict__ L) {
   constexpr int NC = ncoef(P);
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  const int64_t k = lo + t;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 8 * cnt) return;
+  const int64_t k = lo + t / 8;
   const int2 kd = kids[k];
-  if (kd.y == 0) return;
-  float pl[NC];
-  const float *src = L + (size_t)k * ldm;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) pl[c] = src[c];
-  for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
-    const uint4 cc = cell[ch];
-    // (z_C - z_P) / H = -1/4 for the lower half of an axis, +1/4 for the upper
-    L2LBody<P>::run((cc.x & 1u) ? 1.f : -1.f, (cc.y & 1u) ? 1.f : -1.f, (cc.z & 1u) ? 1.f : -1.f, pl,
-                    L + (size_t)ch * ldm);
-  }
+  const int slot = (int)(t % 8);
+  if (slot >= kd.y) return;
+  const int ch = kd.x + slot;
+  float pl[NC], cl[NC];
+  load_row<NC>(L + (size_t)k * ldm, pl);
+  float *dst = L + (size_t)ch * ldm;
+  load_row<NC>(dst, cl);
+  const uint4 cc = cell[ch];
+  // (z_C - z_P) / H = -1/4 for the lower half of an axis, +1/4 for the upper
+  L2LBody<P>::run((cc.x & 1u) ? 1.f : -1.f, (cc.y & 1u) ? 1.f : -1.f, (cc.z & 1u) ? 1.f : -1.f, pl, cl);
+  store_row<NC>(dst, cl);
 }
 
 // L2P, one thread per leaf: a = G h^-2 sum L~_{n+e_d} u^n / n!, written in input order.
@@ -92,9 +114,7 @@ __global__ void k_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uin
   const float inv_h = (float)(1u << cell[k].w) / box;
   const float s = G * inv_h * inv_h;
   float l[NC];
-  const float *src = L + (size_t)k * ldm;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) l[c] = src[c];
+  load_row<NC>(L + (size_t)k * ldm, l);
   for (uint32_t i = r.x; i < r.x + r.y; ++i) {
     const float4 q = pm4[i];
     float ax = 0.f, ay = 0.f, az = 0.f;
@@ -126,7 +146,8 @@ cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st) {
   const int T = 128;
   for (int l = 0; l + 1 < c.nlevels; ++l) {
     int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    k_l2l<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm, hfmm::P<float>(c.L));
+    k_l2l<P><<<blocks_for(8 * cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm,
+                                                   hfmm::P<float>(c.L));
     note_launch();
   }
   k_l2p<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell),

@@ -192,11 +192,11 @@ def gen_passes(P):
     out.append("\n".join(L))
     # ---- M2M
     L = [f"template <> struct M2MBody<{P}> {{",
-         f"  static __device__ __forceinline__ void run(float sx, float sy, float sz, const float *__restrict__ in,"
+         f"  static __device__ __forceinline__ void run(float sx, float sy, float sz, const float (&in)[{NC}],"
          f" float (&o)[{NC}]) {{"]
     for a in ms:
         k = idx(a)
-        L.append(f"    const float i{k} = __ldg(in + {k}) * {2.0 ** -sum(a)!r}f;")
+        L.append(f"    const float i{k} = in[{k}] * {2.0 ** -sum(a)!r}f;")
     for a in ms:
         if a == (0, 0, 0):
             continue
@@ -216,7 +216,7 @@ def gen_passes(P):
     # ---- L2L
     L = [f"template <> struct L2LBody<{P}> {{",
          f"  static __device__ __forceinline__ void run(float sx, float sy, float sz, const float (&p)[{NC}],"
-         f" float *__restrict__ child) {{"]
+         f" float (&child)[{NC}]) {{"]
     for a in ms:
         if a == (0, 0, 0):
             continue
