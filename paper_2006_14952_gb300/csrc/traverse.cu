@@ -222,6 +222,11 @@ struct TravBufs {
 };
 
 constexpr int kTT = 256;  // threads of the traversal kernel
+// a chunk with at most this many open pairs writes their child pairs warp-flattened
+#ifndef HFMM_FLATTEN
+#define HFMM_FLATTEN 16
+#endif
+constexpr int kFlatten = HFMM_FLATTEN;
 constexpr int kTW = kTT / 32;
 
 // Exclusive block-wide prefix of one value per thread (all threads call it);
@@ -575,10 +580,12 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
           }
         }
       }
+      // 2^16 / nbk rounded up: r / nbk = (r * inv) >> 16 exactly for r < 64, nbk <= 8
+      const uint32_t inv = (65536u + nbk - 1) / nbk;
       // many open pairs in the chunk: every lane has work, each writes its own outputs
-      if (__popc(__ballot_sync(0xffffffffu, nout > 0)) > 4) {
+      if (__popc(__ballot_sync(0xffffffffu, nout > 0)) > kFlatten) {
         for (uint32_t r = 0; r < nout; ++r) {
-          const uint32_t i = r / nbk, q = r - i * nbk;
+          const uint32_t i = (r * inv) >> 16, q = r - i * nbk;
           nxt[p0 + (unsigned long long)i * Cs + q] = pack_pair(a0 + i, b0 + q, shv);
         }
         continue;
@@ -591,8 +598,6 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
         if (lane >= o) oin += y;
       }
       const uint32_t oex = oin - nout, ototal = __shfl_sync(0xffffffffu, oin, 31);
-      // 2^16 / nbk rounded up: r / nbk = (r * inv) >> 16 exactly for r < 64, nbk <= 8
-      const uint32_t inv = (65536u + nbk - 1) / nbk;
       for (uint32_t jb = 0; jb < ototal; jb += 32) {  // uniform trip count: every lane shuffles
         const uint32_t j = jb + lane;
         int src = 0;  // the last lane whose outputs start at or before j
