@@ -80,8 +80,13 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
   }
 }
 
+// resident blocks of 128 threads per SM the register budget allows without
+// spilling, by order (measured with -Xptxas -v: p <= 4 at 128, p = 5 at 168 registers)
+template <int P>
+constexpr int m2l_min_blocks() { return P <= 4 ? 4 : P == 5 ? 3 : 2; }
+
 template <int P, int G>
-__global__ void __launch_bounds__(128) k_m2l(int64_t nn, const uint4 *__restrict__ cell,
+__global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_m2l(int64_t nn, const uint4 *__restrict__ cell,
                                              const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
                                              const uint64_t *__restrict__ lst, const float *__restrict__ M,
                                              float *__restrict__ L, int ldm, float inv_rs) {
