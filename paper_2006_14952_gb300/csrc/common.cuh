@@ -171,7 +171,8 @@ struct Ctx {
   DBuf range;   // uint2 {first, count}
   DBuf kids;    // int2 {first child or -1, child count}
   DBuf leaves;  // u32 [nleaves] node index of each leaf
-  DBuf bounds, nkids, koff;  // build scratch
+  DBuf bounds, nkids, koff, tstate;  // build scratch
+  uint64_t cap_nodes = 0;
 
   // traversal
   DBuf front, front_next, cls, counts, offs;

@@ -2,10 +2,16 @@
 // periodic wrap, 63-bit Morton keys, stable key sort, level-synchronous split
 // of cells holding more than leaf_max particles, and per-particle FP32
 // offsets from the geometric centre of the leaf.
+#include <cooperative_groups.h>
+
+#include <cstring>
+
 #include "common.cuh"
 
 namespace hfmm {
 namespace {
+
+namespace cg = cooperative_groups;
 
 // x - L floor(x / L), each operation rounded separately (no FMA contraction).
 __device__ __forceinline__ double wrap_box(double x, double box) {
@@ -51,82 +57,10 @@ __global__ void k_gather(const double *__restrict__ pos, const uint32_t *__restr
   xs[2 * n + s] = wrap_box(pos[2 * n + i], box);
 }
 
-__global__ void k_root(uint4 *cell, uint2 *range, int64_t n) {
-  cell[0] = make_uint4(0, 0, 0, 0);
-  range[0] = make_uint2(0, (uint32_t)n);
-}
 
-// For each node of one level: child boundaries by binary search on the sorted
-// keys (the octant digit is monotone inside the parent's range).
-__global__ void k_split_count(const uint2 *__restrict__ range, int64_t lo, int64_t cnt, int level, int leaf_max,
-                              const uint64_t *__restrict__ key, uint32_t *__restrict__ bounds,
-                              uint32_t *__restrict__ nk) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  uint2 r = range[lo + t];
-  if ((int)r.y <= leaf_max || level >= kDepth) {
-    nk[t] = 0;
-    return;
-  }
-  const int shift = 3 * (kDepth - level - 1);
-  uint32_t b[9];
-  b[0] = r.x;
-  b[8] = r.x + r.y;
-  for (uint32_t o = 1; o < 8; ++o) {
-    uint32_t a = b[o - 1], e = r.x + r.y;  // first index with digit >= o
-    while (a < e) {
-      uint32_t m = a + (e - a) / 2;
-      if (((uint32_t)(key[m] >> shift) & 7u) < o)
-        a = m + 1;
-      else
-        e = m;
-    }
-    b[o] = a;
-  }
-  uint32_t c = 0;
-  for (int o = 0; o < 8; ++o) {
-    bounds[t * 9 + o] = b[o];
-    c += b[o + 1] > b[o];
-  }
-  bounds[t * 9 + 8] = b[8];
-  nk[t] = c;
-}
 
-__global__ void k_emit_children(int64_t lo, int64_t cnt, int64_t next_lo, const uint32_t *__restrict__ bounds,
-                                const uint32_t *__restrict__ nk, const uint32_t *__restrict__ koff,
-                                uint4 *__restrict__ cell, uint2 *__restrict__ range, int2 *__restrict__ kids) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  int64_t k = lo + t;
-  uint32_t c = nk[t];
-  if (c == 0) {
-    kids[k] = make_int2(-1, 0);
-    return;
-  }
-  int64_t base = next_lo + koff[t];
-  kids[k] = make_int2((int)base, (int)c);
-  uint4 pc = cell[k];
-  uint32_t q = 0;
-  for (uint32_t o = 0; o < 8; ++o) {
-    uint32_t b0 = bounds[t * 9 + o], b1 = bounds[t * 9 + o + 1];
-    if (b1 > b0) {
-      cell[base + q] = make_uint4(2 * pc.x + ((o >> 2) & 1u), 2 * pc.y + ((o >> 1) & 1u), 2 * pc.z + (o & 1u), pc.w + 1);
-      range[base + q] = make_uint2(b0, b1 - b0);
-      ++q;
-    }
-  }
-}
 
-__global__ void k_leaf_flags(const int2 *__restrict__ kids, int64_t nn, uint32_t *__restrict__ flag) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nn) flag[k] = kids[k].y == 0;
-}
 
-__global__ void k_leaf_list(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ off, int64_t nn,
-                            uint32_t *__restrict__ leaves) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nn && flag[k]) leaves[off[k]] = (uint32_t)k;
-}
 
 // FP64 offset from the geometric leaf centre, rounded once to FP32.
 __global__ void k_leaf_offsets(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
@@ -142,6 +76,208 @@ __global__ void k_leaf_offsets(const uint32_t *__restrict__ leaves, int64_t nl, 
   double zx = ((double)c.x + 0.5) * h, zy = ((double)c.y + 0.5) * h, zz = ((double)c.z + 0.5) * h;
   for (uint32_t i = r.x; i < r.x + r.y; ++i) {
     pm4[i] = make_float4((float)(xs[i] - zx), (float)(xs[n + i] - zy), (float)(xs[2 * n + i] - zz), mass[perm[i]]);
+  }
+}
+
+struct TreeState {
+  unsigned long long total, nleaves;
+  int nlevels, overflow;
+  unsigned long long level_start[kDepth + 3];
+};
+
+constexpr int kBT = 256;
+
+
+// Level-synchronous octree build in one cooperative launch (Sec. 2.1 tree, as a
+// Morton octree): per level every node with more than leaf_max particles (and
+// above the depth cap) is split at the octant boundaries of the sorted keys;
+// a grid-wide scan of the child counts places the children breadth-first (key
+// order within a level) and a scan of the leaf flags lists the leaves.  The
+// sizes stay on the device; the host reads them once at the end.
+__global__ void __launch_bounds__(kBT) k_tree_levels(const uint64_t *__restrict__ key, int64_t n, int leaf_max,
+                                                     uint4 *__restrict__ cell, uint2 *__restrict__ range,
+                                                     int2 *__restrict__ kids, uint32_t *__restrict__ leaves,
+                                                     unsigned long long capN, uint32_t *__restrict__ nk,
+                                                     uint32_t *__restrict__ bnd, unsigned long long *__restrict__ btot,
+                                                     TreeState *__restrict__ st) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ unsigned long long lo, cnt, total, nleaves;
+  __shared__ unsigned long long wsum[kBT / 32][2], pre[2], all[2], run[2];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const unsigned nb = gridDim.x, bid = blockIdx.x;
+  if (bid == 0 && tid == 0) {
+    cell[0] = make_uint4(0, 0, 0, 0);
+    range[0] = make_uint2(0, (uint32_t)n);
+    st->level_start[0] = 0;
+  }
+  if (tid == 0) {
+    lo = 0;
+    cnt = 1;
+    total = 1;
+    nleaves = 0;
+  }
+  __syncthreads();
+  grid.sync();
+  int level = 0;
+  for (; level <= kDepth; ++level) {
+    const unsigned long long L0 = lo, C = cnt, T0 = total, N0 = nleaves;
+    const unsigned long long ch = (C + nb - 1) / nb;
+    const unsigned long long blo = ch * bid < C ? ch * bid : C, bhi = blo + ch < C ? blo + ch : C;
+    // phase A: eight lanes per node, lane o finds the first key with octant digit >= o
+    // (independent searches over the node's range); child counts and block sums
+    unsigned long long sc = 0, sl = 0;
+    for (unsigned long long tb = 8 * blo; tb < 8 * bhi; tb += kBT) {  // uniform trip count (shuffles)
+      const unsigned long long tt = tb + tid, t = tt / 8;
+      const uint32_t o = (uint32_t)(tt % 8);
+      const bool valid = tt < 8 * bhi;
+      uint2 r = make_uint2(0, 0);
+      bool split = false;
+      if (valid) {
+        r = range[L0 + t];
+        split = (int)r.y > leaf_max && level < kDepth;
+      }
+      uint32_t bo = r.x;
+      if (split && o > 0) {
+        const int shift = 3 * (kDepth - level - 1);
+        uint32_t a = r.x, e = r.x + r.y;
+        while (a < e) {
+          const uint32_t mid = a + (e - a) / 2;
+          if (((uint32_t)(key[mid] >> shift) & 7u) < o)
+            a = mid + 1;
+          else
+            e = mid;
+        }
+        bo = a;
+      }
+      // boundary o + 1 from the next lane of the group (the last lane: the range end)
+      uint32_t bn = __shfl_down_sync(0xffffffffu, bo, 1, 8);
+      if (o == 7) bn = r.x + r.y;
+      const uint32_t nonempty = split && bn > bo ? 1u : 0u;
+      uint32_t c = nonempty;
+      c += __shfl_xor_sync(0xffffffffu, c, 1, 8);
+      c += __shfl_xor_sync(0xffffffffu, c, 2, 8);
+      c += __shfl_xor_sync(0xffffffffu, c, 4, 8);
+      if (valid) {
+        bnd[9 * t + o] = bo;
+        if (o == 7) bnd[9 * t + 8] = r.x + r.y;
+        if (o == 0) {
+          nk[t] = c;
+          sc += c;
+          sl += c == 0;
+        }
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      sc += __shfl_xor_sync(0xffffffffu, sc, o);
+      sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    }
+    if (lane == 0) {
+      wsum[wp][0] = sc;
+      wsum[wp][1] = sl;
+    }
+    __syncthreads();
+    if (tid < 2) {
+      unsigned long long v = 0;
+      for (int q = 0; q < kBT / 32; ++q) v += wsum[q][tid];
+      btot[2 * bid + tid] = v;
+    }
+    __threadfence();
+    grid.sync();
+    // phase B: block prefixes, then each node's children and leaf slot
+    if (tid < 2) {
+      unsigned long long b = 0, a = 0;
+      for (unsigned q = 0; q < nb; ++q) {
+        const unsigned long long v = btot[2 * q + tid];
+        if (q < bid) b += v;
+        a += v;
+      }
+      pre[tid] = b;
+      all[tid] = a;
+      run[tid] = b;
+    }
+    __syncthreads();
+    const unsigned long long Cn = all[0], Ln = all[1];
+    if (T0 + Cn > capN) {
+      if (bid == 0 && tid == 0) st->overflow = 1;
+      break;  // every block takes the same decision
+    }
+    for (unsigned long long tb = blo; tb < bhi; tb += kBT) {
+      const unsigned long long t = tb + tid;
+      const bool valid = t < bhi;
+      const uint32_t c = valid ? nk[t] : 0u;
+      const unsigned long long lf = valid && c == 0 ? 1ull : 0ull;
+      unsigned long long xc = c, xl = lf;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long yc = __shfl_up_sync(0xffffffffu, xc, o), yl = __shfl_up_sync(0xffffffffu, xl, o);
+        if (lane >= o) {
+          xc += yc;
+          xl += yl;
+        }
+      }
+      if (lane == 31) {
+        wsum[wp][0] = xc;
+        wsum[wp][1] = xl;
+      }
+      __syncthreads();
+      unsigned long long wc = 0, wl = 0, tc = 0, tl = 0;
+      for (int q = 0; q < kBT / 32; ++q) {
+        if (q < wp) {
+          wc += wsum[q][0];
+          wl += wsum[q][1];
+        }
+        tc += wsum[q][0];
+        tl += wsum[q][1];
+      }
+      if (valid) {
+        const unsigned long long k = L0 + t;
+        if (c == 0) {
+          kids[k] = make_int2(-1, 0);
+          leaves[N0 + run[1] + wl + xl - lf] = (uint32_t)k;
+        } else {
+          const unsigned long long base = T0 + run[0] + wc + xc - c;
+          kids[k] = make_int2((int)base, (int)c);
+          const uint4 pc = cell[k];
+          uint32_t b[9];
+#pragma unroll
+          for (int o = 0; o < 9; ++o) b[o] = bnd[9 * t + o];
+          uint32_t q = 0;
+          for (uint32_t o = 0; o < 8; ++o) {
+            if (b[o + 1] > b[o]) {
+              cell[base + q] = make_uint4(2 * pc.x + ((o >> 2) & 1u), 2 * pc.y + ((o >> 1) & 1u), 2 * pc.z + (o & 1u),
+                                          pc.w + 1);
+              range[base + q] = make_uint2(b[o], b[o + 1] - b[o]);
+              ++q;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        run[0] += tc;
+        run[1] += tl;
+      }
+      __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      lo = T0;
+      cnt = Cn;
+      total = T0 + Cn;
+      nleaves = N0 + Ln;
+    }
+    if (bid == 0 && tid == 0) st->level_start[level + 1] = T0;  // start of level + 1 (or the end)
+    grid.sync();
+    if (Cn == 0) {
+      ++level;
+      break;
+    }
+  }
+  if (bid == 0 && tid == 0) {
+    st->total = total;
+    st->nleaves = nleaves;
+    st->nlevels = level;
   }
 }
 
@@ -186,65 +322,53 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   k_gather<<<blocks_for(n, T), T, 0, st>>>(pos, perm, n, c.prm.box, P<double>(c.xs));
   note_launch();
 
-  // level-synchronous node build
-  size_t cap_nodes = (size_t)(2 * n / (c.prm.leaf_max > 1 ? c.prm.leaf_max : 1) + 64);
-  TRY(ensure(c.cell, cap_nodes * sizeof(uint4)));
-  TRY(ensure(c.range, cap_nodes * sizeof(uint2)));
-  TRY(ensure(c.kids, cap_nodes * sizeof(int2)));
-  k_root<<<1, 1, 0, st>>>(P<uint4>(c.cell), P<uint2>(c.range), n);
-  note_launch();
-  int64_t lo = 0, cnt = 1, total = 1;
-  int level = 0;
-  c.level_start[0] = 0;
-  uint64_t *d_tot = P<uint64_t>(c.d_small);
-  for (;;) {
-    TRY(ensure(c.bounds, cnt * 9 * sizeof(uint32_t)));
-    TRY(ensure(c.nkids, cnt * sizeof(uint32_t)));
-    TRY(ensure(c.koff, cnt * sizeof(uint32_t)));
-    k_split_count<<<blocks_for(cnt, T), T, 0, st>>>(P<uint2>(c.range), lo, cnt, level, c.prm.leaf_max, key,
-                                                    P<uint32_t>(c.bounds), P<uint32_t>(c.nkids));
+  // octree levels: one cooperative launch; node capacity from the last build, grown on overflow
+  if (c.cap_nodes < (uint64_t)(2 * n / (c.prm.leaf_max > 1 ? c.prm.leaf_max : 1) + 64))
+    c.cap_nodes = (uint64_t)(2 * n / (c.prm.leaf_max > 1 ? c.prm.leaf_max : 1) + 64);
+  int dev = 0, nsm = 0, per_sm = 0;
+  TRY(cudaGetDevice(&dev));
+  TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_levels, kBT, 0));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const unsigned nb = (unsigned)(nsm * (per_sm < 2 ? per_sm : 2));
+  TreeState hs{};
+  TreeState *dst = reinterpret_cast<TreeState *>(c.tstate.p);
+  TRY(ensure(c.tstate, sizeof(TreeState)));
+  dst = reinterpret_cast<TreeState *>(c.tstate.p);
+  TRY(ensure(c.bounds, (size_t)nb * 2 * sizeof(unsigned long long)));
+  for (int attempt = 0;; ++attempt) {
+    if (attempt == 8) return cudaErrorInvalidValue;
+    const unsigned long long capN = c.cap_nodes;
+    TRY(ensure(c.cell, capN * sizeof(uint4)));
+    TRY(ensure(c.range, capN * sizeof(uint2)));
+    TRY(ensure(c.kids, capN * sizeof(int2)));
+    TRY(ensure(c.leaves, capN * sizeof(uint32_t)));
+    TRY(ensure(c.nkids, capN * sizeof(uint32_t)));
+    TRY(ensure(c.koff, capN * 9 * sizeof(uint32_t)));  // octant boundaries of a level's nodes
+    TRY(cudaMemsetAsync(dst, 0, sizeof(TreeState), st));
+    uint4 *cl = P<uint4>(c.cell);
+    uint2 *rg = P<uint2>(c.range);
+    int2 *kd = P<int2>(c.kids);
+    uint32_t *lv = P<uint32_t>(c.leaves), *nkp = P<uint32_t>(c.nkids), *bd = P<uint32_t>(c.koff);
+    unsigned long long *bt = P<unsigned long long>(c.bounds);
+    int lm = c.prm.leaf_max;
+    int64_t nn = n;
+    void *args[] = {(void *)&key, (void *)&nn, (void *)&lm, (void *)&cl, (void *)&rg, (void *)&kd, (void *)&lv,
+                    (void *)&capN, (void *)&nkp, (void *)&bd, (void *)&bt, (void *)&dst};
+    TRY(cudaLaunchCooperativeKernel((const void *)k_tree_levels, dim3(nb), dim3(kBT), args, 0, st));
     note_launch();
-    TRY(scan_u32(P<uint32_t>(c.nkids), P<uint32_t>(c.koff), d_tot, cnt, c.tmp2, st));
-    TRY(cudaMemcpyAsync(c.h_pinned, d_tot, 8, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(c.h_pinned, dst, sizeof(TreeState), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    int64_t nxt = (int64_t)c.h_pinned[0];
-    if (total + nxt > (int64_t)cap_nodes) {
-      size_t nc = (size_t)(total + nxt) * 2;
-      TRY(ensure_keep(c.cell, nc * sizeof(uint4), total * sizeof(uint4), st));
-      TRY(ensure_keep(c.range, nc * sizeof(uint2), total * sizeof(uint2), st));
-      TRY(ensure_keep(c.kids, nc * sizeof(int2), total * sizeof(int2), st));
-      cap_nodes = nc;
-    }
-    k_emit_children<<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, total, P<uint32_t>(c.bounds), P<uint32_t>(c.nkids),
-                                                      P<uint32_t>(c.koff), P<uint4>(c.cell), P<uint2>(c.range),
-                                                      P<int2>(c.kids));
-    note_launch();
-    TRY(cudaGetLastError());
-    ++level;
-    if (nxt == 0) break;
-    lo = total;
-    cnt = nxt;
-    total += nxt;
-    c.level_start[level] = lo;
+    std::memcpy(&hs, c.h_pinned, sizeof(TreeState));
+    if (!hs.overflow) break;
+    c.cap_nodes *= 2;
   }
-  c.nlevels = level;
-  c.level_start[level] = total;
+  const int64_t total = (int64_t)hs.total;
+  c.nlevels = hs.nlevels;
+  for (int l = 0; l <= hs.nlevels && l < kDepth + 3; ++l) c.level_start[l] = (int64_t)hs.level_start[l];
   c.nnodes = total;
+  c.nleaves = (int64_t)hs.nleaves;
   if (total >= ((int64_t)1 << kSinkBits)) return cudaErrorInvalidValue;  // mapped to HFMM_ERR_CAPACITY
-
-  // leaves
-  TRY(ensure(c.nkids, total * sizeof(uint32_t)));
-  TRY(ensure(c.koff, total * sizeof(uint32_t)));
-  k_leaf_flags<<<blocks_for(total, T), T, 0, st>>>(P<int2>(c.kids), total, P<uint32_t>(c.nkids));
-  note_launch();
-  TRY(scan_u32(P<uint32_t>(c.nkids), P<uint32_t>(c.koff), d_tot, total, c.tmp2, st));
-  TRY(cudaMemcpyAsync(c.h_pinned, d_tot, 8, cudaMemcpyDeviceToHost, st));
-  TRY(cudaStreamSynchronize(st));
-  c.nleaves = (int64_t)c.h_pinned[0];
-  TRY(ensure(c.leaves, c.nleaves * sizeof(uint32_t)));
-  k_leaf_list<<<blocks_for(total, T), T, 0, st>>>(P<uint32_t>(c.nkids), P<uint32_t>(c.koff), total,
-                                                  P<uint32_t>(c.leaves));
-  note_launch();
   k_leaf_offsets<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell),
                                                          P<uint2>(c.range), P<double>(c.xs), mass, perm, n,
                                                          c.prm.box, P<float4>(c.pm4));
