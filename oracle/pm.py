@@ -7,7 +7,7 @@ product package.
 Force split (Sec. 2.2): the pair potential 1/r = erfc(r/2r_s)/r + erf(r/2r_s)/r.
 The short-range part is the truncated FMM; the long-range part is the periodic
 convolution of the mass density with erf(r/2r_s)/r, whose Fourier transform is
-4 pi exp(-k^2 r_s^2) / k^2, evaluated on the PM mesh of Sec. 2.1:
+4 pi exp(-k^2 r_s^2) / k^2, evaluated on the PM mesh (Sec. 2.2):
   1. cloud-in-cell (CIC) mass assignment to the mesh points x_g = g L / N_g,
   2. FFT of the mass mesh,
   3. a(k) = i k G 4 pi exp(-k^2 r_s^2) / k^2 / W(k)^2 * m(k) / L^3 with
@@ -18,7 +18,8 @@ convolution of the mass density with erf(r/2r_s)/r, whose Fourier transform is
 Sign: a = G grad Phi with Phi = sum_j m_j psi(x - x_j), the convention of the
 short-range pair force a_i = G sum_j m_j f_(1)(r) r (attractive, f_(1) < 0).
 
-The time step is the kick-drift-kick leapfrog in static space:
+The time step (the synchronised global step of Sec. 4) is the kick-drift-kick
+leapfrog in static space:
   v += a dt/2;  x += v dt (wrapped into the box);  a = a_SR + a_LR at the new x;  v += a dt/2.
 
 Parity status: pinned by closed forms in tests/test_oracle_pm.py (a plane-wave
