@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="same kind of set at another N (profiling only)")
     ap.add_argument("--theta", type=float, default=0.3)
     ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--leaf-max", type=int, default=0, help="octree leaf capacity (0: the workload's own)")
     ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
     ap.add_argument("--graph", type=int, default=0, help="1: post-traversal phases as one CUDA graph")
     ap.add_argument("--tuned", default="", help="autotuner cache (JSON) to take the launch shapes from")
@@ -211,6 +212,8 @@ def main():
     cfg = W.CONFIGS[args.workload]
     if args.n:
         cfg = W.scaled(cfg, args.n)
+    if args.leaf_max:
+        cfg = W.dataclasses.replace(cfg, leaf_max=args.leaf_max)
     if args.impl == "reference":
         run_reference(args, cfg)
         return

@@ -67,14 +67,24 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def _stale(src: str, headers_mtime: float) -> bool:
+    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    return not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), headers_mtime)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the stale objects (source or any shared header newer than the object) and link."""
     os.makedirs(BUILD, exist_ok=True)
     if not force and up_to_date():
         return LIB
     _generate()
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+    hdr = max(os.path.getmtime(h) for h in _inputs() if not h.endswith(".cu"))
+    todo = srcs if force else [s for s in srcs if _stale(s, hdr)]
+    if todo:
+        with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
+            list(ex.map(lambda s: _compile(s, verbose), todo))
+    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcufft", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

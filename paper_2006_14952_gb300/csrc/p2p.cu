@@ -3,18 +3,27 @@
 // already in the caller's particle order (the un-permute).
 //
 // One warp per sink leaf (taken from a global work counter).  The source
-// particles of all leaves on the sink's list are streamed through a per-warp
-// shared-memory buffer, already translated into the sink leaf's frame (the
-// leaf-centre difference is an exact integer in half units).  Lanes are split
-// as (sink i, stream s): with cs sinks in the chunk, S = 32 / cs streams walk
-// the buffer, so small leaves still keep the warp busy; the streams are added
-// in a fixed order at the end (deterministic).
+// particles of all leaves on the sink's list are streamed through per-warp
+// shared memory in fills of up to kCap particles.  A fill takes the next 32
+// list entries (a prefix scan of their particle counts gives each candidate
+// its slot, an entry cut at the buffer's end continues in the next fill) and
+// copies the candidates' particles asynchronously (cp.async) into a raw buffer;
+// the next fill's copies are issued before the current fill is evaluated, so
+// their latency hides behind the arithmetic.  Once a fill has landed it is
+// transformed into the evaluation buffer: moved into the sink leaf's frame (the
+// leaf-centre difference is an exact integer in half units), negated, and kept
+// only if within R_c of the bounding box of the chunk's sinks (a margin of
+// 2^-12 in r^2 keeps every source whose FP32 pair distance could come out
+// below R_c; the others contribute nothing).  Lanes are split as (sink i,
+// stream s): with cs sinks in the chunk, S = 32 / cs streams walk the buffer,
+// so small leaves still keep the warp busy; the streams are added in a fixed
+// order at the end (deterministic).
 //
-// The buffer holds sources in pairs, {-x0, -x1, -y0, -y1} {-z0, -z1, -w0, -w1}
-// (w = mass), so each lane evaluates two pairs per step with the packed FP32x2
-// add / multiply / fma of sm_100+ (half the FP32 instructions; rsqrt and exp2
-// stay per element).  An odd tail is padded with a massless source far outside
-// the cut-off.
+// The evaluation buffer holds sources in pairs, {-x0, -x1, -y0, -y1}
+// {-z0, -z1, -w0, -w1} (w = mass), so each lane evaluates two pairs per step
+// with the packed FP32x2 add / multiply / fma of sm_100+ (half the FP32
+// instructions; rsqrt and exp2 stay per element).  An odd tail is padded with a
+// massless source far outside the cut-off.
 //
 // Pair force: a = -m S(x) r / r^3, S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi),
 // x = r / r_s, evaluated as S = exp2(-x^2 log2(e) / 4) * Q(r / R_c) with Q a
@@ -41,23 +50,30 @@ __device__ __forceinline__ float exp2_mufu(float x) {
   return y;
 }
 
-// kCap: staged source particles per warp (even)
+// kCap: source particles per fill (even); dynamic shared memory: 2 x 8 x kCap float4
 template <bool kCount, int kCap>
-__global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
-                                             const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
-                                             const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
-                                             const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
-                                             const uint32_t *__restrict__ perm, int64_t n, float box, PairFit fit,
-                                             float G, float *__restrict__ acc_out,
-                                             unsigned long long *__restrict__ ctr) {
-  __shared__ float4 sbuf[8][kCap];  // kCap / 2 source pairs, two float4 each
-  // per warp: the 32 list entries of one fill step (first staged particle,
-  // exclusive slot offset, leaf-centre offset in the sink's frame)
+__global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
+                                                const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
+                                                const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
+                                                const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
+                                                const uint32_t *__restrict__ perm, int64_t n, float box, PairFit fit,
+                                                float G, float *__restrict__ acc_out,
+                                                unsigned long long *__restrict__ ctr) {
+  extern __shared__ float4 p2p_smem[];
+  // per warp: the 32 list entries of the pending fill (first particle, exclusive
+  // candidate offset, leaf-centre offset in the sink's frame), each candidate's
+  // entry, and the chunk's sink bounding box (lo xyz, hi xyz)
   __shared__ uint32_t e_src[8][32], e_excl[8][32];
   __shared__ float e_off[8][3][32];
+  __shared__ uint8_t e_own[8][kCap];
+  __shared__ float e_box[8][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float4 *buf = sbuf[wid];
+  float4 *raw = p2p_smem + wid * kCap;            // the pending fill, as copied
+  float4 *buf = p2p_smem + (8 + wid) * kCap;      // the fill being evaluated, in pairs
   float *bf = reinterpret_cast<float *>(buf);
+  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(raw);
+  // cull threshold: R_c^2 (1 + 2^-12), far above the FP32 rounding of either distance
+  const float rc2_cull = fit.rc2 * (1.f + 1.f / 4096.f);
   const float half_unit = box / (float)kHalfBox;
   uint32_t n_in = 0;  // pairs inside the cut-off (profile mode only)
   for (;;) {
@@ -69,6 +85,99 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
     const uint4 ca = cell[k];
     const uint2 r = range[k];
     const uint32_t tb = beg[k], te = end[k];
+
+    // the entry window at q + lane, prefetched in two steps: the list word
+    // (fetch_lst, while the previous fill is evaluated), then the source leaf's
+    // particle range and cell (fetch_src, while the pending fill lands)
+    uint64_t pf_e = 0;
+    uint2 pf_rb = make_uint2(0u, 0u);
+    uint4 pf_cb = make_uint4(0u, 0u, 0u, 0u);
+    auto fetch_lst = [&](uint32_t q) {
+      if (q + lane < te) pf_e = lst[q + lane];
+    };
+    auto fetch_src = [&](uint32_t q) {
+      if (q + lane < te) {
+        const uint32_t b = pair_src(pf_e);
+        pf_rb = range[b];
+        pf_cb = cell[b];
+      }
+    };
+
+    // issue the fill starting at list entry q (the first jq particles of that
+    // entry already taken; its window prefetched): tables, async copies;
+    // advances (q, jq) and starts fetching the next window; returns the number
+    // of candidates
+    auto issue = [&](uint32_t &q, uint32_t &jq) -> uint32_t {
+      const uint32_t qi = q + lane;
+      const bool valid = qi < te;
+      uint32_t cnt = 0, first = 0;
+      float dx = 0.f, dy = 0.f, dz = 0.f;
+      if (valid) {
+        const uint64_t e = pf_e;
+        const uint2 rb = pf_rb;
+        int dd[3];
+        half_delta32(ca, pf_cb, pair_shift(e), dd);
+        dx = (float)dd[0] * half_unit;
+        dy = (float)dd[1] * half_unit;
+        dz = (float)dd[2] * half_unit;
+        first = rb.x;
+        cnt = rb.y;
+      }
+      const uint32_t start = lane == 0 ? jq : 0u;
+      const uint32_t avail = valid ? cnt - start : 0u;
+      uint32_t incl = avail;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t excl = incl - avail;
+      e_src[wid][lane] = first + start;
+      e_excl[wid][lane] = excl;  // non-decreasing in the lane index
+      e_off[wid][0][lane] = dx;
+      e_off[wid][1][lane] = dy;
+      e_off[wid][2][lane] = dz;
+      __syncwarp();
+      const uint32_t all = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t tot = all < (uint32_t)kCap ? all : (uint32_t)kCap;
+      // candidate p belongs to the last entry whose offset is <= p; four per lane
+      // per step: the binary searches first, then the copies
+      for (uint32_t pb = 0; pb < tot; pb += 128) {
+        int own[4];
+        uint32_t idx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t p = pb + lane + 32 * u;
+          int o = 0;
+#pragma unroll
+          for (int step = 16; step; step >>= 1)
+            if (e_excl[wid][o + step] <= p) o += step;
+          own[u] = o;
+          idx[u] = e_src[wid][o] + (p - e_excl[wid][o]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t p = pb + lane + 32 * u;
+          if (p < tot) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(raw_s + 16u * p), "l"(pm4 + idx[u])
+                         : "memory");
+            e_own[wid][p] = (uint8_t)own[u];
+          }
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      // entries taken whole; an entry cut at the buffer's end continues next time
+      const unsigned full = __ballot_sync(0xffffffffu, valid && incl <= (uint32_t)kCap);
+      const int nfull = __popc(full);
+      const uint32_t pex = __shfl_sync(0xffffffffu, excl, nfull & 31);
+      const uint32_t pstart = nfull == 0 ? jq : 0u;
+      const bool partial = nfull < 32 && q + nfull < te;
+      jq = partial ? pstart + (pex < (uint32_t)kCap ? (uint32_t)kCap - pex : 0u) : 0u;
+      q += nfull;
+      fetch_lst(q);
+      return tot;
+    };
+
     for (uint32_t cbase = r.x; cbase < r.x + r.y; cbase += 32) {
       const uint32_t rem = r.x + r.y - cbase;
       const int cs = rem < 32 ? (int)rem : 32;
@@ -76,102 +185,92 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
       const bool active = stream < S;
       const float4 xi = pm4[cbase + il];
       const float2 xx = f2(xi.x), xy = f2(xi.y), xz = f2(xi.z);
+      {
+        float lo0 = xi.x, lo1 = xi.y, lo2 = xi.z, hi0 = xi.x, hi1 = xi.y, hi2 = xi.z;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+          lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+          lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+          hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+          hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+          hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+        }
+        if (lane == 0) {
+          e_box[wid][0] = lo0;
+          e_box[wid][1] = lo1;
+          e_box[wid][2] = lo2;
+          e_box[wid][3] = hi0;
+          e_box[wid][4] = hi1;
+          e_box[wid][5] = hi2;
+        }
+      }
       float2 ax = f2(0.f), ay = f2(0.f), az = f2(0.f);
       uint32_t q = tb, jq = 0;
-      while (q < te) {
-        int fill = 0;
-        while (fill < kCap && q < te) {
-          const uint32_t qi = q + lane;
-          const bool valid = qi < te;
-          uint32_t cnt = 0, first = 0;
-          float dx = 0.f, dy = 0.f, dz = 0.f;
-          if (valid) {
-            const uint64_t e = lst[qi];
-            const uint32_t b = pair_src(e);
-            const uint2 rb = range[b];
-            int dd[3];
-            half_delta32(ca, cell[b], pair_shift(e), dd);
-            dx = (float)dd[0] * half_unit;
-            dy = (float)dd[1] * half_unit;
-            dz = (float)dd[2] * half_unit;
-            first = rb.x;
-            cnt = rb.y;
-          }
-          const uint32_t start = lane == 0 ? jq : 0u;
-          const uint32_t avail = valid ? cnt - start : 0u;
-          uint32_t incl = avail;
+      bool pending = q < te;
+      fetch_lst(q);
+      fetch_src(q);
+      uint32_t tot = pending ? issue(q, jq) : 0u;
+      while (pending) {
+        fetch_src(q);
+        // the pending fill has landed: into the sink's frame, cull, pair up
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        uint32_t kept = 0;
+        {
+          const float bx0 = e_box[wid][0], by0 = e_box[wid][1], bz0 = e_box[wid][2];
+          const float bx1 = e_box[wid][3], by1 = e_box[wid][4], bz1 = e_box[wid][5];
+          // four candidates per lane per step (independent chains), kept in
+          // candidate order
+          for (uint32_t pb = 0; pb < tot; pb += 128) {
+            float4 v[4];
+            int o[4];
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          const uint32_t excl = incl - avail;
-          const uint32_t room = (uint32_t)(kCap - fill);
-          e_src[wid][lane] = first + start;
-          e_excl[wid][lane] = excl;  // non-decreasing in the lane index
-          e_off[wid][0][lane] = dx;
-          e_off[wid][1][lane] = dy;
-          e_off[wid][2][lane] = dz;
-          __syncwarp();
-          {
-            // stage slots [0, min(total, room)) of this step, one slot per lane:
-            // slot p belongs to the last entry whose offset is <= p
-            const uint32_t all = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t tot = all < room ? all : room;
-            // four slots per lane per step: the four binary searches first, then four
-            // independent particle loads in flight, then the stores
-            for (uint32_t pb = lane; pb < tot; pb += 128) {
-              int own[4];
-              uint32_t idx[4];
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t p = pb + lane + 32 * u;
+              const uint32_t pc = p < tot ? p : 0u;
+              v[u] = raw[pc];
+              o[u] = e_own[wid][pc];
+            }
+            bool keep[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const uint32_t p = pb + 32 * u;
-                int o = 0;
+            for (int u = 0; u < 4; ++u) {
+              v[u].x += e_off[wid][0][o[u]];
+              v[u].y += e_off[wid][1][o[u]];
+              v[u].z += e_off[wid][2][o[u]];
+              const float gx = fmaxf(fmaxf(bx0 - v[u].x, v[u].x - bx1), 0.f);
+              const float gy = fmaxf(fmaxf(by0 - v[u].y, v[u].y - by1), 0.f);
+              const float gz = fmaxf(fmaxf(bz0 - v[u].z, v[u].z - bz1), 0.f);
+              keep[u] = pb + lane + 32 * u < tot && gx * gx + gy * gy + gz * gz <= rc2_cull;
+            }
 #pragma unroll
-                for (int step = 16; step; step >>= 1)
-                  if (e_excl[wid][o + step] <= p) o += step;
-                own[u] = o;
-                idx[u] = p < tot ? e_src[wid][o] + (p - e_excl[wid][o]) : 0u;
+            for (int u = 0; u < 4; ++u) {
+              const unsigned kb = __ballot_sync(0xffffffffu, keep[u]);
+              if (keep[u]) {
+                const uint32_t slot = kept + (uint32_t)__popc(kb & ((1u << lane) - 1u));
+                float *a = bf + (slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
+                a[0] = -v[u].x;
+                a[2] = -v[u].y;
+                a[4] = -v[u].z;
+                a[6] = -v[u].w;
               }
-              float4 s4[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u)
-                if (pb + 32 * u < tot) s4[u] = pm4[idx[u]];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const uint32_t p = pb + 32 * u;
-                if (p < tot) {
-                  const uint32_t slot = (uint32_t)fill + p;
-                  float *a = bf + (slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
-                  a[0] = -(s4[u].x + e_off[wid][0][own[u]]);
-                  a[2] = -(s4[u].y + e_off[wid][1][own[u]]);
-                  a[4] = -(s4[u].z + e_off[wid][2][own[u]]);
-                  a[6] = -s4[u].w;
-                }
-              }
+              kept += (uint32_t)__popc(kb);
             }
           }
-          __syncwarp();  // the entry table is rewritten by the next step
-          const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-          const unsigned full = __ballot_sync(0xffffffffu, valid && incl <= room);
-          const int nfull = __popc(full);
-          const uint32_t pex = __shfl_sync(0xffffffffu, excl, nfull & 31);
-          const uint32_t pstart = nfull == 0 ? jq : 0u;
-          const bool partial = nfull < 32 && q + nfull < te;
-          jq = partial ? pstart + (pex < room ? room - pex : 0u) : 0u;
-          q += nfull;
-          fill += (int)(total < room ? total : room);
         }
-        if ((fill & 1) && lane == 0) {  // pad: massless, far beyond the cut-off
-          float *a = bf + (fill >> 1) * 8 + 1;
+        if ((kept & 1) && lane == 0) {  // pad: massless, far beyond the cut-off
+          float *a = bf + (kept >> 1) * 8 + 1;
           a[0] = -1e18f;
           a[2] = -1e18f;
           a[4] = -1e18f;
           a[6] = 0.f;
         }
-        __syncwarp();
+        __syncwarp();  // the raw buffer and the entry tables are free again
+        pending = q < te;
+        if (pending) tot = issue(q, jq);  // in flight during the evaluation below
         if (active) {
-          const int np = (fill + 1) >> 1;
+          const int np = (int)((kept + 1) >> 1);
+#pragma unroll 2
           for (int kk = stream; kk < np; kk += S) {
             const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
             const float2 dx = __fadd2_rn(xx, make_float2(A.x, A.y));
@@ -198,7 +297,7 @@ __global__ void __launch_bounds__(256) k_p2p(const uint32_t *__restrict__ leaves
             az = __ffma2_rn(f, dz, az);
           }
         }
-        __syncwarp();
+        __syncwarp();  // the evaluation buffer is rewritten by the next fill
       }
       // add the streams of each sink in a fixed order
       buf[lane] = make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, 0.f);
@@ -242,9 +341,12 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   auto kern = count ? (small ? k_p2p<true, 128> : k_p2p<true, 256>) : (small ? k_p2p<false, 128> : k_p2p<false, 256>);
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
-  e = cudaMemsetAsync(ctr, 0, 8, st);
+  // two buffers (raw copies, evaluation pairs) of kCap float4 per warp
+  const size_t dyn = (size_t)2 * 8 * (small ? 128 : 256) * sizeof(float4);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 8, st);
   if (e != cudaSuccess) return e;
-  kern<<<g, T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
+  kern<<<g, T, dyn, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
                         (float)c.prm.box, c.fit, (float)c.prm.G, acc, ctr);
   note_launch();
