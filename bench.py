@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nfw-2m")
     ap.add_argument("--n", type=int, default=0, help="same kind of set at another N (profiling only)")
-    ap.add_argument("--theta", type=float, default=0.3)
-    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--theta", type=float, default=0.0, help="acceptance parameter (0: the workload's own)")
+    ap.add_argument("--order", type=int, default=0, help="expansion order (0: the workload's own)")
     ap.add_argument("--leaf-max", type=int, default=0, help="octree leaf capacity (0: the workload's own)")
     ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
     ap.add_argument("--graph", type=int, default=0, help="1: post-traversal phases as one CUDA graph")
@@ -214,6 +214,8 @@ def main():
         cfg = W.scaled(cfg, args.n)
     if args.leaf_max:
         cfg = W.dataclasses.replace(cfg, leaf_max=args.leaf_max)
+    args.theta = args.theta or cfg.theta
+    args.order = args.order or cfg.order
     if args.impl == "reference":
         run_reference(args, cfg)
         return

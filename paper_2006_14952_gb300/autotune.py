@@ -15,7 +15,7 @@ with the times it was chosen on.  `save()` / `lookup()` keep a JSON cache keyed
 by GPU name, workload label and the solver parameters that change the work
 (theta, order, leaf size, acceptance mode).
 
-    python -m paper_2006_14952_gb300.autotune --workload nfw-2m --theta 0.3 --order 5 \\
+    python -m paper_2006_14952_gb300.autotune --workload nfw-2m \\
         --out paper_2006_14952_gb300/tuning/cache.json
 """
 from __future__ import annotations
@@ -29,7 +29,7 @@ import time
 # knob -> (candidates, the phase timing it is judged on); the first candidate is the default
 KNOBS = {
     "tile_p2p_stage": ([256, 128], "t_p2p"),
-    "tile_p2p_blocks": ([8, 6, 4], "t_p2p"),
+    "tile_p2p_blocks": ([8, 4, 2], "t_p2p"),
     "tile_m2l_blocks": ([64, 16, 8, 4], "t_m2l"),
     "tile_trav_blocks": ([4, 3, 2], "t_traverse"),
 }
@@ -113,13 +113,15 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="nfw-2m", choices=sorted(W.CONFIGS))
-    ap.add_argument("--theta", type=float, default=0.3)
-    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--theta", type=float, default=0.0, help="0: the workload's own")
+    ap.add_argument("--order", type=int, default=0, help="0: the workload's own")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning",
                                                   "cache.json"))
     args = ap.parse_args()
     cfg = W.CONFIGS[args.workload]
+    args.theta = args.theta or cfg.theta
+    args.order = args.order or cfg.order
     pos, mass = W.make(cfg)
     params = dict(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
                   order=args.order, leaf_max=cfg.leaf_max)

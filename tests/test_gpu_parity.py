@@ -74,7 +74,8 @@ def test_keys_perm_nodes_bit_exact(case):
 
 
 @pytest.mark.parametrize("rule,size_rule,theta,leaf", [(1, 1, 0.5, 16), (0, 1, 0.5, 16), (1, 0, 0.5, 16),
-                                                        (1, 1, 0.3, 8), (1, 1, 0.7, 1), (1, 1, 0.0, 16)])
+                                                        (1, 1, 0.3, 8), (1, 1, 0.7, 1), (1, 1, 0.0, 16),
+                                                        (1, 1, 0.35, 48), (1, 1, 0.35, 64)])
 def test_interaction_lists_bit_exact(rule, size_rule, theta, leaf):
     pos, mass = W.nfw_clustered(20000 if leaf > 1 else 4000, 30, 0.7, 21)
     s, _ = run_gpu(pos, mass, pm_grid=32, theta=theta, leaf_max=leaf, transition_rule=rule, size_rule=size_rule,
@@ -98,6 +99,40 @@ def test_forces_match_fp64_fmm_on_identical_lists(case, order):
     assert f.size("m2l") > 0
     err = rel_rms(acc, ref)
     assert err < FORCE_TOL, err
+
+
+@pytest.mark.parametrize("leaf,order,theta", [(48, 6, 0.35), (64, 4, 0.3), (32, 5, 0.4)])
+def test_forces_on_identical_lists_with_large_leaves(leaf, order, theta):
+    """Leaves of up to 64 particles: sink chunks of 32 and of fewer lanes, P2P
+    fills cut inside an entry, and the cut-off culling of staged sources."""
+    pos, mass = CASES["nfw-50000"]()
+    s, acc = run_gpu(pos, mass, pm_grid=32, order=order, theta=theta, leaf_max=leaf)
+    f = run_oracle(pos, mass, s)
+    ref = f.forces()
+    assert f.size("p2p") > 0 and f.size("m2l") > 0
+    err = rel_rms(acc, ref)
+    assert err < FORCE_TOL, err
+
+
+def test_full_size_clustered_set_in_the_bench_configuration():
+    """The 2M clustered set with the parameters the benchmark times (leaf 48,
+    theta 0.35, p 6): Morton keys, permutation and tree nodes bit-exact against
+    the oracle; forces on 4000 sampled sinks against the FP64 direct truncated
+    sum within the accuracy bar (RMS 1e-4, 99th percentile 1e-3)."""
+    cfg = W.CONFIGS["nfw-2m"]
+    pos, mass = W.make(cfg)
+    s, acc = run_gpu(pos, mass, pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=cfg.theta,
+                     order=cfg.order, leaf_max=cfg.leaf_max)
+    f = run_oracle(pos, mass, s)
+    key, perm, _ = f.particles()
+    np.testing.assert_array_equal(s.export("keys"), key)
+    np.testing.assert_array_equal(s.export("perm").astype(np.int64), perm)
+    np.testing.assert_array_equal(s.export("nodes"), f.nodes())
+    sinks = W.subsample(cfg.n, 4000, 31)
+    ref = oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks)
+    e = np.linalg.norm(acc[:, sinks] - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert math.sqrt((e ** 2).mean()) < 1e-4
+    assert np.percentile(e, 99) < 1e-3
 
 
 def test_expansions_match_oracle():
