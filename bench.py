@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.0, help="acceptance parameter (0: the workload's own)")
     ap.add_argument("--order", type=int, default=0, help="expansion order (0: the workload's own)")
     ap.add_argument("--leaf-max", type=int, default=0, help="octree leaf capacity (0: the workload's own)")
-    ap.add_argument("--m2l-precision", type=int, default=0, help="0 FP32 CUDA cores, 1 3xTF32 tensor cores")
+    ap.add_argument("--m2l-precision", type=int, default=0,
+                    help="0 FP32 CUDA cores, 1 3xTF32 tensor cores, 2 BF16x3 tensor cores")
     ap.add_argument("--graph", type=int, default=0, help="1: post-traversal phases as one CUDA graph")
     ap.add_argument("--tuned", default="", help="autotuner cache (JSON) to take the launch shapes from")
     ap.add_argument("--m2l-tables", type=int, default=0, help="1: same-level M2L operators from the (level, offset) table")
@@ -379,10 +380,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg),
                        "path": ("learned acceptance (network, safety bound theta), " if learned else
-                                "geometric acceptance, ") + ("3xTF32 tensor-core M2L" if args.m2l_precision == 1
-                                                             else "FP32 CUDA-core M2L" +
-                                                             (" with (level, offset) operator tables"
-                                                              if args.m2l_tables else "")),
+                                "geometric acceptance, ") + (
+                           {1: "3xTF32 tensor-core M2L", 2: "BF16x3 tensor-core M2L"}.get(args.m2l_precision)
+                           or "FP32 CUDA-core M2L" + (" with (level, offset) operator tables"
+                                                      if args.m2l_tables else "")),
                        "theta": args.theta, "order": args.order, "leaf_max": cfg.leaf_max,
                        "transition_rule": 1, "size_rule": 1, "l2": "flushed (512 MB write) before every step",
                        "graph": bool(args.graph), "tiles": tiles or "defaults",

@@ -70,8 +70,10 @@ typedef struct {
                           1: open iff S_max > R_c >= S_m (every M2L pair lies within R_c) */
   int size_rule;       /* L in theta = L / S_c: 0 = side of the source cell (as printed),
                           1 = larger side of the two cells */
-  int m2l_precision;   /* 0 = FP32 on CUDA cores; 1 = 3xTF32 split products on the tcgen05
-                          tensor cores with FP32 accumulation in tensor memory (orders 1..6) */
+  int m2l_precision;   /* 0 = FP32 on CUDA cores; split products hi*hi + hi*lo + lo*hi on the
+                          tcgen05 tensor cores with FP32 accumulation in tensor memory
+                          (orders 1..6): 1 = 3xTF32, 2 = BF16x3 (lo = bf16(x - bf16(x)),
+                          about 2^-16 relative per product) */
   int profile;         /* bit 0: record per-phase CUDA-event timings; bit 1: count P2P
                           particle pairs (extra work; for statistics runs only) */
   int m2l_tables;      /* 1 = same-level M2L pairs whose integer cell offset o satisfies

@@ -38,9 +38,9 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.mac_mode != 0 && p.mac_mode != 1) return why = "mac_mode must be 0 (geometric) or 1 (learned)", false;
   if (p.transition_rule != 0 && p.transition_rule != 1) return why = "transition_rule must be 0 or 1", false;
   if (p.size_rule != 0 && p.size_rule != 1) return why = "size_rule must be 0 or 1", false;
-  if (p.m2l_precision != 0 && p.m2l_precision != 1) return why = "m2l_precision must be 0 or 1", false;
-  if (p.m2l_precision == 1 && !m2l_tc_supported(p.order))
-    return why = "m2l_precision 1 (3xTF32 tensor cores) supports orders 1..6", false;
+  if (p.m2l_precision < 0 || p.m2l_precision > 2) return why = "m2l_precision must be 0, 1 or 2", false;
+  if (p.m2l_precision != 0 && !m2l_tc_supported(p.order))
+    return why = "m2l_precision 1 and 2 (3xTF32 / BF16x3 tensor cores) support orders 1..6", false;
   if (p.profile < 0 || p.profile > 3) return why = "profile must be 0..3", false;
   if (p.m2l_tables != 0 && p.m2l_tables != 1) return why = "m2l_tables must be 0 or 1", false;
   if (p.tile_p2p_stage != 0 && p.tile_p2p_stage != 128 && p.tile_p2p_stage != 256)
@@ -309,11 +309,11 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   }
   if ((e = sort_lists(c, st)) != cudaSuccess) return cuda_fail(c, e, "sort_lists");
   if (prof) cudaEventRecord(c.ev[6], st);
-  if (c.prm.m2l_precision == 1 &&
+  if (c.prm.m2l_precision != 0 &&
       (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 6, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "m2l status");
   if ((e = m2l_all(c, st)) != cudaSuccess) return cuda_fail(c, e, "m2l");
-  if (c.prm.m2l_precision == 1 && c.nm2l > 0) {
+  if (c.prm.m2l_precision != 0 && c.nm2l > 0) {
     int *status = reinterpret_cast<int *>(P<uint64_t>(c.d_small) + 6);
     if ((e = cudaMemcpyAsync(c.h_pinned + 31, status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)

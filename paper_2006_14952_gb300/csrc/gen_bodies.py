@@ -26,6 +26,8 @@ TCStore<P>:  tensor-core M2L operands for one pair: D'_c = u^(|c|+1) D^_c(R^) an
              M'_m = s (v/u)^|m| M~_m, each split x = hi + lo (hi = TF32 rounding),
              stored at row c (or m), column k of K-major 128-byte-swizzled tiles
              (xo[j] = float offset of column k in a row with (row mod 8) = j).
+TCStoreBF<P>: the same operands split into BF16 hi = bf16(x), lo = bf16(x - hi),
+             64 BF16 columns per 128-byte row.
 
 Run by build.py before nvcc (python3 gen_bodies.py <out>).
 """
@@ -283,12 +285,21 @@ def gen_tab_body(P, G, g):
     return "\n".join(L)
 
 
-def gen_tc(P):
+def gen_tc(P, bf=False):
     NC = ncoef(P)
     ms = multi(P)
-    L = [f"template <> struct TCStore<{P}> {{",
+    T = "__nv_bfloat16" if bf else "float"
+    row = 64 if bf else 32  # elements per 128-byte row
+
+    def split(v, dst):
+        if bf:
+            return (f"const __nv_bfloat16 h = __float2bfloat16_rn({v}); hi[{dst}] = h;"
+                    f" lo[{dst}] = __float2bfloat16_rn({v} - __bfloat162float(h));")
+        return f"const float h = tf32_round({v}); hi[{dst}] = h; lo[{dst}] = {v} - h;"
+
+    L = [f"template <> struct {'TCStoreBF' if bf else 'TCStore'}<{P}> {{",
          f"  static __device__ __forceinline__ void store_d(float rx, float ry, float rz, const float (&f)[{P + 1}],"
-         f" const float (&U)[{P + 1}], float *__restrict__ hi, float *__restrict__ lo, const int (&xo)[8]) {{"]
+         f" const float (&U)[{P + 1}], {T} *__restrict__ hi, {T} *__restrict__ lo, const int (&xo)[8]) {{"]
     nm = {}
     for a in ms:
         if a == (0, 0, 0):
@@ -315,12 +326,11 @@ def gen_tc(P):
                     o = cn - kx - ky - kz
                     t = f"f[{o}]" if a == (0, 0, 0) else f"{nm[a]} * f[{o}]"
                     parts.append(t if co == 1 else f"{float(co)}f * {t}")
-        off = (ci >> 3) * 256 + (ci & 7) * 32
-        L.append(f"    {{ const float d = U[{cn}] * ({' + '.join(parts)}); const float h = tf32_round(d);"
-                 f" hi[{off} + xo[{ci & 7}]] = h; lo[{off} + xo[{ci & 7}]] = d - h; }}")
+        off = (ci >> 3) * 8 * row + (ci & 7) * row
+        L.append(f"    {{ const float d = U[{cn}] * ({' + '.join(parts)}); {split('d', f'{off} + xo[{ci & 7}]')} }}")
     L.append("  }")
     L.append(f"  static __device__ __forceinline__ void store_m(const float *__restrict__ Mb, float vr, float s,"
-             f" float *__restrict__ hi, float *__restrict__ lo, const int (&xo)[8]) {{")
+             f" {T} *__restrict__ hi, {T} *__restrict__ lo, const int (&xo)[8]) {{")
     L.append("    float q = s;")
     for k in range(P + 1):
         if k:
@@ -329,20 +339,20 @@ def gen_tc(P):
             if sum(a) != k:
                 continue
             ci = idx(a)
-            off = (ci >> 3) * 256 + (ci & 7) * 32
-            L.append(f"    {{ const float x = __ldg(Mb + {ci}) * q; const float h = tf32_round(x);"
-                     f" hi[{off} + xo[{ci & 7}]] = h; lo[{off} + xo[{ci & 7}]] = x - h; }}")
+            off = (ci >> 3) * 8 * row + (ci & 7) * row
+            L.append(f"    {{ const float x = __ldg(Mb + {ci}) * q; {split('x', f'{off} + xo[{ci & 7}]')} }}")
     L.append("  }")
     L.append("};")
     return "\n".join(L)
 
 
 def main(out):
-    parts = ["// Generated by gen_bodies.py: do not edit.", "#pragma once", "",
+    parts = ["// Generated by gen_bodies.py: do not edit.", "#pragma once", "", "#include <cuda_bf16.h>", "",
              "template <int P, int G, int g> struct M2LBody;", "template <int P> struct M2LLoad;",
              "template <int P, int G, int g> struct M2LTabBody;",
              "template <int P> struct P2MBody;", "template <int P> struct M2MBody;", "template <int P> struct L2LBody;",
-             "template <int P> struct L2PBody;", "template <int P> struct TCStore;", "",
+             "template <int P> struct L2PBody;", "template <int P> struct TCStore;",
+             "template <int P> struct TCStoreBF;", "",
              "__device__ __forceinline__ float tf32_round(float x) {",
              "  uint32_t r;",
              "  asm(\"cvt.rna.tf32.f32 %0, %1;\" : \"=r\"(r) : \"f\"(x));",
@@ -380,6 +390,8 @@ def main(out):
         parts.append("")
     for P in range(1, 7):
         parts.append(gen_tc(P))
+        parts.append("")
+        parts.append(gen_tc(P, bf=True))
         parts.append("")
     g_expr = "1"
     for P in sorted(SLICES, reverse=True):

@@ -1,5 +1,6 @@
 // M2L with split-precision products on the 5th-generation tensor cores
-// (tcgen05, accumulator in tensor memory), the m2l_precision = 1 path.
+// (tcgen05, accumulator in tensor memory): m2l_precision = 1 (3xTF32) and
+// m2l_precision = 2 (BF16x3).
 //
 // For one sink A with pairs (A, B_k), Eq. m2l in the scaled, per-pair
 // normalised form of m2l.cu is
@@ -7,20 +8,26 @@
 //           = sum_m P[n+m][m],   P[c][m] = sum_k D'_c(k) M'_m(k),
 //   D'_c(k) = u_k^(|c|+1) D^_c(R^_k),   M'_m(k) = (v_k / u_k)^|m| M~_m(B_k),
 // a GEMM whose contraction dimension is the sink's pair list.  Each FP32
-// operand is split x = hi + lo with hi its TF32 rounding; P accumulates
-// hi*hi + hi*lo + lo*hi in FP32 (3xTF32).  Only the entries with |n|+|m| <= p
-// of P are used, so at most C(p+6,6) / NC^2 of the tensor work is algorithmic
-// (462 / 3136 at p = 5).
+// operand is split x = hi + lo, hi its TF32 rounding (kind::tf32, K = 8 per
+// instruction) or its BF16 rounding with lo = bf16(x - hi) (kind::f16 with both
+// operands BF16, K = 16); P accumulates hi*hi + hi*lo + lo*hi in FP32.  The
+// dropped terms are lo*lo and, for BF16, the rounding of lo: about 2^-21
+// relative for TF32 and 2^-16 for BF16 per product.  Only the entries with
+// |n|+|m| <= p of P are used, so at most C(p+6,6) / NC^2 of the tensor work is
+// algorithmic (462 / 3136 at p = 5).
 //
 // CTA = 128 threads, one sink at a time (work counter).  A chunk of 128 pairs:
-// thread t computes pair t's D' and M' (generated TCStore bodies) and writes
-// them to the K-major, 128-byte-swizzled tiles of warp t/32 (32 pairs = one
-// 128-byte row per matrix row); one thread then issues 4 tiles x 4 K-steps x 3
-// split products of tcgen05.mma kind::tf32 (M = 128 rows c, N = NCP columns m,
-// K = 8) into the sink's TMEM accumulator and commits to an mbarrier.  After
+// thread t computes pair t's D' and M' (generated TCStore / TCStoreBF bodies)
+// and writes them to the K-major, 128-byte-swizzled tiles (one 128-byte row per
+// matrix row holds 32 TF32 or 64 BF16 pairs: 4 or 2 tiles per chunk); one
+// thread then issues tiles x 4 K-steps x 3 split products of tcgen05.mma
+// (M = 128 rows c, N = NCP columns m) into the sink's TMEM accumulator and
+// commits to an mbarrier.  After
 // the last chunk the four warps read their 32 TMEM lanes (rows c), stage P in
 // shared memory and thread n forms L~_n = sum_m P[n+m][m].  Waits are bounded;
 // on a timeout the kernel records an error and returns after freeing TMEM.
+#include <type_traits>
+
 #include "common.cuh"
 #include "gen_bodies.cuh"
 
@@ -35,8 +42,12 @@ __host__ __device__ constexpr int ncp_of(int p) { return (ncoef(p) + 15) / 16 * 
 __host__ __device__ constexpr int tmem_cols_of(int p) {
   return ncp_of(p) <= 32 ? 32 : (ncp_of(p) <= 64 ? 64 : (ncp_of(p) <= 128 ? 128 : 256));
 }
-// dynamic shared memory: 1 KB alignment slack + A (hi, lo) 4 x 16 KB each + B (hi, lo) 4 x NCP x 128 B each
-__host__ __device__ constexpr size_t smem_of(int p) { return 1024 + 2 * 4 * 16384 + 2 * 4 * (size_t)ncp_of(p) * 128; }
+// 128-byte tiles per 128-pair chunk: 32 TF32 or 64 BF16 pairs per row
+__host__ __device__ constexpr int tiles_of(bool bf) { return bf ? 2 : 4; }
+// dynamic shared memory: 1 KB alignment slack + A (hi, lo) tiles x 16 KB each + B (hi, lo) tiles x NCP x 128 B each
+__host__ __device__ constexpr size_t smem_of(int p, bool bf) {
+  return 1024 + 2 * (size_t)tiles_of(bf) * 16384 + 2 * (size_t)tiles_of(bf) * ncp_of(p) * 128;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
 
@@ -56,11 +67,25 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor: D = F32, A = B = BF16 (kind::f16), both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+// both operands BF16 (the instruction descriptor says so for A and B alike)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
@@ -91,7 +116,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int P>
+template <int P, bool kBF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(int64_t nn, const uint4 *__restrict__ cell, const uint32_t *__restrict__ beg,
              const uint32_t *__restrict__ end, const uint64_t *__restrict__ lst, const float *__restrict__ M,
@@ -100,7 +125,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncp_of(P);
   constexpr uint32_t TCOLS = tmem_cols_of(P);
-  constexpr uint32_t IDESC = idesc_tf32(128, NCP);
+  constexpr uint32_t IDESC = kBF ? idesc_bf16(128, NCP) : idesc_tf32(128, NCP);
+  constexpr int kTiles = tiles_of(kBF), kPerRow = kChunk / kTiles;  // tiles per chunk, pairs per 128-byte row
+  using T = typename std::conditional<kBF, __nv_bfloat16, float>::type;
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -110,11 +137,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *a_hi = reinterpret_cast<float *>(base);           // 4 tiles x 4096 floats
-  float *a_lo = a_hi + 4 * 4096;
-  float *b_hi = a_lo + 4 * 4096;                           // 4 tiles x NCP * 32 floats
-  float *b_lo = b_hi + 4 * NCP * 32;
-  float *pbuf = a_hi;                                      // P staging after a sink's last chunk
+  T *a_hi = reinterpret_cast<T *>(base);  // kTiles tiles x 128 rows x kPerRow elements (16 KB each)
+  T *a_lo = a_hi + kTiles * 128 * kPerRow;
+  T *b_hi = a_lo + kTiles * 128 * kPerRow;  // kTiles tiles x NCP rows x kPerRow elements
+  T *b_lo = b_hi + kTiles * NCP * kPerRow;
+  float *pbuf = reinterpret_cast<float *>(base);  // P staging after a sink's last chunk (NC^2 floats)
 
   for (int c = tid; c < NC; c += kThreads) {
     int x, y, z;
@@ -124,7 +151,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // operand tiles start at zero.  Rows >= NC of B stay zero; rows >= NC of A may
   // later hold the P staging of a finished sink, which only feeds rows of P
   // that are never read.
-  for (int i = tid; i < 2 * 4 * 4096 + 2 * 4 * NCP * 32; i += kThreads) a_hi[i] = 0.f;
+  {
+    uint32_t *w = reinterpret_cast<uint32_t *>(base);
+    for (int i = tid; i < (2 * kTiles * 16384 + 2 * kTiles * NCP * 128) / 4; i += kThreads) w[i] = 0u;
+  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
     abort_flag = 0;
@@ -143,13 +173,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t phase = 0;
   const float kInvSqrtPi = 0.56418958354775628f;
 
-  // this thread's column k within its tile and the swizzled float offsets of that column
-  const int kq = tid >> 5, kk = tid & 31;
+  // this thread's column k within its tile and the swizzled element offsets of
+  // that column (16-byte chunks XOR the row mod 8 within each 8-row atom)
+  const int kq = tid / kPerRow, kk = tid % kPerRow;
+  constexpr int kEl = 16 / (int)sizeof(T);  // elements per 16-byte chunk
   int xo[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) xo[j] = (((kk >> 2) ^ j) << 2) + (kk & 3);
-  float *my_ahi = a_hi + kq * 4096, *my_alo = a_lo + kq * 4096;
-  float *my_bhi = b_hi + kq * NCP * 32, *my_blo = b_lo + kq * NCP * 32;
+  for (int j = 0; j < 8; ++j) xo[j] = (((kk / kEl) ^ j) * kEl) + (kk % kEl);
+  T *my_ahi = a_hi + kq * 128 * kPerRow, *my_alo = a_lo + kq * 128 * kPerRow;
+  T *my_bhi = b_hi + kq * NCP * kPerRow, *my_blo = b_lo + kq * NCP * kPerRow;
 
   for (;;) {
     if (tid == 0) {
@@ -206,22 +238,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       U[0] = u;
 #pragma unroll
       for (int q = 1; q <= P; ++q) U[q] = U[q - 1] * u;
-      TCStore<P>::store_d(rx, ry, rz, f, U, my_ahi, my_alo, xo);
-      TCStore<P>::store_m(Mb, vr, s, my_bhi, my_blo, xo);
+      if constexpr (kBF) {
+        TCStoreBF<P>::store_d(rx, ry, rz, f, U, my_ahi, my_alo, xo);
+        TCStoreBF<P>::store_m(Mb, vr, s, my_bhi, my_blo, xo);
+      } else {
+        TCStore<P>::store_d(rx, ry, rz, f, U, my_ahi, my_alo, xo);
+        TCStore<P>::store_m(Mb, vr, s, my_bhi, my_blo, xo);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kTiles; ++q) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t aoff = (uint32_t)(q * 4096 * 4 + j * 32), boff = (uint32_t)(q * NCP * 32 * 4 + j * 32);
+          for (int j = 0; j < 4; ++j) {  // K-steps of 32 bytes: 8 TF32 or 16 BF16 pairs
+            const uint32_t aoff = (uint32_t)(q * 16384 + j * 32), boff = (uint32_t)(q * NCP * 128 + j * 32);
             const uint64_t ah = desc_sw128(smem_u32(a_hi) + aoff), al = desc_sw128(smem_u32(a_lo) + aoff);
             const uint64_t bh = desc_sw128(smem_u32(b_hi) + boff), bl = desc_sw128(smem_u32(b_lo) + boff);
-            mma_tf32(tmem, ah, bh, IDESC, (ch | q | j) ? 1u : 0u);
-            mma_tf32(tmem, ah, bl, IDESC, 1u);
-            mma_tf32(tmem, al, bh, IDESC, 1u);
+            if constexpr (kBF) {
+              mma_bf16(tmem, ah, bh, IDESC, (ch | q | j) ? 1u : 0u);
+              mma_bf16(tmem, ah, bl, IDESC, 1u);
+              mma_bf16(tmem, al, bh, IDESC, 1u);
+            } else {
+              mma_tf32(tmem, ah, bh, IDESC, (ch | q | j) ? 1u : 0u);
+              mma_tf32(tmem, ah, bl, IDESC, 1u);
+              mma_tf32(tmem, al, bh, IDESC, 1u);
+            }
           }
         }
         mma_commit(mb);
@@ -272,10 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
-template <int P>
+template <int P, bool kBF>
 cudaError_t launch_tc(Ctx &c, cudaStream_t st) {
-  const size_t smem = smem_of(P);
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = smem_of(P, kBF);
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<P, kBF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // d_small[5] = work counter, d_small[6] = status word
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(hfmm::P<uint64_t>(c.d_small) + 5);
@@ -285,7 +328,7 @@ cudaError_t launch_tc(Ctx &c, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
-  k_m2l_tc<P><<<nsm > 0 ? nsm : 152, kThreads, smem, st>>>(
+  k_m2l_tc<P, kBF><<<nsm > 0 ? nsm : 152, kThreads, smem, st>>>(
       c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_beg), hfmm::P<uint32_t>(c.m2l_end),
       hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.ldm, inv_rs, ctr, status);
   note_launch();
@@ -298,13 +341,14 @@ bool m2l_tc_supported(int p) { return p >= 1 && p <= 6; }
 
 cudaError_t m2l_pass_tc(Ctx &c, int q, cudaStream_t st) {
   if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
+  const bool bf = c.prm.m2l_precision == 2;
   switch (q) {
-    case 1: return launch_tc<1>(c, st);
-    case 2: return launch_tc<2>(c, st);
-    case 3: return launch_tc<3>(c, st);
-    case 4: return launch_tc<4>(c, st);
-    case 5: return launch_tc<5>(c, st);
-    case 6: return launch_tc<6>(c, st);
+    case 1: return bf ? launch_tc<1, true>(c, st) : launch_tc<1, false>(c, st);
+    case 2: return bf ? launch_tc<2, true>(c, st) : launch_tc<2, false>(c, st);
+    case 3: return bf ? launch_tc<3, true>(c, st) : launch_tc<3, false>(c, st);
+    case 4: return bf ? launch_tc<4, true>(c, st) : launch_tc<4, false>(c, st);
+    case 5: return bf ? launch_tc<5, true>(c, st) : launch_tc<5, false>(c, st);
+    case 6: return bf ? launch_tc<6, true>(c, st) : launch_tc<6, false>(c, st);
   }
   return cudaErrorInvalidValue;
 }

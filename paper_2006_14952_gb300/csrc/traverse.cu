@@ -998,7 +998,7 @@ cudaError_t m2l_all(Ctx &c, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   auto run = [&](int q) -> cudaError_t {
-    if (c.prm.m2l_precision == 1 && m2l_tc_supported(q)) return m2l_pass_tc(c, q, st);
+    if (c.prm.m2l_precision != 0 && m2l_tc_supported(q)) return m2l_pass_tc(c, q, st);
     if (tab) {
       cudaError_t e = m2l_pass_table(c, q, st);
       if (e != cudaSuccess) return e;

@@ -1,6 +1,13 @@
-"""Split-precision M2L (3xTF32 on tcgen05 tensor cores, m2l_precision = 1)
-against the FP64 oracle FMM on identical lists (1e-5 relative RMS, the stated
-tolerance for the FP32 path) and against the FP32 CUDA-core M2L."""
+"""Split-precision M2L on tcgen05 tensor cores against the FP64 oracle FMM on
+identical lists and against the FP32 CUDA-core M2L.
+
+3xTF32 (m2l_precision = 1): 1e-5 relative RMS, the stated tolerance of the FP32
+path.  BF16x3 (m2l_precision = 2): each operand is hi + lo with hi = bf16(x) and
+lo = bf16(x - hi), so x is represented to 2^-16 relative and the dropped lo*lo
+term is below 2^-16 of the product: at most 3 * 2^-16 = 4.6e-5 relative per
+product.  The tolerance is that bound, 5e-5 relative RMS, for the forces and for
+the local expansions (the RMS of sums of such products with independent
+roundings stays under the per-product bound)."""
 import math
 
 import numpy as np
@@ -50,8 +57,42 @@ def test_tensor_core_m2l_locals_match_cuda_core_locals():
     assert _rel(L1, L0) < 1e-5
 
 
+BF16X3_TOL = 5e-5
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_bf16x3_m2l_matches_oracle(order):
+    pos, mass = W.nfw_clustered(30000, 40, 0.7, 33)
+    s, acc = _run(pos, mass, pm_grid=32, order=order, m2l_precision=2)
+    p = s.params
+    f = oracle.FMM(box=1.0, rs=s.rs, rc=s.rc, theta=p.theta, order=order, leaf_max=p.leaf_max)
+    f.build_tree(pos, mass)
+    ref = f.forces()
+    assert f.size("m2l") > 0
+    assert _rel(acc, ref) < BF16X3_TOL
+    _, acc0 = _run(pos, mass, pm_grid=32, order=order, m2l_precision=0)
+    assert _rel(acc, acc0) < BF16X3_TOL
+
+
+def test_bf16x3_locals_are_a_distinct_split_within_bound():
+    """BF16x3 locals within the bound of the FP32 ones, and not the 3xTF32 result
+    (which is ~2^-21 away from FP32): the BF16 path is the one that ran."""
+    pos, mass = W.nfw_clustered(30000, 40, 0.7, 34)
+    s2, _ = _run(pos, mass, pm_grid=32, order=5, m2l_precision=2)
+    s1, _ = _run(pos, mass, pm_grid=32, order=5, m2l_precision=1)
+    s0, _ = _run(pos, mass, pm_grid=32, order=5, m2l_precision=0)
+    L2, L1, L0 = (x.export("locals").astype(np.float64) for x in (s2, s1, s0))
+    e2, e1 = _rel(L2, L0), _rel(L1, L0)
+    assert e2 < BF16X3_TOL
+    assert e1 < 1e-5
+    assert e2 > 2 * e1
+
+
 def test_tensor_core_m2l_rejects_unsupported_order():
     from paper_2006_14952_gb300 import hfmm
 
-    with pytest.raises(hfmm.HfmmError, match="orders 1..6"):
-        hfmm.Solver(order=7, m2l_precision=1)
+    for prec in (1, 2):
+        with pytest.raises(hfmm.HfmmError, match="orders 1..6"):
+            hfmm.Solver(order=7, m2l_precision=prec)
+    with pytest.raises(hfmm.HfmmError, match="m2l_precision"):
+        hfmm.Solver(m2l_precision=3)
