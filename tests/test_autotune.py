@@ -6,12 +6,12 @@ from paper_2006_14952_gb300 import autotune as A
 
 def test_coordinate_search_finds_the_best_of_each_knob():
     # separable cost: each phase depends on its own knobs only
-    best_want = {"tile_p2p_stage": 128, "tile_p2p_blocks": 6, "tile_m2l_blocks": 8, "tile_trav_blocks": 3}
+    best_want = {"tile_p2p_stage": 128, "tile_p2p_blocks": 4, "tile_m2l_blocks": 8, "tile_trav_blocks": 3}
     calls = []
 
     def measure(t):
         calls.append(dict(t))
-        p2p = abs(t["tile_p2p_stage"] - 128) + 10 * abs(t["tile_p2p_blocks"] - 6)
+        p2p = abs(t["tile_p2p_stage"] - 128) + 10 * abs(t["tile_p2p_blocks"] - 4)
         return {"t_p2p": 1.0 + p2p, "t_m2l": 1.0 + abs(t["tile_m2l_blocks"] - 8),
                 "t_traverse": 1.0 + abs(t["tile_trav_blocks"] - 3)}
 
