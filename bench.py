@@ -38,7 +38,7 @@ N_SM = 152
 # r^2 (1 mul + 2 fma = 5), rsqrt (1), t = r / R_c (2), the truncation factor
 # S = exp2(r^2 k) Q(t) with Q of degree 9 (exponent 1 + exp2 1 + 9 fma 18 +
 # product 1 = 21), -S m / r^3 (4), accumulation (3 fma = 6).
-P2P_FLOPS_PER_PAIR = 42
+P2P_FLOPS_PER_PAIR = 41
 
 
 def parse():

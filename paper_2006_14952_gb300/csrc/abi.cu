@@ -94,20 +94,21 @@ PairFit fit_pair_factor(double rs, double rc) {
     for (int k = 0; k < N; ++k) s += fk[k] * std::cos(pi * j * (k + 0.5) / N);
     cj[j] = (j == 0 ? 1.0 : 2.0) * s / N;
   }
-  // T_j(2t - 1) as monomial coefficients in t
+  // T_j(s) as monomial coefficients in s = 2r / R_c - 1 (the interval's midpoint at 0)
   std::memset(T, 0, sizeof(T));
   T[0][0] = 1.0;
-  T[1][0] = -1.0;
-  T[1][1] = 2.0;
+  T[1][1] = 1.0;
   for (int j = 1; j + 1 < N; ++j)
-    for (int i = 0; i < N; ++i) T[j + 1][i] = (i ? 4.0 * T[j][i - 1] : 0.0) - 2.0 * T[j][i] - T[j - 1][i];
+    for (int i = 0; i < N; ++i) T[j + 1][i] = (i ? 2.0 * T[j][i - 1] : 0.0) - T[j - 1][i];
   for (int i = 0; i < N; ++i) {
     mono[i] = 0.0;
     for (int j = 0; j < N; ++j) mono[i] += cj[j] * T[j][i];
   }
+  // in powers of u = r - R_c / 2 (s = u * 2 / R_c): small coefficients, a well-conditioned Horner sum
   PairFit f;
-  for (int i = 0; i < N; ++i) f.c[i] = (float)mono[i];
-  f.inv_rc = (float)(1.0 / rc);
+  double sc = 1.0;
+  for (int i = 0; i < N; ++i, sc *= 2.0 / rc) f.c[i] = (float)(mono[i] * sc);
+  f.rmid = (float)(0.5 * rc);
   f.rc2 = (float)(rc * rc);
   f.kexp = (float)(-1.4426950408889634 / (4.0 * rs * rs));
   return f;

@@ -132,10 +132,11 @@ cudaError_t radix_sort_u64_into(uint64_t *keys, uint32_t *vals, uint64_t *keys_a
 // S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi) = exp2(r^2 kexp) Q(r / R_c),
 // Q(t) = sum_j c[j] t^j (degree 9), kexp = -log2(e) / (4 r_s^2).
 struct PairFit {
-  float c[10];
-  float inv_rc, rc2, kexp;
+  float c[10];  // Q = sum_i c[i] u^i, u = r - rmid
+  float rmid, rc2, kexp;
 };
-// Chebyshev interpolation (10 nodes on [0, R_c]) of e^(x^2/4) erfc(x/2) + x/sqrt(pi), in FP64.
+// Chebyshev interpolation (10 nodes on [0, R_c]) of e^(x^2/4) erfc(x/2) + x/sqrt(pi),
+// x = r / r_s, in FP64, expanded in powers of u = r - R_c / 2 and rounded to FP32.
 PairFit fit_pair_factor(double rs, double rc);
 struct Ctx;
 void mac_integer_thresholds(Ctx &c);

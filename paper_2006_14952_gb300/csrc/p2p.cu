@@ -26,9 +26,10 @@
 // massless source far outside the cut-off.
 //
 // Pair force: a = -m S(x) r / r^3, S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi),
-// x = r / r_s, evaluated as S = exp2(-x^2 log2(e) / 4) * Q(r / R_c) with Q a
-// degree-9 polynomial interpolating e^(x^2/4) erfc(x/2) + x / sqrt(pi) at
-// Chebyshev nodes on [0, R_c] (coefficients from the host, fit_pair_factor()).
+// x = r / r_s, evaluated as S = exp2(-x^2 log2(e) / 4) * Q(r) with Q a degree-9
+// polynomial interpolating e^(x^2/4) erfc(x/2) + x / sqrt(pi) at Chebyshev
+// nodes on [0, R_c], expanded in powers of u = r - R_c / 2 (coefficients from
+// the host, fit_pair_factor()).
 #include "common.cuh"
 
 namespace hfmm {
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
         if (pending) tot = issue(q, jq);  // in flight during the evaluation below
         if (active) {
           const int np = (int)((kept + 1) >> 1);
-#pragma unroll 2
+#pragma unroll 4
           for (int kk = stream; kk < np; kk += S) {
             const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
             const float2 dx = __fadd2_rn(xx, make_float2(A.x, A.y));
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
             if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
             // outside (0, R_c) the values below may be inf/NaN; the selects discard them
             const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            const float2 tt = __fmul2_rn(__fmul2_rn(r2, rinv), f2(fit.inv_rc));
+            const float2 tt = __ffma2_rn(r2, rinv, f2(-fit.rmid));  // u = r - R_c / 2
             float2 qv = f2(fit.c[9]);
 #pragma unroll
             for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, f2(fit.c[j]));

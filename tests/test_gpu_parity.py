@@ -205,9 +205,14 @@ def test_host_buffer_entry_point_matches_device_path():
 def test_pair_force_law_across_the_cutoff_range():
     """1000 isolated pairs, separations log-spaced over (0.03, 1) R_c, against the
     FP64 direct sum (the closed-form g(r)).  Error budget per pair: 3e-6 for the
-    FP32 evaluation (interpolant 1.2e-6, Horner rounding with alternating
-    coefficients ~1e-6, exp2 and rsqrt a few ulp), plus the rounding of the two
-    FP32 offsets from their leaf centres, 4 * 2^-24 * sqrt(3) h_leaf / r."""
+    FP32 evaluation of the force law at given FP32 separations (interpolant
+    1.1e-6, Horner rounding, exp2 and rsqrt a few ulp), plus the rounding of the
+    separation itself carried through the force law: a relative error e_r of r
+    gives kappa(x) e_r in |a| = G m S(x) / r^2, with kappa(x) = |d ln(S / r^2) /
+    d ln r| = 2 + x^3 e^(-x^2/4) / (2 sqrt(pi) S(x)), x = r / r_s (2 at small x,
+    about 9 at x = 3.9, 11 at R_c: the Gaussian tail steepens the law); e_r is at
+    most two roundings of 2^-24 of the larger of r and the offsets from the leaf
+    centres, 2 * 2^-24 * (1 + sqrt(3) h_leaf / r)."""
     rng = np.random.default_rng(5)
     g = (np.arange(10) + 0.5) / 10.0
     cx, cy, cz = np.meshgrid(g, g, g, indexing="ij")
@@ -225,7 +230,10 @@ def test_pair_force_law_across_the_cutoff_range():
     nodes = s.export("nodes")
     h_leaf = (1.0 / 2.0 ** nodes[nodes[:, 7] == 0, 0]).max()
     rr = np.concatenate([r, r])
-    bound = 3e-6 + 4 * 2.0 ** -24 * np.sqrt(3) * h_leaf / rr
+    x = rr / s.rs
+    S = np.array([math.erfc(v / 2) for v in x]) + x * np.exp(-x * x / 4) / math.sqrt(math.pi)
+    kappa = 2 + x ** 3 * np.exp(-x * x / 4) / (2 * math.sqrt(math.pi) * S)
+    bound = 3e-6 + kappa * 2 * 2.0 ** -24 * (1 + np.sqrt(3) * h_leaf / rr)
     w = int(np.argmax(e / bound))
     assert np.all(e < bound), f"worst r/R_c {rr[w] / rc:.4f}: err {e[w]:.3e} > bound {bound[w]:.3e}"
     assert np.median(e) < 1e-6
