@@ -261,19 +261,85 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v, un
   return tot;
 }
 
-// Prefix over the blocks before this one of column k of the per-block partials.
+// Block-wide exclusive scans of N values per thread in one round (two block
+// barriers for all N); tot receives the N block totals.
+template <int N>
+__device__ __forceinline__ void block_exscan_n(const unsigned long long (&v)[N], unsigned long long (&ex)[N],
+                                               unsigned long long (&tot)[N], unsigned long long (*wsum)[kTW]) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  unsigned long long x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = v[i];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x[i], o);
+      if (lane >= o) x[i] += y;
+    }
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) wsum[i][wp] = x[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    unsigned long long before = 0, all = 0;
+#pragma unroll
+    for (int q = 0; q < kTW; ++q) {
+      const unsigned long long w = wsum[i][q];
+      if (q < wp) before += w;
+      all += w;
+    }
+    ex[i] = before + x[i] - v[i];
+    tot[i] = all;
+  }
+  __syncthreads();
+}
+
+// Prefix over the blocks before this one of column k of the per-block partials
+// (ncol <= 4 columns), and the column totals.  The rows are read by all threads
+// (strided), then reduced over the warps and the block.
 __device__ __forceinline__ void block_prefixes(const unsigned long long *btot, int ncol, unsigned long long *pre,
                                                unsigned long long *all) {
+  __shared__ unsigned long long red[kTW][8];
   const unsigned nb = gridDim.x, bid = blockIdx.x;
-  if ((int)threadIdx.x < ncol) {
-    unsigned long long b = 0, a = 0;
-    for (unsigned q = 0; q < nb; ++q) {
-      const unsigned long long v = btot[4 * q + threadIdx.x];
-      if (q < bid) b += v;
-      a += v;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  unsigned long long b[4] = {0, 0, 0, 0}, a[4] = {0, 0, 0, 0};
+  for (unsigned q = threadIdx.x; q < nb; q += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (c < ncol) {
+        const unsigned long long v = btot[4 * q + c];
+        a[c] += v;
+        if (q < bid) b[c] += v;
+      }
     }
-    pre[threadIdx.x] = b;
-    all[threadIdx.x] = a;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      b[c] += __shfl_xor_sync(0xffffffffu, b[c], o);
+      a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      red[wp][c] = b[c];
+      red[wp][4 + c] = a[c];
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < 2 * ncol) {
+    const int j = threadIdx.x < (unsigned)ncol ? (int)threadIdx.x : 4 + (int)threadIdx.x - ncol;
+    unsigned long long v = 0;
+#pragma unroll
+    for (int w = 0; w < kTW; ++w) v += red[w][j];
+    if ((int)threadIdx.x < ncol) pre[threadIdx.x] = v;
+    else all[threadIdx.x - ncol] = v;
   }
   __syncthreads();
 }
@@ -309,6 +375,7 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
   __shared__ __align__(16) __nv_bfloat16 xs[kTW][kXs];
   __shared__ uint8_t dec[kTW][kDec];
   __shared__ unsigned long long wsum[kTW], pre[4], all[4], run[4];
+  __shared__ unsigned long long wsum4[4][kTW];
   // level state, uniform over the grid (kept in shared memory, out of the registers)
   __shared__ uint64_t *cur, *nxt;
   __shared__ uint32_t *cmap, *nmap, *segs, *nsegs;
@@ -365,31 +432,39 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
     // ---- 2a. chunk scan: block partials over contiguous chunk ranges
     const unsigned long long kch = (K + nb - 1) / nb;
     const unsigned long long klo = kch * bid < K ? kch * bid : K, khi = klo + kch < K ? klo + kch : K;
-    for (int q = 0; q < 3; ++q) {
-      unsigned long long loc = 0;
-      for (unsigned long long k = klo + tid; k < khi; k += kTT) loc += B.ctot[3 * k + q];
-      const unsigned long long tot = block_sum(loc, wsum);
-      if (tid == 0) B.btot[4 * bid + q] = tot;
+    // each thread takes a contiguous run of the block's chunks (also in 2b)
+    const unsigned long long kper = (khi - klo + kTT - 1) / kTT;
+    const unsigned long long tlo = klo + kper * tid < khi ? klo + kper * tid : khi;
+    const unsigned long long thi = tlo + kper < khi ? tlo + kper : khi;
+    {
+      unsigned long long loc[3] = {0, 0, 0}, ex[3], tot[3];
+      for (unsigned long long k = tlo; k < thi; ++k)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) loc[q] += B.ctot[3 * k + q];
+      block_exscan_n<3>(loc, ex, tot, wsum4);
+      if (tid < 3) B.btot[4 * bid + tid] = tot[tid];
     }
     __threadfence();
     grid.sync();
     // ---- 2b. chunk scan: exclusive prefixes in place
     block_prefixes(B.btot, 3, pre, all);
     const unsigned long long Tc = all[0], Tm = all[1], Tp = all[2];
-    if (tid < 3) run[tid] = pre[tid];
-    __syncthreads();
-    for (unsigned long long kb = klo; kb < khi; kb += kTT) {
-      const unsigned long long k = kb + tid;
-      const bool valid = k < khi;
-      for (int q = 0; q < 3; ++q) {
-        const unsigned long long v = valid ? B.ctot[3 * k + q] : 0ull;
-        unsigned long long tot;
-        const unsigned long long ex = block_exscan(v, wsum, &tot);
-        if (valid) B.ctot[3 * k + q] = run[q] + ex;
-        __syncthreads();
-        if (tid == 0) run[q] += tot;
-        __syncthreads();
-      }
+    {
+      unsigned long long loc[3] = {0, 0, 0}, ex[3], tot[3];
+      for (unsigned long long k = tlo; k < thi; ++k)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) loc[q] += B.ctot[3 * k + q];
+      block_exscan_n<3>(loc, ex, tot, wsum4);
+      unsigned long long rq[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) rq[q] = pre[q] + ex[q];
+      for (unsigned long long k = tlo; k < thi; ++k)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const unsigned long long v = B.ctot[3 * k + q];
+          B.ctot[3 * k + q] = rq[q];
+          rq[q] += v;
+        }
     }
     __threadfence();
     grid.sync();
@@ -432,10 +507,9 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
 #pragma unroll
         for (int q = 0; q < 3; ++q) B.spre[3 * s + q] = pv[q];
       }
-      for (int q = 0; q < 4; ++q) {
-        const unsigned long long tot = block_sum(loc[q], wsum);
-        if (tid == 0) B.btot[4 * bid + q] = tot;
-      }
+      unsigned long long ex[4], tot[4];
+      block_exscan_n<4>(loc, ex, tot, wsum4);
+      if (tid < 4) B.btot[4 * bid + tid] = tot[tid];
     }
     __threadfence();
     grid.sync();
@@ -471,10 +545,9 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
       }
       const unsigned long long mult = kk.y > 0 ? (unsigned long long)kk.y : 1ull;
       unsigned long long ex[4], tot[4];
-      ex[0] = block_exscan(valid ? mult * tv[0] : 0ull, wsum, &tot[0]);
-      ex[1] = block_exscan(valid && tv[0] > 0 ? mult : 0ull, wsum, &tot[1]);
-      ex[2] = block_exscan(valid && tv[1] > 0 ? 1ull : 0ull, wsum, &tot[2]);
-      ex[3] = block_exscan(valid && tv[2] > 0 ? 1ull : 0ull, wsum, &tot[3]);
+      const unsigned long long sv[4] = {valid ? mult * tv[0] : 0ull, valid && tv[0] > 0 ? mult : 0ull,
+                                        valid && tv[1] > 0 ? 1ull : 0ull, valid && tv[2] > 0 ? 1ull : 0ull};
+      block_exscan_n<4>(sv, ex, tot, wsum4);
       if (valid) {
         const unsigned long long o = run[0] + ex[0], sn = run[1] + ex[1];
         SegBase sbv;
