@@ -72,6 +72,30 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_config(cfg, rank, ws):
+    """Each rank solves its own seeded copy of the workload (replicas, weak scaling)."""
+    import dataclasses
+
+    return dataclasses.replace(cfg, seed=cfg.seed + rank) if ws > 1 else cfg
+
+
+def max_over_ranks(x, device=None):
+    """The largest of every rank's x (a float); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, n, steps, seconds):
+    """Units processed by all ranks per second of the slowest rank."""
+    return ws * n * steps / seconds
+
+
 def workload_desc(cfg):
     if cfg.kind == "nfw":
         return (f"{cfg.name}: N={cfg.n} in L=1, {int(cfg.halo_frac * 100)}% in {cfg.halo_count} NFW haloes "
@@ -236,7 +260,7 @@ def main():
     from paper_2006_14952_gb300 import hfmm
 
     # replicas: every rank solves its own seeded copy of the workload (weak scaling)
-    cfg_r = W.dataclasses.replace(cfg, seed=cfg.seed + rank) if ws > 1 else cfg
+    cfg_r = replica_config(cfg, rank, ws)
     pos, mass = W.make(cfg_r)
     n = pos.shape[1]
     # timed solver: phase events only (profile bit 0); the pair counts come from
@@ -314,12 +338,10 @@ def main():
     l1 = s.get_stats()["launches"]
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
+    tot_ms = max_over_ranks(tot_ms, dev)
     if ws > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-        tot_ms = float(t.item())
-    value = ws * n * args.steps / (tot_ms / 1e3)
+    value = whole_job_rate(ws, n, args.steps, tot_ms / 1e3)
 
     # end to end through the host-buffer entry point, copies included
     pin_pos = torch.from_numpy(pos).pin_memory()
@@ -337,11 +359,7 @@ def main():
         t0 = time.perf_counter()
         s2.short_range_forces_host(pin_pos, pin_mass, pin_acc)
         e2e_s += time.perf_counter() - t0
-    e2e_v = ws * n * args.steps / e2e_s if ws == 1 else None
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_v = ws * n * args.steps / float(t.item())
+    e2e_v = whole_job_rate(ws, n, args.steps, max_over_ranks(e2e_s, dev))
 
     # phase breakdown (mean over timed steps) and the dominant kernel's roofline
     keys = ["t_keys_sort", "t_tree", "t_upward", "t_traverse", "t_lists", "t_m2l", "t_l2l", "t_p2p"]

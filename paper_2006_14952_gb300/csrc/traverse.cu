@@ -111,18 +111,16 @@ __device__ __forceinline__ bool table_miss(uint4 ca, uint4 cb, uint32_t s, int k
 }
 
 template <bool kNet>
-__device__ __forceinline__ Item mac_item(const uint64_t *__restrict__ f, int64_t t, bool valid,
-                                         const uint4 *__restrict__ cell, const int2 *__restrict__ kids, const Mac &m,
-                                         const uint32_t *sw, __nv_bfloat16 *xs, uint8_t *dec) {
+__device__ __forceinline__ Item mac_item(uint64_t e, bool valid, const uint4 *__restrict__ cell,
+                                         const int2 *__restrict__ kids, const Mac &m, const uint32_t *sw,
+                                         __nv_bfloat16 *xs, uint8_t *dec) {
   const int lane = threadIdx.x & 31;
-  uint64_t e = 0;
   uint32_t a = 0, b = 0, s = 0;
   int2 ka = make_int2(-1, 0), kb = make_int2(-1, 0);
   uint4 ca = make_uint4(0, 0, 0, 0), cb = ca;
   uint8_t c = kSkip;
   uint32_t order = (uint32_t)m.order;
   if (valid) {
-    e = f[t];
     a = pair_sink(e);
     b = pair_src(e);
     s = pair_shift(e);
@@ -409,11 +407,16 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
   int iter = 0;
   for (; iter < max_iters && nf > 0; ++iter) {
     const unsigned long long NF = nf, K = (NF + 31) / 32;  // 32-pair chunks
-    // ---- 1. classify interleaved chunks; chunk totals (C, M, P)
+    // ---- 1. classify interleaved chunks; chunk totals (C, M, P).  The frontier
+    //         pair of the warp's next chunk is fetched while this one is classified.
+    uint64_t e_pf = 0;
+    if (gw < K && 32 * gw + lane < NF) e_pf = cur[32 * gw + lane];
     for (unsigned long long k = gw; k < K; k += nw) {
       const unsigned long long t = 32 * k + lane;
       const bool valid = t < NF;
-      const Item it = mac_item<kNet>(cur, (int64_t)t, valid, cell, kids, m, sw, xs[wp], dec[wp]);
+      const uint64_t e_now = e_pf;
+      if (k + nw < K && t + 32 * nw < NF) e_pf = cur[t + 32 * nw];
+      const Item it = mac_item<kNet>(e_now, valid, cell, kids, m, sw, xs[wp], dec[wp]);
       uint32_t v[3] = {0, 0, 0};
       if (valid) {
         const uint8_t c = it.cls & 7;
@@ -588,7 +591,13 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
     }
     __threadfence();
     grid.sync();
-    // ---- 3. emit interleaved chunks
+    // ---- 3. emit interleaved chunks (the next chunk's pair and class fetched ahead)
+    uint64_t e_nx = 0;
+    uint8_t c_nx = 0;
+    if (gw < K && 32 * gw + lane < NF) {
+      e_nx = cur[32 * gw + lane];
+      c_nx = B.cls[32 * gw + lane];
+    }
     for (unsigned long long k = gw; k < K; k += nw) {
       const unsigned long long t = 32 * k + lane;
       const bool valid = t < NF;
@@ -596,9 +605,15 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
       uint64_t e = 0;
       int2 ka = make_int2(-1, 0), kb = make_int2(-1, 0);
       uint32_t v[3] = {0, 0, 0};
+      const uint64_t e_in = e_nx;
+      const uint8_t c_in = c_nx;
+      if (k + nw < K && t + 32 * nw < NF) {
+        e_nx = cur[t + 32 * nw];
+        c_nx = B.cls[t + 32 * nw];
+      }
       if (valid) {
-        cc = B.cls[t];
-        e = cur[t];
+        cc = c_in;
+        e = e_in;
         const uint8_t c = cc & 7;
         if (c == kM2L) v[1] = 1;
         if (c == kP2P) v[2] = 1;
