@@ -2,6 +2,8 @@
 // packed list entries and the integer cell geometry used by the traversal.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -131,6 +133,12 @@ cudaError_t radix_sort_u64_into(uint64_t *keys, uint32_t *vals, uint64_t *keys_a
 // ---------------------------------------------------------------- pair force
 // S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi) = exp2(r^2 kexp) Q(r / R_c),
 // Q(t) = sum_j c[j] t^j (degree 9), kexp = -log2(e) / (4 r_s^2).
+// 1/L when the box side L is a power of two (then exact), else 0
+inline double box_inverse_if_pow2(double box) {
+  int e = 0;
+  return std::frexp(box, &e) == 0.5 ? 1.0 / box : 0.0;
+}
+
 struct PairFit {
   float c[10];  // Q = sum_i c[i] u^i, u = r - rmid
   float rmid, rc2, kexp;

@@ -40,13 +40,19 @@ cudaError_t scratch_address(void **out) {
   return cudaSuccess;
 }
 
-__device__ __forceinline__ double wrap_box(double x, double box) {
-  double q = floor(__ddiv_rn(x, box));
+// x / L: when L is a power of two, x * (1/L) is the same correctly rounded
+// quotient (1/L exact), without an FP64 division
+__device__ __forceinline__ double div_box(double x, double box, double inv_pow2) {
+  return inv_pow2 != 0.0 ? __dmul_rn(x, inv_pow2) : __ddiv_rn(x, box);
+}
+
+__device__ __forceinline__ double wrap_box(double x, double box, double inv_pow2) {
+  double q = floor(div_box(x, box, inv_pow2));
   return __dsub_rn(x, __dmul_rn(box, q));
 }
 
-__device__ __forceinline__ uint32_t grid_coord(double w, double box) {
-  double t = floor(__dmul_rn(__ddiv_rn(w, box), 2097152.0));
+__device__ __forceinline__ uint32_t grid_coord(double w, double box, double inv_pow2) {
+  double t = floor(__dmul_rn(div_box(w, box, inv_pow2), 2097152.0));
   t = fmax(0.0, fmin(t, 2097151.0));
   return (uint32_t)t;
 }
@@ -61,13 +67,13 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
   return x;
 }
 
-__global__ void k_keys_noalloc(const double *__restrict__ pos, int64_t n, double box, uint64_t *__restrict__ key,
-                               uint32_t *__restrict__ idx) {
+__global__ void k_keys_noalloc(const double *__restrict__ pos, int64_t n, double box, double inv_pow2,
+                               uint64_t *__restrict__ key, uint32_t *__restrict__ idx) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t k0 = grid_coord(wrap_box(pos[i], box), box);
-  uint32_t k1 = grid_coord(wrap_box(pos[n + i], box), box);
-  uint32_t k2 = grid_coord(wrap_box(pos[2 * n + i], box), box);
+  uint32_t k0 = grid_coord(wrap_box(pos[i], box, inv_pow2), box, inv_pow2);
+  uint32_t k1 = grid_coord(wrap_box(pos[n + i], box, inv_pow2), box, inv_pow2);
+  uint32_t k2 = grid_coord(wrap_box(pos[2 * n + i], box, inv_pow2), box, inv_pow2);
   key[i] = (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
   idx[i] = (uint32_t)i;
 }
@@ -90,7 +96,7 @@ extern "C" int hfmm_morton_sort_noalloc(const double *pos_soa, int64_t n, double
   uint64_t *keys_alt = reinterpret_cast<uint64_t *>(sp);
   uint32_t *idx_alt = reinterpret_cast<uint32_t *>(sp + kAltKeyBytes);
   void *sort_scratch = sp + kAltKeyBytes + kAltIdxBytes;
-  k_keys_noalloc<<<blocks_for(n, 256), 256, 0, st>>>(pos_soa, n, box, keys_out, perm_out);
+  k_keys_noalloc<<<blocks_for(n, 256), 256, 0, st>>>(pos_soa, n, box, box_inverse_if_pow2(box), keys_out, perm_out);
   note_launch();
   if (cudaGetLastError() != cudaSuccess) return HFMM_ERR_CUDA;
   bool alt = false;

@@ -14,13 +14,19 @@ namespace {
 namespace cg = cooperative_groups;
 
 // x - L floor(x / L), each operation rounded separately (no FMA contraction).
-__device__ __forceinline__ double wrap_box(double x, double box) {
-  double q = floor(__ddiv_rn(x, box));
+// x / L: when L is a power of two, x * (1/L) is the same correctly rounded
+// quotient (1/L exact), without an FP64 division
+__device__ __forceinline__ double div_box(double x, double box, double inv_pow2) {
+  return inv_pow2 != 0.0 ? __dmul_rn(x, inv_pow2) : __ddiv_rn(x, box);
+}
+
+__device__ __forceinline__ double wrap_box(double x, double box, double inv_pow2) {
+  double q = floor(div_box(x, box, inv_pow2));
   return __dsub_rn(x, __dmul_rn(box, q));
 }
 
-__device__ __forceinline__ uint32_t grid_coord(double w, double box) {
-  double t = floor(__dmul_rn(__ddiv_rn(w, box), 2097152.0));
+__device__ __forceinline__ uint32_t grid_coord(double w, double box, double inv_pow2) {
+  double t = floor(__dmul_rn(div_box(w, box, inv_pow2), 2097152.0));
   t = fmax(0.0, fmin(t, 2097151.0));
   return (uint32_t)t;
 }
@@ -36,25 +42,26 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
   return x;
 }
 
-__global__ void k_keys(const double *__restrict__ pos, int64_t n, double box, uint64_t *__restrict__ key,
+__global__ void k_keys(const double *__restrict__ pos, int64_t n, double box, double inv_pow2, uint64_t *__restrict__ key,
                        uint32_t *__restrict__ idx) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t k0 = grid_coord(wrap_box(pos[i], box), box);
-  uint32_t k1 = grid_coord(wrap_box(pos[n + i], box), box);
-  uint32_t k2 = grid_coord(wrap_box(pos[2 * n + i], box), box);
+  uint32_t k0 = grid_coord(wrap_box(pos[i], box, inv_pow2), box, inv_pow2);
+  uint32_t k1 = grid_coord(wrap_box(pos[n + i], box, inv_pow2), box, inv_pow2);
+  uint32_t k2 = grid_coord(wrap_box(pos[2 * n + i], box, inv_pow2), box, inv_pow2);
   key[i] = (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
   idx[i] = (uint32_t)i;
 }
 
 __global__ void k_gather(const double *__restrict__ pos, const uint32_t *__restrict__ idx, int64_t n, double box,
+                         double inv_pow2,
                          double *__restrict__ xs) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   uint32_t i = idx[s];
-  xs[s] = wrap_box(pos[i], box);
-  xs[n + s] = wrap_box(pos[n + i], box);
-  xs[2 * n + s] = wrap_box(pos[2 * n + i], box);
+  xs[s] = wrap_box(pos[i], box, inv_pow2);
+  xs[n + s] = wrap_box(pos[n + i], box, inv_pow2);
+  xs[2 * n + s] = wrap_box(pos[2 * n + i], box, inv_pow2);
 }
 
 
@@ -307,7 +314,8 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   TRY(ensure(c.pm4, n * 16));
   TRY(ensure(c.d_small, 256));
   if (c.prm.profile & 1) cudaEventRecord(c.ev[0], st);
-  k_keys<<<blocks_for(n, T), T, 0, st>>>(pos, n, c.prm.box, P<uint64_t>(c.key), P<uint32_t>(c.idx));
+  const double inv_pow2 = box_inverse_if_pow2(c.prm.box);
+  k_keys<<<blocks_for(n, T), T, 0, st>>>(pos, n, c.prm.box, inv_pow2, P<uint64_t>(c.key), P<uint32_t>(c.idx));
   note_launch();
   bool alt = false;
   TRY(radix_sort_u64(P<uint64_t>(c.key), P<uint32_t>(c.idx), P<uint64_t>(c.key_alt), P<uint32_t>(c.idx_alt), n, 0,
@@ -319,7 +327,7 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   uint64_t *key = P<uint64_t>(c.key);
   uint32_t *perm = P<uint32_t>(c.idx);
   if (c.prm.profile & 1) cudaEventRecord(c.ev[1], st);
-  k_gather<<<blocks_for(n, T), T, 0, st>>>(pos, perm, n, c.prm.box, P<double>(c.xs));
+  k_gather<<<blocks_for(n, T), T, 0, st>>>(pos, perm, n, c.prm.box, inv_pow2, P<double>(c.xs));
   note_launch();
 
   // octree levels: one cooperative launch; node capacity from the last build, grown on overflow

@@ -73,6 +73,23 @@ def test_keys_perm_nodes_bit_exact(case):
     np.testing.assert_array_equal(s.export("nodes"), f.nodes())
 
 
+@pytest.mark.parametrize("box", [0.5, 3.0])
+def test_keys_perm_nodes_bit_exact_for_other_box_sides(box):
+    """A box side that is a power of two (the key kernel multiplies by the exact
+    1/L) and one that is not (it divides by L), with positions outside the box
+    on both sides: keys, permutation and nodes bit-exact against the oracle."""
+    pos, mass = W.nfw_clustered(20000, 30, 0.7, 61)
+    pos = pos * box
+    pos[:, :500] -= 1.37 * box
+    pos[:, 500:1000] += 2.11 * box
+    s, _ = run_gpu(pos, mass, pm_grid=32, box=box)
+    f = run_oracle(pos, mass, s)
+    key, perm, _ = f.particles()
+    np.testing.assert_array_equal(s.export("keys"), key)
+    np.testing.assert_array_equal(s.export("perm").astype(np.int64), perm)
+    np.testing.assert_array_equal(s.export("nodes"), f.nodes())
+
+
 @pytest.mark.parametrize("rule,size_rule,theta,leaf", [(1, 1, 0.5, 16), (0, 1, 0.5, 16), (1, 0, 0.5, 16),
                                                         (1, 1, 0.3, 8), (1, 1, 0.7, 1), (1, 1, 0.0, 16),
                                                         (1, 1, 0.35, 48), (1, 1, 0.35, 64)])
