@@ -131,19 +131,14 @@ def gen_body(P, G, g):
             t = f"f[{o}]" if a == (0, 0, 0) else f"{mono(a)} * f[{o}]"
             parts.append(t if co == 1 else f"{float(co)}f * {t}")
         expr = " + ".join(parts)
-        L.append(f"    const float D{ci} = {expr};")
-        # contributions of D_c to the slice's outputs n <= c
-        by_deg = {}
+        # D'_c = u^(|c|+1) D^_c; with the sources scaled by (v/u)^|m| every term
+        # D'_{n+m} M''_m carries u^(|n|+1) v^|m|: one FMA per term
+        L.append(f"    const float D{ci} = U[{cn}] * ({expr});")
         for n in outs:
             if all(n[d] <= c[d] for d in range(3)):
-                by_deg.setdefault(sum(n), []).append(n)
-        for k, ns in sorted(by_deg.items()):
-            L.append(f"    {{ const float du = D{ci} * U[{k}];")
-            for n in ns:
                 m = (c[0] - n[0], c[1] - n[1], c[2] - n[2])
                 a = idx(n) // G
-                L.append(f"      acc[{a}] = fmaf(du, {mp(idx(m))}, acc[{a}]);")
-            L.append("    }")
+                L.append(f"    acc[{a}] = fmaf(D{ci}, {mp(idx(m))}, acc[{a}]);")
     L.append("  }")
     L.append("};")
     return "\n".join(L)

@@ -3,7 +3,9 @@
 // evaluated per pair in units of r = |R|:  D_c(R) = r^-(|c|+1) D^_c(R / r), so
 //   L~_n(A) += u^(|n|+1) sum_m (v^|m| M~_m(B)) D^_{n+m}(R^),  u = h_A / r, v = h_B / r,
 // with |R^| = 1 and u, v <= theta: every factor is O(1) or smaller for any pair
-// of levels.  D^ is the derivative tensor of erfc(x r^ / 2) / r^ at r^ = 1,
+// of levels.  The body forms D'_c = u^(|c|+1) D^_c once per c and takes the
+// source coefficients as (v/u)^|m| M~_m, so each term u^(|n|+1) v^|m| D^ M~ is
+// one FMA (u >= 2^-17 at the depth cap, so u^(p+1) and (v/u)^p stay in range).  D^ is the derivative tensor of erfc(x r^ / 2) / r^ at r^ = 1,
 // x = r / r_s, from the radial prefactors f_(k) = ((1/r) d/dr)^k psi:
 //   D^_c = sum_{k_d <= c_d/2} prod_d [c_d! / (2^k_d k_d! (c_d - 2k_d)!)] R^_d^(c_d-2k_d) f_(|c|-|k|).
 //
@@ -45,7 +47,8 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
     const float r2 = Rx * Rx + Ry * Ry + Rz * Rz;
     const float rinv = rsqrtf(r2);
     const float x = r2 * rinv * inv_rs;  // r / r_s
-    const float u = (float)(2 * half_width(ca.w)) * rinv, v = (float)(2 * half_width(cb.w)) * rinv;
+    const float u = (float)(2 * half_width(ca.w)) * rinv;
+    const float v = (float)half_width(cb.w) / (float)half_width(ca.w);  // v/u = h_B / h_A (exact)
     float f[P + 1];
     f[0] = erfcf(0.5f * x);
     float tk = -x * kInvSqrtPi * __expf(-0.25f * x * x);
