@@ -21,6 +21,8 @@
 // every pair (training data for the network).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "mlp.cuh"
@@ -188,6 +190,8 @@ __device__ __forceinline__ Item mac_item(uint64_t e, bool valid, const uint4 *__
 struct TravState {
   unsigned long long nm2l, np2p, nf;
   int iters, overflow;
+  int ovf_lists;                      // capacity overflow: bit 0 M2L, 1 P2P, 2 frontier, 3 segments, 4 runs
+  unsigned long long need[5];         // entries those lists needed up to the level that overflowed
   unsigned long long items;           // frontier pairs classified over all levels
   unsigned long long nrun_m, nrun_p;  // M2L / P2P runs recorded
 };
@@ -521,7 +525,16 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
     const unsigned long long To = all[0], Ts = all[1], Trm = all[2], Trp = all[3];
     if (nm + Tm > B.capM || np + Tp > B.capP || To > B.capF || Ts > B.capS || nrm + Trm > B.capR ||
         nrp + Trp > B.capR) {
-      if (bid == 0 && tid == 0) st->overflow = 1;
+      if (bid == 0 && tid == 0) {
+        st->overflow = 1;
+        st->ovf_lists = (nm + Tm > B.capM ? 1 : 0) | (np + Tp > B.capP ? 2 : 0) | (To > B.capF ? 4 : 0) |
+                        (Ts > B.capS ? 8 : 0) | (nrm + Trm > B.capR || nrp + Trp > B.capR ? 16 : 0);
+        st->need[0] = nm + Tm;
+        st->need[1] = np + Tp;
+        st->need[2] = To;
+        st->need[3] = Ts;
+        st->need[4] = nrm + Trm > nrp + Trp ? nrm + Trm : nrp + Trp;
+      }
       break;  // every block takes the same decision
     }
     if (tid < 4) run[tid] = pre[tid];
@@ -834,13 +847,21 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   TRY(ensure(c.btot2, (size_t)nb * 4 * sizeof(unsigned long long)));
   // capacities: the last call's sizes with head-room, at least a few per node
   auto grow = [](uint64_t want) { return want + want / 4 + 1024; };
-  // (first guesses from the clustered benchmark sets: ~60 frontier pairs, ~50 M2L
-  // and ~115 P2P entries per particle at the largest level / in total)
-  if (c.cap_front < (uint64_t)(64 * c.n + 1024)) c.cap_front = 64 * c.n + 1024;
-  if (c.cap_m2l < (uint64_t)(64 * c.n + 1024)) c.cap_m2l = 64 * c.n + 1024;
-  if (c.cap_p2p < (uint64_t)(128 * c.n + 1024)) c.cap_p2p = 128 * c.n + 1024;
+  // First guesses from the 2M clustered set: at leaves of 16, about 60 frontier
+  // pairs per particle at the largest level, 50 M2L and 115 P2P entries per
+  // particle in total; these fall about as (16 / leaf_max)^1.5 (8 M2L and 21 P2P
+  // per particle at 48), so the guesses are scaled so, with a margin of 1.5.
+  // A list that overflows is grown alone (to what the walk needed so far, at least
+  // twice its size) and the walk is repeated.
+  const double lf = c.prm.leaf_max > 16 ? std::pow(16.0 / c.prm.leaf_max, 1.5) * 1.5 : 1.0;
+  const double sc = lf < 1.0 ? lf : 1.0;
+  if (c.cap_front < (uint64_t)(sc * 64 * c.n + 1024)) c.cap_front = (uint64_t)(sc * 64 * c.n + 1024);
+  if (c.cap_m2l < (uint64_t)(sc * 64 * c.n + 1024)) c.cap_m2l = (uint64_t)(sc * 64 * c.n + 1024);
+  if (c.cap_p2p < (uint64_t)(sc * 128 * c.n + 1024)) c.cap_p2p = (uint64_t)(sc * 128 * c.n + 1024);
   if (c.cap_seg < (uint64_t)(2 * c.nnodes + 1024)) c.cap_seg = 2 * c.nnodes + 1024;
   if (c.cap_run < (uint64_t)(4 * c.nnodes + 1024)) c.cap_run = 4 * c.nnodes + 1024;
+  // the state sits after the eight counters of the 256-byte d_small and is read back into h_pinned (256 bytes)
+  static_assert(8 * sizeof(uint64_t) + sizeof(TravState) <= 256, "TravState must fit in d_small");
   TravState *dst = reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
   for (int attempt = 0; attempt < 8; ++attempt) {
     TRY(ensure(c.front, c.cap_front * 8));
@@ -911,12 +932,16 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
       c.nrun_p = (int64_t)hs.nrun_p;
       return cudaSuccess;
     }
-    // grow every list (the walk stopped at the first overflow, so the sizes seen are lower bounds)
-    c.cap_front = grow(c.cap_front * 2);
-    c.cap_m2l = grow(c.cap_m2l * 2);
-    c.cap_p2p = grow(c.cap_p2p * 2);
-    c.cap_seg = grow(c.cap_seg * 2);
-    c.cap_run = grow(c.cap_run * 2);
+    // grow the lists that overflowed (the walk stopped at the first overflow, so the
+    // sizes seen are lower bounds)
+    auto up = [&](uint64_t &cap, int bit, int k) {
+      if (hs.ovf_lists & bit) cap = grow(std::max<uint64_t>(cap * 2, hs.need[k]));
+    };
+    up(c.cap_m2l, 1, 0);
+    up(c.cap_p2p, 2, 1);
+    up(c.cap_front, 4, 2);
+    up(c.cap_seg, 8, 3);
+    up(c.cap_run, 16, 4);
   }
   return cudaErrorInvalidValue;
 #undef TRY
