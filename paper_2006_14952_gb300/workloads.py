@@ -55,8 +55,9 @@ CONFIGS = {
     # Zel'dovich-like lattice, N = 256^3, 40% in 1000 NFW haloes, PM 256^3, p 6
     "zeldovich-16m": Config("zeldovich-16m", 256 ** 3, 256, "zeldovich", halo_count=1000, halo_frac=0.4,
                             order=6, seed=1003),
-    # learned-acceptance evaluation set, N = 128^3, 85% in 2000 NFW haloes
-    "nfw85-2m": Config("nfw85-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.85, seed=1004),
+    # learned-acceptance evaluation set, N = 128^3, 85% in 2000 NFW haloes (solved like nfw-2m)
+    "nfw85-2m": Config("nfw85-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.85, order=6, theta=0.35,
+                       leaf_max=48, seed=1004),
     # large: 512^3 Zel'dovich + 4000 haloes (50%)
     "zeldovich-134m": Config("zeldovich-134m", 512 ** 3, 512, "zeldovich", halo_count=4000, halo_frac=0.5,
                              seed=1005),
