@@ -17,7 +17,7 @@
  *   - dual-tree traversal with the three-rule MAC       Sec. 2.3, itemised criteria
  *   - P2P with the hard cutoff                          Sec. 2.1 (P2P), Sec. 2.2
  *
- * Readings where the paper is silent or garbled (documented in the design doc):
+ * Readings where the paper is silent or garbled:
  *   D_n uses erfc(r/2r_s) (the factor 2 of the potential equation), is NOT
  *   traceless, and is built from the radial derivatives f_(k) = ((1/r) d/dr)^k psi;
  *   expansion centres are geometric; total order |n|+|m| <= p; the MAC compares
