@@ -54,27 +54,37 @@ __global__ void k_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uin
   store_row<NC>(M + (size_t)k * ldm, acc);
 }
 
-// M2M, one thread per cell of one level: sum of its children's shifted multipoles.
+// M2M, one thread per (cell of one level, child slot): each thread translates
+// one child's multipoles to the parent centre; the eight sibling threads are
+// adjacent lanes and add their results with a fixed xor-shuffle tree (the same
+// order on every run), and slot 0 stores the parent's row.
 template <int P>
 __global__ void k_m2m(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int ldm,
                       float *__restrict__ M) {
   constexpr int NC = ncoef(P);
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  const int64_t k = lo + t;
-  const int2 kd = kids[k];
-  if (kd.y == 0) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in_level = t < 8 * cnt;  // whole groups of 8: cnt * 8 threads, blocks of a multiple of 8
+  const int64_t k = lo + t / 8;
+  const int slot = (int)(t % 8);
+  const int2 kd = in_level ? kids[k] : make_int2(0, 0);
   float o[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) o[c] = 0.f;
-  for (int ch = kd.x; ch < kd.x + kd.y; ++ch) {
+  if (slot < kd.y) {
+    const int ch = kd.x + slot;
     const uint4 cc = cell[ch];
     // (z_P - z_C) / H = +1/4 for the lower half of an axis, -1/4 for the upper
     float ci[NC];
     load_row<NC>(M + (size_t)ch * ldm, ci);
     M2MBody<P>::run((cc.x & 1u) ? -1.f : 1.f, (cc.y & 1u) ? -1.f : 1.f, (cc.z & 1u) ? -1.f : 1.f, ci, o);
   }
-  store_row<NC>(M + (size_t)k * ldm, o);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    o[c] += __shfl_xor_sync(0xffffffffu, o[c], 4);
+    o[c] += __shfl_xor_sync(0xffffffffu, o[c], 2);
+    o[c] += __shfl_xor_sync(0xffffffffu, o[c], 1);
+  }
+  if (in_level && slot == 0 && kd.y > 0) store_row<NC>(M + (size_t)k * ldm, o);
 }
 
 // L2L, one thread per (cell of one level, child slot): the child's local
@@ -135,7 +145,8 @@ cudaError_t upward_p(Ctx &c, cudaStream_t st) {
   note_launch();
   for (int l = c.nlevels - 2; l >= 0; --l) {
     int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    k_m2m<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm, hfmm::P<float>(c.M));
+    k_m2m<P><<<blocks_for(8 * cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm,
+                                                   hfmm::P<float>(c.M));
     note_launch();
   }
   return cudaGetLastError();
