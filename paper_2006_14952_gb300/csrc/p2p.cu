@@ -17,7 +17,10 @@
 // below R_c; the others contribute nothing).  Lanes are split as (sink i,
 // stream s): with cs sinks in the chunk, S = 32 / cs streams walk the buffer,
 // so small leaves still keep the warp busy; the streams are added in a fixed
-// order at the end (deterministic).
+// order at the end (deterministic).  Chunks of 11, 12 or 17..20 sinks, where
+// S = 32 / cs leaves many lanes idle, are split in two halves instead: each lane
+// holds one sink of each half and evaluates both against every staged source
+// pair, which doubles the streams.
 //
 // The evaluation buffer holds sources in pairs, {-x0, -x1, -y0, -y1}
 // {-z0, -z1, -w0, -w1} (w = mass), so each lane evaluates two pairs per step
@@ -182,12 +185,28 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
     for (uint32_t cbase = r.x; cbase < r.x + r.y; cbase += 32) {
       const uint32_t rem = r.x + r.y - cbase;
       const int cs = rem < 32 ? (int)rem : 32;
-      const int S = 32 / cs, stream = lane / cs, il = lane % cs;
+      // two sinks per lane (one from each half of the chunk) where that doubles the
+      // streams: cs in {11, 12, 17..20}; otherwise one sink per lane
+      const int c2 = (cs + 1) >> 1;
+      const bool two = 2 * (32 / cs) < 32 / c2;
+      const int cl = two ? c2 : cs;  // sinks per lane group
+      const int S = 32 / cl, stream = lane / cl, il = lane % cl;
       const bool active = stream < S;
       const float4 xi = pm4[cbase + il];
+      const bool hasb = two && il + c2 < cs;
+      const float4 xib = hasb ? pm4[cbase + il + c2] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
       const float2 xx = f2(xi.x), xy = f2(xi.y), xz = f2(xi.z);
+      const float2 bxx = f2(xib.x), bxy = f2(xib.y), bxz = f2(xib.z);
       {
         float lo0 = xi.x, lo1 = xi.y, lo2 = xi.z, hi0 = xi.x, hi1 = xi.y, hi2 = xi.z;
+        if (hasb) {
+          lo0 = fminf(lo0, xib.x);
+          lo1 = fminf(lo1, xib.y);
+          lo2 = fminf(lo2, xib.z);
+          hi0 = fmaxf(hi0, xib.x);
+          hi1 = fmaxf(hi1, xib.y);
+          hi2 = fmaxf(hi2, xib.z);
+        }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
           lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
@@ -207,6 +226,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
         }
       }
       float2 ax = f2(0.f), ay = f2(0.f), az = f2(0.f);
+      float2 bx = f2(0.f), by = f2(0.f), bz = f2(0.f);
       uint32_t q = tb, jq = 0;
       bool pending = q < te;
       fetch_lst(q);
@@ -269,44 +289,60 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
         __syncwarp();  // the raw buffer and the entry tables are free again
         pending = q < te;
         if (pending) tot = issue(q, jq);  // in flight during the evaluation below
+        // the pair force of two staged sources on one sink, added to (sx, sy, sz)
+        auto pair2 = [&](float2 px, float2 py, float2 pz, const float4 &A, const float4 &B, float2 &sx, float2 &sy,
+                         float2 &sz) {
+          const float2 dx = __fadd2_rn(px, make_float2(A.x, A.y));
+          const float2 dy = __fadd2_rn(py, make_float2(A.z, A.w));
+          const float2 dz = __fadd2_rn(pz, make_float2(B.x, B.y));
+          const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          const bool in0 = (r2.x < fit.rc2) && (r2.x > 0.f);
+          const bool in1 = (r2.y < fit.rc2) && (r2.y > 0.f);
+          if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
+          // outside (0, R_c) the values below may be inf/NaN; the selects discard them
+          const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+          const float2 tt = __ffma2_rn(r2, rinv, f2(-fit.rmid));  // u = r - R_c / 2
+          float2 qv = f2(fit.c[9]);
+#pragma unroll
+          for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, f2(fit.c[j]));
+          const float2 ea = __fmul2_rn(r2, f2(fit.kexp));
+          const float2 sfac = __fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv);
+          const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+          float2 f = __fmul2_rn(__fmul2_rn(sfac, r3), make_float2(B.z, B.w));  // -S m / r^3
+          f.x = in0 ? f.x : 0.f;
+          f.y = in1 ? f.y : 0.f;
+          sx = __ffma2_rn(f, dx, sx);
+          sy = __ffma2_rn(f, dy, sy);
+          sz = __ffma2_rn(f, dz, sz);
+        };
         if (active) {
           const int np = (int)((kept + 1) >> 1);
+          if (two) {
+#pragma unroll 2
+            for (int kk = stream; kk < np; kk += S) {
+              const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
+              pair2(xx, xy, xz, A, B, ax, ay, az);
+              pair2(bxx, bxy, bxz, A, B, bx, by, bz);
+            }
+          } else {
 #pragma unroll 4
-          for (int kk = stream; kk < np; kk += S) {
-            const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
-            const float2 dx = __fadd2_rn(xx, make_float2(A.x, A.y));
-            const float2 dy = __fadd2_rn(xy, make_float2(A.z, A.w));
-            const float2 dz = __fadd2_rn(xz, make_float2(B.x, B.y));
-            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const bool in0 = (r2.x < fit.rc2) && (r2.x > 0.f);
-            const bool in1 = (r2.y < fit.rc2) && (r2.y > 0.f);
-            if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
-            // outside (0, R_c) the values below may be inf/NaN; the selects discard them
-            const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            const float2 tt = __ffma2_rn(r2, rinv, f2(-fit.rmid));  // u = r - R_c / 2
-            float2 qv = f2(fit.c[9]);
-#pragma unroll
-            for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, f2(fit.c[j]));
-            const float2 ea = __fmul2_rn(r2, f2(fit.kexp));
-            const float2 sfac = __fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv);
-            const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
-            float2 f = __fmul2_rn(__fmul2_rn(sfac, r3), make_float2(B.z, B.w));  // -S m / r^3
-            f.x = in0 ? f.x : 0.f;
-            f.y = in1 ? f.y : 0.f;
-            ax = __ffma2_rn(f, dx, ax);
-            ay = __ffma2_rn(f, dy, ay);
-            az = __ffma2_rn(f, dz, az);
+            for (int kk = stream; kk < np; kk += S) {
+              const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
+              pair2(xx, xy, xz, A, B, ax, ay, az);
+            }
           }
         }
         __syncwarp();  // the evaluation buffer is rewritten by the next fill
       }
       // add the streams of each sink in a fixed order
       buf[lane] = make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, 0.f);
+      buf[32 + lane] = make_float4(bx.x + bx.y, by.x + by.y, bz.x + bz.y, 0.f);
       __syncwarp();
       if (lane < cs) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
+        const int i0 = lane < cl ? lane : 32 + lane - cl;  // the sink's slot in the first group
         for (int s = 0; s < S; ++s) {
-          const float4 v = buf[lane + s * cs];
+          const float4 v = buf[i0 + s * cl];
           sx += v.x;
           sy += v.y;
           sz += v.z;
