@@ -55,12 +55,20 @@ __device__ __forceinline__ float exp2_mufu(float x) {
 }
 
 // kCap: source particles per fill (even); dynamic shared memory: 2 x 8 x kCap float4
+// The pair-factor constants duplicated into (x, x) pairs, the operand form of the
+// packed FP32x2 instructions, passed as kernel parameters (no register pairs to fill).
+struct PairFit2 {
+  float2 c[10];
+  float2 nrmid, kexp;  // -R_c / 2, -log2(e) / (4 r_s^2)
+  float rc2;
+};
+
 template <bool kCount, int kCap>
 __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
                                                 const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
                                                 const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
                                                 const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
-                                                const uint32_t *__restrict__ perm, int64_t n, float box, PairFit fit,
+                                                const uint32_t *__restrict__ perm, int64_t n, float box, PairFit2 fit,
                                                 float G, float *__restrict__ acc_out,
                                                 unsigned long long *__restrict__ ctr) {
   extern __shared__ float4 p2p_smem[];
@@ -301,11 +309,11 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
           if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
           // outside (0, R_c) the values below may be inf/NaN; the selects discard them
           const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-          const float2 tt = __ffma2_rn(r2, rinv, f2(-fit.rmid));  // u = r - R_c / 2
-          float2 qv = f2(fit.c[9]);
+          const float2 tt = __ffma2_rn(r2, rinv, fit.nrmid);  // u = r - R_c / 2
+          float2 qv = fit.c[9];
 #pragma unroll
-          for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, f2(fit.c[j]));
-          const float2 ea = __fmul2_rn(r2, f2(fit.kexp));
+          for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, fit.c[j]);
+          const float2 ea = __fmul2_rn(r2, fit.kexp);
           const float2 sfac = __fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv);
           const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
           float2 f = __fmul2_rn(__fmul2_rn(sfac, r3), make_float2(B.z, B.w));  // -S m / r^3
@@ -378,6 +386,11 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   auto kern = count ? (small ? k_p2p<true, 128> : k_p2p<true, 256>) : (small ? k_p2p<false, 128> : k_p2p<false, 256>);
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
+  PairFit2 fit2;  // the context's fit as packed operand pairs
+  for (int j = 0; j < 10; ++j) fit2.c[j] = make_float2(c.fit.c[j], c.fit.c[j]);
+  fit2.nrmid = make_float2(-c.fit.rmid, -c.fit.rmid);
+  fit2.kexp = make_float2(c.fit.kexp, c.fit.kexp);
+  fit2.rc2 = c.fit.rc2;
   // two buffers (raw copies, evaluation pairs) of kCap float4 per warp
   const size_t dyn = (size_t)2 * 8 * (small ? 128 : 256) * sizeof(float4);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -385,7 +398,7 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   kern<<<g, T, dyn, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
-                        (float)c.prm.box, c.fit, (float)c.prm.G, acc, ctr);
+                        (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr);
   note_launch();
   return cudaGetLastError();
 }
