@@ -189,7 +189,7 @@ void hfmm_destroy(hfmm_ctx *h) {
                   &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc, &c.m2l_mid, &c.tab,
                   &c.mlp_w, &c.cand, &c.mlp_scratch, &c.fseg, &c.fseg_next, &c.seg_a, &c.seg_b, &c.acc_a,
                   &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
-                  &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate};
+                  &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p};
   for (DBuf *b : bufs) release(*b);
   pm_release(c);
   if (c.gexec) cudaGraphExecDestroy(c.gexec);

@@ -189,6 +189,8 @@ struct Ctx {
   // segment bases, runs of M2L / P2P entries per (sink, level)
   DBuf fseg, fseg_next, seg_a, seg_b, acc_a, acc_b, segbase, btot2, segpre, ctot;
   DBuf rm_key, rm_beg, rm_cnt, rp_key, rp_beg, rp_cnt;
+  // runs per sink (counters during the walk) and each run's rank among its sink's runs
+  DBuf rm_rank, rp_rank, rcnt_m, rcnt_p;
   uint64_t cap_seg = 0, cap_run = 0;
   int64_t nrun_m = 0, nrun_p = 0, frontier_items = 0;
   DBuf m2l, m2l_alt, p2p, p2p_alt;  // packed u64 entries

@@ -219,6 +219,8 @@ struct TravBufs {
   uint64_t *rm_key, *rp_key;            // runs: (sink << 8 | level)
   uint64_t *rm_beg, *rp_beg;            // runs: first output entry
   uint32_t *rm_cnt, *rp_cnt;            // runs: entries
+  uint32_t *rm_rank, *rp_rank;          // runs: rank among the runs of its sink (its level order)
+  uint32_t *rcnt_m, *rcnt_p;            // per sink: runs recorded so far (one per level at most)
   unsigned long long *btot;             // per-block partial sums (4 per block)
   unsigned long long capF, capS, capM, capP, capR;
 };
@@ -590,12 +592,14 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
           B.rm_key[r] = ((unsigned long long)sink << 8) | (unsigned)iter;
           B.rm_beg[r] = nm + pv[1];
           B.rm_cnt[r] = (uint32_t)tv[1];
+          B.rm_rank[r] = B.rcnt_m[sink]++;  // a sink has one segment per level: no other writer
         }
         if (tv[2] > 0) {
           const unsigned long long r = nrp + run[3] + ex[3];
           B.rp_key[r] = ((unsigned long long)sink << 8) | (unsigned)iter;
           B.rp_beg[r] = np + pv[2];
           B.rp_cnt[r] = (uint32_t)tv[2];
+          B.rp_rank[r] = B.rcnt_p[sink]++;
         }
       }
       __syncthreads();
@@ -884,6 +888,12 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
     TRY(ensure(c.rp_key, c.cap_run * 8));
     TRY(ensure(c.rp_beg, c.cap_run * 8));
     TRY(ensure(c.rp_cnt, c.cap_run * 4));
+    TRY(ensure(c.rm_rank, c.cap_run * 4));
+    TRY(ensure(c.rp_rank, c.cap_run * 4));
+    TRY(ensure(c.rcnt_m, (size_t)c.nnodes * 4 + 64));
+    TRY(ensure(c.rcnt_p, (size_t)c.nnodes * 4 + 64));
+    TRY(cudaMemsetAsync(c.rcnt_m.p, 0, (size_t)c.nnodes * 4, st));
+    TRY(cudaMemsetAsync(c.rcnt_p.p, 0, (size_t)c.nnodes * 4, st));
     TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), st));
     TravBufs B;
     B.fa = P<uint64_t>(c.front);
@@ -907,6 +917,10 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
     B.rp_beg = P<uint64_t>(c.rp_beg);
     B.rm_cnt = P<uint32_t>(c.rm_cnt);
     B.rp_cnt = P<uint32_t>(c.rp_cnt);
+    B.rm_rank = P<uint32_t>(c.rm_rank);
+    B.rp_rank = P<uint32_t>(c.rp_rank);
+    B.rcnt_m = P<uint32_t>(c.rcnt_m);
+    B.rcnt_p = P<uint32_t>(c.rcnt_p);
     B.btot = P<unsigned long long>(c.btot2);
     B.capF = c.cap_front;
     B.capS = c.cap_seg;
@@ -949,9 +963,18 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
 
 namespace {
 
-__global__ void k_iota(uint32_t *__restrict__ v, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = (uint32_t)i;
+// Counting sort of the runs by sink: run r of sink s goes to roff[s] + rank[r]
+// (rank = its level order among the sink's runs), the order a stable sort by
+// (sink, level) gives.
+__global__ void k_run_place(const uint64_t *__restrict__ key, const uint32_t *__restrict__ rank,
+                            const uint32_t *__restrict__ roff, int64_t nr, uint64_t *__restrict__ key_s,
+                            uint32_t *__restrict__ idx) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const uint64_t k = key[r];
+  const uint32_t pos = roff[(uint32_t)(k >> 8)] + rank[r];
+  key_s[pos] = k;
+  idx[pos] = (uint32_t)r;
 }
 
 __global__ void k_run_gather(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ cnt,
@@ -987,34 +1010,29 @@ __global__ void k_run_copy(const uint64_t *__restrict__ key_s, const uint32_t *_
 }  // namespace
 
 // The walk leaves each level's entries grouped by sink; a sink that stays a
-// leaf over several levels has one run per level.  Sort the runs by (sink,
-// level), place them with a prefix sum of their lengths and copy: the list
-// ends up grouped by sink (levels in order, walk order within a level) with
-// CSR bounds.  Cost: a sort of the runs (one per sink and level) and one pass
-// over the entries.
+// leaf over several levels has one run per level.  Order the runs by (sink,
+// level) with a counting sort (the walk counted each sink's runs and ranked
+// them by level), place them with a prefix sum of their lengths and copy: the
+// list ends up grouped by sink (levels in order, walk order within a level)
+// with CSR bounds.  Cost: a scan over the cells, a pass over the runs and one
+// pass over the entries.
 static cudaError_t merge_runs(Ctx &c, DBuf &L, DBuf &A, int64_t n, DBuf &rkey, DBuf &rbeg, DBuf &rcnt, int64_t nr,
-                              uint32_t *csr_beg, uint32_t *csr_end, uint32_t *csr_mid, int sink_bits,
+                              DBuf &rrank, DBuf &rsink, uint32_t *csr_beg, uint32_t *csr_end, uint32_t *csr_mid,
                               cudaStream_t st) {
   cudaError_t e;
   if (n == 0 || nr == 0) return cudaSuccess;
   if ((e = ensure(A, n * 8)) != cudaSuccess) return e;
-  // scratch: key_alt u64 | idx u32 | idx_alt u32 | cnt_s u32 | dst u32
-  if ((e = ensure(c.tmp2, (size_t)nr * 24 + 64)) != cudaSuccess) return e;
-  uint64_t *key_alt = P<uint64_t>(c.tmp2);
-  uint32_t *idx = reinterpret_cast<uint32_t *>(key_alt + nr);
-  uint32_t *idx_alt = idx + nr, *cnt_s = idx_alt + nr, *dst = cnt_s + nr;
+  // scratch: key_s u64 | idx u32 | roff u32 [nnodes] | cnt_s u32 | dst u32
+  const int64_t nn = c.nnodes > 0 ? c.nnodes : 1;
+  if ((e = ensure(c.tmp2, (size_t)nr * 20 + (size_t)nn * 4 + 64)) != cudaSuccess) return e;
+  uint64_t *keys = P<uint64_t>(c.tmp2);
+  uint32_t *idx = reinterpret_cast<uint32_t *>(keys + nr);
+  uint32_t *roff = idx + nr, *cnt_s = roff + nn, *dst = cnt_s + nr;
   const int T = 256;
-  k_iota<<<blocks_for(nr, T), T, 0, st>>>(idx, nr);
+  uint64_t *rtotal = P<uint64_t>(c.d_small) + 1;  // (reused for the entry total below)
+  if ((e = scan_u32(P<uint32_t>(rsink), roff, rtotal, (size_t)nn, c.offs, st)) != cudaSuccess) return e;
+  k_run_place<<<blocks_for(nr, T), T, 0, st>>>(P<uint64_t>(rkey), P<uint32_t>(rrank), roff, nr, keys, idx);
   note_launch();
-  bool alt = false;
-  uint64_t *keys = P<uint64_t>(rkey);
-  if ((e = radix_sort_u64(keys, idx, key_alt, idx_alt, (size_t)nr, 0, 8 + sink_bits, &alt, c.tmp, st)) !=
-      cudaSuccess)
-    return e;
-  if (alt) {
-    keys = key_alt;
-    idx = idx_alt;
-  }
   k_run_gather<<<blocks_for(nr, T), T, 0, st>>>(idx, P<uint32_t>(rcnt), cnt_s, nr);
   note_launch();
   uint64_t *total = P<uint64_t>(c.d_small) + 1;
@@ -1052,12 +1070,12 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   TRY(cudaMemsetAsync(c.p2p_end.p, 0, nn * 4, st));
   int sink_bits = 1;
   while (((int64_t)1 << sink_bits) < nn) ++sink_bits;
-  TRY(merge_runs(c, c.p2p, c.p2p_alt, c.np2p, c.rp_key, c.rp_beg, c.rp_cnt, c.nrun_p, P<uint32_t>(c.p2p_beg),
-                 P<uint32_t>(c.p2p_end), nullptr, sink_bits, st));
+  TRY(merge_runs(c, c.p2p, c.p2p_alt, c.np2p, c.rp_key, c.rp_beg, c.rp_cnt, c.nrun_p, c.rp_rank, c.rcnt_p,
+                 P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), nullptr, st));
   const bool tables = c.prm.m2l_precision == 0 && c.prm.m2l_tables && c.tab_k > 0;
   if (c.nm2l > 0 && !tables) {
-    TRY(merge_runs(c, c.m2l, c.m2l_alt, c.nm2l, c.rm_key, c.rm_beg, c.rm_cnt, c.nrun_m, P<uint32_t>(c.m2l_beg),
-                   P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid), sink_bits, st));
+    TRY(merge_runs(c, c.m2l, c.m2l_alt, c.nm2l, c.rm_key, c.rm_beg, c.rm_cnt, c.nrun_m, c.rm_rank, c.rcnt_m,
+                   P<uint32_t>(c.m2l_beg), P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid), st));
     if (c.prm.mac_mode == 1) {  // learned orders: stable pass on the order bits -> (order, sink)
       bool alt = false;
       TRY(ensure(c.m2l_alt, c.nm2l * 8));
