@@ -233,38 +233,6 @@ constexpr int kTT = 256;  // threads of the traversal kernel
 constexpr int kFlatten = HFMM_FLATTEN;
 constexpr int kTW = kTT / 32;
 
-// Exclusive block-wide prefix of one value per thread (all threads call it);
-// returns the exclusive prefix, *tot receives the block total.
-__device__ __forceinline__ unsigned long long block_exscan(unsigned long long v, unsigned long long *wsum,
-                                                           unsigned long long *tot) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  unsigned long long x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[wp] = x;
-  __syncthreads();
-  unsigned long long before = 0, all = 0;
-#pragma unroll
-  for (int q = 0; q < kTW; ++q) {
-    const unsigned long long w = wsum[q];
-    if (q < wp) before += w;
-    all += w;
-  }
-  __syncthreads();
-  *tot = all;
-  return before + x - v;
-}
-
-// Block-wide sum of one value per thread (all threads call it).
-__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, unsigned long long *wsum) {
-  unsigned long long tot;
-  (void)block_exscan(v, wsum, &tot);
-  return tot;
-}
-
 // Block-wide exclusive scans of N values per thread in one round (two block
 // barriers for all N); tot receives the N block totals.
 template <int N>
@@ -378,7 +346,7 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
   __shared__ uint32_t sw[kSw];
   __shared__ __align__(16) __nv_bfloat16 xs[kTW][kXs];
   __shared__ uint8_t dec[kTW][kDec];
-  __shared__ unsigned long long wsum[kTW], pre[4], all[4], run[4];
+  __shared__ unsigned long long pre[4], all[4], run[4];
   __shared__ unsigned long long wsum4[4][kTW];
   // level state, uniform over the grid (kept in shared memory, out of the registers)
   __shared__ uint64_t *cur, *nxt;
