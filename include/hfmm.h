@@ -81,14 +81,15 @@ typedef struct {
                           T_c = D_c(-o h) h^(|c|+1) (Eq. m2l with the truncated D of Sec. 2.2)
                           from a per-(level, offset) table built once in FP64 on the device;
                           other pairs evaluate D per pair.  0 (default) = every pair
-                          evaluates D: on the 2M-particle clustered set the 224-byte table
-                          row per pair costs more than evaluating D (7.1 vs 6.6 ms of M2L).
-                          Used by m2l_precision 0 only. */
+                          evaluates D: on the 2M-particle clustered set (leaf 48, theta 0.35,
+                          p 6) loading a table row per pair costs more than evaluating D
+                          (2.79 vs 1.90 ms of M2L).  Used by m2l_precision 0 only. */
   /* Launch shapes (0 = built-in default; results do not depend on them beyond
      FP32 summation order).  The autotuner (autotune.py) picks them per GPU and
      workload and stores them in a JSON cache. */
   int tile_p2p_stage;  /* P2P source particles staged per warp: 128 or 256 (default 256) */
-  int tile_p2p_blocks; /* P2P resident blocks of 256 threads per SM, 1..8 (default 8) */
+  int tile_p2p_blocks; /* P2P grid: blocks of 256 threads per SM, 1..8 (default 8; the kernel is
+                          persistent and at most 2 of them are resident per SM) */
   int tile_m2l_blocks; /* cap on M2L blocks of 128 threads, per SM, 1..64 (default 64) */
   int tile_trav_blocks;/* traversal blocks of 256 threads per SM, 1..4 (default 4; capped by occupancy) */
   int use_graph;       /* 1 = after the traversal (the last point where the host reads sizes back),
@@ -138,8 +139,10 @@ const char *hfmm_last_error(const hfmm_ctx *ctx);
  * sort by (key, input index), split cells holding more than leaf_max particles
  * (depth cap 21), per-particle FP32 offsets from the geometric leaf centre.
  * pos_soa: device FP64 [3][n]; mass: device FP32 [n]; n >= 0 (n = 0 gives an
- * empty tree).  Synchronises `stream` once per tree level.  The library keeps
- * no reference to pos/mass after the call returns.
+ * empty tree).  The levels are built in one cooperative launch; `stream` is
+ * synchronised once to read the node and level counts back (again if the node
+ * capacity had to grow).  The library keeps no reference to pos/mass after the
+ * call returns.
  */
 int hfmm_build_tree(hfmm_ctx *ctx, const double *pos_soa, const float *mass, int64_t n, void *stream);
 
@@ -147,8 +150,12 @@ int hfmm_build_tree(hfmm_ctx *ctx, const double *pos_soa, const float *mass, int
  * Short-range accelerations of the particles of the last hfmm_build_tree:
  * P2M, M2M, dual-tree traversal with the hybrid acceptance rules, M2L, L2L,
  * L2P and the cut-off P2P (Secs. 2.1-2.3).  acc_soa: device FP32 [3][n], input
- * particle order, overwritten.  HFMM_ERR_STATE before any build_tree.
- * Synchronises `stream` once per traversal level.
+ * particle order, overwritten.  HFMM_ERR_STATE before any build_tree;
+ * HFMM_ERR_OOM when the interaction lists do not fit in device memory (list
+ * capacities start from a guess scaled with leaf_max and only lists that
+ * overflow are grown, the walk then repeated).  The traversal is one
+ * cooperative launch; `stream` is synchronised once after it to read the list
+ * sizes back, and once more after a tensor-core M2L to read its status word.
  */
 int hfmm_short_range_forces(hfmm_ctx *ctx, float *acc_soa, void *stream);
 
