@@ -11,8 +11,8 @@
 //
 // One lane per (sink, source) pair; a warp walks the pairs of one sink (lists
 // are grouped by sink), keeps its partial local expansion in registers and
-// reduces it across the warp at the end, so no atomics are used and the
-// result is deterministic.  Each launch adds into L (one launch per order).  The expansion order is a template parameter: all
+// reduces it across the warp at the end (through shared memory, in a fixed
+// order), so no atomics are used and the result is deterministic.  Each launch adds into L (one launch per order).  The expansion order is a template parameter: all
 // index arithmetic is literal in the generated straight-line bodies
 // (gen_bodies.py -> gen_bodies.cuh).  For p >= 6 the output coefficients are split
 // over G warps (slice g owns the outputs with index = g mod G); for p >= 7 the
@@ -73,13 +73,30 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
       M2LBody<P, G, g>::run(Rx * rinv, Ry * rinv, Rz * rinv, f, U, Mp, acc);
     }
   }
+  if constexpr (!kSmem) {
+    // sum over the lanes by a transpose in shared memory: each lane writes its
+    // partial row (stride NC + 1: no bank conflicts), then lane c adds column c
+    // over the 32 rows in lane order (deterministic) and stores it
+    static_assert(G == 1, "the transpose path sums whole rows");
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    float a = acc[s];
+    for (int s = 0; s < NC; ++s) wsm[lane * (NC + 1) + s] = acc[s];
+    __syncwarp();
+    for (int cix = lane; cix < NC; cix += 32) {
+      float a = 0.f;
+#pragma unroll 8
+      for (int m = 0; m < 32; ++m) a += wsm[m * (NC + 1) + cix];
+      L[(size_t)k * ldm + cix] += a;
+    }
+    __syncwarp();
+  } else {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    const int n = s * G + g;
-    if (lane == 0 && n < NC) L[(size_t)k * ldm + n] += a;
+    for (int s = 0; s < NS; ++s) {
+      float a = acc[s];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      const int n = s * G + g;
+      if (lane == 0 && n < NC) L[(size_t)k * ldm + n] += a;
+    }
   }
 }
 
@@ -94,7 +111,8 @@ __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_m2l(int64_t nn, co
                                              const uint64_t *__restrict__ lst, const float *__restrict__ M,
                                              float *__restrict__ L, int ldm, float inv_rs) {
   extern __shared__ float sm[];
-  float *wsm = sm + (threadIdx.x >> 5) * (M2LSlices<P>::kSmem ? ncoef(P) * 32 : 0);
+  // per warp: p >= 7 the staged multipoles (32 x NC), else the reduction transpose (32 x (NC + 1))
+  float *wsm = sm + (threadIdx.x >> 5) * (M2LSlices<P>::kSmem ? ncoef(P) * 32 : 32 * (ncoef(P) + 1));
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nn * G; w += nw) {
     const uint32_t k = (uint32_t)(w / G);
@@ -135,7 +153,8 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
   if (g > cap) g = cap;
   // r / r_s with r in half units: x = r_half * (L / 2^22) / r_s
   const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
-  size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float) : 0;
+  size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float)
+                                    : (size_t)4 * 32 * (ncoef(P) + 1) * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_m2l<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
