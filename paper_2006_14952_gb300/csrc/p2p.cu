@@ -326,14 +326,14 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
         if (active) {
           const int np = (int)((kept + 1) >> 1);
           if (two) {
-#pragma unroll 2
+#pragma unroll 4
             for (int kk = stream; kk < np; kk += S) {
               const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
               pair2(xx, xy, xz, A, B, ax, ay, az);
               pair2(bxx, bxy, bxz, A, B, bx, by, bz);
             }
           } else {
-#pragma unroll 4
+#pragma unroll 8
             for (int kk = stream; kk < np; kk += S) {
               const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
               pair2(xx, xy, xz, A, B, ax, ay, az);
