@@ -26,7 +26,7 @@ import os
 import statistics
 import time
 
-# knob -> (candidates, the phase timing it is judged on); the first candidate is the default
+# knob -> (candidates, the phase timing it is scored on); the first candidate is the default
 KNOBS = {
     "tile_p2p_stage": ([256, 128], "t_p2p"),
     "tile_p2p_blocks": ([8, 4, 2], "t_p2p"),
