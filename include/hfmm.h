@@ -203,6 +203,33 @@ int hfmm_step(hfmm_ctx *ctx, double *pos_soa, float *vel_soa, float *acc_soa, do
 int hfmm_get_stats(hfmm_ctx *ctx, hfmm_stats *out);
 
 /*
+ * Interaction counts of the comparison of Sec. 3 (Figs. 5-6: the P2P and M2L
+ * kernel counts of the truncated FMM against a conventional FMM; the counts
+ * depend only on the tree and the acceptance criterion).  Runs the dual-tree
+ * walk alone (no expansions, no forces) on the tree of the last
+ * hfmm_build_tree, with
+ *   conventional = 0: the hybrid acceptance of Sec. 2.3 with the context's
+ *     theta, transition_rule and size_rule and geometric decisions (also on a
+ *     mac_mode 1 context), from the root against its 27 nearest periodic
+ *     images, exactly the walk of hfmm_short_range_forces;
+ *   conventional = 1: a conventional FMM's acceptance, the opening-angle test
+ *     of Sec. 2.3 alone (accept M2L iff L / S_c <= theta with the context's
+ *     size_rule; otherwise open the larger cell, both on a tie; two leaves give
+ *     P2P), with no cut-off skip and no transition region, from the single pair
+ *     (root, root) of the primary box: the walk a conventional FMM performs
+ *     before treating the periodic images by Ewald summation.
+ * out: host int64 [4]: M2L cell pairs, P2P leaf pairs, particle pairs on the
+ * P2P lists (sum over P2P entries of n_sink n_source, a leaf against itself
+ * included), cell pairs classified over all levels.  Replaces the context's
+ * interaction lists (hfmm_get_stats and hfmm_export then report this walk's;
+ * the next hfmm_short_range_forces walks again); list capacities grown by
+ * the walk are kept.  Synchronises the stream.  HFMM_ERR_ARG for a null out or
+ * conventional outside {0, 1}; HFMM_ERR_STATE before any build_tree;
+ * HFMM_ERR_OOM when the lists do not fit in device memory.
+ */
+int hfmm_interaction_counts(hfmm_ctx *ctx, int conventional, int64_t *out, void *stream);
+
+/*
  * Copy an internal array to host memory for inspection.  With host_buf NULL,
  * *bytes receives the size needed; otherwise at most *bytes are copied and
  * *bytes receives the size.  Synchronises the device.  Formats:

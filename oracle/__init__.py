@@ -69,6 +69,7 @@ def lib():
             L.orc_destroy.argtypes = [P]
             L.orc_build_tree.argtypes = [P, i64, P, P]
             L.orc_traverse.argtypes = [P]
+            L.orc_traverse_conventional.argtypes = [P]
             L.orc_upward.argtypes = [P]
             L.orc_m2l_pass.argtypes = [P]
             L.orc_downward.argtypes = [P, P]
@@ -251,8 +252,23 @@ class FMM:
     def size(self, what):
         return int(lib().orc_size(self._c, {"n": 0, "nodes": 1, "levels": 2, "p2p": 3, "m2l": 4}[what]))
 
-    def traverse(self):
-        _check(lib().orc_traverse(self._c), "traverse")
+    def traverse(self, conventional=False):
+        """The hybrid walk of Sec. 2.3, or (conventional=True) the conventional-FMM
+        walk the interaction counts of Sec. 3 are compared against: the opening-angle
+        test alone, from (root, root) of the primary box."""
+        if conventional:
+            _check(lib().orc_traverse_conventional(self._c), "traverse_conventional")
+        else:
+            _check(lib().orc_traverse(self._c), "traverse")
+
+    def counts(self):
+        """Interaction counts of the current lists (Sec. 3): M2L cell pairs, P2P leaf
+        pairs, and particle pairs on the P2P lists (sum of n_sink n_source)."""
+        nodes = self.nodes()
+        p2p, m2l = self.lists()
+        cnt = nodes[:, 5]
+        pp = int((cnt[p2p[:, 0]] * cnt[p2p[:, 1]]).sum()) if len(p2p) else 0
+        return {"m2l": len(m2l), "p2p": len(p2p), "p2p_particle_pairs": pp}
 
     def forces(self) -> np.ndarray:
         acc = np.zeros((3, self.n))

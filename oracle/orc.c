@@ -15,6 +15,8 @@
  *   - direct truncated pair sum a = G sum m f_(1) r     Sec. 2.2, force equation g(r)
  *   - Morton-key octree with a leaf limit               Sec. 2.1 (leaf limiter)
  *   - dual-tree traversal with the three-rule MAC       Sec. 2.3, itemised criteria
+ *   - the conventional-FMM walk the interaction counts  Sec. 3 (Figs. 5-6): the second
+ *     are compared against                                criterion alone, from (root, root)
  *   - P2P with the hard cutoff                          Sec. 2.1 (P2P), Sec. 2.2
  *
  * Readings where the paper is silent or garbled:
@@ -544,8 +546,10 @@ static void push3(int64_t **buf, int64_t *n, int64_t *cap, int64_t a, int64_t b,
  *   transition (must open): S_c > R_c (rule 0) or S_max > R_c (rule 1);
  *   accept: L / S_c <= theta, i.e. (2 w)^2 <= theta^2 S_c^2, with w the half-unit
  *   side of the source (size_rule 0) or of the larger cell (size_rule 1).
+ * conventional != 0: the acceptance test alone (no skip, no transition region),
+ * the opening-angle criterion of a conventional FMM (Sec. 2.3, second item).
  */
-static int mac_classify(const orc_ctx *c, int64_t a, int64_t b, int s) {
+static int mac_classify(const orc_ctx *c, int64_t a, int64_t b, int s, int conventional) {
   int64_t wa = (int64_t)1 << (ORC_DEPTH - c->lev[a]);
   int64_t wb = (int64_t)1 << (ORC_DEPTH - c->lev[b]);
   int sh[3] = {s / 9 - 1, (s / 3) % 3 - 1, s % 3 - 1};
@@ -562,24 +566,37 @@ static int mac_classify(const orc_ctx *c, int64_t a, int64_t b, int s) {
     sm2 += gap * gap;
     sx2 += far * far;
   }
-  if ((double)sm2 > c->rc2h) return 0;
-  int trans = c->rule == 0 ? ((double)sc2 > c->rc2h) : ((double)sx2 > c->rc2h);
+  if (!conventional && (double)sm2 > c->rc2h) return 0;
+  int trans = conventional ? 0 : c->rule == 0 ? ((double)sc2 > c->rc2h) : ((double)sx2 > c->rc2h);
   int64_t wl = (c->size_rule == 0) ? wb : (wa > wb ? wa : wb);
   if (!trans && (double)(4 * wl * wl) <= c->theta2 * (double)sc2) return 1;
   return 2;
 }
 
-int orc_traverse(orc_ctx *c) {
+/*
+ * Dual-tree walk (Sec. 2.3): a stack of (sink, source, shift) cell pairs; an
+ * accepted pair goes to the M2L list, two unaccepted leaves to the P2P list,
+ * otherwise the larger cell is opened (both on a tie, the other one when the
+ * larger is a leaf).  The hybrid walk starts from the root against the 27
+ * nearest periodic images of itself (R_c < L / 2 reaches no further); the
+ * conventional walk (Sec. 3) from the single pair (root, root): the walk of
+ * the primary box, a conventional FMM treating the periodic images apart (by
+ * Ewald summation, Sec. 3).
+ */
+static int walk(orc_ctx *c, int conventional) {
   if (!c) return -1;
   c->np2p = 0; c->nm2l = 0;
   if (c->n == 0) return 0;
   int64_t *stk = NULL, nst = 0, cst = 0;
-  for (int s = 0; s < 27; ++s) push3(&stk, &nst, &cst, 0, 0, s);
+  if (conventional)
+    push3(&stk, &nst, &cst, 0, 0, 13); /* shift index 13 = (0, 0, 0) */
+  else
+    for (int s = 0; s < 27; ++s) push3(&stk, &nst, &cst, 0, 0, s);
   while (nst > 0) {
     --nst;
     int64_t a = stk[3 * nst], b = stk[3 * nst + 1];
     int s = (int)stk[3 * nst + 2];
-    int cls = mac_classify(c, a, b, s);
+    int cls = mac_classify(c, a, b, s, conventional);
     if (cls == 0) continue;
     if (cls == 1) {
       push3(&c->m2l, &c->nm2l, &c->cap_m2l, a, b, s);
@@ -604,6 +621,11 @@ int orc_traverse(orc_ctx *c) {
   free(stk);
   return 0;
 }
+
+int orc_traverse(orc_ctx *c) { return walk(c, 0); }
+
+/* The conventional walk: replaces the lists; for interaction counts only. */
+int orc_traverse_conventional(orc_ctx *c) { return walk(c, 1); }
 
 /* ------------------------------------------------------------------------ */
 /* FMM passes (Sec. 2.1 order: upward, M2L, downward, P2P).                  */

@@ -387,6 +387,29 @@ int hfmm_short_range_forces_host(hfmm_ctx *h, const double *pos, const float *ma
   return HFMM_OK;
 }
 
+int hfmm_interaction_counts(hfmm_ctx *h, int conventional, int64_t *out, void *stream) {
+  if (!h) return HFMM_ERR_ARG;
+  Ctx &c = h->c;
+  if (!out) return fail(c, HFMM_ERR_ARG, "null output pointer");
+  if (conventional != 0 && conventional != 1) return fail(c, HFMM_ERR_ARG, "conventional must be 0 or 1");
+  if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "interaction_counts before build_tree");
+  for (int i = 0; i < 4; ++i) out[i] = 0;
+  if (c.n == 0) return HFMM_OK;
+  cudaStream_t st = S(stream);
+  c.count_walk = conventional ? 2 : 1;
+  cudaError_t e = traverse(c, st);
+  c.count_walk = 0;
+  if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "traversal frontier above 2^32 entries");
+  if (e != cudaSuccess) return cuda_fail(c, e, "traverse");
+  int64_t pp = 0;
+  if ((e = p2p_list_particle_pairs(c, st, &pp)) != cudaSuccess) return cuda_fail(c, e, "count pairs");
+  out[0] = c.nm2l;
+  out[1] = c.np2p;
+  out[2] = pp;
+  out[3] = c.frontier_items;
+  return HFMM_OK;
+}
+
 int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   if (!h || !o) return HFMM_ERR_ARG;
   Ctx &c = h->c;

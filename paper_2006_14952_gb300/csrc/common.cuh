@@ -220,6 +220,10 @@ struct Ctx {
   DBuf mlp_w;
   bool have_mlp = false;
   bool collect = false;
+  // set for the duration of an interaction-count walk: 1 = hybrid acceptance
+  // with geometric decisions, 2 = conventional acceptance (no cut-off rules,
+  // primary box only)
+  int count_walk = 0;
   DBuf cand;
   uint64_t cand_cap = 0;
   int64_t ncand_last = 0;  // candidates written by the last collection
@@ -250,6 +254,8 @@ struct Ctx {
 cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st);
 cudaError_t traverse(Ctx &c, cudaStream_t st);
 cudaError_t sort_lists(Ctx &c, cudaStream_t st);
+// particle pairs on the current P2P list (sum over entries of n_sink n_source); synchronises st
+cudaError_t p2p_list_particle_pairs(Ctx &c, cudaStream_t st, int64_t *out);
 cudaError_t upward(Ctx &c, cudaStream_t st);
 // M2L of the list entries of order q (the CSR bounds m2l_beg/m2l_end cover
 // exactly those entries); adds into L.

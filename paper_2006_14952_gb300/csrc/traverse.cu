@@ -12,6 +12,10 @@
 // shift) pairs is classified, the outputs are counted and prefix-summed, and
 // the M2L pairs, P2P pairs and child pairs are written in frontier order.
 //
+// The conventional walk (interaction counts of Sec. 3) applies rule 2 alone,
+// with no cut-off skip and no transition region, from the single root pair of
+// the primary box (shift index 13) instead of the 27 nearest periodic images.
+//
 // Learned acceptance (mac_mode 1) keeps rules 1 and 3 and the self-pair rule;
 // in place of rule 2 a pair whose larger side satisfies L / S_c <= theta (the
 // safety bound) is a candidate: its 12 features go through the network
@@ -40,6 +44,7 @@ struct Mac {
   int64_t acc_thr[kDepth + 1];  // accept iff S_c^2 >= acc_thr[level of the larger cell]
   int rule, size_rule;
   int mode;   // 0 geometric, 1 learned, 2 collect
+  int conv;   // 1: conventional acceptance (rule 2 alone, primary box only)
   int order;  // p (geometric M2L order, and the largest learned order)
   int tab_k;  // operator-table half extent (0: no table)
   // learned / collect
@@ -86,8 +91,8 @@ __device__ __forceinline__ uint8_t classify(uint4 ca, uint4 cb, uint32_t s, int2
     sm2 += (int64_t)g * g;
     sx2 += (int64_t)f * f;
   }
-  if (sm2 > m.rc2i) return kSkip;
-  const bool trans = m.rule == 0 ? sc2 > m.rc2i : sx2 > m.rc2i;
+  if (!m.conv && sm2 > m.rc2i) return kSkip;
+  const bool trans = !m.conv && (m.rule == 0 ? sc2 > m.rc2i : sx2 > m.rc2i);
   const uint32_t lv = m.size_rule == 0 ? cb.w : (ca.w < cb.w ? ca.w : cb.w);  // level of the cell setting L
   if (!trans && sc2 >= m.acc_thr[lv]) return m.mode == 0 ? kM2L : kCandidate;  // acc_thr >= 1: self pairs open
   return open_rule(ca, cb, ka, kb);
@@ -357,7 +362,9 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
   const unsigned nb = gridDim.x, bid = blockIdx.x;
   const unsigned long long gw = (unsigned long long)bid * kTW + wp, nw = (unsigned long long)nb * kTW;
-  if (bid == 0 && tid < 27) B.fa[tid] = pack_pair(0, 0, (uint32_t)tid);
+  // the root against its 27 nearest periodic images, or (conventional) itself
+  const unsigned nroot = m.conv ? 1u : 27u;
+  if (bid == 0 && tid < nroot) B.fa[tid] = pack_pair(0, 0, m.conv ? 13u : (uint32_t)tid);
   if (bid == 0 && tid == 0) {
     B.map_a[0] = 0;
     B.seg_a[0] = 0;
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
     nsegs = B.seg_b;
     sst = B.st_a;
     nsst = B.st_b;
-    nf = 27;
+    nf = nroot;
     nseg = 1;
     nm = np = nrm = nrp = items = 0;
   }
@@ -793,7 +800,8 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   for (int l = 0; l <= kDepth; ++l) m.acc_thr[l] = c.acc_thr[l];
   m.rule = c.prm.transition_rule;
   m.size_rule = c.prm.size_rule;
-  m.mode = c.collect ? 2 : c.prm.mac_mode;
+  m.mode = c.collect ? 2 : c.count_walk ? 0 : c.prm.mac_mode;
+  m.conv = c.count_walk == 2 ? 1 : 0;
   m.order = c.p;
   m.tab_k = (c.prm.m2l_precision == 0 && c.prm.m2l_tables) ? c.tab_k : 0;
   m.w = static_cast<const __nv_bfloat16 *>(c.mlp_w.p);
@@ -1017,6 +1025,22 @@ static cudaError_t merge_runs(Ctx &c, DBuf &L, DBuf &A, int64_t n, DBuf &rkey, D
 
 // Group both lists by sink (the walk's order kept within a sink) and build CSR
 // bounds; count the particle pairs P2P evaluates.
+cudaError_t p2p_list_particle_pairs(Ctx &c, cudaStream_t st, int64_t *out) {
+  *out = 0;
+  if (c.np2p == 0) return cudaSuccess;
+  const unsigned T = 256;
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c.d_small.p);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(cnt, 0, 8, st)) != cudaSuccess) return e;
+  k_pairs_in_list<<<blocks_for(c.np2p, T), T, 0, st>>>(P<uint64_t>(c.p2p), c.np2p, P<uint2>(c.range), cnt);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(c.h_pinned, cnt, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  *out = (int64_t)c.h_pinned[0];
+  return cudaSuccess;
+}
+
 cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   cudaError_t e;
 #define TRY(x)                      \

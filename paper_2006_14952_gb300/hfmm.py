@@ -29,7 +29,7 @@ MLP_WEIGHTS = 5512
 SYMBOLS = ["hfmm_default_params", "hfmm_create", "hfmm_destroy", "hfmm_last_error", "hfmm_build_tree",
            "hfmm_short_range_forces", "hfmm_short_range_forces_host", "hfmm_get_stats", "hfmm_export",
            "hfmm_load_mlp", "hfmm_collect_training_pairs", "hfmm_mlp_infer", "hfmm_mlp_grad", "hfmm_mlp_adam",
-           "hfmm_morton_sort_noalloc", "hfmm_pm_long_range", "hfmm_step"]
+           "hfmm_morton_sort_noalloc", "hfmm_pm_long_range", "hfmm_step", "hfmm_interaction_counts"]
 
 
 class Params(C.Structure):
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
         L.hfmm_mlp_grad.restype = i32
         L.hfmm_mlp_adam.argtypes = [vp, C.c_float, i32, vp, vp, vp, vp, vp]
         L.hfmm_mlp_adam.restype = i32
+        L.hfmm_interaction_counts.argtypes = [vp, i32, C.POINTER(i64), vp]
+        L.hfmm_interaction_counts.restype = i32
         _lib = L
         return L
 
@@ -246,6 +248,14 @@ class Solver:
         s = Stats()
         self._check(self._lib.hfmm_get_stats(self._h, C.byref(s)), "hfmm_get_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def interaction_counts(self, conventional=False, stream=None) -> dict:
+        """Kernel counts of Sec. 3 on the current tree: the hybrid walk, or the
+        conventional FMM's (opening-angle test alone, primary box)."""
+        out = (C.c_int64 * 4)()
+        self._check(self._lib.hfmm_interaction_counts(self._h, 1 if conventional else 0, out,
+                                                      _stream_handle(stream)), "hfmm_interaction_counts")
+        return {"m2l": out[0], "p2p": out[1], "p2p_particle_pairs": out[2], "frontier_pairs": out[3]}
 
     def load_mlp(self, weights_bf16):
         """weights_bf16: numpy uint16 [5512] holding BF16 bit patterns."""
