@@ -45,7 +45,8 @@ enum {
   HFMM_ERR_ARG = -1,      /* invalid argument (null pointer, bad size or parameter) */
   HFMM_ERR_OOM = -2,      /* device or host allocation failed */
   HFMM_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed */
-  HFMM_ERR_CAPACITY = -4, /* an index format limit was exceeded (e.g. > 2^27 tree nodes) */
+  HFMM_ERR_CAPACITY = -4, /* an index format limit was exceeded (more than 2^27 tree nodes; an
+                             interaction list above 2^32 - 1 entries) */
   HFMM_ERR_STATE = -5,    /* call out of order (e.g. forces before build_tree) */
   HFMM_ERR_TIMEOUT = -6   /* a bounded device-side wait gave up */
 };
@@ -153,7 +154,9 @@ int hfmm_build_tree(hfmm_ctx *ctx, const double *pos_soa, const float *mass, int
  * particle order, overwritten.  HFMM_ERR_STATE before any build_tree;
  * HFMM_ERR_OOM when the interaction lists do not fit in device memory (list
  * capacities start from a guess scaled with leaf_max and only lists that
- * overflow are grown, the walk then repeated).  The traversal is one
+ * overflow are grown, the walk then repeated); HFMM_ERR_CAPACITY when the M2L
+ * or the P2P list exceeds 2^32 - 1 entries (the lists grouped by sink are
+ * addressed through 32-bit bounds).  The traversal is one
  * cooperative launch; `stream` is synchronised once after it to read the list
  * sizes back, and once more after a tensor-core M2L to read its status word.
  */

@@ -277,6 +277,8 @@ cudaError_t post_traversal_graph(Ctx &c, float *acc, cudaStream_t st, bool prof)
 
 }  // namespace
 
+constexpr const char *kWalkLimit = "traversal did not complete within its capacity retries and depth bound";
+
 int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (!h) return HFMM_ERR_ARG;
   Ctx &c = h->c;
@@ -299,8 +301,11 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
   if (prof) cudaEventRecord(c.ev[4], st);
   e = traverse(c, st);
-  if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "traversal frontier above 2^32 entries");
+  if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, kWalkLimit);
   if (e != cudaSuccess) return cuda_fail(c, e, "traverse");
+  // the sink-grouped lists are addressed through 32-bit CSR bounds
+  if (c.nm2l > (int64_t)UINT32_MAX || c.np2p > (int64_t)UINT32_MAX)
+    return fail(c, HFMM_ERR_CAPACITY, "an interaction list above 2^32 - 1 entries");
   if (prof) cudaEventRecord(c.ev[5], st);
   c.last_graph = false;
   if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2)) {
@@ -399,7 +404,7 @@ int hfmm_interaction_counts(hfmm_ctx *h, int conventional, int64_t *out, void *s
   c.count_walk = conventional ? 2 : 1;
   cudaError_t e = traverse(c, st);
   c.count_walk = 0;
-  if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "traversal frontier above 2^32 entries");
+  if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, kWalkLimit);
   if (e != cudaSuccess) return cuda_fail(c, e, "traverse");
   int64_t pp = 0;
   if ((e = p2p_list_particle_pairs(c, st, &pp)) != cudaSuccess) return cuda_fail(c, e, "count pairs");
