@@ -52,9 +52,11 @@ CONFIGS = {
     # M2L against P2P on this set
     "nfw-2m": Config("nfw-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.7, order=6, theta=0.35,
                      leaf_max=48, seed=1002),
-    # Zel'dovich-like lattice, N = 256^3, 40% in 1000 NFW haloes, PM 256^3, p 6
+    # Zel'dovich-like lattice, N = 256^3, 40% in 1000 NFW haloes, PM 256^3, p 6; solved
+    # like nfw-2m (leaves of 48, theta 0.35): at leaves of 16 its interaction lists
+    # and walk frontier outgrow the device memory
     "zeldovich-16m": Config("zeldovich-16m", 256 ** 3, 256, "zeldovich", halo_count=1000, halo_frac=0.4,
-                            order=6, seed=1003),
+                            order=6, theta=0.35, leaf_max=48, seed=1003),
     # learned-acceptance evaluation set, N = 128^3, 85% in 2000 NFW haloes (solved like nfw-2m)
     "nfw85-2m": Config("nfw85-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.85, order=6, theta=0.35,
                        leaf_max=48, seed=1004),
