@@ -1023,8 +1023,6 @@ static cudaError_t merge_runs(Ctx &c, DBuf &L, DBuf &A, int64_t n, DBuf &rkey, D
   return cudaSuccess;
 }
 
-// Group both lists by sink (the walk's order kept within a sink) and build CSR
-// bounds; count the particle pairs P2P evaluates.
 cudaError_t p2p_list_particle_pairs(Ctx &c, cudaStream_t st, int64_t *out) {
   *out = 0;
   if (c.np2p == 0) return cudaSuccess;
@@ -1041,6 +1039,8 @@ cudaError_t p2p_list_particle_pairs(Ctx &c, cudaStream_t st, int64_t *out) {
   return cudaSuccess;
 }
 
+// Group both lists by sink (the walk's order kept within a sink) and build CSR
+// bounds; count the particle pairs P2P evaluates.
 cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   cudaError_t e;
 #define TRY(x)                      \
