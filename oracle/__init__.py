@@ -10,8 +10,11 @@ compiles it with gcc and marshals numpy arrays through ctypes.
 
 Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   prefactors, derivative tensor, P2M/M2M/M2L/L2L/L2P, direct sum, tree,
-  traversal, FMM forces: pinned (closed forms, symbolic derivatives, exact
-  identities, brute force, special cases).
+  traversal (hybrid and conventional), interaction counts, FMM forces, the
+  network's forward and gradient: pinned (closed forms, symbolic derivatives,
+  exact identities, brute force, textbook interaction lists, special cases).
+Sibling modules: ``pm.py`` (PM long range and the KDK step) and
+``poly_split.py`` (a polynomial truncation of the split), both numpy FP64.
 """
 from __future__ import annotations
 
