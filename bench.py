@@ -1,6 +1,7 @@
 """Benchmark: short-range forces/s of the truncated FMM on the clustered
 N = 128^3 set (70% of the particles in 2000 NFW haloes, 30% uniform; PM 128^3,
-r_s = 1.25 cells, R_c = 4.5 r_s, leaves <= 16), one GB300.
+r_s = 1.25 cells, R_c = 4.5 r_s; solved with leaves <= 48, theta 0.35, p 6, the
+setting that meets the 1e-4 RMS accuracy bar), one GB300.
 
 One step = one pass of the whole short-range path over the resident particle
 set: wrap + Morton keys, sort, octree, P2M/M2M, traversal, list grouping, M2L,
@@ -35,9 +36,9 @@ UNIT = "forces/s"
 FP32_LANES_PER_SM = 128
 N_SM = 152
 # FP32 work of one P2P pair inside the cut-off (FMA = 2 flop): separation (3),
-# r^2 (1 mul + 2 fma = 5), rsqrt (1), t = r / R_c (2), the truncation factor
-# S = exp2(r^2 k) Q(t) with Q of degree 9 (exponent 1 + exp2 1 + 9 fma 18 +
-# product 1 = 21), -S m / r^3 (4), accumulation (3 fma = 6).
+# r^2 (1 mul + 2 fma = 5), rsqrt (1), u = r^2 r^-1 - R_c / 2 (1 fma = 2), the
+# truncation factor S = exp2(r^2 k) Q(u) with Q of degree 9 (exponent 1 +
+# exp2 1 + 9 fma 18 + product 1 = 21), -S m / r^3 (4), accumulation (3 fma = 6).
 P2P_FLOPS_PER_PAIR = 41
 
 
