@@ -39,7 +39,7 @@ N_SM = 152
 # r^2 (1 mul + 2 fma = 5), rsqrt (1), u = r^2 r^-1 - R_c / 2 (1 fma = 2), the
 # truncation factor S = exp2(r^2 k) Q(u) with Q of degree 9 (exponent 1 +
 # exp2 1 + 9 fma 18 + product 1 = 21), -S m / r^3 (4), accumulation (3 fma = 6).
-P2P_FLOPS_PER_PAIR = 41
+P2P_FLOPS_PER_PAIR = 42
 
 
 def parse():
