@@ -139,8 +139,9 @@ const char *hfmm_last_error(const hfmm_ctx *ctx);
  * box (x - L floor(x / L)), 63-bit Morton keys on a 2^21 grid per side, stable
  * sort by (key, input index), split cells holding more than leaf_max particles
  * (depth cap 21), per-particle FP32 offsets from the geometric leaf centre.
- * pos_soa: device FP64 [3][n]; mass: device FP32 [n]; n >= 0 (n = 0 gives an
- * empty tree).  The levels are built in one cooperative launch; `stream` is
+ * pos_soa: device FP64 [3][n], finite values (any finite position is wrapped;
+ * a NaN or infinite coordinate is not checked and lands in an arbitrary cell);
+ * mass: device FP32 [n]; n >= 0 (n = 0 gives an empty tree).  The levels are built in one cooperative launch; `stream` is
  * synchronised once to read the node and level counts back (again if the node
  * capacity had to grow).  The library keeps no reference to pos/mass after the
  * call returns.
