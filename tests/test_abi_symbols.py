@@ -64,3 +64,30 @@ def test_struct_layout_matches_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         a, b = map(int, subprocess.check_output([exe]).split())
     assert a == ctypes.sizeof(hfmm.Params) and b == ctypes.sizeof(hfmm.Stats)
+
+
+def test_every_context_call_rejects_a_null_context_without_a_gpu():
+    """A NULL context is an argument error before any CUDA call is made."""
+    from paper_2006_14952_gb300 import hfmm
+
+    L = hfmm.load()
+    out = (ctypes.c_int64 * 4)()
+    nb = ctypes.c_size_t(0)
+    cnt = ctypes.c_int64(0)
+    calls = {
+        "hfmm_build_tree": lambda: L.hfmm_build_tree(None, None, None, 0, None),
+        "hfmm_short_range_forces": lambda: L.hfmm_short_range_forces(None, None, None),
+        "hfmm_short_range_forces_host": lambda: L.hfmm_short_range_forces_host(None, None, None, 0, None, None),
+        "hfmm_pm_long_range": lambda: L.hfmm_pm_long_range(None, None, None),
+        "hfmm_step": lambda: L.hfmm_step(None, None, None, None, 0.0, None),
+        "hfmm_interaction_counts": lambda: L.hfmm_interaction_counts(None, 0, out, None),
+        "hfmm_get_stats": lambda: L.hfmm_get_stats(None, None),
+        "hfmm_export": lambda: L.hfmm_export(None, 0, None, ctypes.byref(nb)),
+        "hfmm_load_mlp": lambda: L.hfmm_load_mlp(None, None, 0),
+        "hfmm_collect_training_pairs": lambda: L.hfmm_collect_training_pairs(None, 1, 1, None, None,
+                                                                             ctypes.byref(cnt), None),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name  # HFMM_ERR_ARG
+    L.hfmm_destroy(None)  # accepted
+    assert L.hfmm_last_error(None) is not None
