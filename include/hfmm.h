@@ -308,6 +308,21 @@ int hfmm_mlp_adam(const float *grad, float lr, int step, float *weights, float *
                   void *stream);
 
 /*
+ * Throughput probe for the roofline denominators of the ALU-bound kernels (the
+ * P2P pair sum and the CUDA-core M2L).  The paper has no counterpart: it is a
+ * measurement aid.  kind 0 = FP32 fused multiply-add (2 flop each), 1 = packed
+ * FP32x2 fused multiply-add (4 flop each), 2 = ex2.approx, 3 = rsqrt.approx
+ * (1 operation each).  Launches 8 blocks of 256 threads per SM, each thread
+ * running 16 independent chains for iters x 8 steps, once untimed and once
+ * timed with CUDA events on `stream`.  scratch: device FP32 buffer of
+ * 2048 x (SM count) values (overwritten).  *rate receives flop/s (kinds 0, 1)
+ * or operations/s (kinds 2, 3); *ms (may be NULL) the timed launch in
+ * milliseconds.  Synchronises the stream.  HFMM_ERR_ARG for a bad kind, iters
+ * < 1 or a null scratch or rate; HFMM_ERR_CUDA if a launch or an event fails.
+ */
+int hfmm_alu_peak(int kind, int iters, float *scratch, double *rate, double *ms, void *stream);
+
+/*
  * Allocation-free Morton keys + sort.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory at the point of
  * the call - for example a host runtime that plans all GPU memory up front and
@@ -320,15 +335,21 @@ int hfmm_mlp_adam(const float *grad, float lr, int step, float *weights, float *
  * Scratch: one file-scope device array of fixed size (about 6.5 MB, enough for
  * HFMM_NOALLOC_MAX_N particles) that every GPU loading the library holds until
  * the process exits.  No cudaMalloc, cudaFree or allocating library routine is
- * called.  The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current, so make the first call on a
- * device before any stream capture.  Every call on a device shares the array:
+ * called.  The first call in each CUDA context looks up that array's device
+ * address (cudaGetSymbolAddress) with the context current, so make the first
+ * call on a device before any stream capture.  The address is kept per context
+ * (keyed by the context's process-unique id), so a call from another context on
+ * the same device, or from the primary context re-created after
+ * cudaDeviceReset, looks the address up again rather than reusing a stale one.
+ * Every call on a device shares the array:
  * calls whose work overlaps on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.  Nothing in the array is
  * assumed to start at zero: each call writes every word before reading it.
  * Returns HFMM_OK; HFMM_ERR_CAPACITY if n > HFMM_NOALLOC_MAX_N; HFMM_ERR_ARG
  * for n < 0, box <= 0 or a null pointer with n > 0; HFMM_ERR_CUDA if a launch
- * fails.  Work is enqueued on `stream`; the call does not synchronise.
+ * fails, or, without launching anything, if a CUDA error of an earlier call
+ * was already pending on entry (that error is left pending for the caller).
+ * Work is enqueued on `stream`; the call does not synchronise.
  */
 #define HFMM_NOALLOC_MAX_N 524288
 int hfmm_morton_sort_noalloc(const double *pos_soa, int64_t n, double box, uint64_t *keys_out, uint32_t *perm_out,

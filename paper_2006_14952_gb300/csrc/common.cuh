@@ -93,6 +93,47 @@ __host__ __device__ inline void half_delta32(uint4 sink, uint4 src, uint32_t s, 
   dd[2] = (int)(((2u * src.z + 1u) << lb) - ((2u * sink.z + 1u) << la)) + shift_component(s, 2) * (int)kHalfBox;
 }
 
+// ---------------------------------------------------------------- Morton keys
+// Periodic wrap and 63-bit Morton key of one position (shared by the octree
+// build and the allocation-free sort, so both give the same keys).
+// x / L: when L is a power of two, x * (1/L) is the same correctly rounded
+// quotient (1/L exact), without an FP64 division.
+__device__ __forceinline__ double div_box(double x, double box, double inv_pow2) {
+  return inv_pow2 != 0.0 ? __dmul_rn(x, inv_pow2) : __ddiv_rn(x, box);
+}
+
+// x - L floor(x / L), each operation rounded separately (no FMA contraction).
+__device__ __forceinline__ double wrap_box(double x, double box, double inv_pow2) {
+  double q = floor(div_box(x, box, inv_pow2));
+  return __dsub_rn(x, __dmul_rn(box, q));
+}
+
+// Cell index of a wrapped coordinate on the 2^21 grid per side.
+__device__ __forceinline__ uint32_t grid_coord(double w, double box, double inv_pow2) {
+  double t = floor(__dmul_rn(div_box(w, box, inv_pow2), 2097152.0));
+  t = fmax(0.0, fmin(t, 2097151.0));
+  return (uint32_t)t;
+}
+
+// Spread the low 21 bits of v to every third bit.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+// Key of the (unwrapped) position (x, y, z): x bits above y bits above z bits.
+__device__ __forceinline__ uint64_t morton_key(double x, double y, double z, double box, double inv_pow2) {
+  const uint32_t k0 = grid_coord(wrap_box(x, box, inv_pow2), box, inv_pow2);
+  const uint32_t k1 = grid_coord(wrap_box(y, box, inv_pow2), box, inv_pow2);
+  const uint32_t k2 = grid_coord(wrap_box(z, box, inv_pow2), box, inv_pow2);
+  return (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
+}
+
 // ---------------------------------------------------------------- buffers
 struct DBuf {
   void *p = nullptr;

@@ -2,6 +2,8 @@
 // 63-bit Morton keys, stable sort by (key, input index)) for callers that may
 // not allocate device memory.  All scratch lives in one file-scope __device__
 // array of fixed size, so the call never reaches cudaMalloc or cudaFree.
+#include <cuda.h>  // driver-API types only; the functions are fetched through the runtime
+
 #include <mutex>
 
 #include "common.cuh"
@@ -19,62 +21,79 @@ constexpr size_t kScratchBytes = kAltKeyBytes + kAltIdxBytes + kSortScratchBytes
 // Shared by every call on a device; held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
+// The device address of g_noalloc_scratch belongs to the CUDA context that
+// loaded this module: another context on the same device (a driver-API
+// context, or the primary context re-created after cudaDeviceReset) has its
+// own copy.  The address is therefore cached per context, keyed by the
+// context's process-unique id (cuCtxGetId), and looked up again for a context
+// not seen before.  The two driver functions are fetched through the runtime,
+// so the library does not link the driver library itself.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+constexpr int kCacheSlots = 64;
+struct ScratchCache {
+  std::mutex mu;
+  bool resolved = false;
+  CtxGetCurrentFn get_current = nullptr;
+  CtxGetIdFn get_id = nullptr;
+  int used = 0, next = 0;
+  unsigned long long id[kCacheSlots] = {};
+  void *ptr[kCacheSlots] = {};
+};
+ScratchCache g_cache;
+
+bool resolve_driver_functions() {
+  if (g_cache.resolved) return g_cache.get_current && g_cache.get_id;
+  g_cache.resolved = true;
+  void *f0 = nullptr, *f1 = nullptr;
+  cudaDriverEntryPointQueryResult q0 = cudaDriverEntryPointSymbolNotFound, q1 = q0;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+      cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+      q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess)
+    return false;
+  g_cache.get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+  g_cache.get_id = reinterpret_cast<CtxGetIdFn>(f1);
+  return true;
+}
+
+// Id of the current context, 0 when there is none yet.
+bool current_context_id(unsigned long long *id) {
+  CUcontext ctx = nullptr;
+  if (g_cache.get_current(&ctx) != CUDA_SUCCESS) return false;
+  *id = 0;
+  return !ctx || g_cache.get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_noalloc_scratch in the current context.
 cudaError_t scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_cache.mu);
+  if (!resolve_driver_functions()) return cudaErrorNotSupported;
+  unsigned long long id = 0;
+  if (!current_context_id(&id)) return cudaErrorContextIsDestroyed;
+  for (int i = 0; id && i < g_cache.used; ++i)
+    if (g_cache.id[i] == id) {
+      *out = g_cache.ptr[i];
+      return cudaSuccess;
+    }
+  // First call in this context: the lookup also makes the runtime's context
+  // current when the thread had none (the id is read again below).
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  if (!current_context_id(&id) || !id) return cudaErrorContextIsDestroyed;
+  const int slot = g_cache.used < kCacheSlots ? g_cache.used++ : (g_cache.next++ % kCacheSlots);
+  g_cache.id[slot] = id;
+  g_cache.ptr[slot] = p;
+  *out = p;
   return cudaSuccess;
-}
-
-// x / L: when L is a power of two, x * (1/L) is the same correctly rounded
-// quotient (1/L exact), without an FP64 division
-__device__ __forceinline__ double div_box(double x, double box, double inv_pow2) {
-  return inv_pow2 != 0.0 ? __dmul_rn(x, inv_pow2) : __ddiv_rn(x, box);
-}
-
-__device__ __forceinline__ double wrap_box(double x, double box, double inv_pow2) {
-  double q = floor(div_box(x, box, inv_pow2));
-  return __dsub_rn(x, __dmul_rn(box, q));
-}
-
-__device__ __forceinline__ uint32_t grid_coord(double w, double box, double inv_pow2) {
-  double t = floor(__dmul_rn(div_box(w, box, inv_pow2), 2097152.0));
-  t = fmax(0.0, fmin(t, 2097151.0));
-  return (uint32_t)t;
-}
-
-__device__ __forceinline__ uint64_t spread3(uint32_t v) {
-  uint64_t x = v & 0x1fffffu;
-  x = (x | (x << 32)) & 0x001f00000000ffffull;
-  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-  x = (x | (x << 8)) & 0x100f00f00f00f00full;
-  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-  x = (x | (x << 2)) & 0x1249249249249249ull;
-  return x;
 }
 
 __global__ void k_keys_noalloc(const double *__restrict__ pos, int64_t n, double box, double inv_pow2,
                                uint64_t *__restrict__ key, uint32_t *__restrict__ idx) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t k0 = grid_coord(wrap_box(pos[i], box, inv_pow2), box, inv_pow2);
-  uint32_t k1 = grid_coord(wrap_box(pos[n + i], box, inv_pow2), box, inv_pow2);
-  uint32_t k2 = grid_coord(wrap_box(pos[2 * n + i], box, inv_pow2), box, inv_pow2);
-  key[i] = (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
+  key[i] = morton_key(pos[i], pos[n + i], pos[2 * n + i], box, inv_pow2);
   idx[i] = (uint32_t)i;
 }
 
@@ -89,6 +108,10 @@ extern "C" int hfmm_morton_sort_noalloc(const double *pos_soa, int64_t n, double
   if (n > kNoAllocMaxN) return HFMM_ERR_CAPACITY;
   if (n == 0) return HFMM_OK;
   if (!pos_soa || !keys_out || !perm_out) return HFMM_ERR_ARG;
+  // An error left by an earlier call of the caller's stays theirs: report it
+  // without launching and without clearing it, so that the launch checks
+  // below see this call's own launches only.
+  if (cudaPeekAtLastError() != cudaSuccess) return HFMM_ERR_CUDA;
   void *base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return HFMM_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -13,43 +13,11 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-// x - L floor(x / L), each operation rounded separately (no FMA contraction).
-// x / L: when L is a power of two, x * (1/L) is the same correctly rounded
-// quotient (1/L exact), without an FP64 division
-__device__ __forceinline__ double div_box(double x, double box, double inv_pow2) {
-  return inv_pow2 != 0.0 ? __dmul_rn(x, inv_pow2) : __ddiv_rn(x, box);
-}
-
-__device__ __forceinline__ double wrap_box(double x, double box, double inv_pow2) {
-  double q = floor(div_box(x, box, inv_pow2));
-  return __dsub_rn(x, __dmul_rn(box, q));
-}
-
-__device__ __forceinline__ uint32_t grid_coord(double w, double box, double inv_pow2) {
-  double t = floor(__dmul_rn(div_box(w, box, inv_pow2), 2097152.0));
-  t = fmax(0.0, fmin(t, 2097151.0));
-  return (uint32_t)t;
-}
-
-// spread the low 21 bits of v to every third bit
-__device__ __forceinline__ uint64_t spread3(uint32_t v) {
-  uint64_t x = v & 0x1fffffu;
-  x = (x | (x << 32)) & 0x001f00000000ffffull;
-  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-  x = (x | (x << 8)) & 0x100f00f00f00f00full;
-  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-  x = (x | (x << 2)) & 0x1249249249249249ull;
-  return x;
-}
-
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, double box, double inv_pow2, uint64_t *__restrict__ key,
                        uint32_t *__restrict__ idx) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t k0 = grid_coord(wrap_box(pos[i], box, inv_pow2), box, inv_pow2);
-  uint32_t k1 = grid_coord(wrap_box(pos[n + i], box, inv_pow2), box, inv_pow2);
-  uint32_t k2 = grid_coord(wrap_box(pos[2 * n + i], box, inv_pow2), box, inv_pow2);
-  key[i] = (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
+  key[i] = morton_key(pos[i], pos[n + i], pos[2 * n + i], box, inv_pow2);
   idx[i] = (uint32_t)i;
 }
 
@@ -63,10 +31,6 @@ __global__ void k_gather(const double *__restrict__ pos, const uint32_t *__restr
   xs[n + s] = wrap_box(pos[n + i], box, inv_pow2);
   xs[2 * n + s] = wrap_box(pos[2 * n + i], box, inv_pow2);
 }
-
-
-
-
 
 
 // FP64 offset from the geometric leaf centre, rounded once to FP32.

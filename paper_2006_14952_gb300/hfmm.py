@@ -29,7 +29,8 @@ MLP_WEIGHTS = 5512
 SYMBOLS = ["hfmm_default_params", "hfmm_create", "hfmm_destroy", "hfmm_last_error", "hfmm_build_tree",
            "hfmm_short_range_forces", "hfmm_short_range_forces_host", "hfmm_get_stats", "hfmm_export",
            "hfmm_load_mlp", "hfmm_collect_training_pairs", "hfmm_mlp_infer", "hfmm_mlp_grad", "hfmm_mlp_adam",
-           "hfmm_morton_sort_noalloc", "hfmm_pm_long_range", "hfmm_step", "hfmm_interaction_counts"]
+           "hfmm_morton_sort_noalloc", "hfmm_pm_long_range", "hfmm_step", "hfmm_interaction_counts",
+           "hfmm_alu_peak"]
 
 
 class Params(C.Structure):
@@ -105,6 +106,8 @@ def load(build_if_missing: bool = True):
         L.hfmm_mlp_adam.restype = i32
         L.hfmm_interaction_counts.argtypes = [vp, i32, C.POINTER(i64), vp]
         L.hfmm_interaction_counts.restype = i32
+        L.hfmm_alu_peak.argtypes = [i32, i32, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+        L.hfmm_alu_peak.restype = i32
         _lib = L
         return L
 
@@ -134,6 +137,24 @@ def mlp_infer(weights_bf16, x, stream=None):
     if rc != HFMM_OK:
         raise HfmmError(f"hfmm_mlp_infer: {ERRORS.get(rc, rc)}")
     return logits, cls
+
+
+ALU_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2, "rsqrt": 3}
+
+
+def alu_peak(kind: str, iters: int = 4096, stream=None):
+    """Measured throughput of one ALU instruction kind over the whole GPU:
+    (rate, ms); rate in flop/s for "ffma"/"ffma2", operations/s for "ex2"/"rsqrt"."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    scratch = torch.empty(2048 * sms, dtype=torch.float32, device="cuda")
+    rate, ms = C.c_double(0.0), C.c_double(0.0)
+    rc = load().hfmm_alu_peak(ALU_KINDS[kind], int(iters), C.c_void_p(scratch.data_ptr()), C.byref(rate),
+                              C.byref(ms), _stream_handle(stream))
+    if rc != HFMM_OK:
+        raise HfmmError(f"hfmm_alu_peak: {ERRORS.get(rc, rc)}")
+    return rate.value, ms.value
 
 
 def mlp_adam(grad, lr, step, weights, m1, m2, weights_bf16=None, stream=None):

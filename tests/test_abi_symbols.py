@@ -91,3 +91,13 @@ def test_every_context_call_rejects_a_null_context_without_a_gpu():
         assert call() == -1, name  # HFMM_ERR_ARG
     L.hfmm_destroy(None)  # accepted
     assert L.hfmm_last_error(None) is not None
+
+
+def test_alu_probe_rejects_bad_arguments_without_a_gpu():
+    from paper_2006_14952_gb300 import hfmm
+
+    L = hfmm.load()
+    rate = ctypes.c_double(0.0)
+    assert L.hfmm_alu_peak(4, 1, None, ctypes.byref(rate), None, None) == -1
+    assert L.hfmm_alu_peak(0, 0, None, ctypes.byref(rate), None, None) == -1
+    assert L.hfmm_alu_peak(0, 1, None, None, None, None) == -1
