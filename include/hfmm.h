@@ -99,6 +99,15 @@ typedef struct {
                           is updated in place while the launch sequence keeps its shape, else
                           re-instantiated.  Geometric acceptance, m2l_precision 0, profile bit 1
                           off; otherwise ignored. */
+  int tc_wait_polls;   /* m2l_precision 1 and 2: polls of the bounded wait for each chunk's MMAs before the
+                          call gives up with HFMM_ERR_TIMEOUT (0 = 2^22; -1 = no poll at all, so that
+                          every chunk gives up at once: a test of the error path).  After a give-up
+                          every CTA waits again, with the full 2^22 polls, for the MMAs it issued
+                          before it frees its tensor memory. */
+  int list_init;       /* initial capacity, in entries, of every traversal list (frontier, M2L, P2P,
+                          segments, runs) of a new context: 0 = a guess scaled with n and leaf_max;
+                          a small value makes the walk overflow and repeat with grown lists (the
+                          lists come out the same either way) */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */
@@ -116,6 +125,7 @@ typedef struct {
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
   int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
   int64_t frontier_pairs;     /* cell pairs the traversal classified, over all levels */
+  int64_t traverse_walks;     /* walks the last traversal took (1 + repeats after a list overflowed) */
 } hfmm_stats;
 
 typedef struct hfmm_ctx hfmm_ctx;

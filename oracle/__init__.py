@@ -11,7 +11,8 @@ compiles it with gcc and marshals numpy arrays through ctypes.
 Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   prefactors, derivative tensor, P2M/M2M/M2L/L2L/L2P, direct sum, tree,
   traversal (hybrid and conventional), interaction counts, FMM forces, the
-  network's forward and gradient: pinned (closed forms, symbolic derivatives,
+  network's forward and gradient, its forward with the FP32 error bound, the
+  pair features of the learned acceptance, the learned walk: pinned (closed forms, symbolic derivatives,
   exact identities, brute force, textbook interaction lists, special cases).
 Sibling modules: ``pm.py`` (PM long range and the KDK step) and
 ``poly_split.py`` (a polynomial truncation of the split), both numpy FP64.
@@ -95,6 +96,10 @@ def lib():
             L.orc_pair_error.restype = d
             L.orc_find_node.argtypes = [P, i32, C.c_uint32, C.c_uint32, C.c_uint32]
             L.orc_find_node.restype = i64
+            L.orc_pair_features.argtypes = [P, i64, i64, i32, P]
+            L.orc_mlp_forward_bound.argtypes = [P, P, P, i64, P, P, P, P]
+            L.orc_traverse_learned.argtypes = [P, P, P, P, P, i64, P]
+            L.orc_export_m2l_orders.argtypes = [P, P]
             _lib = L
     return _lib
 
@@ -215,6 +220,27 @@ def mlp_forward(w, x, rnd=1) -> np.ndarray:
     return out
 
 
+def mlp_forward_bound(w, x, xtol=None):
+    """The network at its rounding points (BF16 inputs and hidden activations,
+    exact sums) with a bound on the logits of any FP32 evaluation of it.
+    x [n][12]; xtol [n][12] or None: how far the evaluated features may be
+    from x before their BF16 rounding.  Returns (logits [n][8], bound [n][8],
+    class [n], mask [n]): the class is the argmax of the logits (ties to the
+    lower class), the mask has bit k set for every class the bound lets an
+    evaluation's argmax take."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 12)
+    n = x.shape[0]
+    xt = None if xtol is None else np.ascontiguousarray(np.broadcast_to(xtol, x.shape), dtype=np.float64)
+    lo = np.zeros((n, 8))
+    el = np.zeros((n, 8))
+    cls = np.zeros(n, dtype=np.int32)
+    mask = np.zeros(n, dtype=np.uint32)
+    _check(lib().orc_mlp_forward_bound(_p(w), _p(x), _p(xt), n, _p(lo), _p(el), _p(cls), _p(mask)),
+           "mlp_forward_bound")
+    return lo, el, cls, mask
+
+
 def mlp_loss_grad(w, x, labels, class_weights=None, rnd=1):
     w = np.ascontiguousarray(w, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 12)
@@ -312,6 +338,44 @@ class FMM:
         acc = np.zeros((3, self.n))
         _check(lib().orc_fmm_forces_given_lists(self._c, _p(acc)), "fmm_forces_given_lists")
         return acc
+
+    def pair_features(self, pairs) -> np.ndarray:
+        """The 12 learned-acceptance features [n][12] of (sink, source, shift) rows;
+        computes the multipoles first when they are missing."""
+        pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)
+        out = np.zeros((len(pairs), 12))
+        for i, (a, b, sh) in enumerate(pairs):
+            rc = lib().orc_pair_features(self._c, int(a), int(b), int(sh), _p(out[i]))
+            if rc != 0:
+                self.upward()
+                _check(lib().orc_pair_features(self._c, int(a), int(b), int(sh), _p(out[i])), "pair_features")
+        return out
+
+    def traverse_learned(self, w, ftol_rel, ftol_abs, ref_m2l=None, ref_orders=None) -> dict:
+        """The walk with the learned acceptance (the network in place of the
+        opening-angle rule, theta the safety bound).  ftol_rel, ftol_abs [12]:
+        feature tolerance of the evaluation the lists are compared with.  With
+        ref_m2l / ref_orders (an evaluation's M2L list and orders) a candidate
+        whose class the bound leaves open takes that list's decision."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        tr = np.ascontiguousarray(np.broadcast_to(ftol_rel, (12,)), dtype=np.float64)
+        ta = np.ascontiguousarray(np.broadcast_to(ftol_abs, (12,)), dtype=np.float64)
+        ref = None
+        nref = 0
+        if ref_m2l is not None:
+            r = np.concatenate([np.asarray(ref_m2l, dtype=np.int64).reshape(-1, 3),
+                                np.asarray(ref_orders, dtype=np.int64).reshape(-1, 1)], axis=1)
+            ref = np.ascontiguousarray(r[np.lexsort((r[:, 2], r[:, 1], r[:, 0]))])
+            nref = len(ref)
+        st = np.zeros(6)
+        _check(lib().orc_traverse_learned(self._c, _p(w), _p(tr), _p(ta), _p(ref), nref, _p(st)), "traverse_learned")
+        return {"candidates": int(st[0]), "ambiguous": int(st[1]), "resolved": int(st[2]),
+                "outside_bound": int(st[3]), "max_bound": float(st[4])}
+
+    def m2l_orders(self) -> np.ndarray:
+        out = np.zeros(self.size("m2l"), dtype=np.int64)
+        lib().orc_export_m2l_orders(self._c, _p(out))
+        return out
 
     def pair_error(self, a, b, s, q):
         return float(lib().orc_pair_error(self._c, int(a), int(b), int(s), int(q)))

@@ -398,6 +398,8 @@ typedef struct {
   /* interaction lists: (sink, source, shift index 0..26) */
   int64_t np2p, nm2l, cap_p2p, cap_m2l;
   int64_t *p2p, *m2l;
+  /* expansion order of each M2L entry (learned walk only; NULL: every entry has order p) */
+  int64_t *m2l_ord, cap_ord;
   /* expansions [nnodes][ncoef(p)] */
   double *M, *L;
   /* MAC thresholds */
@@ -408,7 +410,7 @@ void orc_destroy(orc_ctx *c) {
   if (!c) return;
   free(c->x); free(c->m); free(c->key); free(c->perm);
   free(c->lev); free(c->ic); free(c->first); free(c->count); free(c->child_first); free(c->nchild);
-  free(c->p2p); free(c->m2l); free(c->M); free(c->L);
+  free(c->p2p); free(c->m2l); free(c->m2l_ord); free(c->M); free(c->L);
   free(c);
 }
 
@@ -586,6 +588,7 @@ static int mac_classify(const orc_ctx *c, int64_t a, int64_t b, int s, int conve
 static int walk(orc_ctx *c, int conventional) {
   if (!c) return -1;
   c->np2p = 0; c->nm2l = 0;
+  free(c->m2l_ord); c->m2l_ord = NULL; c->cap_ord = 0;
   if (c->n == 0) return 0;
   int64_t *stk = NULL, nst = 0, cst = 0;
   if (conventional)
@@ -961,6 +964,7 @@ int orc_set_lists(orc_ctx *c, const int64_t *p2p, int64_t np2p, const int64_t *m
   if (!c) return -1;
   free(c->p2p);
   free(c->m2l);
+  free(c->m2l_ord); c->m2l_ord = NULL; c->cap_ord = 0;
   c->p2p = (int64_t *)malloc(sizeof(int64_t) * 3 * (np2p ? np2p : 1));
   c->m2l = (int64_t *)malloc(sizeof(int64_t) * 4 * (nm2l ? nm2l : 1));
   memcpy(c->p2p, p2p, sizeof(int64_t) * 3 * np2p);
@@ -1081,4 +1085,272 @@ int64_t orc_find_node(const orc_ctx *c, int lev, uint32_t ix, uint32_t iy, uint3
   for (int64_t k = c->level_start[lev]; k < c->level_start[lev + 1]; ++k)
     if (c->ic[3 * k] == ix && c->ic[3 * k + 1] == iy && c->ic[3 * k + 2] == iz) return k;
   return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned acceptance: the pair features, the network with a bound on any   */
+/* FP32 evaluation of it, and the walk that applies it.                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The 12 features of an ordered cell pair (sink a, source b displaced by
+ * shift s), all dimensionless (the feature list of the learned acceptance):
+ *   0 S_c / r_s       1 S_m / r_s        2 S_max / R_c
+ *   3 h_a / S_c       4 h_b / S_c        5 max(h_a, h_b) / S_c
+ *   6 (level_a - level_b) / 8            7 log2(1 + n_a) / 16   8 log2(1 + n_b) / 16
+ *   9 |(M~_100, M~_010, M~_001)| / |M~_000|    10 |(M~_m, |m| = 2)| / |M~_000|
+ *  11 S_c / R_c
+ * with S_c the centre distance, S_m and S_max the least and greatest distance
+ * between the two cubes (Sec. 2.3), h the cell sides, n the particle counts
+ * and M~_m = M_m / h_b^|m| the source's multipoles of Eq. p2m about its
+ * geometric centre in units of its side.  A massless source (M_000 = 0) has
+ * |M~_000| read as 1e-30, so its moment features are 0 or huge, never NaN.
+ * Needs the multipoles (orc_upward).  Plain FP64 from the exact integer cell
+ * geometry.
+ */
+int orc_pair_features(const orc_ctx *c, int64_t a, int64_t b, int s, double *f) {
+  if (!c || !c->M || a < 0 || b < 0 || a >= c->nnodes || b >= c->nnodes || s < 0 || s > 26) return -1;
+  int64_t wa = (int64_t)1 << (ORC_DEPTH - c->lev[a]);
+  int64_t wb = (int64_t)1 << (ORC_DEPTH - c->lev[b]);
+  int sh[3] = {s / 9 - 1, (s / 3) % 3 - 1, s % 3 - 1};
+  double sc2 = 0, sm2 = 0, sx2 = 0;
+  for (int d = 0; d < 3; ++d) {
+    int64_t ca = 2 * ((int64_t)c->ic[3 * a + d] * wa) + wa;
+    int64_t cb = 2 * ((int64_t)c->ic[3 * b + d] * wb) + wb + (int64_t)sh[d] * 4194304;
+    int64_t dd = cb - ca;
+    if (dd < 0) dd = -dd;
+    int64_t gap = dd - (wa + wb);
+    if (gap < 0) gap = 0;
+    int64_t far = dd + (wa + wb);
+    sc2 += (double)dd * (double)dd;
+    sm2 += (double)gap * (double)gap;
+    sx2 += (double)far * (double)far;
+  }
+  const double unit = c->box / 4194304.0; /* one half unit */
+  const double Sc = sqrt(sc2) * unit, Sm = sqrt(sm2) * unit, Sx = sqrt(sx2) * unit;
+  const double ha = 2.0 * (double)wa * unit, hb = 2.0 * (double)wb * unit;
+  f[0] = Sc / c->rs;
+  f[1] = Sm / c->rs;
+  f[2] = Sx / c->rc;
+  f[3] = ha / Sc;
+  f[4] = hb / Sc;
+  f[5] = (ha > hb ? ha : hb) / Sc;
+  f[6] = (double)(c->lev[a] - c->lev[b]) / 8.0;
+  f[7] = log2(1.0 + (double)c->count[a]) / 16.0;
+  f[8] = log2(1.0 + (double)c->count[b]) / 16.0;
+  const int nc = orc_ncoef(c->p);
+  const double *M = c->M + b * nc;
+  const double m0 = fabs(M[0]) + 1e-30;
+  double d2 = 0.0, q2 = 0.0;
+  for (int e = 1; e < 10 && e < nc; ++e) {
+    const int *m = g_mi[e];
+    const int deg = m[0] + m[1] + m[2];
+    const double v = M[e] / pow(hb, deg);
+    if (deg == 1) d2 += v * v; else q2 += v * v;
+  }
+  f[9] = sqrt(d2) / m0;
+  f[10] = sqrt(q2) / m0;
+  f[11] = Sc / c->rc;
+  return 0;
+}
+
+/* t > 0 rounded to FP32 and then to BF16, else 0: the activation of a hidden
+ * unit (rounding to FP32 first, as the network's FP32 accumulator does). */
+static double act_bf16(double t) { return t > 0 ? orc_bf16(t) : 0.0; }
+
+/*
+ * One layer, out = act(b + W in), with a bound on how far any FP32 evaluation
+ * can be from `out`.  Its inputs may differ from `in` by up to `ein`; the sum
+ * of the K products and the bias, accumulated in FP32 in any order (rounded
+ * or truncated at each step), differs from the exact sum by at most
+ * (K + 2) 2^-23 times the sum of the magnitudes.  A hidden unit's activation
+ * (FP32 -> BF16 after the ReLU) is monotone in the pre-activation, so the
+ * evaluation lies between the activations of the interval's two ends.
+ */
+static void layer_bound(const double *W, const double *bias, int nout, int nin, const double *in,
+                        const double *ein, int hidden, double *out, double *eout) {
+  const double gam = (double)(nin + 2) * ldexp(1.0, -23);
+  for (int u = 0; u < nout; ++u) {
+    double z = bias[u], mag = fabs(bias[u]), e = 0.0;
+    for (int k = 0; k < nin; ++k) {
+      const double wk = W[u * nin + k];
+      z += wk * in[k];
+      mag += fabs(wk) * (fabs(in[k]) + ein[k]);
+      e += fabs(wk) * ein[k];
+    }
+    e += gam * mag;
+    if (hidden) {
+      out[u] = act_bf16(z);
+      const double hi = act_bf16(z + e) - out[u], lo = out[u] - act_bf16(z - e);
+      eout[u] = hi > lo ? hi : lo;
+    } else {
+      out[u] = z;
+      eout[u] = e;
+    }
+  }
+}
+
+/*
+ * The network on one feature row, at its rounding points (inputs and hidden
+ * activations rounded to BF16, FP32 sums), and bounds elo[8] on the deviation
+ * of any FP32 evaluation's logits.  xtol (may be NULL): the evaluated
+ * features may differ from x by up to xtol[k] before their BF16 rounding.
+ * Returns the bit mask of the classes that can be the evaluation's argmax
+ * (ties to the lower class): classes whose upper bound reaches the largest
+ * lower bound.
+ */
+static uint32_t mlp_bound1(const double *w, const double *x, const double *xtol, double *lo, double *elo) {
+  double xi[MLP_IN], ex[MLP_IN], h1[MLP_H], e1[MLP_H], h2[MLP_H], e2[MLP_H];
+  for (int k = 0; k < MLP_IN; ++k) {
+    xi[k] = orc_bf16(x[k]);
+    ex[k] = 0.0;
+    if (xtol && xtol[k] > 0) {
+      const double up = orc_bf16(x[k] + xtol[k]) - xi[k], dn = xi[k] - orc_bf16(x[k] - xtol[k]);
+      ex[k] = up > dn ? up : dn;
+    }
+  }
+  layer_bound(w + OFF_W1, w + OFF_B1, MLP_H, MLP_IN, xi, ex, 1, h1, e1);
+  layer_bound(w + OFF_W2, w + OFF_B2, MLP_H, MLP_H, h1, e1, 1, h2, e2);
+  layer_bound(w + OFF_W3, w + OFF_B3, MLP_OUT, MLP_H, h2, e2, 0, lo, elo);
+  double lmax = -HUGE_VAL;
+  for (int o = 0; o < MLP_OUT; ++o)
+    if (lo[o] - elo[o] > lmax) lmax = lo[o] - elo[o];
+  uint32_t mask = 0;
+  for (int o = 0; o < MLP_OUT; ++o)
+    if (lo[o] + elo[o] >= lmax) mask |= 1u << o;
+  return mask;
+}
+
+/* Batch form: logits and bounds [n][8], class [n] (argmax of the nominal
+ * logits, ties to the lower class), plausible-class mask [n]. */
+int orc_mlp_forward_bound(const double *w, const double *x, const double *xtol, int64_t n, double *logits,
+                          double *bound, int32_t *cls, uint32_t *mask) {
+  for (int64_t i = 0; i < n; ++i) {
+    double *lo = logits + i * MLP_OUT, *el = bound + i * MLP_OUT;
+    const uint32_t m = mlp_bound1(w, x + i * MLP_IN, xtol ? xtol + i * MLP_IN : NULL, lo, el);
+    int best = 0;
+    for (int o = 1; o < MLP_OUT; ++o)
+      if (lo[o] > lo[best]) best = o;
+    if (cls) cls[i] = best;
+    if (mask) mask[i] = m;
+  }
+  return 0;
+}
+
+static void push1(int64_t **buf, int64_t *cap, int64_t n, int64_t v) {
+  if (n >= *cap) {
+    *cap = *cap ? 2 * *cap : 4096;
+    while (*cap <= n) *cap *= 2;
+    *buf = (int64_t *)realloc(*buf, sizeof(int64_t) * *cap);
+  }
+  (*buf)[n] = v;
+}
+
+static int cmp_ref4(const void *key, const void *row) {
+  const int64_t *x = (const int64_t *)key, *y = (const int64_t *)row;
+  for (int i = 0; i < 3; ++i)
+    if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+  return 0;
+}
+
+/*
+ * Dual-tree walk with the learned acceptance (the network in place of the
+ * opening-angle rule; the feature list above): rules 1 and 3 of Sec. 2.3 and
+ * the opening rules unchanged; a pair that the geometric rule would accept at
+ * the context's theta (the safety bound) is a candidate, and the network's
+ * class decides: 0 = open the pair as the geometric walk would, k >= 1 = M2L
+ * at order min(k + 1, p).  The decision is the argmax of the nominal logits
+ * (mlp_bound1, with the features within ftol_rel |f| + ftol_abs of these FP64
+ * values).  Where the bound admits more than one class, an FP32 evaluation
+ * may take any of them; with `ref` (an M2L list [nref][4] = sink, source,
+ * shift, order, sorted by the first three columns) the walk then takes the
+ * decision that list records (M2L at its order when the pair is in it, else
+ * open) and checks that it is one of the admitted classes.
+ * stats[6]: candidates, candidates with more than one admitted class, those
+ * resolved from ref, ref decisions outside the admitted classes, the largest
+ * logit bound seen, (reserved, 0).  The lists (with their orders,
+ * orc_export_m2l_orders) replace the context's.  Computes the multipoles
+ * (orc_upward) when they are missing.
+ */
+int orc_traverse_learned(orc_ctx *c, const double *w, const double *ftol_rel, const double *ftol_abs,
+                         const int64_t *ref, int64_t nref, double *stats) {
+  if (!c || !w) return -1;
+  c->np2p = 0; c->nm2l = 0;
+  free(c->m2l_ord); c->m2l_ord = NULL; c->cap_ord = 0;
+  double st[6] = {0, 0, 0, 0, 0, 0};
+  if (c->n == 0) {
+    if (stats) memcpy(stats, st, sizeof st);
+    return 0;
+  }
+  if (!c->M && orc_upward(c)) return -1;
+  int64_t *stk = NULL, nst = 0, cst = 0;
+  for (int s = 0; s < 27; ++s) push3(&stk, &nst, &cst, 0, 0, s);
+  while (nst > 0) {
+    --nst;
+    int64_t a = stk[3 * nst], b = stk[3 * nst + 1];
+    int s = (int)stk[3 * nst + 2];
+    int cls = mac_classify(c, a, b, s, 0);
+    if (cls == 0) continue;
+    if (cls == 1) { /* candidate: the network decides */
+      double f[MLP_IN], tol[MLP_IN], lo[MLP_OUT], el[MLP_OUT];
+      orc_pair_features(c, a, b, s, f);
+      for (int k = 0; k < MLP_IN; ++k) tol[k] = ftol_rel[k] * fabs(f[k]) + ftol_abs[k];
+      const uint32_t mask = mlp_bound1(w, f, tol, lo, el);
+      int k = 0;
+      for (int o = 1; o < MLP_OUT; ++o)
+        if (lo[o] > lo[k]) k = o;
+      st[0] += 1;
+      for (int o = 0; o < MLP_OUT; ++o)
+        if (el[o] > st[4]) st[4] = el[o];
+      if (mask != (1u << k)) {
+        st[1] += 1;
+        if (ref) {
+          const int64_t key[3] = {a, b, s};
+          const int64_t *hit = (const int64_t *)bsearch(key, ref, (size_t)nref, 4 * sizeof(int64_t), cmp_ref4);
+          int kr = 0;
+          if (hit) kr = (int)hit[3] - 1; /* order q = k + 1 (orders above p were capped at p) */
+          /* with the cap, class k >= p - 1 all give order p: admitted if any such class is */
+          int ok = 0;
+          if (kr <= 0) ok = (mask & 1u) != 0, kr = 0;
+          else if (kr >= c->p - 1) {
+            for (int o = c->p - 1; o < MLP_OUT; ++o) ok |= (mask >> o) & 1u;
+          } else ok = (mask >> kr) & 1u;
+          st[2] += 1;
+          if (!ok) st[3] += 1;
+          k = kr;
+        }
+      }
+      if (k > 0) {
+        const int q = k + 1 < c->p ? k + 1 : c->p;
+        push1(&c->m2l_ord, &c->cap_ord, c->nm2l, q);
+        push3(&c->m2l, &c->nm2l, &c->cap_m2l, a, b, s);
+        continue;
+      }
+      cls = 2; /* open */
+    }
+    int leafa = c->nchild[a] == 0, leafb = c->nchild[b] == 0;
+    if (leafa && leafb) {
+      push3(&c->p2p, &c->np2p, &c->cap_p2p, a, b, s);
+      continue;
+    }
+    int opena, openb;
+    if (leafa) { opena = 0; openb = 1; }
+    else if (leafb) { opena = 1; openb = 0; }
+    else if (c->lev[a] < c->lev[b]) { opena = 1; openb = 0; }
+    else if (c->lev[b] < c->lev[a]) { opena = 0; openb = 1; }
+    else { opena = 1; openb = 1; }
+    int64_t a0 = opena ? c->child_first[a] : a, a1 = opena ? a0 + c->nchild[a] : a + 1;
+    int64_t b0 = openb ? c->child_first[b] : b, b1 = openb ? b0 + c->nchild[b] : b + 1;
+    for (int64_t x = a0; x < a1; ++x)
+      for (int64_t y = b0; y < b1; ++y) push3(&stk, &nst, &cst, x, y, s);
+  }
+  free(stk);
+  if (stats) memcpy(stats, st, sizeof st);
+  return 0;
+}
+
+/* Order of each M2L entry of the current list (p for every entry after a geometric walk). */
+int orc_export_m2l_orders(const orc_ctx *c, int64_t *out) {
+  for (int64_t t = 0; t < c->nm2l; ++t) out[t] = c->m2l_ord ? c->m2l_ord[t] : c->p;
+  return 0;
 }

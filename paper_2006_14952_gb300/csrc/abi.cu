@@ -49,6 +49,8 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.tile_m2l_blocks < 0 || p.tile_m2l_blocks > 64) return why = "tile_m2l_blocks must be in 0..64", false;
   if (p.tile_trav_blocks < 0 || p.tile_trav_blocks > 4) return why = "tile_trav_blocks must be in 0..4", false;
   if (p.use_graph != 0 && p.use_graph != 1) return why = "use_graph must be 0 or 1", false;
+  if (p.list_init < 0) return why = "list_init must be >= 0", false;
+  if (p.tc_wait_polls < -1) return why = "tc_wait_polls must be >= -1", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
@@ -431,6 +433,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->p2p_particle_pairs = c.p2p_particle_pairs;
   o->nm2l_table = c.nm2l_table;
   o->frontier_pairs = c.frontier_items;
+  o->traverse_walks = c.traverse_walks;
   o->p2p_useful_pairs = -1;
   if ((c.prm.profile & 2) && c.n > 0) {
     unsigned long long u = 0;

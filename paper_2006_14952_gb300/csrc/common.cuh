@@ -237,6 +237,7 @@ struct Ctx {
   DBuf m2l, m2l_alt, p2p, p2p_alt;  // packed u64 entries
   int64_t nm2l = 0, np2p = 0;
   int traverse_iters = 0;
+  int64_t traverse_walks = 0;  // walks of the last traversal (1 + repeats after an overflow)
   uint64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;  // traversal capacities (entries)
   DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
   DBuf m2l_mid;  // u32 [nnodes]: [beg, mid) table pairs, [mid, end) per-pair operator

@@ -25,7 +25,8 @@
 // commits to an mbarrier.  After
 // the last chunk the four warps read their 32 TMEM lanes (rows c), stage P in
 // shared memory and thread n forms L~_n = sum_m P[n+m][m].  Waits are bounded;
-// on a timeout the kernel records an error and returns after freeing TMEM.
+// on a timeout the kernel records an error, waits (with the full limit) for the
+// MMAs it already issued, and returns after freeing TMEM.
 #include <type_traits>
 
 #include "common.cuh"
@@ -93,8 +94,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(int64_t nn, const uint4 *__restrict__ cell, const uint32_t *__restrict__ beg,
              const uint32_t *__restrict__ end, const uint64_t *__restrict__ lst, const float *__restrict__ M,
              float *__restrict__ L, int ldm, float inv_rs, unsigned long long *__restrict__ ctr,
-             int *__restrict__ status) {
+             int *__restrict__ status, uint32_t chunk_wait) {
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncp_of(P);
   constexpr uint32_t TCOLS = tmem_cols_of(P);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mma_commit(mb);
       }
-      const bool ok = mbar_wait(mb, phase);
+      const bool ok = mbar_wait(mb, phase, chunk_wait);
       phase ^= 1u;
       if (!ok) {
         if (lane == 0) {
@@ -309,7 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  if (abort_flag && tid == 0) mbar_wait(mb, phase ^ 1u);  // give an overdue commit one more bounded wait
+  // the MMAs of an abandoned chunk may still be running: wait for them with the
+  // full limit before the tensor memory they write is freed
+  if (abort_flag && tid == 0) mbar_wait(mb, phase ^ 1u, kWaitLimit);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
@@ -330,7 +333,8 @@ cudaError_t launch_tc(Ctx &c, cudaStream_t st) {
   const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
   k_m2l_tc<P, kBF><<<nsm > 0 ? nsm : 152, kThreads, smem, st>>>(
       c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_beg), hfmm::P<uint32_t>(c.m2l_end),
-      hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.ldm, inv_rs, ctr, status);
+      hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.ldm, inv_rs, ctr, status,
+      c.prm.tc_wait_polls > 0 ? (uint32_t)c.prm.tc_wait_polls : c.prm.tc_wait_polls < 0 ? 0u : kWaitLimit);
   note_launch();
   return cudaGetLastError();
 }

@@ -833,17 +833,27 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   // per particle at 48), so the guesses are scaled so, with a margin of 1.5.
   // A list that overflows is grown alone (to what the walk needed so far, at least
   // twice its size) and the walk is repeated.
+  // A positive list_init replaces every first guess (a test knob for the retry path).
   const double lf = c.prm.leaf_max > 16 ? std::pow(16.0 / c.prm.leaf_max, 1.5) * 1.5 : 1.0;
   const double sc = lf < 1.0 ? lf : 1.0;
-  if (c.cap_front < (uint64_t)(sc * 64 * c.n + 1024)) c.cap_front = (uint64_t)(sc * 64 * c.n + 1024);
-  if (c.cap_m2l < (uint64_t)(sc * 64 * c.n + 1024)) c.cap_m2l = (uint64_t)(sc * 64 * c.n + 1024);
-  if (c.cap_p2p < (uint64_t)(sc * 128 * c.n + 1024)) c.cap_p2p = (uint64_t)(sc * 128 * c.n + 1024);
-  if (c.cap_seg < (uint64_t)(2 * c.nnodes + 1024)) c.cap_seg = 2 * c.nnodes + 1024;
-  if (c.cap_run < (uint64_t)(4 * c.nnodes + 1024)) c.cap_run = 4 * c.nnodes + 1024;
+  const uint64_t init = (uint64_t)c.prm.list_init;
+  auto first_guess = [&](uint64_t guess) { return init > 0 ? init : guess; };
+  const uint64_t g_front = first_guess((uint64_t)(sc * 64 * c.n + 1024));
+  const uint64_t g_m2l = first_guess((uint64_t)(sc * 64 * c.n + 1024));
+  const uint64_t g_p2p = first_guess((uint64_t)(sc * 128 * c.n + 1024));
+  const uint64_t g_seg = first_guess((uint64_t)(2 * c.nnodes + 1024));
+  const uint64_t g_run = first_guess((uint64_t)(4 * c.nnodes + 1024));
+  if (c.cap_front < g_front) c.cap_front = g_front;
+  if (c.cap_m2l < g_m2l) c.cap_m2l = g_m2l;
+  if (c.cap_p2p < g_p2p) c.cap_p2p = g_p2p;
+  if (c.cap_seg < g_seg) c.cap_seg = g_seg;
+  if (c.cap_run < g_run) c.cap_run = g_run;
   // the state sits after the eight counters of the 256-byte d_small and is read back into h_pinned (256 bytes)
   static_assert(8 * sizeof(uint64_t) + sizeof(TravState) <= 256, "TravState must fit in d_small");
   TravState *dst = reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
-  for (int attempt = 0; attempt < 8; ++attempt) {
+  c.traverse_walks = 0;
+  for (int attempt = 0; attempt < 32; ++attempt) {
+    ++c.traverse_walks;
     TRY(ensure(c.front, c.cap_front * 8));
     TRY(ensure(c.front_next, c.cap_front * 8));
     TRY(ensure(c.fseg, c.nnodes * 4 + 64));

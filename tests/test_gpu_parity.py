@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from force_check import assert_forces_close
 from paper_2006_14952_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -106,6 +107,28 @@ def test_interaction_lists_bit_exact(rule, size_rule, theta, leaf):
     assert st["np2p"] == len(p2p) and st["nm2l"] == len(m2l)
 
 
+@pytest.mark.parametrize("init", [64, 20000])
+def test_lists_grow_and_repeat_the_walk_from_small_capacities(init):
+    """Every traversal list starts far too small (list_init): the walk overflows,
+    the overflowing lists grow and the walk repeats until it fits.  The lists
+    still equal the oracle's, and the forces are bit-identical to a run whose
+    first guesses fit."""
+    pos, mass = W.nfw_clustered(20000, 30, 0.7, 21)
+    kw = dict(pm_grid=32, theta=0.5, leaf_max=16, order=4)
+    s0, acc0 = run_gpu(pos, mass, **kw)
+    s, acc = run_gpu(pos, mass, list_init=init, **kw)
+    assert s0.get_stats()["traverse_walks"] == 1
+    walks = s.get_stats()["traverse_walks"]
+    print("walks", walks)
+    assert walks > 1
+    f = run_oracle(pos, mass, s)
+    f.traverse()
+    p2p, m2l = f.lists()
+    np.testing.assert_array_equal(sorted_rows(s.export("p2p")), sorted_rows(p2p))
+    np.testing.assert_array_equal(sorted_rows(s.export("m2l")), sorted_rows(m2l))
+    np.testing.assert_array_equal(acc, acc0)
+
+
 @pytest.mark.parametrize("case,order", [("uniform-50000", 4), ("nfw-50000", 2), ("nfw-50000", 4),
                                         ("nfw-50000", 6), ("nfw-50000", 8), ("zeldovich-32768", 5)])
 def test_forces_match_fp64_fmm_on_identical_lists(case, order):
@@ -114,8 +137,7 @@ def test_forces_match_fp64_fmm_on_identical_lists(case, order):
     f = run_oracle(pos, mass, s)
     ref = f.forces()
     assert f.size("m2l") > 0
-    err = rel_rms(acc, ref)
-    assert err < FORCE_TOL, err
+    print("relative RMS %.3e, per particle %.3e" % assert_forces_close(acc, ref))
 
 
 @pytest.mark.parametrize("leaf,order,theta", [(48, 6, 0.35), (64, 4, 0.3), (32, 5, 0.4)])
@@ -127,8 +149,7 @@ def test_forces_on_identical_lists_with_large_leaves(leaf, order, theta):
     f = run_oracle(pos, mass, s)
     ref = f.forces()
     assert f.size("p2p") > 0 and f.size("m2l") > 0
-    err = rel_rms(acc, ref)
-    assert err < FORCE_TOL, err
+    print("relative RMS %.3e, per particle %.3e" % assert_forces_close(acc, ref))
 
 
 def test_full_size_clustered_set_in_the_bench_configuration():
@@ -177,7 +198,7 @@ def test_theta_zero_equals_direct_sum_at_full_uniform_size():
     s, acc = run_gpu(pos, mass, pm_grid=32, theta=0.0)
     assert s.get_stats()["nm2l"] == 0
     ref = oracle.direct_sr(pos, mass, 1.0, s.rs, s.rc)
-    assert rel_rms(acc, ref) < FORCE_TOL
+    assert_forces_close(acc, ref)
 
 
 def test_edge_cases_empty_single_coincident():
@@ -198,7 +219,7 @@ def test_edge_cases_empty_single_coincident():
     nodes = s2.export("nodes")
     assert nodes[:, 0].max() == 21
     ref = oracle.direct_sr(pos, mass, 1.0, s2.rs, s2.rc)
-    assert rel_rms(acc, ref) < FORCE_TOL
+    assert_forces_close(acc, ref)
 
 
 def test_state_and_argument_errors():
