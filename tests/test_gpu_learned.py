@@ -1,10 +1,13 @@
 """Learned acceptance on the GPU against the FP64 oracle.
 
-Network: tensor-core inference vs the oracle forward (BF16 inputs and
-activations), gradients vs the oracle backward, one Adam step vs its formula.
+Network: tensor-core inference vs the oracle forward at the same rounding
+points, element by element within the bound the oracle derives for any FP32
+evaluation; gradients vs the oracle backward per element; one Adam step vs its
+formula.  Pair features: GPU vs oracle element by element (FP32 rounding).
 Training data: the measured per-pair M2L errors vs the oracle's pair error.
-Traversal: lists built with the network cover every close particle pair
-exactly once, and forces on those lists match the oracle FMM on the same lists.
+Traversal: the learned lists equal the oracle's learned walk (bit-exact, with
+the orders), cover every close particle pair exactly once, and forces on those
+lists match the oracle FMM on the same lists.
 """
 import itertools
 import math
@@ -63,9 +66,12 @@ def features(n, seed):
 # exact integer distances through at most ~6 FP32 roundings (squares, sums,
 # sqrt, reciprocal, scale), within 2^-20 relative; 6 is exact; 7-8 use the
 # hardware log2, within 2^-22 absolute before the 1/16 scale; 9-10 divide
-# FP32 multipole moments (P2M and M2M sums in FP32) by the FP32 monopole.
-FEAT_TOL_REL = np.array([2.0 ** -20] * 6 + [0.0, 2.0 ** -20, 2.0 ** -20, 2.0 ** -14, 2.0 ** -14, 2.0 ** -20])
-FEAT_TOL_ABS = np.array([2.0 ** -24] * 6 + [0.0, 2.0 ** -24, 2.0 ** -24, 2.0 ** -17, 2.0 ** -17, 2.0 ** -24])
+# FP32 multipole moments (P2M and M2M sums in FP32, relative error a few
+# 2^-24 times the log of the terms summed) by the FP32 monopole: 2^-18
+# relative and 2^-21 absolute.  (Measured on the clustered set below: at most
+# 0.1 of these bounds for every feature.)
+FEAT_TOL_REL = np.array([2.0 ** -20] * 6 + [0.0, 2.0 ** -20, 2.0 ** -20, 2.0 ** -18, 2.0 ** -18, 2.0 ** -20])
+FEAT_TOL_ABS = np.array([2.0 ** -24] * 6 + [0.0, 2.0 ** -24, 2.0 ** -24, 2.0 ** -21, 2.0 ** -21, 2.0 ** -24])
 
 
 def test_network_inference_within_the_fp32_bound_of_the_oracle():
@@ -132,7 +138,11 @@ def test_network_gradient_and_adam_step():
     print(f"gradient: norm ratio {np.linalg.norm(gg - ref_g) / np.linalg.norm(ref_g):.3e}, "
           f"max |dg| / rms(g) {dev.max() / scale:.3e}, "
           f"max |dg| / (|g| + 1e-2 rms(g)) {(dev / (np.abs(ref_g) + 1e-2 * scale)).max():.3e}")
-    assert np.linalg.norm(gg - ref_g) < 1e-2 * np.linalg.norm(ref_g)
+    # per element: FP32 sums over 2000 samples of products whose BF16-rounded
+    # activations can differ by one BF16 step from the FP64 ones (about 1e-5 of
+    # the gradient's size measured); bound 1e-4 of |g| + 1e-2 rms(g)
+    assert np.linalg.norm(gg - ref_g) < 1e-5 * np.linalg.norm(ref_g)
+    assert np.all(dev <= 1e-4 * (np.abs(ref_g) + 1e-2 * scale))
     # one Adam step against its formula
     m1 = torch.zeros_like(wt)
     m2 = torch.zeros_like(wt)

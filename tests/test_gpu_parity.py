@@ -219,7 +219,10 @@ def test_edge_cases_empty_single_coincident():
     nodes = s2.export("nodes")
     assert nodes[:, 0].max() == 21
     ref = oracle.direct_sr(pos, mass, 1.0, s2.rs, s2.rc)
-    assert_forces_close(acc, ref)
+    # the pulls of the two neighbours cancel on the coincident particles: the
+    # floor is the size of one pull
+    one = oracle.direct_sr(pos[:, [0, 40]], mass[[0, 40]], 1.0, s2.rs, s2.rc)
+    assert_forces_close(acc, ref, scale=float(np.linalg.norm(one[:, 0])))
 
 
 def test_state_and_argument_errors():
