@@ -97,6 +97,10 @@ def lib():
             L.orc_find_node.argtypes = [P, i32, C.c_uint32, C.c_uint32, C.c_uint32]
             L.orc_find_node.restype = i64
             L.orc_pair_features.argtypes = [P, i64, i64, i32, P]
+            L.orc_prefactors_poly.argtypes = [d, d, i32, P]
+            L.orc_deriv_tensor_split.argtypes = [P, d, d, i32, i32, P]
+            L.orc_direct_sr_split.argtypes = [i64, P, P, d, d, d, i32, d, i64, P, P]
+            L.orc_set_split.argtypes = [P, i32]
             L.orc_mlp_forward_bound.argtypes = [P, P, P, i64, P, P, P, P]
             L.orc_traverse_learned.argtypes = [P, P, P, P, P, i64, P]
             L.orc_export_m2l_orders.argtypes = [P, P]
@@ -138,10 +142,24 @@ def prefactors(r: float, rs: float, p: int) -> np.ndarray:
     return f
 
 
-def deriv_tensor(R, rs: float, p: int) -> np.ndarray:
+def prefactors_poly(r: float, rc: float, p: int) -> np.ndarray:
+    """f_(0..p)(r) of the polynomial truncation (Sec. 5 reading): 1/r - P(r) inside R_c."""
+    f = np.zeros(p + 1)
+    _check(lib().orc_prefactors_poly(float(r), float(rc), int(p), _p(f)), "prefactors_poly")
+    return f
+
+
+SPLITS = {"gauss": 0, "poly": 1}
+
+
+def deriv_tensor(R, rs: float, p: int, split="gauss", rc=0.0) -> np.ndarray:
     R = np.ascontiguousarray(R, dtype=np.float64)
     D = np.zeros(ncoef(p))
-    _check(lib().orc_deriv_tensor(_p(R), float(rs), int(p), _p(D)), "deriv_tensor")
+    if split == "gauss":
+        _check(lib().orc_deriv_tensor(_p(R), float(rs), int(p), _p(D)), "deriv_tensor")
+    else:
+        _check(lib().orc_deriv_tensor_split(_p(R), float(rs), float(rc), SPLITS[split], int(p), _p(D)),
+               "deriv_tensor_split")
     return D
 
 
@@ -188,8 +206,9 @@ def l2p(L, u, p, G=1.0):
 
 
 # ---------------------------------------------------------------- direct sum
-def direct_sr(pos, mass, box, rs, rc, G=1.0, sinks=None) -> np.ndarray:
-    """Minimum-image direct truncated sum; pos [3][n] -> acc [3][nsink] (FP64)."""
+def direct_sr(pos, mass, box, rs, rc, G=1.0, sinks=None, split="gauss") -> np.ndarray:
+    """Minimum-image direct truncated sum; pos [3][n] -> acc [3][nsink] (FP64).
+    split: "gauss" (Sec. 2.2) or "poly" (the polynomial truncation of Sec. 5)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     mass = np.ascontiguousarray(mass, dtype=np.float64)
     n = pos.shape[1]
@@ -199,7 +218,8 @@ def direct_sr(pos, mass, box, rs, rc, G=1.0, sinks=None) -> np.ndarray:
         sinks = np.ascontiguousarray(sinks, dtype=np.int64)
         ns, sp = len(sinks), sinks
     acc = np.zeros((3, ns))
-    _check(lib().orc_direct_sr(n, _p(pos), _p(mass), box, rs, rc, G, ns, _p(sp), _p(acc)), "direct_sr")
+    _check(lib().orc_direct_sr_split(n, _p(pos), _p(mass), box, rs, rc, SPLITS[split], G, ns, _p(sp), _p(acc)),
+           "direct_sr")
     return acc
 
 
@@ -258,10 +278,12 @@ class FMM:
     """FP64 truncated FMM with the same tree, MAC and lists as the GPU library."""
 
     def __init__(self, box=1.0, rs=None, rc=None, G=1.0, theta=0.5, order=4, leaf_max=16,
-                 transition_rule=1, size_rule=1):
+                 transition_rule=1, size_rule=1, split="gauss"):
         self._c = lib().orc_create(box, rs, rc, G, theta, order, leaf_max, transition_rule, size_rule)
         if not self._c:
             raise ValueError("invalid oracle parameters")
+        _check(lib().orc_set_split(self._c, SPLITS[split]), "set_split")
+        self.split = split
         self.box, self.rs, self.rc, self.G, self.theta = box, rs, rc, G, theta
         self.order, self.leaf_max, self.rule, self.size_rule = order, leaf_max, transition_rule, size_rule
         self.n = 0

@@ -123,15 +123,48 @@ int orc_prefactors(double r, double rs, int p, double *f) {
 }
 
 /*
- * D_n(R) = d^n psi(R) for all |n| <= p (graded order), psi = erfc(r/2rs)/r
- * (Newtonian 1/r if rs <= 0).  Derivative of a radial function:
+ * The polynomial truncation of the split that Sec. 5 allows in place of the
+ * Gaussian one (the paper names no polynomial; the reading taken is the even
+ * quartic for which the kernel and its first two derivatives vanish at R_c):
+ *   psi(r) = 1/r - P(r) for 0 < r < R_c,  P(r) = (15 - 10 w^2 + 3 w^4) / (8 R_c),  w = r / R_c.
+ * Its prefactors f_(k) = ((1/r) d/dr)^k psi are the Newtonian ones minus those
+ * of P, which vanish beyond k = 2:
+ *   P_(0) = P,  P_(1) = (-5/2 + 3 w^2 / 2) / R_c^3,  P_(2) = 3 / R_c^5.
+ */
+int orc_prefactors_poly(double r, double rc, int p, double *f) {
+  if (p < 0 || p > 2 * ORC_PMAX || !(r > 0.0) || !(rc > 0.0)) return -1;
+  for (int k = 0; k <= p; ++k) {
+    double v = dfact(2 * k - 1) / ipow(r, 2 * k + 1);
+    f[k] = (k & 1) ? -v : v;
+  }
+  const double w2 = (r / rc) * (r / rc);
+  f[0] -= (15.0 - 10.0 * w2 + 3.0 * w2 * w2) / (8.0 * rc);
+  if (p >= 1) f[1] -= (-2.5 + 1.5 * w2) / ipow(rc, 3);
+  if (p >= 2) f[2] -= 3.0 / ipow(rc, 5);
+  return 0;
+}
+
+/* The short-range kernel in use: split 0 = erfc(r / 2 r_s) / r (Sec. 2.2; the
+ * Newtonian 1/r when rs <= 0), split 1 = the polynomial truncation above. */
+typedef struct {
+  double rs, rc;
+  int split;
+} orc_kernel;
+
+static int prefactors_k(double r, const orc_kernel *K, int p, double *f) {
+  return K->split == 1 ? orc_prefactors_poly(r, K->rc, p, f) : orc_prefactors(r, K->rs, p, f);
+}
+
+/*
+ * D_n(R) = d^n psi(R) for all |n| <= p (graded order), psi the kernel K.
+ * Derivative of a radial function:
  *   d^n psi = sum_{k_d <= n_d/2} prod_d [ n_d! / (2^k_d k_d! (n_d-2k_d)!) R_d^(n_d-2k_d) ] f_(|n|-|k|)(r).
  */
-int orc_deriv_tensor(const double *R, double rs, int p, double *D) {
+static int deriv_tensor_k(const double *R, const orc_kernel *K, int p, double *D) {
   if (p < 0 || p > ORC_PMAX) return -1;
   double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
   double f[2 * ORC_PMAX + 1];
-  if (orc_prefactors(r, rs, p, f)) return -1;
+  if (prefactors_k(r, K, p, f)) return -1;
   int nc = orc_ncoef(p);
   for (int c = 0; c < nc; ++c) {
     const int *n = g_mi[c];
@@ -150,6 +183,18 @@ int orc_deriv_tensor(const double *R, double rs, int p, double *D) {
     D[c] = sum;
   }
   return 0;
+}
+
+/* D_n of psi = erfc(r/2rs)/r (Newtonian 1/r if rs <= 0). */
+int orc_deriv_tensor(const double *R, double rs, int p, double *D) {
+  const orc_kernel K = {rs, 0.0, 0};
+  return deriv_tensor_k(R, &K, p, D);
+}
+
+/* D_n of the kernel of the given split (0 Gaussian with rs, 1 polynomial with rc). */
+int orc_deriv_tensor_split(const double *R, double rs, double rc, int split, int p, double *D) {
+  const orc_kernel K = {rs, rc, split};
+  return deriv_tensor_k(R, &K, p, D);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -189,9 +234,9 @@ int orc_m2m(const double *Min, const double *x, int p, double *Mout) {
 }
 
 /* Eq. m2l: L_n += sum_{|m| <= p-|n|} M_m D_{n+m}(R), R = z_sink - z_source. */
-int orc_m2l(const double *M, const double *R, double rs, int p, double *L) {
+static int m2l_k(const double *M, const double *R, const orc_kernel *K, int p, double *L) {
   double D[ORC_NCMAX];
-  if (orc_deriv_tensor(R, rs, p, D)) return -1;
+  if (deriv_tensor_k(R, K, p, D)) return -1;
   int nc = orc_ncoef(p);
   for (int c = 0; c < nc; ++c) {
     const int *n = g_mi[c];
@@ -204,6 +249,11 @@ int orc_m2l(const double *M, const double *R, double rs, int p, double *L) {
     L[c] += s;
   }
   return 0;
+}
+
+int orc_m2l(const double *M, const double *R, double rs, int p, double *L) {
+  const orc_kernel K = {rs, 0.0, 0};
+  return m2l_k(M, R, &K, p, L);
 }
 
 /* Eq. l2l: L_n(z + x) = sum_{|m| <= p-|n|} x^m / m! L_{m+n}(z).  Lout is overwritten. */
@@ -255,11 +305,11 @@ static double wrap1(double x, double box) {
 }
 
 /* Pair force of Sec. 2.2: G m_j f_(1)(r) r, r = x_i - x_j, kept iff 0 < |r| < rc. */
-static void pair_acc(const double *d, double mj, double rs, double rc2, double *acc) {
+static void pair_acc(const double *d, double mj, const orc_kernel *K, double rc2, double *acc) {
   double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   if (!(r2 > 0.0) || !(r2 < rc2)) return;
   double f[2];
-  orc_prefactors(sqrt(r2), rs, 1, f);
+  prefactors_k(sqrt(r2), K, 1, f);
   for (int k = 0; k < 3; ++k) acc[k] += mj * f[1] * d[k];
 }
 
@@ -271,9 +321,10 @@ static void pair_acc(const double *d, double mj, double rs, double rc2, double *
  * for the sinks listed (all particles when sinks == NULL).  A cell list with
  * cells of side >= rc restricts the candidates; it changes no result.
  */
-int orc_direct_sr(int64_t n, const double *pos, const double *mass, double box, double rs, double rc,
-                  double G, int64_t nsink, const int64_t *sinks, double *acc) {
-  if (n < 0 || nsink < 0 || !(rc > 0.0) || !(rc < 0.5 * box)) return -1;
+int orc_direct_sr_split(int64_t n, const double *pos, const double *mass, double box, double rs, double rc,
+                        int split, double G, int64_t nsink, const int64_t *sinks, double *acc) {
+  if (n < 0 || nsink < 0 || !(rc > 0.0) || !(rc < 0.5 * box) || split < 0 || split > 1) return -1;
+  const orc_kernel K = {rs, rc, split};
   if (n == 0 || nsink == 0) return 0;
   double *w = (double *)malloc(sizeof(double) * 3 * n);
   int nc = (int)floor(box / rc);
@@ -334,12 +385,17 @@ int orc_direct_sr(int64_t n, const double *pos, const double *mass, double box, 
           double dd = w[3 * i + k] - w[3 * j + k];
           d[k] = dd - box * nearbyint(dd / box);
         }
-        pair_acc(d, mass[j], rs, rc2, a);
+        pair_acc(d, mass[j], &K, rc2, a);
       }
     for (int k = 0; k < 3; ++k) acc[k * nsink + s] = G * a[k];
   }
   free(w); free(head); free(item); free(cell);
   return 0;
+}
+
+int orc_direct_sr(int64_t n, const double *pos, const double *mass, double box, double rs, double rc,
+                  double G, int64_t nsink, const int64_t *sinks, double *acc) {
+  return orc_direct_sr_split(n, pos, mass, box, rs, rc, 0, G, nsink, sinks, acc);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -381,6 +437,7 @@ typedef struct {
   /* parameters */
   double box, rs, rc, G, theta;
   int p, leaf_max, rule, size_rule;
+  int split; /* short-range kernel: 0 Gaussian (Sec. 2.2), 1 polynomial (Sec. 5) */
   /* particles, sorted by (key, input index) */
   int64_t n;
   double *x;      /* [n][3] wrapped positions */
@@ -432,6 +489,13 @@ orc_ctx *orc_create(double box, double rs, double rc, double G, double theta, in
   c->rc2h = t * t;
   c->theta2 = theta * theta;
   return c;
+}
+
+/* Short-range kernel of the FMM and its direct sums: 0 Gaussian, 1 polynomial (Sec. 5). */
+int orc_set_split(orc_ctx *c, int split) {
+  if (!c || split < 0 || split > 1) return -1;
+  c->split = split;
+  return 0;
 }
 
 static void push_node(orc_ctx *c, int lev, uint32_t ix, uint32_t iy, uint32_t iz, int64_t first, int64_t count) {
@@ -700,7 +764,8 @@ int orc_m2l_pass(orc_ctx *c) {
       node_centre(c, b, zb);
       shift_vec(s, c->box, sv);
       for (int d = 0; d < 3; ++d) R[d] = za[d] - (zb[d] + sv[d]);
-      orc_m2l(c->M + b * nc, R, c->rs, c->p, c->L + a * nc);
+      const orc_kernel K = {c->rs, c->rc, c->split};
+      m2l_k(c->M + b * nc, R, &K, c->p, c->L + a * nc);
     }
   }
   free(off);
@@ -740,6 +805,7 @@ int orc_downward(orc_ctx *c, double *acc_sorted) {
 /* P2P over the leaf-pair list with the hard cutoff 0 < |r| < R_c; adds into acc_sorted [n][3]. */
 int orc_p2p_pass(orc_ctx *c, double *acc_sorted) {
   if (!c) return -1;
+  const orc_kernel K = {c->rs, c->rc, c->split};
   int64_t *off = sink_offsets(c->p2p, c->np2p, c->nnodes);
   double rc2 = c->rc * c->rc;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -754,7 +820,7 @@ int orc_p2p_pass(orc_ctx *c, double *acc_sorted) {
         for (int64_t j = c->first[b]; j < c->first[b] + c->count[b]; ++j) {
           double d[3];
           for (int k = 0; k < 3; ++k) d[k] = c->x[3 * i + k] - (c->x[3 * j + k] + sv[k]);
-          pair_acc(d, c->m[j], c->rs, rc2, acc);
+          pair_acc(d, c->m[j], &K, rc2, acc);
         }
         for (int k = 0; k < 3; ++k) acc_sorted[3 * i + k] += c->G * acc[k];
       }
@@ -1015,7 +1081,8 @@ int orc_fmm_forces_given_lists(orc_ctx *c, double *acc) {
         shift_vec(s, c->box, sv);
         for (int d = 0; d < 3; ++d) R[d] = za[d] - (zb[d] + sv[d]);
         for (int e = 0; e < orc_ncoef(q); ++e) Lq[e] = 0.0;
-        orc_m2l(c->M + b * nc, R, c->rs, q, Lq);
+        const orc_kernel K = {c->rs, c->rc, c->split};
+        m2l_k(c->M + b * nc, R, &K, q, Lq);
         for (int e = 0; e < orc_ncoef(q); ++e) c->L[a * nc + e] += Lq[e];
       }
     }
@@ -1052,7 +1119,8 @@ double orc_pair_error(orc_ctx *c, int64_t a, int64_t b, int s, int q) {
     for (int d = 0; d < 3; ++d) xb[3 * j + d] = c->x[3 * (c->first[b] + j) + d];
   orc_p2m(nb, xb, c->m + c->first[b], zb, q, M);
   for (int e = 0; e < orc_ncoef(q); ++e) L[e] = 0.0;
-  orc_m2l(M, R, c->rs, q, L);
+  const orc_kernel K = {c->rs, c->rc, c->split};
+  m2l_k(M, R, &K, q, L);
   int64_t na = c->count[a];
   int ns = na < 32 ? (int)na : 32;
   double num = 0.0, den = 0.0;
@@ -1065,7 +1133,7 @@ double orc_pair_error(orc_ctx *c, int64_t a, int64_t b, int s, int q) {
       double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       if (!(r2 > 0)) continue;
       double f[2];
-      orc_prefactors(sqrt(r2), c->rs, 1, f);
+      prefactors_k(sqrt(r2), &K, 1, f);
       for (int dd = 0; dd < 3; ++dd) ex[dd] += c->G * c->m[c->first[b] + j] * f[1] * d[dd];
     }
     for (int dd = 0; dd < 3; ++dd) u[dd] = c->x[3 * i + dd] - za[dd];

@@ -79,8 +79,10 @@ def wavenumbers(ng, box):
     return kfull, khalf
 
 
-def long_range_mesh(rho, box, rs, G=1.0):
-    """Long-range acceleration on the mesh points, [3][ng][ng][ng], from the mass mesh."""
+def long_range_mesh(rho, box, rs, G=1.0, green_k2=None):
+    """Long-range acceleration on the mesh points, [3][ng][ng][ng], from the mass mesh.
+    green_k2 (optional): the long-range Green function of another split as a
+    function of k^2 > 0 (default: the Gaussian 4 pi exp(-k^2 r_s^2) / k^2)."""
     ng = rho.shape[0]
     mk = np.fft.rfftn(rho)
     kf, kh = wavenumbers(ng, box)
@@ -95,7 +97,11 @@ def long_range_mesh(rho, box, rs, G=1.0):
 
     w = (sinc(kx * h / 2) * sinc(ky * h / 2) * sinc(kz * h / 2)) ** 2
     with np.errstate(divide="ignore", invalid="ignore"):
-        green = np.where(k2 > 0, 4.0 * np.pi * G * np.exp(-k2 * rs ** 2) / k2 / w ** 2, 0.0)
+        if green_k2 is None:
+            green = np.where(k2 > 0, 4.0 * np.pi * G * np.exp(-k2 * rs ** 2) / k2 / w ** 2, 0.0)
+        else:
+            kk = np.where(k2 > 0, k2, 1.0)
+            green = np.where(k2 > 0, G * np.asarray(green_k2(kk.ravel())).reshape(k2.shape) / w ** 2, 0.0)
     phi = green * mk / box ** 3
     nyq = ng // 2 if ng % 2 == 0 else -1
     out = np.zeros((3, ng, ng, ng))
@@ -113,10 +119,10 @@ def long_range_mesh(rho, box, rs, G=1.0):
     return out
 
 
-def pm_long_range(pos, mass, box, ng, rs, G=1.0):
-    """Long-range accelerations [3][n] of the particles (FP64)."""
+def pm_long_range(pos, mass, box, ng, rs, G=1.0, green_k2=None):
+    """Long-range accelerations [3][n] of the particles (FP64); green_k2 as in long_range_mesh."""
     rho = cic_deposit(pos, mass, box, ng)
-    a = long_range_mesh(rho, box, rs, G)
+    a = long_range_mesh(rho, box, rs, G, green_k2)
     return np.stack([cic_interpolate(a[d], pos, box) for d in range(3)])
 
 

@@ -103,3 +103,78 @@ def test_direct_sum_is_antisymmetric_and_truncated():
     assert a2[0, 0] == pytest.approx(2.0 * PS.pair_factor(0.9 * RC, RC) * d, rel=1e-14)
     far = np.array([[0.1, 0.1 + 1.01 * RC], [0.5, 0.5], [0.5, 0.5]])
     assert (PS.direct_sr(far, np.ones(2), 1.0, RC) == 0).all()
+
+
+# ---------------------------------------------------------------- the C oracle's split mode
+import oracle  # noqa: E402
+from oracle import pm as PM  # noqa: E402
+
+
+@pytest.mark.parametrize("x", [0.05, 0.3, 0.62, 0.97])
+def test_c_prefactors_are_the_symbolic_radial_derivatives(x):
+    r, R, psi = _symbolic_kernel()
+    expr = psi
+    got = oracle.prefactors_poly(x * RC, RC, 8)
+    for k in range(9):
+        want = float(expr.subs({r: x * RC, R: RC}))
+        assert got[k] == pytest.approx(want, rel=1e-11), k
+        expr = sp.diff(expr, r) / r
+
+
+def test_c_derivative_tensor_is_the_symbolic_cartesian_derivative():
+    X, Y, Z = sp.symbols("X Y Z", real=True)
+    s2 = X ** 2 + Y ** 2 + Z ** 2
+    psi = 1 / sp.sqrt(s2) - (15 - 10 * s2 / RC ** 2 + 3 * s2 ** 2 / RC ** 4) / (8 * RC)
+    Rv = np.array([0.031, -0.047, 0.069])  # |R| < R_c
+    p = 5
+    D = oracle.deriv_tensor(Rv, 0.0, p, split="poly", rc=RC)
+    mi = oracle.multi_indices(p)
+    sub = {X: Rv[0], Y: Rv[1], Z: Rv[2]}
+    for c, (a, b, g) in enumerate(mi):
+        e = psi
+        if a:
+            e = sp.diff(e, X, int(a))
+        if b:
+            e = sp.diff(e, Y, int(b))
+        if g:
+            e = sp.diff(e, Z, int(g))
+        want = float(e.subs(sub))
+        assert D[c] == pytest.approx(want, rel=1e-9, abs=1e-9 * abs(D).max()), (a, b, g)
+
+
+def test_c_direct_sum_matches_the_numpy_pair_sum():
+    rng = np.random.default_rng(6)
+    pos = rng.random((3, 400))
+    mass = rng.random(400) / 400
+    ref = PS.direct_sr(pos, mass, 1.0, RC)
+    got = oracle.direct_sr(pos, mass, 1.0, 0.0, RC, split="poly")
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_fmm_with_the_polynomial_split_converges_to_its_direct_sum():
+    from paper_2006_14952_gb300 import workloads as W
+
+    pos, mass = W.nfw_clustered(6000, 10, 0.7, 8)
+    rc = 0.12
+    direct = PS.direct_sr(pos, mass, 1.0, rc)
+    f0 = oracle.FMM(box=1.0, rs=rc / 4.5, rc=rc, theta=0.0, order=2, leaf_max=16, split="poly")
+    f0.build_tree(pos, mass)
+    np.testing.assert_allclose(f0.forces(), direct, rtol=1e-12, atol=1e-12 * np.abs(direct).max())
+    errs = []
+    for p in (2, 4, 6):
+        f = oracle.FMM(box=1.0, rs=rc / 4.5, rc=rc, theta=0.5, order=p, leaf_max=16, split="poly")
+        f.build_tree(pos, mass)
+        a = f.forces()
+        assert f.size("m2l") > 0
+        errs.append(np.linalg.norm(a - direct) / np.linalg.norm(direct))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.1 * errs[0], errs
+
+
+def test_mesh_with_a_given_green_function_reproduces_the_gaussian_mesh():
+    rng = np.random.default_rng(7)
+    pos = rng.random((3, 500))
+    mass = rng.random(500)
+    rs = 1.25 / 16
+    a0 = PM.pm_long_range(pos, mass, 1.0, 16, rs)
+    a1 = PM.pm_long_range(pos, mass, 1.0, 16, rs, green_k2=lambda k2: 4 * np.pi * np.exp(-k2 * rs ** 2) / k2)
+    np.testing.assert_allclose(a1, a0, rtol=1e-12, atol=1e-12 * np.abs(a0).max())
