@@ -9,6 +9,12 @@ L2L, L2P + P2P, accelerations in input order.  L2 is flushed (a 512 MB write)
 before every timed step.  `value` counts particles with forces per second of
 device time (CUDA events on the launching stream); `e2e` repeats the step
 through the host-buffer C entry point with the copies inside the timing.
+`arms` times the metric's other arm on the same set in the same run (learned
+acceptance with the committed network and 3xTF32 tensor-core M2L) and checks
+both against the same FP64 accuracy sinks.  The roofline's FP32 peak is
+measured in the same process by the library's FMA probe.  `--split poly` runs
+the polynomial truncation of Sec. 5 instead (accuracy against its own direct
+sum).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -40,6 +46,10 @@ N_SM = 152
 # truncation factor S = exp2(r^2 k) Q(u) with Q of degree 9 (exponent 1 +
 # exp2 1 + 9 fma 18 + product 1 = 21), -S m / r^3 (4), accumulation (3 fma = 6).
 P2P_FLOPS_PER_PAIR = 42
+# The same count for the polynomial split (Sec. 5): separation 3, r^2 5,
+# rsqrt 1, r^-3 2, -(r^-3 + c0 + c1 r^2) m (1 fma + 1 add + 1 mul = 4),
+# accumulation 6.
+P2P_FLOPS_PER_PAIR_POLY = 21
 
 
 def parse():
@@ -60,6 +70,11 @@ def parse():
     ap.add_argument("--m2l-tables", type=int, default=0, help="1: same-level M2L operators from the (level, offset) table")
     ap.add_argument("--mac", default="geometric", choices=["geometric", "learned"])
     ap.add_argument("--mlp-weights", default=os.path.join(ROOT, "paper_2006_14952_gb300", "weights", "mac_weights.bin"))
+    ap.add_argument("--split", default="gauss", choices=["gauss", "poly"],
+                    help="truncation of the force split: Gaussian (Sec. 2.2) or polynomial (Sec. 5)")
+    ap.add_argument("--compare", type=int, default=1,
+                    help="1: also time the metric's other arm (learned acceptance + 3xTF32 M2L) on the same set")
+    ap.add_argument("--compare-theta", type=float, default=0.5, help="safety bound of the learned arm")
     ap.add_argument("--accuracy-sinks", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=25.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -162,7 +177,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7):
+def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7, split="gauss"):
     """Direct FP64 truncated sum (the oracle) on a bounded random sink sample."""
     import oracle
 
@@ -170,12 +185,12 @@ def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7):
     n = pos.shape[1]
     probe = np.sort(np.random.default_rng(seed).choice(n, size=min(500, n), replace=False))
     t0 = time.perf_counter()
-    oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=probe)
+    oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=probe, split=split)
     dt = max(time.perf_counter() - t0, 1e-3)
     k = int(min(n, max(500, 500 * target_s / dt)))
     sinks = np.sort(np.random.default_rng(seed + 1).choice(n, size=k, replace=False))
     t0 = time.perf_counter()
-    oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks)
+    oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks, split=split)
     dt = time.perf_counter() - t0
     return {"value": k / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 direct truncated sum (oracle) for {k} random sinks against all {n} sources, "
@@ -231,6 +246,60 @@ def measured_traffic(kernel, src):
     return None
 
 
+def accuracy_of(acc, sinks, ref, split="gauss"):
+    """Per-particle relative force error against the FP64 direct sum on the sinks."""
+    a = acc.cpu().numpy()[:, sinks].astype(np.float64)
+    e = np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    what = "FP64 direct truncated sum" + (" (polynomial split)" if split == "poly" else "")
+    return {"rms_rel": float(math.sqrt((e ** 2).mean())), "p99_rel": float(np.percentile(e, 99)),
+            "max_rel": float(e.max()), "sinks": int(len(sinks)), "against": what}
+
+
+def measured_fp32_peak():
+    """FP32 fused multiply-add rate of this GPU (TFLOP/s), the larger of the
+    scalar and packed FP32x2 probes (hfmm_alu_peak), with the clock it ran at."""
+    from paper_2006_14952_gb300 import hfmm
+
+    out = {}
+    for kind in ("ffma", "ffma2", "ex2", "rsqrt"):
+        best = 0.0
+        for _ in range(3):
+            r, _ms = hfmm.alu_peak(kind, 8192 if kind.startswith("ffma") else 2048)
+            best = max(best, r)
+        out[kind] = best / 1e12
+    return out
+
+
+def time_arm(hfmm, torch, common, wts, dpos, dmass, acc, flush, steps, warmup, stream):
+    """Warm up, then time `steps` steps (tree build + short-range forces) with CUDA
+    events; returns (step times in ms, per-step phase stats, launches in the timed steps)."""
+    s = hfmm.Solver(profile=1, **common)
+    if wts is not None:
+        s.load_mlp(wts)
+
+    def step():
+        s.build_tree(dpos, dmass)
+        s.short_range_forces(acc)
+
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    l0 = s.get_stats()["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    phases = []
+    for k in range(steps):
+        flush.fill_(1.0)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        phases.append(s.get_stats())
+    torch.cuda.synchronize()
+    l1 = s.get_stats()["launches"]
+    s.close()
+    return [a.elapsed_time(b) for a, b in ev], phases, l1 - l0
+
+
 def main():
     args = parse()
     from paper_2006_14952_gb300 import workloads as W
@@ -279,7 +348,8 @@ def main():
         tiles = autotune.lookup(args.tuned, key) or {}
     common = dict(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
                   order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision,
-                  m2l_tables=args.m2l_tables, use_graph=args.graph, **tiles, **mac_kw)
+                  m2l_tables=args.m2l_tables, use_graph=args.graph, split=1 if args.split == "poly" else 0,
+                  **tiles, **mac_kw)
     wts = np.fromfile(args.mlp_weights, dtype=np.uint16) if learned else None
     s = hfmm.Solver(profile=1, **common)
     if learned:
@@ -309,16 +379,14 @@ def main():
 
     # accuracy of this configuration against the FP64 direct sum (rank 0, untimed)
     accuracy = None
+    sinks = ref = None
     if rank == 0 and args.accuracy_sinks > 0:
         import oracle
 
         oracle.build()
         sinks = W.subsample(n, args.accuracy_sinks, 2024)
-        ref = oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks)
-        a = acc.cpu().numpy()[:, sinks].astype(np.float64)
-        e = np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
-        accuracy = {"rms_rel": float(math.sqrt((e ** 2).mean())), "p99_rel": float(np.percentile(e, 99)),
-                    "max_rel": float(e.max()), "sinks": int(len(sinks)), "against": "FP64 direct truncated sum"}
+        ref = oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks, split=args.split)
+        accuracy = accuracy_of(acc, sinks, ref, args.split)
 
     # timed region
     if ws > 1:
@@ -366,18 +434,25 @@ def main():
     keys = ["t_keys_sort", "t_tree", "t_upward", "t_traverse", "t_lists", "t_m2l", "t_l2l", "t_p2p"]
     mean = {k: statistics.mean(p[k] for p in phases) for k in keys}
     st = counts
-    peak_fp32 = N_SM * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    derived_fp32 = N_SM * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    alu = measured_fp32_peak()
+    peak_fp32 = max(alu["ffma"], alu["ffma2"])
+    peak_src = (f"measured: FP32 FMA probe (hfmm_alu_peak), max of scalar {alu['ffma']:.1f} and packed FP32x2 "
+                f"{alu['ffma2']:.1f} TFLOP/s (derived at 2070 MHz: {derived_fp32:.1f})")
     if mean["t_p2p"] < 0:  # graph mode: the post-traversal phases are timed as one graph
         roof = {"kernel": "post-traversal graph (lists, M2L, L2L/L2P, P2P)", "bound": "alu", "achieved": None,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "note": "graph mode times the graph as a whole; run without --graph for the P2P roofline"}
     elif mean["t_p2p"] >= mean["t_m2l"]:
-        flops = st["p2p_useful_pairs"] * P2P_FLOPS_PER_PAIR
+        fpp = P2P_FLOPS_PER_PAIR_POLY if args.split == "poly" else P2P_FLOPS_PER_PAIR
+        flops = st["p2p_useful_pairs"] * fpp
         achieved = flops / (mean["t_p2p"] / 1e3) / 1e12
         roof = {"kernel": "k_p2p (cut-off P2P)", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
-                "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": measured_traffic("k_p2p", "p2p.cu"),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "algorithmic": f"{st['p2p_useful_pairs']} pairs inside R_c x {P2P_FLOPS_PER_PAIR} flop"}
+                "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+                "traffic": measured_traffic("k_p2p", "p2p.cu") if args.split == "gauss" else None,
+                "peak_source": peak_src,
+                "algorithmic": f"{st['p2p_useful_pairs']} pairs inside R_c x {fpp} flop",
+                "mufu_peaks_tops": {"ex2": round(alu["ex2"], 3), "rsqrt": round(alu["rsqrt"], 3)}}
     else:
         p = args.order
         fl_pair = 2 * math.comb(p + 6, 6)  # for the learned path: counted at the largest order (an upper bound)
@@ -385,12 +460,34 @@ def main():
         roof = {"kernel": f"k_m2l<{p}> (CUDA cores)", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
                 "unit": "TFLOP/s", "frac": achieved / peak_fp32,
                 "traffic": measured_traffic("k_m2l", "m2l.cu"),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": peak_src,
                 "algorithmic": f"{st['nm2l']} M2L pairs x {fl_pair} flop (2 C(p+6,6))"}
+
+    # the metric's other arm on the same resident set and the same accuracy sinks:
+    # learned acceptance with the committed network + 3xTF32 tensor-core M2L
+    arms = None
+    if args.compare and not learned and args.split == "gauss" and args.m2l_precision == 0:
+        lcommon = dict(common, mac_mode=1, m2l_precision=1, theta=args.compare_theta, use_graph=0)
+        lw = np.fromfile(args.mlp_weights, dtype=np.uint16)
+        lacc = torch.empty_like(acc)
+        l_ms, l_ph, _ = time_arm(hfmm, torch, lcommon, lw, dpos, dmass, lacc, flush, args.steps, args.warmup, stream)
+        l_ms_tot = max_over_ranks(sum(l_ms), dev)
+        lval = whole_job_rate(ws, n, args.steps, l_ms_tot / 1e3)
+        l_acc = accuracy_of(lacc, sinks, ref) if accuracy is not None else None
+        lmean = {k[2:]: round(statistics.mean(p[k] for p in l_ph), 4) for k in keys}
+        arms = {"plain": {"path": "geometric acceptance, FP32 CUDA-core M2L", "value": value,
+                          "accuracy": accuracy},
+                "learned_tf32": {"path": f"learned acceptance (committed network, safety bound theta "
+                                         f"{args.compare_theta}), 3xTF32 tensor-core M2L",
+                                 "value": lval, "accuracy": l_acc, "breakdown_ms": lmean,
+                                 "ms_per_step": l_ms_tot / args.steps},
+                "ratio_learned_tf32_over_plain": lval / value,
+                "both_within_1e-4": bool(accuracy and l_acc and accuracy["rms_rel"] <= 1e-4
+                                         and l_acc["rms_rel"] <= 1e-4)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(pos, mass, cfg, args.cpu_seconds)
+        cpu = cpu_oracle_sample(pos, mass, cfg, args.cpu_seconds, split=args.split)
 
     if rank == 0:
         line = {
@@ -398,6 +495,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg),
+                       "split": "polynomial (Sec. 5)" if args.split == "poly" else "Gaussian (Sec. 2.2)",
                        "path": ("learned acceptance (network, safety bound theta), " if learned else
                                 "geometric acceptance, ") + (
                            {1: "3xTF32 tensor-core M2L", 2: "BF16x3 tensor-core M2L"}.get(args.m2l_precision)
@@ -408,6 +506,7 @@ def main():
                        "graph": bool(args.graph), "tiles": tiles or "defaults",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "accuracy": accuracy,
+            "arms": arms,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 4), "d2h_bytes_per_step": n * 12},

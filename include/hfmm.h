@@ -104,6 +104,15 @@ typedef struct {
                           every chunk gives up at once: a test of the error path).  After a give-up
                           every CTA waits again, with the full 2^22 polls, for the MMAs it issued
                           before it frees its tensor memory. */
+  int split;           /* truncation of the force split: 0 = the Gaussian one of Sec. 2.2 (short-range
+                          kernel erfc(r / 2r_s) / r); 1 = a polynomial one, which Sec. 5 allows in place
+                          of it: kernel 1/r - P(r) for r < R_c and 0 beyond, P(r) = (15 - 10 w^2 +
+                          3 w^4) / (8 R_c), w = r / R_c (the even quartic that makes the kernel and its
+                          first two derivatives vanish at R_c; R_c = rcut_rs r_s is its only scale).
+                          The pair force is then m (-1/r^3 + 5 / (2 R_c^3) - 3 r^2 / (2 R_c^5)) r, the
+                          M2L prefactors the Newtonian ones minus those of P (none beyond the second),
+                          and the PM Green function 4 pi / k^2 minus the transform of the kernel.
+                          Split 1 needs mac_mode 0, m2l_precision 0 and m2l_tables 0. */
   int list_init;       /* initial capacity, in entries, of every traversal list (frontier, M2L, P2P,
                           segments, runs) of a new context: 0 = a guess scaled with n and leaf_max;
                           a small value makes the walk overflow and repeat with grown lists (the
@@ -185,7 +194,9 @@ int hfmm_short_range_forces_host(hfmm_ctx *ctx, const double *pos_soa, const flo
 
 /*
  * Long-range accelerations of the force split (Sec. 2.2: 1/r = erfc(r/2r_s)/r +
- * erf(r/2r_s)/r; the erf part on the PM mesh of the same section), ADDED to acc_soa
+ * erf(r/2r_s)/r; the erf part on the PM mesh of the same section; with split 1 the
+ * complement of the polynomial kernel, Green function 4 pi / k^2 minus the kernel's
+ * transform, tabulated in FP64 per integer |k|^2 on the mesh), ADDED to acc_soa
  * (device float32 [3][n], input order) for the particles of the last
  * hfmm_build_tree.  Mesh: pm_grid^3 points x_g = g L / pm_grid; cloud-in-cell
  * assignment and interpolation; cuFFT; Green function 4 pi G exp(-k^2 r_s^2) / k^2

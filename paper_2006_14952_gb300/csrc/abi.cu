@@ -51,6 +51,9 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.use_graph != 0 && p.use_graph != 1) return why = "use_graph must be 0 or 1", false;
   if (p.list_init < 0) return why = "list_init must be >= 0", false;
   if (p.tc_wait_polls < -1) return why = "tc_wait_polls must be >= -1", false;
+  if (p.split != 0 && p.split != 1) return why = "split must be 0 (Gaussian) or 1 (polynomial)", false;
+  if (p.split == 1 && (p.mac_mode != 0 || p.m2l_precision != 0 || p.m2l_tables != 0))
+    return why = "split 1 needs mac_mode 0, m2l_precision 0 and m2l_tables 0", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;

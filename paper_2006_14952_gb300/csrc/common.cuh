@@ -274,6 +274,8 @@ struct Ctx {
 
   // PM long range (cuFFT plans made on first use; -1 = none) and the step
   DBuf pm_q, pm_rho, pm_mk, pm_ak, pm_a;
+  DBuf pm_gtab;          // polynomial split: long-range Green function per integer |k|^2
+  size_t pm_gtab_n = 0;  // its length (0: not built)
   int pm_plan_r2c = -1, pm_plan_c2r = -1;
   const float *mass_ref = nullptr;  // the mass array of the last build_tree
 

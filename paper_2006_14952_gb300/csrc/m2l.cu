@@ -6,7 +6,8 @@
 // of levels.  The body forms D'_c = u^(|c|+1) D^_c once per c and takes the
 // source coefficients as (v/u)^|m| M~_m, so each term u^(|n|+1) v^|m| D^ M~ is
 // one FMA (u >= 2^-17 at the depth cap, so u^(p+1) and (v/u)^p stay in range).  D^ is the derivative tensor of erfc(x r^ / 2) / r^ at r^ = 1,
-// x = r / r_s, from the radial prefactors f_(k) = ((1/r) d/dr)^k psi:
+// x = r / r_s, from the radial prefactors f_(k) = ((1/r) d/dr)^k psi (or of the
+// polynomial truncation 1/r - P(r) of Sec. 5 with split 1; radial_prefactors):
 //   D^_c = sum_{k_d <= c_d/2} prod_d [c_d! / (2^k_d k_d! (c_d - 2k_d)!)] R^_d^(c_d-2k_d) f_(|c|-|k|).
 //
 // One lane per (sink, source) pair; a warp walks the pairs of one sink (lists
@@ -23,7 +24,39 @@
 namespace hfmm {
 namespace {
 
-template <int P, int G, int g>
+// Normalised prefactors f^_k = r^(2k+1) f_(k)(r), k = 0..P, of the kernel of
+// split S: S = 0 the Gaussian erfc(x/2)/r with x = r / r_s (the recurrence
+// f^_(k+1) = -(2k+1) f^_k + (-1)^(k+1) x^(2k+1) e^(-x^2/4) / (2^k sqrt(pi)));
+// S = 1 the polynomial truncation 1/r - P(r) with w = r / R_c:
+// f^_0 = 1 - w (15 - 10 w^2 + 3 w^4) / 8, f^_1 = -1 + w^3 (5 - 3 w^2) / 2,
+// f^_2 = 3 - 3 w^5 and the Newtonian (-1)^k (2k-1)!! beyond.
+template <int P, int S>
+__device__ __forceinline__ void radial_prefactors(float x, float (&f)[P + 1]) {
+  if constexpr (S == 1) {
+    const float w = x, w2 = w * w;
+    f[0] = 1.f - w * (15.f - 10.f * w2 + 3.f * w2 * w2) * 0.125f;
+    if constexpr (P >= 1) f[1] = -1.f + w2 * w * (5.f - 3.f * w2) * 0.5f;
+    if constexpr (P >= 2) f[2] = 3.f - 3.f * w2 * w2 * w;
+    float dk = 3.f;  // |f^_k| = (2k - 1)!!
+#pragma unroll
+    for (int q = 3; q <= P; ++q) {
+      dk *= (float)(2 * q - 1);
+      f[q] = (q & 1) ? -dk : dk;
+    }
+  } else {
+    const float kInvSqrtPi = 0.56418958354775628f;
+    f[0] = erfcf(0.5f * x);
+    float tk = -x * kInvSqrtPi * __expf(-0.25f * x * x);
+    const float hx2 = 0.5f * x * x;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      f[q + 1] = -(float)(2 * q + 1) * f[q] + tk;
+      tk = -tk * hx2;
+    }
+  }
+}
+
+template <int P, int G, int g, int S>
 __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, const uint4 *__restrict__ cell,
                                          const uint64_t *__restrict__ lst, const float *__restrict__ M,
                                          float *__restrict__ L, int ldm, float inv_rs, float *__restrict__ wsm) {
@@ -31,7 +64,6 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
   constexpr int NS = (NC + G - 1) / G;
   constexpr bool kSmem = M2LSlices<P>::kSmem;
   const int lane = threadIdx.x & 31;
-  const float kInvSqrtPi = 0.56418958354775628f;
   const uint4 ca = cell[k];
   float acc[NS];
 #pragma unroll
@@ -46,18 +78,11 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
     const float Rx = -(float)dd[0], Ry = -(float)dd[1], Rz = -(float)dd[2];
     const float r2 = Rx * Rx + Ry * Ry + Rz * Rz;
     const float rinv = rsqrtf(r2);
-    const float x = r2 * rinv * inv_rs;  // r / r_s
+    const float x = r2 * rinv * inv_rs;  // r / r_s (S = 0) or r / R_c (S = 1)
     const float u = (float)(2 * half_width(ca.w)) * rinv;
     const float v = (float)half_width(cb.w) / (float)half_width(ca.w);  // v/u = h_B / h_A (exact)
     float f[P + 1];
-    f[0] = erfcf(0.5f * x);
-    float tk = -x * kInvSqrtPi * __expf(-0.25f * x * x);
-    const float hx2 = 0.5f * x * x;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      f[q + 1] = -(float)(2 * q + 1) * f[q] + tk;
-      tk = -tk * hx2;
-    }
+    radial_prefactors<P, S>(x, f);
     float U[P + 1];
     U[0] = u;
 #pragma unroll
@@ -105,7 +130,7 @@ __device__ __forceinline__ void m2l_sink(uint32_t k, uint32_t tb, uint32_t te, c
 template <int P>
 constexpr int m2l_min_blocks() { return P <= 4 ? 4 : P == 5 ? 3 : 2; }
 
-template <int P, int G>
+template <int P, int G, int S>
 __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_m2l(int64_t nn, const uint4 *__restrict__ cell,
                                              const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
                                              const uint64_t *__restrict__ lst, const float *__restrict__ M,
@@ -120,47 +145,47 @@ __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_m2l(int64_t nn, co
     const uint32_t tb = beg[k], te = end[k];
     if (tb == te) continue;
     if constexpr (G == 1) {
-      m2l_sink<P, 1, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      m2l_sink<P, 1, 0, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
     } else if constexpr (G == 2) {
-      if (g == 0) m2l_sink<P, 2, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
-      else m2l_sink<P, 2, 1>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      if (g == 0) m2l_sink<P, 2, 0, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else m2l_sink<P, 2, 1, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
     } else if constexpr (G == 4) {
-      if (g == 0) m2l_sink<P, 4, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
-      else if (g == 1) m2l_sink<P, 4, 1>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
-      else if (g == 2) m2l_sink<P, 4, 2>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
-      else m2l_sink<P, 4, 3>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      if (g == 0) m2l_sink<P, 4, 0, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else if (g == 1) m2l_sink<P, 4, 1, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else if (g == 2) m2l_sink<P, 4, 2, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
+      else m2l_sink<P, 4, 3, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm);
     } else {
       static_assert(G == 8, "slices");
       switch (g) {
-        case 0: m2l_sink<P, 8, 0>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        case 1: m2l_sink<P, 8, 1>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        case 2: m2l_sink<P, 8, 2>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        case 3: m2l_sink<P, 8, 3>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        case 4: m2l_sink<P, 8, 4>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        case 5: m2l_sink<P, 8, 5>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        case 6: m2l_sink<P, 8, 6>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
-        default: m2l_sink<P, 8, 7>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 0: m2l_sink<P, 8, 0, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 1: m2l_sink<P, 8, 1, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 2: m2l_sink<P, 8, 2, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 3: m2l_sink<P, 8, 3, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 4: m2l_sink<P, 8, 4, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 5: m2l_sink<P, 8, 5, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        case 6: m2l_sink<P, 8, 6, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
+        default: m2l_sink<P, 8, 7, S>(k, tb, te, cell, lst, M, L, ldm, inv_rs, wsm); break;
       }
     }
   }
 }
 
-template <int P>
+template <int P, int S>
 cudaError_t launch(Ctx &c, cudaStream_t st) {
   constexpr int G = M2LSlices<P>::G;
   unsigned g = blocks_for((size_t)c.nnodes * G, 4);
   const unsigned cap = 152u * (unsigned)(c.prm.tile_m2l_blocks > 0 ? c.prm.tile_m2l_blocks : 64);
   if (g > cap) g = cap;
-  // r / r_s with r in half units: x = r_half * (L / 2^22) / r_s
-  const float inv_rs = (float)(c.prm.box / (double)kHalfBox / c.rs);
+  // r / r_s (Gaussian) or r / R_c (polynomial) with r in half units: x = r_half * (L / 2^22) / scale
+  const float inv_rs = (float)(c.prm.box / (double)kHalfBox / (S == 1 ? c.rc : c.rs));
   size_t smem = M2LSlices<P>::kSmem ? (size_t)4 * ncoef(P) * 32 * sizeof(float)
                                     : (size_t)4 * 32 * (ncoef(P) + 1) * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_m2l<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l<P, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   // the entries [mid, end) of each sink: pairs outside the operator table
-  k_m2l<P, G><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_mid),
+  k_m2l<P, G, S><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_mid),
                                     hfmm::P<uint32_t>(c.m2l_end), hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M),
                                     hfmm::P<float>(c.L), c.ldm, inv_rs);
   note_launch();
@@ -171,15 +196,16 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
 
 cudaError_t m2l_pass(Ctx &c, int q, cudaStream_t st) {
   if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
+  const bool poly = c.prm.split == 1;
   switch (q) {
-    case 1: return launch<1>(c, st);
-    case 2: return launch<2>(c, st);
-    case 3: return launch<3>(c, st);
-    case 4: return launch<4>(c, st);
-    case 5: return launch<5>(c, st);
-    case 6: return launch<6>(c, st);
-    case 7: return launch<7>(c, st);
-    case 8: return launch<8>(c, st);
+    case 1: return poly ? launch<1, 1>(c, st) : launch<1, 0>(c, st);
+    case 2: return poly ? launch<2, 1>(c, st) : launch<2, 0>(c, st);
+    case 3: return poly ? launch<3, 1>(c, st) : launch<3, 0>(c, st);
+    case 4: return poly ? launch<4, 1>(c, st) : launch<4, 0>(c, st);
+    case 5: return poly ? launch<5, 1>(c, st) : launch<5, 0>(c, st);
+    case 6: return poly ? launch<6, 1>(c, st) : launch<6, 0>(c, st);
+    case 7: return poly ? launch<7, 1>(c, st) : launch<7, 0>(c, st);
+    case 8: return poly ? launch<8, 1>(c, st) : launch<8, 0>(c, st);
   }
   return cudaErrorInvalidValue;
 }

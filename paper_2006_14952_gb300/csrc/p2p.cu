@@ -28,7 +28,7 @@
 // instructions; rsqrt and exp2 stay per element).  An odd tail is padded with a
 // massless source far outside the cut-off.
 //
-// Pair force: a = -m S(x) r / r^3, S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi),
+// Pair force (Gaussian split): a = -m S(x) r / r^3, S(x) = erfc(x/2) + x e^(-x^2/4) / sqrt(pi),
 // x = r / r_s, evaluated as S = exp2(-x^2 log2(e) / 4) * Q(r) with Q a degree-9
 // polynomial interpolating e^(x^2/4) erfc(x/2) + x / sqrt(pi) at Chebyshev
 // nodes on [0, R_c], expanded in powers of u = r - R_c / 2 (coefficients from
@@ -60,10 +60,14 @@ __device__ __forceinline__ float exp2_mufu(float x) {
 struct PairFit2 {
   float2 c[10];
   float2 nrmid, kexp;  // -R_c / 2, -log2(e) / (4 r_s^2)
+  float2 pc0, pc1;     // polynomial split: -5 / (2 R_c^3), 3 / (2 R_c^5)
   float rc2;
 };
 
-template <bool kCount, int kCap>
+// kSplit 0: the Gaussian truncation S(x) above; 1: the polynomial truncation of
+// Sec. 5, a = -m (1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5)) r, no exp2 and no
+// fitted factor (see hfmm_params.split).
+template <bool kCount, int kCap, int kSplit>
 __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
                                                 const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
                                                 const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
@@ -309,14 +313,20 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
           if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
           // outside (0, R_c) the values below may be inf/NaN; the selects discard them
           const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-          const float2 tt = __ffma2_rn(r2, rinv, fit.nrmid);  // u = r - R_c / 2
-          float2 qv = fit.c[9];
-#pragma unroll
-          for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, fit.c[j]);
-          const float2 ea = __fmul2_rn(r2, fit.kexp);
-          const float2 sfac = __fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv);
           const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
-          float2 f = __fmul2_rn(__fmul2_rn(sfac, r3), make_float2(B.z, B.w));  // -S m / r^3
+          float2 f;
+          if constexpr (kSplit == 1) {
+            // -m (1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5))
+            f = __fmul2_rn(__fadd2_rn(r3, __ffma2_rn(r2, fit.pc1, fit.pc0)), make_float2(B.z, B.w));
+          } else {
+            const float2 tt = __ffma2_rn(r2, rinv, fit.nrmid);  // u = r - R_c / 2
+            float2 qv = fit.c[9];
+#pragma unroll
+            for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, fit.c[j]);
+            const float2 ea = __fmul2_rn(r2, fit.kexp);
+            const float2 sfac = __fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv);
+            f = __fmul2_rn(__fmul2_rn(sfac, r3), make_float2(B.z, B.w));  // -S m / r^3
+          }
           f.x = in0 ? f.x : 0.f;
           f.y = in1 ? f.y : 0.f;
           sx = __ffma2_rn(f, dx, sx);
@@ -383,13 +393,20 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   unsigned g = (unsigned)(nsm * per_sm);
   if ((size_t)g * 8 > (size_t)c.nleaves) g = blocks_for(c.nleaves, 8);
   const bool small = c.prm.tile_p2p_stage == 128, count = (c.prm.profile & 2) != 0;
-  auto kern = count ? (small ? k_p2p<true, 128> : k_p2p<true, 256>) : (small ? k_p2p<false, 128> : k_p2p<false, 256>);
+  auto kern = c.prm.split == 1
+                  ? (count ? (small ? k_p2p<true, 128, 1> : k_p2p<true, 256, 1>)
+                           : (small ? k_p2p<false, 128, 1> : k_p2p<false, 256, 1>))
+                  : (count ? (small ? k_p2p<true, 128, 0> : k_p2p<true, 256, 0>)
+                           : (small ? k_p2p<false, 128, 0> : k_p2p<false, 256, 0>));
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
   PairFit2 fit2;  // the context's fit as packed operand pairs
   for (int j = 0; j < 10; ++j) fit2.c[j] = make_float2(c.fit.c[j], c.fit.c[j]);
   fit2.nrmid = make_float2(-c.fit.rmid, -c.fit.rmid);
   fit2.kexp = make_float2(c.fit.kexp, c.fit.kexp);
+  const float pc0 = (float)(-2.5 / (c.rc * c.rc * c.rc)), pc1 = (float)(1.5 / (c.rc * c.rc * c.rc * c.rc * c.rc));
+  fit2.pc0 = make_float2(pc0, pc0);
+  fit2.pc1 = make_float2(pc1, pc1);
   fit2.rc2 = c.fit.rc2;
   // two buffers (raw copies, evaluation pairs) of kCap float4 per warp
   const size_t dyn = (size_t)2 * 8 * (small ? 128 : 256) * sizeof(float4);

@@ -20,6 +20,7 @@
 #include <cufft.h>
 
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -95,16 +96,19 @@ __global__ void k_fixed_to_real(const unsigned long long *__restrict__ q, int64_
 __device__ __forceinline__ float sincf_(float x) { return fabsf(x) < 1e-4f ? 1.f - x * x / 6.f : sinf(x) / x; }
 
 // m(k) -> the three gradient components i k_d G(k) m(k) / L^3 (R2C layout [ng][ng][ng/2+1]).
+// gtab == nullptr: the Gaussian Green function; otherwise gtab[i^2 + j^2 + l^2]
+// holds the long-range Green function at that integer |k|^2 (units (2 pi / L)^2).
 __global__ void k_green(const cufftComplex *__restrict__ mk, int ng, float box, float rs, float G,
-                        cufftComplex *__restrict__ ak) {
+                        const float *__restrict__ gtab, cufftComplex *__restrict__ ak) {
   const int nz = ng / 2 + 1;
   const int64_t total = (int64_t)ng * ng * nz;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int iz = (int)(t % nz), iy = (int)((t / nz) % ng), ix = (int)(t / ((int64_t)nz * ng));
   const float kf = 2.f * 3.14159265358979f / box;
-  const float kx = kf * (float)(ix <= ng / 2 ? ix : ix - ng);
-  const float ky = kf * (float)(iy <= ng / 2 ? iy : iy - ng);
+  const int jx = ix <= ng / 2 ? ix : ix - ng, jy = iy <= ng / 2 ? iy : iy - ng;
+  const float kx = kf * (float)jx;
+  const float ky = kf * (float)jy;
   const float kz = kf * (float)iz;
   const float k2 = kx * kx + ky * ky + kz * kz;
   float g = 0.f;
@@ -112,7 +116,10 @@ __global__ void k_green(const cufftComplex *__restrict__ mk, int ng, float box, 
     const float hh = 0.5f * box / (float)ng;
     const float w = sincf_(kx * hh) * sincf_(ky * hh) * sincf_(kz * hh);
     const float w2 = w * w;  // W(k) = (product of sincs)^2, divided out twice
-    g = 4.f * 3.14159265358979f * G * expf(-k2 * rs * rs) / (k2 * w2 * w2) / (box * box * box);
+    if (gtab)
+      g = G * gtab[jx * jx + jy * jy + iz * iz] / (w2 * w2) / (box * box * box);
+    else
+      g = 4.f * 3.14159265358979f * G * expf(-k2 * rs * rs) / (k2 * w2 * w2) / (box * box * box);
   }
   const bool even = (ng & 1) == 0;
   const float kd[3] = {(even && ix == ng / 2) ? 0.f : kx, (even && iy == ng / 2) ? 0.f : ky,
@@ -185,7 +192,67 @@ void pm_release(Ctx &c) {
   release(c.pm_mk);
   release(c.pm_ak);
   release(c.pm_a);
+  release(c.pm_gtab);
+  c.pm_gtab_n = 0;
 }
+
+namespace {
+
+// Gauss-Legendre rule of n points on [0, 1]: Newton's method on the Legendre
+// polynomial P_n (three-term recurrence), started from the Chebyshev-like
+// estimates cos(pi (i + 3/4) / (n + 1/2)) of its roots.
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      const double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[i] = 0.5 * (t + 1.0);
+    w[i] = 1.0 / ((1.0 - t * t) * dp * dp);  // (2 / ((1 - t^2) P'^2)) / 2 for [0, 1]
+  }
+}
+
+// Long-range Green function of the polynomial split at |k|^2 = (2 pi / L)^2 n,
+// n = 0..3 (ng/2)^2: 4 pi / k^2 minus the transform of the short-range kernel
+// 1/r - P(r) (r < R_c),
+//   psi^(k) = (4 pi R_c / k) int_0^1 [1 - (15 x - 10 x^3 + 3 x^5) / 8] sin(k R_c x) dx,
+// by a 96-point Gauss-Legendre rule in FP64 (k R_c stays below 10 pi for the
+// meshes allowed, a few oscillations of a smooth integrand).
+cudaError_t green_table_poly(Ctx &c) {
+  const int ng = c.prm.pm_grid, h = ng / 2;
+  const size_t nt = (size_t)3 * h * h + 1;
+  if (c.pm_gtab_n == nt) return cudaSuccess;
+  std::vector<double> gx, gw;
+  gauss_legendre01(96, gx, gw);
+  std::vector<float> tab(nt, 0.f);
+  const double kf = 2.0 * M_PI / c.prm.box, rc = c.rc;
+  for (size_t n = 1; n < nt; ++n) {
+    const double k = kf * std::sqrt((double)n);
+    double integ = 0.0;
+    for (int i = 0; i < 96; ++i) {
+      const double x = gx[i];
+      integ += gw[i] * (1.0 - (15.0 * x - 10.0 * x * x * x + 3.0 * x * x * x * x * x) / 8.0) * std::sin(k * rc * x);
+    }
+    tab[n] = (float)(4.0 * M_PI / (k * k) - 4.0 * M_PI * rc / k * integ);
+  }
+  cudaError_t e = ensure(c.pm_gtab, nt * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(c.pm_gtab.p, tab.data(), nt * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) c.pm_gtab_n = nt;
+  return e;
+}
+
+}  // namespace
 
 cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
@@ -226,8 +293,10 @@ cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = fft_error(cufftExecR2C(c.pm_plan_r2c, P<cufftReal>(c.pm_rho), P<cufftComplex>(c.pm_mk)))) != cudaSuccess)
     return e;
+  if (c.prm.split == 1 && (e = green_table_poly(c)) != cudaSuccess) return e;
   k_green<<<blocks_for(kcells, T), T, 0, st>>>(P<cufftComplex>(c.pm_mk), ng, (float)c.prm.box, (float)c.rs,
-                                               (float)c.prm.G, P<cufftComplex>(c.pm_ak));
+                                               (float)c.prm.G, c.prm.split == 1 ? P<float>(c.pm_gtab) : nullptr,
+                                               P<cufftComplex>(c.pm_ak));
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = fft_error(cufftExecC2R(c.pm_plan_c2r, P<cufftComplex>(c.pm_ak), P<cufftReal>(c.pm_a)))) != cudaSuccess)
