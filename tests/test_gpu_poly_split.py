@@ -93,7 +93,8 @@ def test_pair_force_law_across_the_cutoff_range():
     w = int(np.argmax(e / bound))
     assert np.all(e < bound), f"worst r/R_c {rr[w] / rc:.4f}: err {e[w]:.3e} > bound {bound[w]:.3e}"
     # and the law itself: the FP64 reference is the pinned closed form
-    np.testing.assert_allclose(ref[:, :1000], ((1 / 2000) * PS.pair_factor(r, s.rc))[None, :] * (-r * d),
+    m = float(mass[0])  # the FP32 mass the particles carry
+    np.testing.assert_allclose(ref[:, :1000], (m * PS.pair_factor(r, s.rc))[None, :] * (-r * d),
                                rtol=1e-12, atol=1e-14 * np.abs(ref).max())
 
 
