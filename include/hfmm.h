@@ -113,6 +113,14 @@ typedef struct {
                           M2L prefactors the Newtonian ones minus those of P (none beyond the second),
                           and the PM Green function 4 pi / k^2 minus the transform of the kernel.
                           Split 1 needs mac_mode 0, m2l_precision 0 and m2l_tables 0. */
+  int p2p_mutual;      /* 1 = mutual P2P (Newton's third law): the walk keeps one of the two ordered
+                          leaf pairs (A, B, s) and (B, A, -s), the one with A < B (A = B: s at or
+                          below the unshifted index 13), the kernel evaluates each particle pair of
+                          it once and adds the reaction on B's particles to per-entry partial sums,
+                          which a second pass adds to B's accelerations in list order (the result
+                          does not depend on scheduling).  A leaf against itself stays one-sided.
+                          Needs mac_mode 0 and size_rule 1 (the walk is then symmetric); ignores
+                          use_graph.  The partials take 12 bytes per (entry, source particle). */
   int list_init;       /* initial capacity, in entries, of every traversal list (frontier, M2L, P2P,
                           segments, runs) of a new context: 0 = a guess scaled with n and leaf_max;
                           a small value makes the walk overflow and repeat with grown lists (the

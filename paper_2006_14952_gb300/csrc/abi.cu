@@ -54,6 +54,9 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.split != 0 && p.split != 1) return why = "split must be 0 (Gaussian) or 1 (polynomial)", false;
   if (p.split == 1 && (p.mac_mode != 0 || p.m2l_precision != 0 || p.m2l_tables != 0))
     return why = "split 1 needs mac_mode 0, m2l_precision 0 and m2l_tables 0", false;
+  if (p.p2p_mutual != 0 && p.p2p_mutual != 1) return why = "p2p_mutual must be 0 or 1", false;
+  if (p.p2p_mutual == 1 && (p.mac_mode != 0 || p.size_rule != 1))
+    return why = "p2p_mutual 1 needs mac_mode 0 and size_rule 1", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
@@ -194,7 +197,9 @@ void hfmm_destroy(hfmm_ctx *h) {
                   &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc, &c.m2l_mid, &c.tab,
                   &c.mlp_w, &c.cand, &c.mlp_scratch, &c.fseg, &c.fseg_next, &c.seg_a, &c.seg_b, &c.acc_a,
                   &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
-                  &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p};
+                  &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p,
+                  &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
+                  &c.mut_bounds, &c.mut_small, &c.mut_part};
   for (DBuf *b : bufs) release(*b);
   pm_release(c);
   if (c.gexec) cudaGraphExecDestroy(c.gexec);
@@ -313,7 +318,8 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
     return fail(c, HFMM_ERR_CAPACITY, "an interaction list above 2^32 - 1 entries");
   if (prof) cudaEventRecord(c.ev[5], st);
   c.last_graph = false;
-  if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2)) {
+  if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
+      !c.prm.p2p_mutual) {
     e = post_traversal_graph(c, acc, st, prof);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph");
     return HFMM_OK;
@@ -335,7 +341,10 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (prof) cudaEventRecord(c.ev[7], st);
   if ((e = downward(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "l2l/l2p");
   if (prof) cudaEventRecord(c.ev[8], st);
-  if ((e = p2p_pass(c, acc, st)) != cudaSuccess) return cuda_fail(c, e, "p2p");
+  e = c.prm.p2p_mutual ? p2p_pass_mutual(c, acc, st) : p2p_pass(c, acc, st);
+  if (e == cudaErrorInvalidValue && c.prm.p2p_mutual)
+    return fail(c, HFMM_ERR_CAPACITY, "mutual P2P: more than 2^32 - 1 partial sums");
+  if (e != cudaSuccess) return cuda_fail(c, e, "p2p");
   if (prof) cudaEventRecord(c.ev[9], st);
   return HFMM_OK;
 }

@@ -274,6 +274,9 @@ struct Ctx {
 
   // PM long range (cuFFT plans made on first use; -1 = none) and the step
   DBuf pm_q, pm_rho, pm_mk, pm_ak, pm_a;
+  // mutual P2P: per entry partial counts and offsets, sort keys and entry indices
+  // (ping-pong), per leaf bounds of its entries as a source, partial sums [3][slots]
+  DBuf mut_cnt, mut_poff, mut_key, mut_key_alt, mut_val, mut_val_alt, mut_bounds, mut_small, mut_part;
   DBuf pm_gtab;          // polynomial split: long-range Green function per integer |k|^2
   size_t pm_gtab_n = 0;  // its length (0: not built)
   int pm_plan_r2c = -1, pm_plan_c2r = -1;
@@ -327,6 +330,8 @@ cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t
 cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st);
 // Cut-off P2P, added to the accelerations written by downward().
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st);
+// Mutual P2P (p2p_mutual = 1): one evaluation per particle pair, reactions through per-entry partials.
+cudaError_t p2p_pass_mutual(Ctx &c, float *acc, cudaStream_t st);
 
 // Training pairs for the learned acceptance: features [n][12] and M2L errors
 // at orders 2..8 [n][7] (device buffers of the caller); *count receives n.

@@ -33,37 +33,13 @@
 // polynomial interpolating e^(x^2/4) erfc(x/2) + x / sqrt(pi) at Chebyshev
 // nodes on [0, R_c], expanded in powers of u = r - R_c / 2 (coefficients from
 // the host, fit_pair_factor()).
-#include "common.cuh"
+#include "p2p_common.cuh"
 
 namespace hfmm {
 namespace {
 
 
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-
-// One MUFU instruction each (relative error about 2^-22); the arguments here are
-// never denormal: r^2 > 0 in the cut-off range, and the exponent is -r^2 log2(e) / 4r_s^2 >= -7.3.
-__device__ __forceinline__ float rsqrt_mufu(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float exp2_mufu(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// kCap: source particles per fill (even); dynamic shared memory: 2 x 8 x kCap float4
-// The pair-factor constants duplicated into (x, x) pairs, the operand form of the
-// packed FP32x2 instructions, passed as kernel parameters (no register pairs to fill).
-struct PairFit2 {
-  float2 c[10];
-  float2 nrmid, kexp;  // -R_c / 2, -log2(e) / (4 r_s^2)
-  float2 pc0, pc1;     // polynomial split: -5 / (2 R_c^3), 3 / (2 R_c^5)
-  float rc2;
-};
-
+// kCap: source particles per fill (even); dynamic shared memory: 2 x 8 x kCap float4.
 // kSplit 0: the Gaussian truncation S(x) above; 1: the polynomial truncation of
 // Sec. 5, a = -m (1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5)) r, no exp2 and no
 // fitted factor (see hfmm_params.split).
@@ -400,14 +376,7 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
                            : (small ? k_p2p<false, 128, 0> : k_p2p<false, 256, 0>));
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
-  PairFit2 fit2;  // the context's fit as packed operand pairs
-  for (int j = 0; j < 10; ++j) fit2.c[j] = make_float2(c.fit.c[j], c.fit.c[j]);
-  fit2.nrmid = make_float2(-c.fit.rmid, -c.fit.rmid);
-  fit2.kexp = make_float2(c.fit.kexp, c.fit.kexp);
-  const float pc0 = (float)(-2.5 / (c.rc * c.rc * c.rc)), pc1 = (float)(1.5 / (c.rc * c.rc * c.rc * c.rc * c.rc));
-  fit2.pc0 = make_float2(pc0, pc0);
-  fit2.pc1 = make_float2(pc1, pc1);
-  fit2.rc2 = c.fit.rc2;
+  const PairFit2 fit2 = pair_fit2(c);  // the context's fit as packed operand pairs
   // two buffers (raw copies, evaluation pairs) of kCap float4 per warp
   const size_t dyn = (size_t)2 * 8 * (small ? 128 : 256) * sizeof(float4);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);

@@ -47,6 +47,7 @@ struct Mac {
   int conv;   // 1: conventional acceptance (rule 2 alone, primary box only)
   int order;  // p (geometric M2L order, and the largest learned order)
   int tab_k;  // operator-table half extent (0: no table)
+  int mutual; // 1: keep a P2P pair only as (A, B, s) with A < B, or A = B and s <= 13
   // learned / collect
   const __nv_bfloat16 *w;
   const float *M;
@@ -182,6 +183,9 @@ __device__ __forceinline__ Item mac_item(uint64_t e, bool valid, const uint4 *__
       __syncwarp();
     }
   }
+  // mutual P2P: of the mirror pairs (a, b, s) and (b, a, 26 - s) the walk meets
+  // both (it is symmetric under size_rule 1); keep one
+  if (m.mutual && c == kP2P && !(a < b || (a == b && s <= 13u))) c = kSkip;
   Item it;
   const uint32_t miss = (c == kM2L && table_miss(ca, cb, s, m.tab_k)) ? 1u : 0u;
   it.cls = (uint8_t)(c | (order << 3) | (miss << 7));
@@ -804,6 +808,7 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   m.conv = c.count_walk == 2 ? 1 : 0;
   m.order = c.p;
   m.tab_k = (c.prm.m2l_precision == 0 && c.prm.m2l_tables) ? c.tab_k : 0;
+  m.mutual = (c.prm.p2p_mutual && !c.collect && !c.count_walk) ? 1 : 0;
   m.w = static_cast<const __nv_bfloat16 *>(c.mlp_w.p);
   m.M = P<float>(c.M);
   m.range = P<uint2>(c.range);

@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("m2l_precision", C.c_int), ("profile", C.c_int), ("m2l_tables", C.c_int),
                 ("tile_p2p_stage", C.c_int), ("tile_p2p_blocks", C.c_int), ("tile_m2l_blocks", C.c_int),
                 ("tile_trav_blocks", C.c_int), ("use_graph", C.c_int), ("tc_wait_polls", C.c_int),
-                ("split", C.c_int), ("list_init", C.c_int)]
+                ("split", C.c_int), ("p2p_mutual", C.c_int), ("list_init", C.c_int)]
 
 
 class Stats(C.Structure):
