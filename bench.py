@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--mlp-weights", default=os.path.join(ROOT, "paper_2006_14952_gb300", "weights", "mac_weights.bin"))
     ap.add_argument("--split", default="gauss", choices=["gauss", "poly"],
                     help="truncation of the force split: Gaussian (Sec. 2.2) or polynomial (Sec. 5)")
+    ap.add_argument("--mutual", type=int, default=0, help="1: mutual (third-law) P2P")
     ap.add_argument("--compare", type=int, default=1,
                     help="1: also time the metric's other arm (learned acceptance + 3xTF32 M2L) on the same set")
     ap.add_argument("--compare-theta", type=float, default=0.5, help="safety bound of the learned arm")
@@ -349,6 +350,7 @@ def main():
     common = dict(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
                   order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision,
                   m2l_tables=args.m2l_tables, use_graph=args.graph, split=1 if args.split == "poly" else 0,
+                  p2p_mutual=args.mutual,
                   **tiles, **mac_kw)
     wts = np.fromfile(args.mlp_weights, dtype=np.uint16) if learned else None
     s = hfmm.Solver(profile=1, **common)
@@ -451,7 +453,9 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak_fp32,
                 "traffic": measured_traffic("k_p2p", "p2p.cu") if args.split == "gauss" else None,
                 "peak_source": peak_src,
-                "algorithmic": f"{st['p2p_useful_pairs']} pairs inside R_c x {fpp} flop",
+                "algorithmic": f"{st['p2p_useful_pairs']} pairs inside R_c x {fpp} flop" + (
+                    " (ordered pairs: the mutual kernel evaluates each unordered pair once and counts both "
+                    "forces)" if args.mutual else ""),
                 "mufu_peaks_tops": {"ex2": round(alu["ex2"], 3), "rsqrt": round(alu["rsqrt"], 3)}}
     else:
         p = args.order
@@ -467,7 +471,7 @@ def main():
     # learned acceptance with the committed network + 3xTF32 tensor-core M2L
     arms = None
     if args.compare and not learned and args.split == "gauss" and args.m2l_precision == 0:
-        lcommon = dict(common, mac_mode=1, m2l_precision=1, theta=args.compare_theta, use_graph=0)
+        lcommon = dict(common, mac_mode=1, m2l_precision=1, theta=args.compare_theta, use_graph=0, p2p_mutual=0)
         lw = np.fromfile(args.mlp_weights, dtype=np.uint16)
         lacc = torch.empty_like(acc)
         l_ms, l_ph, _ = time_arm(hfmm, torch, lcommon, lw, dpos, dmass, lacc, flush, args.steps, args.warmup, stream)
@@ -496,6 +500,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg),
                        "split": "polynomial (Sec. 5)" if args.split == "poly" else "Gaussian (Sec. 2.2)",
+                       "p2p": "mutual (third law)" if args.mutual else "one-sided",
                        "path": ("learned acceptance (network, safety bound theta), " if learned else
                                 "geometric acceptance, ") + (
                            {1: "3xTF32 tensor-core M2L", 2: "BF16x3 tensor-core M2L"}.get(args.m2l_precision)
