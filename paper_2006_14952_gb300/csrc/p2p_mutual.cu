@@ -7,7 +7,7 @@
 // per sink leaf like the one-sided kernel: the sources of the leaf's list are
 // staged through shared memory in fills (asynchronous copies one fill ahead,
 // moved into A's frame, culled against the bounding box of the sink chunk,
-// paired up), and each lane keeps one pair of staged sources in registers for a
+// paired up), and each lane keeps kPL pairs of staged sources in registers for a
 // round while the chunk's sinks rotate through the lanes: in a group of G lanes
 // (G the power of two at or above the chunk size) the sink and the force it has
 // gathered move one lane per step, so after G steps every sink has met every
@@ -29,6 +29,7 @@ namespace {
 
 constexpr uint32_t kNoSlot = 0xffffffffu;  // a staged source without a reaction (the leaf itself)
 constexpr int kCapM = 256;                 // source particles per fill
+constexpr int kPL = 4;                     // source pairs a lane holds in one rotation round
 
 __device__ __forceinline__ int pow2_at_least(int c) {
   return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : c <= 8 ? 8 : c <= 16 ? 16 : 32;
@@ -266,54 +267,73 @@ __global__ void __launch_bounds__(256, 2)
         __syncwarp();
         pending = q < te;
         if (pending) tot = issue(q, jq);
-        // rounds of 32 source pairs: lane holds pair base + lane, the sinks rotate
+        // rounds of 32 kPL source pairs: lane holds pairs base + 32 u + lane (u < kPL,
+        // independent chains between two rotations), the sinks rotate
         const int np = (int)((kept + 1) >> 1);
-        for (int base = 0; base < np; base += 32) {
-          const int qq = base + lane;
-          float4 A = make_float4(-1e18f, -1e18f, -1e18f, -1e18f), B = make_float4(-1e18f, -1e18f, 0.f, 0.f);
-          uint32_t s0 = kNoSlot, s1 = kNoSlot;
-          if (qq < np) {
-            A = buf[2 * qq];
-            B = buf[2 * qq + 1];
-            s0 = ks[wid][2 * qq];
-            s1 = ks[wid][2 * qq + 1];
-          }
-          const float2 jx = make_float2(A.x, A.y), jy = make_float2(A.z, A.w), jz = make_float2(B.x, B.y);
-          const float2 nmj = make_float2(B.z, B.w);  // -m_j
-          float2 Rx = f2(0.f), Ry = f2(0.f), Rz = f2(0.f);
-          for (int st = 0; st < Gs; ++st) {
-            const float2 dx = __fadd2_rn(f2(si.x), jx);
-            const float2 dy = __fadd2_rn(f2(si.y), jy);
-            const float2 dz = __fadd2_rn(f2(si.z), jz);
-            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const bool in0 = (r2.x < fit.rc2) && (r2.x > 0.f);
-            const bool in1 = (r2.y < fit.rc2) && (r2.y > 0.f);
-            if (kCount)
-              n_in += (uint32_t)in0 * (s0 != kNoSlot ? 2u : 1u) + (uint32_t)in1 * (s1 != kNoSlot ? 2u : 1u);
-            const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
-            float2 g;  // -f_(1)(r): S / r^3 (Gaussian) or 1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5)
-            if constexpr (kSplit == 1) {
-              g = __fadd2_rn(r3, __ffma2_rn(r2, fit.pc1, fit.pc0));
-            } else {
-              const float2 tt = __ffma2_rn(r2, rinv, fit.nrmid);
-              float2 qv = fit.c[9];
+        for (int base = 0; base < np; base += 32 * kPL) {
+          float2 jx[kPL], jy[kPL], jz[kPL], nmj[kPL], Rx[kPL], Ry[kPL], Rz[kPL];
+          uint32_t s0[kPL], s1[kPL];
 #pragma unroll
-              for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, fit.c[j]);
-              const float2 ea = __fmul2_rn(r2, fit.kexp);
-              g = __fmul2_rn(__fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv), r3);
+          for (int u = 0; u < kPL; ++u) {
+            const int qq = base + 32 * u + lane;
+            float4 A = make_float4(-1e18f, -1e18f, -1e18f, -1e18f), B = make_float4(-1e18f, -1e18f, 0.f, 0.f);
+            s0[u] = kNoSlot;
+            s1[u] = kNoSlot;
+            if (qq < np) {
+              A = buf[2 * qq];
+              B = buf[2 * qq + 1];
+              s0[u] = ks[wid][2 * qq];
+              s1[u] = ks[wid][2 * qq + 1];
             }
-            g.x = in0 ? g.x : 0.f;
-            g.y = in1 ? g.y : 0.f;
-            // on the sink: m_j f_(1) d = (-m_j) g d; on the sources: m_i g d
-            const float2 fa = __fmul2_rn(g, nmj);
-            ax = fmaf(fa.x, dx.x, fmaf(fa.y, dx.y, ax));
-            ay = fmaf(fa.x, dy.x, fmaf(fa.y, dy.y, ay));
-            az = fmaf(fa.x, dz.x, fmaf(fa.y, dz.y, az));
-            const float2 fr = __fmul2_rn(g, f2(si.w));
-            Rx = __ffma2_rn(fr, dx, Rx);
-            Ry = __ffma2_rn(fr, dy, Ry);
-            Rz = __ffma2_rn(fr, dz, Rz);
+            jx[u] = make_float2(A.x, A.y);
+            jy[u] = make_float2(A.z, A.w);
+            jz[u] = make_float2(B.x, B.y);
+            nmj[u] = make_float2(B.z, B.w);  // -m_j
+            Rx[u] = f2(0.f);
+            Ry[u] = f2(0.f);
+            Rz[u] = f2(0.f);
+          }
+          // slices that hold no source pair in any lane are skipped (warp-uniform)
+          const int nu = (np - base + 31) / 32 < kPL ? (np - base + 31) / 32 : kPL;
+          for (int st = 0; st < Gs; ++st) {
+            const float2 sx = f2(si.x), sy = f2(si.y), sz = f2(si.z), smi = f2(si.w);
+#pragma unroll
+            for (int u = 0; u < kPL; ++u) {
+              if (u < nu) {
+                const float2 dx = __fadd2_rn(sx, jx[u]);
+                const float2 dy = __fadd2_rn(sy, jy[u]);
+                const float2 dz = __fadd2_rn(sz, jz[u]);
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const bool in0 = (r2.x < fit.rc2) && (r2.x > 0.f);
+                const bool in1 = (r2.y < fit.rc2) && (r2.y > 0.f);
+                if (kCount)
+                  n_in += (uint32_t)in0 * (s0[u] != kNoSlot ? 2u : 1u) + (uint32_t)in1 * (s1[u] != kNoSlot ? 2u : 1u);
+                const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+                float2 g;  // -f_(1)(r): S / r^3 (Gaussian) or 1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5)
+                if constexpr (kSplit == 1) {
+                  g = __fadd2_rn(r3, __ffma2_rn(r2, fit.pc1, fit.pc0));
+                } else {
+                  const float2 tt = __ffma2_rn(r2, rinv, fit.nrmid);
+                  float2 qv = fit.c[9];
+#pragma unroll
+                  for (int j = 8; j >= 0; --j) qv = __ffma2_rn(qv, tt, fit.c[j]);
+                  const float2 ea = __fmul2_rn(r2, fit.kexp);
+                  g = __fmul2_rn(__fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv), r3);
+                }
+                g.x = in0 ? g.x : 0.f;
+                g.y = in1 ? g.y : 0.f;
+                // on the sink: m_j f_(1) d = (-m_j) g d; on the sources: m_i g d
+                const float2 fa = __fmul2_rn(g, nmj[u]);
+                ax = fmaf(fa.x, dx.x, fmaf(fa.y, dx.y, ax));
+                ay = fmaf(fa.x, dy.x, fmaf(fa.y, dy.y, ay));
+                az = fmaf(fa.x, dz.x, fmaf(fa.y, dz.y, az));
+                const float2 fr = __fmul2_rn(g, smi);
+                Rx[u] = __ffma2_rn(fr, dx, Rx[u]);
+                Ry[u] = __ffma2_rn(fr, dy, Ry[u]);
+                Rz[u] = __ffma2_rn(fr, dz, Rz[u]);
+              }
+            }
             // the sink and its force move one lane down the group
             si.x = __shfl_sync(0xffffffffu, si.x, src_lane);
             si.y = __shfl_sync(0xffffffffu, si.y, src_lane);
@@ -323,26 +343,29 @@ __global__ void __launch_bounds__(256, 2)
             ay = __shfl_sync(0xffffffffu, ay, src_lane);
             az = __shfl_sync(0xffffffffu, az, src_lane);
           }
-          if (s0 != kNoSlot) {
-            if (first_chunk) {
-              px_part[s0] = Rx.x;
-              py_part[s0] = Ry.x;
-              pz_part[s0] = Rz.x;
-            } else {
-              px_part[s0] += Rx.x;
-              py_part[s0] += Ry.x;
-              pz_part[s0] += Rz.x;
+#pragma unroll
+          for (int u = 0; u < kPL; ++u) {
+            if (s0[u] != kNoSlot) {
+              if (first_chunk) {
+                px_part[s0[u]] = Rx[u].x;
+                py_part[s0[u]] = Ry[u].x;
+                pz_part[s0[u]] = Rz[u].x;
+              } else {
+                px_part[s0[u]] += Rx[u].x;
+                py_part[s0[u]] += Ry[u].x;
+                pz_part[s0[u]] += Rz[u].x;
+              }
             }
-          }
-          if (s1 != kNoSlot) {
-            if (first_chunk) {
-              px_part[s1] = Rx.y;
-              py_part[s1] = Ry.y;
-              pz_part[s1] = Rz.y;
-            } else {
-              px_part[s1] += Rx.y;
-              py_part[s1] += Ry.y;
-              pz_part[s1] += Rz.y;
+            if (s1[u] != kNoSlot) {
+              if (first_chunk) {
+                px_part[s1[u]] = Rx[u].y;
+                py_part[s1[u]] = Ry[u].y;
+                pz_part[s1[u]] = Rz[u].y;
+              } else {
+                px_part[s1[u]] += Rx[u].y;
+                py_part[s1[u]] += Ry[u].y;
+                pz_part[s1[u]] += Rz[u].y;
+              }
             }
           }
         }
