@@ -442,17 +442,24 @@ __global__ void __launch_bounds__(256) k_p2p_reactions(const uint32_t *__restric
     const uint2 rb = range[b];
     const uint32_t lo = rbeg[b], hi = rend[b];
     float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, sx1 = 0.f, sy1 = 0.f, sz1 = 0.f;
-    for (uint32_t i = lo; i < hi; ++i) {
-      const uint64_t base = poff[ents[i]];
-      if ((uint32_t)lane < rb.y) {
-        sx0 += part[base + lane];
-        sy0 += part[npart + base + lane];
-        sz0 += part[2 * npart + base + lane];
-      }
-      if ((uint32_t)lane + 32u < rb.y) {
-        sx1 += part[base + lane + 32];
-        sy1 += part[npart + base + lane + 32];
-        sz1 += part[2 * npart + base + lane + 32];
+    for (uint32_t i0 = lo; i0 < hi; i0 += 32) {
+      // the partial offsets of the next 32 entries, one per lane, then broadcast
+      uint32_t po = 0;
+      if (i0 + lane < hi) po = poff[ents[i0 + lane]];
+      const int m = hi - i0 < 32u ? (int)(hi - i0) : 32;
+#pragma unroll 4
+      for (int j = 0; j < m; ++j) {
+        const uint64_t base = __shfl_sync(0xffffffffu, po, j);
+        if ((uint32_t)lane < rb.y) {
+          sx0 += part[base + lane];
+          sy0 += part[npart + base + lane];
+          sz0 += part[2 * npart + base + lane];
+        }
+        if ((uint32_t)lane + 32u < rb.y) {
+          sx1 += part[base + lane + 32];
+          sy1 += part[npart + base + lane + 32];
+          sz1 += part[2 * npart + base + lane + 32];
+        }
       }
     }
     if (hi > lo) {
