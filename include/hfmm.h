@@ -114,8 +114,9 @@ typedef struct {
                           and the PM Green function 4 pi / k^2 minus the transform of the kernel.
                           Split 1 needs mac_mode 0, m2l_precision 0 and m2l_tables 0. */
   int p2p_mutual;      /* 1 = mutual P2P (Newton's third law): the walk keeps one of the two ordered
-                          leaf pairs (A, B, s) and (B, A, -s), the one with A < B (A = B: s at or
-                          below the unshifted index 13), the kernel evaluates each particle pair of
+                          leaf pairs (A, B, s) and (B, A, -s): the one whose sink A is the deeper
+                          leaf; at equal depth the one with A < B if A + B is odd, A > B if even
+                          (A = B: s at or below the unshifted index 13); the kernel evaluates each particle pair of
                           it once and adds the reaction on B's particles to per-entry partial sums,
                           which a second pass adds to B's accelerations in list order (the result
                           does not depend on scheduling).  A leaf against itself stays one-sided.

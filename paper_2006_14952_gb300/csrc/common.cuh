@@ -134,6 +134,17 @@ __device__ __forceinline__ uint64_t morton_key(double x, double y, double z, dou
   return (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
 }
 
+// Mutual P2P: which of the mirror pairs (a, b, s) and (b, a, 26 - s) evaluates
+// both directions.  The deeper (smaller) leaf owns, so that a large leaf beside
+// a dense region does not take all of that region's pairs on one warp; leaves
+// of one level alternate by the parity of a + b; a leaf against its own
+// periodic images keeps s <= 13 (13 = itself, evaluated one-sided).
+__host__ __device__ inline bool p2p_owner(uint32_t a, uint32_t b, uint32_t s, uint32_t lev_a, uint32_t lev_b) {
+  if (a == b) return s <= 13u;
+  if (lev_a != lev_b) return lev_a > lev_b;
+  return ((a ^ b) & 1u) ? a < b : a > b;
+}
+
 // ---------------------------------------------------------------- buffers
 struct DBuf {
   void *p = nullptr;

@@ -1,9 +1,9 @@
 // Mutual cut-off P2P (Newton's third law; p2p_mutual = 1): every particle pair
 // of a leaf pair is evaluated once and acts on both particles.
 //
-// The walk keeps one ordered pair (A, B, s) of each mirror couple (the one with
-// A < B; a leaf against its own periodic images keeps s <= 13), so each sink
-// leaf A's list holds the partners it owns.  Pass 1 (k_p2p_mut) runs one warp
+// The walk keeps one ordered pair (A, B, s) of each mirror couple (p2p_owner:
+// the deeper leaf, by parity within a level; a leaf against its own periodic
+// images keeps s <= 13), so each sink leaf A's list holds the partners it owns.  Pass 1 (k_p2p_mut) runs one warp
 // per sink leaf like the one-sided kernel: the sources of the leaf's list are
 // staged through shared memory in fills (asynchronous copies one fill ahead,
 // moved into A's frame, culled against the bounding box of the sink chunk,
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256, 2)
       const int src_lane = grp0 + ((lg + 1) & (Gs - 1));
       // the rotating sink (position in the leaf frame, mass) and the force it has gathered
       float4 si = lg < cs ? pm4[cbase + lg] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-      float ax = 0.f, ay = 0.f, az = 0.f;
+      float2 ax = f2(0.f), ay = f2(0.f), az = f2(0.f);  // packed halves, added at the end
       {
         const float4 xi = pm4[cbase + (lane < cs ? lane : 0)];
         float lo0 = xi.x, lo1 = xi.y, lo2 = xi.z, hi0 = xi.x, hi1 = xi.y, hi2 = xi.z;
@@ -325,9 +325,9 @@ __global__ void __launch_bounds__(256, 2)
                 g.y = in1 ? g.y : 0.f;
                 // on the sink: m_j f_(1) d = (-m_j) g d; on the sources: m_i g d
                 const float2 fa = __fmul2_rn(g, nmj[u]);
-                ax = fmaf(fa.x, dx.x, fmaf(fa.y, dx.y, ax));
-                ay = fmaf(fa.x, dy.x, fmaf(fa.y, dy.y, ay));
-                az = fmaf(fa.x, dz.x, fmaf(fa.y, dz.y, az));
+                ax = __ffma2_rn(fa, dx, ax);
+                ay = __ffma2_rn(fa, dy, ay);
+                az = __ffma2_rn(fa, dz, az);
                 const float2 fr = __fmul2_rn(g, smi);
                 Rx[u] = __ffma2_rn(fr, dx, Rx[u]);
                 Ry[u] = __ffma2_rn(fr, dy, Ry[u]);
@@ -339,9 +339,12 @@ __global__ void __launch_bounds__(256, 2)
             si.y = __shfl_sync(0xffffffffu, si.y, src_lane);
             si.z = __shfl_sync(0xffffffffu, si.z, src_lane);
             si.w = __shfl_sync(0xffffffffu, si.w, src_lane);
-            ax = __shfl_sync(0xffffffffu, ax, src_lane);
-            ay = __shfl_sync(0xffffffffu, ay, src_lane);
-            az = __shfl_sync(0xffffffffu, az, src_lane);
+            ax.x = __shfl_sync(0xffffffffu, ax.x, src_lane);
+            ax.y = __shfl_sync(0xffffffffu, ax.y, src_lane);
+            ay.x = __shfl_sync(0xffffffffu, ay.x, src_lane);
+            ay.y = __shfl_sync(0xffffffffu, ay.y, src_lane);
+            az.x = __shfl_sync(0xffffffffu, az.x, src_lane);
+            az.y = __shfl_sync(0xffffffffu, az.y, src_lane);
           }
 #pragma unroll
           for (int u = 0; u < kPL; ++u) {
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(256, 2)
         __syncwarp();  // the evaluation buffer and slots are rewritten by the next fill
       }
       // each group holds every sink's force from its source pairs: add the groups in order
-      buf[lane] = make_float4(ax, ay, az, 0.f);
+      buf[lane] = make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, 0.f);
       __syncwarp();
       if (lane < cs) {
         float sx = 0.f, sy = 0.f, sz = 0.f;

@@ -185,7 +185,7 @@ __device__ __forceinline__ Item mac_item(uint64_t e, bool valid, const uint4 *__
   }
   // mutual P2P: of the mirror pairs (a, b, s) and (b, a, 26 - s) the walk meets
   // both (it is symmetric under size_rule 1); keep one
-  if (m.mutual && c == kP2P && !(a < b || (a == b && s <= 13u))) c = kSkip;
+  if (m.mutual && c == kP2P && !p2p_owner(a, b, s, ca.w, cb.w)) c = kSkip;
   Item it;
   const uint32_t miss = (c == kM2L && table_miss(ca, cb, s, m.tab_k)) ? 1u : 0u;
   it.cls = (uint8_t)(c | (order << 3) | (miss << 7));

@@ -1,8 +1,9 @@
 """Mutual P2P (p2p_mutual = 1, Newton's third law) against the FP64 oracle.
 
 - The walk keeps exactly one ordered pair of each mirror couple: the GPU's P2P
-  list equals the oracle's list restricted to (A, B, s) with A < B, or A = B
-  and s <= 13 (bit-exact as sorted sets); the M2L list is unchanged.
+  list equals the oracle's list restricted to the owned pairs (the deeper sink
+  leaf; at equal depth A < B for odd A + B and A > B for even; A = B with
+  s <= 13), bit-exact as sorted sets; the M2L list is unchanged.
 - Forces on identical interaction pairs: the mutual evaluation against the
   oracle's one-sided FMM (the same particle pairs), within the FP32 tolerances
   of the one-sided path, for both splits, several leaf sizes and orders.
@@ -52,7 +53,12 @@ def test_mutual_walk_keeps_one_of_each_mirror_pair(leaf, theta):
     f = oracle_fmm(pos, mass, s)
     f.traverse()
     p2p, m2l = f.lists()
-    owned = (p2p[:, 0] < p2p[:, 1]) | ((p2p[:, 0] == p2p[:, 1]) & (p2p[:, 2] <= 13))
+    lev = f.nodes()[:, 0]
+    a, b, sh = p2p[:, 0], p2p[:, 1], p2p[:, 2]
+    same = lev[a] == lev[b]
+    odd = ((a ^ b) & 1) == 1
+    owned = np.where(a == b, sh <= 13,
+                     np.where(same, np.where(odd, a < b, a > b), lev[a] > lev[b]))
     assert 0.45 * len(p2p) < owned.sum() < 0.6 * len(p2p)
     np.testing.assert_array_equal(sorted_rows(s.export("p2p")), sorted_rows(p2p[owned]))
     np.testing.assert_array_equal(sorted_rows(s.export("m2l")), sorted_rows(m2l))
