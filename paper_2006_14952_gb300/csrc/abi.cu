@@ -199,7 +199,7 @@ void hfmm_destroy(hfmm_ctx *h) {
                   &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
                   &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p,
                   &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
-                  &c.mut_bounds, &c.mut_small, &c.mut_part};
+                  &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval};
   for (DBuf *b : bufs) release(*b);
   pm_release(c);
   if (c.gexec) cudaGraphExecDestroy(c.gexec);

@@ -288,6 +288,8 @@ struct Ctx {
   // mutual P2P: per entry partial counts and offsets, sort keys and entry indices
   // (ping-pong), per leaf bounds of its entries as a source, partial sums [3][slots]
   DBuf mut_cnt, mut_poff, mut_key, mut_key_alt, mut_val, mut_val_alt, mut_bounds, mut_small, mut_part;
+  DBuf mut_lkey, mut_lval;            // sink leaves sorted by descending work (keys, leaf ids; ping-pong)
+  const uint32_t *mut_order = nullptr;  // the sorted leaf ids (inside mut_lval)
   DBuf pm_gtab;          // polynomial split: long-range Green function per integer |k|^2
   size_t pm_gtab_n = 0;  // its length (0: not built)
   int pm_plan_r2c = -1, pm_plan_c2r = -1;

@@ -416,6 +416,22 @@ __global__ void k_mut_prep(const uint64_t *__restrict__ lst, int64_t ne, const u
   val[t] = (uint32_t)t;
 }
 
+// Work of each sink leaf (its sink chunks times the source particles on its
+// list) as a descending sort key, so the heaviest leaves are handed out first
+// and the last warps to finish hold light ones.
+__global__ void k_leaf_work(const uint32_t *__restrict__ leaves, int64_t nl, const uint2 *__restrict__ range,
+                            const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
+                            const uint64_t *__restrict__ lst, uint64_t *__restrict__ key, uint32_t *__restrict__ val) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const uint32_t a = leaves[t];
+  uint64_t w = 0;
+  for (uint32_t i = beg[a]; i < end[a]; ++i) w += range[pair_src(lst[i])].y;
+  w *= (range[a].y + 31u) / 32u;
+  key[t] = (w > 0xffffffffffull ? 0ull : 0xffffffffffull - w);  // 40-bit descending key
+  val[t] = a;
+}
+
 // Bounds of each source leaf's run in the sorted keys.
 __global__ void k_mut_bounds(const uint64_t *__restrict__ key, int64_t ne, uint32_t nnodes,
                              uint32_t *__restrict__ rbeg, uint32_t *__restrict__ rend) {
@@ -531,6 +547,22 @@ cudaError_t p2p_pass_mutual(Ctx &c, float *acc, cudaStream_t st) {
     TRY(cudaGetLastError());
   }
   TRY(ensure(c.mut_part, (size_t)(npart > 0 ? npart : 1) * 12));
+  // sink leaves in descending order of work (the sort reuses the pass-2 key buffers' alt copies)
+  const size_t nl1 = (size_t)c.nleaves;
+  TRY(ensure(c.mut_lkey, nl1 * 8 * 2));
+  TRY(ensure(c.mut_lval, nl1 * 4 * 2));
+  {
+    uint64_t *lk = P<uint64_t>(c.mut_lkey);
+    uint32_t *lv = P<uint32_t>(c.mut_lval);
+    k_leaf_work<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint2>(c.range),
+                                                        P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end),
+                                                        P<uint64_t>(c.p2p), lk, lv);
+    note_launch();
+    TRY(cudaGetLastError());
+    bool alt = false;
+    TRY(radix_sort_u64(lk, lv, lk + nl1, lv + nl1, nl1, 0, 40, &alt, c.tmp, st));
+    c.mut_order = alt ? lv + nl1 : lv;
+  }
   int dev = 0, nsm = 0;
   TRY(cudaGetDevice(&dev));
   TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -545,7 +577,7 @@ cudaError_t p2p_pass_mutual(Ctx &c, float *acc, cudaStream_t st) {
   const size_t dyn = (size_t)2 * 8 * kCapM * sizeof(float4);
   TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   TRY(cudaMemsetAsync(ctr, 0, 8, st));
-  kern<<<g, T, dyn, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range),
+  kern<<<g, T, dyn, st>>>(c.mut_order, c.nleaves, P<uint4>(c.cell), P<uint2>(c.range),
                           P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<uint32_t>(c.mut_poff),
                           P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, (float)c.prm.box, fit2, (float)c.prm.G, acc,
                           P<float>(c.mut_part), npart, ctr);
