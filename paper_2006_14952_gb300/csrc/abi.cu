@@ -38,9 +38,9 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.mac_mode != 0 && p.mac_mode != 1) return why = "mac_mode must be 0 (geometric) or 1 (learned)", false;
   if (p.transition_rule != 0 && p.transition_rule != 1) return why = "transition_rule must be 0 or 1", false;
   if (p.size_rule != 0 && p.size_rule != 1) return why = "size_rule must be 0 or 1", false;
-  if (p.m2l_precision < 0 || p.m2l_precision > 2) return why = "m2l_precision must be 0, 1 or 2", false;
+  if (p.m2l_precision < 0 || p.m2l_precision > 4) return why = "m2l_precision must be 0..4", false;
   if (p.m2l_precision != 0 && !m2l_tc_supported(p.order))
-    return why = "m2l_precision 1 and 2 (3xTF32 / BF16x3 tensor cores) support orders 1..6", false;
+    return why = "m2l_precision 1..4 (3xTF32 / BF16x3 tensor cores) support orders 1..6", false;
   if (p.profile < 0 || p.profile > 3) return why = "profile must be 0..3", false;
   if (p.m2l_tables != 0 && p.m2l_tables != 1) return why = "m2l_tables must be 0 or 1", false;
   if (p.tile_p2p_stage != 0 && p.tile_p2p_stage != 128 && p.tile_p2p_stage != 256)
@@ -199,7 +199,8 @@ void hfmm_destroy(hfmm_ctx *h) {
                   &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
                   &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p,
                   &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
-                  &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval};
+                  &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval, &c.lo_flag,
+                  &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr};
   for (DBuf *b : bufs) release(*b);
   pm_release(c);
   if (c.gexec) cudaGraphExecDestroy(c.gexec);

@@ -290,6 +290,9 @@ struct Ctx {
   DBuf mut_cnt, mut_poff, mut_key, mut_key_alt, mut_val, mut_val_alt, mut_bounds, mut_small, mut_part;
   DBuf mut_lkey, mut_lval;            // sink leaves sorted by descending work (keys, leaf ids; ping-pong)
   const uint32_t *mut_order = nullptr;  // the sorted leaf ids (inside mut_lval)
+  // (level, offset) tensor-core M2L: node flags and ranks, tile meta, tile sinks,
+  // tile pair counts and offsets, grouped pairs
+  DBuf lo_flag, lo_rank, lo_meta, lo_sink, lo_tcnt, lo_toff, lo_scr;
   DBuf pm_gtab;          // polynomial split: long-range Green function per integer |k|^2
   size_t pm_gtab_n = 0;  // its length (0: not built)
   int pm_plan_r2c = -1, pm_plan_c2r = -1;
@@ -343,6 +346,10 @@ cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t
 cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st);
 // Cut-off P2P, added to the accelerations written by downward().
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st);
+// M2L of order q with m2l_precision 3 / 4: table pairs as (level, offset) tensor-core contractions
+// with the accumulators in tensor memory, the other pairs on the FP32 per-pair kernel.
+bool m2l_lo_supported(int p);
+cudaError_t m2l_pass_lo(Ctx &c, int q, cudaStream_t st);
 // Mutual P2P (p2p_mutual = 1): one evaluation per particle pair, reactions through per-entry partials.
 cudaError_t p2p_pass_mutual(Ctx &c, float *acc, cudaStream_t st);
 

@@ -807,7 +807,7 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   m.mode = c.collect ? 2 : c.count_walk ? 0 : c.prm.mac_mode;
   m.conv = c.count_walk == 2 ? 1 : 0;
   m.order = c.p;
-  m.tab_k = (c.prm.m2l_precision == 0 && c.prm.m2l_tables) ? c.tab_k : 0;
+  m.tab_k = ((c.prm.m2l_precision == 0 && c.prm.m2l_tables) || c.prm.m2l_precision >= 3) ? c.tab_k : 0;
   m.mutual = (c.prm.p2p_mutual && !c.collect && !c.count_walk) ? 1 : 0;
   m.w = static_cast<const __nv_bfloat16 *>(c.mlp_w.p);
   m.M = P<float>(c.M);
@@ -1079,7 +1079,7 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   while (((int64_t)1 << sink_bits) < nn) ++sink_bits;
   TRY(merge_runs(c, c.p2p, c.p2p_alt, c.np2p, c.rp_key, c.rp_beg, c.rp_cnt, c.nrun_p, c.rp_rank, c.rcnt_p,
                  P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), nullptr, st));
-  const bool tables = c.prm.m2l_precision == 0 && c.prm.m2l_tables && c.tab_k > 0;
+  const bool tables = ((c.prm.m2l_precision == 0 && c.prm.m2l_tables) || c.prm.m2l_precision >= 3) && c.tab_k > 0;
   if (c.nm2l > 0 && !tables) {
     TRY(merge_runs(c, c.m2l, c.m2l_alt, c.nm2l, c.rm_key, c.rm_beg, c.rm_cnt, c.nrun_m, c.rm_rank, c.rcnt_m,
                    P<uint32_t>(c.m2l_beg), P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid), st));
@@ -1130,12 +1130,15 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
 
 cudaError_t m2l_all(Ctx &c, cudaStream_t st) {
   if (c.nm2l == 0) return cudaSuccess;
-  const bool tab = c.prm.m2l_precision == 0 && c.prm.m2l_tables && c.tab_k > 0;
+  const bool lo = c.prm.m2l_precision >= 3 && c.tab_k > 0;
+  const bool tab = (c.prm.m2l_precision == 0 && c.prm.m2l_tables && c.tab_k > 0) || lo;
   if (tab && !c.tab_ready) {
     cudaError_t e = m2l_table_build(c, st);
     if (e != cudaSuccess) return e;
   }
   auto run = [&](int q) -> cudaError_t {
+    if (lo && m2l_lo_supported(q)) return m2l_pass_lo(c, q, st);
+    if (c.prm.m2l_precision >= 3) return m2l_pass(c, q, st);  // no table: every pair on the FP32 kernel
     if (c.prm.m2l_precision != 0 && m2l_tc_supported(q)) return m2l_pass_tc(c, q, st);
     if (tab) {
       cudaError_t e = m2l_pass_table(c, q, st);
