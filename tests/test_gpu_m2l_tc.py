@@ -92,11 +92,11 @@ def test_bf16x3_locals_are_a_distinct_split_within_bound():
 def test_tensor_core_m2l_rejects_unsupported_order():
     from paper_2006_14952_gb300 import hfmm
 
-    for prec in (1, 2):
+    for prec in (1, 2, 3, 4):
         with pytest.raises(hfmm.HfmmError, match="orders 1..6"):
             hfmm.Solver(order=7, m2l_precision=prec)
     with pytest.raises(hfmm.HfmmError, match="m2l_precision"):
-        hfmm.Solver(m2l_precision=3)
+        hfmm.Solver(m2l_precision=5)
 
 
 @pytest.mark.parametrize("precision", [1, 2])
