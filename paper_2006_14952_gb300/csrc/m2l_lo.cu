@@ -8,8 +8,9 @@
 // (Eq. m2l with the truncated derivative tensors of Sec. 2.2):
 //   L~_n(A) += sum_m T_{n+m}(l, o) M~_m(B),   |n| + |m| <= p,
 // T the per-(level, offset) table of m2l_table.cu.  A CTA owns a tile of 128
-// sinks of one level (consecutive in node order) and keeps their 128 x NC
-// local coefficients as the accumulator D in tensor memory.  It groups its
+// sinks of one level (consecutive in node order); each offset's contribution
+// to their 128 x NC local coefficients is formed in tensor memory and added
+// to FP32 accumulators in registers (a thread per sink).  It groups its
 // sinks' table pairs by offset (a counting sort in shared memory) and, offset
 // by offset, forms
 //   A = the sources' multipoles in the rows of the sinks that have a pair with
@@ -21,8 +22,8 @@
 // taken in blocks of 16, and block j only runs the K-steps up to the largest
 // ncoef(p - |n|) of its columns, so the MMA covers 2432 operator entries at
 // p = 6 for the 924 the contraction uses (of 84 x 84).  Nothing is summed
-// across CTAs: after the last offset the accumulator is added to the sinks'
-// locals, so the result is deterministic.  Pairs outside the table
+// across CTAs: after the last offset the accumulators are added to the
+// sinks' locals, so the result is deterministic.  Pairs outside the table
 // (mixed levels, offsets beyond the table's extent) go to the FP32 per-pair
 // kernel.  Waits are bounded; on a timeout the kernel records an error,
 // waits (with the full limit) for the MMAs it issued, frees its tensor memory
@@ -267,7 +268,14 @@ __global__ void __launch_bounds__(kLoThreads, 1)
   __syncthreads();
   // cursor[bin] now holds each bin's end; its start is end - hist
 
-  // ---- one contraction per offset, accumulated in tensor memory
+  // ---- one contraction per offset in tensor memory, added to FP32 registers
+  // (one row per thread) after each offset: a long chain of MMAs accumulating
+  // into one tensor-memory element loses precision with its length (measured:
+  // 4.6e-5 relative on the locals when all offsets of a tile accumulate in
+  // place, against 4.7e-6 for chains of the per-sink kernel's length)
+  float racc[NCP];
+#pragma unroll
+  for (int i = 0; i < NCP; ++i) racc[i] = 0.f;
   const int64_t lrow = (int64_t)c0.w * nbins;
   uint32_t phase = 0;
   const int ngroups = (int)nz_n;
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(kLoThreads, 1)
           const uint64_t ah = desc_sw128(a_hs + aoff), al = desc_sw128(a_ls + aoff);
           const uint64_t bh = desc_sw128(b_hs + boff), bl = desc_sw128(b_ls + boff);
           const uint32_t d = tmem + (uint32_t)(16 * j);
-          const uint32_t acc0 = (g > 0 || s > 0) ? 1u : 0u;
+          const uint32_t acc0 = s > 0 ? 1u : 0u;  // each offset starts its accumulator afresh
           if constexpr (kBF) {
             mma_bf16(d, ah, bh, IDESC, acc0);
             mma_bf16(d, ah, bl, IDESC, 1u);
@@ -332,6 +340,14 @@ __global__ void __launch_bounds__(kLoThreads, 1)
     __syncthreads();
     if (abort_flag) break;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int col = 0; col < NCP; col += 8) {
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) racc[col + i] += v[i];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     // the rows written for this offset back to zero (the MMAs that read them are done)
     for (uint32_t i = tid; i < gcnt * Q4; i += kLoThreads) {
       const int row = (int)(scr[gbeg + i / Q4] >> 32), q = (int)(i % Q4);
@@ -342,17 +358,11 @@ __global__ void __launch_bounds__(kLoThreads, 1)
     __syncthreads();
   }
   if (!abort_flag && ngroups > 0) {
-    // TMEM lane 32 warp + lane holds row (sink) 32 warp + lane: add its coefficients to the locals
+    // thread 32 warp + lane holds row (sink) 32 warp + lane: add its coefficients to the locals
     const uint32_t k = s_sink[warp * 32 + lane];
+    if (k != kNoSink) {
 #pragma unroll
-    for (int col = 0; col < NCP; col += 8) {
-      float v[8];
-      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
-      if (k != kNoSink) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (col + i < NC) L[(size_t)k * ldm + col + i] += v[i];
-      }
+      for (int i = 0; i < NC; ++i) L[(size_t)k * ldm + i] += racc[i];
     }
   }
   // the MMAs of an abandoned offset may still be running: wait for them with the
