@@ -93,11 +93,15 @@ typedef struct {
                           persistent and at most 2 of them are resident per SM) */
   int tile_m2l_blocks; /* cap on M2L blocks of 128 threads, per SM, 1..64 (default 64) */
   int tile_trav_blocks;/* traversal blocks of 256 threads per SM, 1..4 (default 4; capped by occupancy) */
-  int use_graph;       /* 1 = after the traversal (the last point where the host reads sizes back),
-                          list grouping, M2L, L2L/L2P and P2P are captured as one CUDA graph on a
-                          library stream and launched on the caller's stream; the executable graph
-                          is updated in place while the launch sequence keeps its shape, else
-                          re-instantiated.  Geometric acceptance, m2l_precision 0, profile bit 1
+  int use_graph;       /* 1 = hfmm_short_range_forces runs as one CUDA graph (captured on a library
+                          stream, launched on the caller's): upward pass, the walk, list grouping,
+                          M2L, L2L/L2P and P2P, with no host read-back inside; the lists take their
+                          capacities from the last call (or the first guess), their sizes stay on
+                          the device, and one read-back after the graph checks them: if a list
+                          overflowed, the call runs again directly (growing the lists), so the
+                          result is the same.  The executable graph is updated in place while the
+                          launch sequence keeps its shape, else re-instantiated.  Geometric
+                          acceptance, m2l_precision 0, m2l_tables 0, p2p_mutual 0, profile bit 1
                           off; otherwise ignored. */
   int tc_wait_polls;   /* m2l_precision 1 and 2: polls of the bounded wait for each chunk's MMAs before the
                           call gives up with HFMM_ERR_TIMEOUT (0 = 2^22; -1 = no poll at all, so that
@@ -138,8 +142,8 @@ typedef struct {
   int64_t p2p_useful_pairs;   /* pairs with 0 < r < R_c (profile bit 1, else -1) */
   int64_t launches;           /* kernels launched by this library in this process so far */
   /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P.
-     After a call in graph mode t_lists covers the whole graph (lists, M2L, L2L/L2P, P2P)
-     and t_m2l, t_l2l, t_p2p are -1. */
+     After a call in graph mode t_upward covers the whole graph (upward pass to P2P) and
+     t_traverse, t_lists, t_m2l, t_l2l, t_p2p are -1. */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
   int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
   int64_t frontier_pairs;     /* cell pairs the traversal classified, over all levels */

@@ -233,27 +233,41 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
 
 namespace {
 
-// List grouping, M2L, L2L/L2P and P2P (no host round trip once the traversal
-// has fixed the sizes) captured on the context's own stream and replayed on
-// `st` as one graph.  With profiling the graph is timed as a whole.
-cudaError_t post_traversal_graph(Ctx &c, float *acc, cudaStream_t st, bool prof) {
+// The whole short-range call captured as one CUDA graph on the context's own
+// stream and replayed on `st`: upward pass, the walk (its list sizes stay on
+// the device: the lists have their capacities from the last call or the first
+// guess), list grouping (run counts read on the device), M2L, L2L/L2P and P2P.
+// Every buffer is sized before the capture.  After the graph, one read-back
+// of the walk's state: *ok is false when a list overflowed (the caller then
+// runs the direct path, which grows the lists).  With profiling the graph is
+// timed as a whole.
+cudaError_t whole_call_graph(Ctx &c, float *acc, cudaStream_t st, bool prof, bool *ok) {
   cudaError_t e;
+  *ok = false;
   if (!c.gstream && (e = cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking)) != cudaSuccess) return e;
-  if (!c.gready && (e = cudaEventCreateWithFlags(&c.gready, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = traverse_graph_prepare(c)) != cudaSuccess) return e;
+  if ((e = sort_lists_prepare(c)) != cudaSuccess) return e;
+  // during the capture the list sizes are their capacities on the host
+  c.nm2l = (int64_t)c.cap_m2l;
+  c.np2p = (int64_t)c.cap_p2p;
+  c.graph_walk = true;
   std::vector<void *> deferred;
   g_deferred_free = &deferred;
   cudaGraph_t graph = nullptr;
   e = cudaStreamBeginCapture(c.gstream, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    cudaError_t r = sort_lists(c, c.gstream);
+    cudaError_t r = upward(c, c.gstream);
+    if (r == cudaSuccess) r = traverse_graph_launch(c, c.gstream);
+    if (r == cudaSuccess) r = sort_lists(c, c.gstream);
     if (r == cudaSuccess) r = m2l_all(c, c.gstream);
     if (r == cudaSuccess) r = downward(c, acc, c.gstream);
     if (r == cudaSuccess) r = p2p_pass(c, acc, c.gstream);
     e = cudaStreamEndCapture(c.gstream, &graph);
     if (r != cudaSuccess) e = r;
   }
+  c.graph_walk = false;
   g_deferred_free = nullptr;
-  for (void *p : deferred) cudaFree(p);  // allocations replaced during the capture
+  for (void *p : deferred) cudaFree(p);  // allocations replaced during the capture (none expected)
   if (e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return e;
@@ -278,12 +292,13 @@ cudaError_t post_traversal_graph(Ctx &c, float *acc, cudaStream_t st, bool prof)
     ++c.graph_instantiations;
   }
   cudaGraphDestroy(graph);
-  if (prof) cudaEventRecord(c.ev[6], st);
+  if (prof) cudaEventRecord(c.ev[3], st);
   e = cudaGraphLaunch(c.gexec, st);
   note_launch();
   if (prof) cudaEventRecord(c.ev[9], st);
+  if (e != cudaSuccess) return e;
   c.last_graph = true;
-  return e;
+  return traverse_graph_finish(c, st, ok);
 }
 
 }  // namespace
@@ -308,6 +323,21 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   bool prof = (c.prm.profile & 1) != 0;
   if ((c.prm.profile & 2) && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "memset counter");
+  c.last_graph = false;
+  if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
+      !c.prm.p2p_mutual && !c.prm.m2l_tables) {
+    bool ok = false;
+    e = whole_call_graph(c, acc, st, prof, &ok);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph");
+    if (ok) {
+      if (c.nm2l > (int64_t)UINT32_MAX || c.np2p > (int64_t)UINT32_MAX)
+        return fail(c, HFMM_ERR_CAPACITY, "an interaction list above 2^32 - 1 entries");
+      return HFMM_OK;
+    }
+    // a list overflowed inside the graph: start again directly (the walk grows the lists)
+    c.last_graph = false;
+    if ((e = cudaMemsetAsync(c.L.p, 0, eb, st)) != cudaSuccess) return cuda_fail(c, e, "memset L");
+  }
   if (prof) cudaEventRecord(c.ev[3], st);
   if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
   if (prof) cudaEventRecord(c.ev[4], st);
@@ -318,13 +348,6 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if (c.nm2l > (int64_t)UINT32_MAX || c.np2p > (int64_t)UINT32_MAX)
     return fail(c, HFMM_ERR_CAPACITY, "an interaction list above 2^32 - 1 entries");
   if (prof) cudaEventRecord(c.ev[5], st);
-  c.last_graph = false;
-  if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
-      !c.prm.p2p_mutual) {
-    e = post_traversal_graph(c, acc, st, prof);
-    if (e != cudaSuccess) return cuda_fail(c, e, "graph");
-    return HFMM_OK;
-  }
   if ((e = sort_lists(c, st)) != cudaSuccess) return cuda_fail(c, e, "sort_lists");
   if (prof) cudaEventRecord(c.ev[6], st);
   if (c.prm.m2l_precision != 0 &&
@@ -457,7 +480,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   float *t[] = {&o->t_keys_sort, &o->t_tree, &o->t_upward, &o->t_traverse, &o->t_lists, &o->t_m2l, &o->t_l2l,
                 &o->t_p2p};
   const int ev_pairs[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};
-  const int ev_graph[][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {6, 9}, {-1, -1}, {-1, -1}, {-1, -1}};
+  const int ev_graph[][2] = {{0, 1}, {1, 2}, {3, 9}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
   for (int i = 0; i < 8; ++i) {
     *t[i] = -1.f;
     if (c.last_graph && ev_graph[i][0] >= 0 && (c.prm.profile & 1) && c.n > 0) {

@@ -303,7 +303,8 @@ struct Ctx {
   cudaEvent_t gready = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_updates = 0, graph_instantiations = 0;
-  bool last_graph = false;  // the last short_range_forces ran its post-traversal part as a graph
+  bool last_graph = false;  // the last short_range_forces ran as one graph
+  bool graph_walk = false;  // while capturing: list sizes live on the device (capacities on the host)
 
   // stats
   int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1, nm2l_table = -1;
@@ -346,6 +347,14 @@ cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t
 cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st);
 // Cut-off P2P, added to the accelerations written by downward().
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st);
+// Graph mode: the walk without its host read-back (sizes every buffer first; the
+// read-back after the graph reports whether the lists fit), and the device
+// address of the walk's run counts (0 M2L, 1 P2P).
+cudaError_t traverse_graph_prepare(Ctx &c);
+cudaError_t traverse_graph_launch(Ctx &c, cudaStream_t st);
+cudaError_t traverse_graph_finish(Ctx &c, cudaStream_t st, bool *ok);
+const unsigned long long *walk_run_counts(Ctx &c, int which);
+cudaError_t sort_lists_prepare(Ctx &c);
 // M2L of order q with m2l_precision 3 / 4: table pairs as (level, offset) tensor-core contractions
 // with the accumulators in tensor memory, the other pairs on the FP32 per-pair kernel.
 bool m2l_lo_supported(int p);

@@ -789,17 +789,18 @@ __global__ void k_count_table(const uint64_t *__restrict__ lst, int64_t n, unsig
 
 }  // namespace
 
-cudaError_t traverse(Ctx &c, cudaStream_t st) {
+namespace {
+
+// The walk's parameters and grid, and the first guesses of its list capacities.
+struct WalkPlan {
+  Mac m;
+  unsigned nb;
+};
+
+cudaError_t walk_plan(Ctx &c, WalkPlan &w) {
   cudaError_t e;
-#define TRY(x)                      \
-  do {                              \
-    e = (x);                        \
-    if (e != cudaSuccess) return e; \
-  } while (0)
-  c.nm2l = c.np2p = 0;
-  c.traverse_iters = 0;
-  if (c.n == 0) return cudaSuccess;
-  Mac m{};
+  Mac &m = w.m;
+  m = Mac{};
   m.rc2i = c.rc2i;
   for (int l = 0; l <= kDepth; ++l) m.acc_thr[l] = c.acc_thr[l];
   m.rule = c.prm.transition_rule;
@@ -821,24 +822,22 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   m.sample_mod = c.sample_mod ? c.sample_mod : 1u;
 
   int dev = 0, nsm = 0, per_sm = 0;
-  TRY(cudaGetDevice(&dev));
-  TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const bool net = m.mode == 1;
-  const void *kern = net ? (const void *)k_traverse<true> : (const void *)k_traverse<false>;
-  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, net ? k_traverse<true> : k_traverse<false>, kTT, 0));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, net ? k_traverse<true> : k_traverse<false>, kTT, 0);
+  if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int want = c.prm.tile_trav_blocks > 0 ? c.prm.tile_trav_blocks : 4;
-  const unsigned nb = (unsigned)(nsm * (per_sm < want ? per_sm : want));
-  TRY(ensure(c.btot2, (size_t)nb * 4 * sizeof(unsigned long long)));
-  // capacities: the last call's sizes with head-room, at least a few per node
-  auto grow = [](uint64_t want) { return want + want / 4 + 1024; };
+  w.nb = (unsigned)(nsm * (per_sm < want ? per_sm : want));
+  // capacities: the last call's sizes with head-room, at least a few per node.
   // First guesses from the 2M clustered set: at leaves of 16, about 60 frontier
   // pairs per particle at the largest level, 50 M2L and 115 P2P entries per
   // particle in total; these fall about as (16 / leaf_max)^1.5 (8 M2L and 21 P2P
   // per particle at 48), so the guesses are scaled so, with a margin of 1.5.
   // A list that overflows is grown alone (to what the walk needed so far, at least
-  // twice its size) and the walk is repeated.
-  // A positive list_init replaces every first guess (a test knob for the retry path).
+  // twice its size) and the walk is repeated.  A positive list_init replaces every
+  // first guess (a test knob for the retry path).
   const double lf = c.prm.leaf_max > 16 ? std::pow(16.0 / c.prm.leaf_max, 1.5) * 1.5 : 1.0;
   const double sc = lf < 1.0 ? lf : 1.0;
   const uint64_t init = (uint64_t)c.prm.list_init;
@@ -853,92 +852,141 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
   if (c.cap_p2p < g_p2p) c.cap_p2p = g_p2p;
   if (c.cap_seg < g_seg) c.cap_seg = g_seg;
   if (c.cap_run < g_run) c.cap_run = g_run;
-  // the state sits after the eight counters of the 256-byte d_small and is read back into h_pinned (256 bytes)
+  return cudaSuccess;
+}
+
+cudaError_t walk_buffers(Ctx &c, unsigned nb) {
+  cudaError_t e;
+#define TRY(x)                      \
+  do {                              \
+    e = (x);                        \
+    if (e != cudaSuccess) return e; \
+  } while (0)
+  TRY(ensure(c.btot2, (size_t)nb * 4 * sizeof(unsigned long long)));
+  TRY(ensure(c.front, c.cap_front * 8));
+  TRY(ensure(c.front_next, c.cap_front * 8));
+  TRY(ensure(c.fseg, c.nnodes * 4 + 64));
+  TRY(ensure(c.fseg_next, c.nnodes * 4 + 64));
+  TRY(ensure(c.cls, c.cap_front * 2));  // class and child count per frontier pair
+  TRY(ensure(c.seg_a, c.cap_seg * 4));
+  TRY(ensure(c.seg_b, c.cap_seg * 4));
+  TRY(ensure(c.acc_a, c.cap_seg * 8));  // segment starts (ping-pong)
+  TRY(ensure(c.acc_b, c.cap_seg * 8));
+  TRY(ensure(c.segpre, c.cap_seg * 24));
+  TRY(ensure(c.segbase, c.cap_seg * sizeof(SegBase)));
+  TRY(ensure(c.ctot, ((c.cap_front + 31) / 32) * 24 + 64));
+  TRY(ensure(c.m2l, c.cap_m2l * 8));
+  TRY(ensure(c.p2p, c.cap_p2p * 8));
+  TRY(ensure(c.rm_key, c.cap_run * 8));
+  TRY(ensure(c.rm_beg, c.cap_run * 8));
+  TRY(ensure(c.rm_cnt, c.cap_run * 4));
+  TRY(ensure(c.rp_key, c.cap_run * 8));
+  TRY(ensure(c.rp_beg, c.cap_run * 8));
+  TRY(ensure(c.rp_cnt, c.cap_run * 4));
+  TRY(ensure(c.rm_rank, c.cap_run * 4));
+  TRY(ensure(c.rp_rank, c.cap_run * 4));
+  TRY(ensure(c.rcnt_m, (size_t)c.nnodes * 4 + 64));
+  TRY(ensure(c.rcnt_p, (size_t)c.nnodes * 4 + 64));
+  return cudaSuccess;
+#undef TRY
+}
+
+// the walk's state sits after the eight counters of the 256-byte d_small and is read back into h_pinned
+TravState *walk_state(Ctx &c) {
   static_assert(8 * sizeof(uint64_t) + sizeof(TravState) <= 256, "TravState must fit in d_small");
-  TravState *dst = reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
+  return reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
+}
+
+// Zero the counters and launch the cooperative walk (no allocation, no read-back).
+cudaError_t walk_launch(Ctx &c, const WalkPlan &w, cudaStream_t st) {
+  cudaError_t e;
+  TravState *dst = walk_state(c);
+  if ((e = cudaMemsetAsync(c.rcnt_m.p, 0, (size_t)c.nnodes * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c.rcnt_p.p, 0, (size_t)c.nnodes * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(dst, 0, sizeof(TravState), st)) != cudaSuccess) return e;
+  TravBufs B;
+  B.fa = P<uint64_t>(c.front);
+  B.fb = P<uint64_t>(c.front_next);
+  B.map_a = P<uint32_t>(c.fseg);
+  B.map_b = P<uint32_t>(c.fseg_next);
+  B.cls = P<uint8_t>(c.cls);
+  B.cc = P<uint8_t>(c.cls) + c.cap_front;
+  B.seg_a = P<uint32_t>(c.seg_a);
+  B.seg_b = P<uint32_t>(c.seg_b);
+  B.st_a = P<unsigned long long>(c.acc_a);
+  B.st_b = P<unsigned long long>(c.acc_b);
+  B.spre = P<unsigned long long>(c.segpre);
+  B.base = P<SegBase>(c.segbase);
+  B.ctot = P<unsigned long long>(c.ctot);
+  B.m2l = P<uint64_t>(c.m2l);
+  B.p2p = P<uint64_t>(c.p2p);
+  B.rm_key = P<uint64_t>(c.rm_key);
+  B.rp_key = P<uint64_t>(c.rp_key);
+  B.rm_beg = P<uint64_t>(c.rm_beg);
+  B.rp_beg = P<uint64_t>(c.rp_beg);
+  B.rm_cnt = P<uint32_t>(c.rm_cnt);
+  B.rp_cnt = P<uint32_t>(c.rp_cnt);
+  B.rm_rank = P<uint32_t>(c.rm_rank);
+  B.rp_rank = P<uint32_t>(c.rp_rank);
+  B.rcnt_m = P<uint32_t>(c.rcnt_m);
+  B.rcnt_p = P<uint32_t>(c.rcnt_p);
+  B.btot = P<unsigned long long>(c.btot2);
+  B.capF = c.cap_front;
+  B.capS = c.cap_seg;
+  B.capM = c.cap_m2l;
+  B.capP = c.cap_p2p;
+  B.capR = c.cap_run;
+  int max_iters = 2 * kDepth + 6;
+  Mac m = w.m;
+  const bool net = m.mode == 1;
+  const void *kern = net ? (const void *)k_traverse<true> : (const void *)k_traverse<false>;
+  void *args[] = {(void *)&c.cell.p, (void *)&c.kids.p, (void *)&m, (void *)&B, (void *)&dst, (void *)&max_iters};
+  e = cudaLaunchCooperativeKernel(kern, dim3(w.nb), dim3(kTT), args, 0, st);
+  note_launch();
+  return e;
+}
+
+// Interpret the read-back state: 0 done, 1 a list overflowed (grow and repeat),
+// -1 the walk cannot complete (more levels than any octree, or a bad opening).
+int walk_result(Ctx &c, const TravState &hs) {
+  if (hs.overflow == 2) return -1;  // a non-leaf sink was asked to open its partner
+  if (hs.overflow) return 1;
+  if (hs.nf != 0) return -1;  // more levels than any octree can have
+  c.nm2l = (int64_t)hs.nm2l;
+  c.np2p = (int64_t)hs.np2p;
+  c.traverse_iters = hs.iters;
+  c.frontier_items = (int64_t)hs.items;
+  c.nrun_m = (int64_t)hs.nrun_m;
+  c.nrun_p = (int64_t)hs.nrun_p;
+  return 0;
+}
+
+}  // namespace
+
+cudaError_t traverse(Ctx &c, cudaStream_t st) {
+  cudaError_t e;
+  c.nm2l = c.np2p = 0;
+  c.traverse_iters = 0;
+  if (c.n == 0) return cudaSuccess;
+  WalkPlan w;
+  if ((e = walk_plan(c, w)) != cudaSuccess) return e;
   c.traverse_walks = 0;
   for (int attempt = 0; attempt < 32; ++attempt) {
     ++c.traverse_walks;
-    TRY(ensure(c.front, c.cap_front * 8));
-    TRY(ensure(c.front_next, c.cap_front * 8));
-    TRY(ensure(c.fseg, c.nnodes * 4 + 64));
-    TRY(ensure(c.fseg_next, c.nnodes * 4 + 64));
-    TRY(ensure(c.cls, c.cap_front * 2));  // class and child count per frontier pair
-    TRY(ensure(c.seg_a, c.cap_seg * 4));
-    TRY(ensure(c.seg_b, c.cap_seg * 4));
-    TRY(ensure(c.acc_a, c.cap_seg * 8));  // segment starts (ping-pong)
-    TRY(ensure(c.acc_b, c.cap_seg * 8));
-    TRY(ensure(c.segpre, c.cap_seg * 24));
-    TRY(ensure(c.segbase, c.cap_seg * sizeof(SegBase)));
-    TRY(ensure(c.ctot, ((c.cap_front + 31) / 32) * 24 + 64));
-    TRY(ensure(c.m2l, c.cap_m2l * 8));
-    TRY(ensure(c.p2p, c.cap_p2p * 8));
-    TRY(ensure(c.rm_key, c.cap_run * 8));
-    TRY(ensure(c.rm_beg, c.cap_run * 8));
-    TRY(ensure(c.rm_cnt, c.cap_run * 4));
-    TRY(ensure(c.rp_key, c.cap_run * 8));
-    TRY(ensure(c.rp_beg, c.cap_run * 8));
-    TRY(ensure(c.rp_cnt, c.cap_run * 4));
-    TRY(ensure(c.rm_rank, c.cap_run * 4));
-    TRY(ensure(c.rp_rank, c.cap_run * 4));
-    TRY(ensure(c.rcnt_m, (size_t)c.nnodes * 4 + 64));
-    TRY(ensure(c.rcnt_p, (size_t)c.nnodes * 4 + 64));
-    TRY(cudaMemsetAsync(c.rcnt_m.p, 0, (size_t)c.nnodes * 4, st));
-    TRY(cudaMemsetAsync(c.rcnt_p.p, 0, (size_t)c.nnodes * 4, st));
-    TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), st));
-    TravBufs B;
-    B.fa = P<uint64_t>(c.front);
-    B.fb = P<uint64_t>(c.front_next);
-    B.map_a = P<uint32_t>(c.fseg);
-    B.map_b = P<uint32_t>(c.fseg_next);
-    B.cls = P<uint8_t>(c.cls);
-    B.cc = P<uint8_t>(c.cls) + c.cap_front;
-    B.seg_a = P<uint32_t>(c.seg_a);
-    B.seg_b = P<uint32_t>(c.seg_b);
-    B.st_a = P<unsigned long long>(c.acc_a);
-    B.st_b = P<unsigned long long>(c.acc_b);
-    B.spre = P<unsigned long long>(c.segpre);
-    B.base = P<SegBase>(c.segbase);
-    B.ctot = P<unsigned long long>(c.ctot);
-    B.m2l = P<uint64_t>(c.m2l);
-    B.p2p = P<uint64_t>(c.p2p);
-    B.rm_key = P<uint64_t>(c.rm_key);
-    B.rp_key = P<uint64_t>(c.rp_key);
-    B.rm_beg = P<uint64_t>(c.rm_beg);
-    B.rp_beg = P<uint64_t>(c.rp_beg);
-    B.rm_cnt = P<uint32_t>(c.rm_cnt);
-    B.rp_cnt = P<uint32_t>(c.rp_cnt);
-    B.rm_rank = P<uint32_t>(c.rm_rank);
-    B.rp_rank = P<uint32_t>(c.rp_rank);
-    B.rcnt_m = P<uint32_t>(c.rcnt_m);
-    B.rcnt_p = P<uint32_t>(c.rcnt_p);
-    B.btot = P<unsigned long long>(c.btot2);
-    B.capF = c.cap_front;
-    B.capS = c.cap_seg;
-    B.capM = c.cap_m2l;
-    B.capP = c.cap_p2p;
-    B.capR = c.cap_run;
-    int max_iters = 2 * kDepth + 6;
-    void *args[] = {(void *)&c.cell.p, (void *)&c.kids.p, (void *)&m, (void *)&B, (void *)&dst, (void *)&max_iters};
-    TRY(cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kTT), args, 0, st));
-    note_launch();
+    if ((e = walk_buffers(c, w.nb)) != cudaSuccess) return e;
+    if ((e = walk_launch(c, w, st)) != cudaSuccess) return e;
     TravState hs;
-    TRY(cudaMemcpyAsync(c.h_pinned, dst, sizeof(TravState), cudaMemcpyDeviceToHost, st));
-    TRY(cudaStreamSynchronize(st));
+    if ((e = cudaMemcpyAsync(c.h_pinned, walk_state(c), sizeof(TravState), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     std::memcpy(&hs, c.h_pinned, sizeof(TravState));
-    if (hs.overflow == 2) return cudaErrorInvalidValue;  // a non-leaf sink was asked to open its partner
-    if (!hs.overflow) {
-      if (hs.nf != 0) return cudaErrorInvalidValue;  // more levels than any octree can have
-      c.nm2l = (int64_t)hs.nm2l;
-      c.np2p = (int64_t)hs.np2p;
-      c.traverse_iters = hs.iters;
-      c.frontier_items = (int64_t)hs.items;
-      c.nrun_m = (int64_t)hs.nrun_m;
-      c.nrun_p = (int64_t)hs.nrun_p;
-      return cudaSuccess;
-    }
+    const int r = walk_result(c, hs);
+    if (r < 0) return cudaErrorInvalidValue;
+    if (r == 0) return cudaSuccess;
     // grow the lists that overflowed (the walk stopped at the first overflow, so the
     // sizes seen are lower bounds)
+    auto grow = [](uint64_t want) { return want + want / 4 + 1024; };
     auto up = [&](uint64_t &cap, int bit, int k) {
       if (hs.ovf_lists & bit) cap = grow(std::max<uint64_t>(cap * 2, hs.need[k]));
     };
@@ -949,7 +997,60 @@ cudaError_t traverse(Ctx &c, cudaStream_t st) {
     up(c.cap_run, 16, 4);
   }
   return cudaErrorInvalidValue;
-#undef TRY
+}
+
+// Graph mode: the walk without its read-back.  _prepare sizes every buffer
+// (outside the capture), _launch enqueues the walk (inside it), _finish reads
+// the state back after the graph ran and reports whether the lists fit.
+cudaError_t traverse_graph_prepare(Ctx &c) {
+  WalkPlan w;
+  cudaError_t e = walk_plan(c, w);
+  if (e == cudaSuccess) e = walk_buffers(c, w.nb);
+  return e;
+}
+
+cudaError_t traverse_graph_launch(Ctx &c, cudaStream_t st) {
+  WalkPlan w;
+  cudaError_t e = walk_plan(c, w);
+  if (e == cudaSuccess) e = walk_launch(c, w, st);
+  return e;
+}
+
+cudaError_t traverse_graph_finish(Ctx &c, cudaStream_t st, bool *ok) {
+  cudaError_t e;
+  TravState hs;
+  if ((e = cudaMemcpyAsync(c.h_pinned, walk_state(c), sizeof(TravState), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  std::memcpy(&hs, c.h_pinned, sizeof(TravState));
+  *ok = walk_result(c, hs) == 0;
+  c.traverse_walks = 1;
+  return cudaSuccess;
+}
+
+// Graph mode: every buffer the list grouping of sort_lists can touch, sized for
+// the capacities, so that nothing is allocated during the capture.
+cudaError_t sort_lists_prepare(Ctx &c) {
+  cudaError_t e;
+  const size_t nn = (size_t)(c.nnodes > 0 ? c.nnodes : 1);
+  const size_t nr = (size_t)c.cap_run;
+  if ((e = ensure(c.m2l_beg, nn * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.m2l_end, nn * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.m2l_mid, nn * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.p2p_beg, nn * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.p2p_end, nn * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.m2l_alt, c.cap_m2l * 8)) != cudaSuccess) return e;
+  if ((e = ensure(c.p2p_alt, c.cap_p2p * 8)) != cudaSuccess) return e;
+  if ((e = ensure(c.tmp2, nr * 20 + nn * 4 + 64)) != cudaSuccess) return e;
+  const size_t most = nr > nn ? nr : nn;
+  return ensure(c.offs, ((most + 4095) / 1024 + 1) * sizeof(uint64_t));  // scan block sums, with room
+}
+
+// Device address of the run counts the walk recorded (M2L, P2P), for the list
+// grouping of graph mode.
+const unsigned long long *walk_run_counts(Ctx &c, int which) {
+  TravState *st = walk_state(c);
+  return which == 0 ? &st->nrun_m : &st->nrun_p;
 }
 
 namespace {
@@ -957,11 +1058,12 @@ namespace {
 // Counting sort of the runs by sink: run r of sink s goes to roff[s] + rank[r]
 // (rank = its level order among the sink's runs), the order a stable sort by
 // (sink, level) gives.
+// nr_dev (graph mode): the run count on the device; the grid then covers the capacity nr.
 __global__ void k_run_place(const uint64_t *__restrict__ key, const uint32_t *__restrict__ rank,
-                            const uint32_t *__restrict__ roff, int64_t nr, uint64_t *__restrict__ key_s,
-                            uint32_t *__restrict__ idx) {
+                            const uint32_t *__restrict__ roff, int64_t nr, const unsigned long long *nr_dev,
+                            uint64_t *__restrict__ key_s, uint32_t *__restrict__ idx) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nr) return;
+  if (r >= (nr_dev ? (int64_t)*nr_dev : nr)) return;
   const uint64_t k = key[r];
   const uint32_t pos = roff[(uint32_t)(k >> 8)] + rank[r];
   key_s[pos] = k;
@@ -969,18 +1071,21 @@ __global__ void k_run_place(const uint64_t *__restrict__ key, const uint32_t *__
 }
 
 __global__ void k_run_gather(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ cnt,
-                             uint32_t *__restrict__ cnt_s, int64_t nr) {
+                             uint32_t *__restrict__ cnt_s, int64_t nr, const unsigned long long *nr_dev) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nr) cnt_s[i] = cnt[idx[i]];
+  if (i >= nr) return;
+  cnt_s[i] = i < (nr_dev ? (int64_t)*nr_dev : nr) ? cnt[idx[i]] : 0u;  // zeros beyond the runs (graph mode)
 }
 
 // One warp per run (runs sorted by (sink, level)): CSR bounds of its sink and a
 // coalesced copy of its entries to their place in the sink-grouped list.
 __global__ void k_run_copy(const uint64_t *__restrict__ key_s, const uint32_t *__restrict__ idx,
                            const uint64_t *__restrict__ beg, const uint32_t *__restrict__ cnt_s,
-                           const uint32_t *__restrict__ dst, int64_t nr, const uint64_t *__restrict__ src,
-                           uint64_t *__restrict__ out, uint32_t *__restrict__ csr_beg, uint32_t *__restrict__ csr_end,
+                           const uint32_t *__restrict__ dst, int64_t nr_host, const unsigned long long *nr_dev,
+                           const uint64_t *__restrict__ src, uint64_t *__restrict__ out,
+                           uint32_t *__restrict__ csr_beg, uint32_t *__restrict__ csr_end,
                            uint32_t *__restrict__ csr_mid) {
+  const int64_t nr = nr_dev ? (int64_t)*nr_dev : nr_host;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nr; i += nw) {
@@ -1007,9 +1112,11 @@ __global__ void k_run_copy(const uint64_t *__restrict__ key_s, const uint32_t *_
 // list ends up grouped by sink (levels in order, walk order within a level)
 // with CSR bounds.  Cost: a scan over the cells, a pass over the runs and one
 // pass over the entries.
+// nr_dev (graph mode): the run count on the device, nr its capacity; n is then the
+// list's capacity.
 static cudaError_t merge_runs(Ctx &c, DBuf &L, DBuf &A, int64_t n, DBuf &rkey, DBuf &rbeg, DBuf &rcnt, int64_t nr,
                               DBuf &rrank, DBuf &rsink, uint32_t *csr_beg, uint32_t *csr_end, uint32_t *csr_mid,
-                              cudaStream_t st) {
+                              cudaStream_t st, const unsigned long long *nr_dev = nullptr) {
   cudaError_t e;
   if (n == 0 || nr == 0) return cudaSuccess;
   if ((e = ensure(A, n * 8)) != cudaSuccess) return e;
@@ -1022,16 +1129,16 @@ static cudaError_t merge_runs(Ctx &c, DBuf &L, DBuf &A, int64_t n, DBuf &rkey, D
   const int T = 256;
   uint64_t *rtotal = P<uint64_t>(c.d_small) + 1;  // (reused for the entry total below)
   if ((e = scan_u32(P<uint32_t>(rsink), roff, rtotal, (size_t)nn, c.offs, st)) != cudaSuccess) return e;
-  k_run_place<<<blocks_for(nr, T), T, 0, st>>>(P<uint64_t>(rkey), P<uint32_t>(rrank), roff, nr, keys, idx);
+  k_run_place<<<blocks_for(nr, T), T, 0, st>>>(P<uint64_t>(rkey), P<uint32_t>(rrank), roff, nr, nr_dev, keys, idx);
   note_launch();
-  k_run_gather<<<blocks_for(nr, T), T, 0, st>>>(idx, P<uint32_t>(rcnt), cnt_s, nr);
+  k_run_gather<<<blocks_for(nr, T), T, 0, st>>>(idx, P<uint32_t>(rcnt), cnt_s, nr, nr_dev);
   note_launch();
   uint64_t *total = P<uint64_t>(c.d_small) + 1;
   if ((e = scan_u32(cnt_s, dst, total, (size_t)nr, c.offs, st)) != cudaSuccess) return e;
   unsigned g = blocks_for((size_t)nr, 8);
   if (g > 152 * 32) g = 152 * 32;
-  k_run_copy<<<g, T, 0, st>>>(keys, idx, P<uint64_t>(rbeg), cnt_s, dst, nr, P<uint64_t>(L), P<uint64_t>(A), csr_beg,
-                              csr_end, csr_mid);
+  k_run_copy<<<g, T, 0, st>>>(keys, idx, P<uint64_t>(rbeg), cnt_s, dst, nr, nr_dev, P<uint64_t>(L), P<uint64_t>(A),
+                              csr_beg, csr_end, csr_mid);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   std::swap(L, A);
@@ -1077,12 +1184,16 @@ cudaError_t sort_lists(Ctx &c, cudaStream_t st) {
   TRY(cudaMemsetAsync(c.p2p_end.p, 0, nn * 4, st));
   int sink_bits = 1;
   while (((int64_t)1 << sink_bits) < nn) ++sink_bits;
-  TRY(merge_runs(c, c.p2p, c.p2p_alt, c.np2p, c.rp_key, c.rp_beg, c.rp_cnt, c.nrun_p, c.rp_rank, c.rcnt_p,
-                 P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), nullptr, st));
+  // graph mode: capacities for the sizes, the run counts read on the device
+  const bool gw = c.graph_walk;
+  TRY(merge_runs(c, c.p2p, c.p2p_alt, gw ? (int64_t)c.cap_p2p : c.np2p, c.rp_key, c.rp_beg, c.rp_cnt,
+                 gw ? (int64_t)c.cap_run : c.nrun_p, c.rp_rank, c.rcnt_p, P<uint32_t>(c.p2p_beg),
+                 P<uint32_t>(c.p2p_end), nullptr, st, gw ? walk_run_counts(c, 1) : nullptr));
   const bool tables = ((c.prm.m2l_precision == 0 && c.prm.m2l_tables) || c.prm.m2l_precision >= 3) && c.tab_k > 0;
   if (c.nm2l > 0 && !tables) {
-    TRY(merge_runs(c, c.m2l, c.m2l_alt, c.nm2l, c.rm_key, c.rm_beg, c.rm_cnt, c.nrun_m, c.rm_rank, c.rcnt_m,
-                   P<uint32_t>(c.m2l_beg), P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid), st));
+    TRY(merge_runs(c, c.m2l, c.m2l_alt, gw ? (int64_t)c.cap_m2l : c.nm2l, c.rm_key, c.rm_beg, c.rm_cnt,
+                   gw ? (int64_t)c.cap_run : c.nrun_m, c.rm_rank, c.rcnt_m, P<uint32_t>(c.m2l_beg),
+                   P<uint32_t>(c.m2l_end), P<uint32_t>(c.m2l_mid), st, gw ? walk_run_counts(c, 0) : nullptr));
     if (c.prm.mac_mode == 1) {  // learned orders: stable pass on the order bits -> (order, sink)
       bool alt = false;
       TRY(ensure(c.m2l_alt, c.nm2l * 8));
