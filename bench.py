@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--leaf-max", type=int, default=0, help="octree leaf capacity (0: the workload's own)")
     ap.add_argument("--m2l-precision", type=int, default=0,
                     help="0 FP32 CUDA cores, 1 3xTF32 tensor cores, 2 BF16x3 tensor cores")
-    ap.add_argument("--graph", type=int, default=0, help="1: post-traversal phases as one CUDA graph")
+    ap.add_argument("--graph", type=int, default=0, help="1: the whole short-range call as one CUDA graph")
     ap.add_argument("--tuned", default="", help="autotuner cache (JSON) to take the launch shapes from")
     ap.add_argument("--m2l-tables", type=int, default=0, help="1: same-level M2L operators from the (level, offset) table")
     ap.add_argument("--mac", default="geometric", choices=["geometric", "learned"])
@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--split", default="gauss", choices=["gauss", "poly"],
                     help="truncation of the force split: Gaussian (Sec. 2.2) or polynomial (Sec. 5)")
     ap.add_argument("--mutual", type=int, default=0, help="1: mutual (third-law) P2P")
+    ap.add_argument("--kdk", type=int, default=1, help="1: also time the whole KDK step, direct and as one graph")
     ap.add_argument("--compare", type=int, default=1,
                     help="1: also time the metric's other arm (learned acceptance + 3xTF32 M2L) on the same set")
     ap.add_argument("--compare-theta", type=float, default=0.5, help="safety bound of the learned arm")
@@ -301,6 +302,39 @@ def time_arm(hfmm, torch, common, wts, dpos, dmass, acc, flush, steps, warmup, s
     return [a.elapsed_time(b) for a, b in ev], phases, l1 - l0
 
 
+def time_kdk(hfmm, torch, common, pos, mass, flush, steps, warmup, stream, graph):
+    """The whole kick-drift-kick step (first kick, drift, tree build, short range,
+    PM long range, second kick) from the same seeded start, by direct launches
+    (graph 0) or as one CUDA graph (graph 1): step times in ms (CUDA events, L2
+    flushed before each step), launches per timed step and the graph counters."""
+    rng = np.random.default_rng(2718)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = hfmm.Solver(**dict(common, use_graph=graph))
+    p = torch.from_numpy(pos).to(dev)
+    m = torch.from_numpy(mass).to(dev)
+    v = torch.from_numpy((0.05 * rng.standard_normal(pos.shape)).astype(np.float32)).to(dev)
+    s.build_tree(p, m)
+    a = s.short_range_forces()
+    s.pm_long_range(a)
+    dt = 1e-4
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        s.step(p, v, a, dt)
+    torch.cuda.synchronize()
+    st0 = s.get_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(1.0)
+        ev[k][0].record(stream)
+        s.step(p, v, a, dt)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    st1 = s.get_stats()
+    s.close()
+    return ([x.elapsed_time(y) for x, y in ev], (st1["launches"] - st0["launches"]) / steps,
+            st1["step_graphs"] - st0["step_graphs"], st1["graph_captures"] - st0["graph_captures"])
+
+
 def main():
     args = parse()
     from paper_2006_14952_gb300 import workloads as W
@@ -442,7 +476,7 @@ def main():
     peak_src = (f"measured: FP32 FMA probe (hfmm_alu_peak), max of scalar {alu['ffma']:.1f} and packed FP32x2 "
                 f"{alu['ffma2']:.1f} TFLOP/s (derived at 2070 MHz: {derived_fp32:.1f})")
     if mean["t_p2p"] < 0:  # graph mode: the post-traversal phases are timed as one graph
-        roof = {"kernel": "post-traversal graph (lists, M2L, L2L/L2P, P2P)", "bound": "alu", "achieved": None,
+        roof = {"kernel": "short-range graph (upward, walk, lists, M2L, L2L/L2P, P2P)", "bound": "alu", "achieved": None,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "note": "graph mode times the graph as a whole; run without --graph for the P2P roofline"}
     elif mean["t_p2p"] >= mean["t_m2l"]:
@@ -489,6 +523,20 @@ def main():
                 "both_within_1e-4": bool(accuracy and l_acc and accuracy["rms_rel"] <= 1e-4
                                          and l_acc["rms_rel"] <= 1e-4)}
 
+    # the whole KDK step (with the PM long range), direct and as one graph
+    kdk = None
+    if args.kdk and args.split == "gauss" and not learned and args.m2l_precision == 0 and not args.mutual:
+        kdk = {"what": "kick, drift, tree build, short range, PM long range, kick (dt 1e-4 from a seeded "
+                       "start with 0.05 rms velocities); L2 flushed before every step"}
+        for mode in (0, 1):
+            k_ms, k_launch, k_graphs, k_caps = time_kdk(hfmm, torch, dict(common, m2l_tables=0), pos, mass, flush,
+                                                        args.steps, args.warmup, stream, mode)
+            k_tot = max_over_ranks(sum(k_ms), dev)
+            kdk["graph" if mode else "direct"] = {
+                "ms_per_step": k_tot / args.steps, "value": whole_job_rate(ws, n, args.steps, k_tot / 1e3),
+                "unit": UNIT, "launches_per_step": k_launch, "step_ms": [round(x, 4) for x in k_ms],
+                **({"steps_as_one_graph": k_graphs, "captures": k_caps} if mode else {})}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(pos, mass, cfg, args.cpu_seconds, split=args.split)
@@ -512,6 +560,7 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "accuracy": accuracy,
             "arms": arms,
+            "kdk_step": kdk,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 4), "d2h_bytes_per_step": n * 12},

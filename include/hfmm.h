@@ -100,9 +100,10 @@ typedef struct {
                           the device, and one read-back after the graph checks them: if a list
                           overflowed, the call runs again directly (growing the lists), so the
                           result is the same.  The executable graph is updated in place while the
-                          launch sequence keeps its shape, else re-instantiated.  Geometric
-                          acceptance, m2l_precision 0, m2l_tables 0, p2p_mutual 0, profile bit 1
-                          off; otherwise ignored. */
+                          launch sequence keeps its shape, else re-instantiated.  hfmm_step then
+                          runs the whole kick-drift-kick step as one graph (see hfmm_step).
+                          Geometric acceptance, m2l_precision 0, m2l_tables 0, p2p_mutual 0,
+                          profile bit 1 off; otherwise ignored. */
   int tc_wait_polls;   /* m2l_precision 1 and 2: polls of the bounded wait for each chunk's MMAs before the
                           call gives up with HFMM_ERR_TIMEOUT (0 = 2^22; -1 = no poll at all, so that
                           every chunk gives up at once: a test of the error path).  After a give-up
@@ -143,11 +144,14 @@ typedef struct {
   int64_t launches;           /* kernels launched by this library in this process so far */
   /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P.
      After a call in graph mode t_upward covers the whole graph (upward pass to P2P) and
-     t_traverse, t_lists, t_m2l, t_l2l, t_p2p are -1. */
+     t_traverse, t_lists, t_m2l, t_l2l, t_p2p are -1; after a step run as one graph
+     t_upward covers the whole step and t_keys_sort, t_tree are -1 too. */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
   int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
   int64_t frontier_pairs;     /* cell pairs the traversal classified, over all levels */
   int64_t traverse_walks;     /* walks the last traversal took (1 + repeats after a list overflowed) */
+  int64_t step_graphs;        /* hfmm_step calls launched as one graph by this context */
+  int64_t graph_captures;     /* graphs this context captured and instantiated or updated */
 } hfmm_stats;
 
 typedef struct hfmm_ctx hfmm_ctx;
@@ -234,6 +238,15 @@ int hfmm_pm_long_range(hfmm_ctx *ctx, float *acc_soa, void *stream);
  * total acceleration at pos_soa (hfmm_short_range_forces then
  * hfmm_pm_long_range, or the previous step).  The mass array given to
  * hfmm_build_tree must stay valid.  Errors as for the calls it makes.
+ * With use_graph (and the configurations it covers) the whole step is one CUDA
+ * graph with no host read-back inside: the tree's sizes stay on the device
+ * (nodes up to a capacity kept in the context, levels up to the last tree's
+ * plus two), the lists take their capacities from the last call, and the
+ * second kick runs only when all of them fitted.  One read-back after the graph
+ * checks them; after an overflow the step goes on directly from the drifted
+ * positions (rebuilding the tree, growing what overflowed), so the result is
+ * the same.  The graph is captured again only when a buffer address, a
+ * capacity or an argument changed since the last capture.
  */
 int hfmm_step(hfmm_ctx *ctx, double *pos_soa, float *vel_soa, float *acc_soa, double dt, void *stream);
 

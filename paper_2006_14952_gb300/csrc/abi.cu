@@ -1,5 +1,6 @@
 // C ABI of libhfmm (declared in include/hfmm.h): context lifecycle, argument
 // checks, error mapping, phase orchestration, statistics and exports.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -124,6 +125,26 @@ PairFit fit_pair_factor(double rs, double rc) {
 
 }  // namespace hfmm
 
+namespace {
+
+// Every device buffer of the context (the PM buffers apart).
+template <class F>
+void for_each_buffer(Ctx &c, F f) {
+  DBuf *bufs[] = {&c.key, &c.key_alt, &c.idx, &c.idx_alt, &c.xs, &c.pm4, &c.perm, &c.cell, &c.range, &c.kids,
+                  &c.leaves, &c.bounds, &c.nkids, &c.koff, &c.front, &c.front_next, &c.cls, &c.counts, &c.offs,
+                  &c.m2l, &c.m2l_alt, &c.p2p, &c.p2p_alt, &c.m2l_beg, &c.m2l_end, &c.p2p_beg, &c.p2p_end, &c.M,
+                  &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc, &c.m2l_mid, &c.tab,
+                  &c.mlp_w, &c.cand, &c.mlp_scratch, &c.fseg, &c.fseg_next, &c.seg_a, &c.seg_b, &c.acc_a,
+                  &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
+                  &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p,
+                  &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
+                  &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval, &c.lo_flag,
+                  &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr};
+  for (DBuf *b : bufs) f(*b);
+}
+
+}  // namespace
+
 extern "C" {
 
 void hfmm_default_params(hfmm_params *o) {
@@ -175,7 +196,7 @@ int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
   c.ldm = (c.nc + 3) & ~3;
   c.fit = fit_pair_factor(c.rs, c.rc);
   c.tab_k = m2l_table_extent(*params);
-  cudaError_t e = cudaMallocHost(&c.h_pinned, 256);
+  cudaError_t e = cudaMallocHost(&c.h_pinned, 1024);
   if (e == cudaSuccess) e = ensure(c.d_small, 256);
   for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&c.ev[i]);
   if (e != cudaSuccess) {
@@ -191,19 +212,10 @@ int hfmm_create(const hfmm_params *params, hfmm_ctx **out) {
 void hfmm_destroy(hfmm_ctx *h) {
   if (!h) return;
   Ctx &c = h->c;
-  DBuf *bufs[] = {&c.key, &c.key_alt, &c.idx, &c.idx_alt, &c.xs, &c.pm4, &c.perm, &c.cell, &c.range, &c.kids,
-                  &c.leaves, &c.bounds, &c.nkids, &c.koff, &c.front, &c.front_next, &c.cls, &c.counts, &c.offs,
-                  &c.m2l, &c.m2l_alt, &c.p2p, &c.p2p_alt, &c.m2l_beg, &c.m2l_end, &c.p2p_beg, &c.p2p_end, &c.M,
-                  &c.L, &c.tmp, &c.tmp2, &c.d_small, &c.hpos, &c.hmass, &c.hacc, &c.m2l_mid, &c.tab,
-                  &c.mlp_w, &c.cand, &c.mlp_scratch, &c.fseg, &c.fseg_next, &c.seg_a, &c.seg_b, &c.acc_a,
-                  &c.acc_b, &c.segbase, &c.btot2, &c.rm_key, &c.rm_beg, &c.rm_cnt, &c.rp_key, &c.rp_beg,
-                  &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p,
-                  &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
-                  &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval, &c.lo_flag,
-                  &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr};
-  for (DBuf *b : bufs) release(*b);
+  for_each_buffer(c, [](DBuf &b) { release(b); });
   pm_release(c);
   if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  if (c.gexec_step) cudaGraphExecDestroy(c.gexec_step);
   if (c.gstream) cudaStreamDestroy(c.gstream);
   if (c.gready) cudaEventDestroy(c.gready);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
@@ -221,6 +233,7 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
   if (!h) return HFMM_ERR_ARG;
   Ctx &c = h->c;
   c.have_tree = false;
+  c.last_step_graph = false;
   if (n < 0 || n > (int64_t)0x7fffffff) return fail(c, HFMM_ERR_ARG, "n must be in [0, 2^31)");
   if (n > 0 && (!pos || !mass)) return fail(c, HFMM_ERR_ARG, "null position or mass pointer");
   c.mass_ref = mass;
@@ -232,6 +245,13 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
 }
 
 namespace {
+
+// The configurations the graphs cover: FP32 CUDA-core M2L without operator
+// tables, the geometric acceptance, one-sided P2P and no pair counting.
+bool graph_eligible(const Ctx &c) {
+  return c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
+         !c.prm.p2p_mutual && !c.prm.m2l_tables;
+}
 
 // The whole short-range call captured as one CUDA graph on the context's own
 // stream and replayed on `st`: upward pass, the walk (its list sizes stay on
@@ -293,8 +313,7 @@ cudaError_t whole_call_graph(Ctx &c, float *acc, cudaStream_t st, bool prof, boo
   }
   cudaGraphDestroy(graph);
   if (prof) cudaEventRecord(c.ev[3], st);
-  e = cudaGraphLaunch(c.gexec, st);
-  note_launch();
+  e = cudaGraphLaunch(c.gexec, st);  // its kernels were counted as they were captured
   if (prof) cudaEventRecord(c.ev[9], st);
   if (e != cudaSuccess) return e;
   c.last_graph = true;
@@ -324,8 +343,7 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if ((c.prm.profile & 2) && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "memset counter");
   c.last_graph = false;
-  if (c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
-      !c.prm.p2p_mutual && !c.prm.m2l_tables) {
+  if (graph_eligible(c)) {
     bool ok = false;
     e = whole_call_graph(c, acc, st, prof, &ok);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph");
@@ -384,17 +402,176 @@ int hfmm_pm_long_range(hfmm_ctx *h, float *acc, void *stream) {
   return HFMM_OK;
 }
 
+namespace {
+
+// What a captured step depends on besides the parameters (fixed for the
+// context): every buffer address, the capacities, the arguments.  Equal
+// signatures before a step and after the last capture: the graph is replayed
+// as it is (each host-side swap of ping-pong buffers made during the capture
+// is part of the state it left).
+std::vector<uint64_t> step_signature(Ctx &c, const double *pos, const float *vel, const float *acc, double dt) {
+  std::vector<uint64_t> v;
+  v.reserve(192);
+  for_each_buffer(c, [&](DBuf &b) {
+    v.push_back((uint64_t)(uintptr_t)b.p);
+    v.push_back((uint64_t)b.cap);
+  });
+  DBuf *pmb[] = {&c.pm_q, &c.pm_rho, &c.pm_mk, &c.pm_ak, &c.pm_a, &c.pm_gtab};
+  for (DBuf *b : pmb) v.push_back((uint64_t)(uintptr_t)b->p);
+  uint64_t dtb;
+  std::memcpy(&dtb, &dt, 8);
+  const uint64_t rest[] = {(uint64_t)c.n, c.cap_nodes, (uint64_t)c.cap_levels, c.cap_front, c.cap_m2l, c.cap_p2p,
+                           c.cap_seg, c.cap_run, (uint64_t)c.pm_plan_r2c, (uint64_t)c.pm_plan_c2r,
+                           (uint64_t)(uintptr_t)pos, (uint64_t)(uintptr_t)vel, (uint64_t)(uintptr_t)acc,
+                           (uint64_t)(uintptr_t)c.mass_ref, dtb};
+  v.insert(v.end(), rest, rest + sizeof(rest) / sizeof(rest[0]));
+  return v;
+}
+
+// The kick-drift-kick step as one CUDA graph (Sec. 4's synchronised step):
+// first kick, drift, the octree build (its sizes stay on the device), the
+// short-range call (upward pass, walk, list grouping, M2L, L2L/L2P, P2P), the
+// PM long range and the second kick.  Kernels after the build read the tree's
+// extent from the device state and treat an overflowed tree as empty; the
+// second kick runs only when the tree and the walk fitted.  Buffers are sized
+// before the capture from the node capacity, the last tree's level count and
+// the list capacities, and the graph is captured again only when an address, a
+// capacity or an argument changed.  One read-back after the graph: *done is
+// false when something overflowed, and the step then continues directly from
+// the drifted positions (the first kick and the drift have been applied).
+cudaError_t step_graph(Ctx &c, double *pos, float *vel, float *acc, double dt, cudaStream_t st, bool prof,
+                       bool *done) {
+  cudaError_t e;
+  *done = false;
+  const int64_t n = c.n;
+  if (!c.gstream && (e = cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = build_tree_prepare(c, n)) != cudaSuccess) return e;
+  // while the step is captured the tree's sizes on the host are the node capacity
+  c.nnodes = c.nleaves = (int64_t)c.cap_nodes;
+  const size_t eb = (size_t)c.cap_nodes * c.ldm * sizeof(float);
+  if ((e = ensure(c.M, eb)) != cudaSuccess) return e;
+  if ((e = ensure(c.L, eb)) != cudaSuccess) return e;
+  if ((e = traverse_graph_prepare(c)) != cudaSuccess) return e;
+  if ((e = sort_lists_prepare(c)) != cudaSuccess) return e;
+  if ((e = pm_prepare(c)) != cudaSuccess) return e;
+  std::vector<uint64_t> sig = step_signature(c, pos, vel, acc, dt);
+  if (!c.gexec_step || sig != c.step_sig) {
+    c.nm2l = (int64_t)c.cap_m2l;
+    c.np2p = (int64_t)c.cap_p2p;
+    c.graph_walk = c.graph_tree = true;
+    std::vector<void *> deferred;
+    g_deferred_free = &deferred;
+    cudaGraph_t graph = nullptr;
+    const long long l0 = g_launches.load();
+    cudaStream_t gs = c.gstream;
+    e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t r = kick(vel, acc, n, 0.5 * dt, gs);
+      if (r == cudaSuccess) r = drift(pos, vel, n, dt, c.prm.box, gs);
+      if (r == cudaSuccess) r = build_tree_launch(c, pos, c.mass_ref, n, gs);
+      if (r == cudaSuccess) r = cudaMemsetAsync(c.L.p, 0, eb, gs);
+      // the padding of each multipole row is read (as part of a float4) but never used: keep it finite
+      if (r == cudaSuccess && c.ldm != c.nc) r = cudaMemsetAsync(c.M.p, 0, eb, gs);
+      if (r == cudaSuccess) r = upward(c, gs);
+      if (r == cudaSuccess) r = traverse_graph_launch(c, gs);
+      if (r == cudaSuccess) r = sort_lists(c, gs);
+      if (r == cudaSuccess) r = m2l_all(c, gs);
+      if (r == cudaSuccess) r = downward(c, acc, gs);
+      if (r == cudaSuccess) r = p2p_pass(c, acc, gs);
+      if (r == cudaSuccess) r = pm_long_range(c, acc, gs);
+      if (r == cudaSuccess) r = kick_guarded(vel, acc, n, 0.5 * dt, step_guard(c), gs);
+      e = cudaStreamEndCapture(gs, &graph);
+      if (r != cudaSuccess) e = r;
+    }
+    c.graph_walk = c.graph_tree = false;
+    g_deferred_free = nullptr;
+    for (void *p : deferred) cudaFree(p);  // allocations replaced during the capture (none expected)
+    c.step_kernels = g_launches.load() - l0;
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (c.gexec_step) cudaGraphExecDestroy(c.gexec_step);
+      c.gexec_step = nullptr;
+      return e;
+    }
+    if (c.gexec_step) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(c.gexec_step, graph, &info) == cudaSuccess) {
+        ++c.graph_updates;
+      } else {
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(c.gexec_step);
+        c.gexec_step = nullptr;
+      }
+    }
+    if (!c.gexec_step) {
+      e = cudaGraphInstantiate(&c.gexec_step, graph, 0);
+      if (e != cudaSuccess) {
+        c.gexec_step = nullptr;
+        cudaGraphDestroy(graph);
+        return e;
+      }
+      ++c.graph_instantiations;
+    }
+    cudaGraphDestroy(graph);
+    c.step_sig = step_signature(c, pos, vel, acc, dt);  // the state the capture left
+  } else {
+    g_launches.fetch_add(c.step_kernels, std::memory_order_relaxed);  // the graph's kernels, counted per replay
+  }
+  if (prof) cudaEventRecord(c.ev[3], st);
+  if ((e = cudaGraphLaunch(c.gexec_step, st)) != cudaSuccess) return e;
+  if (prof) cudaEventRecord(c.ev[9], st);
+  c.last_graph = c.last_step_graph = true;
+  ++c.step_graphs;
+  // the tree's state beside the walk's (both land in one synchronisation)
+  unsigned char *hp = reinterpret_cast<unsigned char *>(c.h_pinned);
+  if ((e = cudaMemcpyAsync(hp + 512, c.tstate.p, sizeof(TreeState), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  bool walk_ok = false;
+  if ((e = traverse_graph_finish(c, st, &walk_ok)) != cudaSuccess) return e;
+  TreeState ts;
+  std::memcpy(&ts, hp + 512, sizeof(TreeState));
+  if (!build_tree_finish(c, ts)) {
+    c.have_tree = false;
+    return cudaSuccess;
+  }
+  *done = walk_ok;
+  return cudaSuccess;
+}
+
+}  // namespace
+
 int hfmm_step(hfmm_ctx *h, double *pos, float *vel, float *acc, double dt, void *stream) {
   if (!h) return HFMM_ERR_ARG;
   Ctx &c = h->c;
   if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "step before build_tree");
   if (c.n > 0 && (!pos || !vel || !acc || !c.mass_ref)) return fail(c, HFMM_ERR_ARG, "null particle array");
   if (!std::isfinite(dt)) return fail(c, HFMM_ERR_ARG, "dt must be finite");
+  if (c.prm.pm_grid < 2 || c.prm.pm_grid > 1024) return fail(c, HFMM_ERR_ARG, "pm_grid must be in 2..1024");
   cudaStream_t st = S(stream);
   const int64_t n = c.n;
   cudaError_t e;
-  if ((e = kick(vel, acc, n, 0.5 * dt, st)) != cudaSuccess) return cuda_fail(c, e, "kick");
-  if ((e = drift(pos, vel, n, dt, c.prm.box, st)) != cudaSuccess) return cuda_fail(c, e, "drift");
+  bool drifted = false;
+  // (node indices of the graph's walk are bounded by the node capacity: keep it below the sink field)
+  const uint64_t cap_guess = std::max<uint64_t>(c.cap_nodes, (uint64_t)(2 * n / std::max(c.prm.leaf_max, 1) + 64));
+  if (graph_eligible(c) && n > 0 && cap_guess < ((uint64_t)1 << kSinkBits)) {
+    bool done = false;
+    e = step_graph(c, pos, vel, acc, dt, st, (c.prm.profile & 1) != 0, &done);
+    if (e != cudaSuccess) {
+      c.have_tree = false;  // the host's tree sizes may be the capture's placeholders
+      return cuda_fail(c, e, "step graph");
+    }
+    if (done) {
+      if (c.nm2l > (int64_t)UINT32_MAX || c.np2p > (int64_t)UINT32_MAX)
+        return fail(c, HFMM_ERR_CAPACITY, "an interaction list above 2^32 - 1 entries");
+      return HFMM_OK;
+    }
+    drifted = true;  // an overflow: the step goes on directly from the drifted positions
+    c.last_graph = c.last_step_graph = false;
+  }
+  if (!drifted) {
+    if ((e = kick(vel, acc, n, 0.5 * dt, st)) != cudaSuccess) return cuda_fail(c, e, "kick");
+    if ((e = drift(pos, vel, n, dt, c.prm.box, st)) != cudaSuccess) return cuda_fail(c, e, "drift");
+  }
   int rc = hfmm_build_tree(h, pos, c.mass_ref, n, stream);
   if (rc != HFMM_OK) return rc;
   if ((rc = hfmm_short_range_forces(h, acc, stream)) != HFMM_OK) return rc;
@@ -470,6 +647,8 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->nm2l_table = c.nm2l_table;
   o->frontier_pairs = c.frontier_items;
   o->traverse_walks = c.traverse_walks;
+  o->step_graphs = c.step_graphs;
+  o->graph_captures = c.graph_updates + c.graph_instantiations;
   o->p2p_useful_pairs = -1;
   if ((c.prm.profile & 2) && c.n > 0) {
     unsigned long long u = 0;
@@ -483,6 +662,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   const int ev_graph[][2] = {{0, 1}, {1, 2}, {3, 9}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
   for (int i = 0; i < 8; ++i) {
     *t[i] = -1.f;
+    if (c.last_step_graph && i < 2) continue;  // the build ran inside the step's graph
     if (c.last_graph && ev_graph[i][0] >= 0 && (c.prm.profile & 1) && c.n > 0) {
       float ms = -1.f;
       if (cudaEventElapsedTime(&ms, c.ev[ev_graph[i][0]], c.ev[ev_graph[i][1]]) == cudaSuccess) *t[i] = ms;

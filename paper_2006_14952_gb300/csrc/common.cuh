@@ -145,6 +145,34 @@ __host__ __device__ inline bool p2p_owner(uint32_t a, uint32_t b, uint32_t s, ui
   return ((a ^ b) & 1u) ? a < b : a > b;
 }
 
+// ---------------------------------------------------------------- tree sizes on the device
+// The octree build's sizes as its cooperative kernel leaves them (node count,
+// leaf count, levels, first node of each level, capacity overflow).  In graph
+// mode the kernels after the build read their sizes here instead of taking
+// them from the host; an overflowed build reads as an empty tree.
+struct TreeState {
+  unsigned long long total, nleaves;
+  int nlevels, overflow;
+  unsigned long long level_start[kDepth + 3];
+};
+__host__ __device__ inline int64_t tree_nodes(const TreeState *t, int64_t host) {
+  return t ? (t->overflow ? 0 : (int64_t)t->total) : host;
+}
+__host__ __device__ inline int64_t tree_leaves(const TreeState *t, int64_t host) {
+  return t ? (t->overflow ? 0 : (int64_t)t->nleaves) : host;
+}
+// nodes [lo, lo + cnt) of level l (cnt = 0 beyond the last level or after an overflow)
+__host__ __device__ inline void tree_level(const TreeState *t, int l, int64_t &lo, int64_t &cnt) {
+  if (!t) return;
+  if (t->overflow || l + 1 >= t->nlevels) {
+    lo = 0;
+    cnt = 0;
+    return;
+  }
+  lo = (int64_t)t->level_start[l];
+  cnt = (int64_t)t->level_start[l + 1] - lo;
+}
+
 // ---------------------------------------------------------------- buffers
 struct DBuf {
   void *p = nullptr;
@@ -250,6 +278,7 @@ struct Ctx {
   int traverse_iters = 0;
   int64_t traverse_walks = 0;  // walks of the last traversal (1 + repeats after an overflow)
   uint64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;  // traversal capacities (entries)
+  int cap_levels = 0;  // graph mode: tree levels the level loops cover
   DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
   DBuf m2l_mid;  // u32 [nnodes]: [beg, mid) table pairs, [mid, end) per-pair operator
 
@@ -305,6 +334,12 @@ struct Ctx {
   int64_t graph_updates = 0, graph_instantiations = 0;
   bool last_graph = false;  // the last short_range_forces ran as one graph
   bool graph_walk = false;  // while capturing: list sizes live on the device (capacities on the host)
+  bool graph_tree = false;  // while capturing a step: tree sizes live on the device (c.tstate)
+  cudaGraphExec_t gexec_step = nullptr;  // the KDK step as one graph (use_graph)
+  std::vector<uint64_t> step_sig;         // the state the step graph's capture left
+  long long step_kernels = 0;             // kernels in the step graph
+  int64_t step_graphs = 0;                // steps launched as one graph
+  bool last_step_graph = false;           // the last call was a step launched as one graph
 
   // stats
   int64_t p2p_particle_pairs = -1, p2p_useful_pairs = -1, nm2l_table = -1;
@@ -341,7 +376,18 @@ cudaError_t downward(Ctx &c, float *acc, cudaStream_t st);
 // Long-range PM accelerations added to acc (input order); mesh buffers and
 // FFT plans are kept in the context (pm_release frees them).
 cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st);
+// Graph mode: the mesh buffers, FFT plans and Green-function table, made
+// outside a capture (pm_long_range calls it too).
+cudaError_t pm_prepare(Ctx &c);
 void pm_release(Ctx &c);
+// A step captured as one graph: the second kick runs only when the tree and the
+// walk fitted their capacities (device flags; null pointers: always).
+struct StepGuard {
+  const int *tree_overflow = nullptr, *walk_overflow = nullptr;
+  const unsigned long long *walk_left = nullptr;
+};
+StepGuard step_guard(Ctx &c);
+cudaError_t kick_guarded(float *vel, const float *acc, int64_t n, double h, StepGuard g, cudaStream_t st);
 // vel += h acc and pos += dt vel (wrapped), [3][n] arrays.
 cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t st);
 cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st);
@@ -355,6 +401,10 @@ cudaError_t traverse_graph_launch(Ctx &c, cudaStream_t st);
 cudaError_t traverse_graph_finish(Ctx &c, cudaStream_t st, bool *ok);
 const unsigned long long *walk_run_counts(Ctx &c, int which);
 cudaError_t sort_lists_prepare(Ctx &c);
+// Graph mode for the step: the octree build without its read-back.
+cudaError_t build_tree_prepare(Ctx &c, int64_t n);
+cudaError_t build_tree_launch(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st);
+bool build_tree_finish(Ctx &c, const TreeState &hs);
 // M2L of order q with m2l_precision 3 / 4: table pairs as (level, offset) tensor-core contractions
 // with the accumulators in tensor memory, the other pairs on the FP32 per-pair kernel.
 bool m2l_lo_supported(int p);

@@ -33,13 +33,14 @@ __device__ __forceinline__ void store_row(float *__restrict__ dst, const float (
 }
 
 // P2M, one thread per leaf: M~_m = sum_a mu_a (-1)^|m| / m! (u_a)^m, u = (x - z) / h.
+// tz (a step captured as one graph): the leaf count from the device tree state.
 template <int P>
 __global__ void k_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
                       const uint2 *__restrict__ range, const float4 *__restrict__ pm4, float box, int ldm,
-                      float *__restrict__ M) {
+                      float *__restrict__ M, const TreeState *tz) {
   constexpr int NC = ncoef(P);
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nl) return;
+  if (t >= tree_leaves(tz, nl)) return;
   const uint32_t k = leaves[t];
   const uint2 r = range[k];
   const float inv_h = (float)(1u << cell[k].w) / box;
@@ -57,34 +58,40 @@ __global__ void k_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uin
 // M2M, one thread per (cell of one level, child slot): each thread translates
 // one child's multipoles to the parent centre; the eight sibling threads are
 // adjacent lanes and add their results with a fixed xor-shuffle tree (the same
-// order on every run), and slot 0 stores the parent's row.
+// order on every run), and slot 0 stores the parent's row.  The loop is
+// block-uniform (whole warps take each trip: the shuffles see all lanes); with
+// tz (graph mode) the level's extent comes from the device tree state.
 template <int P>
 __global__ void k_m2m(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int ldm,
-                      float *__restrict__ M) {
+                      float *__restrict__ M, const TreeState *tz, int level) {
   constexpr int NC = ncoef(P);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in_level = t < 8 * cnt;  // whole groups of 8: cnt * 8 threads, blocks of a multiple of 8
-  const int64_t k = lo + t / 8;
-  const int slot = (int)(t % 8);
-  const int2 kd = in_level ? kids[k] : make_int2(0, 0);
-  float o[NC];
+  tree_level(tz, level, lo, cnt);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < 8 * cnt; b += stride) {
+    const int64_t t = b + threadIdx.x;
+    const bool in_level = t < 8 * cnt;  // whole groups of 8: cnt * 8 threads, blocks of a multiple of 8
+    const int64_t k = lo + t / 8;
+    const int slot = (int)(t % 8);
+    const int2 kd = in_level ? kids[k] : make_int2(0, 0);
+    float o[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) o[c] = 0.f;
-  if (slot < kd.y) {
-    const int ch = kd.x + slot;
-    const uint4 cc = cell[ch];
-    // (z_P - z_C) / H = +1/4 for the lower half of an axis, -1/4 for the upper
-    float ci[NC];
-    load_row<NC>(M + (size_t)ch * ldm, ci);
-    M2MBody<P>::run((cc.x & 1u) ? -1.f : 1.f, (cc.y & 1u) ? -1.f : 1.f, (cc.z & 1u) ? -1.f : 1.f, ci, o);
-  }
+    for (int c = 0; c < NC; ++c) o[c] = 0.f;
+    if (slot < kd.y) {
+      const int ch = kd.x + slot;
+      const uint4 cc = cell[ch];
+      // (z_P - z_C) / H = +1/4 for the lower half of an axis, -1/4 for the upper
+      float ci[NC];
+      load_row<NC>(M + (size_t)ch * ldm, ci);
+      M2MBody<P>::run((cc.x & 1u) ? -1.f : 1.f, (cc.y & 1u) ? -1.f : 1.f, (cc.z & 1u) ? -1.f : 1.f, ci, o);
+    }
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    o[c] += __shfl_xor_sync(0xffffffffu, o[c], 4);
-    o[c] += __shfl_xor_sync(0xffffffffu, o[c], 2);
-    o[c] += __shfl_xor_sync(0xffffffffu, o[c], 1);
+    for (int c = 0; c < NC; ++c) {
+      o[c] += __shfl_xor_sync(0xffffffffu, o[c], 4);
+      o[c] += __shfl_xor_sync(0xffffffffu, o[c], 2);
+      o[c] += __shfl_xor_sync(0xffffffffu, o[c], 1);
+    }
+    if (in_level && slot == 0 && kd.y > 0) store_row<NC>(M + (size_t)k * ldm, o);
   }
-  if (in_level && slot == 0 && kd.y > 0) store_row<NC>(M + (size_t)k * ldm, o);
 }
 
 // L2L, one thread per (cell of one level, child slot): the child's local
@@ -92,33 +99,36 @@ __global__ void k_m2m(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, c
 // siblings of a parent are neighbouring threads (one parent row load, shared).
 template <int P>
 __global__ void k_l2l(int64_t lo, int64_t cnt, const uint4 *__restrict__ cell, const int2 *__restrict__ kids, int ldm,
-                      float *__restrict__ L) {
+                      float *__restrict__ L, const TreeState *tz, int level) {
   constexpr int NC = ncoef(P);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 8 * cnt) return;
-  const int64_t k = lo + t / 8;
-  const int2 kd = kids[k];
-  const int slot = (int)(t % 8);
-  if (slot >= kd.y) return;
-  const int ch = kd.x + slot;
-  float pl[NC], cl[NC];
-  load_row<NC>(L + (size_t)k * ldm, pl);
-  float *dst = L + (size_t)ch * ldm;
-  load_row<NC>(dst, cl);
-  const uint4 cc = cell[ch];
-  // (z_C - z_P) / H = -1/4 for the lower half of an axis, +1/4 for the upper
-  L2LBody<P>::run((cc.x & 1u) ? 1.f : -1.f, (cc.y & 1u) ? 1.f : -1.f, (cc.z & 1u) ? 1.f : -1.f, pl, cl);
-  store_row<NC>(dst, cl);
+  tree_level(tz, level, lo, cnt);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 8 * cnt; t += stride) {
+    const int64_t k = lo + t / 8;
+    const int2 kd = kids[k];
+    const int slot = (int)(t % 8);
+    if (slot >= kd.y) continue;
+    const int ch = kd.x + slot;
+    float pl[NC], cl[NC];
+    load_row<NC>(L + (size_t)k * ldm, pl);
+    float *dst = L + (size_t)ch * ldm;
+    load_row<NC>(dst, cl);
+    const uint4 cc = cell[ch];
+    // (z_C - z_P) / H = -1/4 for the lower half of an axis, +1/4 for the upper
+    L2LBody<P>::run((cc.x & 1u) ? 1.f : -1.f, (cc.y & 1u) ? 1.f : -1.f, (cc.z & 1u) ? 1.f : -1.f, pl, cl);
+    store_row<NC>(dst, cl);
+  }
 }
 
 // L2P, one thread per leaf: a = G h^-2 sum L~_{n+e_d} u^n / n!, written in input order.
 template <int P>
 __global__ void k_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
                       const uint2 *__restrict__ range, const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm,
-                      int64_t n, float box, float G, int ldm, const float *__restrict__ L, float *__restrict__ acc) {
+                      int64_t n, float box, float G, int ldm, const float *__restrict__ L, float *__restrict__ acc,
+                      const TreeState *tz) {
   constexpr int NC = ncoef(P);
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nl) return;
+  if (t >= tree_leaves(tz, nl)) return;
   const uint32_t k = leaves[t];
   const uint2 r = range[k];
   const float inv_h = (float)(1u << cell[k].w) / box;
@@ -136,17 +146,43 @@ __global__ void k_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uin
   }
 }
 
+// Level loops: the tree's levels on the host, or (graph mode) the level
+// capacity, each launch reading its level's extent from the device tree state
+// on a grid sized for the node capacity (at most 16 blocks per SM; the kernels
+// loop).
+struct LevelLoop {
+  const TreeState *tz;
+  int levels;
+  LevelLoop(Ctx &c) : tz(c.graph_tree ? hfmm::P<TreeState>(c.tstate) : nullptr),
+                      levels(c.graph_tree ? c.cap_levels : c.nlevels) {}
+  void extent(const Ctx &c, int l, int64_t &lo, int64_t &cnt) const {
+    if (tz) {
+      lo = 0;
+      cnt = (int64_t)c.nnodes;  // a bound: the kernel reads the level's own extent
+    } else {
+      lo = c.level_start[l];
+      cnt = c.level_start[l + 1] - lo;
+    }
+  }
+  unsigned grid(int64_t cnt, int T) const {
+    const unsigned g = blocks_for(8 * cnt, T);
+    return tz && g > 152u * 16u ? 152u * 16u : g;
+  }
+};
+
 template <int P>
 cudaError_t upward_p(Ctx &c, cudaStream_t st) {
   const int T = 128;
   const float box = (float)c.prm.box;
+  const LevelLoop lv(c);
   k_p2m<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell), hfmm::P<uint2>(c.range),
-                                                   hfmm::P<float4>(c.pm4), box, c.ldm, hfmm::P<float>(c.M));
+                                                   hfmm::P<float4>(c.pm4), box, c.ldm, hfmm::P<float>(c.M), lv.tz);
   note_launch();
-  for (int l = c.nlevels - 2; l >= 0; --l) {
-    int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    k_m2m<P><<<blocks_for(8 * cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm,
-                                                   hfmm::P<float>(c.M));
+  for (int l = lv.levels - 2; l >= 0; --l) {
+    int64_t lo, cnt;
+    lv.extent(c, l, lo, cnt);
+    k_m2m<P><<<lv.grid(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm,
+                                            hfmm::P<float>(c.M), lv.tz, l);
     note_launch();
   }
   return cudaGetLastError();
@@ -155,15 +191,18 @@ cudaError_t upward_p(Ctx &c, cudaStream_t st) {
 template <int P>
 cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st) {
   const int T = 128;
-  for (int l = 0; l + 1 < c.nlevels; ++l) {
-    int64_t lo = c.level_start[l], cnt = c.level_start[l + 1] - lo;
-    k_l2l<P><<<blocks_for(8 * cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm,
-                                                   hfmm::P<float>(c.L));
+  const LevelLoop lv(c);
+  for (int l = 0; l + 1 < lv.levels; ++l) {
+    int64_t lo, cnt;
+    lv.extent(c, l, lo, cnt);
+    k_l2l<P><<<lv.grid(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<uint4>(c.cell), hfmm::P<int2>(c.kids), c.ldm,
+                                            hfmm::P<float>(c.L), lv.tz, l);
     note_launch();
   }
   k_l2p<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell),
                                                    hfmm::P<uint2>(c.range), hfmm::P<float4>(c.pm4), hfmm::P<uint32_t>(c.idx), c.n,
-                                                   (float)c.prm.box, (float)c.prm.G, c.ldm, hfmm::P<float>(c.L), acc);
+                                                   (float)c.prm.box, (float)c.prm.G, c.ldm, hfmm::P<float>(c.L), acc,
+                                                   lv.tz);
   note_launch();
   return cudaGetLastError();
 }

@@ -134,8 +134,10 @@ template <int P, int G, int S>
 __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_m2l(int64_t nn, const uint4 *__restrict__ cell,
                                              const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
                                              const uint64_t *__restrict__ lst, const float *__restrict__ M,
-                                             float *__restrict__ L, int ldm, float inv_rs) {
+                                             float *__restrict__ L, int ldm, float inv_rs,
+                                             const TreeState *tz) {
   extern __shared__ float sm[];
+  nn = tree_nodes(tz, nn);  // graph mode: the node count from the device tree state
   // per warp: p >= 7 the staged multipoles (32 x NC), else the reduction transpose (32 x (NC + 1))
   float *wsm = sm + (threadIdx.x >> 5) * (M2LSlices<P>::kSmem ? ncoef(P) * 32 : 32 * (ncoef(P) + 1));
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -187,7 +189,8 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
   // the entries [mid, end) of each sink: pairs outside the operator table
   k_m2l<P, G, S><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<uint4>(c.cell), hfmm::P<uint32_t>(c.m2l_mid),
                                     hfmm::P<uint32_t>(c.m2l_end), hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M),
-                                    hfmm::P<float>(c.L), c.ldm, inv_rs);
+                                    hfmm::P<float>(c.L), c.ldm, inv_rs,
+                                    c.graph_tree ? hfmm::P<TreeState>(c.tstate) : nullptr);
   note_launch();
   return cudaGetLastError();
 }

@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
                                                 const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
                                                 const uint32_t *__restrict__ perm, int64_t n, float box, PairFit2 fit,
                                                 float G, float *__restrict__ acc_out,
-                                                unsigned long long *__restrict__ ctr) {
+                                                unsigned long long *__restrict__ ctr, const TreeState *tz) {
   extern __shared__ float4 p2p_smem[];
+  nl = tree_leaves(tz, nl);  // graph mode: the leaf count from the device tree state
   // per warp: the 32 list entries of the pending fill (first particle, exclusive
   // candidate offset, leaf-centre offset in the sink's frame), each candidate's
   // entry, and the chunk's sink bounding box (lo xyz, hi xyz)
@@ -384,7 +385,8 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   kern<<<g, T, dyn, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
-                        (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr);
+                        (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr,
+                        c.graph_tree ? P<TreeState>(c.tstate) : nullptr);
   note_launch();
   return cudaGetLastError();
 }

@@ -14,9 +14,9 @@
 // Phi = sum_j m_j psi(x - x_j), as for the short-range pair force.
 //
 // The mass assignment accumulates 64-bit fixed-point integers (mass * weight *
-// 2^s, s chosen from N * max|m| so no sum can overflow), so the mesh, and with
-// it every acceleration, is the same on every run whatever order the atomics
-// land in.  Mesh transforms use cuFFT (FP32, one R2C and a batch of three C2R).
+// 2^s, s chosen from N * max|m| so no sum can overflow; the weights in FP32
+// from FP64 cell offsets), so the mesh, and with it every acceleration, is the
+// same on every run whatever order the atomics land in.  Mesh transforms use cuFFT (FP32, one R2C and a batch of three C2R).
 #include <cufft.h>
 
 #include <cmath>
@@ -35,22 +35,25 @@ __global__ void k_mass_absmax(const float4 *__restrict__ pm4, int64_t n, unsigne
   if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
 }
 
-// Fixed-point scale 2^s with N * max|m| * 2^s <= 2^61.
-__device__ __forceinline__ double fixed_scale(const unsigned *mmax_bits, int64_t n) {
+// Fixed-point scale 2^s with N * max|m| * 2^s <= 2^61 (its exponent s).
+__device__ __forceinline__ int fixed_exponent(const unsigned *mmax_bits, int64_t n) {
   const double bound = (double)__uint_as_float(*mmax_bits) * (double)n;
-  if (!(bound > 0)) return 1.0;
+  if (!(bound > 0)) return 0;
   int e;
   frexp(bound, &e);  // bound < 2^e
-  return ldexp(1.0, 61 - e);
+  return 61 - e;
 }
 
+// Base mesh point and fractional offsets of particle i: u = x N_g / L in FP64
+// (wrapped positions: u in [0, N_g]), the offset u - floor(u) exact in FP64 and
+// then rounded once to FP32 (the CIC weights are formed in FP32).
 __device__ __forceinline__ void cic_setup(const double *__restrict__ xs, int64_t n, int64_t i, double to_mesh,
-                                          int ng, int (&i0)[3], double (&d)[3]) {
+                                          int ng, int (&i0)[3], float (&d)[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double u = xs[k * n + i] * to_mesh;  // wrapped positions: u in [0, ng]
-    double f = floor(u);
-    d[k] = u - f;
+    const double u = xs[k * n + i] * to_mesh;
+    const double f = floor(u);
+    d[k] = (float)(u - f);
     int c = (int)f;
     if (c >= ng) c -= ng;
     if (c < 0) c += ng;
@@ -58,39 +61,68 @@ __device__ __forceinline__ void cic_setup(const double *__restrict__ xs, int64_t
   }
 }
 
+// CIC mass assignment in 64-bit fixed point: corner value round(m 2^s w_x w_y w_z)
+// (FP32 product, one rounding to an integer).  Consecutive particles (Morton
+// order) mostly share their base mesh point: the lanes of a warp with the same
+// base point form groups (match on the point's index); when every group is a run
+// of adjacent lanes, each run adds its eight corner values with a segmented
+// shuffle sum (integers: exact, so the mesh is the same as with one atomic per
+// particle) and the run's first lane issues the eight atomics; otherwise every
+// lane issues its own.
 __global__ void k_deposit(const double *__restrict__ xs, const float4 *__restrict__ pm4, int64_t n, double to_mesh,
                           int ng, const unsigned *__restrict__ mmax, unsigned long long *__restrict__ q) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double S = fixed_scale(mmax, n);
-  int i0[3];
-  double d[3];
-  cic_setup(xs, n, i, to_mesh, ng, i0, d);
-  const double m = (double)pm4[i].w * S;
+  const int lane = threadIdx.x & 31;
+  const bool valid = i < n;  // whole warps stay for the warp-wide steps
+  int i0[3] = {0, 0, 0};
+  float d[3] = {0.f, 0.f, 0.f};
+  float ms = 0.f;
+  uint32_t key = 0xffffffffu - (uint32_t)lane;  // distinct keys (above any mesh index) for lanes past n
+  if (valid) {
+    cic_setup(xs, n, i, to_mesh, ng, i0, d);
+    ms = ldexpf(pm4[i].w, fixed_exponent(mmax, n));
+    key = ((uint32_t)i0[0] * (uint32_t)ng + (uint32_t)i0[1]) * (uint32_t)ng + (uint32_t)i0[2];
+  }
+  const unsigned grp = __match_any_sync(0xffffffffu, key);
+  const int first = __ffs(grp) - 1, last = 31 - __clz(grp);
+  const unsigned run = (unsigned)((1ull << (last - first + 1)) - 1ull);
+  const bool agg = __all_sync(0xffffffffu, (grp >> first) == run);
 #pragma unroll
   for (int ox = 0; ox < 2; ++ox) {
-    const double wx = ox ? d[0] : 1.0 - d[0];
+    const float wx = ox ? d[0] : 1.f - d[0];
     const int gx = i0[0] + ox == ng ? 0 : i0[0] + ox;
 #pragma unroll
     for (int oy = 0; oy < 2; ++oy) {
-      const double wy = oy ? d[1] : 1.0 - d[1];
+      const float wy = oy ? d[1] : 1.f - d[1];
       const int gy = i0[1] + oy == ng ? 0 : i0[1] + oy;
 #pragma unroll
       for (int oz = 0; oz < 2; ++oz) {
-        const double wz = oz ? d[2] : 1.0 - d[2];
+        const float wz = oz ? d[2] : 1.f - d[2];
         const int gz = i0[2] + oz == ng ? 0 : i0[2] + oz;
-        const long long v = __double2ll_rn(m * wx * wy * wz);
-        atomicAdd(q + ((int64_t)gx * ng + gy) * ng + gz, (unsigned long long)v);
+        long long v = valid ? __float2ll_rn(ms * (wx * wy * wz)) : 0ll;
+        unsigned long long *dst = q + ((int64_t)gx * ng + gy) * ng + gz;
+        if (agg) {
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_down_sync(0xffffffffu, v, o);
+            if (lane + o <= last) v += t;
+          }
+          if (valid && lane == first) atomicAdd(dst, (unsigned long long)v);
+        } else if (valid) {
+          atomicAdd(dst, (unsigned long long)v);
+        }
       }
     }
   }
 }
 
+// Mesh density: the fixed-point sums times 2^-s (exact scaling), rounded to FP32.
 __global__ void k_fixed_to_real(const unsigned long long *__restrict__ q, int64_t cells, const unsigned *mmax,
                                 int64_t n, float *__restrict__ rho) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= cells) return;
-  rho[g] = (float)((double)(long long)q[g] / fixed_scale(mmax, n));
+  const double inv = ldexp(1.0, -fixed_exponent(mmax, n));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < cells; g += stride)
+    rho[g] = (float)((double)(long long)q[g] * inv);
 }
 
 __device__ __forceinline__ float sincf_(float x) { return fabsf(x) < 1e-4f ? 1.f - x * x / 6.f : sinf(x) / x; }
@@ -137,21 +169,21 @@ __global__ void k_interpolate(const double *__restrict__ xs, const uint32_t *__r
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int i0[3];
-  double d[3];
+  float d[3];
   cic_setup(xs, n, i, to_mesh, ng, i0, d);
   const int64_t cells = (int64_t)ng * ng * ng;
   float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int ox = 0; ox < 2; ++ox) {
-    const float wx = (float)(ox ? d[0] : 1.0 - d[0]);
+    const float wx = ox ? d[0] : 1.f - d[0];
     const int gx = i0[0] + ox == ng ? 0 : i0[0] + ox;
 #pragma unroll
     for (int oy = 0; oy < 2; ++oy) {
-      const float wy = (float)(oy ? d[1] : 1.0 - d[1]);
+      const float wy = oy ? d[1] : 1.f - d[1];
       const int gy = i0[1] + oy == ng ? 0 : i0[1] + oy;
 #pragma unroll
       for (int oz = 0; oz < 2; ++oz) {
-        const float wz = (float)(oz ? d[2] : 1.0 - d[2]);
+        const float wz = oz ? d[2] : 1.f - d[2];
         const int gz = i0[2] + oz == ng ? 0 : i0[2] + oz;
         const int64_t g = ((int64_t)gx * ng + gy) * ng + gz;
         const float w = wx * wy * wz;
@@ -165,8 +197,9 @@ __global__ void k_interpolate(const double *__restrict__ xs, const uint32_t *__r
   for (int k = 0; k < 3; ++k) acc[k * n + o] += s[k];
 }
 
-__global__ void k_kick(float *__restrict__ vel, const float *__restrict__ acc, int64_t n3, float h) {
+__global__ void k_kick(float *__restrict__ vel, const float *__restrict__ acc, int64_t n3, float h, StepGuard g) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g.tree_overflow && (*g.tree_overflow || *g.walk_overflow || *g.walk_left)) return;
   if (i < n3) vel[i] = fmaf(h, acc[i], vel[i]);
 }
 
@@ -254,8 +287,7 @@ cudaError_t green_table_poly(Ctx &c) {
 
 }  // namespace
 
-cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
-  if (c.n == 0) return cudaSuccess;
+cudaError_t pm_prepare(Ctx &c) {
   const int ng = c.prm.pm_grid;
   const int64_t cells = (int64_t)ng * ng * ng, kcells = (int64_t)ng * ng * (ng / 2 + 1);
   cudaError_t e;
@@ -274,6 +306,16 @@ cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
       return e;
     c.pm_plan_c2r = p;
   }
+  if (c.prm.split == 1 && (e = green_table_poly(c)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  const int ng = c.prm.pm_grid;
+  const int64_t cells = (int64_t)ng * ng * ng, kcells = (int64_t)ng * ng * (ng / 2 + 1);
+  cudaError_t e;
+  if ((e = pm_prepare(c)) != cudaSuccess) return e;
   if ((e = fft_error(cufftSetStream(c.pm_plan_r2c, st))) != cudaSuccess) return e;
   if ((e = fft_error(cufftSetStream(c.pm_plan_c2r, st))) != cudaSuccess) return e;
 
@@ -287,13 +329,14 @@ cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
   k_mass_absmax<<<gm, T, 0, st>>>(P<float4>(c.pm4), c.n, mmax);
   k_deposit<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<float4>(c.pm4), c.n, to_mesh, ng, mmax,
                                               P<unsigned long long>(c.pm_q));
-  k_fixed_to_real<<<blocks_for(cells, T), T, 0, st>>>(P<unsigned long long>(c.pm_q), cells, mmax, c.n,
+  unsigned gc = blocks_for(cells, T);
+  if (gc > 152 * 16) gc = 152 * 16;
+  k_fixed_to_real<<<gc, T, 0, st>>>(P<unsigned long long>(c.pm_q), cells, mmax, c.n,
                                                       P<float>(c.pm_rho));
   note_launch(3);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = fft_error(cufftExecR2C(c.pm_plan_r2c, P<cufftReal>(c.pm_rho), P<cufftComplex>(c.pm_mk)))) != cudaSuccess)
     return e;
-  if (c.prm.split == 1 && (e = green_table_poly(c)) != cudaSuccess) return e;
   k_green<<<blocks_for(kcells, T), T, 0, st>>>(P<cufftComplex>(c.pm_mk), ng, (float)c.prm.box, (float)c.rs,
                                                (float)c.prm.G, c.prm.split == 1 ? P<float>(c.pm_gtab) : nullptr,
                                                P<cufftComplex>(c.pm_ak));
@@ -308,8 +351,12 @@ cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
 }
 
 cudaError_t kick(float *vel, const float *acc, int64_t n, double h, cudaStream_t st) {
+  return kick_guarded(vel, acc, n, h, StepGuard{}, st);
+}
+
+cudaError_t kick_guarded(float *vel, const float *acc, int64_t n, double h, StepGuard g, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_kick<<<blocks_for(3 * n, 256), 256, 0, st>>>(vel, acc, 3 * n, (float)h);
+  k_kick<<<blocks_for(3 * n, 256), 256, 0, st>>>(vel, acc, 3 * n, (float)h, g);
   note_launch();
   return cudaGetLastError();
 }

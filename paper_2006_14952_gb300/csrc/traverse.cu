@@ -232,6 +232,7 @@ struct TravBufs {
   uint32_t *rcnt_m, *rcnt_p;            // per sink: runs recorded so far (one per level at most)
   unsigned long long *btot;             // per-block partial sums (4 per block)
   unsigned long long capF, capS, capM, capP, capR;
+  const TreeState *tz;                  // graph mode: the device tree state (else null)
 };
 
 constexpr int kTT = 256;  // threads of the traversal kernel
@@ -362,6 +363,10 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
   __shared__ uint32_t *cmap, *nmap, *segs, *nsegs;
   __shared__ unsigned long long *sst, *nsst;
   __shared__ unsigned long long nf, nseg, nm, np, nrm, nrp, items;
+  if (B.tz && B.tz->overflow) {  // graph mode, the tree did not fit: no walk (every block leaves here)
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->overflow = 3;
+    return;
+  }
   if (kNet) mlp_stage(m.w, sw);
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
   const unsigned nb = gridDim.x, bid = blockIdx.x;
@@ -936,6 +941,7 @@ cudaError_t walk_launch(Ctx &c, const WalkPlan &w, cudaStream_t st) {
   B.capM = c.cap_m2l;
   B.capP = c.cap_p2p;
   B.capR = c.cap_run;
+  B.tz = c.graph_tree ? P<TreeState>(c.tstate) : nullptr;
   int max_iters = 2 * kDepth + 6;
   Mac m = w.m;
   const bool net = m.mode == 1;
@@ -1044,6 +1050,14 @@ cudaError_t sort_lists_prepare(Ctx &c) {
   if ((e = ensure(c.tmp2, nr * 20 + nn * 4 + 64)) != cudaSuccess) return e;
   const size_t most = nr > nn ? nr : nn;
   return ensure(c.offs, ((most + 4095) / 1024 + 1) * sizeof(uint64_t));  // scan block sums, with room
+}
+
+StepGuard step_guard(Ctx &c) {
+  StepGuard g;
+  g.tree_overflow = &P<TreeState>(c.tstate)->overflow;
+  g.walk_overflow = &walk_state(c)->overflow;
+  g.walk_left = &walk_state(c)->nf;
+  return g;
 }
 
 // Device address of the run counts the walk recorded (M2L, P2P), for the list

@@ -37,9 +37,9 @@ __global__ void k_gather(const double *__restrict__ pos, const uint32_t *__restr
 __global__ void k_leaf_offsets(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
                                const uint2 *__restrict__ range, const double *__restrict__ xs,
                                const float *__restrict__ mass, const uint32_t *__restrict__ perm, int64_t n,
-                               double box, float4 *__restrict__ pm4) {
+                               double box, float4 *__restrict__ pm4, const TreeState *tz) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nl) return;
+  if (t >= tree_leaves(tz, nl)) return;
   uint32_t k = leaves[t];
   uint4 c = cell[k];
   uint2 r = range[k];
@@ -49,12 +49,6 @@ __global__ void k_leaf_offsets(const uint32_t *__restrict__ leaves, int64_t nl, 
     pm4[i] = make_float4((float)(xs[i] - zx), (float)(xs[n + i] - zy), (float)(xs[2 * n + i] - zz), mass[perm[i]]);
   }
 }
-
-struct TreeState {
-  unsigned long long total, nleaves;
-  int nlevels, overflow;
-  unsigned long long level_start[kDepth + 3];
-};
 
 constexpr int kBT = 256;
 
@@ -70,7 +64,7 @@ __global__ void __launch_bounds__(kBT) k_tree_levels(const uint64_t *__restrict_
                                                      int2 *__restrict__ kids, uint32_t *__restrict__ leaves,
                                                      unsigned long long capN, uint32_t *__restrict__ nk,
                                                      uint32_t *__restrict__ bnd, unsigned long long *__restrict__ btot,
-                                                     TreeState *__restrict__ st) {
+                                                     TreeState *__restrict__ st, int max_levels) {
   cg::grid_group grid = cg::this_grid();
   __shared__ unsigned long long lo, cnt, total, nleaves;
   __shared__ unsigned long long wsum[kBT / 32][2], pre[2], all[2], run[2];
@@ -168,7 +162,8 @@ __global__ void __launch_bounds__(kBT) k_tree_levels(const uint64_t *__restrict_
     }
     __syncthreads();
     const unsigned long long Cn = all[0], Ln = all[1];
-    if (T0 + Cn > capN) {
+    // node capacity, or (graph mode) more levels than the host sized its level loops for
+    if (T0 + Cn > capN || (Cn > 0 && level + 2 > max_levels)) {
       if (bid == 0 && tid == 0) st->overflow = 1;
       break;  // every block takes the same decision
     }
@@ -323,10 +318,10 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
     int2 *kd = P<int2>(c.kids);
     uint32_t *lv = P<uint32_t>(c.leaves), *nkp = P<uint32_t>(c.nkids), *bd = P<uint32_t>(c.koff);
     unsigned long long *bt = P<unsigned long long>(c.bounds);
-    int lm = c.prm.leaf_max;
+    int lm = c.prm.leaf_max, ml = kDepth + 1;
     int64_t nn = n;
     void *args[] = {(void *)&key, (void *)&nn, (void *)&lm, (void *)&cl, (void *)&rg, (void *)&kd, (void *)&lv,
-                    (void *)&capN, (void *)&nkp, (void *)&bd, (void *)&bt, (void *)&dst};
+                    (void *)&capN, (void *)&nkp, (void *)&bd, (void *)&bt, (void *)&dst, (void *)&ml};
     TRY(cudaLaunchCooperativeKernel((const void *)k_tree_levels, dim3(nb), dim3(kBT), args, 0, st));
     note_launch();
     TRY(cudaMemcpyAsync(c.h_pinned, dst, sizeof(TreeState), cudaMemcpyDeviceToHost, st));
@@ -343,13 +338,116 @@ cudaError_t build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, 
   if (total >= ((int64_t)1 << kSinkBits)) return cudaErrorInvalidValue;  // mapped to HFMM_ERR_CAPACITY
   k_leaf_offsets<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell),
                                                          P<uint2>(c.range), P<double>(c.xs), mass, perm, n,
-                                                         c.prm.box, P<float4>(c.pm4));
+                                                         c.prm.box, P<float4>(c.pm4), nullptr);
   note_launch();
   TRY(cudaGetLastError());
   if (c.prm.profile & 1) cudaEventRecord(c.ev[2], st);
   c.have_tree = true;
   return cudaSuccess;
 #undef TRY
+}
+
+// Graph mode (a step captured as one graph): every buffer of the build sized
+// for n particles and the node capacity (outside the capture) ...
+cudaError_t build_tree_prepare(Ctx &c, int64_t n) {
+  cudaError_t e;
+#define TRY(x)                      \
+  do {                              \
+    e = (x);                        \
+    if (e != cudaSuccess) return e; \
+  } while (0)
+  TRY(ensure(c.key, n * 8));
+  TRY(ensure(c.key_alt, n * 8));
+  TRY(ensure(c.idx, n * 4));
+  TRY(ensure(c.idx_alt, n * 4));
+  TRY(ensure(c.xs, n * 24));
+  TRY(ensure(c.pm4, n * 16));
+  TRY(ensure(c.tmp, radix_sort_scratch_bytes((size_t)n)));
+  if (c.cap_nodes < (uint64_t)(2 * n / (c.prm.leaf_max > 1 ? c.prm.leaf_max : 1) + 64))
+    c.cap_nodes = (uint64_t)(2 * n / (c.prm.leaf_max > 1 ? c.prm.leaf_max : 1) + 64);
+  const unsigned long long capN = c.cap_nodes;
+  TRY(ensure(c.cell, capN * sizeof(uint4)));
+  TRY(ensure(c.range, capN * sizeof(uint2)));
+  TRY(ensure(c.kids, capN * sizeof(int2)));
+  TRY(ensure(c.leaves, capN * sizeof(uint32_t)));
+  TRY(ensure(c.nkids, capN * sizeof(uint32_t)));
+  TRY(ensure(c.koff, capN * 9 * sizeof(uint32_t)));
+  TRY(ensure(c.tstate, sizeof(TreeState)));
+  // levels the graph's level loops cover: the last tree's and two more
+  if (c.cap_levels < c.nlevels + 2) c.cap_levels = c.nlevels + 2;
+  if (c.cap_levels > kDepth + 1) c.cap_levels = kDepth + 1;
+  int dev = 0, nsm = 0;
+  TRY(cudaGetDevice(&dev));
+  TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  TRY(ensure(c.bounds, (size_t)nsm * 2 * 2 * sizeof(unsigned long long)));
+  return cudaSuccess;
+#undef TRY
+}
+
+// ... and the build enqueued with no read-back: the sizes stay in the device
+// state (c.tstate), which the later kernels of the graph read; a node capacity
+// overflow shows there too and makes them treat the tree as empty.
+cudaError_t build_tree_launch(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st) {
+  cudaError_t e;
+  const int T = 256;
+  const double inv_pow2 = box_inverse_if_pow2(c.prm.box);
+  k_keys<<<blocks_for(n, T), T, 0, st>>>(pos, n, c.prm.box, inv_pow2, P<uint64_t>(c.key), P<uint32_t>(c.idx));
+  note_launch();
+  bool alt = false;
+  if ((e = radix_sort_u64(P<uint64_t>(c.key), P<uint32_t>(c.idx), P<uint64_t>(c.key_alt), P<uint32_t>(c.idx_alt), n,
+                          0, 63, &alt, c.tmp, st)) != cudaSuccess)
+    return e;
+  if (alt) {
+    std::swap(c.key, c.key_alt);
+    std::swap(c.idx, c.idx_alt);
+  }
+  uint64_t *key = P<uint64_t>(c.key);
+  uint32_t *perm = P<uint32_t>(c.idx);
+  k_gather<<<blocks_for(n, T), T, 0, st>>>(pos, perm, n, c.prm.box, inv_pow2, P<double>(c.xs));
+  note_launch();
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_levels, kBT, 0)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const unsigned nb = (unsigned)(nsm * (per_sm < 2 ? per_sm : 2));
+  TreeState *dst = P<TreeState>(c.tstate);
+  if ((e = cudaMemsetAsync(dst, 0, sizeof(TreeState), st)) != cudaSuccess) return e;
+  unsigned long long capN = c.cap_nodes;
+  uint4 *cl = P<uint4>(c.cell);
+  uint2 *rg = P<uint2>(c.range);
+  int2 *kd = P<int2>(c.kids);
+  uint32_t *lv = P<uint32_t>(c.leaves), *nkp = P<uint32_t>(c.nkids), *bd = P<uint32_t>(c.koff);
+  unsigned long long *bt = P<unsigned long long>(c.bounds);
+  int lm = c.prm.leaf_max, ml = c.cap_levels;
+  int64_t nn = n;
+  void *args[] = {(void *)&key, (void *)&nn, (void *)&lm, (void *)&cl, (void *)&rg, (void *)&kd, (void *)&lv,
+                  (void *)&capN, (void *)&nkp, (void *)&bd, (void *)&bt, (void *)&dst, (void *)&ml};
+  if ((e = cudaLaunchCooperativeKernel((const void *)k_tree_levels, dim3(nb), dim3(kBT), args, 0, st)) != cudaSuccess)
+    return e;
+  note_launch();
+  k_leaf_offsets<<<blocks_for(c.cap_nodes, T), T, 0, st>>>(P<uint32_t>(c.leaves), (int64_t)c.cap_nodes,
+                                                           P<uint4>(c.cell), P<uint2>(c.range), P<double>(c.xs),
+                                                           mass, perm, n, c.prm.box, P<float4>(c.pm4), dst);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// After the graph: the device state's sizes on the host.  False on an overflow
+// of the node or level capacity (both are then grown for the next capture).
+bool build_tree_finish(Ctx &c, const TreeState &hs) {
+  if (hs.overflow) {
+    // which limit it was is not recorded: grow both (the direct rebuild sizes them exactly)
+    c.cap_nodes *= 2;
+    c.cap_levels = c.cap_levels + 2 > kDepth + 1 ? kDepth + 1 : c.cap_levels + 2;
+    return false;
+  }
+  c.nlevels = hs.nlevels;
+  for (int l = 0; l <= hs.nlevels && l < kDepth + 3; ++l) c.level_start[l] = (int64_t)hs.level_start[l];
+  c.nnodes = (int64_t)hs.total;
+  c.nleaves = (int64_t)hs.nleaves;
+  c.have_tree = c.nnodes < ((int64_t)1 << kSinkBits);
+  return c.have_tree;
 }
 
 }  // namespace hfmm

@@ -50,7 +50,7 @@ class Stats(C.Structure):
                 ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
                 ("t_upward", C.c_float), ("t_traverse", C.c_float), ("t_lists", C.c_float), ("t_m2l", C.c_float),
                 ("t_l2l", C.c_float), ("t_p2p", C.c_float), ("nm2l_table", C.c_int64), ("frontier_pairs", C.c_int64),
-                ("traverse_walks", C.c_int64)]
+                ("traverse_walks", C.c_int64), ("step_graphs", C.c_int64), ("graph_captures", C.c_int64)]
 
 
 class HfmmError(RuntimeError):
