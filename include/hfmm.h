@@ -131,6 +131,17 @@ typedef struct {
                           segments, runs) of a new context: 0 = a guess scaled with n and leaf_max;
                           a small value makes the walk overflow and repeat with grown lists (the
                           lists come out the same either way) */
+  int sink_batches;    /* hfmm_short_range_forces in batches of sinks (0 = automatic: one batch
+                          while the first guess of the P2P list stays below 2^28 entries, else
+                          enough batches to keep each below that; 1..4096 = that many).  The walk
+                          takes the top four levels once, then each batch of sink cells (a
+                          contiguous Morton range, about equal frontier shares) walks to the
+                          leaves, and its lists are grouped and evaluated before the next batch
+                          reuses the list memory, so memory and the 32-bit list bounds apply per
+                          batch.  The lists hold the same entries, split by sink; a leaf above
+                          level 4 sums its entries in two groups (rounding differs from one batch
+                          in the last bits).  Not in graph mode; after a call in more than one
+                          batch the P2P / M2L lists cannot be exported. */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */
@@ -145,13 +156,16 @@ typedef struct {
   /* milliseconds, filled when profile bit 0 is set (else -1); t_l2l covers L2L and L2P.
      After a call in graph mode t_upward covers the whole graph (upward pass to P2P) and
      t_traverse, t_lists, t_m2l, t_l2l, t_p2p are -1; after a step run as one graph
-     t_upward covers the whole step and t_keys_sort, t_tree are -1 too. */
+     t_upward covers the whole step and t_keys_sort, t_tree are -1 too; after a call in
+     sink batches t_traverse covers everything after the upward pass and t_lists .. t_p2p
+     are -1. */
   float t_keys_sort, t_tree, t_upward, t_traverse, t_lists, t_m2l, t_l2l, t_p2p;
   int64_t nm2l_table;         /* M2L pairs served by the operator table (profile bit 1, else -1) */
   int64_t frontier_pairs;     /* cell pairs the traversal classified, over all levels */
   int64_t traverse_walks;     /* walks the last traversal took (1 + repeats after a list overflowed) */
   int64_t step_graphs;        /* hfmm_step calls launched as one graph by this context */
   int64_t graph_captures;     /* graphs this context captured and instantiated or updated */
+  int64_t sink_batches;       /* batches the last short-range call took */
 } hfmm_stats;
 
 typedef struct hfmm_ctx hfmm_ctx;

@@ -51,6 +51,7 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.tile_trav_blocks < 0 || p.tile_trav_blocks > 4) return why = "tile_trav_blocks must be in 0..4", false;
   if (p.use_graph != 0 && p.use_graph != 1) return why = "use_graph must be 0 or 1", false;
   if (p.list_init < 0) return why = "list_init must be >= 0", false;
+  if (p.sink_batches < 0 || p.sink_batches > 4096) return why = "sink_batches must be in 0..4096", false;
   if (p.tc_wait_polls < -1) return why = "tc_wait_polls must be >= -1", false;
   if (p.split != 0 && p.split != 1) return why = "split must be 0 (Gaussian) or 1 (polynomial)", false;
   if (p.split == 1 && (p.mac_mode != 0 || p.m2l_precision != 0 || p.m2l_tables != 0))
@@ -139,7 +140,8 @@ void for_each_buffer(Ctx &c, F f) {
                   &c.rp_cnt, &c.segpre, &c.ctot, &c.tstate, &c.rm_rank, &c.rp_rank, &c.rcnt_m, &c.rcnt_p,
                   &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
                   &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval, &c.lo_flag,
-                  &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr};
+                  &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr,
+                  &c.pacc, &c.tf_pairs, &c.tf_segs, &c.tf_sst};
   for (DBuf *b : bufs) f(*b);
 }
 
@@ -234,6 +236,8 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
   Ctx &c = h->c;
   c.have_tree = false;
   c.last_step_graph = false;
+  c.lists_split = false;
+  c.last_batches = 1;
   if (n < 0 || n > (int64_t)0x7fffffff) return fail(c, HFMM_ERR_ARG, "n must be in [0, 2^31)");
   if (n > 0 && (!pos || !mass)) return fail(c, HFMM_ERR_ARG, "null position or mass pointer");
   c.mass_ref = mass;
@@ -250,7 +254,7 @@ namespace {
 // tables, the geometric acceptance, one-sided P2P and no pair counting.
 bool graph_eligible(const Ctx &c) {
   return c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
-         !c.prm.p2p_mutual && !c.prm.m2l_tables;
+         !c.prm.p2p_mutual && !c.prm.m2l_tables && sink_batches_for(c) == 1;
 }
 
 // The whole short-range call captured as one CUDA graph on the context's own
@@ -343,6 +347,29 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   if ((c.prm.profile & 2) && (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 4, 0, 8, st)) != cudaSuccess)
     return cuda_fail(c, e, "memset counter");
   c.last_graph = false;
+  c.last_batches = 1;
+  c.lists_split = false;
+  if (const int nbatch = sink_batches_for(c); nbatch > 1) {
+    if (prof) cudaEventRecord(c.ev[3], st);
+    if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
+    if (prof) cudaEventRecord(c.ev[4], st);
+    if (c.prm.m2l_precision != 0 &&
+        (e = cudaMemsetAsync(P<uint64_t>(c.d_small) + 6, 0, 8, st)) != cudaSuccess)
+      return cuda_fail(c, e, "m2l status");
+    e = short_range_batched(c, acc, nbatch, st);
+    if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, kWalkLimit);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sink batches");
+    if (prof) cudaEventRecord(c.ev[9], st);
+    if (c.prm.m2l_precision != 0) {
+      int *status = reinterpret_cast<int *>(P<uint64_t>(c.d_small) + 6);
+      if ((e = cudaMemcpyAsync(c.h_pinned + 31, status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "m2l status");
+      if (*reinterpret_cast<int *>(c.h_pinned + 31) != 0)
+        return fail(c, HFMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait for MMA completion gave up");
+    }
+    return HFMM_OK;
+  }
   if (graph_eligible(c)) {
     bool ok = false;
     e = whole_call_graph(c, acc, st, prof, &ok);
@@ -616,6 +643,7 @@ int hfmm_interaction_counts(hfmm_ctx *h, int conventional, int64_t *out, void *s
   for (int i = 0; i < 4; ++i) out[i] = 0;
   if (c.n == 0) return HFMM_OK;
   cudaStream_t st = S(stream);
+  c.lists_split = false;
   c.count_walk = conventional ? 2 : 1;
   cudaError_t e = traverse(c, st);
   c.count_walk = 0;
@@ -649,6 +677,7 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   o->traverse_walks = c.traverse_walks;
   o->step_graphs = c.step_graphs;
   o->graph_captures = c.graph_updates + c.graph_instantiations;
+  o->sink_batches = c.last_batches;
   o->p2p_useful_pairs = -1;
   if ((c.prm.profile & 2) && c.n > 0) {
     unsigned long long u = 0;
@@ -663,6 +692,14 @@ int hfmm_get_stats(hfmm_ctx *h, hfmm_stats *o) {
   for (int i = 0; i < 8; ++i) {
     *t[i] = -1.f;
     if (c.last_step_graph && i < 2) continue;  // the build ran inside the step's graph
+    if (c.lists_split && i >= 2) {  // sink batches: upward, then everything else as one span
+      const int pr[2][2] = {{3, 4}, {4, 9}};
+      if (i <= 3 && (c.prm.profile & 1) && c.n > 0) {
+        float ms = -1.f;
+        if (cudaEventElapsedTime(&ms, c.ev[pr[i - 2][0]], c.ev[pr[i - 2][1]]) == cudaSuccess) *t[i] = ms;
+      }
+      continue;
+    }
     if (c.last_graph && ev_graph[i][0] >= 0 && (c.prm.profile & 1) && c.n > 0) {
       float ms = -1.f;
       if (cudaEventElapsedTime(&ms, c.ev[ev_graph[i][0]], c.ev[ev_graph[i][1]]) == cudaSuccess) *t[i] = ms;
@@ -685,6 +722,9 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
   size_t need = 0;
+  if (c.lists_split &&
+      (what == HFMM_EXPORT_P2P || what == HFMM_EXPORT_M2L || what == HFMM_EXPORT_M2L_ORDER))
+    return fail(c, HFMM_ERR_STATE, "the last call ran in sink batches: its lists were not kept");
   switch (what) {
     case HFMM_EXPORT_KEYS: need = c.n * 8; break;
     case HFMM_EXPORT_PERM: need = c.n * 4; break;

@@ -279,6 +279,11 @@ struct Ctx {
   int64_t traverse_walks = 0;  // walks of the last traversal (1 + repeats after an overflow)
   uint64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;  // traversal capacities (entries)
   int cap_levels = 0;  // graph mode: tree levels the level loops cover
+  double walk_share = 1.0;  // sink batches: the share of the walk one batch takes (first list guesses)
+  int last_batches = 1;     // sink batches of the last short-range call
+  bool lists_split = false; // the last short-range call's lists were evaluated in parts (not kept)
+  DBuf pacc;                // sink batches: P2P accelerations [3][n], added by L2P
+  DBuf tf_pairs, tf_segs, tf_sst;  // sink batches: the frontier the top levels leave
   DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
   DBuf m2l_mid;  // u32 [nnodes]: [beg, mid) table pairs, [mid, end) per-pair operator
 
@@ -371,8 +376,15 @@ cudaError_t m2l_pass_table(Ctx &c, int q, cudaStream_t st);
 // kernel's status word (d_small[6]) is 1 after a timed-out wait.
 bool m2l_tc_supported(int p);
 cudaError_t m2l_pass_tc(Ctx &c, int q, cudaStream_t st);
-// L2L top-down, then L2P writing the far-field accelerations in input order.
-cudaError_t downward(Ctx &c, float *acc, cudaStream_t st);
+// L2L top-down, then L2P writing the far-field accelerations in input order
+// (plus add[3][n], input order, when given).
+cudaError_t downward(Ctx &c, float *acc, cudaStream_t st, const float *add = nullptr);
+// The short-range call in sink batches (upward pass done by the caller; L must
+// be zero): the walk over the top levels, then per batch of sinks the rest of
+// the walk, list grouping, M2L and P2P (into c.pacc), then L2L and L2P + P2P.
+cudaError_t short_range_batched(Ctx &c, float *acc, int nbatch, cudaStream_t st);
+// The batches the next short-range call takes (sink_batches, or the automatic count).
+int sink_batches_for(const Ctx &c);
 // Long-range PM accelerations added to acc (input order); mesh buffers and
 // FFT plans are kept in the context (pm_release frees them).
 cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st);

@@ -125,7 +125,7 @@ template <int P>
 __global__ void k_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
                       const uint2 *__restrict__ range, const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm,
                       int64_t n, float box, float G, int ldm, const float *__restrict__ L, float *__restrict__ acc,
-                      const TreeState *tz) {
+                      const TreeState *tz, const float *__restrict__ add) {
   constexpr int NC = ncoef(P);
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tree_leaves(tz, nl)) return;
@@ -140,9 +140,15 @@ __global__ void k_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uin
     float ax = 0.f, ay = 0.f, az = 0.f;
     L2PBody<P>::run(q.x * inv_h, q.y * inv_h, q.z * inv_h, l, ax, ay, az);
     const uint32_t o = perm[i];
-    acc[o] = s * ax;
-    acc[n + o] = s * ay;
-    acc[2 * n + o] = s * az;
+    if (add) {  // sink batches: the P2P accelerations, added as P2P itself would add them
+      acc[o] = s * ax + add[o];
+      acc[n + o] = s * ay + add[n + o];
+      acc[2 * n + o] = s * az + add[2 * n + o];
+    } else {
+      acc[o] = s * ax;
+      acc[n + o] = s * ay;
+      acc[2 * n + o] = s * az;
+    }
   }
 }
 
@@ -189,7 +195,7 @@ cudaError_t upward_p(Ctx &c, cudaStream_t st) {
 }
 
 template <int P>
-cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st) {
+cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st, const float *add) {
   const int T = 128;
   const LevelLoop lv(c);
   for (int l = 0; l + 1 < lv.levels; ++l) {
@@ -202,7 +208,7 @@ cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st) {
   k_l2p<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves, hfmm::P<uint4>(c.cell),
                                                    hfmm::P<uint2>(c.range), hfmm::P<float4>(c.pm4), hfmm::P<uint32_t>(c.idx), c.n,
                                                    (float)c.prm.box, (float)c.prm.G, c.ldm, hfmm::P<float>(c.L), acc,
-                                                   lv.tz);
+                                                   lv.tz, add);
   note_launch();
   return cudaGetLastError();
 }
@@ -225,17 +231,17 @@ cudaError_t upward(Ctx &c, cudaStream_t st) {
 }
 
 // L2L top-down, then L2P (overwrites acc in input order; P2P adds to it).
-cudaError_t downward(Ctx &c, float *acc, cudaStream_t st) {
+cudaError_t downward(Ctx &c, float *acc, cudaStream_t st, const float *add) {
   if (c.nleaves == 0) return cudaSuccess;
   switch (c.p) {
-    case 1: return downward_p<1>(c, acc, st);
-    case 2: return downward_p<2>(c, acc, st);
-    case 3: return downward_p<3>(c, acc, st);
-    case 4: return downward_p<4>(c, acc, st);
-    case 5: return downward_p<5>(c, acc, st);
-    case 6: return downward_p<6>(c, acc, st);
-    case 7: return downward_p<7>(c, acc, st);
-    case 8: return downward_p<8>(c, acc, st);
+    case 1: return downward_p<1>(c, acc, st, add);
+    case 2: return downward_p<2>(c, acc, st, add);
+    case 3: return downward_p<3>(c, acc, st, add);
+    case 4: return downward_p<4>(c, acc, st, add);
+    case 5: return downward_p<5>(c, acc, st, add);
+    case 6: return downward_p<6>(c, acc, st, add);
+    case 7: return downward_p<7>(c, acc, st, add);
+    case 8: return downward_p<8>(c, acc, st, add);
   }
   return cudaErrorInvalidValue;
 }

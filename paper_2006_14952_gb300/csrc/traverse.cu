@@ -197,7 +197,7 @@ __device__ __forceinline__ Item mac_item(uint64_t e, bool valid, const uint4 *__
 }
 
 struct TravState {
-  unsigned long long nm2l, np2p, nf;
+  unsigned long long nm2l, np2p, nf, nseg;  // nf, nseg: the frontier left when the walk stopped
   int iters, overflow;
   int ovf_lists;                      // capacity overflow: bit 0 M2L, 1 P2P, 2 frontier, 3 segments, 4 runs
   unsigned long long need[5];         // entries those lists needed up to the level that overflowed
@@ -233,6 +233,11 @@ struct TravBufs {
   unsigned long long *btot;             // per-block partial sums (4 per block)
   unsigned long long capF, capS, capM, capP, capR;
   const TreeState *tz;                  // graph mode: the device tree state (else null)
+  // resume (sink batches): the walk starts from the frontier already in fa, seg_a,
+  // st_a and map_a (init_nf pairs in init_nseg segments) instead of the root,
+  // with level index iter0 for its first iteration
+  int resume, iter0;
+  unsigned long long init_nf, init_nseg;
 };
 
 constexpr int kTT = 256;  // threads of the traversal kernel
@@ -373,11 +378,13 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
   const unsigned long long gw = (unsigned long long)bid * kTW + wp, nw = (unsigned long long)nb * kTW;
   // the root against its 27 nearest periodic images, or (conventional) itself
   const unsigned nroot = m.conv ? 1u : 27u;
-  if (bid == 0 && tid < nroot) B.fa[tid] = pack_pair(0, 0, m.conv ? 13u : (uint32_t)tid);
-  if (bid == 0 && tid == 0) {
-    B.map_a[0] = 0;
-    B.seg_a[0] = 0;
-    B.st_a[0] = 0;
+  if (!B.resume) {
+    if (bid == 0 && tid < nroot) B.fa[tid] = pack_pair(0, 0, m.conv ? 13u : (uint32_t)tid);
+    if (bid == 0 && tid == 0) {
+      B.map_a[0] = 0;
+      B.seg_a[0] = 0;
+      B.st_a[0] = 0;
+    }
   }
   if (tid == 0) {
     cur = B.fa;
@@ -388,8 +395,8 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
     nsegs = B.seg_b;
     sst = B.st_a;
     nsst = B.st_b;
-    nf = nroot;
-    nseg = 1;
+    nf = B.resume ? B.init_nf : nroot;
+    nseg = B.resume ? B.init_nseg : 1;
     nm = np = nrm = nrp = items = 0;
   }
   __syncthreads();
@@ -573,14 +580,14 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
         }
         if (tv[1] > 0) {
           const unsigned long long r = nrm + run[2] + ex[2];
-          B.rm_key[r] = ((unsigned long long)sink << 8) | (unsigned)iter;
+          B.rm_key[r] = ((unsigned long long)sink << 8) | (unsigned)(B.iter0 + iter);
           B.rm_beg[r] = nm + pv[1];
           B.rm_cnt[r] = (uint32_t)tv[1];
           B.rm_rank[r] = B.rcnt_m[sink]++;  // a sink has one segment per level: no other writer
         }
         if (tv[2] > 0) {
           const unsigned long long r = nrp + run[3] + ex[3];
-          B.rp_key[r] = ((unsigned long long)sink << 8) | (unsigned)iter;
+          B.rp_key[r] = ((unsigned long long)sink << 8) | (unsigned)(B.iter0 + iter);
           B.rp_beg[r] = np + pv[2];
           B.rp_cnt[r] = (uint32_t)tv[2];
           B.rp_rank[r] = B.rcnt_p[sink]++;
@@ -734,6 +741,7 @@ __global__ void __launch_bounds__(kTT, 4) k_traverse(const uint4 *__restrict__ c
     st->nm2l = nm;
     st->np2p = np;
     st->nf = nf;
+    st->nseg = nseg;
     st->iters = iter;
     st->items = items;
     st->nrun_m = nrm;
@@ -802,6 +810,12 @@ struct WalkPlan {
   unsigned nb;
 };
 
+// First guess of the P2P list's entries per particle (the scale of the walk_plan guesses).
+double p2p_guess_per_particle(const Ctx &c) {
+  const double lf = c.prm.leaf_max > 16 ? std::pow(16.0 / c.prm.leaf_max, 1.5) * 1.5 : 1.0;
+  return 128.0 * (lf < 1.0 ? lf : 1.0);
+}
+
 cudaError_t walk_plan(Ctx &c, WalkPlan &w) {
   cudaError_t e;
   Mac &m = w.m;
@@ -844,7 +858,7 @@ cudaError_t walk_plan(Ctx &c, WalkPlan &w) {
   // twice its size) and the walk is repeated.  A positive list_init replaces every
   // first guess (a test knob for the retry path).
   const double lf = c.prm.leaf_max > 16 ? std::pow(16.0 / c.prm.leaf_max, 1.5) * 1.5 : 1.0;
-  const double sc = lf < 1.0 ? lf : 1.0;
+  const double sc = (lf < 1.0 ? lf : 1.0) * c.walk_share;  // sink batches: one batch's share
   const uint64_t init = (uint64_t)c.prm.list_init;
   auto first_guess = [&](uint64_t guess) { return init > 0 ? init : guess; };
   const uint64_t g_front = first_guess((uint64_t)(sc * 64 * c.n + 1024));
@@ -902,8 +916,15 @@ TravState *walk_state(Ctx &c) {
   return reinterpret_cast<TravState *>(P<uint64_t>(c.d_small) + 8);
 }
 
+// Where a walk starts: the root (resume 0) or a frontier already in the
+// walk's first buffers (sink batches), and how many levels it may take.
+struct WalkStart {
+  int resume = 0, iter0 = 0, max_iters = 2 * kDepth + 6;
+  unsigned long long nf = 0, nseg = 0;
+};
+
 // Zero the counters and launch the cooperative walk (no allocation, no read-back).
-cudaError_t walk_launch(Ctx &c, const WalkPlan &w, cudaStream_t st) {
+cudaError_t walk_launch(Ctx &c, const WalkPlan &w, cudaStream_t st, const WalkStart &ws = WalkStart()) {
   cudaError_t e;
   TravState *dst = walk_state(c);
   if ((e = cudaMemsetAsync(c.rcnt_m.p, 0, (size_t)c.nnodes * 4, st)) != cudaSuccess) return e;
@@ -942,7 +963,11 @@ cudaError_t walk_launch(Ctx &c, const WalkPlan &w, cudaStream_t st) {
   B.capP = c.cap_p2p;
   B.capR = c.cap_run;
   B.tz = c.graph_tree ? P<TreeState>(c.tstate) : nullptr;
-  int max_iters = 2 * kDepth + 6;
+  B.resume = ws.resume;
+  B.iter0 = ws.iter0;
+  B.init_nf = ws.nf;
+  B.init_nseg = ws.nseg;
+  int max_iters = ws.max_iters;
   Mac m = w.m;
   const bool net = m.mode == 1;
   const void *kern = net ? (const void *)k_traverse<true> : (const void *)k_traverse<false>;
@@ -1294,6 +1319,193 @@ cudaError_t m2l_all(Ctx &c, cudaStream_t st) {
     if ((e = run(q)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
+}
+
+
+namespace {
+
+}  // namespace
+
+int sink_batches_for(const Ctx &c) {
+  if (c.prm.sink_batches > 0) return c.prm.sink_batches;
+  const double guess = p2p_guess_per_particle(c) * (double)c.n;
+  const double per = (double)(1u << 28);
+  return guess <= per ? 1 : (int)std::min(4096.0, std::ceil(guess / per));
+}
+
+namespace {
+
+// One batch's frontier: the pairs [f_lo, f_lo + nfb) and segments
+// [s_lo, s_lo + nsb) of the saved top-level frontier, rebased to the start of
+// the walk's first buffers (segment starts, and the segment of each sink).
+__global__ void k_batch_frontier(const uint64_t *__restrict__ tp, const uint32_t *__restrict__ tsegs,
+                                 const unsigned long long *__restrict__ tsst, unsigned long long f_lo,
+                                 unsigned long long nfb, unsigned long long s_lo, unsigned long long nsb,
+                                 uint64_t *__restrict__ fa, uint32_t *__restrict__ seg_a,
+                                 unsigned long long *__restrict__ st_a, uint32_t *__restrict__ map_a) {
+  const unsigned long long n = nfb > nsb ? nfb : nsb;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (i < nfb) fa[i] = tp[f_lo + i];
+    if (i < nsb) {
+      const uint32_t sk = tsegs[s_lo + i];
+      seg_a[i] = sk;
+      st_a[i] = tsst[s_lo + i] - f_lo;
+      map_a[sk] = (uint32_t)i;
+    }
+  }
+}
+
+// the levels the walk takes before its frontier is split into batches: up to
+// 8^4 sink cells (and shallower leaves), enough to balance a few dozen batches
+constexpr int kBatchLevel = 4;
+
+}  // namespace
+
+// Sink batches.  The walk is sink-major: at each level its frontier is grouped
+// into segments, one per sink cell, in Morton order of the sinks, and a
+// segment's pairs are contiguous.  A batch of sinks is therefore a contiguous
+// run of segments of the frontier, and the walk below it touches no other
+// sink.  The walk first takes the top levels alone; what it emitted there (M2L
+// to cells above the batch level, P2P of leaves above it) is grouped and
+// evaluated at once.  Its frontier is saved and cut into nbatch runs of about
+// equal pair counts; each run is copied into the walk's buffers, the walk
+// resumes from it to the leaves, and its lists are grouped and evaluated (M2L
+// into L, P2P into c.pacc); the next batch reuses the buffers, whose first
+// guesses are a batch's share.  The same pairs are classified as in one walk,
+// so the lists are the same entries, split by sink; a leaf above the batch
+// level gets its entries in two groups (top levels, then its batch), summed in
+// two steps.  Finally L2L, and L2P adds the P2P accelerations.
+cudaError_t short_range_batched(Ctx &c, float *acc, int nbatch, cudaStream_t st) {
+  cudaError_t e;
+#define TRY(x)                      \
+  do {                              \
+    e = (x);                        \
+    if (e != cudaSuccess) return e; \
+  } while (0)
+  const int64_t n = c.n;
+  TRY(ensure(c.pacc, (size_t)3 * n * sizeof(float)));
+  TRY(cudaMemsetAsync(c.pacc.p, 0, (size_t)3 * n * sizeof(float), st));
+  float *pacc = P<float>(c.pacc);
+  c.walk_share = 1.0 / nbatch;
+  WalkPlan w;
+  e = walk_plan(c, w);
+  c.walk_share = 1.0;
+  if (e != cudaSuccess) return e;
+  int64_t tot_m2l = 0, tot_p2p = 0, walks = 0, items = 0;
+  int iters = 0;
+  auto grow_lists = [&](const TravState &hs) {
+    auto grow = [](uint64_t want) { return want + want / 4 + 1024; };
+    auto up = [&](uint64_t &cap, int bit, int k) {
+      if (hs.ovf_lists & bit) cap = grow(std::max<uint64_t>(cap * 2, hs.need[k]));
+    };
+    up(c.cap_m2l, 1, 0);
+    up(c.cap_p2p, 2, 1);
+    up(c.cap_front, 4, 2);
+    up(c.cap_seg, 8, 3);
+    up(c.cap_run, 16, 4);
+  };
+  auto read_state = [&](TravState &hs) -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(c.h_pinned, walk_state(c), sizeof(TravState), cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    if (r == cudaSuccess) std::memcpy(&hs, c.h_pinned, sizeof(TravState));
+    return r;
+  };
+  // group and evaluate what one walk emitted (its sizes from the state)
+  auto evaluate = [&](const TravState &hs) -> cudaError_t {
+    c.nm2l = (int64_t)hs.nm2l;
+    c.np2p = (int64_t)hs.np2p;
+    c.nrun_m = (int64_t)hs.nrun_m;
+    c.nrun_p = (int64_t)hs.nrun_p;
+    tot_m2l += c.nm2l;
+    tot_p2p += c.np2p;
+    items += (int64_t)hs.items;
+    iters += hs.iters;
+    if (c.nm2l > (int64_t)UINT32_MAX || c.np2p > (int64_t)UINT32_MAX) return cudaErrorInvalidValue;
+    cudaError_t r = sort_lists(c, st);
+    if (r == cudaSuccess) r = m2l_all(c, st);
+    if (r == cudaSuccess) r = c.prm.p2p_mutual ? p2p_pass_mutual(c, pacc, st) : p2p_pass(c, pacc, st);
+    return r;
+  };
+  // ---- the top levels
+  TravState hs;
+  WalkStart top;
+  top.max_iters = kBatchLevel;
+  for (int attempt = 0;; ++attempt) {
+    if (attempt == 32) return cudaErrorInvalidValue;
+    ++walks;
+    TRY(walk_buffers(c, w.nb));
+    TRY(walk_launch(c, w, st, top));
+    TRY(read_state(hs));
+    if (hs.overflow == 2) return cudaErrorInvalidValue;
+    if (!hs.overflow) break;
+    grow_lists(hs);
+  }
+  const unsigned long long nf_top = hs.nf, ns_top = hs.nseg;
+  const bool odd = (hs.iters & 1) != 0;  // the frontier left is in the second buffers
+  // save the frontier before the evaluation reuses anything
+  if (nf_top > 0) {
+    TRY(ensure(c.tf_pairs, nf_top * 8));
+    TRY(ensure(c.tf_segs, ns_top * 4));
+    TRY(ensure(c.tf_sst, ns_top * 8));
+    TRY(cudaMemcpyAsync(c.tf_pairs.p, odd ? c.front_next.p : c.front.p, nf_top * 8, cudaMemcpyDeviceToDevice, st));
+    TRY(cudaMemcpyAsync(c.tf_segs.p, odd ? c.seg_b.p : c.seg_a.p, ns_top * 4, cudaMemcpyDeviceToDevice, st));
+    TRY(cudaMemcpyAsync(c.tf_sst.p, odd ? c.acc_b.p : c.acc_a.p, ns_top * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  TRY(evaluate(hs));
+  // ---- the batches: runs of segments with about equal pair counts
+  std::vector<unsigned long long> sst(ns_top);
+  if (ns_top > 0) {
+    TRY(cudaMemcpyAsync(sst.data(), c.tf_sst.p, ns_top * 8, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+  }
+  unsigned long long s_lo = 0;
+  int ran = 0;
+  for (int b = 0; b < nbatch && s_lo < ns_top; ++b, ++ran) {
+    const unsigned long long target = (unsigned long long)((double)nf_top * (b + 1) / nbatch);
+    unsigned long long s_hi = s_lo + 1;
+    while (s_hi < ns_top && (b == nbatch - 1 || sst[s_hi] < target)) ++s_hi;
+    const unsigned long long f_lo = sst[s_lo], f_hi = s_hi < ns_top ? sst[s_hi] : nf_top;
+    WalkStart ws;
+    ws.resume = 1;
+    ws.iter0 = kBatchLevel;
+    ws.max_iters = 2 * kDepth + 6 - kBatchLevel;
+    ws.nf = f_hi - f_lo;
+    ws.nseg = s_hi - s_lo;
+    for (int attempt = 0;; ++attempt) {
+      if (attempt == 32) return cudaErrorInvalidValue;
+      ++walks;
+      if (c.cap_front < ws.nf) c.cap_front = ws.nf + ws.nf / 4 + 1024;
+      if (c.cap_seg < ws.nseg) c.cap_seg = ws.nseg + ws.nseg / 4 + 1024;
+      TRY(walk_buffers(c, w.nb));
+      const int T = 256;
+      unsigned g = blocks_for(std::max(ws.nf, ws.nseg), T);
+      if (g > 152u * 8u) g = 152u * 8u;
+      k_batch_frontier<<<g, T, 0, st>>>(P<uint64_t>(c.tf_pairs), P<uint32_t>(c.tf_segs),
+                                        P<unsigned long long>(c.tf_sst), f_lo, ws.nf, s_lo, ws.nseg,
+                                        P<uint64_t>(c.front), P<uint32_t>(c.seg_a), P<unsigned long long>(c.acc_a),
+                                        P<uint32_t>(c.fseg));
+      note_launch();
+      TRY(cudaGetLastError());
+      TRY(walk_launch(c, w, st, ws));
+      TRY(read_state(hs));
+      if (hs.overflow == 2) return cudaErrorInvalidValue;
+      if (!hs.overflow) break;
+      grow_lists(hs);
+    }
+    if (hs.nf != 0) return cudaErrorInvalidValue;  // more levels than any octree
+    TRY(evaluate(hs));
+    s_lo = s_hi;
+  }
+  c.nm2l = tot_m2l;
+  c.np2p = tot_p2p;
+  c.traverse_walks = walks;
+  c.frontier_items = items;
+  c.traverse_iters = iters;
+  c.last_batches = ran > 1 ? ran : 1;
+  c.lists_split = true;  // the top levels' lists and each batch's were evaluated in turn
+  return downward(c, acc, st, pacc);
+#undef TRY
 }
 
 }  // namespace hfmm

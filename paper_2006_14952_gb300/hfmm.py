@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("m2l_precision", C.c_int), ("profile", C.c_int), ("m2l_tables", C.c_int),
                 ("tile_p2p_stage", C.c_int), ("tile_p2p_blocks", C.c_int), ("tile_m2l_blocks", C.c_int),
                 ("tile_trav_blocks", C.c_int), ("use_graph", C.c_int), ("tc_wait_polls", C.c_int),
-                ("split", C.c_int), ("p2p_mutual", C.c_int), ("list_init", C.c_int)]
+                ("split", C.c_int), ("p2p_mutual", C.c_int), ("list_init", C.c_int),
+                ("sink_batches", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -50,7 +51,8 @@ class Stats(C.Structure):
                 ("t_keys_sort", C.c_float), ("t_tree", C.c_float),
                 ("t_upward", C.c_float), ("t_traverse", C.c_float), ("t_lists", C.c_float), ("t_m2l", C.c_float),
                 ("t_l2l", C.c_float), ("t_p2p", C.c_float), ("nm2l_table", C.c_int64), ("frontier_pairs", C.c_int64),
-                ("traverse_walks", C.c_int64), ("step_graphs", C.c_int64), ("graph_captures", C.c_int64)]
+                ("traverse_walks", C.c_int64), ("step_graphs", C.c_int64), ("graph_captures", C.c_int64),
+                ("sink_batches", C.c_int64)]
 
 
 class HfmmError(RuntimeError):
