@@ -133,14 +133,15 @@ typedef struct {
                           lists come out the same either way) */
   int sink_batches;    /* hfmm_short_range_forces in batches of sinks (0 = automatic: one batch
                           while the first guess of the P2P list stays below 2^28 entries, else
-                          enough batches to keep each below that; 1..4096 = that many).  The walk
-                          takes the top four levels once, then each batch of sink cells (a
-                          contiguous Morton range, about equal frontier shares) walks to the
+                          batches of about 2^27 guessed entries; 1..4096 = that many).  The walk
+                          takes the top levels once (4, 5 or 6 of them as the batches grow),
+                          then each batch of sink cells (a contiguous Morton range, about equal
+                          particle counts) walks to the
                           leaves, and its lists are grouped and evaluated before the next batch
                           reuses the list memory, so memory and the 32-bit list bounds apply per
                           batch.  The lists hold the same entries, split by sink; a leaf above
-                          level 4 sums its entries in two groups (rounding differs from one batch
-                          in the last bits).  Not in graph mode; after a call in more than one
+                          the split level sums its entries in two groups (rounding differs from
+                          one batch in the last bits).  Not in graph mode; after a call in more than one
                           batch the P2P / M2L lists cannot be exported. */
 } hfmm_params;
 

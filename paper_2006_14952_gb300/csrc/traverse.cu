@@ -1329,8 +1329,9 @@ namespace {
 int sink_batches_for(const Ctx &c) {
   if (c.prm.sink_batches > 0) return c.prm.sink_batches;
   const double guess = p2p_guess_per_particle(c) * (double)c.n;
-  const double per = (double)(1u << 28);
-  return guess <= per ? 1 : (int)std::min(4096.0, std::ceil(guess / per));
+  // one batch while the guess stays below 2^28 entries; beyond, batches of about 2^27
+  if (guess <= (double)(1u << 28)) return 1;
+  return (int)std::min(4096.0, std::ceil(guess / (double)(1u << 27)));
 }
 
 namespace {
@@ -1356,9 +1357,17 @@ __global__ void k_batch_frontier(const uint64_t *__restrict__ tp, const uint32_t
   }
 }
 
+// Particles in each segment's sink cell (the batches are balanced on them).
+__global__ void k_seg_counts(const uint32_t *__restrict__ segs, unsigned long long ns, const uint2 *__restrict__ range,
+                             uint32_t *__restrict__ cnt) {
+  const unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < ns) cnt[s] = range[segs[s]].y;
+}
+
 // the levels the walk takes before its frontier is split into batches: up to
-// 8^4 sink cells (and shallower leaves), enough to balance a few dozen batches
-constexpr int kBatchLevel = 4;
+// 8^4 sink cells (and shallower leaves) for a few batches, 8^5 or 8^6 for more,
+// so that one cell holds a small share of a batch
+inline int batch_level(int nbatch) { return 4 + (nbatch > 8 ? 1 : 0) + (nbatch > 64 ? 1 : 0); }
 
 }  // namespace
 
@@ -1368,8 +1377,8 @@ constexpr int kBatchLevel = 4;
 // run of segments of the frontier, and the walk below it touches no other
 // sink.  The walk first takes the top levels alone; what it emitted there (M2L
 // to cells above the batch level, P2P of leaves above it) is grouped and
-// evaluated at once.  Its frontier is saved and cut into nbatch runs of about
-// equal pair counts; each run is copied into the walk's buffers, the walk
+// evaluated at once.  Its frontier is saved and cut into nbatch runs whose sink
+// cells hold about equal particle counts; each run is copied into the walk's buffers, the walk
 // resumes from it to the leaves, and its lists are grouped and evaluated (M2L
 // into L, P2P into c.pacc); the next batch reuses the buffers, whose first
 // guesses are a batch's share.  The same pairs are classified as in one walk,
@@ -1430,7 +1439,8 @@ cudaError_t short_range_batched(Ctx &c, float *acc, int nbatch, cudaStream_t st)
   // ---- the top levels
   TravState hs;
   WalkStart top;
-  top.max_iters = kBatchLevel;
+  const int split_level = batch_level(nbatch);
+  top.max_iters = split_level;
   for (int attempt = 0;; ++attempt) {
     if (attempt == 32) return cudaErrorInvalidValue;
     ++walks;
@@ -1453,23 +1463,31 @@ cudaError_t short_range_batched(Ctx &c, float *acc, int nbatch, cudaStream_t st)
     TRY(cudaMemcpyAsync(c.tf_sst.p, odd ? c.acc_b.p : c.acc_a.p, ns_top * 8, cudaMemcpyDeviceToDevice, st));
   }
   TRY(evaluate(hs));
-  // ---- the batches: runs of segments with about equal pair counts
-  std::vector<unsigned long long> sst(ns_top);
+  // ---- the batches: runs of segments with about equal particle counts in their sinks
+  std::vector<unsigned long long> sst(ns_top), cum(ns_top + 1, 0);
   if (ns_top > 0) {
+    std::vector<uint32_t> cnt(ns_top);
+    TRY(ensure(c.tmp2, ns_top * 4));
+    k_seg_counts<<<blocks_for(ns_top, 256), 256, 0, st>>>(P<uint32_t>(c.tf_segs), ns_top, P<uint2>(c.range),
+                                                           P<uint32_t>(c.tmp2));
+    note_launch();
+    TRY(cudaGetLastError());
+    TRY(cudaMemcpyAsync(cnt.data(), c.tmp2.p, ns_top * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(sst.data(), c.tf_sst.p, ns_top * 8, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
+    for (unsigned long long q = 0; q < ns_top; ++q) cum[q + 1] = cum[q] + cnt[q];
   }
   unsigned long long s_lo = 0;
   int ran = 0;
   for (int b = 0; b < nbatch && s_lo < ns_top; ++b, ++ran) {
-    const unsigned long long target = (unsigned long long)((double)nf_top * (b + 1) / nbatch);
+    const unsigned long long target = (unsigned long long)((double)cum[ns_top] * (b + 1) / nbatch);
     unsigned long long s_hi = s_lo + 1;
-    while (s_hi < ns_top && (b == nbatch - 1 || sst[s_hi] < target)) ++s_hi;
+    while (s_hi < ns_top && (b == nbatch - 1 || cum[s_hi] < target)) ++s_hi;
     const unsigned long long f_lo = sst[s_lo], f_hi = s_hi < ns_top ? sst[s_hi] : nf_top;
     WalkStart ws;
     ws.resume = 1;
-    ws.iter0 = kBatchLevel;
-    ws.max_iters = 2 * kDepth + 6 - kBatchLevel;
+    ws.iter0 = split_level;
+    ws.max_iters = 2 * kDepth + 6 - split_level;
     ws.nf = f_hi - f_lo;
     ws.nseg = s_hi - s_lo;
     for (int attempt = 0;; ++attempt) {

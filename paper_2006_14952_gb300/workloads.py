@@ -60,9 +60,11 @@ CONFIGS = {
     # learned-acceptance evaluation set, N = 128^3, 85% in 2000 NFW haloes (solved like nfw-2m)
     "nfw85-2m": Config("nfw85-2m", 128 ** 3, 128, "nfw", halo_count=2000, halo_frac=0.85, order=6, theta=0.35,
                        leaf_max=48, seed=1004),
-    # large: 512^3 Zel'dovich + 4000 haloes (50%)
+    # large: 512^3 Zel'dovich + 4000 haloes (50%), PM 512^3; solved like nfw-2m (leaves
+    # of 48, theta 0.35, p 6: the settings that meet an RMS force error of 1e-4), in
+    # sink batches (its lists run to billions of entries)
     "zeldovich-134m": Config("zeldovich-134m", 512 ** 3, 512, "zeldovich", halo_count=4000, halo_frac=0.5,
-                             seed=1005),
+                             order=6, theta=0.35, leaf_max=48, seed=1005),
 }
 
 
