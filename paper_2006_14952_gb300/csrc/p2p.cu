@@ -17,14 +17,13 @@
 // below R_c; the others contribute nothing).  Lanes are split as (sink i,
 // stream s): with cs sinks in the chunk, S = 32 / cs streams walk the buffer,
 // so small leaves still keep the warp busy; the streams are added in a fixed
-// order at the end (deterministic).  Most chunks are split in two halves
-// instead: each lane holds one sink of each half and evaluates both against
-// every staged source pair it loads (S = 32 / ceil(cs / 2) streams), where that
-// takes fewer issue slots per source pair than one sink per lane.
+// order at the end (deterministic).  Chunks of 11, 12 or 17..20 sinks, where
+// S = 32 / cs leaves many lanes idle, are split in two halves instead: each lane
+// holds one sink of each half and evaluates both against every staged source
+// pair, which doubles the streams.
 //
 // The evaluation buffer holds sources in pairs, {-x0, -x1, -y0, -y1}
-// {-z0, -z1, -w0, -w1} (w = mass), stream-major (each stream's pairs in one
-// contiguous run), so each lane evaluates two pairs per step
+// {-z0, -z1, -w0, -w1} (w = mass), so each lane evaluates two pairs per step
 // with the packed FP32x2 add / multiply / fma of sm_100+ (half the FP32
 // instructions; rsqrt and exp2 stay per element).  An odd tail is padded with a
 // massless source far outside the cut-off.
@@ -39,13 +38,8 @@
 namespace hfmm {
 namespace {
 
-// source pairs per step of the evaluation loops (one sink per lane, two sinks
-// per lane): eight independent pair chains in flight either way (128 registers,
-// no spills, at two blocks of 256 threads per SM)
-constexpr int kU1 = 8, kU2 = 8;
 
-
-// kCap: source particles per fill (even); dynamic shared memory: 8 x (2 kCap + 64) float4.
+// kCap: source particles per fill (even); dynamic shared memory: 2 x 8 x kCap float4.
 // kSplit 0: the Gaussian truncation S(x) above; 1: the polynomial truncation of
 // Sec. 5, a = -m (1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5)) r, no exp2 and no
 // fitted factor (see hfmm_params.split).
@@ -67,8 +61,8 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
   __shared__ uint8_t e_own[8][kCap];
   __shared__ float e_box[8][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float4 *raw = p2p_smem + wid * kCap;                      // the pending fill, as copied
-  float4 *buf = p2p_smem + 8 * kCap + wid * (kCap + 64);    // the fill being evaluated, in pairs (stream-major)
+  float4 *raw = p2p_smem + wid * kCap;            // the pending fill, as copied
+  float4 *buf = p2p_smem + (8 + wid) * kCap;      // the fill being evaluated, in pairs
   float *bf = reinterpret_cast<float *>(buf);
   const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(raw);
   // cull threshold: R_c^2 (1 + 2^-12), far above the FP32 rounding of either distance
@@ -181,23 +175,13 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
     for (uint32_t cbase = r.x; cbase < r.x + r.y; cbase += 32) {
       const uint32_t rem = r.x + r.y - cbase;
       const int cs = rem < 32 ? (int)rem : 32;
-      // one sink per lane, or two (one from each half of the chunk: a loaded
-      // source pair then serves both), whichever takes fewer issue slots per
-      // staged source pair: (load + calls) / streams, with a pair evaluation about
-      // ten times a load and its loop share
+      // two sinks per lane (one from each half of the chunk) where that doubles the
+      // streams: cs in {11, 12, 17..20}; otherwise one sink per lane
       const int c2 = (cs + 1) >> 1;
-      const bool two = cs > 1 && 21 * (32 / cs) < 11 * (32 / c2);
+      const bool two = 2 * (32 / cs) < 32 / c2;
       const int cl = two ? c2 : cs;  // sinks per lane group
       const int S = 32 / cl, stream = lane / cl, il = lane % cl;
       const bool active = stream < S;
-      // the evaluation buffer is stream-major: pair kk goes to stream kk % S at
-      // position kk / S, in a run of lmax pairs per stream (kk / S by a multiply)
-      const uint64_t magic = 0x100000000ull / (uint64_t)S + (0x100000000ull % (uint64_t)S ? 1u : 0u);
-      const uint32_t lmax = (uint32_t)((kCap / 2 + S - 1) / S);
-      auto epos = [&](uint32_t kk) -> uint32_t {
-        const uint32_t j = (uint32_t)(((uint64_t)kk * magic) >> 32);
-        return (kk - j * (uint32_t)S) * lmax + j;
-      };
       const float4 xi = pm4[cbase + il];
       const bool hasb = two && il + c2 < cs;
       const float4 xib = hasb ? pm4[cbase + il + c2] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
@@ -275,7 +259,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
               const unsigned kb = __ballot_sync(0xffffffffu, keep[u]);
               if (keep[u]) {
                 const uint32_t slot = kept + (uint32_t)__popc(kb & ((1u << lane) - 1u));
-                float *a = bf + epos(slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
+                float *a = bf + (slot >> 1) * 8 + (slot & 1);  // pair slot/2: {x0 x1 y0 y1} {z0 z1 w0 w1}
                 a[0] = -v[u].x;
                 a[2] = -v[u].y;
                 a[4] = -v[u].z;
@@ -286,7 +270,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
           }
         }
         if ((kept & 1) && lane == 0) {  // pad: massless, far beyond the cut-off
-          float *a = bf + epos(kept >> 1) * 8 + 1;
+          float *a = bf + (kept >> 1) * 8 + 1;
           a[0] = -1e18f;
           a[2] = -1e18f;
           a[4] = -1e18f;
@@ -302,15 +286,11 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
           const float2 dy = __fadd2_rn(py, make_float2(A.z, A.w));
           const float2 dz = __fadd2_rn(pz, make_float2(B.x, B.y));
           const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-          const bool in0 = r2.x < fit.rc2, in1 = r2.y < fit.rc2;
-          if (kCount) n_in += (uint32_t)(in0 && r2.x > 0.f) + (uint32_t)(in1 && r2.y > 0.f);
-          // r^2 + 2^-70 under the root: a pair at r = 0 (the sink itself, or a
-          // coincident particle) gets a finite factor (below 2^105 m) times
-          // dx = dy = dz = 0, that is no force, without a test; any other pair's
-          // 1/r moves by at most 2^-71 / r^2 relative (below 1e-9 for r > 1e-6 L).
-          // Beyond R_c the values may be inf/NaN; the selects discard them.
-          const float2 r2e = __fadd2_rn(r2, fit.eps);
-          const float2 rinv = make_float2(rsqrt_mufu(r2e.x), rsqrt_mufu(r2e.y));
+          const bool in0 = (r2.x < fit.rc2) && (r2.x > 0.f);
+          const bool in1 = (r2.y < fit.rc2) && (r2.y > 0.f);
+          if (kCount) n_in += (uint32_t)in0 + (uint32_t)in1;
+          // outside (0, R_c) the values below may be inf/NaN; the selects discard them
+          const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
           const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
           float2 f;
           if constexpr (kSplit == 1) {
@@ -332,37 +312,18 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
           sz = __ffma2_rn(f, dz, sz);
         };
         if (active) {
-          const uint32_t np = (kept + 1) >> 1;
-          // this stream's pairs: kk = stream, stream + S, ... below np, stored contiguously
-          const uint32_t T = np > (uint32_t)stream
-                                 ? (uint32_t)((((uint64_t)(np - stream + S - 1)) * magic) >> 32)
-                                 : 0u;
-          const float4 *pb = buf + 2 * (uint32_t)stream * lmax;
-          uint32_t t = 0;
+          const int np = (int)((kept + 1) >> 1);
           if (two) {
-            for (; t + kU2 <= T; t += kU2, pb += 2 * kU2) {
-#pragma unroll
-              for (int u = 0; u < kU2; ++u) {
-                const float4 A = pb[2 * u], B = pb[2 * u + 1];
-                pair2(xx, xy, xz, A, B, ax, ay, az);
-                pair2(bxx, bxy, bxz, A, B, bx, by, bz);
-              }
-            }
-            for (; t < T; ++t, pb += 2) {
-              const float4 A = pb[0], B = pb[1];
+#pragma unroll 4
+            for (int kk = stream; kk < np; kk += S) {
+              const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
               pair2(xx, xy, xz, A, B, ax, ay, az);
               pair2(bxx, bxy, bxz, A, B, bx, by, bz);
             }
           } else {
-            for (; t + kU1 <= T; t += kU1, pb += 2 * kU1) {
-#pragma unroll
-              for (int u = 0; u < kU1; ++u) {
-                const float4 A = pb[2 * u], B = pb[2 * u + 1];
-                pair2(xx, xy, xz, A, B, ax, ay, az);
-              }
-            }
-            for (; t < T; ++t, pb += 2) {
-              const float4 A = pb[0], B = pb[1];
+#pragma unroll 8
+            for (int kk = stream; kk < np; kk += S) {
+              const float4 A = buf[2 * kk], B = buf[2 * kk + 1];
               pair2(xx, xy, xz, A, B, ax, ay, az);
             }
           }
@@ -418,10 +379,8 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   // d_small[3] = work counter, d_small[4] = in-cut-off pair count (zeroed earlier when profiling)
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(P<uint64_t>(c.d_small) + 3);
   const PairFit2 fit2 = pair_fit2(c);  // the context's fit as packed operand pairs
-  // per warp: raw copies (kCap float4) and evaluation pairs (kCap float4 and room
-  // for the stream-major runs: at most S - 1 pairs beyond kCap / 2, S <= 32)
-  const int cap = small ? 128 : 256;
-  const size_t dyn = (size_t)8 * (2 * cap + 64) * sizeof(float4);
+  // two buffers (raw copies, evaluation pairs) of kCap float4 per warp
+  const size_t dyn = (size_t)2 * 8 * (small ? 128 : 256) * sizeof(float4);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 8, st);
   if (e != cudaSuccess) return e;

@@ -29,7 +29,6 @@ struct PairFit2 {
   float2 c[10];
   float2 nrmid, kexp;  // -R_c / 2, -log2(e) / (4 r_s^2)
   float2 pc0, pc1;     // polynomial split: -5 / (2 R_c^3), 3 / (2 R_c^5)
-  float2 eps;          // 2^-70, added to r^2 under the root (a pair at r = 0 needs no test)
   float rc2;
 };
 
@@ -42,7 +41,6 @@ inline PairFit2 pair_fit2(const Ctx &c) {
   const float pc0 = (float)(-2.5 / (c.rc * c.rc * c.rc)), pc1 = (float)(1.5 / (c.rc * c.rc * c.rc * c.rc * c.rc));
   f.pc0 = make_float2(pc0, pc0);
   f.pc1 = make_float2(pc1, pc1);
-  f.eps = make_float2(0x1p-70f, 0x1p-70f);
   f.rc2 = c.fit.rc2;
   return f;
 }

@@ -203,11 +203,14 @@ __global__ void k_kick(float *__restrict__ vel, const float *__restrict__ acc, i
   if (i < n3) vel[i] = fmaf(h, acc[i], vel[i]);
 }
 
-__global__ void k_drift(double *__restrict__ pos, const float *__restrict__ vel, int64_t n3, double dt, double box) {
+// inv_pow2 = 1 / box when box is a power of two (the quotient is then an exact
+// product: no FP64 division, which is slow on this GPU), else 0.
+__global__ void k_drift(double *__restrict__ pos, const float *__restrict__ vel, int64_t n3, double dt, double box,
+                        double inv_pow2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
   double x = pos[i] + dt * (double)vel[i];
-  x -= box * floor(x / box);
+  x -= box * floor(div_box(x, box, inv_pow2));
   if (x >= box) x -= box;  // rounding of a value just below 0
   pos[i] = x;
 }
@@ -363,7 +366,7 @@ cudaError_t kick_guarded(float *vel, const float *acc, int64_t n, double h, Step
 
 cudaError_t drift(double *pos, const float *vel, int64_t n, double dt, double box, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_drift<<<blocks_for(3 * n, 256), 256, 0, st>>>(pos, vel, 3 * n, dt, box);
+  k_drift<<<blocks_for(3 * n, 256), 256, 0, st>>>(pos, vel, 3 * n, dt, box, box_inverse_if_pow2(box));
   note_launch();
   return cudaGetLastError();
 }
