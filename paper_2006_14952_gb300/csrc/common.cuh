@@ -126,11 +126,50 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
   return x;
 }
 
+// The cell index grid_coord(wrap_box(x)) for a power-of-two L and x already in
+// [0, L), read from the bits of x: x = 1.f 2^(e - 1023), L = 2^(eL - 1023), so
+// floor(x 2^21 / L) is the 53-bit significand shifted right by 52 - (e - eL + 21)
+// (zero when that is negative) -- the same value with no FP64 arithmetic (this
+// GPU's FP64 rate is low).  False, with nothing computed, for x outside [0, L),
+// a denormal x, or NaN; the caller then takes the FP64 route.
+__device__ __forceinline__ bool grid_coord_bits(double x, double box, uint32_t &k) {
+  const long long b = __double_as_longlong(x), lb = __double_as_longlong(box);
+  if (b < 0 || b >= lb) return false;  // positive doubles order like their bit patterns
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) {
+    if (b != 0) return false;
+    k = 0;
+    return true;
+  }
+  const int s = e - (int)((lb >> 52) & 0x7ff) + 21;  // <= 20, since x < L
+  if (s < 0) {
+    k = 0;
+    return true;
+  }
+  const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | (1ull << 52);
+  k = (uint32_t)(m >> (52 - s));
+  return true;
+}
+
+// wrap_box, with the bits of x checked first: a coordinate already in [0, L)
+// of a power-of-two L is its own wrap (no FP64 arithmetic).
+__device__ __forceinline__ double wrap_box_fast(double x, double box, double inv_pow2) {
+  const long long b = __double_as_longlong(x);
+  if (inv_pow2 != 0.0 && b >= 0 && b < __double_as_longlong(box)) return x;
+  return wrap_box(x, box, inv_pow2);
+}
+
+__device__ __forceinline__ uint32_t cell_coord(double x, double box, double inv_pow2) {
+  uint32_t k;
+  if (inv_pow2 != 0.0 && grid_coord_bits(x, box, k)) return k;
+  return grid_coord(wrap_box(x, box, inv_pow2), box, inv_pow2);
+}
+
 // Key of the (unwrapped) position (x, y, z): x bits above y bits above z bits.
 __device__ __forceinline__ uint64_t morton_key(double x, double y, double z, double box, double inv_pow2) {
-  const uint32_t k0 = grid_coord(wrap_box(x, box, inv_pow2), box, inv_pow2);
-  const uint32_t k1 = grid_coord(wrap_box(y, box, inv_pow2), box, inv_pow2);
-  const uint32_t k2 = grid_coord(wrap_box(z, box, inv_pow2), box, inv_pow2);
+  const uint32_t k0 = cell_coord(x, box, inv_pow2);
+  const uint32_t k1 = cell_coord(y, box, inv_pow2);
+  const uint32_t k2 = cell_coord(z, box, inv_pow2);
   return (spread3(k0) << 2) | (spread3(k1) << 1) | spread3(k2);
 }
 

@@ -44,17 +44,51 @@ __device__ __forceinline__ int fixed_exponent(const unsigned *mmax_bits, int64_t
   return 61 - e;
 }
 
+// Mesh cell and offset of one coordinate when N_g / L = 2^tm_exp exactly: u =
+// x 2^tm_exp = 1.f 2^s, floor(u) is the 53-bit significand shifted right by
+// 52 - s and u - floor(u) the bits shifted out, converted to FP32 (one correct
+// rounding, as of the exact FP64 difference) -- no FP64 arithmetic (this GPU's
+// FP64 rate is low).  False, with nothing computed, outside [0, L) (x = L after
+// a wrap that rounded up), for x below 2^-120 or u below 2^-100 (but not zero),
+// or u above 2^51.
+__device__ __forceinline__ bool cic_bits(double x, double box, int tm_exp, int &c, float &d) {
+  const long long b = __double_as_longlong(x);
+  if (b < 0 || b >= __double_as_longlong(box)) return false;
+  if (b == 0) {
+    c = 0;
+    d = 0.f;
+    return true;
+  }
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023, s = ex + tm_exp;
+  if (ex < -120 || s < -100 || s > 51) return false;
+  if (s < 0) {  // u < 1: the offset is u itself, (float)x scaled exactly (both normal in FP32)
+    c = 0;
+    d = ldexpf((float)x, tm_exp);
+    return true;
+  }
+  const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | (1ull << 52);
+  c = (int)(m >> (52 - s));
+  d = ldexpf((float)(m & ((1ull << (52 - s)) - 1ull)), s - 52);
+  return true;
+}
+
 // Base mesh point and fractional offsets of particle i: u = x N_g / L in FP64
 // (wrapped positions: u in [0, N_g]), the offset u - floor(u) exact in FP64 and
-// then rounded once to FP32 (the CIC weights are formed in FP32).
+// then rounded once to FP32 (the CIC weights are formed in FP32).  tm_exp: N_g / L
+// = 2^tm_exp, read from the bits (or kNoExp: the FP64 route).
+constexpr int kNoExp = 1 << 20;
 __device__ __forceinline__ void cic_setup(const double *__restrict__ xs, int64_t n, int64_t i, double to_mesh,
-                                          int ng, int (&i0)[3], float (&d)[3]) {
+                                          int tm_exp, double box, int ng, int (&i0)[3], float (&d)[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double u = xs[k * n + i] * to_mesh;
-    const double f = floor(u);
-    d[k] = (float)(u - f);
-    int c = (int)f;
+    const double x = xs[k * n + i];
+    int c;
+    if (tm_exp == kNoExp || !cic_bits(x, box, tm_exp, c, d[k])) {
+      const double u = x * to_mesh;
+      const double f = floor(u);
+      d[k] = (float)(u - f);
+      c = (int)f;
+    }
     if (c >= ng) c -= ng;
     if (c < 0) c += ng;
     i0[k] = c;
@@ -70,7 +104,7 @@ __device__ __forceinline__ void cic_setup(const double *__restrict__ xs, int64_t
 // particle) and the run's first lane issues the eight atomics; otherwise every
 // lane issues its own.
 __global__ void k_deposit(const double *__restrict__ xs, const float4 *__restrict__ pm4, int64_t n, double to_mesh,
-                          int ng, const unsigned *__restrict__ mmax, unsigned long long *__restrict__ q) {
+                          int tm_exp, double box, int ng, const unsigned *__restrict__ mmax, unsigned long long *__restrict__ q) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < n;  // whole warps stay for the warp-wide steps
@@ -79,7 +113,7 @@ __global__ void k_deposit(const double *__restrict__ xs, const float4 *__restric
   float ms = 0.f;
   uint32_t key = 0xffffffffu - (uint32_t)lane;  // distinct keys (above any mesh index) for lanes past n
   if (valid) {
-    cic_setup(xs, n, i, to_mesh, ng, i0, d);
+    cic_setup(xs, n, i, to_mesh, tm_exp, box, ng, i0, d);
     ms = ldexpf(pm4[i].w, fixed_exponent(mmax, n));
     key = ((uint32_t)i0[0] * (uint32_t)ng + (uint32_t)i0[1]) * (uint32_t)ng + (uint32_t)i0[2];
   }
@@ -165,12 +199,13 @@ __global__ void k_green(const cufftComplex *__restrict__ mk, int ng, float box, 
 }
 
 __global__ void k_interpolate(const double *__restrict__ xs, const uint32_t *__restrict__ perm, int64_t n,
-                              double to_mesh, int ng, const float *__restrict__ a, float *__restrict__ acc) {
+                              double to_mesh, int tm_exp, double box, int ng, const float *__restrict__ a,
+                              float *__restrict__ acc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int i0[3];
   float d[3];
-  cic_setup(xs, n, i, to_mesh, ng, i0, d);
+  cic_setup(xs, n, i, to_mesh, tm_exp, box, ng, i0, d);
   const int64_t cells = (int64_t)ng * ng * ng;
   float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -210,8 +245,11 @@ __global__ void k_drift(double *__restrict__ pos, const float *__restrict__ vel,
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
   double x = pos[i] + dt * (double)vel[i];
-  x -= box * floor(div_box(x, box, inv_pow2));
-  if (x >= box) x -= box;  // rounding of a value just below 0
+  const long long b = __double_as_longlong(x);
+  if (b < 0 || b >= __double_as_longlong(box)) {  // outside [0, L) (or NaN): wrap (in [0, L) nothing to do)
+    x -= box * floor(div_box(x, box, inv_pow2));
+    if (x >= box) x -= box;  // rounding of a value just below 0
+  }
   pos[i] = x;
 }
 
@@ -327,10 +365,14 @@ cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
   if ((e = cudaMemsetAsync(c.pm_q.p, 0, cells * 8, st)) != cudaSuccess) return e;
   const int T = 256;
   const double to_mesh = (double)ng / c.prm.box;
+  int tm_exp = 0;  // N_g / L = 2^tm_exp exactly (both powers of two), else the FP64 route
+  const bool pow2 = std::frexp(to_mesh, &tm_exp) == 0.5 && box_inverse_if_pow2(c.prm.box) != 0.0;
+  tm_exp = pow2 ? tm_exp - 1 : kNoExp;
   unsigned gm = blocks_for(c.n, T);
   if (gm > 152 * 16) gm = 152 * 16;
   k_mass_absmax<<<gm, T, 0, st>>>(P<float4>(c.pm4), c.n, mmax);
-  k_deposit<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<float4>(c.pm4), c.n, to_mesh, ng, mmax,
+  k_deposit<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<float4>(c.pm4), c.n, to_mesh, tm_exp, c.prm.box,
+                                              ng, mmax,
                                               P<unsigned long long>(c.pm_q));
   unsigned gc = blocks_for(cells, T);
   if (gc > 152 * 16) gc = 152 * 16;
@@ -347,7 +389,8 @@ cudaError_t pm_long_range(Ctx &c, float *acc, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = fft_error(cufftExecC2R(c.pm_plan_c2r, P<cufftComplex>(c.pm_ak), P<cufftReal>(c.pm_a)))) != cudaSuccess)
     return e;
-  k_interpolate<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<uint32_t>(c.idx), c.n, to_mesh, ng,
+  k_interpolate<<<blocks_for(c.n, T), T, 0, st>>>(P<double>(c.xs), P<uint32_t>(c.idx), c.n, to_mesh, tm_exp,
+                                                  c.prm.box, ng,
                                                   P<float>(c.pm_a), acc);
   note_launch();
   return cudaGetLastError();

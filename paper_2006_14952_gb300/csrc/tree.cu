@@ -27,13 +27,14 @@ __global__ void k_gather(const double *__restrict__ pos, const uint32_t *__restr
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   uint32_t i = idx[s];
-  xs[s] = wrap_box(pos[i], box, inv_pow2);
-  xs[n + s] = wrap_box(pos[n + i], box, inv_pow2);
-  xs[2 * n + s] = wrap_box(pos[2 * n + i], box, inv_pow2);
+  xs[s] = wrap_box_fast(pos[i], box, inv_pow2);
+  xs[n + s] = wrap_box_fast(pos[n + i], box, inv_pow2);
+  xs[2 * n + s] = wrap_box_fast(pos[2 * n + i], box, inv_pow2);
 }
 
 
-// FP64 offset from the geometric leaf centre, rounded once to FP32.
+// FP64 offset from the geometric leaf centre, rounded once to FP32 (a thread
+// per leaf; the cell side L 2^-level built from its bits: no FP64 division).
 __global__ void k_leaf_offsets(const uint32_t *__restrict__ leaves, int64_t nl, const uint4 *__restrict__ cell,
                                const uint2 *__restrict__ range, const double *__restrict__ xs,
                                const float *__restrict__ mass, const uint32_t *__restrict__ perm, int64_t n,
@@ -43,7 +44,7 @@ __global__ void k_leaf_offsets(const uint32_t *__restrict__ leaves, int64_t nl, 
   uint32_t k = leaves[t];
   uint4 c = cell[k];
   uint2 r = range[k];
-  double h = box / (double)(1u << c.w);
+  const double h = box * __longlong_as_double((long long)(1023 - (int)c.w) << 52);
   double zx = ((double)c.x + 0.5) * h, zy = ((double)c.y + 0.5) * h, zz = ((double)c.z + 0.5) * h;
   for (uint32_t i = r.x; i < r.x + r.y; ++i) {
     pm4[i] = make_float4((float)(xs[i] - zx), (float)(xs[n + i] - zy), (float)(xs[2 * n + i] - zz), mass[perm[i]]);

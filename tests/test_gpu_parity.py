@@ -66,6 +66,10 @@ def test_keys_perm_nodes_bit_exact(case):
     pos, mass = CASES[case]()
     pos = pos.copy()
     pos[:, :4] = [[-0.3, 1.0, 1.7, 0.5], [2.2, -1e-17, 0.25, 0.5], [0.999999999999, 0.5, -2.0, 0.5]]
+    # zero, a denormal, a tiny normal and the largest double below L (the key kernel reads the
+    # cell index from the bits of an in-box coordinate and takes the FP64 route for the rest)
+    top = 1.0 - 2.0 ** -53
+    pos[:, 4:8] = [[0.0, 5e-324, 1e-300, top], [1e-300, 0.0, 5e-324, 0.25], [top, 1e-300, 0.0, 5e-324]]
     s, _ = run_gpu(pos, mass, pm_grid=32)
     f = run_oracle(pos, mass, s)
     key, perm, _ = f.particles()
