@@ -141,7 +141,7 @@ void for_each_buffer(Ctx &c, F f) {
                   &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
                   &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval, &c.lo_flag,
                   &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr,
-                  &c.pacc, &c.tf_pairs, &c.tf_segs, &c.tf_sst};
+                  &c.pacc, &c.tf_pairs, &c.tf_segs, &c.tf_sst, &c.lpt_order, &c.lpt_tmp};
   for (DBuf *b : bufs) f(*b);
 }
 

@@ -322,6 +322,7 @@ struct Ctx {
   int last_batches = 1;     // sink batches of the last short-range call
   bool lists_split = false; // the last short-range call's lists were evaluated in parts (not kept)
   DBuf pacc;                // sink batches: P2P accelerations [3][n], added by L2P
+  DBuf lpt_order, lpt_tmp;  // P2P: the sink leaves longest first, and its buckets and counters
   DBuf tf_pairs, tf_segs, tf_sst;  // sink batches: the frontier the top levels leave
   DBuf m2l_beg, m2l_end, p2p_beg, p2p_end;  // u32 [nnodes] CSR bounds by sink
   DBuf m2l_mid;  // u32 [nnodes]: [beg, mid) table pairs, [mid, end) per-pair operator

@@ -358,6 +358,54 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
   }
 }
 
+// Longest-first order of the sink leaves (list scheduling: the persistent grid
+// takes leaves in this order).  A leaf's work is about its list entries times
+// its sinks; leaves are bucketed by the binary order of magnitude of that
+// (coarse buckets already give the longest-first schedule its bound, the
+// heaviest single leaf) and placed bucket by bucket, heaviest first.  The
+// order within a bucket is whatever the atomics give: each leaf's sums are
+// its own warp's, so the forces do not depend on the order.
+constexpr int kLptBuckets = 64;
+
+__global__ void k_lpt_hist(const uint32_t *__restrict__ leaves, int64_t nl, const uint2 *__restrict__ range,
+                           const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
+                           uint8_t *__restrict__ bucket, unsigned *__restrict__ hist, const TreeState *tz) {
+  __shared__ unsigned h[kLptBuckets];
+  for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  nl = tree_leaves(tz, nl);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nl) {
+    const uint32_t a = leaves[t];
+    const unsigned long long w = (unsigned long long)(end[a] - beg[a]) * range[a].y;
+    const int b = w == 0 ? kLptBuckets - 1 : __clzll(w);  // heavier leaves: smaller bucket index
+    bucket[t] = (uint8_t)b;
+    atomicAdd(&h[b], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+__global__ void k_lpt_place(const uint32_t *__restrict__ leaves, int64_t nl, const uint8_t *__restrict__ bucket,
+                            const unsigned *__restrict__ hist, unsigned *__restrict__ cursor,
+                            uint32_t *__restrict__ order, const TreeState *tz) {
+  __shared__ unsigned base[kLptBuckets];
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int i = 0; i < kLptBuckets; ++i) {
+      base[i] = run;
+      run += hist[i];
+    }
+  }
+  __syncthreads();
+  nl = tree_leaves(tz, nl);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const int b = bucket[t];
+  order[base[b] + atomicAdd(&cursor[b], 1u)] = leaves[t];
+}
+
 }  // namespace
 
 cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
@@ -384,7 +432,19 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 8, st);
   if (e != cudaSuccess) return e;
-  kern<<<g, T, dyn, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
+  // the leaves longest first
+  const TreeState *tz = c.graph_tree ? P<TreeState>(c.tstate) : nullptr;
+  if ((e = ensure(c.lpt_order, (size_t)c.nleaves * 4)) != cudaSuccess) return e;
+  if ((e = ensure(c.lpt_tmp, (size_t)c.nleaves + 2 * kLptBuckets * sizeof(unsigned) + 64)) != cudaSuccess) return e;
+  unsigned *hist = P<unsigned>(c.lpt_tmp), *cursor = hist + kLptBuckets;
+  uint8_t *bucket = reinterpret_cast<uint8_t *>(cursor + kLptBuckets);
+  if ((e = cudaMemsetAsync(hist, 0, 2 * kLptBuckets * sizeof(unsigned), st)) != cudaSuccess) return e;
+  k_lpt_hist<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint2>(c.range),
+                                                      P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), bucket, hist, tz);
+  k_lpt_place<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, bucket, hist, cursor,
+                                                       P<uint32_t>(c.lpt_order), tz);
+  note_launch(2);
+  kern<<<g, T, dyn, st>>>(P<uint32_t>(c.lpt_order), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
                         (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr,
                         c.graph_tree ? P<TreeState>(c.tstate) : nullptr);
