@@ -387,10 +387,13 @@ __global__ void k_lpt_hist(const uint32_t *__restrict__ leaves, int64_t nl, cons
     if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
+// Ranks within a block from shared-memory counters, one global reservation per
+// (block, bucket): the few heavy buckets take few global atomics.
 __global__ void k_lpt_place(const uint32_t *__restrict__ leaves, int64_t nl, const uint8_t *__restrict__ bucket,
                             const unsigned *__restrict__ hist, unsigned *__restrict__ cursor,
                             uint32_t *__restrict__ order, const TreeState *tz) {
-  __shared__ unsigned base[kLptBuckets];
+  __shared__ unsigned base[kLptBuckets], cnt[kLptBuckets];
+  for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x) cnt[i] = 0u;
   if (threadIdx.x == 0) {
     unsigned run = 0;
     for (int i = 0; i < kLptBuckets; ++i) {
@@ -401,9 +404,14 @@ __global__ void k_lpt_place(const uint32_t *__restrict__ leaves, int64_t nl, con
   __syncthreads();
   nl = tree_leaves(tz, nl);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nl) return;
-  const int b = bucket[t];
-  order[base[b] + atomicAdd(&cursor[b], 1u)] = leaves[t];
+  const bool valid = t < nl;
+  const int b = valid ? bucket[t] : 0;
+  const unsigned local = valid ? atomicAdd(&cnt[b], 1u) : 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x)
+    if (cnt[i]) base[i] += atomicAdd(&cursor[i], cnt[i]);
+  __syncthreads();
+  if (valid) order[base[b] + local] = leaves[t];
 }
 
 }  // namespace
