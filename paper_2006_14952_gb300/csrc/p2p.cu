@@ -50,9 +50,9 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
                                                 const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
                                                 const uint32_t *__restrict__ perm, int64_t n, float box, PairFit2 fit,
                                                 float G, float *__restrict__ acc_out,
-                                                unsigned long long *__restrict__ ctr, const TreeState *tz) {
+                                                unsigned long long *__restrict__ ctr, const unsigned *__restrict__ n_items) {
   extern __shared__ float4 p2p_smem[];
-  nl = tree_leaves(tz, nl);  // graph mode: the leaf count from the device tree state
+  nl = *n_items;  // work items: a leaf's chunk of up to 32 sinks (leaf index, chunk in bit 31)
   // per warp: the 32 list entries of the pending fill (first particle, exclusive
   // candidate offset, leaf-centre offset in the sink's frame), each candidate's
   // entry, and the chunk's sink bounding box (lo xyz, hi xyz)
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
     if (lane == 0) t = atomicAdd(ctr, 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);
     if ((int64_t)t >= nl) break;
-    const uint32_t k = leaves[t];
+    const uint32_t item = leaves[t], k = item & 0x7fffffffu;
     const uint4 ca = cell[k];
     const uint2 r = range[k];
     const uint32_t tb = beg[k], te = end[k];
@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
       return tot;
     };
 
-    for (uint32_t cbase = r.x; cbase < r.x + r.y; cbase += 32) {
+    const uint32_t cfirst = r.x + 32u * (item >> 31), cend = min(cfirst + 32u, r.x + r.y);
+    for (uint32_t cbase = cfirst; cbase < cend; cbase += 32) {
       const uint32_t rem = r.x + r.y - cbase;
       const int cs = rem < 32 ? (int)rem : 32;
       // two sinks per lane (one from each half of the chunk) where that doubles the
@@ -358,18 +359,22 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
   }
 }
 
-// Longest-first order of the sink leaves (list scheduling: the persistent grid
-// takes leaves in this order).  A leaf's work is about its list entries times
-// its sinks; leaves are bucketed by the binary order of magnitude of that
-// (coarse buckets already give the longest-first schedule its bound, the
-// heaviest single leaf) and placed bucket by bucket, heaviest first.  The
-// order within a bucket is whatever the atomics give: each leaf's sums are
-// its own warp's, so the forces do not depend on the order.
+// Longest-first order of the work (list scheduling: the persistent grid takes
+// items in this order).  An item is one chunk of up to 32 sinks of a leaf
+// (leaves of 33..64 particles give two, so the heaviest leaves' work is split
+// between two warps; the chunks' sums are independent, so the forces do not
+// change).  An item's work is about the leaf's list entries times its sinks;
+// items are bucketed by the binary order of magnitude of that (coarse buckets
+// already give the longest-first schedule its bound, the heaviest single item)
+// and placed bucket by bucket, heaviest first.  Leaves with empty lists (other
+// sink batches) give no item.  The order within a bucket does not matter: each
+// item's sums are its own warp's.
 constexpr int kLptBuckets = 64;
 
 __global__ void k_lpt_hist(const uint32_t *__restrict__ leaves, int64_t nl, const uint2 *__restrict__ range,
                            const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
-                           uint8_t *__restrict__ bucket, unsigned *__restrict__ hist, const TreeState *tz) {
+                           uint8_t *__restrict__ bucket, unsigned *__restrict__ hist, unsigned *__restrict__ n_items,
+                           const TreeState *tz) {
   __shared__ unsigned h[kLptBuckets];
   for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x) h[i] = 0u;
   __syncthreads();
@@ -377,14 +382,24 @@ __global__ void k_lpt_hist(const uint32_t *__restrict__ leaves, int64_t nl, cons
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nl) {
     const uint32_t a = leaves[t];
-    const unsigned long long w = (unsigned long long)(end[a] - beg[a]) * range[a].y;
-    const int b = w == 0 ? kLptBuckets - 1 : __clzll(w);  // heavier leaves: smaller bucket index
-    bucket[t] = (uint8_t)b;
-    atomicAdd(&h[b], 1u);
+    const uint32_t ent = end[a] - beg[a], cnt = range[a].y;
+#pragma unroll
+    for (uint32_t c = 0; c < 2; ++c) {
+      uint8_t b = 0xff;
+      if (ent > 0 && 32u * c < cnt) {
+        const uint32_t cs = min(32u, cnt - 32u * c);
+        b = (uint8_t)__clzll((unsigned long long)ent * cs);  // heavier: smaller bucket index
+        atomicAdd(&h[b], 1u);
+      }
+      bucket[2 * t + c] = b;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x)
-    if (h[i]) atomicAdd(&hist[i], h[i]);
+    if (h[i]) {
+      atomicAdd(&hist[i], h[i]);
+      atomicAdd(n_items, h[i]);
+    }
 }
 
 // Ranks within a block from shared-memory counters, one global reservation per
@@ -405,13 +420,25 @@ __global__ void k_lpt_place(const uint32_t *__restrict__ leaves, int64_t nl, con
   nl = tree_leaves(tz, nl);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = t < nl;
-  const int b = valid ? bucket[t] : 0;
-  const unsigned local = valid ? atomicAdd(&cnt[b], 1u) : 0u;
+  uint8_t b[2] = {0xff, 0xff};
+  unsigned local[2] = {0u, 0u};
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      b[c] = bucket[2 * t + c];
+      if (b[c] != 0xff) local[c] = atomicAdd(&cnt[b[c]], 1u);
+    }
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < kLptBuckets; i += blockDim.x)
     if (cnt[i]) base[i] += atomicAdd(&cursor[i], cnt[i]);
   __syncthreads();
-  if (valid) order[base[b] + local] = leaves[t];
+  if (valid) {
+    const uint32_t a = leaves[t];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (b[c] != 0xff) order[base[b[c]] + local[c]] = a | ((uint32_t)c << 31);
+  }
 }
 
 }  // namespace
@@ -442,20 +469,22 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   // the leaves longest first
   const TreeState *tz = c.graph_tree ? P<TreeState>(c.tstate) : nullptr;
-  if ((e = ensure(c.lpt_order, (size_t)c.nleaves * 4)) != cudaSuccess) return e;
-  if ((e = ensure(c.lpt_tmp, (size_t)c.nleaves + 2 * kLptBuckets * sizeof(unsigned) + 64)) != cudaSuccess) return e;
-  unsigned *hist = P<unsigned>(c.lpt_tmp), *cursor = hist + kLptBuckets;
-  uint8_t *bucket = reinterpret_cast<uint8_t *>(cursor + kLptBuckets);
-  if ((e = cudaMemsetAsync(hist, 0, 2 * kLptBuckets * sizeof(unsigned), st)) != cudaSuccess) return e;
+  if ((e = ensure(c.lpt_order, (size_t)c.nleaves * 8)) != cudaSuccess) return e;
+  if ((e = ensure(c.lpt_tmp, (size_t)c.nleaves * 2 + (2 * kLptBuckets + 4) * sizeof(unsigned) + 64)) != cudaSuccess)
+    return e;
+  unsigned *hist = P<unsigned>(c.lpt_tmp), *cursor = hist + kLptBuckets, *n_items = cursor + kLptBuckets;
+  uint8_t *bucket = reinterpret_cast<uint8_t *>(n_items + 4);
+  if ((e = cudaMemsetAsync(hist, 0, (2 * kLptBuckets + 4) * sizeof(unsigned), st)) != cudaSuccess) return e;
+  if (c.prm.leaf_max > 64) return cudaErrorInvalidValue;  // two chunks per leaf at most
   k_lpt_hist<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint2>(c.range),
-                                                      P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), bucket, hist, tz);
+                                                      P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), bucket, hist,
+                                                      n_items, tz);
   k_lpt_place<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, bucket, hist, cursor,
                                                        P<uint32_t>(c.lpt_order), tz);
   note_launch(2);
   kern<<<g, T, dyn, st>>>(P<uint32_t>(c.lpt_order), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
-                        (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr,
-                        c.graph_tree ? P<TreeState>(c.tstate) : nullptr);
+                        (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr, n_items);
   note_launch();
   return cudaGetLastError();
 }
