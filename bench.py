@@ -567,6 +567,11 @@ def main():
             "gpu_launches": int(l1 - l0 - 0),
             "clocks": clocks,
             "breakdown_ms": {k[2:]: round(v, 4) for k, v in mean.items()},
+            # the same steps without the tree build (keys, sort, octree): forces per second of the
+            # short-range call on an existing tree
+            "excluding_tree": {"value": whole_job_rate(ws, n, 1, max(tot_ms / args.steps - mean["t_keys_sort"]
+                                                                     - mean["t_tree"], 1e-9) / 1e3),
+                               "unit": UNIT, "ms_per_step": tot_ms / args.steps - mean["t_keys_sort"] - mean["t_tree"]},
             "counts": {"nodes": st["nnodes"], "leaves": st["nleaves"], "levels": st["nlevels"],
                        "traverse_iters": st["traverse_iters"], "p2p_leaf_pairs": st["np2p"],
                        "m2l_pairs": st["nm2l"], "m2l_pairs_table": st["nm2l_table"], "frontier_pairs": st["frontier_pairs"],
