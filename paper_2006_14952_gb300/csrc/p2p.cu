@@ -6,8 +6,10 @@
 // particles of all leaves on the sink's list are streamed through per-warp
 // shared memory in fills of up to kCap particles.  A fill takes the next 32
 // list entries (a prefix scan of their particle counts gives each candidate
-// its slot, an entry cut at the buffer's end continues in the next fill) and
-// copies the candidates' particles asynchronously (cp.async) into a raw buffer;
+// its slot, an entry cut at the buffer's end continues in the next fill; each
+// entry marks its first slot and the marks are carried forward, so every slot
+// knows its entry) and copies the candidates' particles asynchronously
+// (cp.async) into a raw buffer;
 // the next fill's copies are issued before the current fill is evaluated, so
 // their latency hides behind the arithmetic.  Once a fill has landed it is
 // transformed into the evaluation buffer: moved into the sink leaf's frame (the
@@ -131,31 +133,55 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
       e_off[wid][0][lane] = dx;
       e_off[wid][1][lane] = dy;
       e_off[wid][2][lane] = dz;
-      __syncwarp();
       const uint32_t all = __shfl_sync(0xffffffffu, incl, 31);
       const uint32_t tot = all < (uint32_t)kCap ? all : (uint32_t)kCap;
-      // candidate p belongs to the last entry whose offset is <= p; four per lane
-      // per step: the binary searches first, then the copies
-      for (uint32_t pb = 0; pb < tot; pb += 128) {
-        int own[4];
-        uint32_t idx[4];
+      // candidate p belongs to the last entry whose offset is <= p: each
+      // non-empty entry marks its first slot, and the marks are carried forward
+      // (kPer slots per lane, then a prefix maximum over the lanes: the entries'
+      // offsets increase with the lane)
+      constexpr int kPer = kCap / 32;
+      uint8_t *own_row = e_own[wid];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t p = pb + lane + 32 * u;
-          int o = 0;
+      for (int i = 0; i < kPer; ++i) own_row[lane * kPer + i] = 0xffu;
+      __syncwarp();
+      if (avail > 0 && excl < tot) own_row[excl] = (uint8_t)lane;
+      __syncwarp();
+      {
+        uint8_t b[kPer];
+        int lastm = -1;
 #pragma unroll
-          for (int step = 16; step; step >>= 1)
-            if (e_excl[wid][o + step] <= p) o += step;
-          own[u] = o;
-          idx[u] = e_src[wid][o] + (p - e_excl[wid][o]);
+        for (int i = 0; i < kPer; ++i) {
+          b[i] = own_row[lane * kPer + i];
+          if (b[i] != 0xffu) lastm = b[i];
         }
+        int pm = lastm;  // inclusive prefix maximum over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, pm, o);
+          if (lane >= o && y > pm) pm = y;
+        }
+        int cur = __shfl_up_sync(0xffffffffu, pm, 1);  // the mark carried in from the lanes before
+        if (lane == 0) cur = -1;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          if (b[i] != 0xffu) cur = b[i];
+          b[i] = (uint8_t)cur;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) own_row[lane * kPer + i] = b[i];
+      }
+      __syncwarp();
+      // the copies, four candidates per lane per step
+      for (uint32_t pb = 0; pb < tot; pb += 128) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const uint32_t p = pb + lane + 32 * u;
           if (p < tot) {
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(raw_s + 16u * p), "l"(pm4 + idx[u])
+            const int o = own_row[p];
+            const uint32_t idx = e_src[wid][o] + (p - e_excl[wid][o]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(raw_s + 16u * p), "l"(pm4 + idx)
                          : "memory");
-            e_own[wid][p] = (uint8_t)own[u];
           }
         }
       }
