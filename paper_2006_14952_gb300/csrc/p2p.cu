@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
   // candidate offset, leaf-centre offset in the sink's frame), each candidate's
   // entry, and the chunk's sink bounding box (lo xyz, hi xyz)
   __shared__ uint32_t e_src[8][32], e_excl[8][32];
-  __shared__ float e_off[8][3][32];
+  __shared__ float4 e_off[8][32];  // per entry: leaf-centre offset (x, y, z, unused)
   __shared__ uint8_t e_own[8][kCap];
   __shared__ float e_box[8][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -130,9 +130,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
       const uint32_t excl = incl - avail;
       e_src[wid][lane] = first + start;
       e_excl[wid][lane] = excl;  // non-decreasing in the lane index
-      e_off[wid][0][lane] = dx;
-      e_off[wid][1][lane] = dy;
-      e_off[wid][2][lane] = dz;
+      e_off[wid][lane] = make_float4(dx, dy, dz, 0.f);
       const uint32_t all = __shfl_sync(0xffffffffu, incl, 31);
       const uint32_t tot = all < (uint32_t)kCap ? all : (uint32_t)kCap;
       // candidate p belongs to the last entry whose offset is <= p: each
@@ -273,9 +271,10 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
             bool keep[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              v[u].x += e_off[wid][0][o[u]];
-              v[u].y += e_off[wid][1][o[u]];
-              v[u].z += e_off[wid][2][o[u]];
+              const float4 d = e_off[wid][o[u]];
+              v[u].x += d.x;
+              v[u].y += d.y;
+              v[u].z += d.z;
               const float gx = fmaxf(fmaxf(bx0 - v[u].x, v[u].x - bx1), 0.f);
               const float gy = fmaxf(fmaxf(by0 - v[u].y, v[u].y - by1), 0.f);
               const float gz = fmaxf(fmaxf(bz0 - v[u].z, v[u].z - bz1), 0.f);
