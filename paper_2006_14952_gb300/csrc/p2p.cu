@@ -2,8 +2,9 @@
 // f_(1)(r) r of Sec. 2.2, kept for 0 < r < R_c), added to the L2P accelerations
 // already in the caller's particle order (the un-permute).
 //
-// One warp per sink leaf (taken from a global work counter).  The source
-// particles of all leaves on the sink's list are streamed through per-warp
+// One warp per work item: a chunk of up to 32 sinks of a leaf, taken from a
+// global work counter in longest-first order (k_lpt_hist / k_lpt_place below).
+// The source particles of all leaves on the sink's list are streamed through per-warp
 // shared memory in fills of up to kCap particles.  A fill takes the next 32
 // list entries (a prefix scan of their particle counts gives each candidate
 // its slot, an entry cut at the buffer's end continues in the next fill; each
@@ -46,7 +47,7 @@ namespace {
 // Sec. 5, a = -m (1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5)) r, no exp2 and no
 // fitted factor (see hfmm_params.split).
 template <bool kCount, int kCap, int kSplit>
-__global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
+__global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ items,
                                                 const uint4 *__restrict__ cell, const uint2 *__restrict__ range,
                                                 const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
                                                 const uint64_t *__restrict__ lst, const float4 *__restrict__ pm4,
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
                                                 float G, float *__restrict__ acc_out,
                                                 unsigned long long *__restrict__ ctr, const unsigned *__restrict__ n_items) {
   extern __shared__ float4 p2p_smem[];
-  nl = *n_items;  // work items: a leaf's chunk of up to 32 sinks (leaf index, chunk in bit 31)
+  const int64_t nl = *n_items;  // work items: a leaf's chunk of up to 32 sinks (leaf index, chunk in bit 31)
   // per warp: the 32 list entries of the pending fill (first particle, exclusive
   // candidate offset, leaf-centre offset in the sink's frame), each candidate's
   // entry, and the chunk's sink bounding box (lo xyz, hi xyz)
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256, 2) k_p2p(const uint32_t *__restrict__ lea
     if (lane == 0) t = atomicAdd(ctr, 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);
     if ((int64_t)t >= nl) break;
-    const uint32_t item = leaves[t], k = item & 0x7fffffffu;
+    const uint32_t item = items[t], k = item & 0x7fffffffu;
     const uint4 ca = cell[k];
     const uint2 r = range[k];
     const uint32_t tb = beg[k], te = end[k];
@@ -507,7 +508,7 @@ cudaError_t p2p_pass(Ctx &c, float *acc, cudaStream_t st) {
   k_lpt_place<<<blocks_for(c.nleaves, T), T, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, bucket, hist, cursor,
                                                        P<uint32_t>(c.lpt_order), tz);
   note_launch(2);
-  kern<<<g, T, dyn, st>>>(P<uint32_t>(c.lpt_order), c.nleaves, P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
+  kern<<<g, T, dyn, st>>>(P<uint32_t>(c.lpt_order), P<uint4>(c.cell), P<uint2>(c.range), P<uint32_t>(c.p2p_beg),
                         P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n,
                         (float)c.prm.box, fit2, (float)c.prm.G, acc, ctr, n_items);
   note_launch();
