@@ -5,14 +5,16 @@ TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only users.  Nothing in the product
 package imports this module, and this module imports nothing from it.
 
-The C source ``orc.c`` holds the arithmetic (FP64, OpenMP); this file only
-compiles it with gcc and marshals numpy arrays through ctypes.
+The C sources ``orc.c`` (Morton octree) and ``orc_kd.c`` (the ORB / k-d tree
+variant) hold the arithmetic (FP64, OpenMP); this file only compiles them with
+gcc and marshals numpy arrays through ctypes.
 
 Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   prefactors, derivative tensor, P2M/M2M/M2L/L2L/L2P, direct sum, tree,
   traversal (hybrid and conventional), interaction counts, FMM forces, the
   network's forward and gradient, its forward with the FP32 error bound, the
-  pair features of the learned acceptance, the learned walk: pinned (closed forms, symbolic derivatives,
+  pair features of the learned acceptance, the learned walk, the k-d tree, its
+  walk and its FMM forces: pinned (closed forms, symbolic derivatives,
   exact identities, brute force, textbook interaction lists, special cases).
 Sibling modules: ``pm.py`` (PM long range and the KDK step) and
 ``poly_split.py`` (a polynomial truncation of the split), both numpy FP64.
@@ -29,7 +31,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
-_SRC = [os.path.join(_HERE, "orc.c")]
+_SRC = [os.path.join(_HERE, "orc.c"), os.path.join(_HERE, "orc_kd.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -39,7 +41,7 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"
 
 
 def build(force: bool = False) -> str:
-    """Compile ``orc.c`` into ``oracle/_build/liborc.so`` (idempotent)."""
+    """Compile ``orc.c`` and ``orc_kd.c`` into ``oracle/_build/liborc.so`` (idempotent)."""
     os.makedirs(_BUILD, exist_ok=True)
     newest = max(os.path.getmtime(s) for s in _SRC)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
@@ -104,6 +106,22 @@ def lib():
             L.orc_mlp_forward_bound.argtypes = [P, P, P, i64, P, P, P, P]
             L.orc_traverse_learned.argtypes = [P, P, P, P, P, i64, P]
             L.orc_export_m2l_orders.argtypes = [P, P]
+            L.orc_kd_create.argtypes = [d, d, d, d, d, i32, i32, i32, i32]
+            L.orc_kd_create.restype = P
+            L.orc_kd_destroy.argtypes = [P]
+            L.orc_kd_build.argtypes = [P, i64, P, P]
+            L.orc_kd_traverse.argtypes = [P]
+            L.orc_kd_upward.argtypes = [P]
+            L.orc_kd_m2l_pass.argtypes = [P]
+            L.orc_kd_downward.argtypes = [P, P]
+            L.orc_kd_p2p_pass.argtypes = [P, P]
+            L.orc_kd_forces.argtypes = [P, P]
+            L.orc_kd_size.argtypes = [P, i32]
+            L.orc_kd_size.restype = i64
+            L.orc_kd_export.argtypes = [P, P, P, P]
+            L.orc_kd_export_list.argtypes = [P, i32, P]
+            L.orc_kd_set_lists.argtypes = [P, P, i64, P, i64]
+            L.orc_kd_forces_given_lists.argtypes = [P, P]
             _lib = L
     return _lib
 
@@ -421,3 +439,66 @@ class FMM:
         a = np.zeros((self.n, 3))
         _check(lib().orc_p2p_pass(self._c, _p(a)), "p2p_pass")
         return a
+
+
+class KdFMM:
+    """FP64 truncated FMM on the ORB / k-d tree of Sec. 2.1 (Fig. 1) and Sec. 4:
+    nodes split at the particle-count median along the longest axis of their
+    particles' bounding box, boxes as cell geometry (the readings are in orc_kd.c)."""
+
+    def __init__(self, box=1.0, rs=None, rc=None, G=1.0, theta=0.5, order=4, leaf_max=16,
+                 transition_rule=1, size_rule=1):
+        self._c = lib().orc_kd_create(box, rs, rc, G, theta, order, leaf_max, transition_rule, size_rule)
+        if not self._c:
+            raise ValueError("invalid oracle parameters")
+        self.box, self.rs, self.rc, self.G, self.theta = box, rs, rc, G, theta
+        self.order, self.leaf_max, self.rule, self.size_rule = order, leaf_max, transition_rule, size_rule
+        self.n = 0
+
+    def __del__(self):
+        c = getattr(self, "_c", None)
+        if c:
+            lib().orc_kd_destroy(c)
+            self._c = None
+
+    def build_tree(self, pos, mass):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        self.n = pos.shape[1]
+        _check(lib().orc_kd_build(self._c, self.n, _p(pos), _p(mass)), "kd_build")
+
+    def size(self, what):
+        return int(lib().orc_kd_size(self._c, {"n": 0, "nodes": 1, "levels": 2, "p2p": 3, "m2l": 4}[what]))
+
+    def traverse(self):
+        _check(lib().orc_kd_traverse(self._c), "kd_traverse")
+
+    def forces(self) -> np.ndarray:
+        acc = np.zeros((3, self.n))
+        _check(lib().orc_kd_forces(self._c, _p(acc)), "kd_forces")
+        return acc
+
+    def tree(self):
+        """(nodes [nnodes][5] int64: level, first, count, first child or -1, split axis or -1;
+        boxes [nnodes][6] float64: lo xyz, hi xyz; perm [n] int64: input index in tree order)."""
+        k = self.size("nodes")
+        nodes = np.zeros((k, 5), dtype=np.int64)
+        boxes = np.zeros((k, 6))
+        perm = np.zeros(self.n, dtype=np.int64)
+        lib().orc_kd_export(self._c, _p(nodes), _p(boxes), _p(perm))
+        return nodes, boxes, perm
+
+    def lists(self):
+        p2p = np.zeros((self.size("p2p"), 3), dtype=np.int64)
+        m2l = np.zeros((self.size("m2l"), 3), dtype=np.int64)
+        lib().orc_kd_export_list(self._c, 0, _p(p2p))
+        lib().orc_kd_export_list(self._c, 1, _p(m2l))
+        return p2p, m2l
+
+    def forces_given_lists(self, p2p, m2l):
+        p2p = np.ascontiguousarray(p2p, dtype=np.int64).reshape(-1, 3)
+        m2l = np.ascontiguousarray(m2l, dtype=np.int64).reshape(-1, 3)
+        _check(lib().orc_kd_set_lists(self._c, _p(p2p), len(p2p), _p(m2l), len(m2l)), "kd_set_lists")
+        acc = np.zeros((3, self.n))
+        _check(lib().orc_kd_forces_given_lists(self._c, _p(acc)), "kd_forces_given_lists")
+        return acc
