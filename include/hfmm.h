@@ -143,6 +143,21 @@ typedef struct {
                           the split level sums its entries in two groups (rounding differs from
                           one batch in the last bits).  Not in graph mode; after a call in more than one
                           batch the P2P / M2L lists cannot be exported. */
+  int tree;            /* 0 = Morton octree (the default; every option above applies);
+                          1 = the ORB / k-d tree of Sec. 2.1 (Fig. 1) and Sec. 4: a node of more than
+                          leaf_max particles gives the first floor(n / 2) of them, in the order of
+                          (coordinate, input index) along the longest axis of their bounding box, to its
+                          first child and the rest to its second (the lowest axis on a tie); nodes are
+                          numbered breadth first, and a leaf's particles are in (x, input index) order.
+                          The geometry of a node is its particles' bounding box: expansions about its
+                          centre, the rules of Sec. 2.3 on the boxes in FP64 (S_c between the centres,
+                          S_m and S_max from per-axis gaps and spans, side = largest extent; a pair with
+                          theta S_c = 0 is never accepted), the walk opening the node of larger side.
+                          hfmm_build_tree synchronises `stream` once per tree level; the walk once per
+                          walk level.  Needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0,
+                          split 0 and order <= 6; use_graph and sink_batches are ignored, and
+                          hfmm_interaction_counts, HFMM_EXPORT_KEYS and HFMM_EXPORT_NODES are octree
+                          only (HFMM_EXPORT_KD_NODES and _KD_BOXES describe this tree). */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */
@@ -309,6 +324,8 @@ int hfmm_interaction_counts(hfmm_ctx *ctx, int conventional, int64_t *out, void 
  *                                       the source is displaced by s * L)
  *  HFMM_EXPORT_MULTIPOLES float [nnodes][ncoef(p)]  M_m / h^|m|   (h = cell side)
  *  HFMM_EXPORT_LOCALS     float [nnodes][ncoef(p)]  L_n * h^(|n|+1)
+ *                       (tree 1: h = the node's scale, the power of two L 2^-j at or above
+ *                       its side, j <= 21)
  * Multi-index order: for k = 0..p, nx = k..0, ny = k-nx..0, nz = k-nx-ny.
  */
 enum {
@@ -320,7 +337,10 @@ enum {
   HFMM_EXPORT_MULTIPOLES = 5,
   HFMM_EXPORT_LOCALS = 6,
   HFMM_EXPORT_M2L_ORDER = 7, /* int64 [nm2l] expansion order of each M2L entry, list order */
-  HFMM_EXPORT_CANDIDATES = 8 /* int64 [n][3] pairs of the last hfmm_collect_training_pairs (row order) */
+  HFMM_EXPORT_CANDIDATES = 8, /* int64 [n][3] pairs of the last hfmm_collect_training_pairs (row order) */
+  HFMM_EXPORT_KD_NODES = 9,   /* tree 1: int64 [nnodes][5] level, first, count, first child (-1 for a
+                                 leaf; the second child follows it), split axis (-1 for a leaf) */
+  HFMM_EXPORT_KD_BOXES = 10   /* tree 1: double [nnodes][6] bounding box lo x y z, hi x y z */
 };
 int hfmm_export(hfmm_ctx *ctx, int what, void *host_buf, size_t *bytes);
 

@@ -59,6 +59,11 @@ bool valid_params(const hfmm_params &p, std::string &why) {
   if (p.p2p_mutual != 0 && p.p2p_mutual != 1) return why = "p2p_mutual must be 0 or 1", false;
   if (p.p2p_mutual == 1 && (p.mac_mode != 0 || p.size_rule != 1))
     return why = "p2p_mutual 1 needs mac_mode 0 and size_rule 1", false;
+  if (p.tree != 0 && p.tree != 1) return why = "tree must be 0 (Morton octree) or 1 (ORB / k-d tree)", false;
+  if (p.tree == 1 && (p.mac_mode != 0 || p.m2l_precision != 0 || p.m2l_tables != 0 || p.p2p_mutual != 0 ||
+                      p.split != 0 || p.order > 6))
+    return why = "tree 1 needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0, split 0 and order <= 6",
+           false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;
@@ -141,7 +146,11 @@ void for_each_buffer(Ctx &c, F f) {
                   &c.mut_cnt, &c.mut_poff, &c.mut_key, &c.mut_key_alt, &c.mut_val, &c.mut_val_alt,
                   &c.mut_bounds, &c.mut_small, &c.mut_part, &c.mut_lkey, &c.mut_lval, &c.lo_flag,
                   &c.lo_rank, &c.lo_meta, &c.lo_sink, &c.lo_tcnt, &c.lo_toff, &c.lo_scr,
-                  &c.pacc, &c.tf_pairs, &c.tf_segs, &c.tf_sst, &c.lpt_order, &c.lpt_tmp};
+                  &c.pacc, &c.tf_pairs, &c.tf_segs, &c.tf_sst, &c.lpt_order, &c.lpt_tmp, &c.kd.xw,
+                  &c.kd.ord[0], &c.kd.ord[1], &c.kd.ord[2], &c.kd.ord2[0], &c.kd.ord2[1], &c.kd.ord2[2],
+                  &c.kd.side, &c.kd.flag, &c.kd.scan, &c.kd.pnode, &c.kd.nflag, &c.kd.nscan, &c.kd.first,
+                  &c.kd.count, &c.kd.child, &c.kd.parent, &c.kd.axis, &c.kd.box, &c.kd.geo, &c.kd.hs,
+                  &c.kd.ctr};
   for (DBuf *b : bufs) f(*b);
 }
 
@@ -241,7 +250,7 @@ int hfmm_build_tree(hfmm_ctx *h, const double *pos, const float *mass, int64_t n
   if (n < 0 || n > (int64_t)0x7fffffff) return fail(c, HFMM_ERR_ARG, "n must be in [0, 2^31)");
   if (n > 0 && (!pos || !mass)) return fail(c, HFMM_ERR_ARG, "null position or mass pointer");
   c.mass_ref = mass;
-  cudaError_t e = build_tree(c, pos, mass, n, S(stream));
+  cudaError_t e = c.prm.tree == 1 ? kd_build_tree(c, pos, mass, n, S(stream)) : build_tree(c, pos, mass, n, S(stream));
   if (e == cudaErrorInvalidValue && c.nnodes >= ((int64_t)1 << kSinkBits))
     return fail(c, HFMM_ERR_CAPACITY, "more than 2^27 tree nodes");
   if (e != cudaSuccess) return cuda_fail(c, e, "build_tree");
@@ -253,7 +262,7 @@ namespace {
 // The configurations the graphs cover: FP32 CUDA-core M2L without operator
 // tables, the geometric acceptance, one-sided P2P and no pair counting.
 bool graph_eligible(const Ctx &c) {
-  return c.prm.use_graph && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
+  return c.prm.use_graph && c.prm.tree == 0 && c.prm.m2l_precision == 0 && c.prm.mac_mode == 0 && !(c.prm.profile & 2) &&
          !c.prm.p2p_mutual && !c.prm.m2l_tables && sink_batches_for(c) == 1;
 }
 
@@ -349,6 +358,12 @@ int hfmm_short_range_forces(hfmm_ctx *h, float *acc, void *stream) {
   c.last_graph = false;
   c.last_batches = 1;
   c.lists_split = false;
+  if (c.prm.tree == 1) {
+    e = kd_short_range(c, acc, st);
+    if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "an interaction list above 2^32 - 1 entries");
+    if (e != cudaSuccess) return cuda_fail(c, e, "k-d short range");
+    return HFMM_OK;
+  }
   if (const int nbatch = sink_batches_for(c); nbatch > 1) {
     if (prof) cudaEventRecord(c.ev[3], st);
     if ((e = upward(c, st)) != cudaSuccess) return cuda_fail(c, e, "upward");
@@ -640,6 +655,7 @@ int hfmm_interaction_counts(hfmm_ctx *h, int conventional, int64_t *out, void *s
   if (!out) return fail(c, HFMM_ERR_ARG, "null output pointer");
   if (conventional != 0 && conventional != 1) return fail(c, HFMM_ERR_ARG, "conventional must be 0 or 1");
   if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "interaction_counts before build_tree");
+  if (c.prm.tree != 0) return fail(c, HFMM_ERR_ARG, "interaction counts are defined on the octree (tree 0)");
   for (int i = 0; i < 4; ++i) out[i] = 0;
   if (c.n == 0) return HFMM_OK;
   cudaStream_t st = S(stream);
@@ -725,7 +741,14 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
   if (c.lists_split &&
       (what == HFMM_EXPORT_P2P || what == HFMM_EXPORT_M2L || what == HFMM_EXPORT_M2L_ORDER))
     return fail(c, HFMM_ERR_STATE, "the last call ran in sink batches: its lists were not kept");
+  const bool kd = c.prm.tree == 1;
+  if (kd && (what == HFMM_EXPORT_KEYS || what == HFMM_EXPORT_NODES))
+    return fail(c, HFMM_ERR_ARG, "keys and octree nodes do not exist on the k-d tree (tree 1)");
+  if (!kd && (what == HFMM_EXPORT_KD_NODES || what == HFMM_EXPORT_KD_BOXES))
+    return fail(c, HFMM_ERR_ARG, "k-d nodes exist with tree 1 only");
   switch (what) {
+    case HFMM_EXPORT_KD_NODES: need = c.nnodes * 40; break;
+    case HFMM_EXPORT_KD_BOXES: need = c.nnodes * 48; break;
     case HFMM_EXPORT_KEYS: need = c.n * 8; break;
     case HFMM_EXPORT_PERM: need = c.n * 4; break;
     case HFMM_EXPORT_NODES: need = c.nnodes * 64; break;
@@ -768,6 +791,35 @@ int hfmm_export(hfmm_ctx *h, int what, void *buf, size_t *bytes) {
         r[6] = kids[k].y ? kids[k].x : -1;
         r[7] = kids[k].y;
       }
+      break;
+    }
+    case HFMM_EXPORT_KD_NODES: {
+      const size_t nn = (size_t)c.nnodes;
+      std::vector<uint32_t> first(nn), count(nn);
+      std::vector<int> child(nn), axis(nn);
+      e = cudaMemcpy(first.data(), c.kd.first.p, nn * 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(count.data(), c.kd.count.p, nn * 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(child.data(), c.kd.child.p, nn * 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(axis.data(), c.kd.axis.p, nn * 4, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      int64_t *o = static_cast<int64_t *>(buf);
+      int lev = 0;
+      for (size_t k = 0; k < nn; ++k) {
+        while ((int64_t)k >= c.kd.level_start[lev + 1]) ++lev;
+        int64_t *r = o + 5 * k;
+        r[0] = lev; r[1] = first[k]; r[2] = count[k]; r[3] = child[k]; r[4] = axis[k];
+      }
+      break;
+    }
+    case HFMM_EXPORT_KD_BOXES: {
+      const size_t nn = (size_t)c.nnodes;
+      std::vector<double> b(6 * nn);
+      for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+        e = cudaMemcpy(b.data() + q * nn, P<double>(c.kd.box) + q * c.kd.cap, nn * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      double *o = static_cast<double *>(buf);
+      for (size_t k = 0; k < nn; ++k)
+        for (int q = 0; q < 6; ++q) o[6 * k + q] = b[q * nn + k];
       break;
     }
     case HFMM_EXPORT_CANDIDATES: {

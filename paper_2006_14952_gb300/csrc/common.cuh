@@ -269,6 +269,25 @@ struct Ctx;
 void mac_integer_thresholds(Ctx &c);
 
 // ---------------------------------------------------------------- context
+// ORB / k-d tree of tree = 1 (kdtree.cu): binary nodes numbered breadth first.
+struct KdTree {
+  DBuf xw;                       // f64 [3][n] wrapped positions, input order
+  DBuf ord[3], ord2[3];          // u32 [n] per axis: the particles of each node's range in (coordinate, index) order
+  DBuf side;                     // u8 [n] per particle: 1 = in the second child of its node's split
+  DBuf flag, scan;               // u32 [n]
+  DBuf pnode;                    // u32 [n] node of each position on the level being split (its leaf at the end)
+  DBuf nflag, nscan;             // u32 [cap] split flags of a level's nodes and their scan
+  DBuf first, count;             // u32 [cap] particle range
+  DBuf child, parent, axis;      // i32 [cap] first child (-1 leaf), parent (-1 root), split axis (-1 leaf)
+  DBuf box;                      // f64 [6][cap] lo xyz, hi xyz of the particles' bounding box
+  DBuf geo;                      // f64 [7][cap] centre xyz, half extents xyz, side (largest extent)
+  DBuf hs;                       // f32 [cap] expansion scale h: L 2^-j >= side, j <= 21
+  DBuf ctr;                      // u64 [8] walk counters (next frontier, M2L, P2P entries), scan total
+  std::vector<int64_t> level_start;
+  int64_t cap = 0;
+  uint64_t caps[3] = {0, 0, 0};  // frontier, M2L and P2P capacities of the last walk
+};
+
 struct Ctx {
   hfmm_params prm{};
   double rs = 0, rc = 0;        // split scale and cut-off radius
@@ -367,6 +386,7 @@ struct Ctx {
   // (level, offset) tensor-core M2L: node flags and ranks, tile meta, tile sinks,
   // tile pair counts and offsets, grouped pairs
   DBuf lo_flag, lo_rank, lo_meta, lo_sink, lo_tcnt, lo_toff, lo_scr;
+  KdTree kd;  // tree = 1
   DBuf pm_gtab;          // polynomial split: long-range Green function per integer |k|^2
   size_t pm_gtab_n = 0;  // its length (0: not built)
   int pm_plan_r2c = -1, pm_plan_c2r = -1;
@@ -463,6 +483,14 @@ bool m2l_lo_supported(int p);
 cudaError_t m2l_pass_lo(Ctx &c, int q, cudaStream_t st);
 // Mutual P2P (p2p_mutual = 1): one evaluation per particle pair, reactions through per-entry partials.
 cudaError_t p2p_pass_mutual(Ctx &c, float *acc, cudaStream_t st);
+// ORB / k-d tree (tree = 1): the build (fills xs, pm4, idx like the octree
+// build, so the PM half and the step work unchanged), and the short-range call
+// on it: upward pass, walk, lists grouped by sink, M2L, downward pass, P2P.
+cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st);
+cudaError_t kd_short_range(Ctx &c, float *acc, cudaStream_t st);
+cudaError_t kd_upward(Ctx &c, cudaStream_t st);                // expansions.cu
+cudaError_t kd_downward(Ctx &c, float *acc, cudaStream_t st);  // expansions.cu: L2L, then L2P writing acc
+cudaError_t kd_m2l(Ctx &c, cudaStream_t st);                   // m2l.cu
 
 // Training pairs for the learned acceptance: features [n][12] and M2L errors
 // at orders 2..8 [n][7] (device buffers of the caller); *count receives n.

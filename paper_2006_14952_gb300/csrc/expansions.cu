@@ -213,7 +213,165 @@ cudaError_t downward_p(Ctx &c, float *acc, cudaStream_t st, const float *add) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- k-d tree (tree = 1)
+// The same scaled expansions with a node's scale h (a power of two >= its box
+// side) in place of the octree cell side: P2M and L2P as above; the two children
+// of a node translate with any offset d (in units of the parent's h) and scale
+// ratio rho = h_child / h_parent (M2MGenBody, L2LGenBody); one thread per node,
+// the children added in order (deterministic).
+
+template <int P>
+__global__ void k_kd_p2m(const uint32_t *__restrict__ leaves, int64_t nl, const uint32_t *__restrict__ first,
+                         const uint32_t *__restrict__ count, const float *__restrict__ hs,
+                         const float4 *__restrict__ pm4, int ldm, float *__restrict__ M) {
+  constexpr int NC = ncoef(P);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const uint32_t k = leaves[t];
+  const float inv_h = 1.f / hs[k];
+  float acc[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) acc[q] = 0.f;
+  for (uint32_t i = first[k]; i < first[k] + count[k]; ++i) {
+    const float4 q = pm4[i];
+    P2MBody<P>::run(q.x * inv_h, q.y * inv_h, q.z * inv_h, q.w, acc);
+  }
+  P2MBody<P>::finish(acc);
+  store_row<NC>(M + (size_t)k * ldm, acc);
+}
+
+template <int P>
+__global__ void k_kd_m2m(int64_t lo, int64_t cnt, const int *__restrict__ child, const double *__restrict__ geo,
+                         int64_t cap, const float *__restrict__ hs, int ldm, float *__restrict__ M) {
+  constexpr int NC = ncoef(P);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t k = lo + t;
+  const int ch0 = child[k];
+  if (ch0 < 0) return;
+  const float inv_h = 1.f / hs[k];
+  float o[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) o[q] = 0.f;
+  for (int ch = ch0; ch < ch0 + 2; ++ch) {
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = (float)__dsub_rn(geo[a * cap + k], geo[a * cap + ch]) * inv_h;
+    float ci[NC];
+    load_row<NC>(M + (size_t)ch * ldm, ci);
+    M2MGenBody<P>::run(d[0], d[1], d[2], hs[ch] * inv_h, ci, o);
+  }
+  store_row<NC>(M + (size_t)k * ldm, o);
+}
+
+template <int P>
+__global__ void k_kd_l2l(int64_t lo, int64_t cnt, const int *__restrict__ parent, const double *__restrict__ geo,
+                         int64_t cap, const float *__restrict__ hs, int ldm, float *__restrict__ L) {
+  constexpr int NC = ncoef(P);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t k = lo + t;
+  const int p = parent[k];
+  const float inv_h = 1.f / hs[p];
+  float d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = (float)__dsub_rn(geo[a * cap + k], geo[a * cap + p]) * inv_h;
+  float pl[NC], cl[NC];
+  load_row<NC>(L + (size_t)p * ldm, pl);
+  float *dst = L + (size_t)k * ldm;
+  load_row<NC>(dst, cl);
+  L2LGenBody<P>::run(d[0], d[1], d[2], hs[k] * inv_h, pl, cl);
+  store_row<NC>(dst, cl);
+}
+
+template <int P>
+__global__ void k_kd_l2p(const uint32_t *__restrict__ leaves, int64_t nl, const uint32_t *__restrict__ first,
+                         const uint32_t *__restrict__ count, const float *__restrict__ hs,
+                         const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm, int64_t n, float G,
+                         int ldm, const float *__restrict__ L, float *__restrict__ acc) {
+  constexpr int NC = ncoef(P);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const uint32_t k = leaves[t];
+  const float inv_h = 1.f / hs[k];
+  const float s = G * inv_h * inv_h;
+  float l[NC];
+  load_row<NC>(L + (size_t)k * ldm, l);
+  for (uint32_t i = first[k]; i < first[k] + count[k]; ++i) {
+    const float4 q = pm4[i];
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    L2PBody<P>::run(q.x * inv_h, q.y * inv_h, q.z * inv_h, l, ax, ay, az);
+    const uint32_t o = perm[i];
+    acc[o] = s * ax;
+    acc[n + o] = s * ay;
+    acc[2 * n + o] = s * az;
+  }
+}
+
+template <int P>
+cudaError_t kd_upward_p(Ctx &c, cudaStream_t st) {
+  const int T = 128;
+  KdTree &kd = c.kd;
+  k_kd_p2m<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves,
+                                                      hfmm::P<uint32_t>(kd.first), hfmm::P<uint32_t>(kd.count),
+                                                      hfmm::P<float>(kd.hs), hfmm::P<float4>(c.pm4), c.ldm,
+                                                      hfmm::P<float>(c.M));
+  note_launch();
+  for (int l = c.nlevels - 2; l >= 0; --l) {
+    const int64_t lo = kd.level_start[l], cnt = kd.level_start[l + 1] - lo;
+    k_kd_m2m<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<int>(kd.child), hfmm::P<double>(kd.geo), kd.cap,
+                                                 hfmm::P<float>(kd.hs), c.ldm, hfmm::P<float>(c.M));
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t kd_downward_p(Ctx &c, float *acc, cudaStream_t st) {
+  const int T = 128;
+  KdTree &kd = c.kd;
+  for (int l = 1; l < c.nlevels; ++l) {
+    const int64_t lo = kd.level_start[l], cnt = kd.level_start[l + 1] - lo;
+    k_kd_l2l<P><<<blocks_for(cnt, T), T, 0, st>>>(lo, cnt, hfmm::P<int>(kd.parent), hfmm::P<double>(kd.geo), kd.cap,
+                                                 hfmm::P<float>(kd.hs), c.ldm, hfmm::P<float>(c.L));
+    note_launch();
+  }
+  k_kd_l2p<P><<<blocks_for(c.nleaves, T), T, 0, st>>>(hfmm::P<uint32_t>(c.leaves), c.nleaves,
+                                                      hfmm::P<uint32_t>(kd.first), hfmm::P<uint32_t>(kd.count),
+                                                      hfmm::P<float>(kd.hs), hfmm::P<float4>(c.pm4),
+                                                      hfmm::P<uint32_t>(c.idx), c.n, (float)c.prm.G, c.ldm,
+                                                      hfmm::P<float>(c.L), acc);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t kd_upward(Ctx &c, cudaStream_t st) {
+  if (c.nleaves == 0) return cudaSuccess;
+  switch (c.p) {
+    case 1: return kd_upward_p<1>(c, st);
+    case 2: return kd_upward_p<2>(c, st);
+    case 3: return kd_upward_p<3>(c, st);
+    case 4: return kd_upward_p<4>(c, st);
+    case 5: return kd_upward_p<5>(c, st);
+    case 6: return kd_upward_p<6>(c, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t kd_downward(Ctx &c, float *acc, cudaStream_t st) {
+  if (c.nleaves == 0) return cudaSuccess;
+  switch (c.p) {
+    case 1: return kd_downward_p<1>(c, acc, st);
+    case 2: return kd_downward_p<2>(c, acc, st);
+    case 3: return kd_downward_p<3>(c, acc, st);
+    case 4: return kd_downward_p<4>(c, acc, st);
+    case 5: return kd_downward_p<5>(c, acc, st);
+    case 6: return kd_downward_p<6>(c, acc, st);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t upward(Ctx &c, cudaStream_t st) {
   if (c.nleaves == 0) return cudaSuccess;

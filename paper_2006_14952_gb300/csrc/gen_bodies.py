@@ -20,6 +20,11 @@ M2MBody<P>:  out[m] += sum_{n <= m} (x/H)^n / n! 2^-(|m|-|n|) in[m-n] for one
 L2LBody<P>:  out[n] = 2^-(|n|+1) sum_{|m| <= P-|n|} (x/H)^m / m! Lp[m+n] for one
              child, x/H = (sx, sy, sz) / 4 (Eq. l2l, scaled L~ = L h^(|n|+1)).
 L2PBody<P>:  a_d += sum_{|n| <= P-1} Lk[n+e_d] u^n / n! (Eq. l2p gradient).
+M2MGenBody<P>: out[m] += sum_{n <= m} d^n / n! rho^(|m|-|n|) in[m-n] for any
+             offset d = (z_P - z_C) / H and scale ratio rho = h / H of child
+             and parent (the k-d tree's boxes; Eq. m2m, scaled).
+L2LGenBody<P>: out[n] += rho^(|n|+1) sum_{|m| <= P-|n|} d^m / m! Lp[m+n],
+             d = (z_C - z_P) / H, rho = h / H (Eq. l2l, scaled).
 M2LTabBody<P, G, g>: acc[n / G] += sum_m T[n+m] Mp[m] for one pair whose scaled
              operator T_c = D_c h^(|c|+1) comes from the (level, offset) table.
 TCStore<P>:  tensor-core M2L operands for one pair: D'_c = u^(|c|+1) D^_c(R^) and
@@ -230,6 +235,49 @@ def gen_passes(P):
     L.append("  }")
     L.append("};")
     out.append("\n".join(L))
+    # ---- M2M, any offset and scale ratio
+    L = [f"template <> struct M2MGenBody<{P}> {{",
+         f"  static __device__ __forceinline__ void run(float dx, float dy, float dz, float rho,"
+         f" const float (&in)[{NC}], float (&o)[{NC}]) {{",
+         "    float rp = 1.f;"]
+    for k in range(P + 1):
+        for a in ms:
+            if sum(a) == k:
+                L.append(f"    const float i{idx(a)} = in[{idx(a)}] * rp;" if k else f"    const float i{idx(a)} = in[{idx(a)}];")
+        if k < P:
+            L.append("    rp *= rho;")
+    nm = _monomials(P, ("dx", "dy", "dz"), L, prefix="w", include_fact=True)
+    for m in ms:
+        terms = []
+        for n in ms:
+            if all(n[d] <= m[d] for d in range(3)):
+                r = (m[0] - n[0], m[1] - n[1], m[2] - n[2])
+                terms.append(f"i{idx(r)}" if n == (0, 0, 0) else f"{nm[n]} * i{idx(r)}")
+        L.append(f"    o[{idx(m)}] += " + " + ".join(terms) + ";")
+    L.append("  }")
+    L.append("};")
+    out.append("\n".join(L))
+    # ---- L2L, any offset and scale ratio
+    L = [f"template <> struct L2LGenBody<{P}> {{",
+         f"  static __device__ __forceinline__ void run(float dx, float dy, float dz, float rho,"
+         f" const float (&p)[{NC}], float (&child)[{NC}]) {{"]
+    nm = _monomials(P, ("dx", "dy", "dz"), L, prefix="w", include_fact=True)
+    L.append("    float rp = rho;")
+    for k in range(P + 1):
+        for n in ms:
+            if sum(n) != k:
+                continue
+            terms = []
+            for m in ms:
+                if sum(m) + sum(n) <= P:
+                    q = (m[0] + n[0], m[1] + n[1], m[2] + n[2])
+                    terms.append(f"p[{idx(q)}]" if m == (0, 0, 0) else f"{nm[m]} * p[{idx(q)}]")
+            L.append(f"    child[{idx(n)}] += rp * (" + " + ".join(terms) + ");")
+        if k < P:
+            L.append("    rp *= rho;")
+    L.append("  }")
+    L.append("};")
+    out.append("\n".join(L))
     # ---- L2P
     L = [f"template <> struct L2PBody<{P}> {{",
          f"  static __device__ __forceinline__ void run(float ux, float uy, float uz, const float (&l)[{NC}],"
@@ -346,7 +394,8 @@ def main(out):
              "template <int P, int G, int g> struct M2LBody;", "template <int P> struct M2LLoad;",
              "template <int P, int G, int g> struct M2LTabBody;",
              "template <int P> struct P2MBody;", "template <int P> struct M2MBody;", "template <int P> struct L2LBody;",
-             "template <int P> struct L2PBody;", "template <int P> struct TCStore;",
+             "template <int P> struct L2PBody;", "template <int P> struct M2MGenBody;",
+             "template <int P> struct L2LGenBody;", "template <int P> struct TCStore;",
              "template <int P> struct TCStoreBF;", "",
              "__device__ __forceinline__ float tf32_round(float x) {",
              "  uint32_t r;",

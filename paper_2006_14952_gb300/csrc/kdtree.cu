@@ -1,0 +1,753 @@
+// ORB / k-d tree variant of the short-range FMM (tree = 1): the tree of Sec. 2.1
+// (Fig. 1), an ORB tree with a leaf limiter whose cells hand their particles to
+// two children of almost equal count, which Sec. 4 keeps as a k-d tree inside
+// every domain.
+//
+// Build, level by level on the device:
+//   - positions wrapped (x - L floor(x / L), as for the octree); for each axis d
+//     the particle indices sorted once by (coordinate d, input index) with the
+//     stable radix sort of order-preserving 64-bit keys;
+//   - a level's node reads its particles' bounding box from the first and last
+//     entries of its range in the three orders; above leaf_max it splits on the
+//     axis of largest extent (the lowest on a tie): the first floor(n / 2)
+//     particles of that axis' order form the first child.  The other orders are
+//     partitioned stably by the particles' side: an exclusive scan of the side
+//     flags over all positions, less its value at the node's first position,
+//     ranks a particle among the second child's particles.  So every order stays
+//     sorted inside every node, and inside a leaf the x order is the particle
+//     order (that of (x, input index));
+//   - the number of splits of a level is read back to size the next level.
+// Node geometry: the box centre c, half extents e, side (largest extent) in FP64,
+// and the expansion scale h = L 2^-j >= side (j <= 21, the octree's deepest
+// cell side): P2M offsets over h stay within [-1/2, 1/2] and the scale ratios of
+// the translations are powers of two.
+// Walk: level synchronous over the frontier of (sink, source, shift) pairs, one
+// thread per pair, the three rules of Sec. 2.3 on the boxes in FP64 with every
+// operation rounded on its own (no contraction, so the decisions are those of any
+// IEEE FP64 evaluation in the same order); M2L and P2P entries and the next
+// frontier are appended with warp-aggregated atomics, and a list or frontier that
+// outgrows its buffer is grown and the level walked again.  The lists are then
+// sorted by (sink, source, shift), so every sum after them runs in a fixed order.
+// P2P: one warp per sink leaf, its sinks in lanes (a second sink per lane above
+// 32), each source leaf staged in shared memory as FP32 offsets from the sink
+// box centre (the source box's offset formed in FP64 by one lane), keeping only
+// the sources within R_c of the sink box, two sources per packed FP32x2 step.
+#include <algorithm>
+
+#include "p2p_common.cuh"
+
+namespace hfmm {
+namespace {
+
+constexpr int kT = 256;
+
+__global__ void k_kd_wrap(const double *__restrict__ pos, int64_t n, double box, double inv_pow2,
+                          double *__restrict__ xw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  xw[i] = wrap_box_fast(pos[i], box, inv_pow2);
+}
+
+// Order-preserving key of a double (negative values reversed below the positive ones).
+__global__ void k_kd_keys(const double *__restrict__ x, int64_t n, uint64_t *__restrict__ key,
+                          uint32_t *__restrict__ val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t u = (uint64_t)__double_as_longlong(x[i]);
+  key[i] = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+  val[i] = (uint32_t)i;
+}
+
+__global__ void k_kd_root(int64_t n, uint32_t *first, uint32_t *count, int *parent) {
+  first[0] = 0;
+  count[0] = (uint32_t)n;
+  parent[0] = -1;
+}
+
+// One level's nodes [lo, lo + cnt): bounding box and split decision.
+__global__ void k_kd_level(int64_t lo, int64_t cnt, int leaf_max, const double *__restrict__ xw, int64_t n,
+                           const uint32_t *__restrict__ o0, const uint32_t *__restrict__ o1,
+                           const uint32_t *__restrict__ o2, const uint32_t *__restrict__ first,
+                           const uint32_t *__restrict__ count, double *__restrict__ box, int64_t cap,
+                           int *__restrict__ axis, uint32_t *__restrict__ nflag) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t k = lo + t;
+  const uint32_t f = first[k], m = count[k];
+  const uint32_t *ord[3] = {o0, o1, o2};
+  double best = 0.0;
+  int ax = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double a = xw[d * n + ord[d][f]], b = xw[d * n + ord[d][f + m - 1]];
+    box[d * cap + k] = a;
+    box[(3 + d) * cap + k] = b;
+    const double ext = __dsub_rn(b, a);
+    if (d == 0 || ext > best) {  // the lowest axis of the largest extent
+      best = ext;
+      ax = d;
+    }
+  }
+  const bool split = (int64_t)m > leaf_max;
+  axis[k] = split ? ax : -1;
+  nflag[t] = split ? 1u : 0u;
+}
+
+__global__ void k_kd_children(int64_t lo, int64_t cnt, int64_t hi, const int *__restrict__ axis,
+                              const uint32_t *__restrict__ nscan, uint32_t *__restrict__ first,
+                              uint32_t *__restrict__ count, int *__restrict__ child, int *__restrict__ parent) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t k = lo + t;
+  if (axis[k] < 0) {
+    child[k] = -1;
+    return;
+  }
+  const int64_t ch = hi + 2 * (int64_t)nscan[t];
+  const uint32_t f = first[k], m = count[k];
+  child[k] = (int)ch;
+  first[ch] = f;
+  count[ch] = m / 2;
+  first[ch + 1] = f + m / 2;
+  count[ch + 1] = m - m / 2;
+  parent[ch] = parent[ch + 1] = (int)k;
+}
+
+// The side of every particle of a node split on this level (positions of earlier leaves: node < lo).
+__global__ void k_kd_side(int64_t n, int64_t lo, const uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
+                          const uint32_t *__restrict__ count, const int *__restrict__ axis,
+                          const uint32_t *__restrict__ o0, const uint32_t *__restrict__ o1,
+                          const uint32_t *__restrict__ o2, uint8_t *__restrict__ side) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = pnode[i];
+  if ((int64_t)k < lo) return;
+  const int a = axis[k];
+  if (a < 0) return;
+  const uint32_t p = a == 0 ? o0[i] : a == 1 ? o1[i] : o2[i];
+  side[p] = (uint32_t)i - first[k] >= count[k] / 2 ? 1 : 0;
+}
+
+__global__ void k_kd_flag(int64_t n, int64_t lo, const uint32_t *__restrict__ pnode, const int *__restrict__ axis,
+                          const uint32_t *__restrict__ ord, const uint8_t *__restrict__ side,
+                          uint32_t *__restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = pnode[i];
+  flag[i] = ((int64_t)k >= lo && axis[k] >= 0) ? side[ord[i]] : 0u;
+}
+
+// Stable partition of one order inside every node split on this level.
+__global__ void k_kd_scatter(int64_t n, int64_t lo, const uint32_t *__restrict__ pnode,
+                             const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
+                             const int *__restrict__ axis, const uint32_t *__restrict__ ord,
+                             const uint8_t *__restrict__ side, const uint32_t *__restrict__ scan,
+                             uint32_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = pnode[i], v = ord[i];
+  if ((int64_t)k < lo || axis[k] < 0) {
+    out[i] = v;
+    return;
+  }
+  const uint32_t f = first[k], nl = count[k] / 2;
+  const uint32_t r = scan[i] - scan[f];  // particles of the second child before position i
+  out[side[v] ? f + nl + r : (uint32_t)i - r] = v;
+}
+
+__global__ void k_kd_pnode(int64_t n, int64_t lo, uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
+                           const uint32_t *__restrict__ count, const int *__restrict__ child) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = pnode[i];
+  if ((int64_t)k < lo || child[k] < 0) return;
+  pnode[i] = (uint32_t)child[k] + ((uint32_t)i - first[k] >= count[k] / 2 ? 1u : 0u);
+}
+
+// Centre, half extents, side and expansion scale of every node.
+__global__ void k_kd_geo(int64_t nn, int64_t cap, const double *__restrict__ box, double L, double *__restrict__ geo,
+                         float *__restrict__ hs, const int *__restrict__ child, uint32_t *__restrict__ lflag) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nn) return;
+  double side = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double a = box[d * cap + k], b = box[(3 + d) * cap + k];
+    geo[d * cap + k] = __dmul_rn(0.5, __dadd_rn(a, b));
+    geo[(3 + d) * cap + k] = __dmul_rn(0.5, __dsub_rn(b, a));
+    const double e = __dsub_rn(b, a);
+    side = d == 0 ? e : (e > side ? e : side);
+  }
+  geo[6 * cap + k] = side;
+  double h = L;
+  for (int j = 0; j < kDepth && side <= 0.5 * h; ++j) h *= 0.5;
+  hs[k] = (float)h;
+  lflag[k] = child[k] < 0 ? 1u : 0u;
+}
+
+__global__ void k_kd_leaves(int64_t nn, const uint32_t *__restrict__ lflag, const uint32_t *__restrict__ lscan,
+                            uint32_t *__restrict__ leaves) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nn || !lflag[k]) return;
+  leaves[lscan[k]] = (uint32_t)k;
+}
+
+// Particles in tree order: positions, input index, offset from the leaf's box centre and mass.
+__global__ void k_kd_particles(int64_t n, const uint32_t *__restrict__ o0, const double *__restrict__ xw,
+                               const float *__restrict__ mass, const uint32_t *__restrict__ pnode,
+                               const double *__restrict__ geo, int64_t cap, double *__restrict__ xs,
+                               uint32_t *__restrict__ perm, float4 *__restrict__ pm4) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t p = o0[i], k = pnode[i];
+  float off[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double x = xw[d * n + p];
+    xs[d * n + i] = x;
+    off[d] = (float)__dsub_rn(x, geo[d * cap + k]);
+  }
+  perm[i] = p;
+  pm4[i] = make_float4(off[0], off[1], off[2], mass[p]);
+}
+
+// ------------------------------------------------------------------ walk
+struct KdGeo {
+  const double *g;  // [7][cap]
+  int64_t cap;
+  __device__ double c(int d, uint32_t k) const { return g[d * cap + k]; }
+  __device__ double e(int d, uint32_t k) const { return g[(3 + d) * cap + k]; }
+  __device__ double side(uint32_t k) const { return g[6 * cap + k]; }
+};
+
+// 0 skip, 1 M2L, 2 open: the rules of Sec. 2.3 on the boxes (sink a, source b shifted by s L).
+__device__ __forceinline__ int kd_classify(const KdGeo &G, uint32_t a, uint32_t b, uint32_t s, double L, double rc2,
+                                           double theta2, int rule, int size_rule) {
+  double sc2 = 0.0, sm2 = 0.0, sx2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double dc = __dsub_rn(__dadd_rn(G.c(d, b), (double)shift_component(s, d) * L), G.c(d, a));
+    const double ad = fabs(dc);
+    const double w = __dadd_rn(G.e(d, a), G.e(d, b));
+    double gap = __dsub_rn(ad, w);
+    if (gap < 0.0) gap = 0.0;
+    const double far = __dadd_rn(ad, w);
+    sc2 = __dadd_rn(sc2, __dmul_rn(dc, dc));
+    sm2 = __dadd_rn(sm2, __dmul_rn(gap, gap));
+    sx2 = __dadd_rn(sx2, __dmul_rn(far, far));
+  }
+  if (sm2 > rc2) return 0;
+  const bool trans = rule == 0 ? sc2 > rc2 : sx2 > rc2;
+  const double sa = G.side(a), sb = G.side(b);
+  const double wl = size_rule == 0 ? sb : (sa > sb ? sa : sb);
+  const double lim = __dmul_rn(theta2, sc2);  // a pair with theta S_c = 0 is never accepted
+  if (!trans && lim > 0.0 && __dmul_rn(wl, wl) <= lim) return 1;
+  return 2;
+}
+
+__global__ void k_kd_roots(uint64_t *front) {
+  const uint32_t s = threadIdx.x;
+  if (s < 27) front[s] = pack_pair(0u, 0u, s);
+}
+
+__global__ void k_kd_set_ctr(unsigned long long *ctr, unsigned long long a, unsigned long long b,
+                             unsigned long long c) {
+  ctr[0] = a;
+  ctr[1] = b;
+  ctr[2] = c;
+}
+
+// Append the entries of the lanes with `take` at consecutive slots of a list
+// (one atomic per warp); slots at or above cap are counted, not written.
+__device__ __forceinline__ void warp_append(bool take, uint64_t e, unsigned long long *ctr, uint64_t *out,
+                                            unsigned long long cap) {
+  const unsigned mask = __ballot_sync(0xffffffffu, take);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+  if (take && slot < cap) out[slot] = e;
+}
+
+__global__ void __launch_bounds__(kT) k_kd_walk(const uint64_t *__restrict__ front, unsigned long long nf,
+                                                uint64_t *__restrict__ next, unsigned long long cap_next,
+                                                uint64_t *__restrict__ m2l, unsigned long long cap_m2l,
+                                                uint64_t *__restrict__ p2p, unsigned long long cap_p2p,
+                                                unsigned long long *__restrict__ ctr, KdGeo G,
+                                                const int *__restrict__ child, double L, double rc2, double theta2,
+                                                int rule, int size_rule) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < nf; base += stride) {
+    const unsigned long long t = base + threadIdx.x;
+    const bool valid = t < nf;
+    uint32_t a = 0, b = 0, s = 0;
+    int cls = 0;
+    uint64_t e = 0;
+    if (valid) {
+      e = front[t];
+      a = pair_sink(e);
+      b = pair_src(e);
+      s = pair_shift(e);
+      cls = kd_classify(G, a, b, s, L, rc2, theta2, rule, size_rule);
+    }
+    int ca = -1, cb = -1;
+    bool opena = false, openb = false;
+    if (cls == 2) {
+      ca = child[a];
+      cb = child[b];
+      if (ca < 0 && cb < 0) {
+        cls = 3;  // two leaves: P2P
+      } else if (ca < 0) {
+        openb = true;
+      } else if (cb < 0) {
+        opena = true;
+      } else {
+        const double sa = G.side(a), sb = G.side(b);
+        opena = sa >= sb;
+        openb = sb >= sa;
+      }
+    }
+    warp_append(cls == 1, e, ctr + 1, m2l, cap_m2l);
+    warp_append(cls == 3, e, ctr + 2, p2p, cap_p2p);
+    // the children pairs: (opena ? 2 : 1) x (openb ? 2 : 1) of them
+    const uint32_t nkid = cls == 2 ? (opena ? 2u : 1u) * (openb ? 2u : 1u) : 0u;
+    uint32_t incl = nkid;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (tot == 0) continue;
+    unsigned long long wb = 0;
+    if (lane == 31) wb = atomicAdd(ctr, (unsigned long long)tot);
+    wb = __shfl_sync(0xffffffffu, wb, 31);
+    unsigned long long slot = wb + incl - nkid;
+    if (nkid) {
+      const uint32_t a0 = opena ? (uint32_t)ca : a, a1 = opena ? a0 + 2 : a + 1;
+      const uint32_t b0 = openb ? (uint32_t)cb : b, b1 = openb ? b0 + 2 : b + 1;
+      for (uint32_t x = a0; x < a1; ++x)
+        for (uint32_t y = b0; y < b1; ++y, ++slot)
+          if (slot < cap_next) next[slot] = pack_pair(x, y, s);
+    }
+  }
+}
+
+// CSR bounds of a list sorted by sink.
+__global__ void k_kd_csr(const uint64_t *__restrict__ lst, int64_t n, uint32_t *__restrict__ beg,
+                         uint32_t *__restrict__ end) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t k = pair_sink(lst[t]);
+  if (t == 0 || pair_sink(lst[t - 1]) != k) beg[k] = (uint32_t)t;
+  if (t == n - 1 || pair_sink(lst[t + 1]) != k) end[k] = (uint32_t)(t + 1);
+}
+
+// ------------------------------------------------------------------ P2P
+// One warp per sink leaf (grid-stride over the leaves): sinks i = first + lane and
+// first + lane + 32.  Per list entry, one lane forms the source box's offset from
+// the sink box centre in FP64 (this GPU's FP64 rate is low) and broadcasts it; the
+// sources within R_c of the sink box are staged in shared memory (SoA, padded to
+// an even count with a far, massless source) and each lane evaluates two sources
+// at a time with packed FP32x2 operations: the pair force of Sec. 2.2 with the
+// hard cut-off, added to acc in input order.
+constexpr int kKdStage = 64;
+
+__global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
+                                               const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
+                                               KdGeo Gm, const uint32_t *__restrict__ beg,
+                                               const uint32_t *__restrict__ end, const uint64_t *__restrict__ lst,
+                                               const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm,
+                                               int64_t n, double L, PairFit2 fit, float G, float *__restrict__ acc) {
+  __shared__ __align__(16) float sx[kT / 32][kKdStage + 2], sy[kT / 32][kKdStage + 2], sz[kT / 32][kKdStage + 2],
+      sw[kT / 32][kKdStage + 2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float *X = sx[wid], *Y = sy[wid], *Z = sz[wid], *Wm = sw[wid];
+  const float rc2_cull = fit.rc2 * (1.f + 1.f / 4096.f);  // far above the FP32 rounding of either distance
+  const int64_t nw = (int64_t)gridDim.x * (kT / 32);
+  for (int64_t t = (int64_t)blockIdx.x * (kT / 32) + wid; t < nl; t += nw) {
+    const uint32_t k = leaves[t];
+    const uint32_t f = first[k], m = count[k];
+    const uint32_t tb = beg[k], te = end[k];
+    const bool has0 = (uint32_t)lane < m, has1 = (uint32_t)lane + 32u < m;
+    const bool two = m > 32;  // warp-uniform
+    const float4 q0 = has0 ? pm4[f + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 q1 = has1 ? pm4[f + lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the sink offsets, negated, as (x, x) pairs
+    const float2 n0x = f2(-q0.x), n0y = f2(-q0.y), n0z = f2(-q0.z);
+    const float2 n1x = f2(-q1.x), n1y = f2(-q1.y), n1z = f2(-q1.z);
+    // the sink box's half extents (its particles' offsets lie within them, up to FP32 rounding)
+    const float ex = (float)Gm.e(0, k), ey = (float)Gm.e(1, k), ez = (float)Gm.e(2, k);
+    float2 a0x = f2(0.f), a0y = f2(0.f), a0z = f2(0.f), a1x = f2(0.f), a1y = f2(0.f), a1z = f2(0.f);
+    for (uint32_t q = tb; q < te; ++q) {
+      const uint64_t e = lst[q];
+      const uint32_t b = pair_src(e), s = pair_shift(e);
+      const uint32_t fb = first[b], mb = count[b];
+      float ox = 0.f, oy = 0.f, oz = 0.f;
+      if (lane < 3) {
+        const double d = __dsub_rn(__dadd_rn(Gm.c(lane, b), (double)shift_component(s, lane) * L), Gm.c(lane, k));
+        const float v = (float)d;
+        ox = v;
+      }
+      oy = __shfl_sync(0xffffffffu, ox, 1);
+      oz = __shfl_sync(0xffffffffu, ox, 2);
+      ox = __shfl_sync(0xffffffffu, ox, 0);
+      __syncwarp();
+      uint32_t kept = 0;
+      for (uint32_t j0 = 0; j0 < mb; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool keep = false;
+        if (j < mb) {
+          p = pm4[fb + j];
+          p.x += ox;
+          p.y += oy;
+          p.z += oz;
+          const float gx = fmaxf(fabsf(p.x) - ex, 0.f), gy = fmaxf(fabsf(p.y) - ey, 0.f),
+                      gz = fmaxf(fabsf(p.z) - ez, 0.f);
+          keep = gx * gx + gy * gy + gz * gz < rc2_cull;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const uint32_t w = kept + __popc(mask & ((1u << lane) - 1u));
+          X[w] = p.x;
+          Y[w] = p.y;
+          Z[w] = p.z;
+          Wm[w] = p.w;
+        }
+        kept += __popc(mask);
+      }
+      if (kept & 1u) {
+        if (lane == 0) {  // a far, massless partner for the last source
+          X[kept] = 1e18f;
+          Y[kept] = 0.f;
+          Z[kept] = 0.f;
+          Wm[kept] = 0.f;
+        }
+        ++kept;
+      }
+      __syncwarp();
+      auto pair2 = [&](float2 px, float2 py, float2 pz, float2 w, float2 nx, float2 ny, float2 nz, float2 &ax,
+                       float2 &ay, float2 &az) {
+        const float2 dx = __fadd2_rn(px, nx), dy = __fadd2_rn(py, ny), dz = __fadd2_rn(pz, nz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const bool in0 = r2.x < fit.rc2 && r2.x > 0.f, in1 = r2.y < fit.rc2 && r2.y > 0.f;
+        // outside (0, R_c) the values below may be inf / NaN; the selects discard them
+        const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        const float2 r3 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+        const float2 u = __ffma2_rn(r2, ri, fit.nrmid);  // r - R_c / 2
+        float2 qv = fit.c[9];
+#pragma unroll
+        for (int i = 8; i >= 0; --i) qv = __ffma2_rn(qv, u, fit.c[i]);
+        const float2 ea = __fmul2_rn(r2, fit.kexp);
+        float2 fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv), r3), w);
+        fs.x = in0 ? fs.x : 0.f;
+        fs.y = in1 ? fs.y : 0.f;
+        ax = __ffma2_rn(fs, dx, ax);
+        ay = __ffma2_rn(fs, dy, ay);
+        az = __ffma2_rn(fs, dz, az);
+      };
+      if (two) {
+#pragma unroll 2
+        for (uint32_t j = 0; j < kept; j += 2) {
+          const float2 px = *reinterpret_cast<const float2 *>(X + j), py = *reinterpret_cast<const float2 *>(Y + j);
+          const float2 pz = *reinterpret_cast<const float2 *>(Z + j), w = *reinterpret_cast<const float2 *>(Wm + j);
+          pair2(px, py, pz, w, n0x, n0y, n0z, a0x, a0y, a0z);
+          pair2(px, py, pz, w, n1x, n1y, n1z, a1x, a1y, a1z);
+        }
+      } else {
+#pragma unroll 4
+        for (uint32_t j = 0; j < kept; j += 2) {
+          const float2 px = *reinterpret_cast<const float2 *>(X + j), py = *reinterpret_cast<const float2 *>(Y + j);
+          const float2 pz = *reinterpret_cast<const float2 *>(Z + j), w = *reinterpret_cast<const float2 *>(Wm + j);
+          pair2(px, py, pz, w, n0x, n0y, n0z, a0x, a0y, a0z);
+        }
+      }
+    }
+    if (has0) {
+      const uint32_t o = perm[f + lane];
+      acc[o] += G * (a0x.x + a0x.y);
+      acc[n + o] += G * (a0y.x + a0y.y);
+      acc[2 * n + o] += G * (a0z.x + a0z.y);
+    }
+    if (has1) {
+      const uint32_t o = perm[f + lane + 32];
+      acc[o] += G * (a1x.x + a1x.y);
+      acc[n + o] += G * (a1y.x + a1y.y);
+      acc[2 * n + o] += G * (a1z.x + a1z.y);
+    }
+  }
+}
+
+#define TRY(x)                      \
+  do {                              \
+    cudaError_t e_ = (x);           \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+// Read one device uint64 (synchronises st).
+cudaError_t read_u64(Ctx &c, const void *src, uint64_t *out, int count, cudaStream_t st) {
+  TRY(cudaMemcpyAsync(c.h_pinned, src, 8 * (size_t)count, cudaMemcpyDeviceToHost, st));
+  TRY(cudaStreamSynchronize(st));
+  for (int q = 0; q < count; ++q) out[q] = c.h_pinned[q];
+  return cudaSuccess;
+}
+
+KdGeo kd_geo(Ctx &c) { return KdGeo{P<double>(c.kd.geo), c.kd.cap}; }
+
+// The walk, then the lists sorted by (sink, source, shift) and their CSR bounds.
+cudaError_t kd_walk(Ctx &c, cudaStream_t st) {
+  KdTree &kd = c.kd;
+  const uint64_t nl = (uint64_t)std::max<int64_t>(c.nleaves, 1);
+  uint64_t cap_f = std::max<uint64_t>(kd.caps[0], std::max<uint64_t>(1u << 16, 64 * nl));
+  uint64_t cap_m = std::max<uint64_t>(kd.caps[1], std::max<uint64_t>(1u << 16, 48 * nl));
+  uint64_t cap_p = std::max<uint64_t>(kd.caps[2], std::max<uint64_t>(1u << 16, 40 * nl));
+  if (c.prm.list_init > 0 && kd.caps[0] == 0) cap_f = cap_m = cap_p = (uint64_t)c.prm.list_init;
+  cap_f = std::max<uint64_t>(cap_f, 32);  // the 27 root pairs
+  TRY(ensure(c.front, cap_f * 8));
+  TRY(ensure(c.front_next, cap_f * 8));
+  TRY(ensure(c.m2l, cap_m * 8));
+  TRY(ensure(c.p2p, cap_p * 8));
+  TRY(ensure(kd.ctr, 64));
+  unsigned long long *ctr = P<unsigned long long>(kd.ctr);
+  k_kd_roots<<<1, 32, 0, st>>>(P<uint64_t>(c.front));
+  note_launch();
+  int dev = 0, nsm = 0;
+  TRY(cudaGetDevice(&dev));
+  TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  uint64_t nf = 27, nm = 0, np = 0;
+  c.traverse_iters = 0;
+  int64_t pairs = 0, walks = 1;
+  for (;;) {
+    k_kd_set_ctr<<<1, 1, 0, st>>>(ctr, 0ull, nm, np);
+    note_launch();
+    const unsigned g = (unsigned)std::min<uint64_t>((nf + kT - 1) / kT, (uint64_t)nsm * 8);
+    k_kd_walk<<<g, kT, 0, st>>>(P<uint64_t>(c.front), nf, P<uint64_t>(c.front_next), cap_f, P<uint64_t>(c.m2l),
+                                cap_m, P<uint64_t>(c.p2p), cap_p, ctr, kd_geo(c), P<int>(kd.child), c.prm.box,
+                                c.rc * c.rc, c.prm.theta * c.prm.theta, c.prm.transition_rule, c.prm.size_rule);
+    note_launch();
+    TRY(cudaGetLastError());
+    uint64_t h[3];
+    TRY(read_u64(c, ctr, h, 3, st));
+    if (h[0] > cap_f || h[1] > cap_m || h[2] > cap_p) {
+      // an outgrown buffer: grow it (keeping the entries of earlier levels) and walk the level again
+      ++walks;
+      if (h[0] > cap_f) {
+        cap_f = h[0] + h[0] / 2 + 4096;
+        TRY(ensure_keep(c.front, cap_f * 8, nf * 8, st));
+        TRY(ensure(c.front_next, cap_f * 8));
+      }
+      if (h[1] > cap_m) {
+        cap_m = h[1] + h[1] / 2 + 4096;
+        TRY(ensure_keep(c.m2l, cap_m * 8, nm * 8, st));
+      }
+      if (h[2] > cap_p) {
+        cap_p = h[2] + h[2] / 2 + 4096;
+        TRY(ensure_keep(c.p2p, cap_p * 8, np * 8, st));
+      }
+      continue;
+    }
+    pairs += (int64_t)nf;
+    ++c.traverse_iters;
+    nm = h[1];
+    np = h[2];
+    nf = h[0];
+    std::swap(c.front, c.front_next);
+    if (nf == 0) break;
+  }
+  kd.caps[0] = cap_f;
+  kd.caps[1] = cap_m;
+  kd.caps[2] = cap_p;
+  c.nm2l = (int64_t)nm;
+  c.np2p = (int64_t)np;
+  c.frontier_items = pairs;
+  c.traverse_walks = walks;
+  return cudaSuccess;
+}
+
+cudaError_t kd_group(Ctx &c, cudaStream_t st) {
+  const size_t nn = (size_t)c.nnodes;
+  TRY(ensure(c.m2l_beg, nn * 4));
+  TRY(ensure(c.m2l_end, nn * 4));
+  TRY(ensure(c.p2p_beg, nn * 4));
+  TRY(ensure(c.p2p_end, nn * 4));
+  DBuf *lst[2] = {&c.m2l, &c.p2p}, *alt[2] = {&c.m2l_alt, &c.p2p_alt};
+  DBuf *beg[2] = {&c.m2l_beg, &c.p2p_beg}, *end[2] = {&c.m2l_end, &c.p2p_end};
+  const int64_t len[2] = {c.nm2l, c.np2p};
+  for (int w = 0; w < 2; ++w) {
+    TRY(cudaMemsetAsync(beg[w]->p, 0, nn * 4, st));
+    TRY(cudaMemsetAsync(end[w]->p, 0, nn * 4, st));
+    if (len[w] == 0) continue;
+    TRY(ensure(*alt[w], std::max(lst[w]->cap, (size_t)len[w] * 8)));
+    bool in_alt = false;
+    TRY(radix_sort_u64(P<uint64_t>(*lst[w]), nullptr, P<uint64_t>(*alt[w]), nullptr, (size_t)len[w], 0,
+                       kSinkShift + kSinkBits, &in_alt, c.tmp, st));
+    if (in_alt) std::swap(*lst[w], *alt[w]);
+    k_kd_csr<<<blocks_for((size_t)len[w], kT), kT, 0, st>>>(P<uint64_t>(*lst[w]), len[w], P<uint32_t>(*beg[w]),
+                                                             P<uint32_t>(*end[w]));
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t kd_p2p(Ctx &c, float *acc, cudaStream_t st) {
+  if (c.np2p == 0 || c.nleaves == 0) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  TRY(cudaGetDevice(&dev));
+  TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned g = (unsigned)std::min<int64_t>((c.nleaves + 7) / 8, (int64_t)nsm * 8);
+  k_kd_p2p<<<g, kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count),
+                             kd_geo(c), P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p),
+                             P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G,
+                             acc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st) {
+  KdTree &kd = c.kd;
+  c.n = n;
+  c.nnodes = c.nleaves = 0;
+  c.nlevels = 0;
+  c.have_tree = false;
+  kd.level_start.assign(1, 0);
+  if (n == 0) {
+    c.have_tree = true;
+    return cudaSuccess;
+  }
+  // a leaf of a split node holds at least floor((leaf_max + 1) / 2) particles
+  const int64_t lmin = std::max(1, (c.prm.leaf_max + 1) / 2);
+  const int64_t cap = 2 * ((n + lmin - 1) / lmin) + 2;
+  if (cap > ((int64_t)1 << kSinkBits)) return cudaErrorInvalidValue;  // mapped to HFMM_ERR_CAPACITY
+  kd.cap = cap;
+  if (c.prm.profile & 1) cudaEventRecord(c.ev[0], st);
+  TRY(ensure(kd.xw, (size_t)n * 24));
+  for (int d = 0; d < 3; ++d) {
+    TRY(ensure(kd.ord[d], (size_t)n * 4));
+    TRY(ensure(kd.ord2[d], (size_t)n * 4));
+  }
+  TRY(ensure(kd.side, (size_t)n));
+  TRY(ensure(kd.flag, (size_t)n * 4));
+  TRY(ensure(kd.scan, (size_t)n * 4));
+  TRY(ensure(kd.pnode, (size_t)n * 4));
+  TRY(ensure(kd.nflag, (size_t)cap * 4));
+  TRY(ensure(kd.nscan, (size_t)cap * 4));
+  TRY(ensure(kd.first, (size_t)cap * 4));
+  TRY(ensure(kd.count, (size_t)cap * 4));
+  TRY(ensure(kd.child, (size_t)cap * 4));
+  TRY(ensure(kd.parent, (size_t)cap * 4));
+  TRY(ensure(kd.axis, (size_t)cap * 4));
+  TRY(ensure(kd.box, (size_t)cap * 48));
+  TRY(ensure(kd.geo, (size_t)cap * 56));
+  TRY(ensure(kd.hs, (size_t)cap * 4));
+  TRY(ensure(c.key, (size_t)n * 8));
+  TRY(ensure(c.key_alt, (size_t)n * 8));
+  TRY(ensure(c.idx, (size_t)n * 4));
+  TRY(ensure(c.xs, (size_t)n * 24));
+  TRY(ensure(c.pm4, (size_t)n * 16));
+  TRY(ensure(c.leaves, (size_t)cap * 4));
+  const double inv_pow2 = box_inverse_if_pow2(c.prm.box);
+  double *xw = P<double>(kd.xw);
+  k_kd_wrap<<<blocks_for((size_t)(3 * n), kT), kT, 0, st>>>(pos, n, c.prm.box, inv_pow2, xw);
+  note_launch();
+  for (int d = 0; d < 3; ++d) {
+    k_kd_keys<<<blocks_for((size_t)n, kT), kT, 0, st>>>(xw + d * n, n, P<uint64_t>(c.key), P<uint32_t>(kd.ord[d]));
+    note_launch();
+    bool alt = false;
+    TRY(radix_sort_u64(P<uint64_t>(c.key), P<uint32_t>(kd.ord[d]), P<uint64_t>(c.key_alt), P<uint32_t>(kd.ord2[d]),
+                       (size_t)n, 0, 64, &alt, c.tmp, st));
+    if (alt) std::swap(kd.ord[d], kd.ord2[d]);
+  }
+  if (c.prm.profile & 1) cudaEventRecord(c.ev[1], st);
+  uint32_t *first = P<uint32_t>(kd.first), *count = P<uint32_t>(kd.count);
+  int *child = P<int>(kd.child), *parent = P<int>(kd.parent), *axis = P<int>(kd.axis);
+  TRY(ensure(kd.ctr, 64));
+  uint64_t *total = P<uint64_t>(kd.ctr) + 4;
+  k_kd_root<<<1, 1, 0, st>>>(n, first, count, parent);
+  note_launch();
+  TRY(cudaMemsetAsync(kd.pnode.p, 0, (size_t)n * 4, st));
+  const unsigned gn = blocks_for((size_t)n, kT);
+  int64_t lo = 0, hi = 1;
+  for (int level = 0;; ++level) {
+    if (level >= 64) return cudaErrorInvalidValue;
+    const int64_t cnt = hi - lo;
+    const unsigned gl = blocks_for((size_t)cnt, kT);
+    k_kd_level<<<gl, kT, 0, st>>>(lo, cnt, c.prm.leaf_max, xw, n, P<uint32_t>(kd.ord[0]), P<uint32_t>(kd.ord[1]),
+                                  P<uint32_t>(kd.ord[2]), first, count, P<double>(kd.box), cap, axis,
+                                  P<uint32_t>(kd.nflag));
+    note_launch();
+    TRY(scan_u32(P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), total, (size_t)cnt, c.tmp2, st));
+    k_kd_children<<<gl, kT, 0, st>>>(lo, cnt, hi, axis, P<uint32_t>(kd.nscan), first, count, child, parent);
+    note_launch();
+    uint64_t nsplit = 0;
+    TRY(read_u64(c, total, &nsplit, 1, st));
+    kd.level_start.push_back(hi);
+    if (nsplit == 0) {
+      c.nlevels = level + 1;
+      break;
+    }
+    if (hi + 2 * (int64_t)nsplit > cap) return cudaErrorInvalidValue;
+    k_kd_side<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), first, count, axis, P<uint32_t>(kd.ord[0]),
+                                 P<uint32_t>(kd.ord[1]), P<uint32_t>(kd.ord[2]), P<uint8_t>(kd.side));
+    note_launch();
+    for (int d = 0; d < 3; ++d) {
+      k_kd_flag<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), axis, P<uint32_t>(kd.ord[d]), P<uint8_t>(kd.side),
+                                   P<uint32_t>(kd.flag));
+      note_launch();
+      TRY(scan_u32(P<uint32_t>(kd.flag), P<uint32_t>(kd.scan), total, (size_t)n, c.tmp2, st));
+      k_kd_scatter<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), first, count, axis, P<uint32_t>(kd.ord[d]),
+                                      P<uint8_t>(kd.side), P<uint32_t>(kd.scan), P<uint32_t>(kd.ord2[d]));
+      note_launch();
+      std::swap(kd.ord[d], kd.ord2[d]);
+    }
+    k_kd_pnode<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), first, count, child);
+    note_launch();
+    lo = hi;
+    hi += 2 * (int64_t)nsplit;
+  }
+  c.nnodes = hi;
+  const unsigned gk = blocks_for((size_t)hi, kT);
+  k_kd_geo<<<gk, kT, 0, st>>>(hi, cap, P<double>(kd.box), c.prm.box, P<double>(kd.geo), P<float>(kd.hs), child,
+                              P<uint32_t>(kd.nflag));
+  note_launch();
+  TRY(scan_u32(P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), total, (size_t)hi, c.tmp2, st));
+  k_kd_leaves<<<gk, kT, 0, st>>>(hi, P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), P<uint32_t>(c.leaves));
+  note_launch();
+  k_kd_particles<<<gn, kT, 0, st>>>(n, P<uint32_t>(kd.ord[0]), xw, mass, P<uint32_t>(kd.pnode), P<double>(kd.geo),
+                                    cap, P<double>(c.xs), P<uint32_t>(c.idx), P<float4>(c.pm4));
+  note_launch();
+  uint64_t nleaves = 0;
+  TRY(read_u64(c, total, &nleaves, 1, st));
+  c.nleaves = (int64_t)nleaves;
+  if (c.prm.profile & 1) cudaEventRecord(c.ev[2], st);
+  c.have_tree = true;
+  return cudaGetLastError();
+}
+
+cudaError_t kd_short_range(Ctx &c, float *acc, cudaStream_t st) {
+  const bool prof = (c.prm.profile & 1) != 0;
+  if (prof) cudaEventRecord(c.ev[3], st);
+  TRY(kd_upward(c, st));
+  if (prof) cudaEventRecord(c.ev[4], st);
+  TRY(kd_walk(c, st));
+  if (c.nm2l > (int64_t)UINT32_MAX || c.np2p > (int64_t)UINT32_MAX) return cudaErrorInvalidValue;
+  if (prof) cudaEventRecord(c.ev[5], st);
+  TRY(kd_group(c, st));
+  if (prof) cudaEventRecord(c.ev[6], st);
+  TRY(kd_m2l(c, st));
+  if (prof) cudaEventRecord(c.ev[7], st);
+  TRY(kd_downward(c, acc, st));
+  if (prof) cudaEventRecord(c.ev[8], st);
+  TRY(kd_p2p(c, acc, st));
+  if (prof) cudaEventRecord(c.ev[9], st);
+  return cudaSuccess;
+}
+
+#undef TRY
+
+}  // namespace hfmm

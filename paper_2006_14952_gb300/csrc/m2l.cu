@@ -195,7 +195,97 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// M2L on the k-d tree (tree = 1; orders 1..6): one warp per sink node as in
+// k_m2l, with R = c_A - (c_B + s L) formed in FP64 from the box centres and the
+// scales h_A, h_B of the two nodes (powers of two: v / u = h_B / h_A is exact).
+template <int P>
+__global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_kd_m2l(int64_t nn, const double *__restrict__ geo,
+                                                                 int64_t cap, const float *__restrict__ hs,
+                                                                 const uint32_t *__restrict__ beg,
+                                                                 const uint32_t *__restrict__ end,
+                                                                 const uint64_t *__restrict__ lst,
+                                                                 const float *__restrict__ M, float *__restrict__ L,
+                                                                 int ldm, double box, float inv_rs) {
+  constexpr int NC = ncoef(P);
+  static_assert(M2LSlices<P>::G == 1 && !M2LSlices<P>::kSmem, "orders 1..6");
+  extern __shared__ float sm[];
+  float *wsm = sm + (threadIdx.x >> 5) * 32 * (NC + 1);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nn; k += nw) {
+    const uint32_t tb = beg[k], te = end[k];
+    if (tb == te) continue;
+    const double ca[3] = {geo[k], geo[cap + k], geo[2 * cap + k]};
+    const float hA = hs[k];
+    float acc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = 0.f;
+    for (uint32_t t = tb + lane; t < te; t += 32) {
+      const uint64_t e = lst[t];
+      const uint32_t b = pair_src(e), sh = pair_shift(e);
+      float R[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        R[d] = (float)__dsub_rn(ca[d], __dadd_rn(geo[d * cap + b], (double)shift_component(sh, d) * box));
+      const float r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+      const float rinv = rsqrtf(r2);
+      float f[P + 1];
+      radial_prefactors<P, 0>(r2 * rinv * inv_rs, f);
+      const float u = hA * rinv;
+      float U[P + 1];
+      U[0] = u;
+#pragma unroll
+      for (int q = 1; q <= P; ++q) U[q] = U[q - 1] * u;
+      float Mp[NC];
+      M2LLoad<P>::template run<1>(M + (size_t)b * ldm, hs[b] / hA, Mp);
+      M2LBody<P, 1, 0>::run(R[0] * rinv, R[1] * rinv, R[2] * rinv, f, U, Mp, acc);
+    }
+    // sum over the lanes in a fixed order (shared-memory transpose, as in k_m2l)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) wsm[lane * (NC + 1) + q] = acc[q];
+    __syncwarp();
+    for (int cix = lane; cix < NC; cix += 32) {
+      float a = 0.f;
+#pragma unroll 8
+      for (int m = 0; m < 32; ++m) a += wsm[m * (NC + 1) + cix];
+      L[(size_t)k * ldm + cix] += a;
+    }
+    __syncwarp();
+  }
+}
+
+template <int P>
+cudaError_t launch_kd(Ctx &c, cudaStream_t st) {
+  unsigned g = blocks_for((size_t)c.nnodes, 4);
+  const unsigned cap = 152u * (unsigned)(c.prm.tile_m2l_blocks > 0 ? c.prm.tile_m2l_blocks : 64);
+  if (g > cap) g = cap;
+  const size_t smem = (size_t)4 * 32 * (ncoef(P) + 1) * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_kd_m2l<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_kd_m2l<P><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<double>(c.kd.geo), c.kd.cap, hfmm::P<float>(c.kd.hs),
+                                   hfmm::P<uint32_t>(c.m2l_beg), hfmm::P<uint32_t>(c.m2l_end),
+                                   hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.ldm,
+                                   c.prm.box, (float)(1.0 / c.rs));
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t kd_m2l(Ctx &c, cudaStream_t st) {
+  if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
+  switch (c.p) {
+    case 1: return launch_kd<1>(c, st);
+    case 2: return launch_kd<2>(c, st);
+    case 3: return launch_kd<3>(c, st);
+    case 4: return launch_kd<4>(c, st);
+    case 5: return launch_kd<5>(c, st);
+    case 6: return launch_kd<6>(c, st);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t m2l_pass(Ctx &c, int q, cudaStream_t st) {
   if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;

@@ -22,7 +22,7 @@ HFMM_OK = 0
 ERRORS = {-1: "HFMM_ERR_ARG", -2: "HFMM_ERR_OOM", -3: "HFMM_ERR_CUDA", -4: "HFMM_ERR_CAPACITY",
           -5: "HFMM_ERR_STATE", -6: "HFMM_ERR_TIMEOUT"}
 EXPORT = {"keys": 0, "perm": 1, "nodes": 2, "p2p": 3, "m2l": 4, "multipoles": 5, "locals": 6, "m2l_order": 7,
-          "candidates": 8}
+          "candidates": 8, "kd_nodes": 9, "kd_boxes": 10}
 MLP_WEIGHTS = 5512
 
 # Every symbol include/hfmm.h declares.
@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("tile_p2p_stage", C.c_int), ("tile_p2p_blocks", C.c_int), ("tile_m2l_blocks", C.c_int),
                 ("tile_trav_blocks", C.c_int), ("use_graph", C.c_int), ("tc_wait_polls", C.c_int),
                 ("split", C.c_int), ("p2p_mutual", C.c_int), ("list_init", C.c_int),
-                ("sink_batches", C.c_int)]
+                ("sink_batches", C.c_int), ("tree", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -319,7 +319,8 @@ class Solver:
         self._check(self._lib.hfmm_export(self._h, code, None, C.byref(nb)), "hfmm_export")
         dtype, cols = {"keys": (np.uint64, 0), "perm": (np.uint32, 0), "nodes": (np.int64, 8), "p2p": (np.int64, 3),
                        "m2l": (np.int64, 3), "multipoles": (np.float32, -1), "locals": (np.float32, -1),
-                       "m2l_order": (np.int64, 0), "candidates": (np.int64, 3)}[what]
+                       "m2l_order": (np.int64, 0), "candidates": (np.int64, 3), "kd_nodes": (np.int64, 5),
+                       "kd_boxes": (np.float64, 6)}[what]
         out = np.empty(nb.value // np.dtype(dtype).itemsize, dtype=dtype)
         if nb.value:
             self._check(self._lib.hfmm_export(self._h, code, out.ctypes.data_as(C.c_void_p), C.byref(nb)),
