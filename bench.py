@@ -11,7 +11,8 @@ device time (CUDA events on the launching stream); `e2e` repeats the step
 through the host-buffer C entry point with the copies inside the timing.
 `arms` times the metric's other arm on the same set in the same run (learned
 acceptance with the committed network and 3xTF32 tensor-core M2L) and checks
-both against the same FP64 accuracy sinks.  The roofline's FP32 peak is
+both against the same FP64 accuracy sinks; `kd_tree` times the ORB / k-d tree
+variant (tree 1) with the same parameters and sinks.  The roofline's FP32 peak is
 measured in the same process by the library's FMA probe.  `--split poly` runs
 the polynomial truncation of Sec. 5 instead (accuracy against its own direct
 sum).
@@ -77,6 +78,10 @@ def parse():
     ap.add_argument("--compare", type=int, default=1,
                     help="1: also time the metric's other arm (learned acceptance + 3xTF32 M2L) on the same set")
     ap.add_argument("--compare-theta", type=float, default=0.5, help="safety bound of the learned arm")
+    ap.add_argument("--kd-compare", type=int, default=1,
+                    help="1: also time the ORB / k-d tree variant (tree 1) with the same parameters and sinks")
+    ap.add_argument("--tree", default="octree", choices=["octree", "kd"],
+                    help="tree of the timed arm: Morton octree or the ORB / k-d tree (Sec. 2.1, Sec. 4)")
     ap.add_argument("--accuracy-sinks", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=25.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -384,7 +389,7 @@ def main():
     common = dict(pm_grid=cfg.pm_grid, rs_cells=cfg.rs_cells, rcut_rs=cfg.rcut_rs, theta=args.theta,
                   order=args.order, leaf_max=cfg.leaf_max, m2l_precision=args.m2l_precision,
                   m2l_tables=args.m2l_tables, use_graph=args.graph, split=1 if args.split == "poly" else 0,
-                  p2p_mutual=args.mutual,
+                  p2p_mutual=args.mutual, tree=1 if args.tree == "kd" else 0,
                   **tiles, **mac_kw)
     wts = np.fromfile(args.mlp_weights, dtype=np.uint16) if learned else None
     s = hfmm.Solver(profile=1, **common)
@@ -475,7 +480,11 @@ def main():
     peak_fp32 = max(alu["ffma"], alu["ffma2"])
     peak_src = (f"measured: FP32 FMA probe (hfmm_alu_peak), max of scalar {alu['ffma']:.1f} and packed FP32x2 "
                 f"{alu['ffma2']:.1f} TFLOP/s (derived at 2070 MHz: {derived_fp32:.1f})")
-    if mean["t_p2p"] < 0:  # graph mode: the post-traversal phases are timed as one graph
+    if args.tree == "kd":
+        roof = {"kernel": "k_kd_p2p", "bound": "alu", "achieved": None, "peak": peak_fp32, "unit": "TFLOP/s",
+                "frac": None, "traffic": None,
+                "note": "the k-d tree counts no particle pairs; run with the octree for the P2P roofline"}
+    elif mean["t_p2p"] < 0:  # graph mode: the post-traversal phases are timed as one graph
         roof = {"kernel": "short-range graph (upward, walk, lists, M2L, L2L/L2P, P2P)", "bound": "alu", "achieved": None,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "note": "graph mode times the graph as a whole; run without --graph for the P2P roofline"}
@@ -523,6 +532,28 @@ def main():
                 "both_within_1e-4": bool(accuracy and l_acc and accuracy["rms_rel"] <= 1e-4
                                          and l_acc["rms_rel"] <= 1e-4)}
 
+    # the ORB / k-d tree variant with the same parameters, on the same set and sinks
+    kd_arm = None
+    if args.kd_compare and args.tree == "octree" and not learned and args.split == "gauss" \
+            and args.m2l_precision == 0 and not args.mutual and not args.m2l_tables and args.order <= 6:
+        kcommon = dict(common, tree=1, use_graph=0)
+        kacc = torch.empty_like(acc)
+        k_ms, k_ph, k_launch = time_arm(hfmm, torch, kcommon, None, dpos, dmass, kacc, flush, args.steps,
+                                        args.warmup, stream)
+        k_tot = max_over_ranks(sum(k_ms), dev)
+        kmean = {k[2:]: round(statistics.mean(p[k] for p in k_ph), 4) for k in keys}
+        kst = k_ph[-1]
+        kd_arm = {"path": "ORB / k-d tree (tree 1): median splits along the longest axis of the particles' "
+                          "bounding box, box geometry in the acceptance rules, geometric acceptance, FP32 M2L",
+                  "value": whole_job_rate(ws, n, args.steps, k_tot / 1e3), "unit": UNIT,
+                  "ms_per_step": k_tot / args.steps,
+                  "accuracy": accuracy_of(kacc, sinks, ref) if accuracy is not None else None,
+                  "ratio_over_octree": (whole_job_rate(ws, n, args.steps, k_tot / 1e3) / value),
+                  "breakdown_ms": kmean, "launches_per_step": k_launch / args.steps,
+                  "counts": {"nodes": kst["nnodes"], "leaves": kst["nleaves"], "levels": kst["nlevels"],
+                             "walk_levels": kst["traverse_iters"], "p2p_leaf_pairs": kst["np2p"],
+                             "m2l_pairs": kst["nm2l"], "frontier_pairs": kst["frontier_pairs"]}}
+
     # the whole KDK step (with the PM long range), direct and as one graph
     kdk = None
     if args.kdk and args.split == "gauss" and not learned and args.m2l_precision == 0 and not args.mutual:
@@ -549,6 +580,7 @@ def main():
             "config": {"workload": workload_desc(cfg),
                        "split": "polynomial (Sec. 5)" if args.split == "poly" else "Gaussian (Sec. 2.2)",
                        "p2p": "mutual (third law)" if args.mutual else "one-sided",
+                       "tree": "ORB / k-d tree" if args.tree == "kd" else "Morton octree",
                        "path": ("learned acceptance (network, safety bound theta), " if learned else
                                 "geometric acceptance, ") + (
                            {1: "3xTF32 tensor-core M2L", 2: "BF16x3 tensor-core M2L"}.get(args.m2l_precision)
@@ -561,6 +593,7 @@ def main():
             "accuracy": accuracy,
             "arms": arms,
             "kdk_step": kdk,
+            "kd_tree": kd_arm,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 4), "d2h_bytes_per_step": n * 12},

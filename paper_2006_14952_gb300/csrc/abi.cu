@@ -149,7 +149,7 @@ void for_each_buffer(Ctx &c, F f) {
                   &c.pacc, &c.tf_pairs, &c.tf_segs, &c.tf_sst, &c.lpt_order, &c.lpt_tmp, &c.kd.xw,
                   &c.kd.ord[0], &c.kd.ord[1], &c.kd.ord[2], &c.kd.ord2[0], &c.kd.ord2[1], &c.kd.ord2[2],
                   &c.kd.side, &c.kd.flag, &c.kd.scan, &c.kd.pnode, &c.kd.nflag, &c.kd.nscan, &c.kd.first,
-                  &c.kd.count, &c.kd.child, &c.kd.parent, &c.kd.axis, &c.kd.box, &c.kd.geo, &c.kd.hs,
+                  &c.kd.count, &c.kd.child, &c.kd.parent, &c.kd.axis, &c.kd.box, &c.kd.geo, &c.kd.geof, &c.kd.hs,
                   &c.kd.ctr};
   for (DBuf *b : bufs) f(*b);
 }

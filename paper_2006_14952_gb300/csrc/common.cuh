@@ -281,8 +281,9 @@ struct KdTree {
   DBuf child, parent, axis;      // i32 [cap] first child (-1 leaf), parent (-1 root), split axis (-1 leaf)
   DBuf box;                      // f64 [6][cap] lo xyz, hi xyz of the particles' bounding box
   DBuf geo;                      // f64 [7][cap] centre xyz, half extents xyz, side (largest extent)
+  DBuf geof;                     // f32 [7][cap] the same rounded (the walk's FP32 filter)
   DBuf hs;                       // f32 [cap] expansion scale h: L 2^-j >= side, j <= 21
-  DBuf ctr;                      // u64 [8] walk counters (next frontier, M2L, P2P entries), scan total
+  DBuf ctr;                      // u64 [16]: the walk's counters, then the build's scan total
   std::vector<int64_t> level_start;
   int64_t cap = 0;
   uint64_t caps[3] = {0, 0, 0};  // frontier, M2L and P2P capacities of the last walk

@@ -21,12 +21,14 @@
 // and the expansion scale h = L 2^-j >= side (j <= 21, the octree's deepest
 // cell side): P2M offsets over h stay within [-1/2, 1/2] and the scale ratios of
 // the translations are powers of two.
-// Walk: level synchronous over the frontier of (sink, source, shift) pairs, one
-// thread per pair, the three rules of Sec. 2.3 on the boxes in FP64 with every
-// operation rounded on its own (no contraction, so the decisions are those of any
-// IEEE FP64 evaluation in the same order); M2L and P2P entries and the next
-// frontier are appended with warp-aggregated atomics, and a list or frontier that
-// outgrows its buffer is grown and the level walked again.  The lists are then
+// Walk: one cooperative launch, level synchronous over the frontier of (sink,
+// source, shift) pairs with grid-wide barriers between the levels, one thread per
+// pair, the three rules of Sec. 2.3 on the boxes in FP64 with every operation
+// rounded on its own (no contraction, so the decisions are those of any IEEE FP64
+// evaluation in the same order), taken in FP32 wherever an error bound shows the
+// FP32 comparison cannot differ; M2L and P2P entries and the next frontier are
+// appended with warp-aggregated atomics, and when a list or the frontier outgrows
+// its buffer the buffers are grown and the walk repeated.  The lists are then
 // sorted by (sink, source, shift), so every sum after them runs in a fixed order.
 // P2P: one warp per sink leaf, its sinks in lanes (a second sink per lane above
 // 32), each source leaf staged in shared memory as FP32 offsets from the sink
@@ -34,7 +36,11 @@
 // the sources within R_c of the sink box, two sources per packed FP32x2 step.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "p2p_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hfmm {
 namespace {
@@ -166,7 +172,8 @@ __global__ void k_kd_pnode(int64_t n, int64_t lo, uint32_t *__restrict__ pnode, 
 
 // Centre, half extents, side and expansion scale of every node.
 __global__ void k_kd_geo(int64_t nn, int64_t cap, const double *__restrict__ box, double L, double *__restrict__ geo,
-                         float *__restrict__ hs, const int *__restrict__ child, uint32_t *__restrict__ lflag) {
+                         float *__restrict__ geof, float *__restrict__ hs, const int *__restrict__ child,
+                         uint32_t *__restrict__ lflag) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nn) return;
   double side = 0.0;
@@ -179,6 +186,11 @@ __global__ void k_kd_geo(int64_t nn, int64_t cap, const double *__restrict__ box
     side = d == 0 ? e : (e > side ? e : side);
   }
   geo[6 * cap + k] = side;
+  // the walk's FP32 record of the node: (centre xyz, side), (half extents xyz, first child)
+  reinterpret_cast<float4 *>(geof)[2 * k] = make_float4((float)geo[k], (float)geo[cap + k], (float)geo[2 * cap + k],
+                                                         (float)side);
+  reinterpret_cast<float4 *>(geof)[2 * k + 1] = make_float4((float)geo[3 * cap + k], (float)geo[4 * cap + k],
+                                                             (float)geo[5 * cap + k], __int_as_float(child[k]));
   double h = L;
   for (int j = 0; j < kDepth && side <= 0.5 * h; ++j) h *= 0.5;
   hs[k] = (float)h;
@@ -213,20 +225,34 @@ __global__ void k_kd_particles(int64_t n, const uint32_t *__restrict__ o0, const
 
 // ------------------------------------------------------------------ walk
 struct KdGeo {
-  const double *g;  // [7][cap]
+  const double *g;  // [7][cap]: centre xyz, half extents xyz, side
+  const float *gf;  // [cap][8]: (centre xyz, side), (half extents xyz, first child) rounded to FP32
   int64_t cap;
   __device__ double c(int d, uint32_t k) const { return g[d * cap + k]; }
   __device__ double e(int d, uint32_t k) const { return g[(3 + d) * cap + k]; }
   __device__ double side(uint32_t k) const { return g[6 * cap + k]; }
+  __device__ void rec(uint32_t k, float4 &p, float4 &q) const {
+    const float4 *r = reinterpret_cast<const float4 *>(gf) + 2 * (size_t)k;
+    p = __ldg(r);
+    q = __ldg(r + 1);
+  }
 };
 
-// 0 skip, 1 M2L, 2 open: the rules of Sec. 2.3 on the boxes (sink a, source b shifted by s L).
-__device__ __forceinline__ int kd_classify(const KdGeo &G, uint32_t a, uint32_t b, uint32_t s, double L, double rc2,
-                                           double theta2, int rule, int size_rule) {
+__device__ __forceinline__ float comp(const float4 &v, int d) { return d == 0 ? v.x : d == 1 ? v.y : v.z; }
+
+struct WalkRule {
+  double L, rc2, theta2;
+  float Lf, rc2f, theta2f, dl;  // dl: 16 2^-24 L, the FP32 error bound of a shifted difference
+  int rule, size_rule;
+};
+
+// 0 skip, 1 M2L, 2 open: the rules of Sec. 2.3 on the boxes (sink a, source b shifted by s L),
+// in FP64 with every operation rounded on its own.
+__device__ __forceinline__ int kd_classify64(const KdGeo &G, uint32_t a, uint32_t b, uint32_t s, const WalkRule &R) {
   double sc2 = 0.0, sm2 = 0.0, sx2 = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double dc = __dsub_rn(__dadd_rn(G.c(d, b), (double)shift_component(s, d) * L), G.c(d, a));
+    const double dc = __dsub_rn(__dadd_rn(G.c(d, b), (double)shift_component(s, d) * R.L), G.c(d, a));
     const double ad = fabs(dc);
     const double w = __dadd_rn(G.e(d, a), G.e(d, b));
     double gap = __dsub_rn(ad, w);
@@ -236,25 +262,66 @@ __device__ __forceinline__ int kd_classify(const KdGeo &G, uint32_t a, uint32_t 
     sm2 = __dadd_rn(sm2, __dmul_rn(gap, gap));
     sx2 = __dadd_rn(sx2, __dmul_rn(far, far));
   }
-  if (sm2 > rc2) return 0;
-  const bool trans = rule == 0 ? sc2 > rc2 : sx2 > rc2;
+  if (sm2 > R.rc2) return 0;
+  const bool trans = R.rule == 0 ? sc2 > R.rc2 : sx2 > R.rc2;
   const double sa = G.side(a), sb = G.side(b);
-  const double wl = size_rule == 0 ? sb : (sa > sb ? sa : sb);
-  const double lim = __dmul_rn(theta2, sc2);  // a pair with theta S_c = 0 is never accepted
+  const double wl = R.size_rule == 0 ? sb : (sa > sb ? sa : sb);
+  const double lim = __dmul_rn(R.theta2, sc2);  // a pair with theta S_c = 0 is never accepted
   if (!trans && lim > 0.0 && __dmul_rn(wl, wl) <= lim) return 1;
   return 2;
 }
 
-__global__ void k_kd_roots(uint64_t *front) {
-  const uint32_t s = threadIdx.x;
-  if (s < 27) front[s] = pack_pair(0u, 0u, s);
+// The same decisions, taken in FP32 where they are certain.  In FP32 the node
+// geometry is off by at most 2^-24 L (centres) and 2^-25 L (half extents), so each
+// shifted per-axis difference dc, gap and span (coordinates in [-L, 2L]) is within
+// delta = 16 2^-24 L of its FP64 value, and a sum q of three squares x^2 within
+//   E(q) = 2 (2 delta sum |x| + 3 delta^2 + 8 2^-24 q)
+// (the factor 2 a margin above the rounding analysis); theta^2 S_c^2 within
+// 2 (theta^2 E(S_c^2) + 3 2^-24 theta^2 S_c^2), the squared side within 6 2^-24 of
+// itself, R_c^2 within 2^-23 of itself.  A comparison whose two sides' intervals
+// overlap is taken again in FP64 (this GPU's FP64 rate is low), so the result is
+// always the FP64 one.
+__device__ __noinline__ int kd_classify64_call(const KdGeo &G, uint32_t a, uint32_t b, uint32_t s,
+                                               const WalkRule &R) {
+  return kd_classify64(G, a, b, s, R);
 }
 
-__global__ void k_kd_set_ctr(unsigned long long *ctr, unsigned long long a, unsigned long long b,
-                             unsigned long long c) {
-  ctr[0] = a;
-  ctr[1] = b;
-  ctr[2] = c;
+__device__ __forceinline__ int kd_classify(const KdGeo &G, uint32_t a, uint32_t b, uint32_t s, const WalkRule &R,
+                                           const float4 &A0, const float4 &A1, const float4 &B0, const float4 &B1) {
+  constexpr float u = 5.9604645e-8f;  // 2^-24
+  float sc2 = 0.f, sm2 = 0.f, sx2 = 0.f, Sc = 0.f, Sm = 0.f, Sx = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float dc = __fsub_rn(__fadd_rn(comp(B0, d), (float)shift_component(s, d) * R.Lf), comp(A0, d));
+    const float ad = fabsf(dc);
+    const float w = __fadd_rn(comp(A1, d), comp(B1, d));
+    const float gap = fmaxf(__fsub_rn(ad, w), 0.f);
+    const float far = __fadd_rn(ad, w);
+    sc2 = __fadd_rn(sc2, __fmul_rn(dc, dc));
+    sm2 = __fadd_rn(sm2, __fmul_rn(gap, gap));
+    sx2 = __fadd_rn(sx2, __fmul_rn(far, far));
+    Sc += ad;
+    Sm += gap;
+    Sx += far;
+  }
+  const float dl = R.dl, d2 = 3.f * dl * dl;
+  const float erc = 2.f * u * R.rc2f;
+  const float em = 2.f * (2.f * dl * Sm + d2 + 8.f * u * sm2);
+  if (sm2 - em > R.rc2f + erc) return 0;
+  if (sm2 + em >= R.rc2f - erc) return kd_classify64_call(G, a, b, s, R);
+  const float ec = 2.f * (2.f * dl * Sc + d2 + 8.f * u * sc2);
+  const float tq = R.rule == 0 ? sc2 : sx2;
+  const float et = R.rule == 0 ? ec : 2.f * (2.f * dl * Sx + d2 + 8.f * u * sx2);
+  if (tq - et > R.rc2f + erc) return 2;
+  if (tq + et >= R.rc2f - erc) return kd_classify64_call(G, a, b, s, R);
+  if (R.theta2 == 0.0) return 2;
+  const float sa = A0.w, sb = B0.w;
+  const float wl = R.size_rule == 0 ? sb : fmaxf(sa, sb);
+  const float lim = __fmul_rn(R.theta2f, sc2), w2 = __fmul_rn(wl, wl);
+  const float el = 2.f * (R.theta2f * ec + 3.f * u * lim), ew = 6.f * u * w2;
+  if (lim - el > 0.f && w2 + ew < lim - el) return 1;
+  if (w2 - ew > lim + el) return 2;
+  return kd_classify64_call(G, a, b, s, R);
 }
 
 // Append the entries of the lanes with `take` at consecutive slots of a list
@@ -271,68 +338,109 @@ __device__ __forceinline__ void warp_append(bool take, uint64_t e, unsigned long
   if (take && slot < cap) out[slot] = e;
 }
 
-__global__ void __launch_bounds__(kT) k_kd_walk(const uint64_t *__restrict__ front, unsigned long long nf,
-                                                uint64_t *__restrict__ next, unsigned long long cap_next,
-                                                uint64_t *__restrict__ m2l, unsigned long long cap_m2l,
-                                                uint64_t *__restrict__ p2p, unsigned long long cap_p2p,
-                                                unsigned long long *__restrict__ ctr, KdGeo G,
-                                                const int *__restrict__ child, double L, double rc2, double theta2,
-                                                int rule, int size_rule) {
+// Walk counters (u64): [0] M2L entries, [1] P2P entries, [2] status (1: the frontier
+// buffer outgrown), [3] levels walked, [4] pairs classified, [5..7] next-frontier counts
+// of three consecutive levels (level l appends to [5 + l % 3]; the one of level
+// l + 1 is cleared during level l, after every block has read it at level l - 2).
+constexpr int kWalkCtr = 8;
+
+// The whole walk in one cooperative launch: the 27 root pairs (root, root, s) as
+// the first frontier, then level after level with grid-wide barriers between
+// them, until the frontier is empty or outgrows its buffer (the caller grows the
+// buffers that were outgrown, the frontier's or a list's, and walks again).
+__global__ void __launch_bounds__(kT, 4) k_kd_walk(uint64_t *__restrict__ fa, uint64_t *__restrict__ fb,
+                                                unsigned long long cap_f, uint64_t *__restrict__ m2l,
+                                                unsigned long long cap_m, uint64_t *__restrict__ p2p,
+                                                unsigned long long cap_p, unsigned long long *__restrict__ ctr,
+                                                KdGeo G, const int *__restrict__ child, WalkRule R) {
+  cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < nf; base += stride) {
-    const unsigned long long t = base + threadIdx.x;
-    const bool valid = t < nf;
-    uint32_t a = 0, b = 0, s = 0;
-    int cls = 0;
-    uint64_t e = 0;
-    if (valid) {
-      e = front[t];
-      a = pair_sink(e);
-      b = pair_src(e);
-      s = pair_shift(e);
-      cls = kd_classify(G, a, b, s, L, rc2, theta2, rule, size_rule);
-    }
-    int ca = -1, cb = -1;
-    bool opena = false, openb = false;
-    if (cls == 2) {
-      ca = child[a];
-      cb = child[b];
-      if (ca < 0 && cb < 0) {
-        cls = 3;  // two leaves: P2P
-      } else if (ca < 0) {
-        openb = true;
-      } else if (cb < 0) {
-        opena = true;
-      } else {
-        const double sa = G.side(a), sb = G.side(b);
-        opena = sa >= sb;
-        openb = sb >= sa;
+  const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt < 27) fa[gt] = pack_pair(0u, 0u, (uint32_t)gt);
+  unsigned long long nf = 27, pairs = 0;
+  grid.sync();
+  for (int level = 0;; ++level) {
+    uint64_t *cur = (level & 1) ? fb : fa, *next = (level & 1) ? fa : fb;
+    unsigned long long *ncount = ctr + 5 + level % 3;
+    if (gt == 0) ctr[5 + (level + 1) % 3] = 0;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < nf; base += stride) {
+      const unsigned long long t = base + threadIdx.x;
+      uint32_t a = 0, b = 0, s = 0;
+      int cls = 0;
+      uint64_t e = 0;
+      float4 A0, A1, B0, B1;
+      if (t < nf) {
+        e = cur[t];
+        a = pair_sink(e);
+        b = pair_src(e);
+        s = pair_shift(e);
+        G.rec(a, A0, A1);
+        G.rec(b, B0, B1);
+        cls = kd_classify(G, a, b, s, R, A0, A1, B0, B1);
+      }
+      int ca = -1, cb = -1;
+      bool opena = false, openb = false;
+      if (cls == 2) {
+        ca = __float_as_int(A1.w);
+        cb = __float_as_int(B1.w);
+        if (ca < 0 && cb < 0) {
+          cls = 3;  // two leaves: P2P
+        } else if (ca < 0) {
+          openb = true;
+        } else if (cb < 0) {
+          opena = true;
+        } else if (A0.w != B0.w) {  // rounding to FP32 keeps the order of unequal sides
+          opena = A0.w > B0.w;
+          openb = !opena;
+        } else {
+          const double sa = G.side(a), sb = G.side(b);
+          opena = sa >= sb;
+          openb = sb >= sa;
+        }
+      }
+      warp_append(cls == 1, e, ctr + 0, m2l, cap_m);
+      warp_append(cls == 3, e, ctr + 1, p2p, cap_p);
+      // the children pairs: (opena ? 2 : 1) x (openb ? 2 : 1) of them
+      const uint32_t nkid = cls == 2 ? (opena ? 2u : 1u) * (openb ? 2u : 1u) : 0u;
+      uint32_t incl = nkid;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (tot == 0) continue;
+      unsigned long long wb = 0;
+      if (lane == 31) wb = atomicAdd(ncount, (unsigned long long)tot);
+      wb = __shfl_sync(0xffffffffu, wb, 31);
+      unsigned long long slot = wb + incl - nkid;
+      if (nkid) {
+        const uint32_t a0 = opena ? (uint32_t)ca : a, a1 = opena ? a0 + 2 : a + 1;
+        const uint32_t b0 = openb ? (uint32_t)cb : b, b1 = openb ? b0 + 2 : b + 1;
+        for (uint32_t x = a0; x < a1; ++x)
+          for (uint32_t y = b0; y < b1; ++y, ++slot)
+            if (slot < cap_f) next[slot] = pack_pair(x, y, s);
       }
     }
-    warp_append(cls == 1, e, ctr + 1, m2l, cap_m2l);
-    warp_append(cls == 3, e, ctr + 2, p2p, cap_p2p);
-    // the children pairs: (opena ? 2 : 1) x (openb ? 2 : 1) of them
-    const uint32_t nkid = cls == 2 ? (opena ? 2u : 1u) * (openb ? 2u : 1u) : 0u;
-    uint32_t incl = nkid;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+    pairs += nf;
+    grid.sync();
+    // Every block reads the same count (this level's counter takes no appends until
+    // it is cleared two levels on), so every block takes the same decision.  The
+    // M2L and P2P counters are not read here: blocks already in the next level
+    // append to them.  An outgrown list only stops being written (the counts go on);
+    // the caller compares the final counts with the capacities.
+    const unsigned long long nn = *(volatile unsigned long long *)ncount;
+    const bool over = nn > cap_f;
+    if (over || nn == 0) {
+      if (gt == 0) {
+        ctr[2] = over ? 1ull : 0ull;
+        ctr[3] = (unsigned long long)level + 1;
+        ctr[4] = pairs;
+      }
+      return;
     }
-    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-    if (tot == 0) continue;
-    unsigned long long wb = 0;
-    if (lane == 31) wb = atomicAdd(ctr, (unsigned long long)tot);
-    wb = __shfl_sync(0xffffffffu, wb, 31);
-    unsigned long long slot = wb + incl - nkid;
-    if (nkid) {
-      const uint32_t a0 = opena ? (uint32_t)ca : a, a1 = opena ? a0 + 2 : a + 1;
-      const uint32_t b0 = openb ? (uint32_t)cb : b, b1 = openb ? b0 + 2 : b + 1;
-      for (uint32_t x = a0; x < a1; ++x)
-        for (uint32_t y = b0; y < b1; ++y, ++slot)
-          if (slot < cap_next) next[slot] = pack_pair(x, y, s);
-    }
+    nf = nn;
   }
 }
 
@@ -348,12 +456,13 @@ __global__ void k_kd_csr(const uint64_t *__restrict__ lst, int64_t n, uint32_t *
 
 // ------------------------------------------------------------------ P2P
 // One warp per sink leaf (grid-stride over the leaves): sinks i = first + lane and
-// first + lane + 32.  Per list entry, one lane forms the source box's offset from
-// the sink box centre in FP64 (this GPU's FP64 rate is low) and broadcasts it; the
-// sources within R_c of the sink box are staged in shared memory (SoA, padded to
-// an even count with a far, massless source) and each lane evaluates two sources
-// at a time with packed FP32x2 operations: the pair force of Sec. 2.2 with the
-// hard cut-off, added to acc in input order.
+// first + lane + 32.  The list entries come in windows of 32, one per lane, each
+// lane forming its entry's source-box offset from the sink box centre in FP64
+// (once per entry: this GPU's FP64 rate is low); each entry's sources are held in
+// registers one entry ahead; the sources within R_c of the sink box are staged in
+// shared memory (SoA, padded to an even count with a far, massless source) and
+// each lane evaluates two sources at a time with packed FP32x2 operations: the
+// pair force of Sec. 2.2 with the hard cut-off, added to acc in input order.
 constexpr int kKdStage = 64;
 
 __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
@@ -382,27 +491,54 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
     // the sink box's half extents (its particles' offsets lie within them, up to FP32 rounding)
     const float ex = (float)Gm.e(0, k), ey = (float)Gm.e(1, k), ez = (float)Gm.e(2, k);
     float2 a0x = f2(0.f), a0y = f2(0.f), a0z = f2(0.f), a1x = f2(0.f), a1y = f2(0.f), a1z = f2(0.f);
-    for (uint32_t q = tb; q < te; ++q) {
-      const uint64_t e = lst[q];
-      const uint32_t b = pair_src(e), s = pair_shift(e);
-      const uint32_t fb = first[b], mb = count[b];
-      float ox = 0.f, oy = 0.f, oz = 0.f;
-      if (lane < 3) {
-        const double d = __dsub_rn(__dadd_rn(Gm.c(lane, b), (double)shift_component(s, lane) * L), Gm.c(lane, k));
-        const float v = (float)d;
-        ox = v;
+    // a window of 32 list entries, one per lane: source range and the source box's
+    // offset from the sink box centre (FP64, then FP32)
+    uint32_t wfb = 0, wmb = 0;
+    float wox = 0.f, woy = 0.f, woz = 0.f;
+    auto load_window = [&](uint32_t base) {
+      wmb = 0;
+      if (base + lane < te) {
+        const uint64_t e = lst[base + lane];
+        const uint32_t b = pair_src(e), s = pair_shift(e);
+        wfb = first[b];
+        wmb = count[b];
+        wox = (float)__dsub_rn(__dadd_rn(Gm.c(0, b), (double)shift_component(s, 0) * L), Gm.c(0, k));
+        woy = (float)__dsub_rn(__dadd_rn(Gm.c(1, b), (double)shift_component(s, 1) * L), Gm.c(1, k));
+        woz = (float)__dsub_rn(__dadd_rn(Gm.c(2, b), (double)shift_component(s, 2) * L), Gm.c(2, k));
       }
-      oy = __shfl_sync(0xffffffffu, ox, 1);
-      oz = __shfl_sync(0xffffffffu, ox, 2);
-      ox = __shfl_sync(0xffffffffu, ox, 0);
+    };
+    // the sources of one entry in registers: lane j holds sources j and j + 32
+    float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+    uint32_t cmb = 0;
+    float cox = 0.f, coy = 0.f, coz = 0.f;
+    auto fetch = [&](uint32_t slot) {
+      const uint32_t fb = __shfl_sync(0xffffffffu, wfb, slot);
+      cmb = __shfl_sync(0xffffffffu, wmb, slot);
+      cox = __shfl_sync(0xffffffffu, wox, slot);
+      coy = __shfl_sync(0xffffffffu, woy, slot);
+      coz = __shfl_sync(0xffffffffu, woz, slot);
+      if ((uint32_t)lane < cmb) pa = pm4[fb + lane];
+      if ((uint32_t)lane + 32u < cmb) pb = pm4[fb + lane + 32];
+    };
+    uint32_t wbase = tb;
+    if (tb < te) {
+      load_window(tb);
+      fetch(0);
+    }
+    for (uint32_t q = tb; q < te; ++q) {
+      // stage the sources of entry q within R_c of the sink box (R_c^2 (1 + 2^-12): far
+      // above the FP32 rounding of either distance), compacted in their order
+      const uint32_t mb = cmb;
+      const float ox = cox, oy = coy, oz = coz;
+      const float4 p0 = pa, p1 = pb;
       __syncwarp();
       uint32_t kept = 0;
-      for (uint32_t j0 = 0; j0 < mb; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t j = (uint32_t)(32 * h + lane);
+        float4 p = h ? p1 : p0;
         bool keep = false;
         if (j < mb) {
-          p = pm4[fb + j];
           p.x += ox;
           p.y += oy;
           p.z += oz;
@@ -428,6 +564,14 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
           Wm[kept] = 0.f;
         }
         ++kept;
+      }
+      // the next entry's sources are loaded while this entry's pairs are evaluated
+      if (q + 1 < te) {
+        if (q + 1 - wbase == 32) {
+          wbase = q + 1;
+          load_window(wbase);
+        }
+        fetch(q + 1 - wbase);
       }
       __syncwarp();
       auto pair2 = [&](float2 px, float2 py, float2 pz, float2 w, float2 nx, float2 ny, float2 nz, float2 &ax,
@@ -496,74 +640,68 @@ cudaError_t read_u64(Ctx &c, const void *src, uint64_t *out, int count, cudaStre
   return cudaSuccess;
 }
 
-KdGeo kd_geo(Ctx &c) { return KdGeo{P<double>(c.kd.geo), c.kd.cap}; }
+KdGeo kd_geo(Ctx &c) { return KdGeo{P<double>(c.kd.geo), P<float>(c.kd.geof), c.kd.cap}; }
 
-// The walk, then the lists sorted by (sink, source, shift) and their CSR bounds.
+// The walk (one cooperative launch, repeated with grown buffers while one is outgrown).
 cudaError_t kd_walk(Ctx &c, cudaStream_t st) {
   KdTree &kd = c.kd;
   const uint64_t nl = (uint64_t)std::max<int64_t>(c.nleaves, 1);
-  uint64_t cap_f = std::max<uint64_t>(kd.caps[0], std::max<uint64_t>(1u << 16, 64 * nl));
-  uint64_t cap_m = std::max<uint64_t>(kd.caps[1], std::max<uint64_t>(1u << 16, 48 * nl));
-  uint64_t cap_p = std::max<uint64_t>(kd.caps[2], std::max<uint64_t>(1u << 16, 40 * nl));
+  uint64_t cap_f = std::max<uint64_t>(kd.caps[0], std::max<uint64_t>(1u << 16, 256 * nl));
+  uint64_t cap_m = std::max<uint64_t>(kd.caps[1], std::max<uint64_t>(1u << 16, 32 * nl));
+  uint64_t cap_p = std::max<uint64_t>(kd.caps[2], std::max<uint64_t>(1u << 16, 256 * nl));
   if (c.prm.list_init > 0 && kd.caps[0] == 0) cap_f = cap_m = cap_p = (uint64_t)c.prm.list_init;
   cap_f = std::max<uint64_t>(cap_f, 32);  // the 27 root pairs
-  TRY(ensure(c.front, cap_f * 8));
-  TRY(ensure(c.front_next, cap_f * 8));
-  TRY(ensure(c.m2l, cap_m * 8));
-  TRY(ensure(c.p2p, cap_p * 8));
-  TRY(ensure(kd.ctr, 64));
+  TRY(ensure(kd.ctr, 128));
   unsigned long long *ctr = P<unsigned long long>(kd.ctr);
-  k_kd_roots<<<1, 32, 0, st>>>(P<uint64_t>(c.front));
-  note_launch();
-  int dev = 0, nsm = 0;
+  int dev = 0, nsm = 0, per_sm = 0;
   TRY(cudaGetDevice(&dev));
   TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  uint64_t nf = 27, nm = 0, np = 0;
-  c.traverse_iters = 0;
-  int64_t pairs = 0, walks = 1;
+  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kd_walk, kT, 0));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const unsigned nb = (unsigned)(nsm * std::min(per_sm, 4));
+  WalkRule R;
+  R.L = c.prm.box;
+  R.rc2 = c.rc * c.rc;
+  R.theta2 = c.prm.theta * c.prm.theta;
+  R.Lf = (float)R.L;
+  R.rc2f = (float)R.rc2;
+  R.theta2f = (float)R.theta2;
+  R.dl = (float)std::ldexp(16.0 * R.L, -24);
+  R.rule = c.prm.transition_rule;
+  R.size_rule = c.prm.size_rule;
+  KdGeo G = kd_geo(c);
+  int *child = P<int>(kd.child);
+  int64_t walks = 0;
+  uint64_t h[kWalkCtr];
   for (;;) {
-    k_kd_set_ctr<<<1, 1, 0, st>>>(ctr, 0ull, nm, np);
+    if (++walks > 16) return cudaErrorInvalidValue;
+    TRY(ensure(c.front, cap_f * 8));
+    TRY(ensure(c.front_next, cap_f * 8));
+    TRY(ensure(c.m2l, cap_m * 8));
+    TRY(ensure(c.p2p, cap_p * 8));
+    TRY(cudaMemsetAsync(ctr, 0, kWalkCtr * 8, st));
+    uint64_t *fa = P<uint64_t>(c.front), *fb = P<uint64_t>(c.front_next), *m2l = P<uint64_t>(c.m2l),
+             *p2p = P<uint64_t>(c.p2p);
+    unsigned long long cf = cap_f, cm = cap_m, cp = cap_p;
+    void *args[] = {(void *)&fa, (void *)&fb, (void *)&cf, (void *)&m2l, (void *)&cm, (void *)&p2p, (void *)&cp,
+                    (void *)&ctr, (void *)&G, (void *)&child, (void *)&R};
+    TRY(cudaLaunchCooperativeKernel((const void *)k_kd_walk, dim3(nb), dim3(kT), args, 0, st));
     note_launch();
-    const unsigned g = (unsigned)std::min<uint64_t>((nf + kT - 1) / kT, (uint64_t)nsm * 8);
-    k_kd_walk<<<g, kT, 0, st>>>(P<uint64_t>(c.front), nf, P<uint64_t>(c.front_next), cap_f, P<uint64_t>(c.m2l),
-                                cap_m, P<uint64_t>(c.p2p), cap_p, ctr, kd_geo(c), P<int>(kd.child), c.prm.box,
-                                c.rc * c.rc, c.prm.theta * c.prm.theta, c.prm.transition_rule, c.prm.size_rule);
-    note_launch();
-    TRY(cudaGetLastError());
-    uint64_t h[3];
-    TRY(read_u64(c, ctr, h, 3, st));
-    if (h[0] > cap_f || h[1] > cap_m || h[2] > cap_p) {
-      // an outgrown buffer: grow it (keeping the entries of earlier levels) and walk the level again
-      ++walks;
-      if (h[0] > cap_f) {
-        cap_f = h[0] + h[0] / 2 + 4096;
-        TRY(ensure_keep(c.front, cap_f * 8, nf * 8, st));
-        TRY(ensure(c.front_next, cap_f * 8));
-      }
-      if (h[1] > cap_m) {
-        cap_m = h[1] + h[1] / 2 + 4096;
-        TRY(ensure_keep(c.m2l, cap_m * 8, nm * 8, st));
-      }
-      if (h[2] > cap_p) {
-        cap_p = h[2] + h[2] / 2 + 4096;
-        TRY(ensure_keep(c.p2p, cap_p * 8, np * 8, st));
-      }
-      continue;
-    }
-    pairs += (int64_t)nf;
-    ++c.traverse_iters;
-    nm = h[1];
-    np = h[2];
-    nf = h[0];
-    std::swap(c.front, c.front_next);
-    if (nf == 0) break;
+    TRY(read_u64(c, ctr, h, kWalkCtr, st));
+    if (!h[2] && h[0] <= cap_m && h[1] <= cap_p) break;
+    // an outgrown buffer: grow what the counts ask for (the counts went on past the capacities)
+    const uint64_t nn = std::max(std::max(h[5], h[6]), h[7]);
+    if (nn > cap_f) cap_f = nn + nn / 2 + 4096;
+    if (h[0] > cap_m) cap_m = h[0] + h[0] / 2 + 4096;
+    if (h[1] > cap_p) cap_p = h[1] + h[1] / 2 + 4096;
   }
   kd.caps[0] = cap_f;
   kd.caps[1] = cap_m;
   kd.caps[2] = cap_p;
-  c.nm2l = (int64_t)nm;
-  c.np2p = (int64_t)np;
-  c.frontier_items = pairs;
+  c.nm2l = (int64_t)h[0];
+  c.np2p = (int64_t)h[1];
+  c.traverse_iters = (int)h[3];
+  c.frontier_items = (int64_t)h[4];
   c.traverse_walks = walks;
   return cudaSuccess;
 }
@@ -644,6 +782,7 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
   TRY(ensure(kd.axis, (size_t)cap * 4));
   TRY(ensure(kd.box, (size_t)cap * 48));
   TRY(ensure(kd.geo, (size_t)cap * 56));
+  TRY(ensure(kd.geof, (size_t)cap * 32));
   TRY(ensure(kd.hs, (size_t)cap * 4));
   TRY(ensure(c.key, (size_t)n * 8));
   TRY(ensure(c.key_alt, (size_t)n * 8));
@@ -666,8 +805,8 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
   if (c.prm.profile & 1) cudaEventRecord(c.ev[1], st);
   uint32_t *first = P<uint32_t>(kd.first), *count = P<uint32_t>(kd.count);
   int *child = P<int>(kd.child), *parent = P<int>(kd.parent), *axis = P<int>(kd.axis);
-  TRY(ensure(kd.ctr, 64));
-  uint64_t *total = P<uint64_t>(kd.ctr) + 4;
+  TRY(ensure(kd.ctr, 128));
+  uint64_t *total = P<uint64_t>(kd.ctr) + kWalkCtr;  // after the walk's counters
   k_kd_root<<<1, 1, 0, st>>>(n, first, count, parent);
   note_launch();
   TRY(cudaMemsetAsync(kd.pnode.p, 0, (size_t)n * 4, st));
@@ -712,8 +851,8 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
   }
   c.nnodes = hi;
   const unsigned gk = blocks_for((size_t)hi, kT);
-  k_kd_geo<<<gk, kT, 0, st>>>(hi, cap, P<double>(kd.box), c.prm.box, P<double>(kd.geo), P<float>(kd.hs), child,
-                              P<uint32_t>(kd.nflag));
+  k_kd_geo<<<gk, kT, 0, st>>>(hi, cap, P<double>(kd.box), c.prm.box, P<double>(kd.geo), P<float>(kd.geof),
+                              P<float>(kd.hs), child, P<uint32_t>(kd.nflag));
   note_launch();
   TRY(scan_u32(P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), total, (size_t)hi, c.tmp2, st));
   k_kd_leaves<<<gk, kT, 0, st>>>(hi, P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), P<uint32_t>(c.leaves));
