@@ -465,18 +465,22 @@ __global__ void k_kd_csr(const uint64_t *__restrict__ lst, int64_t n, uint32_t *
 // pair force of Sec. 2.2 with the hard cut-off, added to acc in input order.
 constexpr int kKdStage = 64;
 
+// kCount (statistics runs): also count the pairs inside (0, R_c) into *useful.
+template <bool kCount>
 __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
                                                const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
                                                KdGeo Gm, const uint32_t *__restrict__ beg,
                                                const uint32_t *__restrict__ end, const uint64_t *__restrict__ lst,
                                                const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm,
-                                               int64_t n, double L, PairFit2 fit, float G, float *__restrict__ acc) {
+                                               int64_t n, double L, PairFit2 fit, float G, float *__restrict__ acc,
+                                               unsigned long long *__restrict__ useful) {
   __shared__ __align__(16) float sx[kT / 32][kKdStage + 2], sy[kT / 32][kKdStage + 2], sz[kT / 32][kKdStage + 2],
       sw[kT / 32][kKdStage + 2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float *X = sx[wid], *Y = sy[wid], *Z = sz[wid], *Wm = sw[wid];
   const float rc2_cull = fit.rc2 * (1.f + 1.f / 4096.f);  // far above the FP32 rounding of either distance
   const int64_t nw = (int64_t)gridDim.x * (kT / 32);
+  uint32_t n_in = 0;
   for (int64_t t = (int64_t)blockIdx.x * (kT / 32) + wid; t < nl; t += nw) {
     const uint32_t k = leaves[t];
     const uint32_t f = first[k], m = count[k];
@@ -574,11 +578,13 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
         fetch(q + 1 - wbase);
       }
       __syncwarp();
+      // (real: the lane holds this sink; the others evaluate a phantom sink whose result is dropped)
       auto pair2 = [&](float2 px, float2 py, float2 pz, float2 w, float2 nx, float2 ny, float2 nz, float2 &ax,
-                       float2 &ay, float2 &az) {
+                       float2 &ay, float2 &az, bool real) {
         const float2 dx = __fadd2_rn(px, nx), dy = __fadd2_rn(py, ny), dz = __fadd2_rn(pz, nz);
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
         const bool in0 = r2.x < fit.rc2 && r2.x > 0.f, in1 = r2.y < fit.rc2 && r2.y > 0.f;
+        if (kCount && real) n_in += (uint32_t)in0 + (uint32_t)in1;
         // outside (0, R_c) the values below may be inf / NaN; the selects discard them
         const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
         const float2 r3 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
@@ -599,15 +605,15 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
         for (uint32_t j = 0; j < kept; j += 2) {
           const float2 px = *reinterpret_cast<const float2 *>(X + j), py = *reinterpret_cast<const float2 *>(Y + j);
           const float2 pz = *reinterpret_cast<const float2 *>(Z + j), w = *reinterpret_cast<const float2 *>(Wm + j);
-          pair2(px, py, pz, w, n0x, n0y, n0z, a0x, a0y, a0z);
-          pair2(px, py, pz, w, n1x, n1y, n1z, a1x, a1y, a1z);
+          pair2(px, py, pz, w, n0x, n0y, n0z, a0x, a0y, a0z, has0);
+          pair2(px, py, pz, w, n1x, n1y, n1z, a1x, a1y, a1z, has1);
         }
       } else {
 #pragma unroll 4
         for (uint32_t j = 0; j < kept; j += 2) {
           const float2 px = *reinterpret_cast<const float2 *>(X + j), py = *reinterpret_cast<const float2 *>(Y + j);
           const float2 pz = *reinterpret_cast<const float2 *>(Z + j), w = *reinterpret_cast<const float2 *>(Wm + j);
-          pair2(px, py, pz, w, n0x, n0y, n0z, a0x, a0y, a0z);
+          pair2(px, py, pz, w, n0x, n0y, n0z, a0x, a0y, a0z, has0);
         }
       }
     }
@@ -624,6 +630,21 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
       acc[2 * n + o] += G * (a1z.x + a1z.y);
     }
   }
+  if (kCount) {
+    unsigned long long v = n_in;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(useful, v);
+  }
+}
+
+// Particle pairs on the P2P list: sum over entries of n_sink n_source.
+__global__ void k_kd_list_pairs(const uint64_t *__restrict__ lst, int64_t n, const uint32_t *__restrict__ count,
+                                unsigned long long *__restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = 0;
+  if (t < n) v = (unsigned long long)count[pair_sink(lst[t])] * count[pair_src(lst[t])];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
 }
 
 #define TRY(x)                      \
@@ -728,6 +749,20 @@ cudaError_t kd_group(Ctx &c, cudaStream_t st) {
                                                              P<uint32_t>(*end[w]));
     note_launch();
   }
+  // statistics runs: the particle pairs on the P2P list
+  c.p2p_particle_pairs = -1;
+  if (c.prm.profile & 2) {
+    unsigned long long *cnt = P<unsigned long long>(c.kd.ctr) + kWalkCtr + 1;
+    TRY(cudaMemsetAsync(cnt, 0, 8, st));
+    if (c.np2p > 0) {
+      k_kd_list_pairs<<<blocks_for((size_t)c.np2p, kT), kT, 0, st>>>(P<uint64_t>(c.p2p), c.np2p,
+                                                                      P<uint32_t>(c.kd.count), cnt);
+      note_launch();
+    }
+    uint64_t pp = 0;
+    TRY(read_u64(c, cnt, &pp, 1, st));
+    c.p2p_particle_pairs = (int64_t)pp;
+  }
   return cudaGetLastError();
 }
 
@@ -737,10 +772,18 @@ cudaError_t kd_p2p(Ctx &c, float *acc, cudaStream_t st) {
   TRY(cudaGetDevice(&dev));
   TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const unsigned g = (unsigned)std::min<int64_t>((c.nleaves + 7) / 8, (int64_t)nsm * 8);
-  k_kd_p2p<<<g, kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count),
-                             kd_geo(c), P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p),
-                             P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G,
-                             acc);
+  unsigned long long *useful = P<unsigned long long>(c.d_small) + 4;  // the statistics counter of stats
+  if (c.prm.profile & 2)
+    k_kd_p2p<true><<<g, kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.first),
+                                     P<uint32_t>(c.kd.count), kd_geo(c), P<uint32_t>(c.p2p_beg),
+                                     P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4),
+                                     P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G, acc, useful);
+  else
+    k_kd_p2p<false><<<g, kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.first),
+                                      P<uint32_t>(c.kd.count), kd_geo(c), P<uint32_t>(c.p2p_beg),
+                                      P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4),
+                                      P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G, acc,
+                                      useful);
   note_launch();
   return cudaGetLastError();
 }

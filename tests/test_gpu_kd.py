@@ -267,3 +267,28 @@ def test_unsupported_combinations_are_refused():
     o.build_tree(torch.zeros((3, 4), dtype=torch.float64, device="cuda") + 0.5, torch.ones(4, device="cuda"))
     with pytest.raises(hfmm.HfmmError, match="ARG"):
         o.export("kd_nodes")
+
+
+def test_statistics_counts_of_the_p2p_pairs():
+    """profile bit 1: the particle pairs on the P2P list (sum of n_sink n_source,
+    exact) and the pairs inside (0, R_c) the kernel evaluated, against an FP64
+    count over the oracle's list (equal up to pairs within FP32 rounding of R_c)."""
+    pos, mass = W.nfw_clustered(20000, 30, 0.7, 23)
+    s, _ = run_gpu(pos, mass, pm_grid=32, theta=0.4, leaf_max=32, order=4, profile=3)
+    st = s.get_stats()
+    f = run_oracle(pos, mass, s)
+    f.traverse()
+    nodes, _, perm = f.tree()
+    p2p, _ = f.lists()
+    cnt = nodes[:, 2]
+    assert st["p2p_particle_pairs"] == int((cnt[p2p[:, 0]] * cnt[p2p[:, 1]]).sum())
+    x = (pos - np.floor(pos)).T
+    useful = 0
+    for a, b, sh in p2p:
+        ia = perm[nodes[a, 1]:nodes[a, 1] + nodes[a, 2]]
+        ib = perm[nodes[b, 1]:nodes[b, 1] + nodes[b, 2]]
+        shv = np.array([sh // 9 - 1, (sh // 3) % 3 - 1, sh % 3 - 1], dtype=np.float64)
+        d = x[ib][None, :, :] + shv - x[ia][:, None, :]
+        r2 = (d * d).sum(axis=2)
+        useful += int(((r2 > 0) & (r2 < s.rc * s.rc)).sum())
+    assert abs(st["p2p_useful_pairs"] - useful) <= max(2, useful // 100000), (st["p2p_useful_pairs"], useful)
