@@ -150,7 +150,7 @@ void for_each_buffer(Ctx &c, F f) {
                   &c.kd.ord[0], &c.kd.ord[1], &c.kd.ord[2], &c.kd.ord2[0], &c.kd.ord2[1], &c.kd.ord2[2],
                   &c.kd.side, &c.kd.flag, &c.kd.scan, &c.kd.pnode, &c.kd.nflag, &c.kd.nscan, &c.kd.first,
                   &c.kd.count, &c.kd.child, &c.kd.parent, &c.kd.axis, &c.kd.box, &c.kd.geo, &c.kd.geof, &c.kd.hs,
-                  &c.kd.ctr};
+                  &c.kd.ctr, &c.kd.lv};
   for (DBuf *b : bufs) f(*b);
 }
 

@@ -274,7 +274,7 @@ struct KdTree {
   DBuf xw;                       // f64 [3][n] wrapped positions, input order
   DBuf ord[3], ord2[3];          // u32 [n] per axis: the particles of each node's range in (coordinate, index) order
   DBuf side;                     // u8 [n] per particle: 1 = in the second child of its node's split
-  DBuf flag, scan;               // u32 [n]
+  DBuf flag, scan;               // u32 [3][n]: side flags of the three orders and their scan
   DBuf pnode;                    // u32 [n] node of each position on the level being split (its leaf at the end)
   DBuf nflag, nscan;             // u32 [cap] split flags of a level's nodes and their scan
   DBuf first, count;             // u32 [cap] particle range
@@ -284,6 +284,7 @@ struct KdTree {
   DBuf geof;                     // f32 [7][cap] the same rounded (the walk's FP32 filter)
   DBuf hs;                       // f32 [cap] expansion scale h: L 2^-j >= side, j <= 21
   DBuf ctr;                      // u64 [16]: the walk's counters, then the build's scan total
+  DBuf lv;                       // u64 [2][levels]: each level's node extent [lo, hi) during the build
   std::vector<int64_t> level_start;
   int64_t cap = 0;
   uint64_t caps[3] = {0, 0, 0};  // frontier, M2L and P2P capacities of the last walk

@@ -15,8 +15,11 @@
 //     flags over all positions, less its value at the node's first position,
 //     ranks a particle among the second child's particles.  So every order stays
 //     sorted inside every node, and inside a leaf the x order is the particle
-//     order (that of (x, input index));
-//   - the number of splits of a level is read back to size the next level.
+//     order (that of (x, input index)); the three orders are flagged, scanned
+//     (one scan over the concatenated flags) and scattered together;
+//   - the counts of a level differ by at most one, so the depth follows from N
+//     and leaf_max on the host; each level's extent stays on the device (the
+//     kernels read it) and is read back once, after the last level.
 // Node geometry: the box centre c, half extents e, side (largest extent) in FP64,
 // and the expansion scale h = L 2^-j >= side (j <= 21, the octree's deepest
 // cell side): P2M offsets over h stay within [-1/2, 1/2] and the scale ratios of
@@ -46,6 +49,7 @@ namespace hfmm {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kKdMaxLevels = 64;
 
 __global__ void k_kd_wrap(const double *__restrict__ pos, int64_t n, double box, double inv_pow2,
                           double *__restrict__ xw) {
@@ -64,20 +68,36 @@ __global__ void k_kd_keys(const double *__restrict__ x, int64_t n, uint64_t *__r
   val[i] = (uint32_t)i;
 }
 
-__global__ void k_kd_root(int64_t n, uint32_t *first, uint32_t *count, int *parent) {
+__global__ void k_kd_root(int64_t n, uint32_t *first, uint32_t *count, int *parent, unsigned long long *lv) {
   first[0] = 0;
   count[0] = (uint32_t)n;
   parent[0] = -1;
+  lv[0] = 0;
+  lv[1] = 1;
 }
 
-// One level's nodes [lo, lo + cnt): bounding box and split decision.
-__global__ void k_kd_level(int64_t lo, int64_t cnt, int leaf_max, const double *__restrict__ xw, int64_t n,
+// The extent [lo, hi) of tree level l on the device: lv[2 l], lv[2 l + 1].
+__device__ __forceinline__ void level_extent(const unsigned long long *lv, int l, int64_t &lo, int64_t &hi) {
+  lo = (int64_t)lv[2 * l];
+  hi = (int64_t)lv[2 * l + 1];
+}
+
+// One level's nodes: bounding box and split decision (split flags zero up to `bound`
+// nodes, the grid's size, so the scan of a level of unknown size on the host works).
+__global__ void k_kd_level(const unsigned long long *__restrict__ lv, int level, int64_t bound, int leaf_max,
+                           const double *__restrict__ xw, int64_t n,
                            const uint32_t *__restrict__ o0, const uint32_t *__restrict__ o1,
                            const uint32_t *__restrict__ o2, const uint32_t *__restrict__ first,
                            const uint32_t *__restrict__ count, double *__restrict__ box, int64_t cap,
                            int *__restrict__ axis, uint32_t *__restrict__ nflag) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
+  if (t >= bound) return;
+  int64_t lo, hi;
+  level_extent(lv, level, lo, hi);
+  if (t >= hi - lo) {
+    nflag[t] = 0u;
+    return;
+  }
   const int64_t k = lo + t;
   const uint32_t f = first[k], m = count[k];
   const uint32_t *ord[3] = {o0, o1, o2};
@@ -99,11 +119,13 @@ __global__ void k_kd_level(int64_t lo, int64_t cnt, int leaf_max, const double *
   nflag[t] = split ? 1u : 0u;
 }
 
-__global__ void k_kd_children(int64_t lo, int64_t cnt, int64_t hi, const int *__restrict__ axis,
+__global__ void k_kd_children(const unsigned long long *__restrict__ lv, int level, const int *__restrict__ axis,
                               const uint32_t *__restrict__ nscan, uint32_t *__restrict__ first,
                               uint32_t *__restrict__ count, int *__restrict__ child, int *__restrict__ parent) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
+  int64_t lo, hi;
+  level_extent(lv, level, lo, hi);
+  if (t >= hi - lo) return;
   const int64_t k = lo + t;
   if (axis[k] < 0) {
     child[k] = -1;
@@ -119,13 +141,21 @@ __global__ void k_kd_children(int64_t lo, int64_t cnt, int64_t hi, const int *__
   parent[ch] = parent[ch + 1] = (int)k;
 }
 
+// The next level's extent: [hi, hi + 2 splits).
+__global__ void k_kd_next(unsigned long long *__restrict__ lv, int level, const uint64_t *__restrict__ nsplit) {
+  lv[2 * level + 2] = lv[2 * level + 1];
+  lv[2 * level + 3] = lv[2 * level + 1] + 2ull * nsplit[0];
+}
+
 // The side of every particle of a node split on this level (positions of earlier leaves: node < lo).
-__global__ void k_kd_side(int64_t n, int64_t lo, const uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
+__global__ void k_kd_side(int64_t n, const unsigned long long *__restrict__ lv, int level,
+                          const uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
                           const uint32_t *__restrict__ count, const int *__restrict__ axis,
                           const uint32_t *__restrict__ o0, const uint32_t *__restrict__ o1,
                           const uint32_t *__restrict__ o2, uint8_t *__restrict__ side) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int64_t lo = (int64_t)lv[2 * level];
   const uint32_t k = pnode[i];
   if ((int64_t)k < lo) return;
   const int a = axis[k];
@@ -134,37 +164,59 @@ __global__ void k_kd_side(int64_t n, int64_t lo, const uint32_t *__restrict__ pn
   side[p] = (uint32_t)i - first[k] >= count[k] / 2 ? 1 : 0;
 }
 
-__global__ void k_kd_flag(int64_t n, int64_t lo, const uint32_t *__restrict__ pnode, const int *__restrict__ axis,
-                          const uint32_t *__restrict__ ord, const uint8_t *__restrict__ side,
+// The side flags of the three orders, concatenated ([3][n]; zero outside the nodes
+// split on this level), for one scan over all of them.
+__global__ void k_kd_flag(int64_t n, const unsigned long long *__restrict__ lv, int level,
+                          const uint32_t *__restrict__ pnode, const int *__restrict__ axis,
+                          const uint32_t *__restrict__ o0, const uint32_t *__restrict__ o1,
+                          const uint32_t *__restrict__ o2, const uint8_t *__restrict__ side,
                           uint32_t *__restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int64_t lo = (int64_t)lv[2 * level];
   const uint32_t k = pnode[i];
-  flag[i] = ((int64_t)k >= lo && axis[k] >= 0) ? side[ord[i]] : 0u;
+  const bool split = (int64_t)k >= lo && axis[k] >= 0;
+  flag[i] = split ? side[o0[i]] : 0u;
+  flag[n + i] = split ? side[o1[i]] : 0u;
+  flag[2 * n + i] = split ? side[o2[i]] : 0u;
 }
 
-// Stable partition of one order inside every node split on this level.
-__global__ void k_kd_scatter(int64_t n, int64_t lo, const uint32_t *__restrict__ pnode,
-                             const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
-                             const int *__restrict__ axis, const uint32_t *__restrict__ ord,
-                             const uint8_t *__restrict__ side, const uint32_t *__restrict__ scan,
-                             uint32_t *__restrict__ out) {
+// Stable partition of the three orders inside every node split on this level:
+// in order d a particle of the second child is preceded in it by scan[d n + i] -
+// scan[d n + first] such particles (the scan runs over the concatenated flags).
+__global__ void k_kd_scatter(int64_t n, const unsigned long long *__restrict__ lv, int level,
+                             const uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
+                             const uint32_t *__restrict__ count, const int *__restrict__ axis,
+                             const uint32_t *__restrict__ o0, const uint32_t *__restrict__ o1,
+                             const uint32_t *__restrict__ o2, const uint8_t *__restrict__ side,
+                             const uint32_t *__restrict__ scan, uint32_t *__restrict__ r0,
+                             uint32_t *__restrict__ r1, uint32_t *__restrict__ r2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t k = pnode[i], v = ord[i];
+  const int64_t lo = (int64_t)lv[2 * level];
+  const uint32_t k = pnode[i];
+  const uint32_t *ord[3] = {o0, o1, o2};
+  uint32_t *out[3] = {r0, r1, r2};
   if ((int64_t)k < lo || axis[k] < 0) {
-    out[i] = v;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[d][i] = ord[d][i];
     return;
   }
   const uint32_t f = first[k], nl = count[k] / 2;
-  const uint32_t r = scan[i] - scan[f];  // particles of the second child before position i
-  out[side[v] ? f + nl + r : (uint32_t)i - r] = v;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const uint32_t v = ord[d][i];
+    const uint32_t r = scan[d * n + i] - scan[d * n + f];  // particles of the second child before position i
+    out[d][side[v] ? f + nl + r : (uint32_t)i - r] = v;
+  }
 }
 
-__global__ void k_kd_pnode(int64_t n, int64_t lo, uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
+__global__ void k_kd_pnode(int64_t n, const unsigned long long *__restrict__ lv, int level,
+                           uint32_t *__restrict__ pnode, const uint32_t *__restrict__ first,
                            const uint32_t *__restrict__ count, const int *__restrict__ child) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int64_t lo = (int64_t)lv[2 * level];
   const uint32_t k = pnode[i];
   if ((int64_t)k < lo || child[k] < 0) return;
   pnode[i] = (uint32_t)child[k] + ((uint32_t)i - first[k] >= count[k] / 2 ? 1u : 0u);
@@ -813,8 +865,8 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
     TRY(ensure(kd.ord2[d], (size_t)n * 4));
   }
   TRY(ensure(kd.side, (size_t)n));
-  TRY(ensure(kd.flag, (size_t)n * 4));
-  TRY(ensure(kd.scan, (size_t)n * 4));
+  TRY(ensure(kd.flag, (size_t)n * 12));
+  TRY(ensure(kd.scan, (size_t)n * 12));
   TRY(ensure(kd.pnode, (size_t)n * 4));
   TRY(ensure(kd.nflag, (size_t)cap * 4));
   TRY(ensure(kd.nscan, (size_t)cap * 4));
@@ -850,48 +902,63 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
   int *child = P<int>(kd.child), *parent = P<int>(kd.parent), *axis = P<int>(kd.axis);
   TRY(ensure(kd.ctr, 128));
   uint64_t *total = P<uint64_t>(kd.ctr) + kWalkCtr;  // after the walk's counters
-  k_kd_root<<<1, 1, 0, st>>>(n, first, count, parent);
+  // The depth from the counts alone: the counts of a level differ by at most one (a
+  // split gives floor and ceil halves), so [qmin, qmax] bounds them level by level.
+  int levels = 1;
+  for (int64_t qmin = n, qmax = n; qmax > c.prm.leaf_max; ++levels) {
+    qmin = std::max<int64_t>(qmin, c.prm.leaf_max + 1) / 2;
+    qmax = (qmax + 1) / 2;
+  }
+  if (levels > kKdMaxLevels) return cudaErrorInvalidValue;
+  TRY(ensure(kd.lv, sizeof(unsigned long long) * 2 * (kKdMaxLevels + 1)));
+  unsigned long long *lv = P<unsigned long long>(kd.lv);
+  k_kd_root<<<1, 1, 0, st>>>(n, first, count, parent, lv);
   note_launch();
   TRY(cudaMemsetAsync(kd.pnode.p, 0, (size_t)n * 4, st));
   const unsigned gn = blocks_for((size_t)n, kT);
-  int64_t lo = 0, hi = 1;
-  for (int level = 0;; ++level) {
-    if (level >= 64) return cudaErrorInvalidValue;
-    const int64_t cnt = hi - lo;
-    const unsigned gl = blocks_for((size_t)cnt, kT);
-    k_kd_level<<<gl, kT, 0, st>>>(lo, cnt, c.prm.leaf_max, xw, n, P<uint32_t>(kd.ord[0]), P<uint32_t>(kd.ord[1]),
-                                  P<uint32_t>(kd.ord[2]), first, count, P<double>(kd.box), cap, axis,
-                                  P<uint32_t>(kd.nflag));
+  // every level on the device, its extent read by the kernels (no read-back per level)
+  for (int level = 0; level < levels; ++level) {
+    const int64_t bound = std::min<int64_t>(level < 62 ? (int64_t)1 << level : cap, cap);
+    const unsigned gl = blocks_for((size_t)bound, kT);
+    k_kd_level<<<gl, kT, 0, st>>>(lv, level, bound, c.prm.leaf_max, xw, n, P<uint32_t>(kd.ord[0]),
+                                  P<uint32_t>(kd.ord[1]), P<uint32_t>(kd.ord[2]), first, count, P<double>(kd.box),
+                                  cap, axis, P<uint32_t>(kd.nflag));
     note_launch();
-    TRY(scan_u32(P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), total, (size_t)cnt, c.tmp2, st));
-    k_kd_children<<<gl, kT, 0, st>>>(lo, cnt, hi, axis, P<uint32_t>(kd.nscan), first, count, child, parent);
+    const bool last = level + 1 == levels;  // no node of the last level splits
+    if (!last) TRY(scan_u32(P<uint32_t>(kd.nflag), P<uint32_t>(kd.nscan), total, (size_t)bound, c.tmp2, st));
+    k_kd_children<<<gl, kT, 0, st>>>(lv, level, axis, P<uint32_t>(kd.nscan), first, count, child, parent);
     note_launch();
-    uint64_t nsplit = 0;
-    TRY(read_u64(c, total, &nsplit, 1, st));
-    kd.level_start.push_back(hi);
-    if (nsplit == 0) {
-      c.nlevels = level + 1;
-      break;
-    }
-    if (hi + 2 * (int64_t)nsplit > cap) return cudaErrorInvalidValue;
-    k_kd_side<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), first, count, axis, P<uint32_t>(kd.ord[0]),
+    if (last) break;
+    k_kd_next<<<1, 1, 0, st>>>(lv, level, total);
+    note_launch();
+    k_kd_side<<<gn, kT, 0, st>>>(n, lv, level, P<uint32_t>(kd.pnode), first, count, axis, P<uint32_t>(kd.ord[0]),
                                  P<uint32_t>(kd.ord[1]), P<uint32_t>(kd.ord[2]), P<uint8_t>(kd.side));
     note_launch();
-    for (int d = 0; d < 3; ++d) {
-      k_kd_flag<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), axis, P<uint32_t>(kd.ord[d]), P<uint8_t>(kd.side),
-                                   P<uint32_t>(kd.flag));
-      note_launch();
-      TRY(scan_u32(P<uint32_t>(kd.flag), P<uint32_t>(kd.scan), total, (size_t)n, c.tmp2, st));
-      k_kd_scatter<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), first, count, axis, P<uint32_t>(kd.ord[d]),
-                                      P<uint8_t>(kd.side), P<uint32_t>(kd.scan), P<uint32_t>(kd.ord2[d]));
-      note_launch();
-      std::swap(kd.ord[d], kd.ord2[d]);
-    }
-    k_kd_pnode<<<gn, kT, 0, st>>>(n, lo, P<uint32_t>(kd.pnode), first, count, child);
+    k_kd_flag<<<gn, kT, 0, st>>>(n, lv, level, P<uint32_t>(kd.pnode), axis, P<uint32_t>(kd.ord[0]),
+                                 P<uint32_t>(kd.ord[1]), P<uint32_t>(kd.ord[2]), P<uint8_t>(kd.side),
+                                 P<uint32_t>(kd.flag));
     note_launch();
-    lo = hi;
-    hi += 2 * (int64_t)nsplit;
+    TRY(scan_u32(P<uint32_t>(kd.flag), P<uint32_t>(kd.scan), total, (size_t)(3 * n), c.tmp2, st));
+    k_kd_scatter<<<gn, kT, 0, st>>>(n, lv, level, P<uint32_t>(kd.pnode), first, count, axis, P<uint32_t>(kd.ord[0]),
+                                    P<uint32_t>(kd.ord[1]), P<uint32_t>(kd.ord[2]), P<uint8_t>(kd.side),
+                                    P<uint32_t>(kd.scan), P<uint32_t>(kd.ord2[0]), P<uint32_t>(kd.ord2[1]),
+                                    P<uint32_t>(kd.ord2[2]));
+    note_launch();
+    for (int d = 0; d < 3; ++d) std::swap(kd.ord[d], kd.ord2[d]);
+    k_kd_pnode<<<gn, kT, 0, st>>>(n, lv, level, P<uint32_t>(kd.pnode), first, count, child);
+    note_launch();
   }
+  // the level extents back (one read-back): nodes, levels, and a full binary tree's leaves
+  uint64_t ext[2 * (kKdMaxLevels + 1)];
+  TRY(read_u64(c, lv, ext, 2 * levels, st));
+  int64_t hi = 0;
+  for (int level = 0; level < levels; ++level) {
+    if (ext[2 * level + 1] == ext[2 * level]) break;  // an empty level: the tree ended above
+    kd.level_start.push_back((int64_t)ext[2 * level + 1]);
+    hi = (int64_t)ext[2 * level + 1];
+    c.nlevels = level + 1;
+  }
+  if (hi > cap) return cudaErrorInvalidValue;
   c.nnodes = hi;
   const unsigned gk = blocks_for((size_t)hi, kT);
   k_kd_geo<<<gk, kT, 0, st>>>(hi, cap, P<double>(kd.box), c.prm.box, P<double>(kd.geo), P<float>(kd.geof),
@@ -903,9 +970,7 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
   k_kd_particles<<<gn, kT, 0, st>>>(n, P<uint32_t>(kd.ord[0]), xw, mass, P<uint32_t>(kd.pnode), P<double>(kd.geo),
                                     cap, P<double>(c.xs), P<uint32_t>(c.idx), P<float4>(c.pm4));
   note_launch();
-  uint64_t nleaves = 0;
-  TRY(read_u64(c, total, &nleaves, 1, st));
-  c.nleaves = (int64_t)nleaves;
+  c.nleaves = (hi + 1) / 2;  // every split node has two children
   if (c.prm.profile & 1) cudaEventRecord(c.ev[2], st);
   c.have_tree = true;
   return cudaGetLastError();
