@@ -153,8 +153,9 @@ typedef struct {
                           centre, the rules of Sec. 2.3 on the boxes in FP64 (S_c between the centres,
                           S_m and S_max from per-axis gaps and spans, side = largest extent; a pair with
                           theta S_c = 0 is never accepted), the walk opening the node of larger side.
-                          hfmm_build_tree synchronises `stream` once per tree level; the walk once per
-                          walk level.  Needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0,
+                          hfmm_build_tree synchronises `stream` once (the level extents); the walk is
+                          one cooperative launch, followed by one read-back (repeated with grown
+                          buffers when a list or the frontier outgrew its buffer).  Needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0,
                           split 0 and order <= 6; use_graph and sink_batches are ignored, and
                           hfmm_interaction_counts, HFMM_EXPORT_KEYS and HFMM_EXPORT_NODES are octree
                           only (HFMM_EXPORT_KD_NODES and _KD_BOXES describe this tree). */
