@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kT, 4) k_kd_walk(uint64_t *__restrict__ fa, ui
                                                 unsigned long long cap_f, uint64_t *__restrict__ m2l,
                                                 unsigned long long cap_m, uint64_t *__restrict__ p2p,
                                                 unsigned long long cap_p, unsigned long long *__restrict__ ctr,
-                                                KdGeo G, const int *__restrict__ child, WalkRule R) {
+                                                KdGeo G, WalkRule R) {
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -743,7 +743,6 @@ cudaError_t kd_walk(Ctx &c, cudaStream_t st) {
   R.rule = c.prm.transition_rule;
   R.size_rule = c.prm.size_rule;
   KdGeo G = kd_geo(c);
-  int *child = P<int>(kd.child);
   int64_t walks = 0;
   uint64_t h[kWalkCtr];
   for (;;) {
@@ -757,7 +756,7 @@ cudaError_t kd_walk(Ctx &c, cudaStream_t st) {
              *p2p = P<uint64_t>(c.p2p);
     unsigned long long cf = cap_f, cm = cap_m, cp = cap_p;
     void *args[] = {(void *)&fa, (void *)&fb, (void *)&cf, (void *)&m2l, (void *)&cm, (void *)&p2p, (void *)&cp,
-                    (void *)&ctr, (void *)&G, (void *)&child, (void *)&R};
+                    (void *)&ctr, (void *)&G, (void *)&R};
     TRY(cudaLaunchCooperativeKernel((const void *)k_kd_walk, dim3(nb), dim3(kT), args, 0, st));
     note_launch();
     TRY(read_u64(c, ctr, h, kWalkCtr, st));
