@@ -10,7 +10,8 @@
  *     a_i = G sum_{j != i, 0 < |r_ij| < R_c} m_j f_(1)(|r_ij|) r_ij,
  *     f_(1)(r) = -[erfc(r / 2r_s) + r / (r_s sqrt(pi)) exp(-r^2 / 4r_s^2)] / r^3,
  * r_ij the minimum-image separation x_i - x_j, approximated by a truncated FMM:
- * Morton octree, P2M/M2M (Eqs. p2m, m2m), dual-tree traversal with the
+ * Morton octree (or, with hfmm_params.tree = 1, the ORB / k-d tree of Sec. 2.1
+ * and Sec. 4), P2M/M2M (Eqs. p2m, m2m), dual-tree traversal with the
  * three-rule acceptance criterion (Sec. 2.3), M2L with the derivative tensors
  * of erfc(r/2r_s)/r (Eq. m2l and the general-order prefactors of Sec. 2.2),
  * L2L/L2P (Eqs. l2l, l2p) and a cut-off P2P sum.
