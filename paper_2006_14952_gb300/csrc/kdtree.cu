@@ -784,14 +784,18 @@ cudaError_t kd_group(Ctx &c, cudaStream_t st) {
   TRY(ensure(c.m2l_end, nn * 4));
   TRY(ensure(c.p2p_beg, nn * 4));
   TRY(ensure(c.p2p_end, nn * 4));
-  DBuf *lst[2] = {&c.m2l, &c.p2p}, *alt[2] = {&c.m2l_alt, &c.p2p_alt};
+  // the sorts' scratch: the walk's frontier buffers, free once the walk is done, when
+  // they are large enough (at 134M particles they hold tens of GB), else a buffer of its own
+  DBuf *lst[2] = {&c.m2l, &c.p2p}, *alt[2] = {&c.front_next, &c.front};
+  if (c.front_next.cap < (size_t)c.nm2l * 8) alt[0] = &c.m2l_alt;
+  if (c.front.cap < (size_t)c.np2p * 8) alt[1] = &c.p2p_alt;
   DBuf *beg[2] = {&c.m2l_beg, &c.p2p_beg}, *end[2] = {&c.m2l_end, &c.p2p_end};
   const int64_t len[2] = {c.nm2l, c.np2p};
   for (int w = 0; w < 2; ++w) {
     TRY(cudaMemsetAsync(beg[w]->p, 0, nn * 4, st));
     TRY(cudaMemsetAsync(end[w]->p, 0, nn * 4, st));
     if (len[w] == 0) continue;
-    TRY(ensure(*alt[w], std::max(lst[w]->cap, (size_t)len[w] * 8)));
+    TRY(ensure(*alt[w], (size_t)len[w] * 8));
     bool in_alt = false;
     TRY(radix_sort_u64(P<uint64_t>(*lst[w]), nullptr, P<uint64_t>(*alt[w]), nullptr, (size_t)len[w], 0,
                        kSinkShift + kSinkBits, &in_alt, c.tmp, st));
