@@ -47,6 +47,17 @@ def test_parameter_validation_needs_no_gpu():
     p.rcut_rs = 1000.0
     assert L.hfmm_create(ctypes.byref(p), ctypes.byref(h)) == -1
     assert L.hfmm_create(None, ctypes.byref(h)) == -1
+    # the tree choice: 0 or 1, and the k-d tree only with the options it supports
+    p = hfmm.default_params()
+    assert p.tree == 0
+    p.tree = 2
+    assert L.hfmm_create(ctypes.byref(p), ctypes.byref(h)) == -1 and b"tree" in L.hfmm_last_error(None)
+    for field, value in (("mac_mode", 1), ("m2l_precision", 1), ("m2l_tables", 1), ("split", 1), ("order", 7)):
+        p = hfmm.default_params()
+        p.tree = 1
+        setattr(p, field, value)
+        assert L.hfmm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+        assert b"tree 1" in L.hfmm_last_error(None), field
 
 
 def test_struct_layout_matches_header():
