@@ -111,6 +111,7 @@ def lib():
             L.orc_kd_destroy.argtypes = [P]
             L.orc_kd_build.argtypes = [P, i64, P, P]
             L.orc_kd_traverse.argtypes = [P]
+            L.orc_kd_traverse_conventional.argtypes = [P]
             L.orc_kd_upward.argtypes = [P]
             L.orc_kd_m2l_pass.argtypes = [P]
             L.orc_kd_downward.argtypes = [P, P]
@@ -470,8 +471,23 @@ class KdFMM:
     def size(self, what):
         return int(lib().orc_kd_size(self._c, {"n": 0, "nodes": 1, "levels": 2, "p2p": 3, "m2l": 4}[what]))
 
-    def traverse(self):
-        _check(lib().orc_kd_traverse(self._c), "kd_traverse")
+    def traverse(self, conventional=False):
+        """The hybrid walk of Sec. 2.3 on the k-d boxes, or (conventional=True) the
+        conventional FMM's: the opening-angle test alone, from (root, root) of the
+        primary box."""
+        if conventional:
+            _check(lib().orc_kd_traverse_conventional(self._c), "kd_traverse_conventional")
+        else:
+            _check(lib().orc_kd_traverse(self._c), "kd_traverse")
+
+    def counts(self):
+        """Interaction counts of the current lists (Sec. 3): M2L cell pairs, P2P leaf
+        pairs, and particle pairs on the P2P lists (sum of n_sink n_source)."""
+        nodes, _, _ = self.tree()
+        p2p, m2l = self.lists()
+        cnt = nodes[:, 2]
+        pp = int((cnt[p2p[:, 0]] * cnt[p2p[:, 1]]).sum()) if len(p2p) else 0
+        return {"m2l": len(m2l), "p2p": len(p2p), "p2p_particle_pairs": pp}
 
     def forces(self) -> np.ndarray:
         acc = np.zeros((3, self.n))

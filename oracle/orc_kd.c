@@ -237,8 +237,10 @@ static void push3(int64_t **buf, int64_t *n, int64_t *cap, int64_t a, int64_t b,
   ++*n;
 }
 
-/* 0 skip, 1 M2L, 2 open: sink a, source b shifted by s (index (sx+1)*9+(sy+1)*3+(sz+1)). */
-static int kd_classify(const orc_kd *c, int64_t a, int64_t b, int s) {
+/* 0 skip, 1 M2L, 2 open: sink a, source b shifted by s (index (sx+1)*9+(sy+1)*3+(sz+1)).
+ * conventional != 0: the opening-angle test alone (no skip, no transition region),
+ * the acceptance of a conventional FMM (Sec. 3). */
+static int kd_classify(const orc_kd *c, int64_t a, int64_t b, int s, int conventional) {
   const int sh[3] = {s / 9 - 1, (s / 3) % 3 - 1, s % 3 - 1};
   double sc2 = 0.0, sm2 = 0.0, sx2 = 0.0;
   for (int d = 0; d < 3; ++d) {
@@ -257,8 +259,8 @@ static int kd_classify(const orc_kd *c, int64_t a, int64_t b, int s) {
     sx2 = sx2 + far * far;
   }
   const double rc2 = c->rc * c->rc;
-  if (sm2 > rc2) return 0;
-  int trans = c->rule == 0 ? (sc2 > rc2) : (sx2 > rc2);
+  if (!conventional && sm2 > rc2) return 0;
+  int trans = conventional ? 0 : c->rule == 0 ? (sc2 > rc2) : (sx2 > rc2);
   double sa = kd_side(c, a), sb = kd_side(c, b);
   double wl = c->size_rule == 0 ? sb : (sa > sb ? sa : sb);
   const double lim = (c->theta * c->theta) * sc2; /* theta^2 S_c^2; a pair with theta S_c = 0 is never accepted */
@@ -266,18 +268,23 @@ static int kd_classify(const orc_kd *c, int64_t a, int64_t b, int s) {
   return 2;
 }
 
-/* Dual walk from the root against its 27 nearest periodic images (R_c < L / 2). */
-int orc_kd_traverse(orc_kd *c) {
+/* Dual walk from the root against its 27 nearest periodic images (R_c < L / 2);
+ * conventional: the walk of a conventional FMM, from the single pair (root, root)
+ * of the primary box (its periodic images go to an Ewald sum, Sec. 3). */
+static int kd_walk(orc_kd *c, int conventional) {
   if (!c) return -1;
   c->np2p = 0; c->nm2l = 0;
   if (c->n == 0) return 0;
   int64_t *stk = NULL, nst = 0, cst = 0;
-  for (int s = 0; s < 27; ++s) push3(&stk, &nst, &cst, 0, 0, s);
+  if (conventional)
+    push3(&stk, &nst, &cst, 0, 0, 13);
+  else
+    for (int s = 0; s < 27; ++s) push3(&stk, &nst, &cst, 0, 0, s);
   while (nst > 0) {
     --nst;
     int64_t a = stk[3 * nst], b = stk[3 * nst + 1];
     int s = (int)stk[3 * nst + 2];
-    int cls = kd_classify(c, a, b, s);
+    int cls = kd_classify(c, a, b, s, conventional);
     if (cls == 0) continue;
     if (cls == 1) {
       push3(&c->m2l, &c->nm2l, &c->cap_m2l, a, b, s);
@@ -304,6 +311,11 @@ int orc_kd_traverse(orc_kd *c) {
   free(stk);
   return 0;
 }
+
+int orc_kd_traverse(orc_kd *c) { return kd_walk(c, 0); }
+
+/* The conventional walk: replaces the lists; for interaction counts only. */
+int orc_kd_traverse_conventional(orc_kd *c) { return kd_walk(c, 1); }
 
 /* ------------------------------------------------------------------------ */
 /* FMM passes (Sec. 2.1 order), the same operators as the octree             */

@@ -245,3 +245,50 @@ def test_forces_on_given_lists_equal_the_walk(clustered):
                                a, rtol=0, atol=0)
     with pytest.raises(RuntimeError):
         f.forces_given_lists(np.array([[0, 10 ** 9, 13]]), m2l)
+
+
+@pytest.mark.parametrize("theta,leaf", [(0.5, 4), (0.7, 1), (0.3, 8)])
+def test_conventional_lists_cover_every_particle_pair_exactly_once(theta, leaf):
+    """The conventional FMM's walk on the k-d tree (Sec. 3): the opening-angle test
+    alone from (root, root) of the primary box covers every ordered particle pair,
+    a particle with itself included, exactly once, and every accepted pair passes
+    the test."""
+    n = 300
+    pos, mass = W.nfw_clustered(n, 4, 0.6, 70 + leaf)
+    f = _kd(leaf, theta=theta)
+    f.build_tree(pos, mass)
+    f.traverse(conventional=True)
+    nodes, boxes, perm = f.tree()
+    p2p, m2l = f.lists()
+    assert len(m2l) > 0 and len(p2p) > 0
+    assert (p2p[:, 2] == 13).all() and (m2l[:, 2] == 13).all()
+    cov = np.zeros((n, n), dtype=np.int64)
+    for lst in (p2p, m2l):
+        for a, b, _ in lst:
+            cov[np.ix_(perm[nodes[a, 1]:nodes[a, 1] + nodes[a, 2]], perm[nodes[b, 1]:nodes[b, 1] + nodes[b, 2]])] += 1
+    assert (cov == 1).all()
+    side = (boxes[:, 3:] - boxes[:, :3]).max(axis=1)
+    c = 0.5 * (boxes[:, :3] + boxes[:, 3:])
+    sc2 = ((c[m2l[:, 1]] - c[m2l[:, 0]]) ** 2).sum(axis=1)
+    wl = np.maximum(side[m2l[:, 0]], side[m2l[:, 1]])
+    assert (wl * wl <= theta * theta * sc2 * (1 + 1e-12)).all() and (sc2 > 0).all()
+    cnt = f.counts()
+    assert cnt["p2p_particle_pairs"] + int((nodes[m2l[:, 0], 2] * nodes[m2l[:, 1], 2]).sum()) == n * n
+
+
+def test_conventional_theta_zero_leaves_only_leaf_pairs_and_hybrid_is_unchanged():
+    pos, mass = W.nfw_clustered(400, 5, 0.6, 99)
+    f = _kd(4, theta=0.0)
+    f.build_tree(pos, mass)
+    f.traverse(conventional=True)
+    p2p, m2l = f.lists()
+    nleaves = int((f.tree()[0][:, 3] < 0).sum())
+    assert len(m2l) == 0 and len(p2p) == nleaves * nleaves
+    g = _kd(4, theta=0.5)
+    g.build_tree(pos, mass)
+    g.traverse()
+    before = [x.copy() for x in g.lists()]
+    g.traverse(conventional=True)
+    g.traverse()
+    for x, y in zip(g.lists(), before):
+        np.testing.assert_array_equal(x, y)
