@@ -158,8 +158,9 @@ typedef struct {
                           one cooperative launch, followed by one read-back (repeated with grown
                           buffers when a list or the frontier outgrew its buffer).  Needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0,
                           split 0 and order <= 6; use_graph and sink_batches are ignored, and
-                          hfmm_interaction_counts, HFMM_EXPORT_KEYS and HFMM_EXPORT_NODES are octree
-                          only (HFMM_EXPORT_KD_NODES and _KD_BOXES describe this tree). */
+                          HFMM_EXPORT_KEYS and HFMM_EXPORT_NODES are octree only
+                          (HFMM_EXPORT_KD_NODES and _KD_BOXES describe this tree).  The conventional
+                          walk of hfmm_interaction_counts uses the same boxes and opening order. */
 } hfmm_params;
 
 /* Counters and timings of the last build_tree / short_range_forces call. */

@@ -655,10 +655,16 @@ int hfmm_interaction_counts(hfmm_ctx *h, int conventional, int64_t *out, void *s
   if (!out) return fail(c, HFMM_ERR_ARG, "null output pointer");
   if (conventional != 0 && conventional != 1) return fail(c, HFMM_ERR_ARG, "conventional must be 0 or 1");
   if (!c.have_tree) return fail(c, HFMM_ERR_STATE, "interaction_counts before build_tree");
-  if (c.prm.tree != 0) return fail(c, HFMM_ERR_ARG, "interaction counts are defined on the octree (tree 0)");
   for (int i = 0; i < 4; ++i) out[i] = 0;
   if (c.n == 0) return HFMM_OK;
   cudaStream_t st = S(stream);
+  if (c.prm.tree == 1) {
+    c.lists_split = false;
+    cudaError_t e = kd_interaction_counts(c, conventional != 0, out, st);
+    if (e == cudaErrorInvalidValue) return fail(c, HFMM_ERR_CAPACITY, "k-d walk: buffers outgrown 16 times");
+    if (e != cudaSuccess) return cuda_fail(c, e, "k-d walk");
+    return HFMM_OK;
+  }
   c.lists_split = false;
   c.count_walk = conventional ? 2 : 1;
   cudaError_t e = traverse(c, st);

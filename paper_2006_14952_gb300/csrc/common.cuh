@@ -490,6 +490,9 @@ cudaError_t p2p_pass_mutual(Ctx &c, float *acc, cudaStream_t st);
 // on it: upward pass, walk, lists grouped by sink, M2L, downward pass, P2P.
 cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t n, cudaStream_t st);
 cudaError_t kd_short_range(Ctx &c, float *acc, cudaStream_t st);
+// The walk alone (hybrid or conventional acceptance) and its counts: M2L pairs, P2P
+// leaf pairs, particle pairs on the P2P list, pairs classified (Sec. 3).
+cudaError_t kd_interaction_counts(Ctx &c, bool conventional, int64_t *out, cudaStream_t st);
 cudaError_t kd_upward(Ctx &c, cudaStream_t st);                // expansions.cu
 cudaError_t kd_downward(Ctx &c, float *acc, cudaStream_t st);  // expansions.cu: L2L, then L2P writing acc
 cudaError_t kd_m2l(Ctx &c, cudaStream_t st);                   // m2l.cu

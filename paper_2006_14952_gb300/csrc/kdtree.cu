@@ -296,6 +296,7 @@ struct WalkRule {
   double L, rc2, theta2;
   float Lf, rc2f, theta2f, dl;  // dl: 16 2^-24 L, the FP32 error bound of a shifted difference
   int rule, size_rule;
+  int conventional;  // 1: the opening-angle test alone (a conventional FMM, Sec. 3), primary box
 };
 
 // 0 skip, 1 M2L, 2 open: the rules of Sec. 2.3 on the boxes (sink a, source b shifted by s L),
@@ -314,8 +315,8 @@ __device__ __forceinline__ int kd_classify64(const KdGeo &G, uint32_t a, uint32_
     sm2 = __dadd_rn(sm2, __dmul_rn(gap, gap));
     sx2 = __dadd_rn(sx2, __dmul_rn(far, far));
   }
-  if (sm2 > R.rc2) return 0;
-  const bool trans = R.rule == 0 ? sc2 > R.rc2 : sx2 > R.rc2;
+  if (!R.conventional && sm2 > R.rc2) return 0;
+  const bool trans = R.conventional ? false : R.rule == 0 ? sc2 > R.rc2 : sx2 > R.rc2;
   const double sa = G.side(a), sb = G.side(b);
   const double wl = R.size_rule == 0 ? sb : (sa > sb ? sa : sb);
   const double lim = __dmul_rn(R.theta2, sc2);  // a pair with theta S_c = 0 is never accepted
@@ -358,14 +359,16 @@ __device__ __forceinline__ int kd_classify(const KdGeo &G, uint32_t a, uint32_t 
   }
   const float dl = R.dl, d2 = 3.f * dl * dl;
   const float erc = 2.f * u * R.rc2f;
-  const float em = 2.f * (2.f * dl * Sm + d2 + 8.f * u * sm2);
-  if (sm2 - em > R.rc2f + erc) return 0;
-  if (sm2 + em >= R.rc2f - erc) return kd_classify64_call(G, a, b, s, R);
   const float ec = 2.f * (2.f * dl * Sc + d2 + 8.f * u * sc2);
-  const float tq = R.rule == 0 ? sc2 : sx2;
-  const float et = R.rule == 0 ? ec : 2.f * (2.f * dl * Sx + d2 + 8.f * u * sx2);
-  if (tq - et > R.rc2f + erc) return 2;
-  if (tq + et >= R.rc2f - erc) return kd_classify64_call(G, a, b, s, R);
+  if (!R.conventional) {
+    const float em = 2.f * (2.f * dl * Sm + d2 + 8.f * u * sm2);
+    if (sm2 - em > R.rc2f + erc) return 0;
+    if (sm2 + em >= R.rc2f - erc) return kd_classify64_call(G, a, b, s, R);
+    const float tq = R.rule == 0 ? sc2 : sx2;
+    const float et = R.rule == 0 ? ec : 2.f * (2.f * dl * Sx + d2 + 8.f * u * sx2);
+    if (tq - et > R.rc2f + erc) return 2;
+    if (tq + et >= R.rc2f - erc) return kd_classify64_call(G, a, b, s, R);
+  }
   if (R.theta2 == 0.0) return 2;
   const float sa = A0.w, sb = B0.w;
   const float wl = R.size_rule == 0 ? sb : fmaxf(sa, sb);
@@ -409,8 +412,9 @@ __global__ void __launch_bounds__(kT, 4) k_kd_walk(uint64_t *__restrict__ fa, ui
   const int lane = threadIdx.x & 31;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gt < 27) fa[gt] = pack_pair(0u, 0u, (uint32_t)gt);
-  unsigned long long nf = 27, pairs = 0;
+  // the root against its 27 nearest images (a conventional walk: against itself only)
+  if (R.conventional ? gt == 0 : gt < 27) fa[gt] = pack_pair(0u, 0u, R.conventional ? 13u : (uint32_t)gt);
+  unsigned long long nf = R.conventional ? 1 : 27, pairs = 0;
   grid.sync();
   for (int level = 0;; ++level) {
     uint64_t *cur = (level & 1) ? fb : fa, *next = (level & 1) ? fa : fb;
@@ -716,7 +720,7 @@ cudaError_t read_u64(Ctx &c, const void *src, uint64_t *out, int count, cudaStre
 KdGeo kd_geo(Ctx &c) { return KdGeo{P<double>(c.kd.geo), P<float>(c.kd.geof), c.kd.cap}; }
 
 // The walk (one cooperative launch, repeated with grown buffers while one is outgrown).
-cudaError_t kd_walk(Ctx &c, cudaStream_t st) {
+cudaError_t kd_walk(Ctx &c, cudaStream_t st, bool conventional = false) {
   KdTree &kd = c.kd;
   const uint64_t nl = (uint64_t)std::max<int64_t>(c.nleaves, 1);
   uint64_t cap_f = std::max<uint64_t>(kd.caps[0], std::max<uint64_t>(1u << 16, 256 * nl));
@@ -742,6 +746,7 @@ cudaError_t kd_walk(Ctx &c, cudaStream_t st) {
   R.dl = (float)std::ldexp(16.0 * R.L, -24);
   R.rule = c.prm.transition_rule;
   R.size_rule = c.prm.size_rule;
+  R.conventional = conventional ? 1 : 0;
   KdGeo G = kd_geo(c);
   int64_t walks = 0;
   uint64_t h[kWalkCtr];
@@ -977,6 +982,25 @@ cudaError_t kd_build_tree(Ctx &c, const double *pos, const float *mass, int64_t 
   if (c.prm.profile & 1) cudaEventRecord(c.ev[2], st);
   c.have_tree = true;
   return cudaGetLastError();
+}
+
+cudaError_t kd_interaction_counts(Ctx &c, bool conventional, int64_t *out, cudaStream_t st) {
+  TRY(kd_walk(c, st, conventional));
+  out[0] = c.nm2l;
+  out[1] = c.np2p;
+  out[2] = 0;
+  out[3] = c.frontier_items;
+  if (c.np2p > 0) {
+    unsigned long long *cnt = P<unsigned long long>(c.kd.ctr) + kWalkCtr + 1;
+    TRY(cudaMemsetAsync(cnt, 0, 8, st));
+    k_kd_list_pairs<<<blocks_for((size_t)c.np2p, kT), kT, 0, st>>>(P<uint64_t>(c.p2p), c.np2p,
+                                                                    P<uint32_t>(c.kd.count), cnt);
+    note_launch();
+    uint64_t pp = 0;
+    TRY(read_u64(c, cnt, &pp, 1, st));
+    out[2] = (int64_t)pp;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t kd_short_range(Ctx &c, float *acc, cudaStream_t st) {

@@ -261,8 +261,6 @@ def test_unsupported_combinations_are_refused():
     for what in ("keys", "nodes"):
         with pytest.raises(hfmm.HfmmError, match="ARG"):
             s.export(what)
-    with pytest.raises(hfmm.HfmmError, match="ARG"):
-        s.interaction_counts()
     o = hfmm.Solver(pm_grid=32)
     o.build_tree(torch.zeros((3, 4), dtype=torch.float64, device="cuda") + 0.5, torch.ones(4, device="cuda"))
     with pytest.raises(hfmm.HfmmError, match="ARG"):
@@ -292,3 +290,28 @@ def test_statistics_counts_of_the_p2p_pairs():
         r2 = (d * d).sum(axis=2)
         useful += int(((r2 > 0) & (r2 < s.rc * s.rc)).sum())
     assert abs(st["p2p_useful_pairs"] - useful) <= max(2, useful // 100000), (st["p2p_useful_pairs"], useful)
+
+
+@pytest.mark.parametrize("theta,leaf", [(0.3, 1), (0.5, 8), (0.7, 32)])
+def test_interaction_counts_bit_exact(theta, leaf):
+    """hfmm_interaction_counts on the k-d tree (Sec. 3): the hybrid and the
+    conventional walk give the oracle's lists (as sorted sets) and counts."""
+    pos, mass = W.nfw_clustered(20000 if leaf > 1 else 5000, 30, 0.7, 29)
+    s, _ = run_gpu(pos, mass, pm_grid=32, theta=theta, leaf_max=leaf, order=2)
+    f = run_oracle(pos, mass, s)
+    for conv in (False, True):
+        c = s.interaction_counts(conventional=conv)
+        f.traverse(conventional=conv)
+        p2p, m2l = f.lists()
+        np.testing.assert_array_equal(sorted_rows(s.export("p2p")), sorted_rows(p2p))
+        np.testing.assert_array_equal(sorted_rows(s.export("m2l")), sorted_rows(m2l))
+        ref = f.counts()
+        assert (c["m2l"], c["p2p"], c["p2p_particle_pairs"]) == (ref["m2l"], ref["p2p"], ref["p2p_particle_pairs"])
+        if conv:
+            nodes = f.tree()[0]
+            assert c["p2p_particle_pairs"] + int((nodes[m2l[:, 0], 2] * nodes[m2l[:, 1], 2]).sum()) == len(mass) ** 2
+    # the forces afterwards walk again with the hybrid rules
+    acc = s.short_range_forces().cpu().numpy().astype(np.float64)
+    f2 = run_oracle(pos, mass, s)
+    assert_forces_close(acc, f2.forces())
+    assert s.get_stats()["nm2l"] == f2.size("m2l")
