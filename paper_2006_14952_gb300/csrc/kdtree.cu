@@ -511,7 +511,7 @@ __global__ void k_kd_csr(const uint64_t *__restrict__ lst, int64_t n, uint32_t *
 }
 
 // ------------------------------------------------------------------ P2P
-// One warp per sink leaf (grid-stride over the leaves): sinks i = first + lane and
+// One warp per sink leaf (the leaves heaviest first, taken from a counter): sinks i = first + lane and
 // first + lane + 32.  The list entries come in windows of 32, one per lane, each
 // lane forming its entry's source-box offset from the sink box centre in FP64
 // (once per entry: this GPU's FP64 rate is low); each entry's sources are held in
@@ -529,15 +529,20 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
                                                const uint32_t *__restrict__ end, const uint64_t *__restrict__ lst,
                                                const float4 *__restrict__ pm4, const uint32_t *__restrict__ perm,
                                                int64_t n, double L, PairFit2 fit, float G, float *__restrict__ acc,
-                                               unsigned long long *__restrict__ useful) {
+                                               unsigned long long *__restrict__ useful,
+                                               unsigned long long *__restrict__ next) {
   __shared__ __align__(16) float sx[kT / 32][kKdStage + 2], sy[kT / 32][kKdStage + 2], sz[kT / 32][kKdStage + 2],
       sw[kT / 32][kKdStage + 2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float *X = sx[wid], *Y = sy[wid], *Z = sz[wid], *Wm = sw[wid];
   const float rc2_cull = fit.rc2 * (1.f + 1.f / 4096.f);  // far above the FP32 rounding of either distance
-  const int64_t nw = (int64_t)gridDim.x * (kT / 32);
   uint32_t n_in = 0;
-  for (int64_t t = (int64_t)blockIdx.x * (kT / 32) + wid; t < nl; t += nw) {
+  for (;;) {
+    // the next leaf of the heaviest-first order (each leaf's sums stay its own warp's)
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(next, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if ((int64_t)t >= nl) break;
     const uint32_t k = leaves[t];
     const uint32_t f = first[k], m = count[k];
     const uint32_t tb = beg[k], te = end[k];
@@ -693,6 +698,18 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
   }
 }
 
+// Sort keys of the sink leaves, heaviest first: the complement of entries x sinks (40 bits).
+__global__ void k_kd_work(const uint32_t *__restrict__ leaves, int64_t nl, const uint32_t *__restrict__ count,
+                          const uint32_t *__restrict__ beg, const uint32_t *__restrict__ end,
+                          uint64_t *__restrict__ key, uint32_t *__restrict__ val) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const uint32_t k = leaves[t];
+  const uint64_t w = (uint64_t)(end[k] - beg[k]) * count[k];
+  key[t] = (~w) & ((1ull << 40) - 1ull);
+  val[t] = k;
+}
+
 // Particle pairs on the P2P list: sum over entries of n_sink n_source.
 __global__ void k_kd_list_pairs(const uint64_t *__restrict__ lst, int64_t n, const uint32_t *__restrict__ count,
                                 unsigned long long *__restrict__ out) {
@@ -832,18 +849,30 @@ cudaError_t kd_p2p(Ctx &c, float *acc, cudaStream_t st) {
   TRY(cudaGetDevice(&dev));
   TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const unsigned g = (unsigned)std::min<int64_t>((c.nleaves + 7) / 8, (int64_t)nsm * 8);
+  // the sink leaves heaviest first (stable: equal work keeps the leaf order), taken from a counter
+  const size_t nl = (size_t)c.nleaves;
+  TRY(ensure(c.lpt_tmp, nl * 24 + 64));
+  uint64_t *key = P<uint64_t>(c.lpt_tmp), *key2 = key + nl;
+  uint32_t *val = reinterpret_cast<uint32_t *>(key2 + nl), *val2 = val + nl;
+  k_kd_work<<<blocks_for(nl, kT), kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.count),
+                                               P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), key, val);
+  note_launch();
+  bool alt = false;
+  TRY(radix_sort_u64(key, val, key2, val2, nl, 0, 40, &alt, c.tmp, st));
+  const uint32_t *order = alt ? val2 : val;
+  unsigned long long *next = P<unsigned long long>(c.kd.ctr) + kWalkCtr + 2;
+  TRY(cudaMemsetAsync(next, 0, 8, st));
   unsigned long long *useful = P<unsigned long long>(c.d_small) + 4;  // the statistics counter of stats
   if (c.prm.profile & 2)
-    k_kd_p2p<true><<<g, kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.first),
-                                     P<uint32_t>(c.kd.count), kd_geo(c), P<uint32_t>(c.p2p_beg),
-                                     P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4),
-                                     P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G, acc, useful);
+    k_kd_p2p<true><<<g, kT, 0, st>>>(order, c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count),
+                                     kd_geo(c), P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end),
+                                     P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, c.prm.box,
+                                     pair_fit2(c), (float)c.prm.G, acc, useful, next);
   else
-    k_kd_p2p<false><<<g, kT, 0, st>>>(P<uint32_t>(c.leaves), c.nleaves, P<uint32_t>(c.kd.first),
-                                      P<uint32_t>(c.kd.count), kd_geo(c), P<uint32_t>(c.p2p_beg),
-                                      P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4),
-                                      P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G, acc,
-                                      useful);
+    k_kd_p2p<false><<<g, kT, 0, st>>>(order, c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count),
+                                      kd_geo(c), P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end),
+                                      P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, c.prm.box,
+                                      pair_fit2(c), (float)c.prm.G, acc, useful, next);
   note_launch();
   return cudaGetLastError();
 }
