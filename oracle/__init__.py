@@ -111,6 +111,7 @@ def lib():
             L.orc_kd_destroy.argtypes = [P]
             L.orc_kd_build.argtypes = [P, i64, P, P]
             L.orc_kd_traverse.argtypes = [P]
+            L.orc_kd_set_split.argtypes = [P, i32]
             L.orc_kd_traverse_conventional.argtypes = [P]
             L.orc_kd_upward.argtypes = [P]
             L.orc_kd_m2l_pass.argtypes = [P]
@@ -448,10 +449,12 @@ class KdFMM:
     particles' bounding box, boxes as cell geometry (the readings are in orc_kd.c)."""
 
     def __init__(self, box=1.0, rs=None, rc=None, G=1.0, theta=0.5, order=4, leaf_max=16,
-                 transition_rule=1, size_rule=1):
+                 transition_rule=1, size_rule=1, split="gauss"):
         self._c = lib().orc_kd_create(box, rs, rc, G, theta, order, leaf_max, transition_rule, size_rule)
         if not self._c:
             raise ValueError("invalid oracle parameters")
+        _check(lib().orc_kd_set_split(self._c, SPLITS[split]), "kd_set_split")
+        self.split = split
         self.box, self.rs, self.rc, self.G, self.theta = box, rs, rc, G, theta
         self.order, self.leaf_max, self.rule, self.size_rule = order, leaf_max, transition_rule, size_rule
         self.n = 0

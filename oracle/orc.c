@@ -256,6 +256,12 @@ int orc_m2l(const double *M, const double *R, double rs, int p, double *L) {
   return m2l_k(M, R, &K, p, L);
 }
 
+/* The same for the kernel of a given split (0 Gaussian with rs, 1 polynomial with rc). */
+int orc_m2l_split(const double *M, const double *R, double rs, double rc, int split, int p, double *L) {
+  const orc_kernel K = {rs, rc, split};
+  return m2l_k(M, R, &K, p, L);
+}
+
 /* Eq. l2l: L_n(z + x) = sum_{|m| <= p-|n|} x^m / m! L_{m+n}(z).  Lout is overwritten. */
 int orc_l2l(const double *Lin, const double *x, int p, double *Lout) {
   int nc = orc_ncoef(p);

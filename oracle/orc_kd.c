@@ -36,7 +36,8 @@
  *   - the walk opens the cell of larger side (both on equal sides; the other
  *     one when a cell is a leaf), like the octree walk opens the cell of lower
  *     level.
- * The short-range kernel is the Gaussian one of Sec. 2.2.
+ * The short-range kernel is the Gaussian one of Sec. 2.2, or (orc_kd_set_split) the
+ * polynomial truncation that Sec. 5 allows in its place (the reading of orc.c).
  */
 #include <math.h>
 #include <stdint.h>
@@ -47,10 +48,11 @@
 int orc_ncoef(int p);
 int orc_p2m(int64_t n, const double *x, const double *mu, const double *z, int p, double *M);
 int orc_m2m(const double *Min, const double *x, int p, double *Mout);
-int orc_m2l(const double *M, const double *R, double rs, int p, double *L);
+int orc_m2l_split(const double *M, const double *R, double rs, double rc, int split, int p, double *L);
 int orc_l2l(const double *Lin, const double *x, int p, double *Lout);
 int orc_l2p(const double *L, const double *u, int p, double G, double *phi, double *acc);
 int orc_prefactors(double r, double rs, int p, double *f);
+int orc_prefactors_poly(double r, double rc, int p, double *f);
 
 #define KD_PMAX 10
 #define KD_NCMAX 286
@@ -59,6 +61,7 @@ int orc_prefactors(double r, double rs, int p, double *f);
 typedef struct {
   double box, rs, rc, G, theta;
   int p, leaf_max, rule, size_rule;
+  int split; /* short-range kernel: 0 Gaussian (Sec. 2.2), 1 polynomial (Sec. 5) */
   int64_t n;
   double *x;     /* [n][3] wrapped positions in tree order */
   double *m;     /* [n] */
@@ -91,6 +94,13 @@ orc_kd *orc_kd_create(double box, double rs, double rc, double G, double theta, 
   c->box = box; c->rs = rs; c->rc = rc; c->G = G; c->theta = theta;
   c->p = p; c->leaf_max = leaf_max; c->rule = rule; c->size_rule = size_rule;
   return c;
+}
+
+/* Short-range kernel of the FMM and its pair force: 0 Gaussian, 1 polynomial (Sec. 5). */
+int orc_kd_set_split(orc_kd *c, int split) {
+  if (!c || split < 0 || split > 1) return -1;
+  c->split = split;
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -387,7 +397,7 @@ int orc_kd_m2l_pass(orc_kd *c) {
       kd_centre(c, b, zb);
       kd_shift((int)c->m2l[3 * t + 2], c->box, sv);
       for (int d = 0; d < 3; ++d) R[d] = za[d] - (zb[d] + sv[d]);
-      orc_m2l(c->M + b * nc, R, c->rs, c->p, c->L + a * nc);
+      orc_m2l_split(c->M + b * nc, R, c->rs, c->rc, c->split, c->p, c->L + a * nc);
     }
   }
   free(off);
@@ -443,7 +453,10 @@ int orc_kd_p2p_pass(orc_kd *c, double *acc_tree) {
           double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
           if (!(r2 > 0.0) || !(r2 < rc2)) continue;
           double f[2];
-          orc_prefactors(sqrt(r2), c->rs, 1, f);
+          if (c->split == 1)
+            orc_prefactors_poly(sqrt(r2), c->rc, 1, f);
+          else
+            orc_prefactors(sqrt(r2), c->rs, 1, f);
           for (int k = 0; k < 3; ++k) acc[k] += c->m[j] * f[1] * d[k];
         }
         for (int k = 0; k < 3; ++k) acc_tree[3 * i + k] += c->G * acc[k];

@@ -292,3 +292,19 @@ def test_conventional_theta_zero_leaves_only_leaf_pairs_and_hybrid_is_unchanged(
     g.traverse()
     for x, y in zip(g.lists(), before):
         np.testing.assert_array_equal(x, y)
+
+
+def test_polynomial_split_theta_zero_is_its_direct_sum_and_converges():
+    """The k-d FMM with the polynomial truncation of Sec. 5: theta = 0 gives that
+    split's direct truncated sum, and its error falls with the order."""
+    pos, mass = W.nfw_clustered(6000, 12, 0.7, 100)
+    ref = oracle.direct_sr(pos, mass, 1.0, RS, RC, split="poly")
+    f = oracle.KdFMM(box=1.0, rs=RS, rc=RC, theta=0.0, order=4, leaf_max=16, split="poly")
+    f.build_tree(pos, mass)
+    assert _err(f.forces(), ref) < 1e-13
+    errs = []
+    for p in (2, 4, 6):
+        g = oracle.KdFMM(box=1.0, rs=RS, rc=RC, theta=0.35, order=p, leaf_max=16, split="poly")
+        g.build_tree(pos, mass)
+        errs.append(_err(g.forces(), ref))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 1e-5 and errs[0] > 1e-8, errs
