@@ -156,8 +156,9 @@ typedef struct {
                           theta S_c = 0 is never accepted), the walk opening the node of larger side.
                           hfmm_build_tree synchronises `stream` once (the level extents); the walk is
                           one cooperative launch, followed by one read-back (repeated with grown
-                          buffers when a list or the frontier outgrew its buffer).  Needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0,
-                          split 0 and order <= 6; use_graph and sink_batches are ignored, and
+                          buffers when a list or the frontier outgrew its buffer).  Needs mac_mode 0,
+                          m2l_precision 0, m2l_tables 0, p2p_mutual 0 and order <= 6 (either split);
+                          use_graph and sink_batches are ignored, and
                           HFMM_EXPORT_KEYS and HFMM_EXPORT_NODES are octree only
                           (HFMM_EXPORT_KD_NODES and _KD_BOXES describe this tree).  The conventional
                           walk of hfmm_interaction_counts uses the same boxes and opening order. */

@@ -61,9 +61,8 @@ bool valid_params(const hfmm_params &p, std::string &why) {
     return why = "p2p_mutual 1 needs mac_mode 0 and size_rule 1", false;
   if (p.tree != 0 && p.tree != 1) return why = "tree must be 0 (Morton octree) or 1 (ORB / k-d tree)", false;
   if (p.tree == 1 && (p.mac_mode != 0 || p.m2l_precision != 0 || p.m2l_tables != 0 || p.p2p_mutual != 0 ||
-                      p.split != 0 || p.order > 6))
-    return why = "tree 1 needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0, split 0 and order <= 6",
-           false;
+                      p.order > 6))
+    return why = "tree 1 needs mac_mode 0, m2l_precision 0, m2l_tables 0, p2p_mutual 0 and order <= 6", false;
   double rs = p.rs_cells * (p.box / (double)p.pm_grid);
   double rc = p.rcut_rs * rs;
   if (!(rc < 0.5 * p.box)) return why = "cut-off radius must be below half the box", false;

@@ -522,7 +522,8 @@ __global__ void k_kd_csr(const uint64_t *__restrict__ lst, int64_t n, uint32_t *
 constexpr int kKdStage = 64;
 
 // kCount (statistics runs): also count the pairs inside (0, R_c) into *useful.
-template <bool kCount>
+// kSplit: 0 the Gaussian pair force of Sec. 2.2, 1 the polynomial one of Sec. 5.
+template <bool kCount, int kSplit>
 __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leaves, int64_t nl,
                                                const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
                                                KdGeo Gm, const uint32_t *__restrict__ beg,
@@ -649,12 +650,18 @@ __global__ void __launch_bounds__(kT) k_kd_p2p(const uint32_t *__restrict__ leav
         // outside (0, R_c) the values below may be inf / NaN; the selects discard them
         const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
         const float2 r3 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
-        const float2 u = __ffma2_rn(r2, ri, fit.nrmid);  // r - R_c / 2
-        float2 qv = fit.c[9];
+        float2 fs;
+        if constexpr (kSplit == 1) {
+          // m (1/r^3 - 5 / (2 R_c^3) + 3 r^2 / (2 R_c^5))
+          fs = __fmul2_rn(__fadd2_rn(r3, __ffma2_rn(r2, fit.pc1, fit.pc0)), w);
+        } else {
+          const float2 u = __ffma2_rn(r2, ri, fit.nrmid);  // r - R_c / 2
+          float2 qv = fit.c[9];
 #pragma unroll
-        for (int i = 8; i >= 0; --i) qv = __ffma2_rn(qv, u, fit.c[i]);
-        const float2 ea = __fmul2_rn(r2, fit.kexp);
-        float2 fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv), r3), w);
+          for (int i = 8; i >= 0; --i) qv = __ffma2_rn(qv, u, fit.c[i]);
+          const float2 ea = __fmul2_rn(r2, fit.kexp);
+          fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(exp2_mufu(ea.x), exp2_mufu(ea.y)), qv), r3), w);
+        }
         fs.x = in0 ? fs.x : 0.f;
         fs.y = in1 ? fs.y : 0.f;
         ax = __ffma2_rn(fs, dx, ax);
@@ -863,16 +870,16 @@ cudaError_t kd_p2p(Ctx &c, float *acc, cudaStream_t st) {
   unsigned long long *next = P<unsigned long long>(c.kd.ctr) + kWalkCtr + 2;
   TRY(cudaMemsetAsync(next, 0, 8, st));
   unsigned long long *useful = P<unsigned long long>(c.d_small) + 4;  // the statistics counter of stats
-  if (c.prm.profile & 2)
-    k_kd_p2p<true><<<g, kT, 0, st>>>(order, c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count),
-                                     kd_geo(c), P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end),
-                                     P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, c.prm.box,
-                                     pair_fit2(c), (float)c.prm.G, acc, useful, next);
+  auto run = [&](auto kernel) {
+    kernel<<<g, kT, 0, st>>>(order, c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count), kd_geo(c),
+                             P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end), P<uint64_t>(c.p2p), P<float4>(c.pm4),
+                             P<uint32_t>(c.idx), c.n, c.prm.box, pair_fit2(c), (float)c.prm.G, acc, useful, next);
+  };
+  const bool count_pairs = (c.prm.profile & 2) != 0, poly = c.prm.split == 1;
+  if (count_pairs)
+    poly ? run(k_kd_p2p<true, 1>) : run(k_kd_p2p<true, 0>);
   else
-    k_kd_p2p<false><<<g, kT, 0, st>>>(order, c.nleaves, P<uint32_t>(c.kd.first), P<uint32_t>(c.kd.count),
-                                      kd_geo(c), P<uint32_t>(c.p2p_beg), P<uint32_t>(c.p2p_end),
-                                      P<uint64_t>(c.p2p), P<float4>(c.pm4), P<uint32_t>(c.idx), c.n, c.prm.box,
-                                      pair_fit2(c), (float)c.prm.G, acc, useful, next);
+    poly ? run(k_kd_p2p<false, 1>) : run(k_kd_p2p<false, 0>);
   note_launch();
   return cudaGetLastError();
 }

@@ -195,10 +195,10 @@ cudaError_t launch(Ctx &c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// M2L on the k-d tree (tree = 1; orders 1..6): one warp per sink node as in
+// M2L on the k-d tree (tree = 1; orders 1..6; split S as in k_m2l): one warp per sink node as in
 // k_m2l, with R = c_A - (c_B + s L) formed in FP64 from the box centres and the
 // scales h_A, h_B of the two nodes (powers of two: v / u = h_B / h_A is exact).
-template <int P>
+template <int P, int S>
 __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_kd_m2l(int64_t nn, const double *__restrict__ geo,
                                                                  int64_t cap, const float *__restrict__ hs,
                                                                  const uint32_t *__restrict__ beg,
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_kd_m2l(int64_t nn,
       const float r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
       const float rinv = rsqrtf(r2);
       float f[P + 1];
-      radial_prefactors<P, 0>(r2 * rinv * inv_rs, f);
+      radial_prefactors<P, S>(r2 * rinv * inv_rs, f);
       const float u = hA * rinv;
       float U[P + 1];
       U[0] = u;
@@ -254,20 +254,20 @@ __global__ void __launch_bounds__(128, m2l_min_blocks<P>()) k_kd_m2l(int64_t nn,
   }
 }
 
-template <int P>
+template <int P, int S>
 cudaError_t launch_kd(Ctx &c, cudaStream_t st) {
   unsigned g = blocks_for((size_t)c.nnodes, 4);
   const unsigned cap = 152u * (unsigned)(c.prm.tile_m2l_blocks > 0 ? c.prm.tile_m2l_blocks : 64);
   if (g > cap) g = cap;
   const size_t smem = (size_t)4 * 32 * (ncoef(P) + 1) * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_kd_m2l<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_kd_m2l<P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_kd_m2l<P><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<double>(c.kd.geo), c.kd.cap, hfmm::P<float>(c.kd.hs),
+  k_kd_m2l<P, S><<<g, 128, smem, st>>>(c.nnodes, hfmm::P<double>(c.kd.geo), c.kd.cap, hfmm::P<float>(c.kd.hs),
                                    hfmm::P<uint32_t>(c.m2l_beg), hfmm::P<uint32_t>(c.m2l_end),
                                    hfmm::P<uint64_t>(c.m2l), hfmm::P<float>(c.M), hfmm::P<float>(c.L), c.ldm,
-                                   c.prm.box, (float)(1.0 / c.rs));
+                                   c.prm.box, (float)(1.0 / (S == 1 ? c.rc : c.rs)));
   note_launch();
   return cudaGetLastError();
 }
@@ -276,13 +276,14 @@ cudaError_t launch_kd(Ctx &c, cudaStream_t st) {
 
 cudaError_t kd_m2l(Ctx &c, cudaStream_t st) {
   if (c.nm2l == 0 || c.nnodes == 0) return cudaSuccess;
+  const bool poly = c.prm.split == 1;
   switch (c.p) {
-    case 1: return launch_kd<1>(c, st);
-    case 2: return launch_kd<2>(c, st);
-    case 3: return launch_kd<3>(c, st);
-    case 4: return launch_kd<4>(c, st);
-    case 5: return launch_kd<5>(c, st);
-    case 6: return launch_kd<6>(c, st);
+    case 1: return poly ? launch_kd<1, 1>(c, st) : launch_kd<1, 0>(c, st);
+    case 2: return poly ? launch_kd<2, 1>(c, st) : launch_kd<2, 0>(c, st);
+    case 3: return poly ? launch_kd<3, 1>(c, st) : launch_kd<3, 0>(c, st);
+    case 4: return poly ? launch_kd<4, 1>(c, st) : launch_kd<4, 0>(c, st);
+    case 5: return poly ? launch_kd<5, 1>(c, st) : launch_kd<5, 0>(c, st);
+    case 6: return poly ? launch_kd<6, 1>(c, st) : launch_kd<6, 0>(c, st);
   }
   return cudaErrorInvalidValue;
 }

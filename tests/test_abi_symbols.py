@@ -52,7 +52,7 @@ def test_parameter_validation_needs_no_gpu():
     assert p.tree == 0
     p.tree = 2
     assert L.hfmm_create(ctypes.byref(p), ctypes.byref(h)) == -1 and b"tree" in L.hfmm_last_error(None)
-    for field, value in (("mac_mode", 1), ("m2l_precision", 1), ("m2l_tables", 1), ("split", 1), ("order", 7)):
+    for field, value in (("mac_mode", 1), ("m2l_precision", 1), ("m2l_tables", 1), ("order", 7)):
         p = hfmm.default_params()
         p.tree = 1
         setattr(p, field, value)

@@ -52,7 +52,8 @@ def run_gpu(pos, mass, **kw):
 def run_oracle(pos, mass, s):
     p = s.params
     f = oracle.KdFMM(box=p.box, rs=s.rs, rc=s.rc, G=p.G, theta=p.theta, order=p.order, leaf_max=p.leaf_max,
-                     transition_rule=p.transition_rule, size_rule=p.size_rule)
+                     transition_rule=p.transition_rule, size_rule=p.size_rule,
+                     split="poly" if p.split == 1 else "gauss")
     f.build_tree(pos, np.asarray(mass, dtype=np.float32).astype(np.float64))
     return f
 
@@ -252,7 +253,7 @@ def test_unsupported_combinations_are_refused():
     from paper_2006_14952_gb300 import hfmm
 
     for kw in (dict(mac_mode=1), dict(m2l_precision=1), dict(m2l_tables=1), dict(p2p_mutual=1, size_rule=1),
-               dict(split=1), dict(order=7)):
+               dict(order=7)):
         with pytest.raises(hfmm.HfmmError, match="ARG"):
             solver(**kw)
     with pytest.raises(hfmm.HfmmError, match="ARG"):
@@ -315,3 +316,18 @@ def test_interaction_counts_bit_exact(theta, leaf):
     f2 = run_oracle(pos, mass, s)
     assert_forces_close(acc, f2.forces())
     assert s.get_stats()["nm2l"] == f2.size("m2l")
+
+
+@pytest.mark.parametrize("order,leaf,theta", [(4, 16, 0.5), (6, 48, 0.35)])
+def test_polynomial_split_forces_on_identical_lists(order, leaf, theta):
+    """The polynomial truncation of Sec. 5 (split 1) on the k-d tree: forces
+    against the oracle's k-d FMM in that split (its lists equal the GPU's: the
+    walk does not depend on the split), and theta = 0 against its direct sum."""
+    pos, mass = CASES["nfw-50000"]()
+    s, acc = run_gpu(pos, mass, pm_grid=32, order=order, leaf_max=leaf, theta=theta, split=1)
+    f = run_oracle(pos, mass, s)
+    assert f.split == "poly" and f.size("nodes") == s.get_stats()["nnodes"]
+    print("relative RMS %.3e, per particle %.3e" % assert_forces_close(acc, f.forces()))
+    assert s.get_stats()["nm2l"] == f.size("m2l") > 0
+    s0, acc0 = run_gpu(pos, mass, pm_grid=32, theta=0.0, split=1)
+    assert_forces_close(acc0, oracle.direct_sr(pos, mass, 1.0, s0.rs, s0.rc, split="poly"))
