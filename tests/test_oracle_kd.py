@@ -308,3 +308,21 @@ def test_polynomial_split_theta_zero_is_its_direct_sum_and_converges():
         g.build_tree(pos, mass)
         errs.append(_err(g.forces(), ref))
     assert errs[2] < errs[1] < errs[0] and errs[2] < 1e-5 and errs[0] > 1e-8, errs
+
+
+@pytest.mark.parametrize("box", [0.5, 3.0])
+def test_tree_equals_the_definition_for_other_box_sides(box):
+    """A power-of-two box side and one that is not, with positions outside the
+    box on both sides (the wrap x - L floor(x / L) brings them in)."""
+    pos, mass = W.nfw_clustered(900, 6, 0.7, 104)
+    pos = pos * box
+    pos[:, :50] -= 1.37 * box
+    pos[:, 50:100] += 2.11 * box
+    f = oracle.KdFMM(box=box, rs=RS * box, rc=RC * box, theta=0.5, order=4, leaf_max=8)
+    f.build_tree(pos, mass)
+    nodes, boxes, perm = f.tree()
+    rn, rb, rp = kd_reference(pos, 8, box=box)
+    np.testing.assert_array_equal(nodes, rn)
+    np.testing.assert_array_equal(boxes, rb)
+    np.testing.assert_array_equal(perm, rp)
+    assert (boxes[:, :3] >= 0).all() and (boxes[:, 3:] <= box).all()
