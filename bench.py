@@ -11,7 +11,9 @@ device time (CUDA events on the launching stream); `e2e` repeats the step
 through the host-buffer C entry point with the copies inside the timing.
 `arms` times the metric's other arm on the same set in the same run (learned
 acceptance with the committed network and 3xTF32 tensor-core M2L) and checks
-both against the same FP64 accuracy sinks; `kd_tree` times the ORB / k-d tree
+both against the same FP64 accuracy sinks (their direct sums come from the
+CPU-baseline leg, the one place this arm runs the oracle: it times the direct
+sum on those sinks and on random ones; without it, accuracy is null); `kd_tree` times the ORB / k-d tree
 variant (tree 1) with the same parameters and sinks.  The roofline's FP32 peak is
 measured in the same process by the library's FMA probe.  `--split poly` runs
 the polynomial truncation of Sec. 5 instead (accuracy against its own direct
@@ -184,8 +186,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7, split="gauss"):
-    """Direct FP64 truncated sum (the oracle) on a bounded random sink sample."""
+def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7, split="gauss", fixed_sinks=None):
+    """Direct FP64 truncated sum (the oracle) on a bounded sink sample: the fixed
+    sinks (the accuracy sinks, whose forces are returned as the reference of the
+    accuracy checks) and random ones up to about target_s seconds in all.
+    Returns (the baseline's record, the reference forces [3][len(fixed_sinks)] or None)."""
     import oracle
 
     oracle.build()
@@ -193,15 +198,21 @@ def cpu_oracle_sample(pos, mass, cfg, target_s, seed=7, split="gauss"):
     probe = np.sort(np.random.default_rng(seed).choice(n, size=min(500, n), replace=False))
     t0 = time.perf_counter()
     oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=probe, split=split)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    k = int(min(n, max(500, 500 * target_s / dt)))
+    rate = min(n, 500) / max(time.perf_counter() - t0, 1e-3)  # sinks per second
+    ref, k0, t_fixed = None, 0, 0.0
+    if fixed_sinks is not None and len(fixed_sinks):
+        k0 = len(fixed_sinks)
+        t0 = time.perf_counter()
+        ref = oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=fixed_sinks, split=split)
+        t_fixed = time.perf_counter() - t0
+    k = int(min(n, max(500, rate * max(target_s - t_fixed, 0.0))))
     sinks = np.sort(np.random.default_rng(seed + 1).choice(n, size=k, replace=False))
     t0 = time.perf_counter()
     oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks, split=split)
     dt = time.perf_counter() - t0
-    return {"value": k / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 direct truncated sum (oracle) for {k} random sinks against all {n} sources, "
-                      f"{dt:.1f} s"}
+    return ({"value": (k0 + k) / (t_fixed + dt), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+             "sample": f"FP64 direct truncated sum (oracle) for {k0} fixed (accuracy) and {k} random sinks "
+                       f"against all {n} sources, {t_fixed + dt:.1f} s"}, ref)
 
 
 def run_reference(args, cfg):
@@ -418,16 +429,9 @@ def main():
     sc.close()
     del sc
 
-    # accuracy of this configuration against the FP64 direct sum (rank 0, untimed)
-    accuracy = None
-    sinks = ref = None
-    if rank == 0 and args.accuracy_sinks > 0:
-        import oracle
-
-        oracle.build()
-        sinks = W.subsample(n, args.accuracy_sinks, 2024)
-        ref = oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks, split=args.split)
-        accuracy = accuracy_of(acc, sinks, ref, args.split)
+    # the accuracy sinks: their FP64 direct sums come from the CPU-baseline leg (rank 0,
+    # after the GPU work); each arm keeps its accelerations until then
+    sinks = W.subsample(n, args.accuracy_sinks, 2024) if args.accuracy_sinks > 0 else None
 
     # timed region
     if ws > 1:
@@ -518,17 +522,14 @@ def main():
         l_ms, l_ph, _ = time_arm(hfmm, torch, lcommon, lw, dpos, dmass, lacc, flush, args.steps, args.warmup, stream)
         l_ms_tot = max_over_ranks(sum(l_ms), dev)
         lval = whole_job_rate(ws, n, args.steps, l_ms_tot / 1e3)
-        l_acc = accuracy_of(lacc, sinks, ref) if accuracy is not None else None
         lmean = {k[2:]: round(statistics.mean(p[k] for p in l_ph), 4) for k in keys}
         arms = {"plain": {"path": "geometric acceptance, FP32 CUDA-core M2L", "value": value,
-                          "accuracy": accuracy},
+                          "accuracy": None},
                 "learned_tf32": {"path": f"learned acceptance (committed network, safety bound theta "
                                          f"{args.compare_theta}), 3xTF32 tensor-core M2L",
-                                 "value": lval, "accuracy": l_acc, "breakdown_ms": lmean,
+                                 "value": lval, "accuracy": None, "breakdown_ms": lmean,
                                  "ms_per_step": l_ms_tot / args.steps},
-                "ratio_learned_tf32_over_plain": lval / value,
-                "both_within_1e-4": bool(accuracy and l_acc and accuracy["rms_rel"] <= 1e-4
-                                         and l_acc["rms_rel"] <= 1e-4)}
+                "ratio_learned_tf32_over_plain": lval / value, "both_within_1e-4": None}
 
     # the ORB / k-d tree variant with the same parameters, on the same set and sinks
     kd_arm = None
@@ -553,7 +554,7 @@ def main():
                           "bounding box, box geometry in the acceptance rules, geometric acceptance, FP32 M2L",
                   "value": whole_job_rate(ws, n, args.steps, k_tot / 1e3), "unit": UNIT,
                   "ms_per_step": k_tot / args.steps,
-                  "accuracy": accuracy_of(kacc, sinks, ref) if accuracy is not None else None,
+                  "accuracy": None,
                   "ratio_over_octree": (whole_job_rate(ws, n, args.steps, k_tot / 1e3) / value),
                   "breakdown_ms": kmean, "launches_per_step": k_launch / args.steps,
                   "roofline": {"kernel": "k_kd_p2p (cut-off P2P on the k-d tree)", "bound": "alu",
@@ -581,9 +582,20 @@ def main():
                 "unit": UNIT, "launches_per_step": k_launch, "step_ms": [round(x, 4) for x in k_ms],
                 **({"steps_as_one_graph": k_graphs, "captures": k_caps} if mode else {})}
 
-    cpu = None
+    # the CPU-baseline leg: the oracle's direct sum on a bounded sample that holds the
+    # accuracy sinks, whose forces then check every arm (rank 0 at N = 1, after the GPU work)
+    cpu = accuracy = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(pos, mass, cfg, args.cpu_seconds, split=args.split)
+        cpu, ref = cpu_oracle_sample(pos, mass, cfg, args.cpu_seconds, split=args.split, fixed_sinks=sinks)
+        if ref is not None:
+            accuracy = accuracy_of(acc, sinks, ref, args.split)
+            if arms is not None:
+                l_acc = accuracy_of(lacc, sinks, ref)
+                arms["plain"]["accuracy"] = accuracy
+                arms["learned_tf32"]["accuracy"] = l_acc
+                arms["both_within_1e-4"] = bool(accuracy["rms_rel"] <= 1e-4 and l_acc["rms_rel"] <= 1e-4)
+            if kd_arm is not None:
+                kd_arm["accuracy"] = accuracy_of(kacc, sinks, ref)
 
     if rank == 0:
         line = {
