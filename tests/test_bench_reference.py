@@ -27,3 +27,24 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_leg_returns_the_accuracy_reference():
+    """The CPU-baseline leg times the oracle's direct sum on the accuracy sinks and
+    on random ones, and hands back the accuracy sinks' forces: equal to a direct
+    call on them, and counted in the baseline's sample."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2006_14952_gb300 import workloads as W
+
+    cfg = W.CONFIGS["uniform-32k"]
+    pos, mass = W.make(cfg)
+    sinks = W.subsample(cfg.n, 300, 2024)
+    rec, ref = bench.cpu_oracle_sample(pos, mass, cfg, 0.2, fixed_sinks=sinks)
+    np.testing.assert_array_equal(ref, oracle.direct_sr(pos, mass, cfg.box, cfg.rs, cfg.rc, sinks=sinks))
+    assert rec["kind"] == "oracle" and rec["value"] > 0 and "300 fixed (accuracy)" in rec["sample"]
+    rec2, ref2 = bench.cpu_oracle_sample(pos, mass, cfg, 0.2)
+    assert ref2 is None and "0 fixed" in rec2["sample"]
