@@ -33,10 +33,15 @@
 // appended with warp-aggregated atomics, and when a list or the frontier outgrows
 // its buffer the buffers are grown and the walk repeated.  The lists are then
 // sorted by (sink, source, shift), so every sum after them runs in a fixed order.
-// P2P: one warp per sink leaf, its sinks in lanes (a second sink per lane above
-// 32), each source leaf staged in shared memory as FP32 offsets from the sink
-// box centre (the source box's offset formed in FP64 by one lane), keeping only
-// the sources within R_c of the sink box, two sources per packed FP32x2 step.
+// The same walk with the opening-angle test alone, from the root against itself,
+// is the conventional FMM's of the interaction counts (Sec. 3).
+// P2P: one warp per sink leaf, the leaves taken heaviest first from a counter,
+// its sinks in lanes (a second sink per lane above 32); the list read in windows
+// of 32 entries, each lane forming its entry's source-box offset from the sink
+// box centre in FP64; each entry's sources loaded one entry ahead, kept only
+// within R_c of the sink box, staged in shared memory and evaluated two at a
+// time in packed FP32x2, with the Gaussian (Sec. 2.2) or polynomial (Sec. 5)
+// pair force.
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -400,7 +405,8 @@ __device__ __forceinline__ void warp_append(bool take, uint64_t e, unsigned long
 constexpr int kWalkCtr = 8;
 
 // The whole walk in one cooperative launch: the 27 root pairs (root, root, s) as
-// the first frontier, then level after level with grid-wide barriers between
+// the first frontier (the conventional walk: the root against itself alone),
+// then level after level with grid-wide barriers between
 // them, until the frontier is empty or outgrows its buffer (the caller grows the
 // buffers that were outgrown, the frontier's or a list's, and walks again).
 __global__ void __launch_bounds__(kT, 4) k_kd_walk(uint64_t *__restrict__ fa, uint64_t *__restrict__ fb,
@@ -511,14 +517,15 @@ __global__ void k_kd_csr(const uint64_t *__restrict__ lst, int64_t n, uint32_t *
 }
 
 // ------------------------------------------------------------------ P2P
-// One warp per sink leaf (the leaves heaviest first, taken from a counter): sinks i = first + lane and
-// first + lane + 32.  The list entries come in windows of 32, one per lane, each
+// One warp per sink leaf (the leaves heaviest first, taken from a counter):
+// sinks i = first + lane and first + lane + 32.  The list entries come in windows of 32, one per lane, each
 // lane forming its entry's source-box offset from the sink box centre in FP64
 // (once per entry: this GPU's FP64 rate is low); each entry's sources are held in
 // registers one entry ahead; the sources within R_c of the sink box are staged in
 // shared memory (SoA, padded to an even count with a far, massless source) and
 // each lane evaluates two sources at a time with packed FP32x2 operations: the
-// pair force of Sec. 2.2 with the hard cut-off, added to acc in input order.
+// pair force of Sec. 2.2 (or of Sec. 5) with the hard cut-off, added to acc in
+// input order.
 constexpr int kKdStage = 64;
 
 // kCount (statistics runs): also count the pairs inside (0, R_c) into *useful.
@@ -733,7 +740,7 @@ __global__ void k_kd_list_pairs(const uint64_t *__restrict__ lst, int64_t n, con
     if (e_ != cudaSuccess) return e_; \
   } while (0)
 
-// Read one device uint64 (synchronises st).
+// Read `count` device uint64 values into out (synchronises st).
 cudaError_t read_u64(Ctx &c, const void *src, uint64_t *out, int count, cudaStream_t st) {
   TRY(cudaMemcpyAsync(c.h_pinned, src, 8 * (size_t)count, cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
