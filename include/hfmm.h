@@ -292,7 +292,7 @@ int hfmm_get_stats(hfmm_ctx *ctx, hfmm_stats *out);
  * kernel counts of the truncated FMM against a conventional FMM; the counts
  * depend only on the tree and the acceptance criterion).  Runs the dual-tree
  * walk alone (no expansions, no forces) on the tree of the last
- * hfmm_build_tree, with
+ * hfmm_build_tree (the octree, or with tree = 1 the k-d tree and its boxes), with
  *   conventional = 0: the hybrid acceptance of Sec. 2.3 with the context's
  *     theta, transition_rule and size_rule and geometric decisions (also on a
  *     mac_mode 1 context), from the root against its 27 nearest periodic
